@@ -1,0 +1,395 @@
+"""FP64 CPU oracle of the L1 IRLS + PCG phase-unwrapping method (test infrastructure only).
+
+This is the plain, slow, obviously-correct statement of what the CUDA path computes.  It follows
+the paper's steps in the paper's order and notation, with dense NumPy algebra and no blocking or
+fusion.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` use it.
+
+Notation (Sec. 2):  X is the N x M wrapped phase; U the N x M unwrapped estimate; Gv, Cv, Vv,
+Wv live on the (N-1) x M vertical edges and Gh, Ch, Vh, Wh on the N x (M-1) horizontal edges;
+S is the (N-1) x N forward difference (S U)_{ij} = U_{i+1,j} - U_{ij}; T is the M x (M-1)
+difference with (U T)_{ij} = U_{i,j+1} - U_{ij}.
+
+Readings where the paper is silent or inconsistent (each is repeated in the design notes):
+  * wrap: "mod 2 pi" of a difference is taken as the representative in [-pi, pi), evaluated
+    in float32 as t - 2pi * floor((t + pi) / 2pi) with t = fl32(X1 - X0) and 2pi, pi the float32
+    constants (the wrap decides an integer, so both sides decide it in the same precision);
+  * the linear system is the symmetric one of Prop. (linear system) / eq. (vectorised A, b),
+    not the unscaled U row printed inside Alg. 1;
+  * CG is warm-started from the current IRLS iterate (Alg. 2 leaves the start open);
+  * CG stops when ||r||_2 / ||b||_2 <= cg_tol (full three-block residual) or after cg_max
+    matrix-vector products;
+  * coherence -> edge weights: Cv_ij = (coh_ij + coh_{i+1,j}) / 2, Ch_ij = (coh_ij + coh_{i,j+1}) / 2;
+  * the singular preconditioner uses the pseudo-inverse (zero-frequency DCT coefficient -> 0,
+    Appendix B) and U is shifted to zero mean after every solve (Prop. 'minimising (alt1)');
+  * eps of the library's signature is the smoothing delta of F_delta (Sec. 3.1); tau defaults to
+    the paper's 1e-2 (Sec. 4.4).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "TWO_PI_F32", "PI_F32", "wrap_f32", "wrapped_gradients", "edge_weights",
+    "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
+    "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
+    "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "k_map",
+    "best_shift_error", "dense_operators", "Problem",
+]
+
+TWO_PI_F32 = np.float32(2.0 * np.pi)
+PI_F32 = np.float32(np.pi)
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 2: wrapped phase gradients and weights
+# --------------------------------------------------------------------------------------------
+def wrap_f32(t):
+    """Wrapped value of a float32 phase difference, in [-pi, pi) (Sec. 2, 'mod 2 pi').
+
+    Evaluated in float32, one correctly rounded operation at a time:
+    k = floor((t + pi) / 2pi), result = t - (2pi * k)."""
+    t = np.asarray(t, dtype=np.float32)
+    k = np.floor((t + PI_F32) / TWO_PI_F32).astype(np.float32)
+    prod = (TWO_PI_F32 * k).astype(np.float32)
+    return (t - prod).astype(np.float32)
+
+
+def wrapped_gradients(X):
+    """Gv = wrap(X_{i+1,j} - X_{ij}) ((N-1) x M) and Gh = wrap(X_{i,j+1} - X_{ij}) (N x (M-1)),
+    Sec. 2.  The float32 input difference is formed in float32, then held in float64."""
+    X = np.asarray(X, dtype=np.float32)
+    dv = (X[1:, :] - X[:-1, :]).astype(np.float32)
+    dh = (X[:, 1:] - X[:, :-1]).astype(np.float32)
+    return wrap_f32(dv).astype(np.float64), wrap_f32(dh).astype(np.float64)
+
+
+def edge_weights(coherence, N, M):
+    """Edge weights (Cv, Ch) of problem (main), Sec. 2.  Uniform weights (all ones) when no
+    coherence is given (Sec. 4.4, 'uniform'); otherwise the mean of the two end-pixel
+    coherences of each edge."""
+    if coherence is None:
+        return np.ones((N - 1, M)), np.ones((N, M - 1))
+    c = np.asarray(coherence, dtype=np.float64)
+    return 0.5 * (c[1:, :] + c[:-1, :]), 0.5 * (c[:, 1:] + c[:, :-1])
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 2: difference operators S, T and their transposes (definitions of S_N and T_M)
+# --------------------------------------------------------------------------------------------
+def S_op(U):
+    """(S U)_{ij} = U_{i+1,j} - U_{ij}, S in R^{(N-1) x N}."""
+    return U[1:, :] - U[:-1, :]
+
+
+def St_op(Y, N):
+    """S^T Y for Y of shape (N-1) x M: (S^T Y)_i = Y_{i-1} [i >= 1] - Y_i [i <= N-2]."""
+    out = np.zeros((N, Y.shape[1]))
+    out[1:, :] += Y
+    out[:-1, :] -= Y
+    return out
+
+
+def T_op(U):
+    """(U T)_{ij} = U_{i,j+1} - U_{ij}, T in R^{M x (M-1)}."""
+    return U[:, 1:] - U[:, :-1]
+
+
+def Tt_op(Y, M):
+    """Y T^T for Y of shape N x (M-1): (Y T^T)_{:,j} = Y_{:,j-1} [j >= 1] - Y_{:,j} [j <= M-2]."""
+    out = np.zeros((Y.shape[0], M))
+    out[:, 1:] += Y
+    out[:, :-1] -= Y
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 3.1 / 3.2: reweighting, linear system, right-hand side
+# --------------------------------------------------------------------------------------------
+def reweight(Vv, Vh, Cv, Ch, delta):
+    """Closed-form weight update W = sqrt(C^2 V^2 + delta^2) (Sec. 3.1, Alg. 1)."""
+    return np.sqrt(Cv * Cv * Vv * Vv + delta * delta), np.sqrt(Ch * Ch * Vh * Vh + delta * delta)
+
+
+def diag_d(Cv, Ch, Wv, Wh):
+    """Diagonal blocks Dv = C^2 / W, Dh = C^2 / W of the vectorised matrix A (Sec. 3.2)."""
+    return Cv * Cv / Wv, Ch * Ch / Wh
+
+
+def rhs_b(Gv, Gh, tau):
+    """b = (B1, B2, B3) with B1 = (S^T Gv + Gh T^T) / tau, B2 = -Gv / tau, B3 = -Gh / tau
+    (Sec. 3.2, definition of B1, B2, B3)."""
+    N, M = Gh.shape[0], Gv.shape[1]
+    return ((St_op(Gv, N) + Tt_op(Gh, M)) / tau, -Gv / tau, -Gh / tau)
+
+
+def apply_A(x, dv, dh, tau):
+    """Left-hand side of the linear system (Prop. 'linear system', Sec. 3.1):
+
+        q_U  = (S^T S U + U T T^T - S^T Vv - Vh T^T) / tau
+        q_Vv = Dv o Vv + (Vv - S U) / tau
+        q_Vh = Dh o Vh + (Vh - U T) / tau
+    """
+    U, Vv, Vh = x
+    N, M = U.shape
+    SU, UT = S_op(U), T_op(U)
+    qU = (St_op(SU, N) + Tt_op(UT, M) - St_op(Vv, N) - Tt_op(Vh, M)) / tau
+    qVv = dv * Vv + (Vv - SU) / tau
+    qVh = dh * Vh + (Vh - UT) / tau
+    return (qU, qVv, qVh)
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 3.3: block-diagonal preconditioner, Sylvester block by eigendecomposition
+# --------------------------------------------------------------------------------------------
+def dct_basis(N):
+    """Eigendecomposition S^T S = P diag(lam) P^T of the 1-D Neumann Laplacian (Sec. 3.3).
+
+    Closed form (orthonormal DCT-II vectors): P[i, k] = c_k cos(pi k (i + 1/2) / N),
+    c_0 = sqrt(1/N), c_k = sqrt(2/N); lam_k = 2 - 2 cos(pi k / N).  Built with plain loops."""
+    P = np.empty((N, N))
+    lam = np.empty(N)
+    for k in range(N):
+        ck = math.sqrt(1.0 / N) if k == 0 else math.sqrt(2.0 / N)
+        lam[k] = 2.0 - 2.0 * math.cos(math.pi * k / N)
+        for i in range(N):
+            P[i, k] = ck * math.cos(math.pi * k * (i + 0.5) / N)
+    return P, lam
+
+
+def precond_apply(r, dv, dh, tau, basis_N, basis_M):
+    """z = D^+ r for the block-diagonal preconditioner D (Sec. 3.3).
+
+    U block: solve S^T S Z + Z T T^T = tau R by Z = P_S [(P_S^T tau R P_T) / (lam_i + mu_j)] P_T^T,
+    with the zero-frequency coefficient set to 0 (the pseudo-inverse choice of Appendix B).
+    V blocks: z = r / (D + 1/tau)."""
+    rU, rVv, rVh = r
+    PN, lamN = basis_N
+    PM, lamM = basis_M
+    Y = PN.T @ (tau * rU) @ PM
+    den = lamN[:, None] + lamM[None, :]
+    Zp = np.zeros_like(Y)
+    nz = den > 0
+    nz[0, 0] = False
+    Zp[nz] = Y[nz] / den[nz]
+    zU = PN @ Zp @ PM.T
+    return (zU, rVv / (dv + 1.0 / tau), rVh / (dh + 1.0 / tau))
+
+
+# --------------------------------------------------------------------------------------------
+# Alg. 2: preconditioned conjugate gradient
+# --------------------------------------------------------------------------------------------
+def _dot(a, b):
+    return float(sum(np.vdot(x, y) for x, y in zip(a, b)))
+
+
+def _axpy(alpha, x, y):
+    return tuple(yi + alpha * xi for xi, yi in zip(x, y))
+
+
+def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr"):
+    """Preconditioned CG (Alg. 2) on A x = b from the warm start x0.
+
+    Stops when ||r|| / ||b|| <= tol or after cg_max products with A.  ``beta_rule`` 'fr' is the
+    Fletcher-Reeves ratio printed in Alg. 2; 'pr' is the Polak-Ribiere (flexible) ratio
+    r_{l+1}^T (z_{l+1} - z_l) / rho_l, which equals it in exact arithmetic.
+    Returns (x, iterations, final relative residual, status); status -5 flags a breakdown."""
+    x = tuple(np.array(a, dtype=np.float64) for a in x0)
+    bnorm = math.sqrt(_dot(b, b))
+    r = tuple(bi - qi for bi, qi in zip(b, apply_A(x, dv, dh, tau)))
+    rel = math.sqrt(_dot(r, r)) / bnorm if bnorm > 0 else 0.0
+    if bnorm == 0.0 or rel <= tol or cg_max <= 0:
+        return x, 0, rel, 0
+    z = precond_apply(r, dv, dh, tau, basis_N, basis_M)
+    p = z
+    rho = _dot(r, z)
+    it = 0
+    while True:
+        q = apply_A(p, dv, dh, tau)
+        pq = _dot(p, q)
+        if not (pq > 0.0 and rho > 0.0):
+            return x, it, rel, -5
+        alpha = rho / pq
+        x = _axpy(alpha, p, x)
+        r = _axpy(-alpha, q, r)
+        it += 1
+        rel = math.sqrt(_dot(r, r)) / bnorm
+        if rel <= tol or it >= cg_max:
+            return x, it, rel, 0
+        z_new = precond_apply(r, dv, dh, tau, basis_N, basis_M)
+        rho_new = _dot(r, z_new)
+        if beta_rule == "pr":
+            beta = (rho_new - _dot(r, z)) / rho
+        else:
+            beta = rho_new / rho
+        rho = rho_new
+        z = z_new
+        p = tuple(zi + beta * pi for zi, pi in zip(z_new, p))
+
+
+# --------------------------------------------------------------------------------------------
+# Objectives: problem (main), F (soft constraints), F_delta, H_delta (problem alt1)
+# --------------------------------------------------------------------------------------------
+def l1_objective(U, Gv, Gh, Cv, Ch):
+    """sum Cv |U_{i+1,j} - U_{ij} - Gv| + sum Ch |U_{i,j+1} - U_{ij} - Gh| (problem (main), Sec. 2)."""
+    return float(np.sum(Cv * np.abs(S_op(U) - Gv)) + np.sum(Ch * np.abs(T_op(U) - Gh)))
+
+
+def _penalty(U, Vv, Vh, Gv, Gh, tau):
+    return (float(np.sum((S_op(U) - Gv - Vv) ** 2)) + float(np.sum((T_op(U) - Gh - Vh) ** 2))) / (2 * tau)
+
+
+def F_value(U, Vv, Vh, Gv, Gh, Cv, Ch, tau):
+    """F of problem (soft constraints), Sec. 3.1."""
+    return float(np.sum(Cv * np.abs(Vv)) + np.sum(Ch * np.abs(Vh))) + _penalty(U, Vv, Vh, Gv, Gh, tau)
+
+
+def F_delta_value(U, Vv, Vh, Gv, Gh, Cv, Ch, tau, delta):
+    """F_delta, Sec. 3.1 (the delta-smoothed F)."""
+    s = float(np.sum(np.sqrt(Cv * Cv * Vv * Vv + delta * delta))
+              + np.sum(np.sqrt(Ch * Ch * Vh * Vh + delta * delta)))
+    return s + _penalty(U, Vv, Vh, Gv, Gh, tau)
+
+
+def H_delta_value(U, Vv, Vh, Wv, Wh, Gv, Gh, Cv, Ch, tau, delta):
+    """Objective of problem (alt1), Sec. 3.1: 1/2 sum [(C^2 V^2 + delta^2) / W + W] + penalties."""
+    s = 0.5 * float(np.sum((Cv * Cv * Vv * Vv + delta * delta) / Wv + Wv)
+                    + np.sum((Ch * Ch * Vh * Vh + delta * delta) / Wh + Wh))
+    return s + _penalty(U, Vv, Vh, Gv, Gh, tau)
+
+
+def smoothness_L(Cv, Ch, tau, delta):
+    """L = 12 / tau + C_max^2 / delta (Theorem on the sublinear rate, Sec. 3.1)."""
+    cmax = max(float(np.max(Cv, initial=0.0)), float(np.max(Ch, initial=0.0)))
+    return 12.0 / tau + cmax * cmax / delta
+
+
+def gradient_candidate(U, Vv, Vh, Wv, Wh, Gv, Gh, Cv, Ch, tau, delta):
+    """One gradient step of length 1/L on (U, Vv, Vh) at fixed W: the candidate of the
+    sufficient-decrease condition (Theorem on the sublinear rate, Sec. 3.1)."""
+    N, M = U.shape
+    L = smoothness_L(Cv, Ch, tau, delta)
+    Ev = S_op(U) - Gv - Vv
+    Eh = T_op(U) - Gh - Vh
+    Ut = U - (St_op(Ev, N) + Tt_op(Eh, M)) / (tau * L)
+    Vvt = Vv - (Cv * Cv / Wv * Vv + (Vv - S_op(U) + Gv) / tau) / L
+    Vht = Vh - (Ch * Ch / Wh * Vh + (Vh - T_op(U) + Gh) / tau) / L
+    return Ut, Vvt, Vht
+
+
+# --------------------------------------------------------------------------------------------
+# Alg. 1: IRLS
+# --------------------------------------------------------------------------------------------
+class Problem:
+    """Inputs of Alg. 1 for one image: G, C, b and the two DCT bases."""
+
+    def __init__(self, X, coherence=None, Cv=None, Ch=None, tau=1e-2):
+        X = np.asarray(X, dtype=np.float32)
+        self.N, self.M = X.shape
+        self.tau = float(tau)
+        self.Gv, self.Gh = wrapped_gradients(X)
+        if Cv is None or Ch is None:
+            Cv, Ch = edge_weights(coherence, self.N, self.M)
+        self.Cv = np.asarray(Cv, dtype=np.float64)
+        self.Ch = np.asarray(Ch, dtype=np.float64)
+        self.b = rhs_b(self.Gv, self.Gh, self.tau)
+        self.basis_N = dct_basis(self.N)
+        self.basis_M = self.basis_N if self.M == self.N else dct_basis(self.M)
+
+
+def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
+                cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False):
+    """Alg. 1 with Alg. 2 as the inner solver, for a fixed number of outer iterations.
+
+    Returns a dict with U (zero mean), Vv, Vh, and per-outer statistics: cg_iters, rel_res,
+    l1_obj (problem (main) at U^{k+1}), h_delta (H_delta(x^{k+1}, W^k)), h_before
+    (H_delta(x^k, W^k)), h_after_rw (H_delta(x^{k+1}, W^{k+1})), f_delta, status.  With
+    ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint)."""
+    pb = Problem(X, coherence, Cv, Ch, tau)
+    N, M = pb.N, pb.M
+    if x0 is None:
+        U = np.zeros((N, M))
+        Vv = S_op(U) - pb.Gv          # V^0 = S U^0 - Gv
+        Vh = T_op(U) - pb.Gh
+    else:
+        U, Vv, Vh = (np.array(a, dtype=np.float64) for a in x0)
+    st = {k: [] for k in ("cg_iters", "rel_res", "l1_obj", "h_delta", "h_before", "h_after_rw",
+                          "f_delta")}
+    rec = {"W": [], "x": []}
+    status = 0
+    for k in range(outer_iters):
+        Wv, Wh = reweight(Vv, Vh, pb.Cv, pb.Ch, delta)
+        dv, dh = diag_d(pb.Cv, pb.Ch, Wv, Wh)
+        if record:
+            rec["W"].append((Wv, Wh))
+            rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
+        st["h_before"].append(H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
+        (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
+                                      cg_tol, cg_max, beta_rule)
+        if s < 0:
+            status = s
+        elif it >= cg_max and rel > cg_tol and status == 0:
+            status = 1
+        U = U - U.mean()
+        st["cg_iters"].append(it)
+        st["rel_res"].append(rel)
+        st["h_delta"].append(H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
+        Wv2, Wh2 = reweight(Vv, Vh, pb.Cv, pb.Ch, delta)
+        st["h_after_rw"].append(H_delta_value(U, Vv, Vh, Wv2, Wh2, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
+        st["l1_obj"].append(l1_objective(U, pb.Gv, pb.Gh, pb.Cv, pb.Ch))
+        st["f_delta"].append(F_delta_value(U, Vv, Vh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
+        if s < 0:
+            break
+    out = {"U": U, "Vv": Vv, "Vh": Vh, "status": status, "problem": pb, **st}
+    if record:
+        out["record"] = rec
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 4.5: evaluation helpers
+# --------------------------------------------------------------------------------------------
+def best_shift_error(U, Xu):
+    """E(U, Xu) = Xu - (U + alpha), alpha = mean(Xu - U) (Sec. 4.5)."""
+    alpha = float(np.mean(Xu - U))
+    return Xu - (U + alpha)
+
+
+def k_map(U, X):
+    """Integer ambiguity map of an unwrapped estimate: the global offset c is the circular mean
+    of U - X, then K = round((U - c - X) / 2pi).  The paper's 'rounded IRLS' (Sec. 4.5) is
+    X + 2pi K + c."""
+    X = np.asarray(X, dtype=np.float64)
+    c = float(np.angle(np.sum(np.exp(1j * (U - X)))))
+    return np.rint((U - c - X) / (2.0 * np.pi)).astype(np.int64)
+
+
+# --------------------------------------------------------------------------------------------
+# Appendix A: explicit Kronecker matrices (tiny grids only)
+# --------------------------------------------------------------------------------------------
+def dense_operators(N, M):
+    """Explicit S_N ((N-1) x N) and T_M (M x (M-1)) from their element definitions (Sec. 2),
+    and B = [[I_M (x) S_N, -I, 0], [T_M^T (x) I_N, 0, -I]] (proof of Theorem 'existence').
+    Vectorisation is column-major (vec stacks the columns), as in the paper's notation."""
+    S = np.zeros((N - 1, N))
+    for i in range(N - 1):
+        for j in range(N):
+            if j == i + 1:
+                S[i, j] = 1.0
+            elif j == i:
+                S[i, j] = -1.0
+    T = np.zeros((M, M - 1))
+    for i in range(M):
+        for j in range(M - 1):
+            if i == j + 1:
+                T[i, j] = 1.0
+            elif i == j:
+                T[i, j] = -1.0
+    nv, nh = (N - 1) * M, N * (M - 1)
+    B = np.zeros((nv + nh, N * M + nv + nh))
+    B[:nv, :N * M] = np.kron(np.eye(M), S)
+    B[nv:, :N * M] = np.kron(T.T, np.eye(N))
+    B[:nv, N * M:N * M + nv] = -np.eye(nv)
+    B[nv:, N * M + nv:] = -np.eye(nh)
+    return S, T, B

@@ -1,0 +1,526 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Every check here compares the oracle with something other than itself: explicit Kronecker
+matrices built from the element definitions (Sec. 2, Appendix A), the gradient of the objective
+of problem (alt1) by central differences, the closed-form DCT eigenpairs against a library
+eigensolver, a dense pseudo-inverse, a least-squares solve, an LP solve of problem (main), a
+damped-Newton minimiser of F_delta, the paper's printed Gershgorin figures, and the theorems of
+Sec. 3.1 used as invariants.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import irls as O
+import synthetic
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def vecF(a):
+    """Column-major vectorisation, the paper's vec (Sec. 1, notation)."""
+    return np.asarray(a).flatten(order="F")
+
+
+def pack(x):
+    return np.concatenate([vecF(a) for a in x])
+
+
+def unpack(v, N, M):
+    nu, nv = N * M, (N - 1) * M
+    return (v[:nu].reshape((N, M), order="F"), v[nu:nu + nv].reshape((N - 1, M), order="F"),
+            v[nu + nv:].reshape((N, M - 1), order="F"))
+
+
+def dense_A(N, M, dv, dh, tau):
+    """A of eq. (matrix-soft-constraints), written block by block from the Kronecker forms."""
+    S, T, _ = O.dense_operators(N, M)
+    IN, IM = np.eye(N), np.eye(M)
+    nu, nv, nh = N * M, (N - 1) * M, N * (M - 1)
+    A = np.zeros((nu + nv + nh, nu + nv + nh))
+    A[:nu, :nu] = (np.kron(IM, S.T @ S) + np.kron(T @ T.T, IN)) / tau
+    A[:nu, nu:nu + nv] = -np.kron(IM, S.T) / tau
+    A[:nu, nu + nv:] = -np.kron(T, IN) / tau
+    A[nu:nu + nv, :nu] = -np.kron(IM, S) / tau
+    A[nu:nu + nv, nu:nu + nv] = np.diag(vecF(dv)) + np.eye(nv) / tau
+    A[nu + nv:, :nu] = -np.kron(T.T, IN) / tau
+    A[nu + nv:, nu + nv:] = np.diag(vecF(dh)) + np.eye(nh) / tau
+    return A
+
+
+def rand_state(N, M, rng):
+    U = rng.standard_normal((N, M))
+    Vv = rng.standard_normal((N - 1, M))
+    Vh = rng.standard_normal((N, M - 1))
+    return U, Vv, Vh
+
+
+def rand_problem(N, M, rng, tau=1e-2):
+    X = rng.uniform(-np.pi, np.pi, size=(N, M)).astype(np.float32)
+    coh = rng.uniform(0.05, 1.0, size=(N, M)).astype(np.float32)
+    return O.Problem(X, coh, tau=tau)
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 2: wrap
+# ------------------------------------------------------------------------------------------
+def test_wrap_special_values():
+    two_pi = np.float32(2 * np.pi)
+    t = np.array([0.0, 3.0, -3.0, 4.0, -4.0, 7.0, 10.0], dtype=np.float32)
+    w = O.wrap_f32(t)
+    assert w[0] == 0.0 and w[1] == np.float32(3.0) and w[2] == np.float32(-3.0)
+    np.testing.assert_allclose(w[3], np.float32(4.0) - two_pi, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(w[4], np.float32(-4.0) + two_pi, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(w[5], np.float32(7.0) - two_pi, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(w[6], np.float32(10.0) - 2 * two_pi, rtol=0, atol=2e-6)
+    # the half-open convention: +pi maps to -pi
+    assert O.wrap_f32(np.float32(np.pi)) < 0
+
+
+def test_wrap_range_and_congruence():
+    rng = np.random.default_rng(1)
+    t = rng.uniform(-2 * np.pi, 2 * np.pi, size=100000).astype(np.float32)
+    w = O.wrap_f32(t).astype(np.float64)
+    assert np.all(w >= -np.pi - 1e-6) and np.all(w < np.pi + 1e-6)
+    k = (t.astype(np.float64) - w) / (2 * np.pi)
+    np.testing.assert_allclose(k, np.rint(k), atol=1e-5)
+    # differences that already lie well inside (-pi, pi) are returned unchanged
+    s = rng.uniform(-3.0, 3.0, size=1000).astype(np.float32)
+    assert np.array_equal(O.wrap_f32(s), s)
+
+
+def test_wrapped_gradients_of_wrapped_smooth_phase_are_true_gradients():
+    # Itoh's condition: |true difference| < pi  =>  wrapped difference == true difference
+    X, phi = synthetic.smooth_phase(20, 17, seed=3, max_step=2.0)
+    Gv, Gh = O.wrapped_gradients(X)
+    np.testing.assert_allclose(Gv, np.diff(phi, axis=0), atol=2e-5)
+    np.testing.assert_allclose(Gh, np.diff(phi, axis=1), atol=2e-5)
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 3.2: the matrix A, the right-hand side b, and the gradient of H_delta
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N,M", [(2, 2), (3, 5), (5, 4), (1, 6), (6, 1)])
+def test_matvec_equals_kronecker_matrix(N, M):
+    rng = np.random.default_rng(N * 10 + M)
+    tau = 0.3
+    dv = rng.uniform(0.1, 5.0, size=(N - 1, M))
+    dh = rng.uniform(0.1, 5.0, size=(N, M - 1))
+    A = dense_A(N, M, dv, dh, tau)
+    x = rand_state(N, M, rng)
+    q = O.apply_A(x, dv, dh, tau)
+    np.testing.assert_allclose(pack(q), A @ pack(x), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M", [(3, 4), (4, 4)])
+def test_A_equals_hessian_of_penalty_plus_D(N, M):
+    # proof of the rate theorem: the Hessian of s is (1/tau) B^T B; A adds diag(0, Dv, Dh)
+    rng = np.random.default_rng(5)
+    tau = 0.7
+    dv = rng.uniform(0.1, 2.0, size=(N - 1, M))
+    dh = rng.uniform(0.1, 2.0, size=(N, M - 1))
+    _, _, B = O.dense_operators(N, M)
+    Ad = B.T @ B / tau
+    Ad[N * M:, N * M:] += np.diag(np.concatenate([vecF(dv), vecF(dh)]))
+    np.testing.assert_allclose(dense_A(N, M, dv, dh, tau), Ad, atol=1e-12)
+
+
+def test_gershgorin_figures_printed_in_the_paper():
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))["gershgorin"]
+    N, M, tau = 5, 6, 0.25
+    _, _, B = O.dense_operators(N, M)
+    H = B.T @ B / tau
+    diag = np.diag(H)
+    off = np.abs(H).sum(axis=1) - np.abs(diag)
+    assert math.isclose(diag.max() * tau, g["max_diagonal_times_tau"], rel_tol=1e-12)
+    assert math.isclose(off.max() * tau, g["max_offdiagonal_row_sum_times_tau"], rel_tol=1e-12)
+    row = N + 2 - 1   # 'line N+2' of the paper, 1-based
+    assert math.isclose(diag[row] * tau, 4.0) and math.isclose(off[row] * tau, 8.0)
+    assert np.linalg.eigvalsh(H).max() * tau <= g["L_s_bound_times_tau"] + 1e-12
+
+
+@pytest.mark.parametrize("N,M", [(3, 4), (4, 2)])
+def test_residual_is_gradient_of_H_delta(N, M):
+    """A x - b = grad_x H_delta(x, W) at fixed W (Prop. 'linear system' is the stationarity
+    condition of problem (alt1)); checked by central differences of H_delta itself."""
+    rng = np.random.default_rng(7)
+    tau, delta = 0.2, 0.05
+    pb = rand_problem(N, M, rng, tau)
+    x = rand_state(N, M, rng)
+    Wv = rng.uniform(0.1, 1.0, size=(N - 1, M))
+    Wh = rng.uniform(0.1, 1.0, size=(N, M - 1))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+    res = pack(O.apply_A(x, dv, dh, tau)) - pack(pb.b)
+
+    def H(v):
+        U, Vv, Vh = unpack(v, N, M)
+        return O.H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
+
+    v0 = pack(x)
+    h = 1e-5
+    grad = np.array([(H(v0 + h * e) - H(v0 - h * e)) / (2 * h) for e in np.eye(v0.size)])
+    np.testing.assert_allclose(res, grad, rtol=1e-6, atol=1e-6)
+
+
+def test_b_in_range_of_A():
+    rng = np.random.default_rng(2)
+    pb = rand_problem(9, 7, rng)
+    assert abs(pb.b[0].sum()) < 1e-9 * np.abs(pb.b[0]).sum()
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 3.3: the preconditioner
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 2, 3, 8, 13])
+def test_dct_basis_diagonalises_neumann_laplacian(N):
+    P, lam = O.dct_basis(N)
+    S, _, _ = O.dense_operators(N, 2)
+    L = S.T @ S
+    np.testing.assert_allclose(P.T @ P, np.eye(N), atol=1e-13)
+    np.testing.assert_allclose(L @ P, P * lam[None, :], atol=1e-12)
+    np.testing.assert_allclose(np.sort(lam), np.linalg.eigvalsh(L), atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M", [(4, 4), (5, 3), (1, 7), (6, 9)])
+def test_preconditioner_equals_dense_pseudo_inverse(N, M):
+    rng = np.random.default_rng(N + 100 * M)
+    tau = 0.1
+    S, T, _ = O.dense_operators(N, M)
+    Lap = np.kron(np.eye(M), S.T @ S) + np.kron(T @ T.T, np.eye(N))
+    dv = rng.uniform(0, 10, size=(N - 1, M))
+    dh = rng.uniform(0, 10, size=(N, M - 1))
+    r = rand_state(N, M, rng)
+    z = O.precond_apply(r, dv, dh, tau, O.dct_basis(N), O.dct_basis(M))
+    zu_ref = np.linalg.pinv(Lap, rcond=1e-10, hermitian=True) @ (tau * vecF(r[0]))
+    np.testing.assert_allclose(vecF(z[0]), zu_ref, atol=1e-10)
+    np.testing.assert_allclose(z[1], r[1] / (dv + 1 / tau), rtol=1e-14)
+    np.testing.assert_allclose(z[2], r[2] / (dh + 1 / tau), rtol=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Alg. 2: PCG reaches the least-squares solution
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("rule", ["fr", "pr"])
+def test_pcg_matches_lstsq(rule):
+    N, M, tau = 6, 5, 1e-2
+    rng = np.random.default_rng(11)
+    pb = rand_problem(N, M, rng, tau)
+    Wv = rng.uniform(1e-3, 1.0, size=(N - 1, M))
+    Wh = rng.uniform(1e-3, 1.0, size=(N, M - 1))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+    A = dense_A(N, M, dv, dh, tau)
+    x_ref = np.linalg.lstsq(A, pack(pb.b), rcond=None)[0]
+    x0 = rand_state(N, M, rng)
+    x, it, rel, st = O.pcg(x0, pb.b, dv, dh, tau, pb.basis_N, pb.basis_M, 1e-13, 500, rule)
+    assert st == 0 and rel <= 1e-13 and it > 0
+    U = x[0] - x[0].mean()
+    xs = pack((U, x[1], x[2]))
+    np.testing.assert_allclose(xs, x_ref, atol=1e-9 * np.abs(x_ref).max())
+
+
+def test_pcg_stops_on_tolerance_and_cap():
+    N, M, tau = 8, 8, 1e-2
+    rng = np.random.default_rng(12)
+    pb = rand_problem(N, M, rng, tau)
+    dv, dh = np.ones((N - 1, M)), np.ones((N, M - 1))
+    z0 = (np.zeros((N, M)), np.zeros((N - 1, M)), np.zeros((N, M - 1)))
+    _, it, rel, _ = O.pcg(z0, pb.b, dv, dh, tau, pb.basis_N, pb.basis_M, 0.0, 3)
+    assert it == 3
+    _, it0, _, _ = O.pcg(z0, pb.b, dv, dh, tau, pb.basis_N, pb.basis_M, 10.0, 100)
+    assert it0 == 0
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 3.1: theorems as invariants along the IRLS trajectory
+# ------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_run():
+    d = synthetic.config_small(seed=0, H=40, W=36)
+    res = O.irls_unwrap(d["X"], None, tau=1e-2, delta=1e-3, outer_iters=8, cg_tol=1e-9,
+                        cg_max=400)
+    return d, res
+
+
+def test_H_delta_monotone(small_run):
+    _, res = small_run
+    hb, hd, ha = res["h_before"], res["h_delta"], res["h_after_rw"]
+    for k in range(len(hd)):
+        assert hd[k] <= hb[k] * (1 + 1e-12)          # CG decreases the quadratic in (U, V)
+        assert ha[k] <= hd[k] * (1 + 1e-12)          # exact W-minimisation (closed form)
+        if k + 1 < len(hb):
+            assert math.isclose(hb[k + 1], ha[k], rel_tol=1e-12)
+
+
+def test_sufficient_decrease_condition_holds(small_run):
+    """Eq. (sufficient-decrease): H_delta(x^{k+1}, W^k) <= H_delta(candidate, W^k); the paper
+    reports it always held in practice (remark after the rate theorem)."""
+    d, _ = small_run
+    tau, delta = 1e-2, 1e-3
+    pb = O.Problem(d["X"], None, tau=tau)
+    U = np.zeros((pb.N, pb.M))
+    Vv, Vh = O.S_op(U) - pb.Gv, O.T_op(U) - pb.Gh
+    for k in range(4):
+        Wv, Wh = O.reweight(Vv, Vh, pb.Cv, pb.Ch, delta)
+        dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+        cand = O.gradient_candidate(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
+        h_cand = O.H_delta_value(*cand, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
+        (U, Vv, Vh), _, _, _ = O.pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
+                                     1e-3, 5)
+        U = U - U.mean()
+        h_new = O.H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
+        assert h_new <= h_cand
+
+
+def test_F_vs_F_delta_bound(small_run):
+    """Theorem 'F vs F_delta': F <= F_delta <= F + delta ((N-1) M + N (M-1))."""
+    d, res = small_run
+    pb = res["problem"]
+    N, M = pb.N, pb.M
+    E = (N - 1) * M + N * (M - 1)
+    rng = np.random.default_rng(4)
+    for delta in (1e-3, 0.5):
+        for x in [(res["U"], res["Vv"], res["Vh"]), rand_state(N, M, rng)]:
+            F = O.F_value(*x, pb.Gv, pb.Gh, pb.Cv, pb.Ch, 1e-2)
+            Fd = O.F_delta_value(*x, pb.Gv, pb.Gh, pb.Cv, pb.Ch, 1e-2, delta)
+            assert F <= Fd <= F + delta * E * (1 + 1e-12)
+
+
+def test_L1_objective_decreases_on_the_small_workload(small_run):
+    _, res = small_run
+    l1 = res["l1_obj"]
+    assert all(l1[k + 1] <= l1[k] * (1 + 1e-9) for k in range(len(l1) - 1))
+    assert np.allclose(res["U"].mean(), 0.0, atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# Exact recovery, LP brute force, Newton minimiser, Schur complement
+# ------------------------------------------------------------------------------------------
+def test_exact_recovery_on_itoh_phase():
+    X, phi = synthetic.smooth_phase(24, 20, seed=9, max_step=1.5)
+    res = O.irls_unwrap(X, None, tau=1e-2, delta=1e-3, outer_iters=12, cg_tol=1e-10,
+                        cg_max=500)
+    err = O.best_shift_error(res["U"], phi)
+    assert np.abs(err).max() < 1e-4
+    K = O.k_map(res["U"], X)
+    assert np.all(K - K.flat[0] == O.k_map(phi, X) - O.k_map(phi, X).flat[0])
+    assert res["l1_obj"][-1] < 1e-3
+
+
+def _lp_l1(pb):
+    from scipy.optimize import linprog
+    from scipy.sparse import csr_matrix, hstack, vstack, identity, kron, eye
+    N, M = pb.N, pb.M
+    S, T, _ = O.dense_operators(N, M)
+    D = vstack([kron(eye(M), csr_matrix(S)), kron(csr_matrix(T.T), eye(N))]).tocsr()
+    g = np.concatenate([vecF(pb.Gv), vecF(pb.Gh)])
+    c = np.concatenate([vecF(pb.Cv), vecF(pb.Ch)])
+    E = g.size
+    # variables [u (NM), e+ (E), e- (E)];  D u - e+ + e- = g
+    A_eq = hstack([D, -identity(E), identity(E)]).tocsr()
+    cost = np.concatenate([np.zeros(N * M), c, c])
+    bounds = [(None, None)] * (N * M) + [(0, None)] * (2 * E)
+    bounds[0] = (0.0, 0.0)
+    r = linprog(cost, A_eq=A_eq, b_eq=g, bounds=bounds, method="highs-ds")
+    assert r.status == 0
+    u = r.x[:N * M].reshape((N, M), order="F")
+    return r.fun, u, D, g
+
+
+def test_irls_objective_within_lp_bound_6x6():
+    """L1* <= L1(U_irls) <= L1* + E (tau C_max^2 / 2 + delta) (Huber form of min_V F, plus
+    the F_delta bound); the LP optimum itself is 2 pi-congruent (Sec. 2, total unimodularity)."""
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-np.pi, np.pi, size=(6, 6)).astype(np.float32)
+    coh = rng.uniform(0.3, 1.0, size=(6, 6)).astype(np.float32)
+    tau, delta = 1e-4, 1e-6
+    pb = O.Problem(X, coh, tau=tau)
+    l1_star, u_star, D, g = _lp_l1(pb)
+    kk = (D @ vecF(u_star) - g) / (2 * np.pi)
+    np.testing.assert_allclose(kk, np.rint(kk), atol=1e-7)
+    res = O.irls_unwrap(X, coh, tau=tau, delta=delta, outer_iters=200, cg_tol=1e-12,
+                        cg_max=2000)
+    E = g.size
+    cmax = max(pb.Cv.max(), pb.Ch.max())
+    l1 = res["l1_obj"][-1]
+    assert l1_star - 1e-9 <= l1 <= l1_star + E * (tau * cmax ** 2 / 2 + delta) + 1e-6
+
+
+def _newton_F_delta(pb, tau, delta, iters=200):
+    N, M = pb.N, pb.M
+    _, _, B = O.dense_operators(N, M)
+    nu = N * M
+    g = np.concatenate([vecF(pb.Gv), vecF(pb.Gh)])
+    c = np.concatenate([vecF(pb.Cv), vecF(pb.Ch)])
+    one = np.zeros(B.shape[1])
+    one[:nu] = 1.0 / math.sqrt(nu)
+
+    def f(x):
+        v = x[nu:]
+        r = B @ x - g
+        return np.sum(np.sqrt(c * c * v * v + delta * delta)) + r @ r / (2 * tau)
+
+    x = np.zeros(B.shape[1])
+    x[nu:] = -g
+    for _ in range(iters):
+        v = x[nu:]
+        s = np.sqrt(c * c * v * v + delta * delta)
+        grad = B.T @ (B @ x - g) / tau
+        grad[nu:] += c * c * v / s
+        Hm = B.T @ B / tau
+        Hm[nu:, nu:] += np.diag(c * c * delta * delta / s ** 3)
+        Hm += np.outer(one, one)          # fixes the constant mode of U (C0)
+        step = np.linalg.solve(Hm, grad)
+        t = 1.0
+        f0 = f(x)
+        while f(x - t * step) > f0 - 1e-4 * t * (grad @ step) and t > 1e-12:
+            t *= 0.5
+        x = x - t * step
+        if np.abs(step).max() * t < 1e-15:
+            break
+    u = x[:nu].reshape((N, M), order="F")
+    return u - u.mean()
+
+
+@pytest.mark.parametrize("n,delta,outer", [(6, 1.0, 200), (8, 3.0, 80)])
+def test_irls_converges_to_newton_minimiser_of_F_delta(n, delta, outer):
+    """IRLS with tight inner solves reaches the unique minimiser of F_delta (theorems of
+    Sec. 3.1).  A large delta keeps the sublinear outer rate short on random phases."""
+    rng = np.random.default_rng(33 + n)
+    X = rng.uniform(-np.pi, np.pi, size=(n, n)).astype(np.float32)
+    tau = 1e-2
+    pb = O.Problem(X, None, tau=tau)
+    u_star = _newton_F_delta(pb, tau, delta)
+    res = O.irls_unwrap(X, None, tau=tau, delta=delta, outer_iters=outer, cg_tol=1e-13,
+                        cg_max=2000)
+    np.testing.assert_allclose(res["U"], u_star, atol=1e-8)
+
+
+def test_schur_complement_equivalence():
+    """Eliminating V from the linear system gives D^T Omega D U = D^T Omega G with
+    Omega = C^2 / (W + tau C^2) (the sandwiched form of the remark at the end of Sec. 3.3)."""
+    N, M, tau = 5, 6, 1e-2
+    rng = np.random.default_rng(8)
+    pb = rand_problem(N, M, rng, tau)
+    Wv = rng.uniform(1e-3, 1.0, size=(N - 1, M))
+    Wh = rng.uniform(1e-3, 1.0, size=(N, M - 1))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+    A = dense_A(N, M, dv, dh, tau)
+    x = np.linalg.lstsq(A, pack(pb.b), rcond=None)[0]
+    U_full = unpack(x, N, M)[0]
+    S, T, _ = O.dense_operators(N, M)
+    D = np.vstack([np.kron(np.eye(M), S), np.kron(T.T, np.eye(N))])
+    Om = np.concatenate([vecF(pb.Cv ** 2 / (Wv + tau * pb.Cv ** 2)),
+                         vecF(pb.Ch ** 2 / (Wh + tau * pb.Ch ** 2))])
+    g = np.concatenate([vecF(pb.Gv), vecF(pb.Gh)])
+    u = np.linalg.lstsq(D.T @ (Om[:, None] * D), D.T @ (Om * g), rcond=None)[0]
+    u = u.reshape((N, M), order="F")
+    np.testing.assert_allclose(U_full - U_full.mean(), u - u.mean(), atol=1e-10)
+
+
+# ------------------------------------------------------------------------------------------
+# Invariances
+# ------------------------------------------------------------------------------------------
+def test_invariances():
+    d = synthetic.config_small(seed=1, H=20, W=18)
+    X = d["X"]
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=4, cg_tol=1e-10, cg_max=300)
+    base = O.irls_unwrap(X, None, **kw)["U"]
+    # transposition
+    tr = O.irls_unwrap(X.T.copy(), None, **kw)["U"]
+    np.testing.assert_allclose(tr.T, base, atol=1e-8)
+    # 2 pi integer field and a constant added to X (float32 rounding perturbs G slightly)
+    rng = np.random.default_rng(0)
+    X2 = (X.astype(np.float64) + 2 * np.pi * rng.integers(-2, 3, size=X.shape) + 0.7)
+    u2 = O.irls_unwrap(X2.astype(np.float32), None, **kw)["U"]
+    np.testing.assert_allclose(u2, base, atol=1e-4)
+    # scaling: C -> sC, delta -> s delta, tau -> tau / s leaves the trajectory unchanged
+    s = 3.0
+    pb = O.Problem(X, None)
+    us = O.irls_unwrap(X, None, Cv=s * pb.Cv, Ch=s * pb.Ch, tau=1e-2 / s, delta=1e-3 * s,
+                       outer_iters=4, cg_tol=1e-10, cg_max=300)["U"]
+    np.testing.assert_allclose(us, base, atol=1e-8)
+
+
+def test_preconditioner_clusters_spectrum():
+    """Sec. 3.3.2: C* A C* has a far smaller condition number than A (N = M = 8 here)."""
+    N = M = 8
+    tau, delta = 1e-2, 1e-6
+    rng = np.random.default_rng(0)
+    dv = rng.uniform(0, 1 / delta, size=(N - 1, M))
+    dh = rng.uniform(0, 1 / delta, size=(N, M - 1))
+    A = dense_A(N, M, dv, dh, tau)
+    S, T, _ = O.dense_operators(N, M)
+    Dm = np.zeros_like(A)
+    nu = N * M
+    Dm[:nu, :nu] = A[:nu, :nu]
+    Dm[nu:, nu:] = np.diag(np.diag(A)[nu:])
+    w, V = np.linalg.eigh(Dm)
+    keep = w > 1e-9 * w.max()
+    Cs = (V[:, keep] / np.sqrt(w[keep])) @ V[:, keep].T
+    def kappa(Mx):
+        e = np.linalg.eigvalsh((Mx + Mx.T) / 2)
+        e = e[e > 1e-9 * e.max()]
+        return e.max() / e.min()
+    assert kappa(Cs @ A @ Cs) < 1e-3 * kappa(A)
+
+
+# ------------------------------------------------------------------------------------------
+# Planted mistakes: each pin above must catch a plausible slip in the oracle
+# ------------------------------------------------------------------------------------------
+def _matvec_matches(apply):
+    rng = np.random.default_rng(3)
+    N, M, tau = 4, 5, 0.3
+    dv = rng.uniform(0.1, 5.0, size=(N - 1, M))
+    dh = rng.uniform(0.1, 5.0, size=(N, M - 1))
+    x = rand_state(N, M, rng)
+    return np.allclose(pack(apply(x, dv, dh, tau)), dense_A(N, M, dv, dh, tau) @ pack(x))
+
+
+def test_planted_sign_error_in_matvec_is_caught():
+    def bad(x, dv, dh, tau):
+        qU, qV, qH = O.apply_A(x, dv, dh, tau)
+        return qU, qV + 2 * O.S_op(x[0]) / tau, qH     # flips the sign of the -S U / tau term
+    assert _matvec_matches(O.apply_A) and not _matvec_matches(bad)
+
+
+def test_planted_transposed_dct_is_caught():
+    N, M = 5, 4
+    rng = np.random.default_rng(0)
+    S, T, _ = O.dense_operators(N, M)
+    Lap = np.kron(np.eye(M), S.T @ S) + np.kron(T @ T.T, np.eye(N))
+    r = rand_state(N, M, rng)
+    PN, lN = O.dct_basis(N)
+    PM, lM = O.dct_basis(M)
+    z_bad = O.precond_apply(r, np.ones((N - 1, M)), np.ones((N, M - 1)), 1.0, (PN.T, lN),
+                            (PM, lM))
+    ref = np.linalg.pinv(Lap, rcond=1e-10, hermitian=True) @ vecF(r[0])
+    assert not np.allclose(vecF(z_bad[0]), ref, atol=1e-6)
+
+
+def test_planted_missing_tau_in_rhs_is_caught():
+    rng = np.random.default_rng(7)
+    N, M, tau = 3, 3, 0.2
+    pb = rand_problem(N, M, rng, tau)
+    b_bad = (pb.b[0] * tau, pb.b[1], pb.b[2])       # drops the 1/tau of B1
+    x = rand_state(N, M, rng)
+    W = (np.ones((N - 1, M)), np.ones((N, M - 1)))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, *W)
+    res_bad = pack(O.apply_A(x, dv, dh, tau)) - pack(b_bad)
+
+    def H(v):
+        U, Vv, Vh = unpack(v, N, M)
+        return O.H_delta_value(U, Vv, Vh, *W, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, 0.1)
+
+    v0 = pack(x)
+    grad = np.array([(H(v0 + 1e-5 * e) - H(v0 - 1e-5 * e)) / 2e-5 for e in np.eye(v0.size)])
+    assert not np.allclose(res_bad, grad, rtol=1e-6, atol=1e-6)
+
+
+def test_paper_parameters_fixture():
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    assert g["tau"] == 1e-2 and g["delta"] == 1e-6
+    assert g["max_iter_CG_start"] == 5 and g["increase_CG_iteration_factor"] == 1.7
