@@ -1,0 +1,158 @@
+/*
+ * irls.h - C ABI of libirls: GPU L1 phase unwrapping by iteratively reweighted least squares
+ * (IRLS) with a DCT-preconditioned conjugate gradient inner solver, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: "Iteratively Reweighted Least Squares for Phase Unwrapping" (arXiv 2401.09961).
+ *   - problem (main), Sec. 2: minimise over U the weighted L1 mismatch
+ *       sum Cv |U[i+1,j] - U[i,j] - Gv[i,j]| + sum Ch |U[i,j+1] - U[i,j] - Gh[i,j]|
+ *     of the wrapped phase differences Gv, Gh of the observed phase X;
+ *   - Sec. 3.1: slack variables Vv, Vh with penalty 1/(2 tau), delta-smoothing F_delta, and the
+ *     IRLS loop of Alg. 1 (closed-form weights W = sqrt(C^2 V^2 + delta^2), then an approximate
+ *     solve of the linear system of Prop. 'linear system' for (U, Vv, Vh), then U -= mean(U));
+ *   - Sec. 3.2: the inner solve is the preconditioned CG of Alg. 2;
+ *   - Sec. 3.3: the preconditioner is block diagonal; its Laplacian block is a Sylvester
+ *     equation solved through the DCT-II eigenbasis of the 1-D Neumann Laplacians.
+ *
+ * Conventions shared by every entry point
+ *   - Images are H x W (H = the paper's N rows, W = the paper's M columns), float32, row-major
+ *     and contiguous (element (i, j) at offset i*W + j).  Vertical-edge arrays (Gv, Cv, Vv) are
+ *     (H-1) x W row-major; horizontal-edge arrays (Gh, Ch, Vh) are H x (W-1) row-major.
+ *   - Pointers named d_* are DEVICE memory on the plan's device; h_* are HOST memory.  The
+ *     caller owns every buffer it passes; the library never frees or retains caller pointers
+ *     beyond the call (asynchronous calls read/write them until the stream reaches that point).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Return value: 0 = success; 1 = warning (CG reached cg_max_iter in some outer iteration
+ *     without meeting cg_tol); negative = error (IRLS_ERR_*).  No C++ exception crosses the ABI.
+ *   - H = 1 or W = 1 is valid: the corresponding edge set is empty.
+ *   - A plan is not thread-safe: use one plan per host thread / stream.
+ */
+#ifndef IRLS_H
+#define IRLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------- */
+#define IRLS_OK              0
+#define IRLS_WARN_CG_MAX     1   /* CG stopped on cg_max_iter before cg_tol in some outer step */
+#define IRLS_ERR_ARG        -1   /* null pointer, tau <= 0, delta <= 0, cg_tol < 0, ...        */
+#define IRLS_ERR_SHAPE      -2   /* H < 1, W < 1, or H*W too large                             */
+#define IRLS_ERR_NONFINITE  -3   /* NaN or Inf found in X, coherence or the weights            */
+#define IRLS_ERR_OOM        -4   /* device allocation failed                                   */
+#define IRLS_ERR_BREAKDOWN  -5   /* CG breakdown: rho <= 0 or p^T A p <= 0 with r != 0         */
+#define IRLS_ERR_TIMEOUT    -6   /* a bounded device-side wait gave up                         */
+#define IRLS_ERR_CUDA       -7   /* a CUDA runtime call failed (see irls_last_cuda_error)      */
+#define IRLS_ERR_UNSUPPORTED -8  /* option not available for this shape / device               */
+
+/* ---- precision of the DCT preconditioner (Sec. 3.3 dense products) -------------------- */
+#define IRLS_PREC_FP32  0   /* float32 operands, float32 accumulation (SIMT FMA)              */
+#define IRLS_PREC_BF16  1   /* bfloat16 operands, float32 accumulation (tcgen05 tensor cores) */
+#define IRLS_PREC_FP16  2   /* float16 operands with per-apply scaling, float32 accumulation  */
+
+#define IRLS_MAX_OUTER 256
+
+typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
+
+/* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
+ * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
+ * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1. */
+typedef struct {
+    float tau;          /* penalty tau of problem (soft constraints), Sec. 3.1; > 0            */
+    float delta;        /* smoothing delta of F_delta, Sec. 3.1; > 0                           */
+    int   outer_iters;  /* number of IRLS (Alg. 1) iterations; 1 .. IRLS_MAX_OUTER             */
+    float cg_tol;       /* stop CG when ||r||_2 <= cg_tol * ||b||_2 (full 3-block residual)     */
+    int   cg_max_iter;  /* cap on products with A per outer iteration; >= 0                    */
+    int   precision;    /* IRLS_PREC_*                                                         */
+    int   flexible_cg;  /* 0: beta = rho_new / rho (Alg. 2); 1: Polak-Ribiere (flexible) beta  */
+    int   warm_start;   /* 1: CG starts from the current (U, V); 0: from zero each outer step  */
+} irls_opts;
+
+/* Per-call statistics (host struct filled by the library). */
+typedef struct {
+    int    outer_done;                  /* outer iterations completed                         */
+    int    cg_total;                    /* sum of CG iterations                               */
+    int    status;                      /* status of the call (same code as the return value) */
+    int    cg_iters[IRLS_MAX_OUTER];    /* CG iterations (products with A) per outer step     */
+    double rel_res[IRLS_MAX_OUTER];     /* final ||r|| / ||b|| of each inner solve            */
+    double l1_obj[IRLS_MAX_OUTER];      /* objective of problem (main) at U^{k+1}             */
+    double h_delta[IRLS_MAX_OUTER];     /* H_delta(U^{k+1}, V^{k+1}, W^k), problem (alt1)     */
+    double f_delta[IRLS_MAX_OUTER];     /* F_delta(U^k, V^k) = H_delta(x^k, W^k) before solve */
+} irls_stats;
+
+/* Fill *opts with the defaults above.  Returns IRLS_ERR_ARG if opts is NULL. */
+int irls_opts_default(irls_opts* opts);
+
+/* Bytes of device memory a plan for an H x W image allocates (workspace, DCT bases, state).
+ * Returns 0 on invalid arguments. */
+size_t irls_workspace_bytes(int H, int W, const irls_opts* opts);
+
+/* Create a plan on the current CUDA device: allocates the workspace and precomputes the
+ * eigendecompositions S^T S = P_S L_S P_S^T and T T^T = P_T L_T P_T^T (Sec. 3.3: computed
+ * once, kept in memory).  opts may be NULL (defaults).  *out receives the plan.  Synchronous. */
+int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out);
+
+/* Release a plan and its device memory (synchronises the device first).  NULL is a no-op. */
+int irls_plan_destroy(irls_plan plan);
+
+/* Replace the plan's options (same H, W).  Changing `precision` is allowed only between the
+ * values the plan was created with support for (IRLS_ERR_UNSUPPORTED otherwise). */
+int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
+
+/* Simple form: unwrap d_X (H x W) into d_U (H x W, zero mean) with weights from d_coherence
+ * (H x W, may be NULL for uniform weights), delta = eps, the given number of IRLS iterations
+ * and CG tolerance, and the remaining options at their defaults (tau = 1e-2).  Edge weights from
+ * coherence: Cv[i,j] = (coh[i,j] + coh[i+1,j]) / 2, Ch[i,j] = (coh[i,j] + coh[i,j+1]) / 2.
+ * Synchronises `stream` before returning, so the status covers device-side failures. */
+int irls_unwrap(const float* d_X, const float* d_coherence, int H, int W, float eps,
+                int outer_iters, float cg_tol, float* d_U, void* stream);
+
+/* Full form (Alg. 1 with Alg. 2).  d_Cv ((H-1) x W) and d_Ch (H x (W-1)), when both non-NULL,
+ * are the edge weights and take precedence over d_coherence (as in the paper's unwrap(),
+ * Sec. 4.4).  d_Vv / d_Vh may be NULL; when non-NULL they receive the final slacks.  When
+ * d_U_init is non-NULL, (d_U_init, d_Vv, d_Vh) are the starting iterate (a restart point; the
+ * default start is U = 0, V = -G as in Alg. 1).  h_stats may be NULL.  The call is
+ * synchronous with respect to the host (it polls the device-side CG stopping flag). */
+int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
+                   const float* d_Cv, const float* d_Ch, const float* d_U_init,
+                   float* d_U, float* d_Vv, float* d_Vh, irls_stats* h_stats, void* stream);
+
+/* One application of the Laplacian block of the preconditioner (Sec. 3.3, Sylvester equation
+ * S^T S Z + Z T T^T = tau R solved in the DCT eigenbasis, zero-frequency coefficient set to 0):
+ * d_Z = P_S [(P_S^T (tau d_R) P_T) / (l_i + m_j)] P_T^T, both H x W, in the plan's precision.
+ * Asynchronous on `stream`. */
+int irls_precond_laplacian(irls_plan plan, const float* d_R, float* d_Z, void* stream);
+
+/* One product with the matrix A of Sec. 3.2 (eq. 'matrix-soft-constraints'):
+ *   q_U  = (S^T S U + U T T^T - S^T Vv - Vh T^T) / tau
+ *   q_Vv = Dv o Vv + (Vv - S U) / tau,    q_Vh = Dh o Vh + (Vh - U T) / tau
+ * with Dv = d_Dv ((H-1) x W), Dh = d_Dh (H x (W-1)) and tau from the plan's options.
+ * Runs the same update kernel as the CG loop.  Asynchronous on `stream`. */
+int irls_apply_A(irls_plan plan, const float* d_U, const float* d_Vv, const float* d_Vh,
+                 const float* d_Dv, const float* d_Dh, float* d_qU, float* d_qVv, float* d_qVh,
+                 void* stream);
+
+/* Live profiler (for measurement tools).  When on, every solve on this plan records a CUDA
+ * event pair around each kernel launch on the solve's stream and accumulates the elapsed time
+ * per kernel class; turning it on (or off) clears the totals.  Classes, in order:
+ *   0 gradients/weights/||b|| (once per solve)   1 reweight + initial residual (per outer)
+ *   2 search direction + p^T A p (per CG iter)    3 CG update x, r (per CG iter)
+ *   4 Laplacian preconditioner, all four GEMMs    5 end-of-outer reductions and U -= mean
+ * irls_plan_profile copies min(n, classes) totals (milliseconds) and launch counts and returns
+ * the number of classes (6); launches skipped on the device after CG stopped are counted too. */
+int irls_plan_set_profiling(irls_plan plan, int on);
+int irls_plan_profile(irls_plan plan, double* ms, long long* launches, int n);
+
+/* Human-readable text for a status code (static storage). */
+const char* irls_status_string(int status);
+
+/* The CUDA error code behind the last IRLS_ERR_CUDA returned on this host thread (0 if none). */
+int irls_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRLS_H */

@@ -147,14 +147,13 @@ def dct_basis(N):
     """Eigendecomposition S^T S = P diag(lam) P^T of the 1-D Neumann Laplacian (Sec. 3.3).
 
     Closed form (orthonormal DCT-II vectors): P[i, k] = c_k cos(pi k (i + 1/2) / N),
-    c_0 = sqrt(1/N), c_k = sqrt(2/N); lam_k = 2 - 2 cos(pi k / N).  Built with plain loops."""
-    P = np.empty((N, N))
-    lam = np.empty(N)
-    for k in range(N):
-        ck = math.sqrt(1.0 / N) if k == 0 else math.sqrt(2.0 / N)
-        lam[k] = 2.0 - 2.0 * math.cos(math.pi * k / N)
-        for i in range(N):
-            P[i, k] = ck * math.cos(math.pi * k * (i + 0.5) / N)
+    c_0 = sqrt(1/N), c_k = sqrt(2/N); lam_k = 2 - 2 cos(pi k / N)."""
+    i = np.arange(N, dtype=np.float64)[:, None]
+    k = np.arange(N, dtype=np.float64)[None, :]
+    c = np.full((1, N), math.sqrt(2.0 / N))
+    c[0, 0] = math.sqrt(1.0 / N)
+    P = c * np.cos(np.pi * k * (i + 0.5) / N)
+    lam = 2.0 - 2.0 * np.cos(np.pi * np.arange(N, dtype=np.float64) / N)
     return P, lam
 
 

@@ -1,0 +1,171 @@
+"""GB300-native L1 phase unwrapping by IRLS + DCT-preconditioned CG (arXiv 2401.09961).
+
+The compute path is libirls.so (hand-written CUDA for sm_103a behind a C ABI, include/irls.h);
+this package marshals torch tensors into it.  PyTorch provides device memory and streams only.
+
+    import torch, paper_2401_09961_gb300 as irls
+    U = irls.unwrap(X_cuda, coherence_cuda, eps=1e-3, outer_iters=20, cg_tol=1e-6)
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._binding import (IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
+                       lib)
+
+__all__ = ["Plan", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
+           "Opts", "Stats", "PRECISIONS"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    torch = _torch()
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns an irls_plan: device workspace, DCT eigenbases and device-resident solver state
+    for one H x W image shape (Sec. 3.3: the eigendecompositions are computed once)."""
+
+    def __init__(self, H, W, **opts):
+        self.H, self.W = int(H), int(W)
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        check(lib().irls_plan_create(self.H, self.W, ctypes.byref(self.opts), ctypes.byref(h)),
+              "irls_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def set_opts(self, **kw):
+        o = Opts.from_buffer_copy(self.opts)
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISIONS[v]
+            setattr(o, k, v)
+        check(lib().irls_plan_set_opts(self.handle, ctypes.byref(o)), "irls_plan_set_opts")
+        self.opts = o
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().irls_plan_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self):
+        return int(lib().irls_workspace_bytes(self.H, self.W, ctypes.byref(self.opts)))
+
+    def unwrap(self, X, coherence=None, *, Cv=None, Ch=None, U_init=None, Vv_init=None,
+               Vh_init=None, out=None, return_slacks=False, stream=None):
+        """Run Alg. 1 on device tensors; returns U (and (Vv, Vh) with return_slacks) and stats."""
+        torch = _torch()
+        H, W = self.H, self.W
+        if tuple(X.shape) != (H, W):
+            raise ValueError(f"X has shape {tuple(X.shape)}, plan is {(H, W)}")
+        dev = X.device
+        U = out if out is not None else torch.empty((H, W), device=dev, dtype=torch.float32)
+        Vv = Vh = None
+        if return_slacks or U_init is not None:
+            Vv = torch.empty((max(H - 1, 0), W), device=dev, dtype=torch.float32)
+            Vh = torch.empty((H, max(W - 1, 0)), device=dev, dtype=torch.float32)
+            if U_init is not None:
+                Vv.copy_(Vv_init)
+                Vh.copy_(Vh_init)
+        st = Stats()
+        rc = lib().irls_unwrap_ex(self.handle, _ptr(X), _ptr(coherence), _ptr(Cv), _ptr(Ch),
+                                  _ptr(U_init), _ptr(U),
+                                  _ptr(Vv) if Vv is not None and Vv.numel() else None,
+                                  _ptr(Vh) if Vh is not None and Vh.numel() else None,
+                                  ctypes.byref(st), _stream(stream))
+        check(rc, "irls_unwrap_ex")
+        stats = st.to_dict()
+        stats["return_code"] = rc
+        if return_slacks:
+            return U, Vv, Vh, stats
+        return U, stats
+
+
+def unwrap(X, coherence=None, *, eps=1e-3, outer_iters=20, cg_tol=1e-6, tau=1e-2,
+           cg_max_iter=1000, precision="fp32", flexible_cg=None, Cv=None, Ch=None,
+           return_stats=False, plan=None):
+    """Unwrap the wrapped phase X (H x W float32) with the L1 IRLS method.
+
+    X and the optional coherence / Cv / Ch may be CUDA tensors (the result stays on the device)
+    or host arrays / CPU tensors (they are copied to the current CUDA device and U is copied
+    back).  eps is the smoothing delta of F_delta (Sec. 3.1)."""
+    torch = _torch()
+    import numpy as np
+    host = not (isinstance(X, torch.Tensor) and X.is_cuda)
+
+    def dev(a):
+        if a is None:
+            return None
+        t = torch.as_tensor(np.asarray(a) if not isinstance(a, torch.Tensor) else a)
+        return t.to(device="cuda", dtype=torch.float32).contiguous()
+
+    Xd = dev(X)
+    H, W = Xd.shape
+    if flexible_cg is None:
+        flexible_cg = 0 if precision == "fp32" else 1
+    own = plan is None
+    if own:
+        plan = Plan(H, W, tau=tau, delta=eps, outer_iters=outer_iters, cg_tol=cg_tol,
+                    cg_max_iter=cg_max_iter, precision=precision, flexible_cg=flexible_cg)
+    try:
+        U, stats = plan.unwrap(Xd, dev(coherence), Cv=dev(Cv), Ch=dev(Ch))
+    finally:
+        if own:
+            plan.close()
+    if host:
+        U = U.cpu()
+    return (U, stats) if return_stats else U
+
+
+def precond_laplacian(plan, R, stream=None):
+    """Z solving S^T S Z + Z T T^T = tau R in the DCT eigenbasis (Sec. 3.3), on device."""
+    torch = _torch()
+    Z = torch.empty_like(R)
+    check(lib().irls_precond_laplacian(plan.handle, _ptr(R), _ptr(Z), _stream(stream)),
+          "irls_precond_laplacian")
+    return Z
+
+
+def apply_A(plan, U, Vv, Vh, Dv, Dh, stream=None):
+    """(q_U, q_Vv, q_Vh) = A (U, Vv, Vh) with the matrix A of Sec. 3.2, on device."""
+    torch = _torch()
+    qU = torch.empty_like(U)
+    qVv = torch.empty_like(Vv)
+    qVh = torch.empty_like(Vh)
+    nz = lambda t: _ptr(t) if t.numel() else None  # noqa: E731
+    check(lib().irls_apply_A(plan.handle, _ptr(U), nz(Vv), nz(Vh), nz(Dv), nz(Dh), _ptr(qU),
+                             nz(qVv), nz(qVh), _stream(stream)), "irls_apply_A")
+    return qU, qVv, qVh

@@ -1,0 +1,129 @@
+"""ctypes binding of libirls (include/irls.h): argument marshalling only.
+
+Every step of the unwrapping path runs in the library's CUDA kernels; this module converts
+Python arguments into the C ABI's plain pointers and sizes.  There is no CPU fallback: if the
+library is missing the import of the functions below raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libirls.so")
+
+IRLS_MAX_OUTER = 256
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+STATUS = {
+    0: "IRLS_OK", 1: "IRLS_WARN_CG_MAX", -1: "IRLS_ERR_ARG", -2: "IRLS_ERR_SHAPE",
+    -3: "IRLS_ERR_NONFINITE", -4: "IRLS_ERR_OOM", -5: "IRLS_ERR_BREAKDOWN",
+    -6: "IRLS_ERR_TIMEOUT", -7: "IRLS_ERR_CUDA", -8: "IRLS_ERR_UNSUPPORTED",
+}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_float),
+        ("delta", ctypes.c_float),
+        ("outer_iters", ctypes.c_int),
+        ("cg_tol", ctypes.c_float),
+        ("cg_max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("flexible_cg", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("outer_done", ctypes.c_int),
+        ("cg_total", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("cg_iters", ctypes.c_int * IRLS_MAX_OUTER),
+        ("rel_res", ctypes.c_double * IRLS_MAX_OUTER),
+        ("l1_obj", ctypes.c_double * IRLS_MAX_OUTER),
+        ("h_delta", ctypes.c_double * IRLS_MAX_OUTER),
+        ("f_delta", ctypes.c_double * IRLS_MAX_OUTER),
+    ]
+
+    def to_dict(self):
+        n = self.outer_done
+        return {
+            "outer_done": n,
+            "cg_total": self.cg_total,
+            "status": self.status,
+            "cg_iters": list(self.cg_iters[:n]),
+            "rel_res": list(self.rel_res[:n]),
+            "l1_obj": list(self.l1_obj[:n]),
+            "h_delta": list(self.h_delta[:n]),
+            "f_delta": list(self.f_delta[:n]),
+        }
+
+
+_P = ctypes.c_void_p
+_F = ctypes.c_float
+_I = ctypes.c_int
+
+# name -> (restype, argtypes); mirrors include/irls.h
+SIGNATURES = {
+    "irls_opts_default": (_I, [ctypes.POINTER(Opts)]),
+    "irls_workspace_bytes": (ctypes.c_size_t, [_I, _I, ctypes.POINTER(Opts)]),
+    "irls_plan_create": (_I, [_I, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "irls_plan_destroy": (_I, [_P]),
+    "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
+    "irls_unwrap": (_I, [_P, _P, _I, _I, _F, _I, _F, _P, _P]),
+    "irls_unwrap_ex": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
+    "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "irls_plan_set_profiling": (_I, [_P, _I]),
+    "irls_plan_profile": (_I, [_P, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_longlong), _I]),
+    "irls_status_string": (ctypes.c_char_p, [_I]),
+    "irls_last_cuda_error": (_I, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libirls.so (built in-tree by ``paper_2401_09961_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libirls.so not found at {LIB_PATH}; build it with "
+                "`python -m paper_2401_09961_gb300.build` (the CUDA path has no fallback)")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+class IrlsError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = lib().irls_status_string(code).decode()
+        extra = ""
+        if code == -7:
+            extra = f" (cudaError {lib().irls_last_cuda_error()})"
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}{extra}")
+
+
+def check(code, where=""):
+    if code < 0:
+        raise IrlsError(code, where)
+    return code
+
+
+def default_opts(**kw):
+    o = Opts()
+    check(lib().irls_opts_default(ctypes.byref(o)), "irls_opts_default")
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o

@@ -1,0 +1,516 @@
+// Host driver and C ABI of libirls (see include/irls.h).
+//
+// A plan owns one device allocation that is carved into the image planes, the device-resident
+// PCG state, the reduction scratch and the DCT bases.  A solve runs Alg. 1 of arXiv 2401.09961:
+// per outer step one reweighting/residual pass, then PCG iterations (Alg. 2) whose scalars
+// (alpha, beta, rho, the stopping flag) stay on the device.  The host only issues kernels in
+// chunks and polls the device stopping flag through pinned memory, one chunk behind, so the GPU
+// never idles waiting for the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "irls_internal.cuh"
+
+using namespace irls;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+constexpr int kPlanes = 21;
+constexpr int kChunk = 8;
+
+struct Fail {};
+
+inline void ck(cudaError_t e) {
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        throw Fail{};
+    }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int row_pitch(int W) { return (W + 31) / 32 * 32; }
+
+bool opts_valid(const irls_opts& o) {
+    if (!(o.tau > 0.f) || !(o.delta > 0.f) || !std::isfinite(o.tau) || !std::isfinite(o.delta))
+        return false;
+    if (!(o.cg_tol >= 0.f)) return false;
+    if (o.outer_iters < 0 || o.outer_iters > IRLS_MAX_OUTER) return false;
+    if (o.cg_max_iter < 0) return false;
+    if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_FP16) return false;
+    return true;
+}
+
+bool shape_valid(int H, int W) {
+    if (H < 1 || W < 1) return false;
+    if ((long long)H * (long long)row_pitch(W) > (1LL << 31)) return false;
+    return true;
+}
+
+struct Layout {
+    size_t plane_bytes, planes, state, partials, dct, total;
+    int max_blocks;
+};
+
+Layout layout(int H, int W, int prec) {
+    Layout L{};
+    const int ld = row_pitch(W);
+    L.plane_bytes = align_up((size_t)H * ld * sizeof(float), 256);
+    L.planes = 0;
+    L.state = L.planes + kPlanes * L.plane_bytes;
+    L.partials = L.state + align_up(sizeof(DevState), 256);
+    L.max_blocks = std::max(stencil_grid_blocks(H, W), dct_max_blocks(H, W));
+    L.dct = L.partials + align_up((size_t)8 * L.max_blocks * sizeof(double), 1024);
+    L.total = L.dct + align_up(dct_bytes(H, W, prec), 1024) + 1024;
+    return L;
+}
+
+int status_to_code(int st) {
+    if (st & ST_NONFINITE) return IRLS_ERR_NONFINITE;
+    if (st & ST_BREAKDOWN) return IRLS_ERR_BREAKDOWN;
+    if (st & ST_TIMEOUT) return IRLS_ERR_TIMEOUT;
+    if (st & ST_CGMAX) return IRLS_WARN_CG_MAX;
+    return IRLS_OK;
+}
+
+// Kernel classes timed by the optional live profiler (CUDA events on the solve's stream).
+enum ProfClass : int {
+    PC_INIT = 0, PC_REWEIGHT, PC_DIRECTION, PC_UPDATE, PC_DCT, PC_FINALIZE, PC_N
+};
+
+// Records an event pair around each profiled launch and folds the elapsed times in once the
+// stream has passed them (the solve already waits on chunk boundaries, so draining adds no
+// synchronisation of its own).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> free_ev;
+    struct Pair { int cls; cudaEvent_t a, b; };
+    std::vector<Pair> pend;
+    double ms[PC_N] = {0};
+    long long n[PC_N] = {0};
+
+    cudaEvent_t get() {
+        if (free_ev.empty()) {
+            cudaEvent_t e;
+            ck(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = free_ev.back();
+        free_ev.pop_back();
+        return e;
+    }
+    cudaEvent_t begin(cudaStream_t s) {
+        if (!on) return nullptr;
+        cudaEvent_t e = get();
+        ck(cudaEventRecord(e, s));
+        return e;
+    }
+    void end(int cls, cudaEvent_t a, cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t b = get();
+        ck(cudaEventRecord(b, s));
+        pend.push_back({cls, a, b});
+    }
+    // fold in every pair recorded before `upto` pairs (all of them complete)
+    void drain(size_t upto) {
+        upto = std::min(upto, pend.size());
+        for (size_t i = 0; i < upto; ++i) {
+            float t = 0.f;
+            ck(cudaEventElapsedTime(&t, pend[i].a, pend[i].b));
+            ms[pend[i].cls] += t;
+            n[pend[i].cls] += 1;
+            free_ev.push_back(pend[i].a);
+            free_ev.push_back(pend[i].b);
+        }
+        pend.erase(pend.begin(), pend.begin() + upto);
+    }
+    void reset() {
+        for (int i = 0; i < PC_N; ++i) { ms[i] = 0; n[i] = 0; }
+    }
+    ~Profiler() {
+        for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : free_ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct irls_plan_s {
+    int H = 0, W = 0, ld = 0, dev = 0;
+    irls_opts opts{};
+    int prec_alloc = 0;
+    char* mem = nullptr;
+    Layout L{};
+    Planes P{};
+    DevState* st = nullptr;
+    double* partials = nullptr;
+    DctPlan dct{};
+    int* h_flag = nullptr;     // pinned, 2 slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    Profiler prof;
+};
+
+namespace {
+
+StencilArgs make_args(const irls_plan_s* p) {
+    StencilArgs a{};
+    a.H = p->H; a.W = p->W; a.ld = p->ld;
+    a.tau = p->opts.tau;
+    a.inv_tau = 1.0f / p->opts.tau;
+    a.delta = p->opts.delta;
+    a.tol2 = (double)p->opts.cg_tol * (double)p->opts.cg_tol;
+    a.cg_max = p->opts.cg_max_iter;
+    a.flexible = p->opts.flexible_cg;
+    a.warm_start = p->opts.warm_start;
+    a.prec = p->opts.precision;
+    a.r16 = (p->opts.precision != IRLS_PREC_FP32) ? p->dct.R16 : nullptr;
+    a.ld16 = p->dct.Wp;
+    return a;
+}
+
+void destroy_plan(irls_plan_s* p) {
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->dev);
+    cudaDeviceSynchronize();
+    if (p->mem) cudaFree(p->mem);
+    if (p->h_flag) cudaFreeHost(p->h_flag);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ck(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Runs the whole of Alg. 1 on the plan's workspace; returns the device status bits.
+int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv, const float* Ch,
+              const float* U0, const float* Vv0, const float* Vh0, cudaStream_t s,
+              irls_stats* stats) {
+    const StencilArgs a = make_args(p);
+    DevState* st = p->st;
+    Profiler& pf = p->prof;
+    cudaEvent_t t0;
+    ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    t0 = pf.begin(s);
+    ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
+    ck(launch_bnorm(p->P, a, st, p->partials, s));
+    pf.end(PC_INIT, t0, s);
+    // stop early on invalid input
+    ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    pf.drain(pf.pend.size());
+    if (p->h_flag[0] & ST_NONFINITE) return p->h_flag[0];
+
+    for (int k = 0; k < p->opts.outer_iters; ++k) {
+        t0 = pf.begin(s);
+        ck(launch_reweight_residual(p->P, a, st, p->partials, s));
+        pf.end(PC_REWEIGHT, t0, s);
+        t0 = pf.begin(s);
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, a, p->partials, 1, s));
+        pf.end(PC_DCT, t0, s);
+        int issued = 0, slot = 0;
+        bool pending = false;
+        size_t mark[2] = {0, 0};
+        while (issued < p->opts.cg_max_iter) {
+            const int n = std::min(kChunk, p->opts.cg_max_iter - issued);
+            for (int c = 0; c < n; ++c) {
+                t0 = pf.begin(s);
+                ck(launch_direction_pap(p->P, a, st, p->partials, s));
+                pf.end(PC_DIRECTION, t0, s);
+                t0 = pf.begin(s);
+                ck(launch_update(p->P, a, st, p->partials, s));
+                pf.end(PC_UPDATE, t0, s);
+                t0 = pf.begin(s);
+                ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, a, p->partials, 1, s));
+                pf.end(PC_DCT, t0, s);
+            }
+            issued += n;
+            ck(cudaMemcpyAsync(&p->h_flag[slot], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            ck(cudaEventRecord(p->ev[slot], s));
+            mark[slot] = pf.pend.size();
+            if (pending) {
+                ck(cudaEventSynchronize(p->ev[slot ^ 1]));
+                pf.drain(mark[slot ^ 1]);
+                mark[slot] -= std::min(mark[slot], mark[slot ^ 1]);
+                if (p->h_flag[slot ^ 1]) break;
+            }
+            pending = true;
+            slot ^= 1;
+        }
+        t0 = pf.begin(s);
+        ck(launch_finalize(p->P, a, st, p->partials, s));
+        pf.end(PC_FINALIZE, t0, s);
+    }
+    if (pf.on) {
+        ck(cudaStreamSynchronize(s));
+        pf.drain(pf.pend.size());
+    }
+    if (stats) {
+        DevState h;
+        ck(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        std::memset(stats, 0, sizeof(*stats));
+        stats->outer_done = h.outer;
+        stats->cg_total = h.cg_total;
+        const int n = std::min(h.outer, IRLS_MAX_OUTER);
+        for (int k = 0; k < n; ++k) {
+            stats->cg_iters[k] = h.cg_iters[k];
+            stats->rel_res[k] = h.rel_res[k];
+            stats->l1_obj[k] = h.l1_obj[k];
+            stats->h_delta[k] = h.h_delta[k];
+            stats->f_delta[k] = h.f_delta[k];
+        }
+        stats->status = status_to_code(h.status);
+        return h.status;
+    }
+    int status = 0;
+    ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    status = p->h_flag[0];
+    return status;
+}
+
+std::mutex g_simple_mu;
+
+}  // namespace
+
+extern "C" {
+
+int irls_opts_default(irls_opts* o) {
+    if (!o) return IRLS_ERR_ARG;
+    o->tau = 1e-2f;
+    o->delta = 1e-6f;
+    o->outer_iters = 20;
+    o->cg_tol = 1e-6f;
+    o->cg_max_iter = 1000;
+    o->precision = IRLS_PREC_FP32;
+    o->flexible_cg = 0;
+    o->warm_start = 1;
+    return IRLS_OK;
+}
+
+size_t irls_workspace_bytes(int H, int W, const irls_opts* opts) {
+    irls_opts o;
+    irls_opts_default(&o);
+    if (opts) o = *opts;
+    if (!shape_valid(H, W) || !opts_valid(o)) return 0;
+    return layout(H, W, o.precision).total;
+}
+
+int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
+    if (!out) return IRLS_ERR_ARG;
+    *out = nullptr;
+    irls_opts o;
+    irls_opts_default(&o);
+    if (opts) o = *opts;
+    if (!opts_valid(o)) return IRLS_ERR_ARG;
+    if (!shape_valid(H, W)) return IRLS_ERR_SHAPE;
+    irls_plan_s* p = new (std::nothrow) irls_plan_s();
+    if (!p) return IRLS_ERR_OOM;
+    try {
+        ck(cudaGetDevice(&p->dev));
+        p->H = H; p->W = W; p->ld = row_pitch(W);
+        p->opts = o;
+        p->prec_alloc = o.precision;
+        p->L = layout(H, W, o.precision);
+        cudaError_t e = cudaMalloc(&p->mem, p->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->mem = nullptr;
+            destroy_plan(p);
+            return IRLS_ERR_OOM;
+        }
+        ck(cudaMemset(p->mem, 0, p->L.total));
+        float* f[kPlanes];
+        for (int i = 0; i < kPlanes; ++i)
+            f[i] = reinterpret_cast<float*>(p->mem + p->L.planes + (size_t)i * p->L.plane_bytes);
+        Planes& P = p->P;
+        int q = 0;
+        P.U = f[q++]; P.Vv = f[q++]; P.Vh = f[q++];
+        P.rU = f[q++]; P.rVv = f[q++]; P.rVh = f[q++];
+        for (int b = 0; b < 2; ++b) { P.pU[b] = f[q++]; P.pVv[b] = f[q++]; P.pVh[b] = f[q++]; }
+        P.zU = f[q++];
+        P.dv = f[q++]; P.dh = f[q++];
+        P.Wv = f[q++]; P.Wh = f[q++];
+        P.Gv = f[q++]; P.Gh = f[q++];
+        P.Cv = f[q++]; P.Ch = f[q++];
+        p->st = reinterpret_cast<DevState*>(p->mem + p->L.state);
+        p->partials = reinterpret_cast<double*>(p->mem + p->L.partials);
+        ck(dct_setup(p->dct, H, W, o.precision, o.tau, p->mem + p->L.dct));
+        ck(cudaHostAlloc(&p->h_flag, 2 * sizeof(int), cudaHostAllocDefault));
+        for (auto& ev : p->ev) ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ck(cudaDeviceSynchronize());
+    } catch (Fail&) {
+        destroy_plan(p);
+        return IRLS_ERR_CUDA;
+    }
+    *out = p;
+    return IRLS_OK;
+}
+
+int irls_plan_destroy(irls_plan p) {
+    destroy_plan(p);
+    return IRLS_OK;
+}
+
+int irls_plan_set_opts(irls_plan p, const irls_opts* opts) {
+    if (!p || !opts) return IRLS_ERR_ARG;
+    if (!opts_valid(*opts)) return IRLS_ERR_ARG;
+    if (opts->precision != p->opts.precision && opts->precision != IRLS_PREC_FP32 &&
+        p->prec_alloc == IRLS_PREC_FP32)
+        return IRLS_ERR_UNSUPPORTED;
+    if (opts->tau != p->opts.tau) {
+        p->dct.tau = opts->tau;
+    }
+    p->opts = *opts;
+    p->dct.prec = opts->precision;
+    return IRLS_OK;
+}
+
+int irls_unwrap_ex(irls_plan p, const float* X, const float* coh, const float* Cv,
+                   const float* Ch, const float* U0, float* U, float* Vv, float* Vh,
+                   irls_stats* stats, void* stream) {
+    if (!p || !X || !U) return IRLS_ERR_ARG;
+    if ((Cv == nullptr) != (Ch == nullptr)) return IRLS_ERR_ARG;
+    if (U0 && ((p->H > 1 && !Vv) || (p->W > 1 && !Vh))) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int status = 0;
+    try {
+        DeviceGuard g(p->dev);
+        status = run_solve(p, X, coh, Cv, Ch, U0, U0 ? Vv : nullptr, U0 ? Vh : nullptr, s, stats);
+        if (status & ST_NONFINITE) {
+            if (stats) stats->status = IRLS_ERR_NONFINITE;
+            return IRLS_ERR_NONFINITE;
+        }
+        ck(launch_copy_out(p->P.U, p->H, p->W, p->ld, U, s));
+        if (Vv) ck(launch_copy_out(p->P.Vv, p->H - 1, p->W, p->ld, Vv, s));
+        if (Vh) ck(launch_copy_out(p->P.Vh, p->H, p->W - 1, p->ld, Vh, s));
+        ck(cudaStreamSynchronize(s));
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return status_to_code(status);
+}
+
+int irls_unwrap(const float* X, const float* coh, int H, int W, float eps, int outer_iters,
+                float cg_tol, float* U, void* stream) {
+    if (!X || !U) return IRLS_ERR_ARG;
+    if (!shape_valid(H, W)) return IRLS_ERR_SHAPE;
+    irls_opts o;
+    irls_opts_default(&o);
+    o.delta = eps;
+    o.outer_iters = outer_iters;
+    o.cg_tol = cg_tol;
+    if (!opts_valid(o)) return IRLS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_simple_mu);
+    irls_plan p = nullptr;
+    int rc = irls_plan_create(H, W, &o, &p);
+    if (rc != IRLS_OK) return rc;
+    rc = irls_unwrap_ex(p, X, coh, nullptr, nullptr, nullptr, U, nullptr, nullptr, nullptr, stream);
+    irls_plan_destroy(p);
+    return rc;
+}
+
+int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) {
+    if (!p || !R || !Z) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        DeviceGuard g(p->dev);
+        StencilArgs a = make_args(p);
+        ck(cudaMemsetAsync(p->P.rU, 0, p->L.plane_bytes, s));
+        ck(launch_copy_in(R, p->H, p->W, p->P.rU, p->ld, s));
+        if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.ld16, s));
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, nullptr, a, nullptr, 0, s));
+        ck(launch_copy_out(p->P.zU, p->H, p->W, p->ld, Z, s));
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return IRLS_OK;
+}
+
+int irls_apply_A(irls_plan p, const float* U, const float* Vv, const float* Vh, const float* Dv,
+                 const float* Dh, float* qU, float* qVv, float* qVh, void* stream) {
+    if (!p || !U || !qU) return IRLS_ERR_ARG;
+    if (p->H > 1 && (!Vv || !Dv || !qVv)) return IRLS_ERR_ARG;
+    if (p->W > 1 && (!Vh || !Dh || !qVh)) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        DeviceGuard g(p->dev);
+        StencilArgs a = make_args(p);
+        const Planes& P = p->P;
+        const size_t pb = p->L.plane_bytes;
+        float* zero[] = {P.U, P.Vv, P.Vh, P.rU, P.rVv, P.rVh, P.pU[0], P.pVv[0], P.pVh[0], P.dv, P.dh};
+        for (float* z : zero) ck(cudaMemsetAsync(z, 0, pb, s));
+        ck(launch_copy_in(U, p->H, p->W, P.pU[0], p->ld, s));
+        if (p->H > 1) {
+            ck(launch_copy_in(Vv, p->H - 1, p->W, P.pVv[0], p->ld, s));
+            ck(launch_copy_in(Dv, p->H - 1, p->W, P.dv, p->ld, s));
+        }
+        if (p->W > 1) {
+            ck(launch_copy_in(Vh, p->H, p->W - 1, P.pVh[0], p->ld, s));
+            ck(launch_copy_in(Dh, p->H, p->W - 1, P.dh, p->ld, s));
+        }
+        ck(launch_matvec_via_update(P, a, p->st, p->partials, s));
+        ck(launch_copy_out(P.rU, p->H, p->W, p->ld, qU, s));
+        if (p->H > 1) ck(launch_copy_out(P.rVv, p->H - 1, p->W, p->ld, qVv, s));
+        if (p->W > 1) ck(launch_copy_out(P.rVh, p->H, p->W - 1, p->ld, qVh, s));
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return IRLS_OK;
+}
+
+int irls_plan_set_profiling(irls_plan p, int on) {
+    if (!p) return IRLS_ERR_ARG;
+    p->prof.on = on != 0;
+    p->prof.reset();
+    return IRLS_OK;
+}
+
+int irls_plan_profile(irls_plan p, double* ms, long long* launches, int n) {
+    if (!p || n < 0 || (n > 0 && (!ms || !launches))) return IRLS_ERR_ARG;
+    for (int i = 0; i < n && i < PC_N; ++i) {
+        ms[i] = p->prof.ms[i];
+        launches[i] = p->prof.n[i];
+    }
+    return PC_N;
+}
+
+const char* irls_status_string(int status) {
+    switch (status) {
+        case IRLS_OK: return "ok";
+        case IRLS_WARN_CG_MAX: return "warning: CG stopped on cg_max_iter before reaching cg_tol";
+        case IRLS_ERR_ARG: return "invalid argument";
+        case IRLS_ERR_SHAPE: return "invalid shape";
+        case IRLS_ERR_NONFINITE: return "non-finite input";
+        case IRLS_ERR_OOM: return "device out of memory";
+        case IRLS_ERR_BREAKDOWN: return "CG breakdown (non-positive curvature or rho)";
+        case IRLS_ERR_TIMEOUT: return "device-side wait timed out";
+        case IRLS_ERR_CUDA: return "CUDA runtime error";
+        case IRLS_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+int irls_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

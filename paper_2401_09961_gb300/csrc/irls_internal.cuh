@@ -1,0 +1,130 @@
+// Internal declarations shared by the libirls translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/irls.h"
+
+namespace irls {
+
+constexpr int kMaxOuter = IRLS_MAX_OUTER;
+
+// Device-side error bits, OR-ed into DevState::status.
+enum : int {
+    ST_NONFINITE = 1,
+    ST_BREAKDOWN = 2,
+    ST_TIMEOUT = 4,
+    ST_CGMAX = 8,
+};
+
+// Scalars of the IRLS / PCG state that never leave the device during a solve (Alg. 1, Alg. 2).
+// All reductions are FP64; every kernel that produces one finishes it in its last block.
+struct DevState {
+    double rho;      // r^T z of the current iterate
+    double alpha;    // rho / p^T A p
+    double beta;     // ratio that forms the next search direction
+    double pq;       // p^T A p
+    double rr;       // ||r||^2 after the last update
+    double bb;       // ||b||^2
+    double rz_v;     // V-block part of r^T z (from the kernel that produced r)
+    double rz_old;   // r_{l+1}^T z_l (Polak-Ribiere numerator term)
+    double mean_u;   // mean of U at the end of an outer step
+    double rel;      // ||r|| / ||b|| after the last update
+    double rnorm_u;  // ||r_U||_2 (used to scale the fp16 preconditioner input)
+    double pad0;
+    int done;        // the current CG run has stopped
+    int iter;        // CG iterations of the current run
+    int p_fresh;     // the next search direction is p = z (start of a CG run)
+    int status;      // OR of ST_* bits
+    int outer;       // outer iterations completed
+    int cg_total;
+    unsigned int counter;   // last-block-done ticket for the deterministic reductions
+    int pbuf;        // which ping-pong buffer holds the newest search direction
+    int cg_iters[kMaxOuter];
+    double rel_res[kMaxOuter];
+    double l1_obj[kMaxOuter];
+    double h_delta[kMaxOuter];
+    double f_delta[kMaxOuter];
+};
+
+// Image-shaped planes.  Every plane is H rows x ld floats (ld a multiple of 32); the vertical
+// edge planes use rows 0..H-2 and the horizontal ones columns 0..W-2; the unused row / column
+// and the pitch padding are kept at zero by every kernel.
+struct Planes {
+    float* U;  float* Vv;  float* Vh;          // iterate x = (U, Vv, Vh)
+    float* rU; float* rVv; float* rVh;         // residual r = b - A x
+    float* pU[2]; float* pVv[2]; float* pVh[2];// search directions (ping-pong)
+    float* zU;                                 // Laplacian-block preconditioner output
+    float* dv; float* dh;                      // D = C^2 / W
+    float* Wv; float* Wh;                      // W of the current outer step
+    float* Gv; float* Gh;                      // wrapped gradients
+    float* Cv; float* Ch;                      // edge weights
+};
+
+struct StencilArgs {
+    int H, W, ld;
+    float tau, inv_tau, delta;
+    double tol2;        // cg_tol^2
+    int cg_max;
+    int flexible;
+    int warm_start;
+    int cur;            // which pU/pVv/pVh buffer holds the newest direction
+    // optional bf16/fp16 emission of r_U for the tensor-core preconditioner
+    void* r16;          // Hp x Wp (row-major, pitch Wp) or nullptr
+    int ld16;
+    int prec;           // IRLS_PREC_*
+};
+
+// DCT-preconditioner resources owned by a plan.
+struct DctPlan {
+    int H, W, Hp, Wp;
+    int prec;
+    float tau;
+    // fp32 bases: P_N (Hp x Hp) with P_N[i][k], its transpose, and the same for M (may alias N)
+    float *PN, *PNT, *PM, *PMT;
+    float *lamN, *lamM;     // eigenvalues, padded with zeros
+    float *T1, *T2;         // fp32 intermediates (Wp x Hp each, reused)
+    // 16-bit copies for the tensor-core path
+    void *PN16, *PNT16, *PM16, *PMT16;
+    void *R16, *S16a, *S16b;   // 16-bit input and intermediates
+    void* tmaps;               // device-independent host copy of the TMA descriptors (opaque)
+    int umma_ok;
+};
+
+// ---- launchers (stencil kernels, irls_kernels.cu) -----------------------------------------
+cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, const float* Ch_in,
+                        const float* U0, const float* Vv0, const float* Vh0, const Planes& P,
+                        const StencilArgs& a, DevState* st, double* partials, cudaStream_t s);
+cudaError_t launch_bnorm(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                         cudaStream_t s);
+cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevState* st,
+                                     double* partials, cudaStream_t s);
+cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
+                                 double* partials, cudaStream_t s);
+cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                          cudaStream_t s);
+cudaError_t launch_finalize(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                            cudaStream_t s);
+cudaError_t launch_copy_out(const float* src, int rows, int cols, int ld, float* dst,
+                            cudaStream_t s);
+cudaError_t launch_copy_in(const float* src, int rows, int cols, float* dst, int ld,
+                           cudaStream_t s);
+cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevState* st,
+                                     double* partials, cudaStream_t s);
+cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, int ld16,
+                         cudaStream_t s);
+int stencil_grid_blocks(int H, int W);
+
+// ---- DCT preconditioner (dct.cu) ------------------------------------------------------------
+size_t dct_bytes(int H, int W, int prec);
+cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
+// z_U = L^+ (tau r_U) from the plane rU (pitch ld) into zU (pitch ld); with `st` non-null the
+// last GEMM also forms rho = r_U^T z_U + st->rz_v and the next beta (Alg. 2).
+cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
+                      const StencilArgs& a, double* partials, int skip_if_done, cudaStream_t s);
+int dct_max_blocks(int H, int W);
+
+}  // namespace irls

@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (stated by the method's acceptance bar for float32 unwraps): L1 objective within
+1e-4 relative, max |U_gpu - U_oracle| <= 1e-3 rad with both zero-mean, rounded integer maps
+agreeing on >= 99.9 % of the pixels.  Single operators (A x, the Laplacian preconditioner) are
+compared with a float32-rounding tolerance derived in the design notes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import irls as O
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def irls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_09961_gb300 as m
+    m.lib()
+    return m
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def k_agreement(U1, U2, X):
+    d = O.k_map(U1, X) - O.k_map(U2, X)
+    vals, cnt = np.unique(d, return_counts=True)
+    return cnt.max() / d.size
+
+
+def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4):
+    Ug = Ug - Ug.mean()
+    Uo = Uo - Uo.mean()
+    err = np.abs(Ug - Uo).max()
+    assert err <= atol, f"max |U_gpu - U_oracle| = {err}"
+    assert abs(l1g - l1o) <= l1_rtol * max(abs(l1o), 1e-12) + 1e-6, (l1g, l1o)
+    assert k_agreement(Ug, Uo, X) >= 0.999
+
+
+# ------------------------------------------------------------------------------------------
+# single operators
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W", [(64, 48), (130, 257), (256, 256), (1, 200), (300, 1), (3, 3)])
+def test_precond_laplacian_matches_oracle(irls, H, W):
+    rng = np.random.default_rng(H * 1000 + W)
+    R = rng.standard_normal((H, W)).astype(np.float32)
+    tau = 1e-2
+    with irls.Plan(H, W, tau=tau) as plan:
+        Z = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+    z_ref = O.precond_apply((R.astype(np.float64), np.zeros((H - 1, W)), np.zeros((H, W - 1))),
+                            np.zeros((H - 1, W)), np.zeros((H, W - 1)), tau, O.dct_basis(H),
+                            O.dct_basis(W))[0]
+    scale = np.abs(z_ref).max() + 1e-30
+    assert np.abs(Z - z_ref).max() <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (1, 64), (64, 1), (256, 256), (129, 130)])
+def test_apply_A_matches_oracle(irls, H, W):
+    rng = np.random.default_rng(H + 7 * W)
+    tau = 1e-2
+    U = rng.standard_normal((H, W)).astype(np.float32)
+    Vv = rng.standard_normal((H - 1, W)).astype(np.float32)
+    Vh = rng.standard_normal((H, W - 1)).astype(np.float32)
+    Dv = rng.uniform(0, 1e3, size=(H - 1, W)).astype(np.float32)
+    Dh = rng.uniform(0, 1e3, size=(H, W - 1)).astype(np.float32)
+    with irls.Plan(H, W, tau=tau) as plan:
+        q = irls.apply_A(plan, cuda(U), cuda(Vv), cuda(Vh), cuda(Dv), cuda(Dh))
+    qr = O.apply_A(tuple(a.astype(np.float64) for a in (U, Vv, Vh)), Dv.astype(np.float64),
+                   Dh.astype(np.float64), tau)
+    for g, r in zip(q, qr):
+        g = g.cpu().numpy()
+        if r.size:
+            assert np.abs(g - r).max() <= 2e-6 * (np.abs(r).max() + 1e-30) + 1e-5
+
+
+def test_apply_A_full_size_sampled(irls):
+    """4096 x 4096 (the benchmarked launch size): sampled outputs against a pointwise evaluation
+    of the stencil of eq. 'matrix-soft-constraints' at those pixels only."""
+    H = W = 4096
+    g = torch.Generator(device="cuda").manual_seed(5)
+    U = torch.randn(H, W, device="cuda", generator=g)
+    Vv = torch.randn(H - 1, W, device="cuda", generator=g)
+    Vh = torch.randn(H, W - 1, device="cuda", generator=g)
+    Dv = torch.rand(H - 1, W, device="cuda", generator=g) * 100
+    Dh = torch.rand(H, W - 1, device="cuda", generator=g) * 100
+    tau = 1e-2
+    with irls.Plan(H, W, tau=tau) as plan:
+        qU, qV, qH = (t.cpu().numpy() for t in irls.apply_A(plan, U, Vv, Vh, Dv, Dh))
+    Uc, Vvc, Vhc, Dvc, Dhc = (t.cpu().numpy().astype(np.float64) for t in (U, Vv, Vh, Dv, Dh))
+    rng = np.random.default_rng(0)
+    pts = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0), (2047, 128), (4095, 2000)]
+    pts += [tuple(x) for x in rng.integers(0, H, size=(200, 2))]
+    it = 1.0 / tau
+    for i, j in pts:
+        yv = lambda a, b: (Uc[a + 1, b] - Uc[a, b] - Vvc[a, b]) if 0 <= a < H - 1 else 0.0
+        yh = lambda a, b: (Uc[a, b + 1] - Uc[a, b] - Vhc[a, b]) if 0 <= b < W - 1 else 0.0
+        qu = it * (yv(i - 1, j) - yv(i, j) + yh(i, j - 1) - yh(i, j))
+        assert abs(qU[i, j] - qu) <= 1e-4 * (1 + abs(qu))
+        if i < H - 1:
+            qv = Dvc[i, j] * Vvc[i, j] - it * yv(i, j)
+            assert abs(qV[i, j] - qv) <= 1e-4 * (1 + abs(qv))
+        if j < W - 1:
+            qh = Dhc[i, j] * Vhc[i, j] - it * yh(i, j)
+            assert abs(qH[i, j] - qh) <= 1e-4 * (1 + abs(qh))
+
+
+# ------------------------------------------------------------------------------------------
+# full IRLS trajectories
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1])
+def test_unwrap_256_matches_oracle(irls, seed):
+    d = synthetic.config_small(seed)
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=10, cg_tol=1e-5, cg_max=1000)
+    ref = O.irls_unwrap(d["X"], None, **kw)
+    U, st = irls.unwrap(cuda(d["X"]), None, eps=1e-3, outer_iters=10, cg_tol=1e-5,
+                        return_stats=True)
+    assert st["outer_done"] == 10
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"])
+
+
+@pytest.mark.parametrize("H,W,seed", [(100, 75, 3), (67, 131, 4)])
+def test_unwrap_ragged_with_coherence_matches_oracle(irls, H, W, seed):
+    d = synthetic.config_2048(seed=seed, H=H, W=W)
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=6, cg_tol=1e-6, cg_max=1000)
+    ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
+    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=6,
+                        cg_tol=1e-6, return_stats=True)
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"])
+    np.testing.assert_allclose(st["f_delta"], ref["h_before"], rtol=1e-4)
+
+
+def test_unwrap_line_images(irls):
+    for H, W in ((1, 80), (80, 1)):
+        X = synthetic.config_small(5, H=H, W=W)["X"]
+        ref = O.irls_unwrap(X, None, tau=1e-2, delta=1e-3, outer_iters=4, cg_tol=1e-6)
+        U, st = irls.unwrap(cuda(X), None, eps=1e-3, outer_iters=4, cg_tol=1e-6, return_stats=True)
+        assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], X)
+
+
+def test_unwrap_2048_first_outer_matches_oracle(irls):
+    """2048 x 2048 coherence-weighted workload: one outer step with 4 CG iterations compared
+    element by element (the oracle finishes that in seconds)."""
+    d = synthetic.config_2048(seed=10)
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=1, cg_tol=1e-6, cg_max=4)
+    ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
+    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=1,
+                        cg_tol=1e-6, cg_max_iter=4, return_stats=True)
+    assert st["cg_iters"] == [4]
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"])
+
+
+def test_unwrap_2048_invariants(irls):
+    """Full 20-outer solve at 2048 x 2048: the monotone quantities of Sec. 3.1 hold on the
+    device statistics (H_delta after the solve <= before; reweighting decreases it further)."""
+    d = synthetic.config_2048(seed=11)
+    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=20,
+                        cg_tol=1e-6, return_stats=True)
+    f, h = st["f_delta"], st["h_delta"]
+    for k in range(len(h)):
+        assert h[k] <= f[k] * (1 + 1e-5)
+        if k + 1 < len(f):
+            assert f[k + 1] <= h[k] * (1 + 1e-5)
+    assert abs(float(U.mean())) < 1e-3
+    assert st["l1_obj"][-1] < st["l1_obj"][0]
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases and host-visible behaviour
+# ------------------------------------------------------------------------------------------
+def test_constant_input_gives_zero(irls):
+    X = np.full((33, 40), 1.25, dtype=np.float32)
+    U, st = irls.unwrap(cuda(X), None, eps=1e-3, outer_iters=3, cg_tol=1e-6, return_stats=True)
+    assert np.abs(U.cpu().numpy()).max() == 0.0
+    assert st["cg_iters"] == [0, 0, 0]
+
+
+def test_nonfinite_input_is_rejected(irls):
+    X = synthetic.config_small(0, H=32, W=32)["X"].copy()
+    X[5, 7] = np.nan
+    with pytest.raises(irls.IrlsError) as e:
+        irls.unwrap(cuda(X), None, outer_iters=2)
+    assert e.value.code == -3
+
+
+def test_cg_cap_warning_and_zero_cap(irls):
+    d = synthetic.config_2048(seed=3, H=64, W=64)
+    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=2,
+                        cg_tol=1e-12, cg_max_iter=3, return_stats=True)
+    assert st["cg_iters"] == [3, 3] and st["return_code"] == 1
+    U0, st0 = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=2,
+                          cg_tol=1e-6, cg_max_iter=0, return_stats=True)
+    assert st0["cg_iters"] == [0, 0] and np.abs(U0.cpu().numpy()).max() == 0.0
+
+
+def test_bitwise_deterministic(irls):
+    d = synthetic.config_2048(seed=7, H=300, W=200)
+    with irls.Plan(300, 200, delta=1e-3, outer_iters=5) as plan:
+        U1, s1 = plan.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+        U1 = U1.clone()
+        U2, s2 = plan.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+    assert torch.equal(U1, U2)
+    assert s1["l1_obj"] == s2["l1_obj"] and s1["cg_iters"] == s2["cg_iters"]
+
+
+def test_restart_from_returned_iterate(irls):
+    """(U, Vv, Vh) is a complete restart point: 3 + 3 outer steps equal 6 in one call."""
+    d = synthetic.config_2048(seed=8, H=96, W=80)
+    X, C = cuda(d["X"]), cuda(d["coherence"])
+    with irls.Plan(96, 80, delta=1e-3, outer_iters=6, cg_tol=1e-7) as plan:
+        U6, _ = plan.unwrap(X, C)
+        U6 = U6.clone()
+        plan.set_opts(outer_iters=3)
+        U3, Vv, Vh, _ = plan.unwrap(X, C, return_slacks=True)
+        U33, _ = plan.unwrap(X, C, U_init=U3.clone(), Vv_init=Vv.clone(), Vh_init=Vh.clone())
+    assert torch.allclose(U33, U6, atol=2e-4)
+
+
+def test_user_edge_weights_take_precedence(irls):
+    d = synthetic.config_2048(seed=9, H=50, W=60)
+    Cv, Ch = O.edge_weights(d["coherence"], 50, 60)
+    ref = O.irls_unwrap(d["X"], None, Cv=Cv ** 2, Ch=Ch ** 2, tau=1e-2, delta=1e-3,
+                        outer_iters=4, cg_tol=1e-6)
+    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), Cv=cuda(Cv ** 2), Ch=cuda(Ch ** 2),
+                        eps=1e-3, outer_iters=4, cg_tol=1e-6, return_stats=True)
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"])
+
+
+def test_host_arrays_round_trip(irls):
+    d = synthetic.config_small(2, H=64, W=64)
+    U = irls.unwrap(d["X"], None, eps=1e-3, outer_iters=3, cg_tol=1e-6)
+    assert not U.is_cuda and U.shape == (64, 64)
