@@ -19,8 +19,9 @@
 
 namespace irls {
 
-cudaError_t umma_dct_apply(const DctPlan& d, float* zU, int ld, DevState* st, const StencilArgs& a,
-                           double* partials, int skip_if_done, cudaStream_t s);
+cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
+                           int reduce_rho, const StencilArgs& a, double* partials,
+                           int skip_if_done, cudaStream_t s);
 size_t umma_dct_bytes(int H, int W);
 cudaError_t umma_dct_setup(DctPlan& d, char* mem);
 
@@ -240,9 +241,10 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) 
 }
 
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
-                      const StencilArgs& a, double* partials, int skip_if_done, cudaStream_t s) {
+                      int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
+                      cudaStream_t s) {
     if (d.prec != IRLS_PREC_FP32)
-        return umma_dct_apply(d, zU, ld, st, a, partials, skip_if_done, s);
+        return umma_dct_apply(d, rU, zU, ld, st, reduce_rho, a, partials, skip_if_done, s);
     const int H = d.H, W = d.W, Hp = d.Hp, Wp = d.Wp;
     cudaError_t e;
     EpiArgs ep{};
@@ -264,7 +266,7 @@ cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevS
     if (e != cudaSuccess) return e;
     // stage 4: Z[i][j] = sum_l T1[i][l] PM[j][l]
     ep.C = zU; ep.ldc = ld; ep.vm = H; ep.vn = W; ep.rU = rU;
-    if (st != nullptr && partials != nullptr)
+    if (reduce_rho)
         e = gemm<EPI_ZU_RHO>(d.T1, Wp, Hp, d.PM, Wp, Hp, Wp, W, ep, skip_if_done, s);
     else
         e = gemm<EPI_ZU>(d.T1, Wp, Hp, d.PM, Wp, Hp, Wp, W, ep, skip_if_done, s);

@@ -1,13 +1,541 @@
-// Tensor-core (tcgen05) form of the DCT preconditioner: placeholder until the kernel lands.
+// Tensor-core form of the Laplacian preconditioner block (Sec. 3.3 of arXiv 2401.09961): the
+// four dense products P_S^T R P_T and P_S Z' P_T^T on sm_103a tcgen05 tensor cores, bfloat16
+// operands with float32 accumulation in tensor memory.
+//
+// Every stage is a "TN" GEMM  D[m][n] = sum_k A[m][k] B[n][k]  with both operands K-contiguous,
+// arranged so that each stage's output is again K-contiguous for the next one:
+//   stage 1: T1[l][i] = sum_j PMT[l][j] R[i][j]                     (= (R P_T)^T)
+//   stage 2: T2[l][k] = tau sum_i T1[l][i] PNT[k][i] / (m_l + l_k)  (= ((P_S^T R P_T) / eig)^T)
+//   stage 3: T3[i][l] = sum_k PN[i][k] T2[l][k]                     (= P_S Z')
+//   stage 4: Z[i][j]  = sum_l T3[i][l] PM[j][l]                     (= P_S Z' P_T^T)
+//
+// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
+//   warp 0 lane 0  TMA producer: cp.async.bulk.tensor 2-D loads (128-byte swizzle) of the
+//                  128 x 64 A tile and the BN x 64 B tile into a ring of shared-memory stages,
+//                  each guarded by a full / empty mbarrier pair;
+//   warp 1 lane 0  MMA issuer: 4 x tcgen05.mma (K = 16 each) per stage into a 128 x BN fp32
+//                  accumulator in tensor memory, tcgen05.commit frees the stage;
+//   warp 2         allocates / frees the tensor-memory columns;
+//   all 4 warps    epilogue: tcgen05.ld of their 32 accumulator lanes, fused scaling
+//                  (eigenvalue divide, zero-frequency drop), conversion and store; the last stage
+//                  also reduces r_U^T z_U and forms the CG ratio beta (Alg. 2).
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel flags ST_TIMEOUT, stops
+// the CG run, releases its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "irls_internal.cuh"
+#include "reduce.cuh"
 
 namespace irls {
 
-size_t umma_dct_bytes(int, int) { return 0; }
-cudaError_t umma_dct_setup(DctPlan&, char*) { return cudaErrorNotSupported; }
-cudaError_t umma_dct_apply(const DctPlan&, float*, int, DevState*, const StencilArgs&, double*, int,
-                           cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int UBM = 128, UBK = 64;
+constexpr int kUThreads = 128;
+constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (about 2 s at 2 GHz)
+
+enum UEpi : int { UE_STORE16 = 0, UE_EIG16 = 1, UE_ZU = 2, UE_ZU_RHO = 3 };
+
+struct UEpiArgs {
+    void* C;             // bf16 output (STORE16 / EIG16) or float output (ZU)
+    int ldc;
+    int vm, vn;          // valid extents of the output
+    const float* lam_m;
+    const float* lam_n;
+    float scale;
+    const float* rU;     // residual plane (ZU_RHO), pitch ldc
+    DevState* st;        // never null: error flags; rho / beta for ZU_RHO
+    double* partials;
+    int flexible;
+    int skip_if_done;
+};
+
+template <int BN>
+struct UCfg {
+    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr int kABytes = UBM * UBK * 2;
+    static constexpr int kBBytes = BN * UBK * 2;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr uint32_t kTmemCols = BN;
+    // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (7-9 = 1), B bf16
+    // (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(UBM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the given phase parity; false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    if (mbar_try_wait(a, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(a, parity)) {
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns of tensor memory into 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with 128-byte swizzling:
+// rows of 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset), descriptor version 1,
+// layout code 2 (SWIZZLE_128B).  The leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kUThreads, 1)
+k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
+            UEpiArgs ep) {
+    using C = UCfg<BN>;
+    if (ep.skip_if_done && ep.st->done) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* accf = empty + C::kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    __shared__ int s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * UBM, n0 = blockIdx.x * BN;
+    const int nkb = K / UBK;
+
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        fence_mbar_init();
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, C::kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % C::kStages;
+                const uint32_t ph = (uint32_t)(kb / C::kStages) & 1u;
+                if (kb >= C::kStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                uint8_t* sa = smem + s * C::kStageBytes;
+                mbar_expect_tx(&full[s], C::kStageBytes);
+                tma_load_2d(sa, &tmA, &full[s], kb * UBK, m0);
+                tma_load_2d(sa + C::kABytes, &tmB, &full[s], kb * UBK, n0);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % C::kStages;
+                const uint32_t ph = (uint32_t)(kb / C::kStages) & 1u;
+                if (!mbar_wait(&full[s], ph)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
+                const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + C::kABytes);
+#pragma unroll
+                for (int j = 0; j < UBK / 16; ++j)   // K = 16 per MMA: +32 bytes (= 2 in >> 4)
+                    umma_bf16(tmem, da + 2 * j, db + 2 * j, C::kIdesc, (kb | j) != 0);
+                umma_commit(&empty[s]);
+            }
+            umma_commit(accf);
+        }
+        __syncwarp();
+    }
+
+    // ---- epilogue ----
+    const bool ok = mbar_wait(accf, 0);
+    tc_fence_after();
+    __syncthreads();
+    const bool good = ok && (*(volatile int*)&s_err == 0);
+    if (!good && threadIdx.x == 0) {
+        atomicOr(&ep.st->status, ST_TIMEOUT);
+        ep.st->done = 1;
+    }
+    const int m = m0 + warp * 32 + lane;
+    float part = 0.f;
+    if (good) {
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+            const int nb = n0 + c * 32;
+            if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+                float v[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+                if constexpr (EPI == UE_EIG16) {
+                    const bool rowok = m < ep.vm;
+                    const float lm = rowok ? ep.lam_m[m] : 0.f;
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int n = nb + t;
+                        const bool keep = rowok && n < ep.vn && (m | n) != 0;
+                        v[t] = keep ? ep.scale * v[t] / (lm + __ldg(&ep.lam_n[n])) : 0.f;
+                    }
+                }
+                uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C) +
+                                                      (size_t)m * ep.ldc + nb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 w;
+                    w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                    w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                    w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                    w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                    dst[q] = w;
+                }
+            } else {
+                if (m < ep.vm) {
+                    float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
+                    const float* rr = ep.rU + (size_t)m * ep.ldc;
+                    if (nb + 32 <= ep.vn) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            float4 w = make_float4(__uint_as_float(r[4 * q]),
+                                                   __uint_as_float(r[4 * q + 1]),
+                                                   __uint_as_float(r[4 * q + 2]),
+                                                   __uint_as_float(r[4 * q + 3]));
+                            reinterpret_cast<float4*>(out + nb)[q] = w;
+                            if constexpr (EPI == UE_ZU_RHO) {
+                                const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
+                                part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 32; ++t) {
+                            if (nb + t < ep.vn) {
+                                const float z = __uint_as_float(r[t]);
+                                out[nb + t] = z;
+                                if constexpr (EPI == UE_ZU_RHO) part += rr[nb + t] * z;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        tmem_dealloc(tmem, C::kTmemCols);
+    }
+    if constexpr (EPI == UE_ZU_RHO) {
+        double vv[1] = {(double)part}, tot[1];
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot) && threadIdx.x == 0) {
+            DevState* st = ep.st;
+            const double rho_new = tot[0] + st->rz_v;
+            if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+                if (st->rr > 0.0) st->status |= ST_BREAKDOWN;
+                st->done = 1;
+            } else if (st->p_fresh) {
+                st->rho = rho_new;
+                st->beta = 0.0;
+            } else {
+                const double num = ep.flexible ? rho_new - st->rz_old : rho_new;
+                st->beta = num / st->rho;
+                st->rho = rho_new;
+            }
+        }
+    }
+}
+
+__global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, int N, int Np) {
+    const size_t total = (size_t)Np * Np;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / Np), k = (int)(t % Np);
+        double v = 0.0;
+        if (i < N && k < N) {
+            const long long mm = ((long long)(2 * i + 1) * k) % (4LL * N);
+            const double ck = k == 0 ? sqrt(1.0 / N) : sqrt(2.0 / N);
+            v = ck * cospi((double)mm / (2.0 * N));
+        }
+        P16[(size_t)i * Np + k] = __double2bfloat16(v);
+        PT16[(size_t)k * Np + i] = __double2bfloat16(v);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side: TMA descriptors and launches
+// ------------------------------------------------------------------------------------------
+struct TmapSet {
+    CUtensorMap a[4];
+    CUtensorMap b[4];
+};
+static_assert(sizeof(TmapSet) <= sizeof(((DctPlan*)nullptr)->tmap_storage), "tmap storage");
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// row-major bf16 matrix rows x cols (cols contiguous), box = 64 columns x box_rows rows
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)UBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int pick_bn(int N) { return (N % 256 == 0) ? 256 : 128; }
+
+template <int BN, int EPI>
+cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
+                       const UEpiArgs& ep, cudaStream_t s) {
+    using C = UCfg<BN>;
+    dim3 grid(N / BN, M / UBM);
+    k_umma_gemm<BN, EPI><<<grid, kUThreads, C::kSmem, s>>>(a, b, K, ep);
+    return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t launch_stage(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
+                         const UEpiArgs& ep, cudaStream_t s) {
+    if (pick_bn(N) == 256) return launch_one<256, EPI>(a, b, M, N, K, ep, s);
+    return launch_one<128, EPI>(a, b, M, N, K, ep, s);
+}
+
+inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <int BN>
+cudaError_t set_attrs() {
+    const int sm = UCfg<BN>::kSmem;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_STORE16>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_EIG16>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU_RHO>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+}  // namespace
+
+size_t umma_dct_bytes(int H, int W) {
+    const size_t Hp = rup(H, 128), Wp = rup(W, 128);
+    size_t n = 2 * Hp * Hp + 3 * Hp * Wp;
+    if (H != W) n += 2 * Wp * Wp;
+    return n * 2 + 16 * 1024;
+}
+
+cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
+    const size_t Hp = d.Hp, Wp = d.Wp;
+    char* p = mem;
+    auto take = [&](size_t elems) {
+        void* r = p;
+        p += rup(elems * 2, 1024);
+        return r;
+    };
+    d.PN16 = take(Hp * Hp);
+    d.PNT16 = take(Hp * Hp);
+    if (d.H != d.W) {
+        d.PM16 = take(Wp * Wp);
+        d.PMT16 = take(Wp * Wp);
+    } else {
+        d.PM16 = d.PN16;
+        d.PMT16 = d.PNT16;
+    }
+    d.R16 = take(Hp * Wp);
+    d.S16a = take(Hp * Wp);
+    d.S16b = take(Hp * Wp);
+    k_build_basis16<<<1024, 256>>>(static_cast<__nv_bfloat16*>(d.PN16),
+                                   static_cast<__nv_bfloat16*>(d.PNT16), d.H, d.Hp);
+    if (d.H != d.W)
+        k_build_basis16<<<1024, 256>>>(static_cast<__nv_bfloat16*>(d.PM16),
+                                       static_cast<__nv_bfloat16*>(d.PMT16), d.W, d.Wp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TmapSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    const int H_ = d.Hp, W_ = d.Wp;
+    bool ok = true;
+    // stage 1: A = PMT (Wp x Wp), B = R (Hp x Wp)
+    ok &= make_map(&ts.a[0], d.PMT16, W_, W_, UBM);
+    ok &= make_map(&ts.b[0], d.R16, H_, W_, pick_bn(H_));
+    // stage 2: A = T1 (Wp x Hp), B = PNT (Hp x Hp)
+    ok &= make_map(&ts.a[1], d.S16a, W_, H_, UBM);
+    ok &= make_map(&ts.b[1], d.PNT16, H_, H_, pick_bn(H_));
+    // stage 3: A = PN (Hp x Hp), B = T2 (Wp x Hp)
+    ok &= make_map(&ts.a[2], d.PN16, H_, H_, UBM);
+    ok &= make_map(&ts.b[2], d.S16b, W_, H_, pick_bn(W_));
+    // stage 4: A = T3 (Hp x Wp), B = PM (Wp x Wp)
+    ok &= make_map(&ts.a[3], d.S16a, H_, W_, UBM);
+    ok &= make_map(&ts.b[3], d.PM16, W_, W_, pick_bn(W_));
+    if (!ok) return cudaErrorNotSupported;
+    if ((e = set_attrs<256>()) != cudaSuccess) return e;
+    if ((e = set_attrs<128>()) != cudaSuccess) return e;
+    std::memcpy(d.tmap_storage, &ts, sizeof(ts));
+    d.umma_ok = 1;
+    return cudaSuccess;
+}
+
+cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
+                           int reduce_rho, const StencilArgs& a, double* partials,
+                           int skip_if_done, cudaStream_t s) {
+    if (!d.umma_ok) return cudaErrorNotSupported;
+    const TmapSet& ts = *reinterpret_cast<const TmapSet*>(d.tmap_storage);
+    const int Hp = d.Hp, Wp = d.Wp;
+    UEpiArgs ep{};
+    ep.st = st;
+    ep.partials = partials;
+    ep.flexible = a.flexible;
+    ep.skip_if_done = skip_if_done;
+    cudaError_t e;
+    // stage 1: T1 (Wp x Hp) = PMT . R^T
+    ep.C = d.S16a; ep.ldc = Hp;
+    e = launch_stage<UE_STORE16>(ts.a[0], ts.b[0], Wp, Hp, Wp, ep, s);
+    if (e != cudaSuccess) return e;
+    // stage 2: T2 (Wp x Hp) = tau (T1 . PNT^T) / eig, zero frequency and padding -> 0
+    ep.C = d.S16b; ep.ldc = Hp; ep.vm = d.W; ep.vn = d.H; ep.lam_m = d.lamM; ep.lam_n = d.lamN;
+    ep.scale = d.tau;
+    e = launch_stage<UE_EIG16>(ts.a[1], ts.b[1], Wp, Hp, Hp, ep, s);
+    if (e != cudaSuccess) return e;
+    // stage 3: T3 (Hp x Wp) = PN . T2^T
+    ep.C = d.S16a; ep.ldc = Wp;
+    e = launch_stage<UE_STORE16>(ts.a[2], ts.b[2], Hp, Wp, Hp, ep, s);
+    if (e != cudaSuccess) return e;
+    // stage 4: Z (H x W, pitch ld) = T3 . PM^T, and rho / beta
+    ep.C = zU; ep.ldc = ld; ep.vm = d.H; ep.vn = d.W; ep.rU = rU;
+    if (reduce_rho) {
+        return launch_stage<UE_ZU_RHO>(ts.a[3], ts.b[3], Hp, Wp, Wp, ep, s);
+    }
+    return launch_stage<UE_ZU>(ts.a[3], ts.b[3], Hp, Wp, Wp, ep, s);
 }
 
 }  // namespace irls

@@ -225,7 +225,7 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
         ck(launch_reweight_residual(p->P, a, st, p->partials, s));
         pf.end(PC_REWEIGHT, t0, s);
         t0 = pf.begin(s);
-        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, a, p->partials, 1, s));
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
         pf.end(PC_DCT, t0, s);
         int issued = 0, slot = 0;
         bool pending = false;
@@ -240,7 +240,7 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
                 ck(launch_update(p->P, a, st, p->partials, s));
                 pf.end(PC_UPDATE, t0, s);
                 t0 = pf.begin(s);
-                ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, a, p->partials, 1, s));
+                ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
                 pf.end(PC_DCT, t0, s);
             }
             issued += n;
@@ -439,7 +439,7 @@ int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) 
         ck(cudaMemsetAsync(p->P.rU, 0, p->L.plane_bytes, s));
         ck(launch_copy_in(R, p->H, p->W, p->P.rU, p->ld, s));
         if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.ld16, s));
-        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, nullptr, a, nullptr, 0, s));
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, p->st, 0, a, p->partials, 0, s));
         ck(launch_copy_out(p->P.zU, p->H, p->W, p->ld, Z, s));
     } catch (Fail&) {
         return IRLS_ERR_CUDA;

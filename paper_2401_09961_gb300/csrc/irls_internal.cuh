@@ -90,8 +90,8 @@ struct DctPlan {
     // 16-bit copies for the tensor-core path
     void *PN16, *PNT16, *PM16, *PMT16;
     void *R16, *S16a, *S16b;   // 16-bit input and intermediates
-    void* tmaps;               // device-independent host copy of the TMA descriptors (opaque)
     int umma_ok;
+    alignas(64) unsigned char tmap_storage[1024];   // TMA descriptors of the four stages
 };
 
 // ---- launchers (stencil kernels, irls_kernels.cu) -----------------------------------------
@@ -121,10 +121,12 @@ int stencil_grid_blocks(int H, int W);
 // ---- DCT preconditioner (dct.cu) ------------------------------------------------------------
 size_t dct_bytes(int H, int W, int prec);
 cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
-// z_U = L^+ (tau r_U) from the plane rU (pitch ld) into zU (pitch ld); with `st` non-null the
-// last GEMM also forms rho = r_U^T z_U + st->rz_v and the next beta (Alg. 2).
+// z_U = L^+ (tau r_U) from the plane rU (pitch ld) into zU (pitch ld).  `st` (never null)
+// receives error flags; with reduce_rho the last GEMM also forms rho = r_U^T z_U + st->rz_v
+// and the next beta (Alg. 2).  With skip_if_done the launches return at once once CG stopped.
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
-                      const StencilArgs& a, double* partials, int skip_if_done, cudaStream_t s);
+                      int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
+                      cudaStream_t s);
 int dct_max_blocks(int H, int W);
 
 }  // namespace irls

@@ -356,30 +356,32 @@ k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blockIdx.x * kThreads + threadIdx.x;
     const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
-    const float it = a.inv_tau, d2 = a.delta * a.delta;
-    float su = 0.f, l1 = 0.f, hd = 0.f;
+    const double it = 1.0 / (double)a.tau, d2 = (double)a.delta * (double)a.delta;
+    // FP64 evaluation: the difference of two float32 values is exact in double, so the edge
+    // residuals of the objective carry no cancellation error of their own
+    double su = 0.0, l1 = 0.0, hd = 0.0;
     if (j < W) {
         for (int i = i0; i < i1; ++i) {
             const size_t o = (size_t)i * ld + j;
-            const float u = P.U[o];
+            const double u = P.U[o];
             su += u;
             if (i + 1 < H) {
-                const float e = P.U[o + ld] - u - P.Gv[o];
-                const float c = P.Cv[o], v = P.Vv[o], w = P.Wv[o];
-                l1 += c * fabsf(e);
-                const float pe = e - v;
-                hd += 0.5f * ((c * c * v * v + d2) / w + w) + 0.5f * it * pe * pe;
+                const double e = ((double)P.U[o + ld] - u) - (double)P.Gv[o];
+                const double c = P.Cv[o], v = P.Vv[o], w = P.Wv[o];
+                l1 += c * fabs(e);
+                const double pe = e - v;
+                hd += 0.5 * ((c * c * v * v + d2) / w + w) + 0.5 * it * pe * pe;
             }
             if (j + 1 < W) {
-                const float e = P.U[o + 1] - u - P.Gh[o];
-                const float c = P.Ch[o], v = P.Vh[o], w = P.Wh[o];
-                l1 += c * fabsf(e);
-                const float pe = e - v;
-                hd += 0.5f * ((c * c * v * v + d2) / w + w) + 0.5f * it * pe * pe;
+                const double e = ((double)P.U[o + 1] - u) - (double)P.Gh[o];
+                const double c = P.Ch[o], v = P.Vh[o], w = P.Wh[o];
+                l1 += c * fabs(e);
+                const double pe = e - v;
+                hd += 0.5 * ((c * c * v * v + d2) / w + w) + 0.5 * it * pe * pe;
             }
         }
     }
-    double v[3] = {(double)su, (double)l1, (double)hd}, tot[3];
+    double v[3] = {su, l1, hd}, tot[3];
     if (grid_reduce<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
         st->mean_u = tot[0] / ((double)H * (double)W);
         const int k = st->outer;
