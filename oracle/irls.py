@@ -187,20 +187,30 @@ def _axpy(alpha, x, y):
     return tuple(yi + alpha * xi for xi, yi in zip(x, y))
 
 
-def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr"):
+def _stored(v, storage):
+    if storage is None:
+        return v
+    return tuple(np.asarray(a, dtype=storage).astype(np.float64) for a in v)
+
+
+def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None):
     """Preconditioned CG (Alg. 2) on A x = b from the warm start x0.
 
     Stops when ||r|| / ||b|| <= tol or after cg_max products with A.  ``beta_rule`` 'fr' is the
     Fletcher-Reeves ratio printed in Alg. 2; 'pr' is the Polak-Ribiere (flexible) ratio
-    r_{l+1}^T (z_{l+1} - z_l) / rho_l, which equals it in exact arithmetic.
+    r_{l+1}^T (z_{l+1} - z_l) / rho_l, which equals it in exact arithmetic.  ``storage`` (None or
+    a numpy dtype such as float32) rounds the vectors x, r, z, p to that type after every update:
+    another valid floating-point execution of the same algorithm, used to measure how far such
+    executions spread; the arithmetic itself stays float64.
     Returns (x, iterations, final relative residual, status); status -5 flags a breakdown."""
-    x = tuple(np.array(a, dtype=np.float64) for a in x0)
+    x = _stored(tuple(np.array(a, dtype=np.float64) for a in x0), storage)
     bnorm = math.sqrt(_dot(b, b))
     r = tuple(bi - qi for bi, qi in zip(b, apply_A(x, dv, dh, tau)))
     rel = math.sqrt(_dot(r, r)) / bnorm if bnorm > 0 else 0.0
     if bnorm == 0.0 or rel <= tol or cg_max <= 0:
         return x, 0, rel, 0
-    z = precond_apply(r, dv, dh, tau, basis_N, basis_M)
+    r = _stored(r, storage)
+    z = _stored(precond_apply(r, dv, dh, tau, basis_N, basis_M), storage)
     p = z
     rho = _dot(r, z)
     it = 0
@@ -210,13 +220,13 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr"):
         if not (pq > 0.0 and rho > 0.0):
             return x, it, rel, -5
         alpha = rho / pq
-        x = _axpy(alpha, p, x)
-        r = _axpy(-alpha, q, r)
+        x = _stored(_axpy(alpha, p, x), storage)
+        r = _stored(_axpy(-alpha, q, r), storage)
         it += 1
         rel = math.sqrt(_dot(r, r)) / bnorm
         if rel <= tol or it >= cg_max:
             return x, it, rel, 0
-        z_new = precond_apply(r, dv, dh, tau, basis_N, basis_M)
+        z_new = _stored(precond_apply(r, dv, dh, tau, basis_N, basis_M), storage)
         rho_new = _dot(r, z_new)
         if beta_rule == "pr":
             beta = (rho_new - _dot(r, z)) / rho
@@ -224,7 +234,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr"):
             beta = rho_new / rho
         rho = rho_new
         z = z_new
-        p = tuple(zi + beta * pi for zi, pi in zip(z_new, p))
+        p = _stored(tuple(zi + beta * pi for zi, pi in zip(z_new, p)), storage)
 
 
 # --------------------------------------------------------------------------------------------
@@ -298,13 +308,14 @@ class Problem:
 
 
 def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
-                cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False):
+                cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None):
     """Alg. 1 with Alg. 2 as the inner solver, for a fixed number of outer iterations.
 
     Returns a dict with U (zero mean), Vv, Vh, and per-outer statistics: cg_iters, rel_res,
     l1_obj (problem (main) at U^{k+1}), h_delta (H_delta(x^{k+1}, W^k)), h_before
     (H_delta(x^k, W^k)), h_after_rw (H_delta(x^{k+1}, W^{k+1})), f_delta, status.  With
-    ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint)."""
+    ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
+    ``storage`` is passed to pcg (float64 arithmetic with rounded vector storage)."""
     pb = Problem(X, coherence, Cv, Ch, tau)
     N, M = pb.N, pb.M
     if x0 is None:
@@ -325,7 +336,7 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
             rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         st["h_before"].append(H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
         (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
-                                      cg_tol, cg_max, beta_rule)
+                                      cg_tol, cg_max, beta_rule, storage)
         if s < 0:
             status = s
         elif it >= cg_max and rel > cg_tol and status == 0:
