@@ -151,7 +151,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=4096)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -178,7 +178,7 @@ def main():
     d = synthetic.config_4096_mixed(seed=20 + rank, H=n, W=n)
     X = torch.as_tensor(d["X"]).cuda()
     C = torch.as_tensor(d["coherence"]).cuda()
-    flexible = 0 if prec == "fp32" else 1
+    flexible = 1 if prec == "bf16" else 0
     plan = irls.Plan(n, n, tau=TAU, delta=DELTA, outer_iters=OUTER, cg_tol=CG_TOL,
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible)
     stream = torch.cuda.current_stream()

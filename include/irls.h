@@ -49,9 +49,10 @@ extern "C" {
 #define IRLS_ERR_UNSUPPORTED -8  /* option not available for this shape / device               */
 
 /* ---- precision of the DCT preconditioner (Sec. 3.3 dense products) -------------------- */
-#define IRLS_PREC_FP32  0   /* float32 operands, float32 accumulation (SIMT FMA)              */
-#define IRLS_PREC_BF16  1   /* bfloat16 operands, float32 accumulation (tcgen05 tensor cores) */
-#define IRLS_PREC_FP16  2   /* float16 operands with per-apply scaling, float32 accumulation  */
+#define IRLS_PREC_FP32   0  /* float32 operands, float32 accumulation (SIMT FMA)              */
+#define IRLS_PREC_BF16   1  /* bfloat16 operands, float32 accumulation (tcgen05), one pass    */
+#define IRLS_PREC_BF16X3 2  /* split bfloat16: x = hi + lo, three tcgen05 products per GEMM   */
+                            /* (hi*hi + hi*lo + lo*hi), float32 accumulation                  */
 
 #define IRLS_MAX_OUTER 256
 
@@ -98,8 +99,8 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out);
 /* Release a plan and its device memory (synchronises the device first).  NULL is a no-op. */
 int irls_plan_destroy(irls_plan plan);
 
-/* Replace the plan's options (same H, W).  Changing `precision` is allowed only between the
- * values the plan was created with support for (IRLS_ERR_UNSUPPORTED otherwise). */
+/* Replace the plan's options (same H, W).  `precision` may change only to IRLS_PREC_FP32 or to
+ * the precision the plan was created with (IRLS_ERR_UNSUPPORTED otherwise). */
 int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
 
 /* Simple form: unwrap d_X (H x W) into d_U (H x W, zero mean) with weights from d_coherence

@@ -135,7 +135,9 @@ def unwrap(X, coherence=None, *, eps=1e-3, outer_iters=20, cg_tol=1e-6, tau=1e-2
     Xd = dev(X)
     H, W = Xd.shape
     if flexible_cg is None:
-        flexible_cg = 0 if precision == "fp32" else 1
+        # the single-pass bf16 preconditioner is inexact enough to need the flexible ratio;
+        # fp32 and the split bf16x3 form converge like exact arithmetic with the ratio of Alg. 2
+        flexible_cg = 1 if precision == "bf16" else 0
     own = plan is None
     if own:
         plan = Plan(H, W, tau=tau, delta=eps, outer_iters=outer_iters, cg_tol=cg_tol,

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libirls.so")
 
 IRLS_MAX_OUTER = 256
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
 STATUS = {
     0: "IRLS_OK", 1: "IRLS_WARN_CG_MAX", -1: "IRLS_ERR_ARG", -2: "IRLS_ERR_SHAPE",

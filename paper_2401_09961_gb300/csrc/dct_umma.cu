@@ -21,6 +21,13 @@
 //                  also reduces r_U^T z_U and forms the CG ratio beta (Alg. 2).
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel flags ST_TIMEOUT, stops
 // the CG run, releases its tensor memory and returns.
+//
+// Split precision (IRLS_PREC_BF16X3): every float32 operand x is carried as two bfloat16 parts,
+// hi = bf16(x) and lo = bf16(x - hi), and each product is formed as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi in the same float32 accumulator (the dropped A_lo B_lo term
+// and the residual of the split are below 2^-16 relative).  A single bfloat16 pass rounds at
+// 2^-9, and that error, leaked into the lowest frequencies by the forward transform, is
+// amplified by tau / (l_i + m_j) (about 1e4 at 4096 x 4096): the inner CG then stalls.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -41,6 +48,7 @@ enum UEpi : int { UE_STORE16 = 0, UE_EIG16 = 1, UE_ZU = 2, UE_ZU_RHO = 3 };
 
 struct UEpiArgs {
     void* C;             // bf16 output (STORE16 / EIG16) or float output (ZU)
+    void* C_lo;          // bf16 low part of a split output, or null
     int ldc;
     int vm, vn;          // valid extents of the output
     const float* lam_m;
@@ -53,12 +61,12 @@ struct UEpiArgs {
     int skip_if_done;
 };
 
-template <int BN>
+template <int BN, int SA, int SB>
 struct UCfg {
-    static constexpr int kStages = BN == 256 ? 4 : 6;
-    static constexpr int kABytes = UBM * UBK * 2;
-    static constexpr int kBBytes = BN * UBK * 2;
-    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kABytes = UBM * UBK * 2;             // one bf16 part of the A tile
+    static constexpr int kBBytes = BN * UBK * 2;              // one bf16 part of the B tile
+    static constexpr int kStageBytes = SA * kABytes + SB * kBBytes;
+    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
     static constexpr uint32_t kTmemCols = BN;
     // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (7-9 = 1), B bf16
@@ -185,11 +193,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int SA, int SB>
 __global__ void __launch_bounds__(kUThreads, 1)
-k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
-            UEpiArgs ep) {
-    using C = UCfg<BN>;
+k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+            const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+            int K, UEpiArgs ep) {
+    using C = UCfg<BN, SA, SB>;
     if (ep.skip_if_done && ep.st->done) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -229,9 +238,12 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     break;
                 }
                 uint8_t* sa = smem + s * C::kStageBytes;
+                uint8_t* sb = sa + SA * C::kABytes;
                 mbar_expect_tx(&full[s], C::kStageBytes);
-                tma_load_2d(sa, &tmA, &full[s], kb * UBK, m0);
-                tma_load_2d(sa + C::kABytes, &tmB, &full[s], kb * UBK, n0);
+                tma_load_2d(sa, &tmA0, &full[s], kb * UBK, m0);
+                if constexpr (SA == 2) tma_load_2d(sa + C::kABytes, &tmA1, &full[s], kb * UBK, m0);
+                tma_load_2d(sb, &tmB0, &full[s], kb * UBK, n0);
+                if constexpr (SB == 2) tma_load_2d(sb + C::kBBytes, &tmB1, &full[s], kb * UBK, n0);
             }
         }
         __syncwarp();
@@ -246,10 +258,16 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
-                const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + C::kABytes);
+                const uint32_t sb = sa + SA * C::kABytes;
+                const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
+                const uint64_t dal = desc_sw128(sa + C::kABytes), dbl = desc_sw128(sb + C::kBBytes);
 #pragma unroll
-                for (int j = 0; j < UBK / 16; ++j)   // K = 16 per MMA: +32 bytes (= 2 in >> 4)
-                    umma_bf16(tmem, da + 2 * j, db + 2 * j, C::kIdesc, (kb | j) != 0);
+                for (int j = 0; j < UBK / 16; ++j) {   // K = 16 per MMA: +32 bytes (= 2 in >> 4)
+                    if constexpr (SB == 2) umma_bf16(tmem, da + 2 * j, dbl + 2 * j, C::kIdesc, (kb | j) != 0);
+                    if constexpr (SA == 2)
+                        umma_bf16(tmem, dal + 2 * j, db + 2 * j, C::kIdesc, SB == 2 || (kb | j) != 0);
+                    umma_bf16(tmem, da + 2 * j, db + 2 * j, C::kIdesc, SA == 2 || SB == 2 || (kb | j) != 0);
+                }
                 umma_commit(&empty[s]);
             }
             umma_commit(accf);
@@ -290,14 +308,40 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C) +
                                                       (size_t)m * ep.ldc + nb);
+                if (ep.C_lo == nullptr) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 w;
-                    w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-                    w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-                    w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-                    w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-                    dst[q] = w;
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 w;
+                        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                        dst[q] = w;
+                    }
+                } else {
+                    uint4* dlo = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C_lo) +
+                                                          (size_t)m * ep.ldc + nb);
+                    float lo[32];
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const float h = __bfloat162float(__float2bfloat16_rn(v[t]));
+                        lo[t] = v[t] - h;
+                        v[t] = h;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 w, wl;
+                        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                        wl.x = pack_bf16(lo[8 * q + 0], lo[8 * q + 1]);
+                        wl.y = pack_bf16(lo[8 * q + 2], lo[8 * q + 3]);
+                        wl.z = pack_bf16(lo[8 * q + 4], lo[8 * q + 5]);
+                        wl.w = pack_bf16(lo[8 * q + 6], lo[8 * q + 7]);
+                        dst[q] = w;
+                        dlo[q] = wl;
+                    }
                 }
             } else {
                 if (m < ep.vm) {
@@ -356,7 +400,8 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
-__global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, int N, int Np) {
+__global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bfloat16* P16lo,
+                                __nv_bfloat16* PT16lo, int N, int Np) {
     const size_t total = (size_t)Np * Np;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
@@ -367,17 +412,25 @@ __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, int N, 
             const double ck = k == 0 ? sqrt(1.0 / N) : sqrt(2.0 / N);
             v = ck * cospi((double)mm / (2.0 * N));
         }
-        P16[(size_t)i * Np + k] = __double2bfloat16(v);
-        PT16[(size_t)k * Np + i] = __double2bfloat16(v);
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        P16[(size_t)i * Np + k] = h;
+        PT16[(size_t)k * Np + i] = h;
+        if (P16lo) {
+            const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+            P16lo[(size_t)i * Np + k] = l;
+            PT16lo[(size_t)k * Np + i] = l;
+        }
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // host side: TMA descriptors and launches
 // ------------------------------------------------------------------------------------------
+struct StageMaps {
+    CUtensorMap a0, a1, b0, b1;
+};
 struct TmapSet {
-    CUtensorMap a[4];
-    CUtensorMap b[4];
+    StageMaps st[4];
 };
 static_assert(sizeof(TmapSet) <= sizeof(((DctPlan*)nullptr)->tmap_storage), "tmap storage");
 
@@ -408,98 +461,116 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-int pick_bn(int N) { return (N % 256 == 0) ? 256 : 128; }
+// output tile width: 256 for single-pass stages when N allows it; split stages use 128 so that
+// three shared-memory stages of four operand parts fit
+int pick_bn(int N, bool split) { return (!split && N % 256 == 0) ? 256 : 128; }
 
-template <int BN, int EPI>
-cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
-                       const UEpiArgs& ep, cudaStream_t s) {
-    using C = UCfg<BN>;
+template <int BN, int EPI, int SA, int SB>
+cudaError_t launch_one(const StageMaps& m, int M, int N, int K, const UEpiArgs& ep,
+                       cudaStream_t s) {
+    using C = UCfg<BN, SA, SB>;
     dim3 grid(N / BN, M / UBM);
-    k_umma_gemm<BN, EPI><<<grid, kUThreads, C::kSmem, s>>>(a, b, K, ep);
+    k_umma_gemm<BN, EPI, SA, SB><<<grid, kUThreads, C::kSmem, s>>>(m.a0, m.a1, m.b0, m.b1, K, ep);
     return cudaGetLastError();
 }
 
 template <int EPI>
-cudaError_t launch_stage(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
-                         const UEpiArgs& ep, cudaStream_t s) {
-    if (pick_bn(N) == 256) return launch_one<256, EPI>(a, b, M, N, K, ep, s);
-    return launch_one<128, EPI>(a, b, M, N, K, ep, s);
+cudaError_t launch_stage(const StageMaps& m, int M, int N, int K, bool split, const UEpiArgs& ep,
+                         cudaStream_t s) {
+    if (split) return launch_one<128, EPI, 2, 2>(m, M, N, K, ep, s);
+    if (pick_bn(N, false) == 256) return launch_one<256, EPI, 1, 1>(m, M, N, K, ep, s);
+    return launch_one<128, EPI, 1, 1>(m, M, N, K, ep, s);
 }
 
 inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int BN>
+template <int BN, int SA, int SB>
 cudaError_t set_attrs() {
-    const int sm = UCfg<BN>::kSmem;
+    const int sm = UCfg<BN, SA, SB>::kSmem;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_STORE16>,
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_STORE16, SA, SB>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_EIG16>,
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_EIG16, SA, SB>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU>,
+    if ((e = cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU, SA, SB>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU_RHO>,
+    return cudaFuncSetAttribute(k_umma_gemm<BN, UE_ZU_RHO, SA, SB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 }  // namespace
 
-size_t umma_dct_bytes(int H, int W) {
+size_t umma_dct_bytes(int H, int W, int split) {
     const size_t Hp = rup(H, 128), Wp = rup(W, 128);
     size_t n = 2 * Hp * Hp + 3 * Hp * Wp;
     if (H != W) n += 2 * Wp * Wp;
-    return n * 2 + 16 * 1024;
+    if (split) n *= 2;
+    return n * 2 + 32 * 1024;
 }
 
 cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
     const size_t Hp = d.Hp, Wp = d.Wp;
+    const bool split = d.prec == IRLS_PREC_BF16X3;
+    d.split = split ? 1 : 0;
     char* p = mem;
     auto take = [&](size_t elems) {
         void* r = p;
         p += rup(elems * 2, 1024);
         return r;
     };
-    d.PN16 = take(Hp * Hp);
-    d.PNT16 = take(Hp * Hp);
+    auto take2 = [&](size_t elems, void*& hi, void*& lo) {
+        hi = take(elems);
+        lo = split ? take(elems) : nullptr;
+    };
+    take2(Hp * Hp, d.PN16, d.PN16lo);
+    take2(Hp * Hp, d.PNT16, d.PNT16lo);
     if (d.H != d.W) {
-        d.PM16 = take(Wp * Wp);
-        d.PMT16 = take(Wp * Wp);
+        take2(Wp * Wp, d.PM16, d.PM16lo);
+        take2(Wp * Wp, d.PMT16, d.PMT16lo);
     } else {
-        d.PM16 = d.PN16;
-        d.PMT16 = d.PNT16;
+        d.PM16 = d.PN16; d.PM16lo = d.PN16lo;
+        d.PMT16 = d.PNT16; d.PMT16lo = d.PNT16lo;
     }
-    d.R16 = take(Hp * Wp);
-    d.S16a = take(Hp * Wp);
-    d.S16b = take(Hp * Wp);
-    k_build_basis16<<<1024, 256>>>(static_cast<__nv_bfloat16*>(d.PN16),
-                                   static_cast<__nv_bfloat16*>(d.PNT16), d.H, d.Hp);
+    take2(Hp * Wp, d.R16, d.R16lo);
+    take2(Hp * Wp, d.S16a, d.S16alo);
+    take2(Hp * Wp, d.S16b, d.S16blo);
+    using B = __nv_bfloat16;
+    k_build_basis16<<<1024, 256>>>(static_cast<B*>(d.PN16), static_cast<B*>(d.PNT16),
+                                   static_cast<B*>(d.PN16lo), static_cast<B*>(d.PNT16lo), d.H, d.Hp);
     if (d.H != d.W)
-        k_build_basis16<<<1024, 256>>>(static_cast<__nv_bfloat16*>(d.PM16),
-                                       static_cast<__nv_bfloat16*>(d.PMT16), d.W, d.Wp);
+        k_build_basis16<<<1024, 256>>>(static_cast<B*>(d.PM16), static_cast<B*>(d.PMT16),
+                                       static_cast<B*>(d.PM16lo), static_cast<B*>(d.PMT16lo), d.W,
+                                       d.Wp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     TmapSet ts;
     std::memset(&ts, 0, sizeof(ts));
     const int H_ = d.Hp, W_ = d.Wp;
     bool ok = true;
-    // stage 1: A = PMT (Wp x Wp), B = R (Hp x Wp)
-    ok &= make_map(&ts.a[0], d.PMT16, W_, W_, UBM);
-    ok &= make_map(&ts.b[0], d.R16, H_, W_, pick_bn(H_));
-    // stage 2: A = T1 (Wp x Hp), B = PNT (Hp x Hp)
-    ok &= make_map(&ts.a[1], d.S16a, W_, H_, UBM);
-    ok &= make_map(&ts.b[1], d.PNT16, H_, H_, pick_bn(H_));
-    // stage 3: A = PN (Hp x Hp), B = T2 (Wp x Hp)
-    ok &= make_map(&ts.a[2], d.PN16, H_, H_, UBM);
-    ok &= make_map(&ts.b[2], d.S16b, W_, H_, pick_bn(W_));
-    // stage 4: A = T3 (Hp x Wp), B = PM (Wp x Wp)
-    ok &= make_map(&ts.a[3], d.S16a, H_, W_, UBM);
-    ok &= make_map(&ts.b[3], d.PM16, W_, W_, pick_bn(W_));
+    // (rows, cols) of A and B per stage, and the output width N that fixes the B box height
+    auto stage = [&](StageMaps& m, void* a, void* al, int ar, int ac, void* b, void* bl, int br,
+                     int bc, int N) {
+        const int bn = pick_bn(N, split);
+        ok &= make_map(&m.a0, a, ar, ac, UBM);
+        ok &= make_map(&m.a1, split ? al : a, ar, ac, UBM);
+        ok &= make_map(&m.b0, b, br, bc, bn);
+        ok &= make_map(&m.b1, split ? bl : b, br, bc, bn);
+    };
+    // stage 1: A = PMT (Wp x Wp), B = R (Hp x Wp), N = Hp
+    stage(ts.st[0], d.PMT16, d.PMT16lo, W_, W_, d.R16, d.R16lo, H_, W_, H_);
+    // stage 2: A = T1 (Wp x Hp), B = PNT (Hp x Hp), N = Hp
+    stage(ts.st[1], d.S16a, d.S16alo, W_, H_, d.PNT16, d.PNT16lo, H_, H_, H_);
+    // stage 3: A = PN (Hp x Hp), B = T2 (Wp x Hp), N = Wp
+    stage(ts.st[2], d.PN16, d.PN16lo, H_, H_, d.S16b, d.S16blo, W_, H_, W_);
+    // stage 4: A = T3 (Hp x Wp), B = PM (Wp x Wp), N = Wp
+    stage(ts.st[3], d.S16a, d.S16alo, H_, W_, d.PM16, d.PM16lo, W_, W_, W_);
     if (!ok) return cudaErrorNotSupported;
-    if ((e = set_attrs<256>()) != cudaSuccess) return e;
-    if ((e = set_attrs<128>()) != cudaSuccess) return e;
+    if ((e = set_attrs<256, 1, 1>()) != cudaSuccess) return e;
+    if ((e = set_attrs<128, 1, 1>()) != cudaSuccess) return e;
+    if ((e = set_attrs<128, 2, 2>()) != cudaSuccess) return e;
     std::memcpy(d.tmap_storage, &ts, sizeof(ts));
     d.umma_ok = 1;
     return cudaSuccess;
@@ -511,6 +582,7 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
     if (!d.umma_ok) return cudaErrorNotSupported;
     const TmapSet& ts = *reinterpret_cast<const TmapSet*>(d.tmap_storage);
     const int Hp = d.Hp, Wp = d.Wp;
+    const bool split = d.split != 0;
     UEpiArgs ep{};
     ep.st = st;
     ep.partials = partials;
@@ -518,24 +590,22 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
     ep.skip_if_done = skip_if_done;
     cudaError_t e;
     // stage 1: T1 (Wp x Hp) = PMT . R^T
-    ep.C = d.S16a; ep.ldc = Hp;
-    e = launch_stage<UE_STORE16>(ts.a[0], ts.b[0], Wp, Hp, Wp, ep, s);
+    ep.C = d.S16a; ep.C_lo = d.S16alo; ep.ldc = Hp;
+    e = launch_stage<UE_STORE16>(ts.st[0], Wp, Hp, Wp, split, ep, s);
     if (e != cudaSuccess) return e;
     // stage 2: T2 (Wp x Hp) = tau (T1 . PNT^T) / eig, zero frequency and padding -> 0
-    ep.C = d.S16b; ep.ldc = Hp; ep.vm = d.W; ep.vn = d.H; ep.lam_m = d.lamM; ep.lam_n = d.lamN;
-    ep.scale = d.tau;
-    e = launch_stage<UE_EIG16>(ts.a[1], ts.b[1], Wp, Hp, Hp, ep, s);
+    ep.C = d.S16b; ep.C_lo = d.S16blo; ep.ldc = Hp; ep.vm = d.W; ep.vn = d.H;
+    ep.lam_m = d.lamM; ep.lam_n = d.lamN; ep.scale = d.tau;
+    e = launch_stage<UE_EIG16>(ts.st[1], Wp, Hp, Hp, split, ep, s);
     if (e != cudaSuccess) return e;
     // stage 3: T3 (Hp x Wp) = PN . T2^T
-    ep.C = d.S16a; ep.ldc = Wp;
-    e = launch_stage<UE_STORE16>(ts.a[2], ts.b[2], Hp, Wp, Hp, ep, s);
+    ep.C = d.S16a; ep.C_lo = d.S16alo; ep.ldc = Wp;
+    e = launch_stage<UE_STORE16>(ts.st[2], Hp, Wp, Hp, split, ep, s);
     if (e != cudaSuccess) return e;
     // stage 4: Z (H x W, pitch ld) = T3 . PM^T, and rho / beta
-    ep.C = zU; ep.ldc = ld; ep.vm = d.H; ep.vn = d.W; ep.rU = rU;
-    if (reduce_rho) {
-        return launch_stage<UE_ZU_RHO>(ts.a[3], ts.b[3], Hp, Wp, Wp, ep, s);
-    }
-    return launch_stage<UE_ZU>(ts.a[3], ts.b[3], Hp, Wp, Wp, ep, s);
+    ep.C = zU; ep.C_lo = nullptr; ep.ldc = ld; ep.vm = d.H; ep.vn = d.W; ep.rU = rU;
+    if (reduce_rho) return launch_stage<UE_ZU_RHO>(ts.st[3], Hp, Wp, Wp, split, ep, s);
+    return launch_stage<UE_ZU>(ts.st[3], Hp, Wp, Wp, split, ep, s);
 }
 
 }  // namespace irls

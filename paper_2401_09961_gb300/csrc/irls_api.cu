@@ -44,7 +44,7 @@ bool opts_valid(const irls_opts& o) {
     if (!(o.cg_tol >= 0.f)) return false;
     if (o.outer_iters < 0 || o.outer_iters > IRLS_MAX_OUTER) return false;
     if (o.cg_max_iter < 0) return false;
-    if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_FP16) return false;
+    if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_BF16X3) return false;
     return true;
 }
 
@@ -171,6 +171,7 @@ StencilArgs make_args(const irls_plan_s* p) {
     a.warm_start = p->opts.warm_start;
     a.prec = p->opts.precision;
     a.r16 = (p->opts.precision != IRLS_PREC_FP32) ? p->dct.R16 : nullptr;
+    a.r16lo = (p->opts.precision == IRLS_PREC_BF16X3) ? p->dct.R16lo : nullptr;
     a.ld16 = p->dct.Wp;
     return a;
 }
@@ -376,7 +377,7 @@ int irls_plan_set_opts(irls_plan p, const irls_opts* opts) {
     if (!p || !opts) return IRLS_ERR_ARG;
     if (!opts_valid(*opts)) return IRLS_ERR_ARG;
     if (opts->precision != p->opts.precision && opts->precision != IRLS_PREC_FP32 &&
-        p->prec_alloc == IRLS_PREC_FP32)
+        opts->precision != p->prec_alloc)
         return IRLS_ERR_UNSUPPORTED;
     if (opts->tau != p->opts.tau) {
         p->dct.tau = opts->tau;
@@ -438,7 +439,7 @@ int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) 
         StencilArgs a = make_args(p);
         ck(cudaMemsetAsync(p->P.rU, 0, p->L.plane_bytes, s));
         ck(launch_copy_in(R, p->H, p->W, p->P.rU, p->ld, s));
-        if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.ld16, s));
+        if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.r16lo, a.ld16, s));
         ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, p->st, 0, a, p->partials, 0, s));
         ck(launch_copy_out(p->P.zU, p->H, p->W, p->ld, Z, s));
     } catch (Fail&) {

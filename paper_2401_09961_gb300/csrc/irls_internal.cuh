@@ -72,8 +72,9 @@ struct StencilArgs {
     int flexible;
     int warm_start;
     int cur;            // which pU/pVv/pVh buffer holds the newest direction
-    // optional bf16/fp16 emission of r_U for the tensor-core preconditioner
-    void* r16;          // Hp x Wp (row-major, pitch Wp) or nullptr
+    // optional bf16 emission of r_U for the tensor-core preconditioner
+    void* r16;          // Hp x Wp (row-major, pitch Wp) or nullptr: bf16(r_U)
+    void* r16lo;        // same shape or nullptr: bf16(r_U - bf16(r_U)) for split precision
     int ld16;
     int prec;           // IRLS_PREC_*
 };
@@ -87,11 +88,14 @@ struct DctPlan {
     float *PN, *PNT, *PM, *PMT;
     float *lamN, *lamM;     // eigenvalues, padded with zeros
     float *T1, *T2;         // fp32 intermediates (Wp x Hp each, reused)
-    // 16-bit copies for the tensor-core path
+    // bfloat16 copies for the tensor-core path (the *lo parts only in split precision)
     void *PN16, *PNT16, *PM16, *PMT16;
-    void *R16, *S16a, *S16b;   // 16-bit input and intermediates
+    void *PN16lo, *PNT16lo, *PM16lo, *PMT16lo;
+    void *R16, *S16a, *S16b;        // bf16 input and intermediates (hi parts)
+    void *R16lo, *S16alo, *S16blo;  // lo parts
+    int split;
     int umma_ok;
-    alignas(64) unsigned char tmap_storage[1024];   // TMA descriptors of the four stages
+    alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
 };
 
 // ---- launchers (stencil kernels, irls_kernels.cu) -----------------------------------------
@@ -114,7 +118,7 @@ cudaError_t launch_copy_in(const float* src, int rows, int cols, float* dst, int
                            cudaStream_t s);
 cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevState* st,
                                      double* partials, cudaStream_t s);
-cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, int ld16,
+cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, void* r16lo, int ld16,
                          cudaStream_t s);
 int stencil_grid_blocks(int H, int W);
 

@@ -114,11 +114,14 @@ k_bnorm(Planes P, StencilArgs a, DevState* st, double* partials) {
 // A cold start (warm_start = 0) uses x = 0, i.e. r = b, and zeroes the iterate.
 // Also F_delta(x^k) = sum W + ||e||^2 / (2 tau)  (= H_delta(x^k, W^k)).
 // ------------------------------------------------------------------------------------------
-template <typename T16>
-__device__ __forceinline__ void emit16(void* r16, int ld16, int i, int j, float v);
-template <>
-__device__ __forceinline__ void emit16<__nv_bfloat16>(void* r16, int ld16, int i, int j, float v) {
-    static_cast<__nv_bfloat16*>(r16)[(size_t)i * ld16 + j] = __float2bfloat16_rn(v);
+// bfloat16 copy of r_U for the tensor-core preconditioner; with a lo plane the value is split
+// as hi = bf16(v), lo = bf16(v - hi) (split precision).
+__device__ __forceinline__ void emit16(void* r16, void* r16lo, int ld16, int i, int j, float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(r16)[(size_t)i * ld16 + j] = h;
+    if (r16lo != nullptr)
+        static_cast<__nv_bfloat16*>(r16lo)[(size_t)i * ld16 + j] =
+            __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -170,7 +173,7 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
             P.Wv[o] = wv; P.Wh[o] = wh; P.dv[o] = dv; P.dh[o] = dh;
             P.rU[o] = ru; P.rVv[o] = rv; P.rVh[o] = rh;
             if (!warm) { P.U[o] = 0.f; P.Vv[o] = 0.f; P.Vh[o] = 0.f; }
-            if (a.r16 != nullptr) emit16<__nv_bfloat16>(a.r16, a.ld16, i, j, ru);
+            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
             rr += ru * ru + rv * rv + rh * rh;
             ru2 += ru * ru;
             rzv += rv * rv / (dv + it) + rh * rh / (dh + it);
@@ -327,7 +330,7 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
             ru2 += ru * ru;
             rzv += rv * rv * iv + rh * rh * ih;
             if (flex) rzo += ru * P.zU[o] + (rv * rv0) * iv + (rh * rh0) * ih;
-            if (a.r16 != nullptr) emit16<__nv_bfloat16>(a.r16, a.ld16, i, j, ru);
+            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
         }
         yv_prev = yv;
         cu = nu; cvv = nvv; cvh = nvh;
@@ -426,12 +429,13 @@ __global__ void k_copy_in(const float* __restrict__ src, int rows, int cols,
     }
 }
 
-__global__ void k_emit16(const float* __restrict__ src, int H, int W, int ld, void* r16, int ld16) {
+__global__ void k_emit16(const float* __restrict__ src, int H, int W, int ld, void* r16, void* r16lo,
+                         int ld16) {
     const size_t n = (size_t)H * W;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
          t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / W), j = (int)(t % W);
-        emit16<__nv_bfloat16>(r16, ld16, i, j, src[(size_t)i * ld + j]);
+        emit16(r16, r16lo, ld16, i, j, src[(size_t)i * ld + j]);
     }
 }
 
@@ -511,11 +515,11 @@ cudaError_t launch_copy_in(const float* src, int rows, int cols, float* dst, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, int ld16,
+cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, void* r16lo, int ld16,
                          cudaStream_t s) {
     const size_t n = (size_t)H * W;
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
-    k_emit16<<<blocks, 256, 0, s>>>(src, H, W, ld, r16, ld16);
+    k_emit16<<<blocks, 256, 0, s>>>(src, H, W, ld, r16, r16lo, ld16);
     return cudaGetLastError();
 }
 
@@ -527,6 +531,7 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
     StencilArgs b = a;
     b.flexible = 0;
     b.r16 = nullptr;
+    b.r16lo = nullptr;
     b.cg_max = 1 << 30;
     b.tol2 = -1.0;
     k_update<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, b, st, partials);
