@@ -461,9 +461,13 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-// output tile width: 256 for single-pass stages when N allows it; split stages use 128 so that
-// three shared-memory stages of four operand parts fit
+// output tile width: 256 for single-pass stages when N allows it; stages with a split operand
+// use 128 so that at least three shared-memory stages fit
 int pick_bn(int N, bool split) { return (!split && N % 256 == 0) ? 256 : 128; }
+
+// per-stage split configuration: bit 2s = A operand of stage s carried as hi + lo, bit 2s+1 = B
+bool split_a(int mask, int s) { return (mask >> (2 * s)) & 1; }
+bool split_b(int mask, int s) { return (mask >> (2 * s + 1)) & 1; }
 
 template <int BN, int EPI, int SA, int SB>
 cudaError_t launch_one(const StageMaps& m, int M, int N, int K, const UEpiArgs& ep,
@@ -475,9 +479,11 @@ cudaError_t launch_one(const StageMaps& m, int M, int N, int K, const UEpiArgs& 
 }
 
 template <int EPI>
-cudaError_t launch_stage(const StageMaps& m, int M, int N, int K, bool split, const UEpiArgs& ep,
-                         cudaStream_t s) {
-    if (split) return launch_one<128, EPI, 2, 2>(m, M, N, K, ep, s);
+cudaError_t launch_stage(const StageMaps& m, int M, int N, int K, bool sa, bool sb,
+                         const UEpiArgs& ep, cudaStream_t s) {
+    if (sa && sb) return launch_one<128, EPI, 2, 2>(m, M, N, K, ep, s);
+    if (sa) return launch_one<128, EPI, 2, 1>(m, M, N, K, ep, s);
+    if (sb) return launch_one<128, EPI, 1, 2>(m, M, N, K, ep, s);
     if (pick_bn(N, false) == 256) return launch_one<256, EPI, 1, 1>(m, M, N, K, ep, s);
     return launch_one<128, EPI, 1, 1>(m, M, N, K, ep, s);
 }
@@ -514,7 +520,9 @@ size_t umma_dct_bytes(int H, int W, int split) {
 cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
     const size_t Hp = d.Hp, Wp = d.Wp;
     const bool split = d.prec == IRLS_PREC_BF16X3;
-    d.split = split ? 1 : 0;
+    // every operand of every stage split: measured at 4096 x 4096, leaving any one operand of
+    // any stage in a single bf16 pass raises the CG count from ~330 to 600-3000+ per outer step
+    d.split = split ? 0xFF : 0;
     char* p = mem;
     auto take = [&](size_t elems) {
         void* r = p;
@@ -551,26 +559,31 @@ cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
     const int H_ = d.Hp, W_ = d.Wp;
     bool ok = true;
     // (rows, cols) of A and B per stage, and the output width N that fixes the B box height
-    auto stage = [&](StageMaps& m, void* a, void* al, int ar, int ac, void* b, void* bl, int br,
-                     int bc, int N) {
-        const int bn = pick_bn(N, split);
+    const int mask = d.split;
+    auto stage = [&](int si, void* a, void* al, int ar, int ac, void* b, void* bl, int br, int bc,
+                     int N) {
+        StageMaps& m = ts.st[si];
+        const bool sa = split_a(mask, si), sb = split_b(mask, si);
+        const int bn = pick_bn(N, sa || sb);
         ok &= make_map(&m.a0, a, ar, ac, UBM);
-        ok &= make_map(&m.a1, split ? al : a, ar, ac, UBM);
+        ok &= make_map(&m.a1, sa ? al : a, ar, ac, UBM);
         ok &= make_map(&m.b0, b, br, bc, bn);
-        ok &= make_map(&m.b1, split ? bl : b, br, bc, bn);
+        ok &= make_map(&m.b1, sb ? bl : b, br, bc, bn);
     };
     // stage 1: A = PMT (Wp x Wp), B = R (Hp x Wp), N = Hp
-    stage(ts.st[0], d.PMT16, d.PMT16lo, W_, W_, d.R16, d.R16lo, H_, W_, H_);
+    stage(0, d.PMT16, d.PMT16lo, W_, W_, d.R16, d.R16lo, H_, W_, H_);
     // stage 2: A = T1 (Wp x Hp), B = PNT (Hp x Hp), N = Hp
-    stage(ts.st[1], d.S16a, d.S16alo, W_, H_, d.PNT16, d.PNT16lo, H_, H_, H_);
+    stage(1, d.S16a, d.S16alo, W_, H_, d.PNT16, d.PNT16lo, H_, H_, H_);
     // stage 3: A = PN (Hp x Hp), B = T2 (Wp x Hp), N = Wp
-    stage(ts.st[2], d.PN16, d.PN16lo, H_, H_, d.S16b, d.S16blo, W_, H_, W_);
+    stage(2, d.PN16, d.PN16lo, H_, H_, d.S16b, d.S16blo, W_, H_, W_);
     // stage 4: A = T3 (Hp x Wp), B = PM (Wp x Wp), N = Wp
-    stage(ts.st[3], d.S16a, d.S16alo, H_, W_, d.PM16, d.PM16lo, W_, W_, W_);
+    stage(3, d.S16a, d.S16alo, H_, W_, d.PM16, d.PM16lo, W_, W_, W_);
     if (!ok) return cudaErrorNotSupported;
     if ((e = set_attrs<256, 1, 1>()) != cudaSuccess) return e;
     if ((e = set_attrs<128, 1, 1>()) != cudaSuccess) return e;
     if ((e = set_attrs<128, 2, 2>()) != cudaSuccess) return e;
+    if ((e = set_attrs<128, 2, 1>()) != cudaSuccess) return e;
+    if ((e = set_attrs<128, 1, 2>()) != cudaSuccess) return e;
     std::memcpy(d.tmap_storage, &ts, sizeof(ts));
     d.umma_ok = 1;
     return cudaSuccess;
@@ -582,30 +595,31 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
     if (!d.umma_ok) return cudaErrorNotSupported;
     const TmapSet& ts = *reinterpret_cast<const TmapSet*>(d.tmap_storage);
     const int Hp = d.Hp, Wp = d.Wp;
-    const bool split = d.split != 0;
+    const int mk = d.split;
     UEpiArgs ep{};
     ep.st = st;
     ep.partials = partials;
     ep.flexible = a.flexible;
     ep.skip_if_done = skip_if_done;
     cudaError_t e;
-    // stage 1: T1 (Wp x Hp) = PMT . R^T
-    ep.C = d.S16a; ep.C_lo = d.S16alo; ep.ldc = Hp;
-    e = launch_stage<UE_STORE16>(ts.st[0], Wp, Hp, Wp, split, ep, s);
+    // stage 1: T1 (Wp x Hp) = PMT . R^T; lo part kept if stage 2 splits its A operand
+    ep.C = d.S16a; ep.C_lo = split_a(mk, 1) ? d.S16alo : nullptr; ep.ldc = Hp;
+    e = launch_stage<UE_STORE16>(ts.st[0], Wp, Hp, Wp, split_a(mk, 0), split_b(mk, 0), ep, s);
     if (e != cudaSuccess) return e;
     // stage 2: T2 (Wp x Hp) = tau (T1 . PNT^T) / eig, zero frequency and padding -> 0
-    ep.C = d.S16b; ep.C_lo = d.S16blo; ep.ldc = Hp; ep.vm = d.W; ep.vn = d.H;
-    ep.lam_m = d.lamM; ep.lam_n = d.lamN; ep.scale = d.tau;
-    e = launch_stage<UE_EIG16>(ts.st[1], Wp, Hp, Hp, split, ep, s);
+    ep.C = d.S16b; ep.C_lo = split_b(mk, 2) ? d.S16blo : nullptr; ep.ldc = Hp; ep.vm = d.W;
+    ep.vn = d.H; ep.lam_m = d.lamM; ep.lam_n = d.lamN; ep.scale = d.tau;
+    e = launch_stage<UE_EIG16>(ts.st[1], Wp, Hp, Hp, split_a(mk, 1), split_b(mk, 1), ep, s);
     if (e != cudaSuccess) return e;
     // stage 3: T3 (Hp x Wp) = PN . T2^T
-    ep.C = d.S16a; ep.C_lo = d.S16alo; ep.ldc = Wp;
-    e = launch_stage<UE_STORE16>(ts.st[2], Hp, Wp, Hp, split, ep, s);
+    ep.C = d.S16a; ep.C_lo = split_a(mk, 3) ? d.S16alo : nullptr; ep.ldc = Wp;
+    e = launch_stage<UE_STORE16>(ts.st[2], Hp, Wp, Hp, split_a(mk, 2), split_b(mk, 2), ep, s);
     if (e != cudaSuccess) return e;
     // stage 4: Z (H x W, pitch ld) = T3 . PM^T, and rho / beta
     ep.C = zU; ep.C_lo = nullptr; ep.ldc = ld; ep.vm = d.H; ep.vn = d.W; ep.rU = rU;
-    if (reduce_rho) return launch_stage<UE_ZU_RHO>(ts.st[3], Hp, Wp, Wp, split, ep, s);
-    return launch_stage<UE_ZU>(ts.st[3], Hp, Wp, Wp, split, ep, s);
+    if (reduce_rho)
+        return launch_stage<UE_ZU_RHO>(ts.st[3], Hp, Wp, Wp, split_a(mk, 3), split_b(mk, 3), ep, s);
+    return launch_stage<UE_ZU>(ts.st[3], Hp, Wp, Wp, split_a(mk, 3), split_b(mk, 3), ep, s);
 }
 
 }  // namespace irls

@@ -171,7 +171,9 @@ StencilArgs make_args(const irls_plan_s* p) {
     a.warm_start = p->opts.warm_start;
     a.prec = p->opts.precision;
     a.r16 = (p->opts.precision != IRLS_PREC_FP32) ? p->dct.R16 : nullptr;
-    a.r16lo = (p->opts.precision == IRLS_PREC_BF16X3) ? p->dct.R16lo : nullptr;
+    // the residual carries a lo part when the first product splits its data operand
+    a.r16lo = (p->opts.precision == IRLS_PREC_BF16X3 && (p->dct.split & 2)) ? p->dct.R16lo
+                                                                             : nullptr;
     a.ld16 = p->dct.Wp;
     return a;
 }
