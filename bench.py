@@ -154,6 +154,9 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--outer", type=int, default=OUTER,
+                    help="IRLS iterations per unwrap (short profiling runs only; the benchmark "
+                         "workload is 20)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -179,7 +182,7 @@ def main():
     X = torch.as_tensor(d["X"]).cuda()
     C = torch.as_tensor(d["coherence"]).cuda()
     flexible = 1 if prec == "bf16" else 0
-    plan = irls.Plan(n, n, tau=TAU, delta=DELTA, outer_iters=OUTER, cg_tol=CG_TOL,
+    plan = irls.Plan(n, n, tau=TAU, delta=DELTA, outer_iters=args.outer, cg_tol=CG_TOL,
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible)
     stream = torch.cuda.current_stream()
     U = torch.empty_like(X)
@@ -229,7 +232,8 @@ def main():
     per_cls = {c: {"ms": prof_ms[i], "launches": int(prof_n[i])} for i, c in enumerate(classes)}
     # live launches (skipped launches after CG stopped are excluded from the averages)
     live = {"direction_pap": cg_total * args.steps, "update": cg_total * args.steps,
-            "dct_precond": (cg_total + OUTER) * args.steps, "reweight_residual": OUTER * args.steps}
+            "dct_precond": (cg_total + args.outer) * args.steps,
+            "reweight_residual": args.outer * args.steps}
     bytes_px = {"direction_pap": 44.0, "reweight_residual": 56.0 + (2.0 if prec != "fp32" else 0),
                 "update": 68.0 + (2.0 if prec != "fp32" else 0) + (4.0 if flexible else 0)}
     dct_flops = 4.0 * Hp * Wp * (n + n)
@@ -300,7 +304,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else
             f"f32+{prec}-tensor-core-dct", "data": "synthetic",
             "config": {"workload": workload_name(n, prec), "size": [n, n],
-                       "outer_iters": OUTER, "delta": DELTA, "tau": TAU, "cg_tol": CG_TOL,
+                       "outer_iters": args.outer, "delta": DELTA, "tau": TAU, "cg_tol": CG_TOL,
                        "precision": prec, "flexible_cg": bool(flexible),
                        "cg_iters_total": cg_total, "l1_objective": stats[-1]["l1_obj"][-1],
                        "cg_iters_per_outer": stats[-1]["cg_iters"],
