@@ -56,7 +56,7 @@ def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None)
     if ref is not None:
         floor = l1_float32_floor(ref)
         tol += 4.0 * floor
-        if floor >= 0.1 * abs(l1o):
+        if floor >= 0.01 * abs(l1o):
             # an objective at the float32 noise level (near-perfect unwrap): the relative bar has
             # no meaning there, and the agreement of U bounds the objective's difference by the
             # triangle inequality, |dL1| <= 2 max|dU| sum C
@@ -64,6 +64,34 @@ def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None)
             tol += 2.0 * err * (pb.Cv.sum() + pb.Ch.sum())
     assert abs(l1g - l1o) <= tol, (l1g, l1o, tol)
     assert k_agreement(Ug, Uo, X) >= 0.999
+
+
+def oracle_with_envelope(X, coh, kw, Cv=None, Ch=None):
+    """The oracle's result plus the spread between equally valid floating-point executions of
+    the same algorithm: the algebraically identical Polak-Ribiere ratio instead of the
+    Fletcher-Reeves one of Alg. 2, the CG vectors stored in float32 (the library's storage type,
+    arithmetic still float64), and the weights perturbed at float32 level (relative 1e-7).
+    Where the truncated CG solves leave U weakly determined this spread is what any float32
+    trajectory can promise; where it is small the 1e-3 rad bar applies unchanged."""
+    base = O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, **kw)
+    U0 = base["U"] - base["U"].mean()
+    runs = [O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, beta_rule="pr", **kw),
+            O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, **kw),
+            O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, beta_rule="pr", **kw)]
+    for s in (0, 1):
+        rng = np.random.default_rng(100 + s)
+        if Cv is not None:
+            runs.append(O.irls_unwrap(X, None, Cv=Cv * (1 + 1e-7 * rng.standard_normal(Cv.shape)),
+                                      Ch=Ch * (1 + 1e-7 * rng.standard_normal(Ch.shape)), **kw))
+        elif coh is not None:
+            c2 = coh.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(coh.shape))
+            runs.append(O.irls_unwrap(X, c2, **kw))
+    env = max([0.0] + [np.abs((r["U"] - r["U"].mean()) - U0).max() for r in runs])
+    return base, env
+
+
+def parity_atol(env):
+    return max(1e-3, 2.0 * env)
 
 
 # ------------------------------------------------------------------------------------------
