@@ -136,6 +136,27 @@ int irls_apply_A(irls_plan plan, const float* d_U, const float* d_Vv, const floa
                  const float* d_Dv, const float* d_Dh, float* d_qU, float* d_qVv, float* d_qVh,
                  void* stream);
 
+/* Allocation-free Laplacian preconditioner.  The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory - plug-ins whose host framework owns every
+ * device byte through its own allocator, and latency-critical code that must never meet
+ * cudaMalloc's implicit device synchronisation or an out-of-memory failure after start-up.
+ * It computes what irls_precond_laplacian computes with IRLS_PREC_FP32, d_Z = L^+ (tau d_R), but
+ * needs no plan and allocates nothing: the DCT bases and intermediates live in one fixed
+ * 1.84 MB buffer compiled into the library (every GPU that loads the library holds it until the
+ * process exits), sized for H, W <= IRLS_NOALLOC_MAX_SIDE.
+ *   d_R, d_Z  H x W float32 device arrays, row-major and contiguous, owned by the caller;
+ *   tau       > 0 (the penalty of the plan-based form);
+ *   returns   IRLS_ERR_SHAPE if H or W is < 1 or > IRLS_NOALLOC_MAX_SIDE, IRLS_ERR_ARG for a
+ *             null pointer or tau <= 0, IRLS_ERR_CUDA if a launch fails; asynchronous on stream.
+ * The first call on a device looks up the buffer's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the one
+ * buffer and each call rewrites every part of it that it reads, so nothing needs clearing
+ * between calls - but calls that overlap on the GPU (other streams or host threads without
+ * ordering between them) race on the buffer and corrupt each other's results. */
+#define IRLS_NOALLOC_MAX_SIDE 256
+int irls_precond_laplacian_noalloc(const float* d_R, float* d_Z, int H, int W, float tau,
+                                   void* stream);
+
 /* Live profiler (for measurement tools).  When on, every solve on this plan records a CUDA
  * event pair around each kernel launch on the solve's stream and accumulates the elapsed time
  * per kernel class; turning it on (or off) clears the totals.  Classes, in order:

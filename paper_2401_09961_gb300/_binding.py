@@ -76,6 +76,7 @@ SIGNATURES = {
     "irls_unwrap_ex": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),
     "irls_plan_set_profiling": (_I, [_P, _I]),
     "irls_plan_profile": (_I, [_P, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_longlong), _I]),

@@ -273,4 +273,47 @@ cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevS
     return e;
 }
 
+// Floats of scratch that dct_apply_fp32_scratch needs for an H x W image.
+size_t dct_scratch_floats(int H, int W) {
+    const size_t Hp = rup(H, 128), Wp = rup(W, 128);
+    size_t n = 2 * Hp * Hp + Hp + 3 * Hp * Wp;
+    if (H != W) n += 2 * Wp * Wp + Wp;
+    return n;
+}
+
+// The float32 Laplacian preconditioner on caller-provided scratch: builds the DCT bases into
+// `work`, copies R into a 128-aligned pitch, runs the four products and writes Z (pitch W).
+// Every scratch element that is read is written earlier in the same call.
+cudaError_t dct_apply_fp32_scratch(const float* R, float* Z, int H, int W, float tau, float* work,
+                                   cudaStream_t s) {
+    const int Hp = rup(H, 128), Wp = rup(W, 128);
+    float* f = work;
+    float* PN = f; f += (size_t)Hp * Hp;
+    float* PNT = f; f += (size_t)Hp * Hp;
+    float *PM = PN, *PMT = PNT;
+    if (H != W) { PM = f; f += (size_t)Wp * Wp; PMT = f; f += (size_t)Wp * Wp; }
+    float* lamN = f; f += Hp;
+    float* lamM = lamN;
+    if (H != W) { lamM = f; f += Wp; }
+    float* T1 = f; f += (size_t)Hp * Wp;
+    float* T2 = f; f += (size_t)Hp * Wp;
+    float* Rp = f;
+    k_build_basis<<<256, 256, 0, s>>>(PN, PNT, nullptr, nullptr, H, Hp);
+    if (H != W) k_build_basis<<<256, 256, 0, s>>>(PM, PMT, nullptr, nullptr, W, Wp);
+    k_build_lambda<<<2, 256, 0, s>>>(lamN, H, Hp);
+    if (H != W) k_build_lambda<<<2, 256, 0, s>>>(lamM, W, Wp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_copy_in(R, H, W, Rp, Wp, s)) != cudaSuccess) return e;
+    EpiArgs ep{};
+    ep.C = T1; ep.ldc = Hp;
+    if ((e = gemm<EPI_TRANS>(Rp, Wp, H, PMT, Wp, Hp, Wp, W, ep, 0, s)) != cudaSuccess) return e;
+    ep.C = T2; ep.ldc = Hp; ep.vm = W; ep.vn = H; ep.lam_m = lamM; ep.lam_n = lamN; ep.scale = tau;
+    if ((e = gemm<EPI_EIG>(T1, Hp, Wp, PNT, Hp, Wp, Hp, H, ep, 0, s)) != cudaSuccess) return e;
+    ep.C = T1; ep.ldc = Wp;
+    if ((e = gemm<EPI_TRANS>(T2, Hp, Wp, PN, Hp, Wp, Hp, H, ep, 0, s)) != cudaSuccess) return e;
+    ep.C = Z; ep.ldc = W; ep.vm = H; ep.vn = W;
+    return gemm<EPI_ZU>(T1, Wp, Hp, PM, Wp, Hp, Wp, W, ep, 0, s);
+}
+
 }  // namespace irls

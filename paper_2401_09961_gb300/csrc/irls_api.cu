@@ -22,6 +22,14 @@ namespace {
 
 thread_local int g_last_cuda = 0;
 
+}  // namespace
+
+namespace irls {
+void set_last_cuda_error(int code) { g_last_cuda = code; }
+}  // namespace irls
+
+namespace {
+
 constexpr int kPlanes = 21;
 constexpr int kChunk = 8;
 
