@@ -198,18 +198,37 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
 }
 
 // ------------------------------------------------------------------------------------------
+// The two per-iteration kernels work on float4 lanes: a thread owns 4 consecutive columns, a
+// warp 128 and a block of 128 threads 512, so each warp moves 512-byte rows; the next row's
+// loads are issued before the current row's stores (all plane pointers are __restrict__).
+// Columns at or beyond W are zero in every plane; they are computed like the others (their
+// values stay zero) and only the edge masks hh[] exclude the edges that do not exist.
+// ------------------------------------------------------------------------------------------
+constexpr int kVec = 4;
+constexpr int kVRows = 16;
+
+__device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// ------------------------------------------------------------------------------------------
 // Search direction and curvature (Alg. 2): p_new = z + beta p_old with z_U from the Laplacian
 // block and z_V = r_V / (D + 1/tau) (the diagonal blocks of the preconditioner, Sec. 3.3);
 // p^T A p = sum (y_v^2 + y_h^2) / tau + D p_V^2; alpha = rho / p^T A p.
 // ------------------------------------------------------------------------------------------
+template <int ROWS>
 __global__ void __launch_bounds__(kThreads)
 k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
     if (st->done) return;
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int j0 = (blockIdx.x * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
-    const bool col = j < W, hh = j + 1 < W;
+    const int i0 = blockIdx.y * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf, nxt = cur ^ 1;
     const bool fresh = st->p_fresh != 0;
@@ -221,40 +240,92 @@ k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
     float* __restrict__ pVvn = P.pVv[nxt];
     float* __restrict__ pVhn = P.pVh[nxt];
     const float* __restrict__ zU = P.zU;
+    const float* __restrict__ rVv = P.rVv;
+    const float* __restrict__ rVh = P.rVh;
+    const float* __restrict__ Dv = P.dv;
+    const float* __restrict__ Dh = P.dh;
+    bool hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
 
-    float cu = 0.f, cvv = 0.f, cvh = 0.f, cdv = 0.f, cdh = 0.f;
-    if (col) {
-        const size_t o = (size_t)i0 * ld + j;
-        cu = fresh ? zU[o] : zU[o] + beta * pUo[o];
-        cdv = P.dv[o]; cdh = P.dh[o];
-        cvv = P.rVv[o] / (cdv + it);
-        cvh = P.rVh[o] / (cdh + it);
-        if (!fresh) { cvv += beta * pVvo[o]; cvh += beta * pVho[o]; }
+    // direction at (row, j0..j0+3): U part only, or all three parts with the diagonals
+    auto dir_u = [&](size_t o, float (&pu)[4]) {
+        float z[4];
+        ld4(zU + o, z);
+        if (fresh) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pu[e] = z[e];
+        } else {
+            float q[4];
+            ld4(pUo + o, q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pu[e] = z[e] + beta * q[e];
+        }
+    };
+    auto dir_v = [&](size_t o, float (&pvv)[4], float (&pvh)[4], float (&dv)[4], float (&dh)[4]) {
+        float r1[4], r2[4];
+        ld4(Dv + o, dv); ld4(Dh + o, dh); ld4(rVv + o, r1); ld4(rVh + o, r2);
+        if (fresh) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { pvv[e] = r1[e] / (dv[e] + it); pvh[e] = r2[e] / (dh[e] + it); }
+        } else {
+            float q1[4], q2[4];
+            ld4(pVvo + o, q1); ld4(pVho + o, q2);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                pvv[e] = r1[e] / (dv[e] + it) + beta * q1[e];
+                pvh[e] = r2[e] / (dh[e] + it) + beta * q2[e];
+            }
+        }
+    };
+
+    float cu[4] = {0, 0, 0, 0}, cvv[4] = {0, 0, 0, 0}, cvh[4] = {0, 0, 0, 0};
+    float cdv[4] = {0, 0, 0, 0}, cdh[4] = {0, 0, 0, 0};
+    float nu[4] = {0, 0, 0, 0}, nvv[4] = {0, 0, 0, 0}, nvh[4] = {0, 0, 0, 0};
+    float ndv[4] = {0, 0, 0, 0}, ndh[4] = {0, 0, 0, 0};
+    if (act) {
+        const size_t o = (size_t)i0 * ld + j0;
+        dir_u(o, cu);
+        dir_v(o, cvv, cvh, cdv, cdh);
+        if (i0 + 1 < H) {
+            dir_u(o + ld, nu);
+            if (i0 + 1 < i1) dir_v(o + ld, nvv, nvh, ndv, ndh);
+        }
     }
     float acc = 0.f;
     for (int i = i0; i < i1; ++i) {
-        const size_t o = (size_t)i * ld + j;
+        const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
-        float nu = 0.f, nvv = 0.f, nvh = 0.f, ndv = 0.f, ndh = 0.f;
-        if (col && hv) {
-            const size_t on = o + ld;
-            nu = fresh ? zU[on] : zU[on] + beta * pUo[on];
-            if (i + 1 < i1) {
-                ndv = P.dv[on]; ndh = P.dh[on];
-                nvv = P.rVv[on] / (ndv + it);
-                nvh = P.rVh[on] / (ndh + it);
-                if (!fresh) { nvv += beta * pVvo[on]; nvh += beta * pVho[on]; }
+        // direction of row i + 2 (its U part closes row i + 1's vertical edges)
+        float mu[4] = {0, 0, 0, 0}, mvv[4] = {0, 0, 0, 0}, mvh[4] = {0, 0, 0, 0};
+        float mdv[4] = {0, 0, 0, 0}, mdh[4] = {0, 0, 0, 0};
+        if (act && i + 1 < i1 && i + 2 < H) {
+            dir_u(o + 2 * (size_t)ld, mu);
+            if (i + 2 < i1) dir_v(o + 2 * (size_t)ld, mvv, mvh, mdv, mdh);
+        }
+        float right = __shfl_down_sync(kFull, cu[0], 1);
+        if (lane == 31) {
+            right = 0.f;
+            if (act && j0 + kVec < W) {
+                float z = zU[o + kVec];
+                right = fresh ? z : z + beta * pUo[o + kVec];
             }
         }
-        float ur = __shfl_down_sync(kFull, cu, 1);
-        if (lane == 31 && col && hh) ur = fresh ? zU[o + 1] : zU[o + 1] + beta * pUo[o + 1];
-        if (col) {
-            pUn[o] = cu; pVvn[o] = cvv; pVhn[o] = cvh;
-            const float yh = hh ? (ur - cu - cvh) : 0.f;
-            const float yv = hv ? (nu - cu - cvv) : 0.f;
-            acc += it * (yh * yh + yv * yv) + cdv * cvv * cvv + cdh * cvh * cvh;
+        if (act) {
+            st4(pUn + o, cu); st4(pVvn + o, cvv); st4(pVhn + o, cvh);
+            const float pr[4] = {cu[1], cu[2], cu[3], right};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float yh = hh[e] ? (pr[e] - cu[e] - cvh[e]) : 0.f;
+                const float yv = hv ? (nu[e] - cu[e] - cvv[e]) : 0.f;
+                acc += it * (yh * yh + yv * yv) + cdv[e] * cvv[e] * cvv[e] + cdh[e] * cvh[e] * cvh[e];
+            }
         }
-        cu = nu; cvv = nvv; cvh = nvh; cdv = ndv; cdh = ndh;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            cu[e] = nu[e]; cvv[e] = nvv[e]; cvh[e] = nvh[e]; cdv[e] = ndv[e]; cdh[e] = ndh[e];
+            nu[e] = mu[e]; nvv[e] = mvv[e]; nvh[e] = mvh[e]; ndv[e] = mdv[e]; ndh[e] = mdh[e];
+        }
     }
     double v[1] = {(double)acc}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
@@ -277,14 +348,15 @@ k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
 // eq. 'matrix-soft-constraints'), then ||r||^2, r_V^T z_V (z_V = r_V / (D + 1/tau)) and, for the
 // flexible variant, r_new^T z_old.  Stops the run when ||r|| <= cg_tol ||b|| or on cg_max.
 // ------------------------------------------------------------------------------------------
+template <int ROWS>
 __global__ void __launch_bounds__(kThreads)
 k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
     if (st->done) return;
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int j0 = (blockIdx.x * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
-    const bool col = j < W, hh = j + 1 < W;
+    const int i0 = blockIdx.y * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf;
     const float alpha = (float)st->alpha;
@@ -292,48 +364,99 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
     const float* __restrict__ pU = P.pU[cur];
     const float* __restrict__ pVv = P.pVv[cur];
     const float* __restrict__ pVh = P.pVh[cur];
+    const float* __restrict__ Dv = P.dv;
+    const float* __restrict__ Dh = P.dh;
+    const float* __restrict__ Zu = P.zU;
+    float* __restrict__ U = P.U;
+    float* __restrict__ Vv = P.Vv;
+    float* __restrict__ Vh = P.Vh;
+    float* __restrict__ rU = P.rU;
+    float* __restrict__ rVv = P.rVv;
+    float* __restrict__ rVh = P.rVh;
+    bool hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
 
-    float cu = 0.f, cvv = 0.f, cvh = 0.f, yv_prev = 0.f;
-    if (col) {
-        const size_t o = (size_t)i0 * ld + j;
-        cu = pU[o]; cvv = pVv[o]; cvh = pVh[o];
-        if (i0 > 0) yv_prev = cu - pU[o - ld] - pVv[o - ld];
+    float cu[4] = {0, 0, 0, 0}, cvv[4] = {0, 0, 0, 0}, cvh[4] = {0, 0, 0, 0};
+    float nu[4] = {0, 0, 0, 0}, nvv[4] = {0, 0, 0, 0}, nvh[4] = {0, 0, 0, 0};
+    float yvp[4] = {0, 0, 0, 0};
+    if (act) {
+        const size_t o = (size_t)i0 * ld + j0;
+        ld4(pU + o, cu); ld4(pVv + o, cvv); ld4(pVh + o, cvh);
+        if (i0 > 0) {
+            float q[4], w[4];
+            ld4(pU + o - ld, q); ld4(pVv + o - ld, w);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) yvp[e] = cu[e] - q[e] - w[e];
+        }
+        if (i0 + 1 < H) {
+            ld4(pU + o + ld, nu);
+            if (i0 + 1 < i1) { ld4(pVv + o + ld, nvv); ld4(pVh + o + ld, nvh); }
+        }
     }
     float rr = 0.f, rzv = 0.f, rzo = 0.f, ru2 = 0.f;
     for (int i = i0; i < i1; ++i) {
-        const size_t o = (size_t)i * ld + j;
+        const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
-        float nu = 0.f, nvv = 0.f, nvh = 0.f;
-        if (col && hv) {
-            nu = pU[o + ld];
-            if (i + 1 < i1) { nvv = pVv[o + ld]; nvh = pVh[o + ld]; }
+        float dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0}, u[4] = {0, 0, 0, 0};
+        float vv[4] = {0, 0, 0, 0}, vh[4] = {0, 0, 0, 0};
+        float r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, r2[4] = {0, 0, 0, 0};
+        float z[4] = {0, 0, 0, 0};
+        float mu[4] = {0, 0, 0, 0}, mvv[4] = {0, 0, 0, 0}, mvh[4] = {0, 0, 0, 0};
+        if (act) {
+            ld4(Dv + o, dv); ld4(Dh + o, dh);
+            ld4(U + o, u); ld4(Vv + o, vv); ld4(Vh + o, vh);
+            ld4(rU + o, r0); ld4(rVv + o, r1); ld4(rVh + o, r2);
+            if (flex) ld4(Zu + o, z);
+            if (i + 1 < i1 && i + 2 < H) {
+                ld4(pU + o + 2 * (size_t)ld, mu);
+                if (i + 2 < i1) { ld4(pVv + o + 2 * (size_t)ld, mvv); ld4(pVh + o + 2 * (size_t)ld, mvh); }
+            }
         }
-        const float yv = (col && hv) ? (nu - cu - cvv) : 0.f;
-        float ur = __shfl_down_sync(kFull, cu, 1);
-        if (lane == 31 && col && hh) ur = pU[o + 1];
-        const float yh = (col && hh) ? (ur - cu - cvh) : 0.f;
-        float yh_l = __shfl_up_sync(kFull, yh, 1);
-        if (lane == 0) yh_l = (col && j > 0) ? (cu - pU[o - 1] - pVh[o - 1]) : 0.f;
-        if (col) {
-            const float dv = P.dv[o], dh = P.dh[o];
-            const float qu = it * (yv_prev - yv + yh_l - yh);
-            const float qv = dv * cvv - it * yv;
-            const float qh = dh * cvh - it * yh;
-            P.U[o] += alpha * cu;
-            P.Vv[o] += alpha * cvv;
-            P.Vh[o] += alpha * cvh;
-            const float ru0 = P.rU[o], rv0 = P.rVv[o], rh0 = P.rVh[o];
-            const float ru = ru0 - alpha * qu, rv = rv0 - alpha * qv, rh = rh0 - alpha * qh;
-            P.rU[o] = ru; P.rVv[o] = rv; P.rVh[o] = rh;
-            const float iv = 1.f / (dv + it), ih = 1.f / (dh + it);
-            rr += ru * ru + rv * rv + rh * rh;
-            ru2 += ru * ru;
-            rzv += rv * rv * iv + rh * rh * ih;
-            if (flex) rzo += ru * P.zU[o] + (rv * rv0) * iv + (rh * rh0) * ih;
-            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
+        float yv[4], yh[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) yv[e] = hv ? (nu[e] - cu[e] - cvv[e]) : 0.f;
+        float right = __shfl_down_sync(kFull, cu[0], 1);
+        if (lane == 31) right = (act && j0 + kVec < W) ? pU[o + kVec] : 0.f;
+        const float pr[4] = {cu[1], cu[2], cu[3], right};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) yh[e] = hh[e] ? (pr[e] - cu[e] - cvh[e]) : 0.f;
+        float left = __shfl_up_sync(kFull, yh[3], 1);
+        if (lane == 0) left = (act && j0 > 0) ? (cu[0] - pU[o - 1] - pVh[o - 1]) : 0.f;
+        const float yl[4] = {left, yh[0], yh[1], yh[2]};
+        if (act) {
+            float n0[4], n1[4], n2[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float qu = it * (yvp[e] - yv[e] + yl[e] - yh[e]);
+                const float qv = dv[e] * cvv[e] - it * yv[e];
+                const float qh = dh[e] * cvh[e] - it * yh[e];
+                u[e] += alpha * cu[e];
+                vv[e] += alpha * cvv[e];
+                vh[e] += alpha * cvh[e];
+                n0[e] = r0[e] - alpha * qu;
+                n1[e] = r1[e] - alpha * qv;
+                n2[e] = r2[e] - alpha * qh;
+                const float iv = 1.f / (dv[e] + it), ih = 1.f / (dh[e] + it);
+                rr += n0[e] * n0[e] + n1[e] * n1[e] + n2[e] * n2[e];
+                ru2 += n0[e] * n0[e];
+                rzv += n1[e] * n1[e] * iv + n2[e] * n2[e] * ih;
+                if (flex) rzo += n0[e] * z[e] + (n1[e] * r1[e]) * iv + (n2[e] * r2[e]) * ih;
+            }
+            st4(U + o, u); st4(Vv + o, vv); st4(Vh + o, vh);
+            st4(rU + o, n0); st4(rVv + o, n1); st4(rVh + o, n2);
+            if (a.r16 != nullptr) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j0 + e < W) emit16(a.r16, a.r16lo, a.ld16, i, j0 + e, n0[e]);
+            }
         }
-        yv_prev = yv;
-        cu = nu; cvv = nvv; cvh = nvh;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            yvp[e] = yv[e];
+            cu[e] = nu[e]; cvv[e] = nvv[e]; cvh[e] = nvh[e];
+            nu[e] = mu[e]; nvv[e] = mvv[e]; nvh[e] = mvh[e];
+        }
     }
     double v[4] = {(double)rr, (double)rzv, (double)rzo, (double)ru2}, tot[4];
     if (grid_reduce<4>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
@@ -449,11 +572,15 @@ __global__ void k_prepare_matvec(DevState* st) {
 
 dim3 strip_grid(int H, int W) { return dim3((W + kThreads - 1) / kThreads, (H + kRows - 1) / kRows); }
 
+dim3 vec_grid(int H, int W) {
+    return dim3((W + kThreads * kVec - 1) / (kThreads * kVec), (H + kVRows - 1) / kVRows);
+}
+
 }  // namespace
 
 int stencil_grid_blocks(int H, int W) {
-    dim3 g = strip_grid(H, W);
-    return (int)(g.x * g.y);
+    dim3 g = strip_grid(H, W), v = vec_grid(H, W);
+    return (int)std::max(g.x * g.y, v.x * v.y);
 }
 
 cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, const float* Ch_in,
@@ -478,13 +605,13 @@ cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevS
 
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
                                  double* partials, cudaStream_t s) {
-    k_direction_pap<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_direction_pap<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                           cudaStream_t s) {
-    k_update<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
@@ -534,7 +661,7 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
     b.r16lo = nullptr;
     b.cg_max = 1 << 30;
     b.tol2 = -1.0;
-    k_update<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, b, st, partials);
+    k_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, b, st, partials);
     return cudaGetLastError();
 }
 
