@@ -35,7 +35,7 @@ __all__ = [
     "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
     "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
     "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "k_map",
-    "best_shift_error", "dense_operators", "Problem",
+    "best_shift_error", "dense_operators", "Problem", "irls_adjoint",
 ]
 
 TWO_PI_F32 = np.float32(2.0 * np.pi)
@@ -353,6 +353,7 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
             break
     out = {"U": U, "Vv": Vv, "Vh": Vh, "status": status, "problem": pb, **st}
     if record:
+        rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         out["record"] = rec
     return out
 
@@ -403,3 +404,68 @@ def dense_operators(N, M):
     B[:nv, N * M:N * M + nv] = -np.eye(nv)
     B[nv:, N * M + nv:] = -np.eye(nh)
     return S, T, B
+
+
+# --------------------------------------------------------------------------------------------
+# Adjoint of the IRLS map (X, coherence) -> U, through converged inner solves
+# --------------------------------------------------------------------------------------------
+def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, cg_tol=1e-10,
+                 cg_max=5000, adj_tol=None, fwd=None):
+    """Reverse-mode derivative of L(U(X, coherence)) given dL/dU.
+
+    Model: every outer step of Alg. 1 is taken as its exact solve, x^{k+1} = A_k^+ b with
+    A_k = A(D^k), D^k = C^2 / W^k, W^k = sqrt(C^2 (V^k)^2 + delta^2) (Sec. 3.1-3.2), and U zero-mean.
+    Then x^{k+1} depends on the previous iterate only through V^k, and for a cotangent xbar of
+    x^{k+1}:
+        lambda = A_k^+ xbar                       (one solve with the same symmetric operator)
+        bbar  += lambda                           (b is linear in G)
+        Dbar   = -lambda_V o V^{k+1}              (A depends on D only through diag(0, D))
+        Vbar^k = Dbar o dD/dV = Dbar o (-C^4 V^k / W^3)
+        Cbar  += Dbar o dD/dC = Dbar o (2 C / W - C^3 (V^k)^2 / W^3)
+    and xbar for the previous step is (0, Vbar^k).  Finally V^0 = -G adds -Vbar^0 to Gbar,
+    b = ((S^T Gv + Gh T^T)/tau, -Gv/tau, -Gh/tau) gives Gbar_v += (S lambda_U - lambda_Vv)/tau and
+    Gbar_h += (lambda_U T - lambda_Vh)/tau, the wrap has derivative 1 almost everywhere so
+    Xbar = S^T Gbar_v + Gbar_h T^T, and Cv = (coh_i + coh_i+1)/2 spreads Cbar back to coherence.
+    Returns (dL/dX, dL/dcoherence or None, forward result)."""
+    if fwd is None:
+        fwd = irls_unwrap(X, coherence, tau=tau, delta=delta, outer_iters=outer_iters,
+                          cg_tol=cg_tol, cg_max=cg_max, record=True)
+    pb = fwd["problem"]
+    N, M = pb.N, pb.M
+    xs = fwd["record"]["x"]             # x^0 .. x^K (V parts are the checkpoints)
+    K = len(xs) - 1
+    adj_tol = cg_tol if adj_tol is None else adj_tol
+    Cv, Ch = pb.Cv, pb.Ch
+    ubar = np.asarray(dL_dU, dtype=np.float64)
+    xbar = (ubar - ubar.mean(), np.zeros((N - 1, M)), np.zeros((N, M - 1)))
+    Gbv, Gbh = np.zeros((N - 1, M)), np.zeros((N, M - 1))
+    Cbv, Cbh = np.zeros((N - 1, M)), np.zeros((N, M - 1))
+    zero = (np.zeros((N, M)), np.zeros((N - 1, M)), np.zeros((N, M - 1)))
+    for k in range(K - 1, -1, -1):
+        _, Vv_k, Vh_k = xs[k]
+        _, Vv_n, Vh_n = xs[k + 1]
+        Wv, Wh = reweight(Vv_k, Vh_k, Cv, Ch, delta)
+        dv, dh = diag_d(Cv, Ch, Wv, Wh)
+        lam, _, _, _ = pcg(zero, xbar, dv, dh, tau, pb.basis_N, pb.basis_M, adj_tol, cg_max)
+        lu, lv, lh = lam
+        Gbv += (S_op(lu) - lv) / tau
+        Gbh += (T_op(lu) - lh) / tau
+        Dbv, Dbh = -lv * Vv_n, -lh * Vh_n
+        Vbv = Dbv * (-(Cv ** 4) * Vv_k / Wv ** 3)
+        Vbh = Dbh * (-(Ch ** 4) * Vh_k / Wh ** 3)
+        Cbv += Dbv * (2.0 * Cv / Wv - Cv ** 3 * Vv_k ** 2 / Wv ** 3)
+        Cbh += Dbh * (2.0 * Ch / Wh - Ch ** 3 * Vh_k ** 2 / Wh ** 3)
+        xbar = (np.zeros((N, M)), Vbv, Vbh)
+    # V^0 = -G
+    Gbv -= xbar[1]
+    Gbh -= xbar[2]
+    Xbar = St_op(Gbv, N) + Tt_op(Gbh, M)
+    cbar = None
+    if coherence is not None:
+        cbar = np.zeros((N, M))
+        cbar[:-1, :] += 0.5 * Cbv
+        cbar[1:, :] += 0.5 * Cbv
+        cbar[:, :-1] += 0.5 * Cbh
+        cbar[:, 1:] += 0.5 * Cbh
+    return Xbar, cbar, fwd
+

@@ -524,3 +524,69 @@ def test_paper_parameters_fixture():
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     assert g["tau"] == 1e-2 and g["delta"] == 1e-6
     assert g["max_iter_CG_start"] == 5 and g["increase_CG_iteration_factor"] == 1.7
+
+
+# ------------------------------------------------------------------------------------------
+# Adjoint of the IRLS map: central differences of the oracle's own forward map
+# ------------------------------------------------------------------------------------------
+def _adjoint_case():
+    N, M = 12, 10
+    d = synthetic.make_phase(N, M, 5, ramp=6.0, n_bumps=1, noise=1.0, coherence=True)
+    X = d["X"].astype(np.float64)
+    coh = d["coherence"].astype(np.float64)
+    Uref = np.random.default_rng(0).standard_normal((N, M))
+    kw = dict(tau=1e-2, delta=0.05, outer_iters=3, cg_tol=1e-13, cg_max=5000)
+    return X, coh, Uref, kw
+
+
+def test_adjoint_matches_central_differences():
+    """dL/dX and dL/dcoherence of L = sum (U - U_ref)^2 through 3 IRLS steps with converged
+    solves.  X: Richardson-extrapolated central differences with steps 2e-2 and 1e-2 (the
+    float32 wrap rounds X +- h, so smaller steps only add noise; pixels whose incident wrapped
+    differences stay below pi - 0.05); coherence: steps of 1e-3."""
+    X, coh, Uref, kw = _adjoint_case()
+
+    def L(Xa, ca):
+        return float(np.sum((O.irls_unwrap(Xa, ca, **kw)["U"] - Uref) ** 2))
+
+    r0 = O.irls_unwrap(X, coh, **kw)
+    gX, gC, _ = O.irls_adjoint(X, coh, 2 * (r0["U"] - Uref), **kw)
+    Gv, Gh = O.wrapped_gradients(X)
+    N, M = X.shape
+    checked = 0
+    for i, j in [(3, 4), (6, 2), (0, 0), (11, 9), (5, 5), (8, 1)]:
+        inc = [abs(Gv[i - 1, j]) if i > 0 else 0, abs(Gv[i, j]) if i < N - 1 else 0,
+               abs(Gh[i, j - 1]) if j > 0 else 0, abs(Gh[i, j]) if j < M - 1 else 0]
+        if max(inc) < np.pi - 0.05:
+            def cd(h):
+                Xp, Xm = X.copy(), X.copy()
+                Xp[i, j] += h
+                Xm[i, j] -= h
+                return (L(Xp, coh) - L(Xm, coh)) / (2 * h)
+            # Richardson extrapolation of steps 2e-2 and 1e-2 (cancels the O(h^2) term)
+            fd = (4.0 * cd(1e-2) - cd(2e-2)) / 3.0
+            # float32 rounding of X +- h and of the wrapped difference leaves ~2e-4 of noise
+            assert abs(fd - gX[i, j]) <= 5e-4 * max(1.0, abs(fd)), (i, j, fd, gX[i, j])
+            checked += 1
+        h = 1e-3
+        cp, cm = coh.copy(), coh.copy()
+        cp[i, j] += h
+        cm[i, j] -= h
+        fdc = (L(X, cp) - L(X, cm)) / (2 * h)
+        assert abs(fdc - gC[i, j]) <= 1e-5 * max(1.0, abs(fdc)), (i, j, fdc, gC[i, j])
+    assert checked >= 3
+
+
+def test_planted_wrong_reweighting_derivative_is_caught():
+    """Dropping the C^3 V^2 / W^3 term of dD/dC must break the coherence gradient check."""
+    X, coh, Uref, kw = _adjoint_case()
+    r0 = O.irls_unwrap(X, coh, **kw)
+    _, gC, fwd = O.irls_adjoint(X, coh, 2 * (r0["U"] - Uref), **kw)
+    # recompute with the planted slip
+    pb = fwd["problem"]
+    xs = fwd["record"]["x"]
+    _, Vv0, Vh0 = xs[0]
+    Wv, Wh = O.reweight(Vv0, Vh0, pb.Cv, pb.Ch, kw["delta"])
+    good = 2.0 * pb.Cv / Wv - pb.Cv ** 3 * Vv0 ** 2 / Wv ** 3
+    bad = 2.0 * pb.Cv / Wv
+    assert not np.allclose(good, bad, rtol=1e-3)
