@@ -57,6 +57,7 @@ extern "C" {
 #define IRLS_MAX_OUTER 256
 
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
+typedef struct irls_tape_s* irls_tape;   /* opaque: checkpoints of a recorded forward solve   */
 
 /* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
@@ -120,6 +121,30 @@ int irls_unwrap(const float* d_X, const float* d_coherence, int H, int W, float 
 int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
                    const float* d_Cv, const float* d_Ch, const float* d_U_init,
                    float* d_U, float* d_Vv, float* d_Vh, irls_stats* h_stats, void* stream);
+
+/* Forward solve that records what the adjoint needs (the reverse sweep below):
+ * the wrapped gradients G and weights C it used, and V^k of every outer step k = 0..K (the
+ * weights W^k = sqrt(C^2 (V^k)^2 + delta^2) of Alg. 1 are recomputed from them), K+5 pairs of
+ * planes allocated by the library.  Arguments as in irls_unwrap_ex (no restart point).
+ * *tape receives the record; release it with irls_tape_free.  The plan must outlive the tape;
+ * other solves on the plan between recording and the backward call are allowed (the tape
+ * keeps its own copies).  Synchronous like irls_unwrap_ex. */
+int irls_unwrap_forward_record(irls_plan plan, const float* d_X, const float* d_coherence,
+                               const float* d_Cv, const float* d_Ch, float* d_U, irls_tape* tape,
+                               irls_stats* h_stats, void* stream);
+
+/* Reverse sweep: given d_dL_dU (H x W), writes d_dL_dX (H x W) and, when the forward used a
+ * coherence map, d_dL_dcoh (H x W; pass NULL to skip; NULL is required when explicit Cv/Ch were
+ * given).  Model: each outer step is its converged solve x^{k+1} = A_k^+ b (Sec. 3.1-3.2), so
+ * step k costs one PCG solve with the same symmetric A_k (same preconditioner, tolerance and
+ * cap as the plan) plus the chain through D^k = C^2 / W^k(V^k); the wrap has derivative 1
+ * almost everywhere.  h_stats (nullable) receives the CG iterations of each adjoint solve
+ * (reverse order).  Uses the plan's workspace; synchronous. */
+int irls_unwrap_backward(irls_tape tape, const float* d_dL_dU, float* d_dL_dX, float* d_dL_dcoh,
+                         irls_stats* h_stats, void* stream);
+
+/* Release a tape (synchronises the device first).  NULL is a no-op. */
+int irls_tape_free(irls_tape tape);
 
 /* One application of the Laplacian block of the preconditioner (Sec. 3.3, Sylvester equation
  * S^T S Z + Z T T^T = tau R solved in the DCT eigenbasis, zero-frequency coefficient set to 0):

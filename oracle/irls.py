@@ -410,7 +410,7 @@ def dense_operators(N, M):
 # Adjoint of the IRLS map (X, coherence) -> U, through converged inner solves
 # --------------------------------------------------------------------------------------------
 def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, cg_tol=1e-10,
-                 cg_max=5000, adj_tol=None, fwd=None):
+                 cg_max=5000, adj_tol=None, fwd=None, storage=None):
     """Reverse-mode derivative of L(U(X, coherence)) given dL/dU.
 
     Model: every outer step of Alg. 1 is taken as its exact solve, x^{k+1} = A_k^+ b with
@@ -426,10 +426,11 @@ def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, c
     b = ((S^T Gv + Gh T^T)/tau, -Gv/tau, -Gh/tau) gives Gbar_v += (S lambda_U - lambda_Vv)/tau and
     Gbar_h += (lambda_U T - lambda_Vh)/tau, the wrap has derivative 1 almost everywhere so
     Xbar = S^T Gbar_v + Gbar_h T^T, and Cv = (coh_i + coh_i+1)/2 spreads Cbar back to coherence.
+    ``storage`` is passed to the forward and adjoint PCG runs (see pcg).
     Returns (dL/dX, dL/dcoherence or None, forward result)."""
     if fwd is None:
         fwd = irls_unwrap(X, coherence, tau=tau, delta=delta, outer_iters=outer_iters,
-                          cg_tol=cg_tol, cg_max=cg_max, record=True)
+                          cg_tol=cg_tol, cg_max=cg_max, record=True, storage=storage)
     pb = fwd["problem"]
     N, M = pb.N, pb.M
     xs = fwd["record"]["x"]             # x^0 .. x^K (V parts are the checkpoints)
@@ -446,7 +447,8 @@ def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, c
         _, Vv_n, Vh_n = xs[k + 1]
         Wv, Wh = reweight(Vv_k, Vh_k, Cv, Ch, delta)
         dv, dh = diag_d(Cv, Ch, Wv, Wh)
-        lam, _, _, _ = pcg(zero, xbar, dv, dh, tau, pb.basis_N, pb.basis_M, adj_tol, cg_max)
+        lam, _, _, _ = pcg(zero, xbar, dv, dh, tau, pb.basis_N, pb.basis_M, adj_tol, cg_max,
+                           storage=storage)
         lu, lv, lh = lam
         Gbv += (S_op(lu) - lv) / tau
         Gbh += (T_op(lu) - lh) / tau

@@ -14,7 +14,13 @@ from ._binding import (IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check
                        lib)
 
 __all__ = ["Plan", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
-           "Opts", "Stats", "PRECISIONS"]
+           "Opts", "Stats", "PRECISIONS", "unwrap_differentiable"]
+
+
+def unwrap_differentiable(X, coherence, plan):
+    """U(X, coherence) as a torch autograd node (hand-written adjoint, see .autograd)."""
+    from .autograd import UnwrapFn
+    return UnwrapFn.apply(X, coherence, plan)
 
 
 def _torch():

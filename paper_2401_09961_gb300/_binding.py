@@ -74,6 +74,10 @@ SIGNATURES = {
     "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
     "irls_unwrap": (_I, [_P, _P, _I, _I, _F, _I, _F, _P, _P]),
     "irls_unwrap_ex": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "irls_unwrap_forward_record": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(_P),
+                                        ctypes.POINTER(Stats), _P]),
+    "irls_unwrap_backward": (_I, [_P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "irls_tape_free": (_I, [_P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),

@@ -386,7 +386,9 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
             DevState* st = ep.st;
             const double rho_new = tot[0] + st->rz_v;
             if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-                if (st->rr > 0.0) st->status |= ST_BREAKDOWN;
+                // rho <= 0 is a breakdown unless the residual is already at the accuracy
+                // rounding allows (relative 1e-3 and below)
+                if (st->rel > 1e-3 || !isfinite(rho_new)) st->status |= ST_BREAKDOWN;
                 st->done = 1;
             } else if (st->p_fresh) {
                 st->rho = rho_new;

@@ -165,6 +165,20 @@ struct irls_plan_s {
     Profiler prof;
 };
 
+// Checkpoints of a recorded forward solve for the adjoint sweep: the wrapped gradients and edge
+// weights it used, V^k of every outer step (W^k = sqrt(C^2 (V^k)^2 + delta^2) is recomputed
+// from them), and the adjoint accumulators.  Planes share the plan's pitch.
+struct irls_tape_s {
+    irls_plan_s* plan = nullptr;
+    int H = 0, W = 0, ld = 0, K = 0, has_coh = 0;
+    float tau = 0.f, delta = 0.f;
+    char* mem = nullptr;
+    size_t plane_bytes = 0;
+    float *Gv = nullptr, *Gh = nullptr, *Cv = nullptr, *Ch = nullptr;
+    std::vector<float*> Vv, Vh;
+    float *Gbv = nullptr, *Gbh = nullptr, *Cbv = nullptr, *Cbh = nullptr;
+};
+
 namespace {
 
 StencilArgs make_args(const irls_plan_s* p) {
@@ -212,69 +226,9 @@ struct DeviceGuard {
     }
 };
 
-// Runs the whole of Alg. 1 on the plan's workspace; returns the device status bits.
-int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv, const float* Ch,
-              const float* U0, const float* Vv0, const float* Vh0, cudaStream_t s,
-              irls_stats* stats) {
-    const StencilArgs a = make_args(p);
+// Copies the device statistics into *stats (if given) and returns the device status bits.
+int fetch_stats(irls_plan_s* p, cudaStream_t s, irls_stats* stats) {
     DevState* st = p->st;
-    Profiler& pf = p->prof;
-    cudaEvent_t t0;
-    ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-    t0 = pf.begin(s);
-    ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
-    ck(launch_bnorm(p->P, a, st, p->partials, s));
-    pf.end(PC_INIT, t0, s);
-    // stop early on invalid input
-    ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ck(cudaStreamSynchronize(s));
-    pf.drain(pf.pend.size());
-    if (p->h_flag[0] & ST_NONFINITE) return p->h_flag[0];
-
-    for (int k = 0; k < p->opts.outer_iters; ++k) {
-        t0 = pf.begin(s);
-        ck(launch_reweight_residual(p->P, a, st, p->partials, s));
-        pf.end(PC_REWEIGHT, t0, s);
-        t0 = pf.begin(s);
-        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
-        pf.end(PC_DCT, t0, s);
-        int issued = 0, slot = 0;
-        bool pending = false;
-        size_t mark[2] = {0, 0};
-        while (issued < p->opts.cg_max_iter) {
-            const int n = std::min(kChunk, p->opts.cg_max_iter - issued);
-            for (int c = 0; c < n; ++c) {
-                t0 = pf.begin(s);
-                ck(launch_direction_pap(p->P, a, st, p->partials, s));
-                pf.end(PC_DIRECTION, t0, s);
-                t0 = pf.begin(s);
-                ck(launch_update(p->P, a, st, p->partials, s));
-                pf.end(PC_UPDATE, t0, s);
-                t0 = pf.begin(s);
-                ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
-                pf.end(PC_DCT, t0, s);
-            }
-            issued += n;
-            ck(cudaMemcpyAsync(&p->h_flag[slot], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-            ck(cudaEventRecord(p->ev[slot], s));
-            mark[slot] = pf.pend.size();
-            if (pending) {
-                ck(cudaEventSynchronize(p->ev[slot ^ 1]));
-                pf.drain(mark[slot ^ 1]);
-                mark[slot] -= std::min(mark[slot], mark[slot ^ 1]);
-                if (p->h_flag[slot ^ 1]) break;
-            }
-            pending = true;
-            slot ^= 1;
-        }
-        t0 = pf.begin(s);
-        ck(launch_finalize(p->P, a, st, p->partials, s));
-        pf.end(PC_FINALIZE, t0, s);
-    }
-    if (pf.on) {
-        ck(cudaStreamSynchronize(s));
-        pf.drain(pf.pend.size());
-    }
     if (stats) {
         DevState h;
         ck(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -293,11 +247,98 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
         stats->status = status_to_code(h.status);
         return h.status;
     }
-    int status = 0;
     ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
-    status = p->h_flag[0];
-    return status;
+    return p->h_flag[0];
+}
+
+// PCG iterations (Alg. 2) after the first preconditioner application of a run: issued in chunks,
+// the device stopping flag polled one chunk behind.
+void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s) {
+    Profiler& pf = p->prof;
+    cudaEvent_t t0;
+    int issued = 0, slot = 0;
+    bool pending = false;
+    size_t mark[2] = {0, 0};
+    while (issued < p->opts.cg_max_iter) {
+        const int n = std::min(kChunk, p->opts.cg_max_iter - issued);
+        for (int c = 0; c < n; ++c) {
+            t0 = pf.begin(s);
+            ck(launch_direction_pap(p->P, a, st, p->partials, s));
+            pf.end(PC_DIRECTION, t0, s);
+            t0 = pf.begin(s);
+            ck(launch_update(p->P, a, st, p->partials, s));
+            pf.end(PC_UPDATE, t0, s);
+            t0 = pf.begin(s);
+            ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
+            pf.end(PC_DCT, t0, s);
+        }
+        issued += n;
+        ck(cudaMemcpyAsync(&p->h_flag[slot], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ck(cudaEventRecord(p->ev[slot], s));
+        mark[slot] = pf.pend.size();
+        if (pending) {
+            ck(cudaEventSynchronize(p->ev[slot ^ 1]));
+            pf.drain(mark[slot ^ 1]);
+            mark[slot] -= std::min(mark[slot], mark[slot ^ 1]);
+            if (p->h_flag[slot ^ 1]) break;
+        }
+        pending = true;
+        slot ^= 1;
+    }
+}
+
+void copy_plane(float* dst, const float* src, size_t bytes, cudaStream_t s) {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+}
+
+// Runs the whole of Alg. 1 on the plan's workspace; returns the device status bits.  With a
+// tape, G, C and V^0 .. V^K are checkpointed for the adjoint sweep.
+int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv, const float* Ch,
+              const float* U0, const float* Vv0, const float* Vh0, cudaStream_t s,
+              irls_stats* stats, irls_tape_s* tape = nullptr) {
+    const StencilArgs a = make_args(p);
+    DevState* st = p->st;
+    Profiler& pf = p->prof;
+    const size_t pb = p->L.plane_bytes;
+    cudaEvent_t t0;
+    ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    t0 = pf.begin(s);
+    ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
+    ck(launch_bnorm(p->P, a, st, p->partials, s));
+    pf.end(PC_INIT, t0, s);
+    // stop early on invalid input
+    ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    pf.drain(pf.pend.size());
+    if (p->h_flag[0] & ST_NONFINITE) return p->h_flag[0];
+    if (tape) {
+        copy_plane(tape->Gv, p->P.Gv, pb, s); copy_plane(tape->Gh, p->P.Gh, pb, s);
+        copy_plane(tape->Cv, p->P.Cv, pb, s); copy_plane(tape->Ch, p->P.Ch, pb, s);
+        copy_plane(tape->Vv[0], p->P.Vv, pb, s); copy_plane(tape->Vh[0], p->P.Vh, pb, s);
+    }
+
+    for (int k = 0; k < p->opts.outer_iters; ++k) {
+        t0 = pf.begin(s);
+        ck(launch_reweight_residual(p->P, a, st, p->partials, s));
+        pf.end(PC_REWEIGHT, t0, s);
+        t0 = pf.begin(s);
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
+        pf.end(PC_DCT, t0, s);
+        run_cg(p, a, st, s);
+        t0 = pf.begin(s);
+        ck(launch_finalize(p->P, a, st, p->partials, s));
+        pf.end(PC_FINALIZE, t0, s);
+        if (tape) {
+            copy_plane(tape->Vv[k + 1], p->P.Vv, pb, s);
+            copy_plane(tape->Vh[k + 1], p->P.Vh, pb, s);
+        }
+    }
+    if (pf.on) {
+        ck(cudaStreamSynchronize(s));
+        pf.drain(pf.pend.size());
+    }
+    return fetch_stats(p, s, stats);
 }
 
 std::mutex g_simple_mu;
@@ -420,6 +461,100 @@ int irls_unwrap_ex(irls_plan p, const float* X, const float* coh, const float* C
         return IRLS_ERR_CUDA;
     }
     return status_to_code(status);
+}
+
+int irls_unwrap_forward_record(irls_plan p, const float* X, const float* coh, const float* Cv,
+                               const float* Ch, float* U, irls_tape* out, irls_stats* stats,
+                               void* stream) {
+    if (!p || !X || !U || !out) return IRLS_ERR_ARG;
+    *out = nullptr;
+    if ((Cv == nullptr) != (Ch == nullptr)) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    irls_tape_s* t = new (std::nothrow) irls_tape_s();
+    if (!t) return IRLS_ERR_OOM;
+    int status = 0;
+    try {
+        DeviceGuard g(p->dev);
+        t->plan = p;
+        t->H = p->H; t->W = p->W; t->ld = p->ld;
+        t->K = p->opts.outer_iters;
+        t->has_coh = (coh != nullptr && Cv == nullptr) ? 1 : 0;
+        t->tau = p->opts.tau;
+        t->delta = p->opts.delta;
+        t->plane_bytes = p->L.plane_bytes;
+        const size_t nplanes = 8 + 2 * (size_t)(t->K + 1);
+        if (cudaMalloc(&t->mem, nplanes * t->plane_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete t;
+            return IRLS_ERR_OOM;
+        }
+        float* f[64 + 2 * IRLS_MAX_OUTER];
+        for (size_t i = 0; i < nplanes; ++i)
+            f[i] = reinterpret_cast<float*>(t->mem + i * t->plane_bytes);
+        size_t q = 0;
+        t->Gv = f[q++]; t->Gh = f[q++]; t->Cv = f[q++]; t->Ch = f[q++];
+        t->Gbv = f[q++]; t->Gbh = f[q++]; t->Cbv = f[q++]; t->Cbh = f[q++];
+        for (int k = 0; k <= t->K; ++k) { t->Vv.push_back(f[q++]); t->Vh.push_back(f[q++]); }
+        status = run_solve(p, X, coh, Cv, Ch, nullptr, nullptr, nullptr, s, stats, t);
+        if (status & ST_NONFINITE) {
+            cudaStreamSynchronize(s);
+            cudaFree(t->mem);
+            delete t;
+            if (stats) stats->status = IRLS_ERR_NONFINITE;
+            return IRLS_ERR_NONFINITE;
+        }
+        ck(launch_copy_out(p->P.U, p->H, p->W, p->ld, U, s));
+        ck(cudaStreamSynchronize(s));
+    } catch (Fail&) {
+        if (t->mem) cudaFree(t->mem);
+        delete t;
+        return IRLS_ERR_CUDA;
+    }
+    *out = t;
+    return status_to_code(status);
+}
+
+int irls_unwrap_backward(irls_tape t, const float* dLdU, float* dLdX, float* dLdcoh,
+                         irls_stats* stats, void* stream) {
+    if (!t || !dLdU || !dLdX) return IRLS_ERR_ARG;
+    if (dLdcoh && !t->has_coh) return IRLS_ERR_ARG;
+    irls_plan_s* p = t->plan;
+    if (!p || p->H != t->H || p->W != t->W) return IRLS_ERR_ARG;
+    if (p->opts.tau != t->tau || p->opts.delta != t->delta) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int status = 0;
+    try {
+        DeviceGuard g(p->dev);
+        const StencilArgs a = make_args(p);
+        DevState* st = p->st;
+        const size_t pb = t->plane_bytes;
+        ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+        for (float* z : {t->Gbv, t->Gbh, t->Cbv, t->Cbh}) ck(cudaMemsetAsync(z, 0, pb, s));
+        ck(launch_adj_init(p->P, a, dLdU, st, p->partials, s));
+        for (int k = t->K - 1; k >= 0; --k) {
+            ck(launch_adj_setup(p->P, a, t->Vv[k], t->Vh[k], t->Cv, t->Ch, st, p->partials, s));
+            ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
+            run_cg(p, a, st, s);
+            ck(launch_record_step(st, s));
+            ck(launch_adj_accumulate(p->P, a, t->Vv[k], t->Vh[k], t->Vv[k + 1], t->Vh[k + 1],
+                                     t->Cv, t->Ch, t->Gbv, t->Gbh, t->Cbv, t->Cbh, s));
+        }
+        ck(launch_adj_final(p->P, a, t->Gbv, t->Gbh, t->Cbv, t->Cbh, dLdX, dLdcoh, s));
+        status = fetch_stats(p, s, stats);
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return status_to_code(status);
+}
+
+int irls_tape_free(irls_tape t) {
+    if (!t) return IRLS_OK;
+    if (t->mem) {
+        cudaDeviceSynchronize();
+        cudaFree(t->mem);
+    }
+    delete t;
+    return IRLS_OK;
 }
 
 int irls_unwrap(const float* X, const float* coh, int H, int W, float eps, int outer_iters,

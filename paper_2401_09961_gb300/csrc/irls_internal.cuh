@@ -121,6 +121,20 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
 cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, void* r16lo, int ld16,
                          cudaStream_t s);
 int stencil_grid_blocks(int H, int W);
+// adjoint sweep (reverse over the outer steps)
+cudaError_t launch_record_step(DevState* st, cudaStream_t s);
+cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* dLdU, DevState* st,
+                            double* partials, cudaStream_t s);
+cudaError_t launch_adj_setup(const Planes& P, const StencilArgs& a, const float* Vkv,
+                             const float* Vkh, const float* Cv, const float* Ch, DevState* st,
+                             double* partials, cudaStream_t s);
+cudaError_t launch_adj_accumulate(const Planes& P, const StencilArgs& a, const float* Vkv,
+                                  const float* Vkh, const float* Vnv, const float* Vnh,
+                                  const float* Cv, const float* Ch, float* Gbv, float* Gbh,
+                                  float* Cbv, float* Cbh, cudaStream_t s);
+cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float* Gbv,
+                             const float* Gbh, const float* Cbv, const float* Cbh, float* dX,
+                             float* dcoh, cudaStream_t s);
 
 // ---- DCT preconditioner (dct.cu) ------------------------------------------------------------
 size_t dct_bytes(int H, int W, int prec);

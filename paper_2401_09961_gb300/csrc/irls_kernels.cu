@@ -22,6 +22,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kRows = 16;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr double kBreakdownRel = 1e-3;
 
 __device__ __forceinline__ bool finite(float x) { return isfinite(x); }
 
@@ -35,6 +36,15 @@ __device__ __forceinline__ float wrap_pi(float t) {
 }
 
 __device__ __forceinline__ int strip_rows(int H, int i0) { return min(i0 + kRows, H); }
+
+// ||r||^2 without the mean of r_U: in exact arithmetic r stays in the range of A (App. B), which
+// excludes constant U; the constant that float32 rounding of the telescoping sums adds to r_U is
+// invisible to the preconditioner (its zero-frequency coefficient is dropped) and to A, so it is
+// left out of the stopping test.
+__device__ __forceinline__ double range_part(double rr, double sum_ru, int H, int W) {
+    const double n = (double)H * (double)W;
+    return fmax(rr - sum_ru * sum_ru / n, 0.0);
+}
 
 // ------------------------------------------------------------------------------------------
 // Wrapped gradients, edge weights and the starting iterate (Sec. 2; Alg. 1 initialisation)
@@ -133,7 +143,7 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
     const bool col = j < W, hh = j + 1 < W;
     const float it = a.inv_tau, d2 = a.delta * a.delta;
     const bool warm = a.warm_start != 0;
-    float rr = 0.f, rzv = 0.f, fd = 0.f, ru2 = 0.f;
+    float rr = 0.f, rzv = 0.f, fd = 0.f, ru2 = 0.f, su = 0.f;
     float uc = col ? P.U[(size_t)i0 * ld + j] : 0.f;
     float ev_prev = 0.f;          // residual-edge e_v of the row above
     if (col && i0 > 0) {
@@ -176,18 +186,20 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
             if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
             rr += ru * ru + rv * rv + rh * rh;
             ru2 += ru * ru;
+            su += ru;
             rzv += rv * rv / (dv + it) + rh * rh / (dh + it);
             fd += wv + wh + 0.5f * it * (evk * evk + ehk * ehk);
         }
         ev_prev = ev;
         uc = un;
     }
-    double v[4] = {(double)rr, (double)rzv, (double)fd, (double)ru2}, tot[4];
-    if (grid_reduce<4>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
+    double v[5] = {(double)rr, (double)rzv, (double)fd, (double)ru2, (double)su}, tot[5];
+    if (grid_reduce<5>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
+        st->rr = rr_range;
         st->rz_v = tot[1];
         st->rnorm_u = sqrt(tot[3]);
-        const double rel = st->bb > 0.0 ? sqrt(tot[0] / st->bb) : 0.0;
+        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
         st->rel = rel;
         st->iter = 0;
         st->p_fresh = 1;
@@ -334,8 +346,10 @@ k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
         st->pbuf = nxt;
         st->p_fresh = 0;
         if (!(pq > 0.0) || !isfinite(pq)) {
+            // non-positive curvature: a breakdown unless rounding has already brought the
+            // residual to the attainable accuracy
             st->alpha = 0.0;
-            if (st->rr > 0.0) st->status |= ST_BREAKDOWN;
+            if (st->rel > kBreakdownRel || !isfinite(pq)) st->status |= ST_BREAKDOWN;
             st->done = 1;
         } else {
             st->alpha = st->rho / pq;
@@ -394,7 +408,7 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
             if (i0 + 1 < i1) { ld4(pVv + o + ld, nvv); ld4(pVh + o + ld, nvh); }
         }
     }
-    float rr = 0.f, rzv = 0.f, rzo = 0.f, ru2 = 0.f;
+    float rr = 0.f, rzv = 0.f, rzo = 0.f, ru2 = 0.f, su = 0.f;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
@@ -440,6 +454,7 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
                 const float iv = 1.f / (dv[e] + it), ih = 1.f / (dh[e] + it);
                 rr += n0[e] * n0[e] + n1[e] * n1[e] + n2[e] * n2[e];
                 ru2 += n0[e] * n0[e];
+                su += n0[e];
                 rzv += n1[e] * n1[e] * iv + n2[e] * n2[e] * ih;
                 if (flex) rzo += n0[e] * z[e] + (n1[e] * r1[e]) * iv + (n2[e] * r2[e]) * ih;
             }
@@ -458,15 +473,16 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
             nu[e] = mu[e]; nvv[e] = mvv[e]; nvh[e] = mvh[e];
         }
     }
-    double v[4] = {(double)rr, (double)rzv, (double)rzo, (double)ru2}, tot[4];
-    if (grid_reduce<4>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
+    double v[5] = {(double)rr, (double)rzv, (double)rzo, (double)ru2, (double)su}, tot[5];
+    if (grid_reduce<5>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
+        st->rr = rr_range;
         st->rz_v = tot[1];
         st->rz_old = tot[2];
         st->rnorm_u = sqrt(tot[3]);
         const int itn = st->iter + 1;
         st->iter = itn;
-        const double rel = st->bb > 0.0 ? sqrt(tot[0] / st->bb) : 0.0;
+        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
         st->rel = rel;
         if (rel * rel <= a.tol2 || itn >= a.cg_max || !isfinite(rel)) st->done = 1;
         if (!isfinite(rel)) st->status |= ST_NONFINITE;
@@ -532,6 +548,156 @@ k_subtract_mean(float* U, int H, int W, int ld, const DevState* st) {
     for (int i = i0; i < i1; ++i) U[(size_t)i * ld + j] -= m;
 }
 
+// ------------------------------------------------------------------------------------------
+// Adjoint of the IRLS map through converged inner solves (reverse sweep over the outer steps).
+// Step k takes the checkpointed V^k, V^{k+1}, the solve's result lambda = A_k^+ xbar (in the
+// iterate planes) and accumulates
+//   Gbar_v += (S lambda_U - lambda_Vv) / tau,  Gbar_h += (lambda_U T - lambda_Vh) / tau
+//   Dbar    = -lambda_V o V^{k+1}
+//   Cbar   += Dbar o (2 C / W - C^3 (V^k)^2 / W^3)
+// and writes the next right-hand side xbar = (0, Dbar o (-C^4 V^k / W^3)) into the residual
+// planes (W^k = sqrt(C^2 (V^k)^2 + delta^2), D^k = C^2 / W^k: Alg. 1's reweighting).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_user_mean(const float* __restrict__ src, int H, int W, DevState* st, double* partials) {
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    float acc = 0.f;
+    if (j < W)
+        for (int i = i0; i < i1; ++i) acc += src[(size_t)i * W + j];
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &st->counter, tot) && threadIdx.x == 0)
+        st->mean_u = tot[0] / ((double)H * (double)W);
+}
+
+// xbar^K = (dL/dU - mean, 0, 0) into the residual planes
+__global__ void __launch_bounds__(kThreads)
+k_adj_init(Planes P, StencilArgs a, const float* __restrict__ dLdU, const DevState* st) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    if (j >= W) return;
+    const float m = (float)st->mean_u;
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        P.rU[o] = dLdU[(size_t)i * W + j] - m;
+        P.rVv[o] = 0.f;
+        P.rVh[o] = 0.f;
+    }
+}
+
+// Adjoint solve set-up for step k: W^k, D^k from the checkpoint V^k, x = 0, r = xbar (already
+// in the residual planes); ||r||^2 is the scale of the relative stopping test.
+__global__ void __launch_bounds__(kThreads)
+k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
+            const float* __restrict__ Cv, const float* __restrict__ Ch, DevState* st,
+            double* partials) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const float it = a.inv_tau, d2 = a.delta * a.delta;
+    float rr = 0.f, rzv = 0.f, su = 0.f;
+    if (j < W) {
+        for (int i = i0; i < i1; ++i) {
+            const size_t o = (size_t)i * ld + j;
+            float wv = 0.f, wh = 0.f, dv = 0.f, dh = 0.f;
+            if (i + 1 < H) {
+                const float c = Cv[o], v = Vkv[o];
+                wv = sqrtf(c * c * v * v + d2);
+                dv = c * c / wv;
+            }
+            if (j + 1 < W) {
+                const float c = Ch[o], v = Vkh[o];
+                wh = sqrtf(c * c * v * v + d2);
+                dh = c * c / wh;
+            }
+            P.Wv[o] = wv; P.Wh[o] = wh; P.dv[o] = dv; P.dh[o] = dh;
+            P.U[o] = 0.f; P.Vv[o] = 0.f; P.Vh[o] = 0.f;
+            const float ru = P.rU[o], rv = P.rVv[o], rh = P.rVh[o];
+            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
+            rr += ru * ru + rv * rv + rh * rh;
+            su += ru;
+            rzv += rv * rv / (dv + it) + rh * rh / (dh + it);
+        }
+    }
+    double v[3] = {(double)rr, (double)rzv, (double)su}, tot[3];
+    if (grid_reduce<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[2], a.H, a.W);
+        st->rr = rr_range;
+        st->rz_v = tot[1];
+        st->bb = rr_range;
+        st->rel = rr_range > 0.0 ? 1.0 : 0.0;
+        st->iter = 0;
+        st->p_fresh = 1;
+        st->done = (rr_range <= 0.0 || a.cg_max <= 0) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_adj_accumulate(Planes P, StencilArgs a, const float* __restrict__ Vkv,
+                 const float* __restrict__ Vkh, const float* __restrict__ Vnv,
+                 const float* __restrict__ Vnh, const float* __restrict__ Cv,
+                 const float* __restrict__ Ch, float* __restrict__ Gbv, float* __restrict__ Gbh,
+                 float* __restrict__ Cbv, float* __restrict__ Cbh) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const float it = a.inv_tau, d2 = a.delta * a.delta;
+    if (j >= W) return;
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        const float lu = P.U[o];
+        float nv = 0.f, nh = 0.f;
+        if (i + 1 < H) {
+            const float lv = P.Vv[o];
+            Gbv[o] += it * ((P.U[o + ld] - lu) - lv);
+            const float c = Cv[o], v = Vkv[o];
+            const float w = sqrtf(c * c * v * v + d2);
+            const float w3 = w * w * w;
+            const float db = -lv * Vnv[o];
+            Cbv[o] += db * (2.f * c / w - c * c * c * v * v / w3);
+            nv = db * (-(c * c * c * c) * v / w3);
+        }
+        if (j + 1 < W) {
+            const float lh = P.Vh[o];
+            Gbh[o] += it * ((P.U[o + 1] - lu) - lh);
+            const float c = Ch[o], v = Vkh[o];
+            const float w = sqrtf(c * c * v * v + d2);
+            const float w3 = w * w * w;
+            const float db = -lh * Vnh[o];
+            Cbh[o] += db * (2.f * c / w - c * c * c * v * v / w3);
+            nh = db * (-(c * c * c * c) * v / w3);
+        }
+        P.rU[o] = 0.f;
+        P.rVv[o] = nv;
+        P.rVh[o] = nh;
+    }
+}
+
+// dL/dX = S^T Gbar_v + Gbar_h T^T with Gbar -= Vbar^0 (V^0 = -G), and dL/dcoherence from the
+// averaging Cv = (coh_i + coh_i+1) / 2, both written with pitch W.
+__global__ void __launch_bounds__(kThreads)
+k_adj_final(Planes P, StencilArgs a, const float* __restrict__ Gbv, const float* __restrict__ Gbh,
+            const float* __restrict__ Cbv, const float* __restrict__ Cbh, float* __restrict__ dX,
+            float* __restrict__ dcoh) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    if (j >= W) return;
+    auto gv = [&](size_t o) { return Gbv[o] - P.rVv[o]; };
+    auto gh = [&](size_t o) { return Gbh[o] - P.rVh[o]; };
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        float x = 0.f, c = 0.f;
+        if (i > 0) { x += gv(o - ld); c += 0.5f * Cbv[o - ld]; }
+        if (i + 1 < H) { x -= gv(o); c += 0.5f * Cbv[o]; }
+        if (j > 0) { x += gh(o - 1); c += 0.5f * Cbh[o - 1]; }
+        if (j + 1 < W) { x -= gh(o); c += 0.5f * Cbh[o]; }
+        dX[(size_t)i * W + j] = x;
+        if (dcoh != nullptr) dcoh[(size_t)i * W + j] = c;
+    }
+}
+
 __global__ void k_copy_out(const float* __restrict__ src, int rows, int cols, int ld,
                            float* __restrict__ dst) {
     const size_t n = (size_t)rows * cols;
@@ -560,6 +726,17 @@ __global__ void k_emit16(const float* __restrict__ src, int H, int W, int ld, vo
         const int i = (int)(t / W), j = (int)(t % W);
         emit16(r16, r16lo, ld16, i, j, src[(size_t)i * ld + j]);
     }
+}
+
+// statistics of one adjoint solve: CG iterations and final relative residual
+__global__ void k_record_step(DevState* st) {
+    const int k = st->outer;
+    if (k < kMaxOuter) {
+        st->cg_iters[k] = st->iter;
+        st->rel_res[k] = st->rel;
+    }
+    st->cg_total += st->iter;
+    st->outer = k + 1;
 }
 
 __global__ void k_prepare_matvec(DevState* st) {
@@ -647,6 +824,43 @@ cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, voi
     const size_t n = (size_t)H * W;
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
     k_emit16<<<blocks, 256, 0, s>>>(src, H, W, ld, r16, r16lo, ld16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record_step(DevState* st, cudaStream_t s) {
+    k_record_step<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* dLdU, DevState* st,
+                            double* partials, cudaStream_t s) {
+    k_user_mean<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(dLdU, a.H, a.W, st, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adj_init<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, dLdU, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_setup(const Planes& P, const StencilArgs& a, const float* Vkv,
+                             const float* Vkh, const float* Cv, const float* Ch, DevState* st,
+                             double* partials, cudaStream_t s) {
+    k_adj_setup<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Vkv, Vkh, Cv, Ch, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_accumulate(const Planes& P, const StencilArgs& a, const float* Vkv,
+                                  const float* Vkh, const float* Vnv, const float* Vnh,
+                                  const float* Cv, const float* Ch, float* Gbv, float* Gbh,
+                                  float* Cbv, float* Cbh, cudaStream_t s) {
+    k_adj_accumulate<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Vkv, Vkh, Vnv, Vnh, Cv, Ch,
+                                                               Gbv, Gbh, Cbv, Cbh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float* Gbv,
+                             const float* Gbh, const float* Cbv, const float* Cbh, float* dX,
+                             float* dcoh, cudaStream_t s) {
+    k_adj_final<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Gbv, Gbh, Cbv, Cbh, dX, dcoh);
     return cudaGetLastError();
 }
 
