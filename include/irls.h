@@ -58,6 +58,7 @@ extern "C" {
 
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
 typedef struct irls_tape_s* irls_tape;   /* opaque: checkpoints of a recorded forward solve   */
+typedef struct irls_batch_s* irls_batch; /* opaque: a batched solve of many images            */
 
 /* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
@@ -121,6 +122,31 @@ int irls_unwrap(const float* d_X, const float* d_coherence, int H, int W, float 
 int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
                    const float* d_Cv, const float* d_Ch, const float* d_U_init,
                    float* d_U, float* d_Vv, float* d_Vh, irls_stats* h_stats, void* stream);
+
+/* Batched solve: ntiles independent images of their own sizes H[t] x W[t] (non-square allowed),
+ * each unwrapped as by irls_unwrap_ex with the options `opts`, with one GPU launch per phase of
+ * Alg. 1 / Alg. 2 for all images together (the stencil kernels over the union of the images'
+ * blocks, the preconditioner as one grouped tensor-core GEMM per DCT stage over all images'
+ * tiles).  Each image keeps its own CG scalars and stopping test: an image whose CG run has
+ * stopped drops out of later launches of the same outer step (its blocks return at once).  The
+ * inner CG iterations are replayed from CUDA graphs captured once per batch.  Precision must be
+ * IRLS_PREC_BF16X3 or IRLS_PREC_BF16 (IRLS_ERR_UNSUPPORTED for IRLS_PREC_FP32).
+ * irls_batch_create allocates the workspace of all images and the DCT bases (one set per
+ * distinct side length); irls_unwrap_batched_ex runs a batch on arrays of ntiles device pointers
+ * d_X[t], d_coherence[t] (the array may be NULL for uniform weights; entries may be NULL),
+ * d_U[t]; per_tile (nullable) receives ntiles statistics.  Synchronous with respect to the host;
+ * `stream` is ordered before and after the batch.  irls_unwrap_batched is create + run +
+ * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist. */
+int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* opts,
+                      irls_batch* out);
+int irls_batch_destroy(irls_batch batch);
+int irls_unwrap_batched_ex(irls_batch batch, const float* const* d_X,
+                           const float* const* d_coherence, float* const* d_U,
+                           irls_stats* per_tile, void* stream);
+int irls_unwrap_batched(int ntiles, const int* H, const int* W, const float* const* d_X,
+                        const float* const* d_coherence, float* const* d_U, const irls_opts* opts,
+                        irls_stats* per_tile, void* stream);
+int irls_batch_uses_graphs(irls_batch batch);
 
 /* Forward solve that records what the adjoint needs (the reverse sweep below):
  * the wrapped gradients G and weights C it used, and V^k of every outer step k = 0..K (the

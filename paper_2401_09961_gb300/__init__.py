@@ -13,7 +13,7 @@ import ctypes
 from ._binding import (IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
                        lib)
 
-__all__ = ["Plan", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
+__all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
            "Opts", "Stats", "PRECISIONS", "unwrap_differentiable"]
 
 
@@ -156,6 +156,63 @@ def unwrap(X, coherence=None, *, eps=1e-3, outer_iters=20, cg_tol=1e-6, tau=1e-2
     if host:
         U = U.cpu()
     return (U, stats) if return_stats else U
+
+
+class Batch:
+    """A batched solve of images of uneven sizes (one launch per phase for all of them)."""
+
+    def __init__(self, shapes, **opts):
+        self.shapes = [(int(h), int(w)) for h, w in shapes]
+        T = len(self.shapes)
+        if "precision" not in opts:
+            opts["precision"] = "bf16x3"
+        self.opts = default_opts(**opts)
+        Hs = (ctypes.c_int * T)(*[h for h, _ in self.shapes])
+        Ws = (ctypes.c_int * T)(*[w for _, w in self.shapes])
+        h = ctypes.c_void_p()
+        check(lib().irls_batch_create(T, Hs, Ws, ctypes.byref(self.opts), ctypes.byref(h)),
+              "irls_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().irls_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def uses_graphs(self):
+        return lib().irls_batch_uses_graphs(self._h) == 1
+
+    def unwrap(self, Xs, cohs=None, outs=None, stream=None):
+        """Xs, cohs: lists of contiguous float32 CUDA tensors; returns (list of U, list of stats)."""
+        torch = _torch()
+        T = len(self.shapes)
+        if len(Xs) != T:
+            raise ValueError("one X per image")
+        for X, (h, w) in zip(Xs, self.shapes):
+            if tuple(X.shape) != (h, w):
+                raise ValueError("image shape does not match the batch")
+        Us = outs if outs is not None else [torch.empty_like(X) for X in Xs]
+        P = ctypes.c_void_p
+        xa = (P * T)(*[_ptr(X) for X in Xs])
+        ua = (P * T)(*[_ptr(U) for U in Us])
+        ca = (P * T)(*[_ptr(c) for c in cohs]) if cohs is not None else None
+        st = (Stats * T)()
+        rc = lib().irls_unwrap_batched_ex(self._h, xa, ca, ua, st, _stream(stream))
+        check(rc, "irls_unwrap_batched_ex")
+        return Us, [x.to_dict() for x in st]
 
 
 def precond_laplacian(plan, R, stream=None):

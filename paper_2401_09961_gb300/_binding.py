@@ -78,6 +78,15 @@ SIGNATURES = {
                                         ctypes.POINTER(Stats), _P]),
     "irls_unwrap_backward": (_I, [_P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "irls_tape_free": (_I, [_P]),
+    "irls_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(Opts),
+                               ctypes.POINTER(_P)]),
+    "irls_batch_destroy": (_I, [_P]),
+    "irls_unwrap_batched_ex": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    ctypes.POINTER(_P), ctypes.POINTER(Stats), _P]),
+    "irls_unwrap_batched": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_P),
+                                 ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(Opts),
+                                 ctypes.POINTER(Stats), _P]),
+    "irls_batch_uses_graphs": (_I, [_P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),

@@ -138,7 +138,8 @@ k_gemm_tn_f32(const float* __restrict__ A, int lda, int a_rows, const float* __r
     }
     if constexpr (EPI == EPI_ZU_RHO) {
         double vv[1] = {(double)part}, tot[1];
-        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot) && tid == 0) {
+        const Blk blk = single_blk();
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, blk.nblk, blk.bid) && tid == 0) {
             DevState* st = ep.st;
             const double rho_new = tot[0] + st->rz_v;
             if (!(rho_new > 0.0) || !isfinite(rho_new)) {

@@ -31,7 +31,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "irls_internal.cuh"
 #include "reduce.cuh"
@@ -194,10 +196,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 template <int BN, int EPI, int SA, int SB>
-__global__ void __launch_bounds__(kUThreads, 1)
-k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-            const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-            int K, UEpiArgs ep) {
+__device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtensorMap* tmA1,
+                                          const CUtensorMap* tmB0, const CUtensorMap* tmB1,
+                                          int K, const UEpiArgs& ep, int m0, int n0,
+                                          unsigned nblk, unsigned bid) {
     using C = UCfg<BN, SA, SB>;
     if (ep.skip_if_done && ep.st->done) return;
     extern __shared__ uint8_t smem_raw[];
@@ -210,7 +212,6 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
     __shared__ int s_err;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * UBM, n0 = blockIdx.x * BN;
     const int nkb = K / UBK;
 
     if (threadIdx.x == 0) {
@@ -240,10 +241,10 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
                 uint8_t* sa = smem + s * C::kStageBytes;
                 uint8_t* sb = sa + SA * C::kABytes;
                 mbar_expect_tx(&full[s], C::kStageBytes);
-                tma_load_2d(sa, &tmA0, &full[s], kb * UBK, m0);
-                if constexpr (SA == 2) tma_load_2d(sa + C::kABytes, &tmA1, &full[s], kb * UBK, m0);
-                tma_load_2d(sb, &tmB0, &full[s], kb * UBK, n0);
-                if constexpr (SB == 2) tma_load_2d(sb + C::kBBytes, &tmB1, &full[s], kb * UBK, n0);
+                tma_load_2d(sa, tmA0, &full[s], kb * UBK, m0);
+                if constexpr (SA == 2) tma_load_2d(sa + C::kABytes, tmA1, &full[s], kb * UBK, m0);
+                tma_load_2d(sb, tmB0, &full[s], kb * UBK, n0);
+                if constexpr (SB == 2) tma_load_2d(sb + C::kBBytes, tmB1, &full[s], kb * UBK, n0);
             }
         }
         __syncwarp();
@@ -382,7 +383,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
     }
     if constexpr (EPI == UE_ZU_RHO) {
         double vv[1] = {(double)part}, tot[1];
-        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot) && threadIdx.x == 0) {
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0) {
             DevState* st = ep.st;
             const double rho_new = tot[0] + st->rz_v;
             if (!(rho_new > 0.0) || !isfinite(rho_new)) {
@@ -400,6 +401,43 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
             }
         }
     }
+}
+
+template <int BN, int EPI, int SA, int SB>
+__global__ void __launch_bounds__(kUThreads, 1)
+k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+            const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+            int K, UEpiArgs ep) {
+    umma_body<BN, EPI, SA, SB>(&tmA0, &tmA1, &tmB0, &tmB1, K, ep, blockIdx.y * UBM, blockIdx.x * BN,
+                               gridDim.x * gridDim.y, blockIdx.x + gridDim.x * blockIdx.y);
+}
+
+// One problem of a grouped GEMM launch: its TMA descriptors (in global memory), shape,
+// epilogue arguments and the index of its first CTA in the launch.
+struct alignas(64) GemmTile {
+    CUtensorMap a0, a1, b0, b1;
+    UEpiArgs ep;
+    int M, N, K;
+    int blk0, gx;
+};
+
+// Grouped GEMM: one launch over the output tiles of every problem (BN = 128).  A CTA finds its
+// problem by a binary search over the first-CTA indices; problems whose CG run has stopped
+// return at once (the per-problem convergence mask).
+template <int EPI, int SA, int SB>
+__global__ void __launch_bounds__(kUThreads, 1)
+kb_umma_gemm(const GemmTile* __restrict__ tiles, int T) {
+    int lo = 0, hi = T - 1;
+    const int bid = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tiles[mid].blk0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    const GemmTile& g = tiles[lo];
+    const int local = bid - g.blk0;
+    const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * 128;
+    umma_body<128, EPI, SA, SB>(&g.a0, &g.a1, &g.b0, &g.b1, g.K, g.ep, m0, n0,
+                                (unsigned)((g.M / UBM) * g.gx), (unsigned)local);
 }
 
 __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bfloat16* P16lo,
@@ -622,6 +660,190 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
     if (reduce_rho)
         return launch_stage<UE_ZU_RHO>(ts.st[3], Hp, Wp, Wp, split_a(mk, 3), split_b(mk, 3), ep, s);
     return launch_stage<UE_ZU>(ts.st[3], Hp, Wp, Wp, split_a(mk, 3), split_b(mk, 3), ep, s);
+}
+
+
+// ------------------------------------------------------------------------------------------
+// batched (grouped) form
+// ------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_build_lambda16(float* lam, int N, int Np) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Np; k += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (k < N) {
+            const double sn = sinpi((double)k / (2.0 * N));
+            v = 4.0 * sn * sn;
+        }
+        lam[k] = (float)v;
+    }
+}
+
+struct SideBasis {
+    int n, np;
+    void *P, *PT, *Plo, *PTlo;
+    float* lam;
+};
+
+struct BatchLayout {
+    std::vector<int> sides;        // distinct side lengths
+    size_t side_bytes = 0, image_bytes = 0, tiles_bytes = 0, total = 0;
+};
+
+BatchLayout batch_layout(const int* H, const int* W, int T, int prec) {
+    BatchLayout L;
+    const size_t mult = prec == IRLS_PREC_BF16X3 ? 2 : 1;
+    for (int t = 0; t < T; ++t)
+        for (int n : {H[t], W[t]})
+            if (std::find(L.sides.begin(), L.sides.end(), n) == L.sides.end()) L.sides.push_back(n);
+    for (int n : L.sides) {
+        const size_t np = rup(n, 128);
+        L.side_bytes += mult * 2 * rup(np * np * 2, 1024) + rup(np * 4, 1024);
+    }
+    for (int t = 0; t < T; ++t)
+        L.image_bytes += mult * 3 * rup((size_t)rup(H[t], 128) * rup(W[t], 128) * 2, 1024);
+    L.tiles_bytes = 4 * rup((size_t)T * sizeof(GemmTile), 1024);
+    L.total = L.side_bytes + L.image_bytes + L.tiles_bytes + 4096;
+    return L;
+}
+
+}  // namespace
+
+size_t batch_dct_bytes(const int* H, const int* W, int T, int prec) {
+    return batch_layout(H, W, T, prec).total;
+}
+
+cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T, int prec,
+                            float tau, int flexible, char* mem, const float* const* rU,
+                            float* const* zU, const int* ld, DevState* states,
+                            double* const* partials) {
+    const bool split = prec == IRLS_PREC_BF16X3;
+    bd.T = T; bd.prec = prec; bd.split = split ? 1 : 0; bd.tau = tau;
+    BatchLayout L = batch_layout(H, W, T, prec);
+    char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(mem) + 1023) & ~uintptr_t(1023));
+    auto take = [&](size_t bytes) {
+        void* r = p;
+        p += rup(bytes, 1024);
+        return r;
+    };
+    using B = __nv_bfloat16;
+    std::vector<SideBasis> basis;
+    for (int n : L.sides) {
+        SideBasis sb{};
+        sb.n = n;
+        sb.np = (int)rup(n, 128);
+        const size_t e = (size_t)sb.np * sb.np * 2;
+        sb.P = take(e); sb.PT = take(e);
+        sb.Plo = split ? take(e) : nullptr;
+        sb.PTlo = split ? take(e) : nullptr;
+        sb.lam = static_cast<float*>(take((size_t)sb.np * 4));
+        k_build_basis16<<<1024, 256>>>(static_cast<B*>(sb.P), static_cast<B*>(sb.PT),
+                                       static_cast<B*>(sb.Plo), static_cast<B*>(sb.PTlo), n, sb.np);
+        k_build_lambda16<<<4, 256>>>(sb.lam, n, sb.np);
+        basis.push_back(sb);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto side = [&](int n) -> const SideBasis& {
+        for (const auto& b : basis)
+            if (b.n == n) return b;
+        return basis[0];
+    };
+    std::vector<GemmTile> host[4];
+    for (auto& h : host) h.resize(T);
+    int cta[4] = {0, 0, 0, 0};
+    bd.r16.resize(T); bd.r16lo.resize(T); bd.ld16.resize(T);
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+        const int Hp = (int)rup(H[t], 128), Wp = (int)rup(W[t], 128);
+        const size_t e16 = (size_t)Hp * Wp * 2;
+        void* R = take(e16); void* Rlo = split ? take(e16) : nullptr;
+        void* Sa = take(e16); void* Salo = split ? take(e16) : nullptr;
+        void* Sb = take(e16); void* Sblo = split ? take(e16) : nullptr;
+        bd.r16[t] = R; bd.r16lo[t] = Rlo; bd.ld16[t] = Wp;
+        const SideBasis& bn = side(H[t]);
+        const SideBasis& bm = side(W[t]);
+        auto maps = [&](GemmTile& g, void* a, void* al, int ar, int ac, void* b, void* bl, int br,
+                        int bc) {
+            ok &= make_map(&g.a0, a, ar, ac, UBM);
+            ok &= make_map(&g.a1, split ? al : a, ar, ac, UBM);
+            ok &= make_map(&g.b0, b, br, bc, 128);
+            ok &= make_map(&g.b1, split ? bl : b, br, bc, 128);
+        };
+        UEpiArgs ep{};
+        ep.st = states + t;
+        ep.partials = partials[t];
+        ep.flexible = flexible;
+        ep.skip_if_done = 1;
+        // stage 1: T1 (Wp x Hp) = PMT . R^T
+        GemmTile& g0 = host[0][t];
+        maps(g0, bm.PT, bm.PTlo, Wp, Wp, R, Rlo, Hp, Wp);
+        g0.ep = ep; g0.ep.C = Sa; g0.ep.C_lo = split ? Salo : nullptr; g0.ep.ldc = Hp;
+        g0.M = Wp; g0.N = Hp; g0.K = Wp;
+        // stage 2: T2 (Wp x Hp) = tau (T1 . PNT^T) / eig
+        GemmTile& g1 = host[1][t];
+        maps(g1, Sa, Salo, Wp, Hp, bn.PT, bn.PTlo, Hp, Hp);
+        g1.ep = ep; g1.ep.C = Sb; g1.ep.C_lo = split ? Sblo : nullptr; g1.ep.ldc = Hp;
+        g1.ep.vm = W[t]; g1.ep.vn = H[t]; g1.ep.lam_m = bm.lam; g1.ep.lam_n = bn.lam;
+        g1.ep.scale = tau;
+        g1.M = Wp; g1.N = Hp; g1.K = Hp;
+        // stage 3: T3 (Hp x Wp) = PN . T2^T
+        GemmTile& g2 = host[2][t];
+        maps(g2, bn.P, bn.Plo, Hp, Hp, Sb, Sblo, Wp, Hp);
+        g2.ep = ep; g2.ep.C = Sa; g2.ep.C_lo = split ? Salo : nullptr; g2.ep.ldc = Wp;
+        g2.M = Hp; g2.N = Wp; g2.K = Hp;
+        // stage 4: Z (H x W, pitch ld) = T3 . PM^T, and rho / beta
+        GemmTile& g3 = host[3][t];
+        maps(g3, Sa, Salo, Hp, Wp, bm.P, bm.Plo, Wp, Wp);
+        g3.ep = ep; g3.ep.C = zU[t]; g3.ep.C_lo = nullptr; g3.ep.ldc = ld[t];
+        g3.ep.vm = H[t]; g3.ep.vn = W[t]; g3.ep.rU = rU[t];
+        g3.M = Hp; g3.N = Wp; g3.K = Wp;
+        for (int s = 0; s < 4; ++s) {
+            GemmTile& g = host[s][t];
+            g.gx = g.N / 128;
+            g.blk0 = cta[s];
+            cta[s] += (g.M / UBM) * g.gx;
+        }
+    }
+    if (!ok) return cudaErrorNotSupported;
+    for (int s = 0; s < 4; ++s) {
+        bd.d_tiles[s] = take((size_t)T * sizeof(GemmTile));
+        bd.total_ctas[s] = cta[s];
+        e = cudaMemcpy(bd.d_tiles[s], host[s].data(), (size_t)T * sizeof(GemmTile),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    using C22 = UCfg<128, 2, 2>;
+    using C11 = UCfg<128, 1, 1>;
+    const int sm = split ? C22::kSmem : C11::kSmem;
+    for (auto f : {kb_umma_gemm<UE_STORE16, 2, 2>, kb_umma_gemm<UE_EIG16, 2, 2>,
+                   kb_umma_gemm<UE_ZU_RHO, 2, 2>, kb_umma_gemm<UE_STORE16, 1, 1>,
+                   kb_umma_gemm<UE_EIG16, 1, 1>, kb_umma_gemm<UE_ZU_RHO, 1, 1>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 split ? C22::kSmem : C11::kSmem);
+        if (e != cudaSuccess) return e;
+    }
+    (void)sm;
+    return cudaSuccess;
+}
+
+cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s) {
+    using C22 = UCfg<128, 2, 2>;
+    using C11 = UCfg<128, 1, 1>;
+    const int T = bd.T;
+    auto tiles = [&](int k) { return static_cast<const GemmTile*>(bd.d_tiles[k]); };
+    if (bd.split) {
+        kb_umma_gemm<UE_STORE16, 2, 2><<<bd.total_ctas[0], kUThreads, C22::kSmem, s>>>(tiles(0), T);
+        kb_umma_gemm<UE_EIG16, 2, 2><<<bd.total_ctas[1], kUThreads, C22::kSmem, s>>>(tiles(1), T);
+        kb_umma_gemm<UE_STORE16, 2, 2><<<bd.total_ctas[2], kUThreads, C22::kSmem, s>>>(tiles(2), T);
+        kb_umma_gemm<UE_ZU_RHO, 2, 2><<<bd.total_ctas[3], kUThreads, C22::kSmem, s>>>(tiles(3), T);
+    } else {
+        kb_umma_gemm<UE_STORE16, 1, 1><<<bd.total_ctas[0], kUThreads, C11::kSmem, s>>>(tiles(0), T);
+        kb_umma_gemm<UE_EIG16, 1, 1><<<bd.total_ctas[1], kUThreads, C11::kSmem, s>>>(tiles(1), T);
+        kb_umma_gemm<UE_STORE16, 1, 1><<<bd.total_ctas[2], kUThreads, C11::kSmem, s>>>(tiles(2), T);
+        kb_umma_gemm<UE_ZU_RHO, 1, 1><<<bd.total_ctas[3], kUThreads, C11::kSmem, s>>>(tiles(3), T);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace irls

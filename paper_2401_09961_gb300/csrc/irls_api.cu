@@ -345,6 +345,169 @@ std::mutex g_simple_mu;
 
 }  // namespace
 
+// A batched solve: T images of their own sizes, one launch per phase for all of them.
+struct irls_batch_s {
+    int T = 0, dev = 0;
+    irls_opts opts{};
+    std::vector<int> H, W, ld;
+    char* mem = nullptr;
+    std::vector<TileRec> recs;
+    TileRec* d_recs = nullptr;
+    DevState* states = nullptr;
+    int total_strip = 0, total_vec = 0;
+    BatchDctPlan dct;
+    int* d_count = nullptr;          // device, 2 slots
+    int* h_count = nullptr;          // pinned, 2 slots
+    cudaStream_t stream = nullptr;   // internal stream (capturable)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t join = nullptr;
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    int chunk_iters = 0;
+    bool graphs_tried = false;
+};
+
+namespace {
+
+void destroy_batch(irls_batch_s* b) {
+    if (!b) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(b->dev);
+    cudaDeviceSynchronize();
+    for (auto& g : b->chunk)
+        if (g) cudaGraphExecDestroy(g);
+    if (b->mem) cudaFree(b->mem);
+    if (b->h_count) cudaFreeHost(b->h_count);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaSetDevice(cur);
+    delete b;
+}
+
+// one chunk of n batched CG iterations followed by the count of images still iterating
+void issue_chunk(irls_batch_s* b, int n, int slot, cudaStream_t s) {
+    for (int c = 0; c < n; ++c) {
+        ck(launch_direction_batched(b->d_recs, b->T, b->total_vec, s));
+        ck(launch_update_batched(b->d_recs, b->T, b->total_vec, s));
+        ck(batch_dct_apply(b->dct, s));
+    }
+    ck(launch_count_active(b->states, b->T, b->d_count + slot, s));
+}
+
+// Captures the full-size chunk once per batch (two graphs: one per count slot); eager launches
+// are used if capture is unavailable.
+void prepare_graphs(irls_batch_s* b) {
+    if (b->graphs_tried) return;
+    b->graphs_tried = true;
+    b->chunk_iters = kChunk;
+    for (int slot = 0; slot < 2; ++slot) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        bool ok = true;
+        try {
+            issue_chunk(b, kChunk, slot, b->stream);
+        } catch (Fail&) {
+            ok = false;
+        }
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (!ok || e != cudaSuccess || !g) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            for (auto& x : b->chunk)
+                if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+            return;
+        }
+        e = cudaGraphInstantiate(&b->chunk[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& x : b->chunk)
+                if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+            return;
+        }
+    }
+}
+
+int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, float* const* U,
+              irls_stats* stats, cudaStream_t user) {
+    const int T = b->T;
+    cudaStream_t s = b->stream;
+    // order after the caller's stream
+    ck(cudaEventRecord(b->join, user));
+    ck(cudaStreamWaitEvent(s, b->join, 0));
+    for (int t = 0; t < T; ++t) {
+        b->recs[t].X = X[t];
+        b->recs[t].coh = coh ? coh[t] : nullptr;
+    }
+    ck(cudaMemcpyAsync(b->d_recs, b->recs.data(), (size_t)T * sizeof(TileRec),
+                       cudaMemcpyHostToDevice, s));
+    ck(cudaMemsetAsync(b->states, 0, (size_t)T * sizeof(DevState), s));
+    ck(launch_init_batched(b->d_recs, T, b->total_strip, s));
+    ck(launch_bnorm_batched(b->d_recs, T, b->total_strip, s));
+    std::vector<DevState> h(T);
+    ck(cudaMemcpyAsync(h.data(), b->states, (size_t)T * sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    int bad = 0;
+    for (int t = 0; t < T; ++t) bad |= h[t].status & ST_NONFINITE;
+    if (bad) return ST_NONFINITE;
+    prepare_graphs(b);
+    for (int k = 0; k < b->opts.outer_iters; ++k) {
+        ck(launch_reweight_batched(b->d_recs, T, b->total_strip, s));
+        ck(batch_dct_apply(b->dct, s));
+        int issued = 0, slot = 0;
+        bool pending = false;
+        while (issued < b->opts.cg_max_iter) {
+            const int n = std::min(kChunk, b->opts.cg_max_iter - issued);
+            if (n == kChunk && b->chunk[slot])
+                ck(cudaGraphLaunch(b->chunk[slot], s));
+            else
+                issue_chunk(b, n, slot, s);
+            issued += n;
+            ck(cudaMemcpyAsync(&b->h_count[slot], b->d_count + slot, sizeof(int),
+                               cudaMemcpyDeviceToHost, s));
+            ck(cudaEventRecord(b->ev[slot], s));
+            if (pending) {
+                ck(cudaEventSynchronize(b->ev[slot ^ 1]));
+                if (b->h_count[slot ^ 1] == 0) break;
+            }
+            pending = true;
+            slot ^= 1;
+        }
+        ck(launch_finalize_batched(b->d_recs, T, b->total_strip, s));
+    }
+    for (int t = 0; t < T; ++t)
+        ck(launch_copy_out(b->recs[t].P.U, b->H[t], b->W[t], b->ld[t], U[t], s));
+    ck(cudaMemcpyAsync(h.data(), b->states, (size_t)T * sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    int all = 0;
+    for (int t = 0; t < T; ++t) {
+        all |= h[t].status;
+        if (stats) {
+            irls_stats& o = stats[t];
+            std::memset(&o, 0, sizeof(o));
+            o.outer_done = h[t].outer;
+            o.cg_total = h[t].cg_total;
+            const int n = std::min(h[t].outer, IRLS_MAX_OUTER);
+            for (int q = 0; q < n; ++q) {
+                o.cg_iters[q] = h[t].cg_iters[q];
+                o.rel_res[q] = h[t].rel_res[q];
+                o.l1_obj[q] = h[t].l1_obj[q];
+                o.h_delta[q] = h[t].h_delta[q];
+                o.f_delta[q] = h[t].f_delta[q];
+            }
+            o.status = status_to_code(h[t].status);
+        }
+    }
+    return all;
+}
+
+}  // namespace
+
 extern "C" {
 
 int irls_opts_default(irls_opts* o) {
@@ -573,6 +736,159 @@ int irls_unwrap(const float* X, const float* coh, int H, int W, float eps, int o
     if (rc != IRLS_OK) return rc;
     rc = irls_unwrap_ex(p, X, coh, nullptr, nullptr, nullptr, U, nullptr, nullptr, nullptr, stream);
     irls_plan_destroy(p);
+    return rc;
+}
+
+int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* opts,
+                      irls_batch* out) {
+    if (!out || !H || !W || ntiles < 1) return IRLS_ERR_ARG;
+    *out = nullptr;
+    irls_opts o;
+    irls_opts_default(&o);
+    if (opts) o = *opts;
+    if (!opts_valid(o)) return IRLS_ERR_ARG;
+    if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
+    for (int t = 0; t < ntiles; ++t)
+        if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
+    irls_batch_s* b = new (std::nothrow) irls_batch_s();
+    if (!b) return IRLS_ERR_OOM;
+    try {
+        ck(cudaGetDevice(&b->dev));
+        const int T = ntiles;
+        b->T = T;
+        b->opts = o;
+        b->H.assign(H, H + T);
+        b->W.assign(W, W + T);
+        std::vector<size_t> plane_bytes(T), part_bytes(T);
+        size_t total = 0;
+        for (int t = 0; t < T; ++t) {
+            const int ld = row_pitch(W[t]);
+            b->ld.push_back(ld);
+            plane_bytes[t] = align_up((size_t)H[t] * ld * sizeof(float), 256);
+            const int nb = std::max(stencil_grid_blocks(H[t], W[t]), dct_max_blocks(H[t], W[t]));
+            part_bytes[t] = align_up((size_t)8 * nb * sizeof(double), 256);
+            total += kPlanes * plane_bytes[t] + part_bytes[t];
+        }
+        const size_t state_off = align_up(total, 1024);
+        const size_t recs_off = align_up(state_off + (size_t)T * sizeof(DevState), 1024);
+        const size_t count_off = align_up(recs_off + (size_t)T * sizeof(TileRec), 256);
+        const size_t dct_off = align_up(count_off + 256, 1024);
+        const size_t all = dct_off + batch_dct_bytes(H, W, T, o.precision);
+        if (cudaMalloc(&b->mem, all) != cudaSuccess) {
+            cudaGetLastError();
+            b->mem = nullptr;
+            destroy_batch(b);
+            return IRLS_ERR_OOM;
+        }
+        ck(cudaMemset(b->mem, 0, all));
+        b->states = reinterpret_cast<DevState*>(b->mem + state_off);
+        b->d_recs = reinterpret_cast<TileRec*>(b->mem + recs_off);
+        b->d_count = reinterpret_cast<int*>(b->mem + count_off);
+        b->recs.resize(T);
+        std::vector<const float*> rU(T);
+        std::vector<float*> zU(T);
+        std::vector<double*> parts(T);
+        size_t off = 0;
+        for (int t = 0; t < T; ++t) {
+            float* f[kPlanes];
+            for (int i = 0; i < kPlanes; ++i)
+                f[i] = reinterpret_cast<float*>(b->mem + off + (size_t)i * plane_bytes[t]);
+            off += kPlanes * plane_bytes[t];
+            parts[t] = reinterpret_cast<double*>(b->mem + off);
+            off += part_bytes[t];
+            TileRec& r = b->recs[t];
+            Planes& P = r.P;
+            int q = 0;
+            P.U = f[q++]; P.Vv = f[q++]; P.Vh = f[q++];
+            P.rU = f[q++]; P.rVv = f[q++]; P.rVh = f[q++];
+            for (int bb = 0; bb < 2; ++bb) { P.pU[bb] = f[q++]; P.pVv[bb] = f[q++]; P.pVh[bb] = f[q++]; }
+            P.zU = f[q++];
+            P.dv = f[q++]; P.dh = f[q++];
+            P.Wv = f[q++]; P.Wh = f[q++];
+            P.Gv = f[q++]; P.Gh = f[q++];
+            P.Cv = f[q++]; P.Ch = f[q++];
+            rU[t] = P.rU;
+            zU[t] = P.zU;
+            r.st = b->states + t;
+            r.partials = parts[t];
+        }
+        ck(batch_dct_setup(b->dct, H, W, T, o.precision, o.tau, o.flexible_cg, b->mem + dct_off,
+                           rU.data(), zU.data(), b->ld.data(), b->states, parts.data()));
+        int sblk = 0, vblk = 0;
+        for (int t = 0; t < T; ++t) {
+            TileRec& r = b->recs[t];
+            StencilArgs& a = r.a;
+            a = StencilArgs{};
+            a.H = H[t]; a.W = W[t]; a.ld = b->ld[t];
+            a.tau = o.tau; a.inv_tau = 1.0f / o.tau; a.delta = o.delta;
+            a.tol2 = (double)o.cg_tol * (double)o.cg_tol;
+            a.cg_max = o.cg_max_iter;
+            a.flexible = o.flexible_cg;
+            a.warm_start = o.warm_start;
+            a.prec = o.precision;
+            a.r16 = b->dct.r16[t];
+            a.r16lo = b->dct.split ? b->dct.r16lo[t] : nullptr;
+            a.ld16 = b->dct.ld16[t];
+            strip_dims(H[t], W[t], r.sgx, r.sgy);
+            vec_dims(H[t], W[t], r.vgx, r.vgy);
+            r.sblk0 = sblk;
+            r.vblk0 = vblk;
+            sblk += r.sgx * r.sgy;
+            vblk += r.vgx * r.vgy;
+        }
+        b->total_strip = sblk;
+        b->total_vec = vblk;
+        ck(cudaMemcpy(b->d_recs, b->recs.data(), (size_t)T * sizeof(TileRec), cudaMemcpyHostToDevice));
+        ck(cudaHostAlloc(&b->h_count, 2 * sizeof(int), cudaHostAllocDefault));
+        for (auto& e : b->ev) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+        ck(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        ck(cudaDeviceSynchronize());
+    } catch (Fail&) {
+        destroy_batch(b);
+        return IRLS_ERR_CUDA;
+    }
+    *out = b;
+    return IRLS_OK;
+}
+
+int irls_batch_destroy(irls_batch b) {
+    destroy_batch(b);
+    return IRLS_OK;
+}
+
+int irls_batch_uses_graphs(irls_batch b) {
+    if (!b) return IRLS_ERR_ARG;
+    return (b->chunk[0] && b->chunk[1]) ? 1 : 0;
+}
+
+int irls_unwrap_batched_ex(irls_batch b, const float* const* X, const float* const* coh,
+                           float* const* U, irls_stats* per_tile, void* stream) {
+    if (!b || !X || !U) return IRLS_ERR_ARG;
+    for (int t = 0; t < b->T; ++t)
+        if (!X[t] || !U[t]) return IRLS_ERR_ARG;
+    int status = 0;
+    try {
+        DeviceGuard g(b->dev);
+        status = run_batch(b, X, coh, U, per_tile, static_cast<cudaStream_t>(stream));
+        if (status & ST_NONFINITE) return IRLS_ERR_NONFINITE;
+        // the caller's stream waits for the batch
+        ck(cudaEventRecord(b->join, b->stream));
+        ck(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), b->join, 0));
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return status_to_code(status);
+}
+
+int irls_unwrap_batched(int ntiles, const int* H, const int* W, const float* const* X,
+                        const float* const* coh, float* const* U, const irls_opts* opts,
+                        irls_stats* per_tile, void* stream) {
+    irls_batch b = nullptr;
+    int rc = irls_batch_create(ntiles, H, W, opts, &b);
+    if (rc != IRLS_OK) return rc;
+    rc = irls_unwrap_batched_ex(b, X, coh, U, per_tile, stream);
+    irls_batch_destroy(b);
     return rc;
 }
 

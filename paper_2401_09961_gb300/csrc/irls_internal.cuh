@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/irls.h"
 
 namespace irls {
@@ -98,6 +100,32 @@ struct DctPlan {
     alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
 };
 
+// One image of a batched solve: its planes, arguments, device state, reduction scratch and
+// inputs, and where its blocks start in the two stencil launch grids (one column per thread:
+// "strip"; four columns per thread: "vec").  Kept in device memory as an array over images.
+struct TileRec {
+    Planes P;
+    StencilArgs a;
+    DevState* st;
+    double* partials;
+    const float* X;
+    const float* coh;
+    int sblk0, sgx, sgy;
+    int vblk0, vgx, vgy;
+};
+
+// Tensor-core preconditioner of a batched solve: per-stage device arrays of grouped-GEMM
+// problems (one per image), the images' bf16 copies of r_U, and the DCT bases cached per
+// distinct side length.
+struct BatchDctPlan {
+    int T = 0, prec = 0, split = 0;
+    float tau = 0.f;
+    void* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
+    int total_ctas[4] = {0, 0, 0, 0};
+    std::vector<void*> r16, r16lo;
+    std::vector<int> ld16;
+};
+
 // ---- launchers (stencil kernels, irls_kernels.cu) -----------------------------------------
 cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, const float* Ch_in,
                         const float* U0, const float* Vv0, const float* Vh0, const Planes& P,
@@ -136,6 +164,18 @@ cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float*
                              const float* Gbh, const float* Cbv, const float* Cbh, float* dX,
                              float* dcoh, cudaStream_t s);
 
+// batched launches over a device array of TileRec (one launch for all images; images whose CG
+// run has stopped return at once)
+void strip_dims(int H, int W, int& gx, int& gy);
+void vec_dims(int H, int W, int& gx, int& gy);
+cudaError_t launch_init_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_direction_batched(const TileRec* recs, int T, int total_vec, cudaStream_t s);
+cudaError_t launch_update_batched(const TileRec* recs, int T, int total_vec, cudaStream_t s);
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStream_t s);
+
 // ---- DCT preconditioner (dct.cu) ------------------------------------------------------------
 size_t dct_bytes(int H, int W, int prec);
 cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
@@ -146,5 +186,12 @@ cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevS
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
                       cudaStream_t s);
 int dct_max_blocks(int H, int W);
+// batched form (dct_umma.cu): memory for T images of sizes H[t] x W[t], set-up, application
+size_t batch_dct_bytes(const int* H, const int* W, int T, int prec);
+cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T, int prec,
+                            float tau, int flexible, char* mem, const float* const* rU,
+                            float* const* zU, const int* ld, DevState* states,
+                            double* const* partials);
+cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s);
 
 }  // namespace irls

@@ -49,13 +49,12 @@ __device__ __forceinline__ double range_part(double rr, double sum_ru, int H, in
 // ------------------------------------------------------------------------------------------
 // Wrapped gradients, edge weights and the starting iterate (Sec. 2; Alg. 1 initialisation)
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_init(const float* __restrict__ X, const float* __restrict__ coh, const float* __restrict__ Cv_in,
+__device__ __forceinline__ void k_init_body(const float* __restrict__ X, const float* __restrict__ coh, const float* __restrict__ Cv_in,
        const float* __restrict__ Ch_in, const float* __restrict__ U0, const float* __restrict__ Vv0,
-       const float* __restrict__ Vh0, Planes P, StencilArgs a, DevState* st) {
+       const float* __restrict__ Vh0, Planes P, StencilArgs a, DevState* st, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     int bad = 0;
     if (j < W) {
         for (int i = i0; i < i1; ++i) {
@@ -95,12 +94,18 @@ k_init(const float* __restrict__ X, const float* __restrict__ coh, const float* 
     if (bad) atomicOr(&st->status, ST_NONFINITE);
 }
 
-// ||b||^2 with b = ((S^T Gv + Gh T^T)/tau, -Gv/tau, -Gh/tau)  (Sec. 3.2, definition of B1..B3)
 __global__ void __launch_bounds__(kThreads)
-k_bnorm(Planes P, StencilArgs a, DevState* st, double* partials) {
+k_init(const float* __restrict__ X, const float* __restrict__ coh, const float* __restrict__ Cv_in,
+       const float* __restrict__ Ch_in, const float* __restrict__ U0, const float* __restrict__ Vv0,
+       const float* __restrict__ Vh0, Planes P, StencilArgs a, DevState* st) {
+    k_init_body(X, coh, Cv_in, Ch_in, U0, Vv0, Vh0, P, a, st, single_blk());
+}
+
+// ||b||^2 with b = ((S^T Gv + Gh T^T)/tau, -Gv/tau, -Gh/tau)  (Sec. 3.2, definition of B1..B3)
+__device__ __forceinline__ void k_bnorm_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     float acc = 0.f;
     if (j < W) {
         for (int i = i0; i < i1; ++i) {
@@ -113,7 +118,12 @@ k_bnorm(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
     }
     double v[1] = {(double)acc}, tot[1];
-    if (grid_reduce<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st->bb = tot[0];
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) st->bb = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bnorm(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_bnorm_body(P, a, st, partials, single_blk());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -134,12 +144,11 @@ __device__ __forceinline__ void emit16(void* r16, void* r16lo, int ld16, int i, 
             __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
+__device__ __forceinline__ void k_reweight_residual_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int j = blk.bx * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     const bool col = j < W, hh = j + 1 < W;
     const float it = a.inv_tau, d2 = a.delta * a.delta;
     const bool warm = a.warm_start != 0;
@@ -194,7 +203,7 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
         uc = un;
     }
     double v[5] = {(double)rr, (double)rzv, (double)fd, (double)ru2, (double)su}, tot[5];
-    if (grid_reduce<5>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<5>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
         st->rr = rr_range;
         st->rz_v = tot[1];
@@ -207,6 +216,11 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
         const int k = st->outer;
         if (k < kMaxOuter) st->f_delta[k] = tot[2];
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_reweight_residual_body(P, a, st, partials, single_blk());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -233,13 +247,12 @@ __device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4]) 
 // p^T A p = sum (y_v^2 + y_h^2) / tau + D p_V^2; alpha = rho / p^T A p.
 // ------------------------------------------------------------------------------------------
 template <int ROWS>
-__global__ void __launch_bounds__(kThreads)
-k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
+__device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
     if (st->done) return;
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j0 = (blockIdx.x * kThreads + threadIdx.x) * kVec;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * ROWS, i1 = min(i0 + ROWS, H);
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
     const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf, nxt = cur ^ 1;
@@ -340,7 +353,7 @@ k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
     }
     double v[1] = {(double)acc}, tot[1];
-    if (grid_reduce<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double pq = tot[0];
         st->pq = pq;
         st->pbuf = nxt;
@@ -357,19 +370,24 @@ k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
     }
 }
 
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_direction_pap(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_direction_pap_body<ROWS>(P, a, st, partials, single_blk());
+}
+
 // ------------------------------------------------------------------------------------------
 // CG update (Alg. 2): x += alpha p, r -= alpha A p with A p recomputed from p (the stencil of
 // eq. 'matrix-soft-constraints'), then ||r||^2, r_V^T z_V (z_V = r_V / (D + 1/tau)) and, for the
 // flexible variant, r_new^T z_old.  Stops the run when ||r|| <= cg_tol ||b|| or on cg_max.
 // ------------------------------------------------------------------------------------------
 template <int ROWS>
-__global__ void __launch_bounds__(kThreads)
-k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
+__device__ __forceinline__ void k_update_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
     if (st->done) return;
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j0 = (blockIdx.x * kThreads + threadIdx.x) * kVec;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * ROWS, i1 = min(i0 + ROWS, H);
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
     const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf;
@@ -474,7 +492,7 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
     }
     double v[5] = {(double)rr, (double)rzv, (double)rzo, (double)ru2, (double)su}, tot[5];
-    if (grid_reduce<5>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<5>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
         st->rr = rr_range;
         st->rz_v = tot[1];
@@ -489,15 +507,20 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
     }
 }
 
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_update_body<ROWS>(P, a, st, partials, single_blk());
+}
+
 // ------------------------------------------------------------------------------------------
 // End of an outer step: sum U (for U -= mean(U), Prop. 'minimising (alt1)'), the objective of
 // problem (main) and H_delta(x^{k+1}, W^k) of problem (alt1); then record the statistics.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
+__device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     const double it = 1.0 / (double)a.tau, d2 = (double)a.delta * (double)a.delta;
     // FP64 evaluation: the difference of two float32 values is exact in double, so the edge
     // residuals of the objective carry no cancellation error of their own
@@ -524,7 +547,7 @@ k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
     }
     double v[3] = {su, l1, hd}, tot[3];
-    if (grid_reduce<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         st->mean_u = tot[0] / ((double)H * (double)W);
         const int k = st->outer;
         if (k < kMaxOuter) {
@@ -540,12 +563,21 @@ k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_subtract_mean(float* U, int H, int W, int ld, const DevState* st) {
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_finalize_reduce_body(P, a, st, partials, single_blk());
+}
+
+__device__ __forceinline__ void k_subtract_mean_body(float* U, int H, int W, int ld, const DevState* st, const Blk& blk) {
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     if (j >= W) return;
     const float m = (float)st->mean_u;
     for (int i = i0; i < i1; ++i) U[(size_t)i * ld + j] -= m;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_subtract_mean(float* U, int H, int W, int ld, const DevState* st) {
+    k_subtract_mean_body(U, H, W, ld, st, single_blk());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -558,16 +590,20 @@ k_subtract_mean(float* U, int H, int W, int ld, const DevState* st) {
 // and writes the next right-hand side xbar = (0, Dbar o (-C^4 V^k / W^3)) into the residual
 // planes (W^k = sqrt(C^2 (V^k)^2 + delta^2), D^k = C^2 / W^k: Alg. 1's reweighting).
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_user_mean(const float* __restrict__ src, int H, int W, DevState* st, double* partials) {
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+__device__ __forceinline__ void k_user_mean_body(const float* __restrict__ src, int H, int W, DevState* st, double* partials, const Blk& blk) {
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     float acc = 0.f;
     if (j < W)
         for (int i = i0; i < i1; ++i) acc += src[(size_t)i * W + j];
     double v[1] = {(double)acc}, tot[1];
-    if (grid_reduce<1>(v, partials, &st->counter, tot) && threadIdx.x == 0)
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0)
         st->mean_u = tot[0] / ((double)H * (double)W);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_user_mean(const float* __restrict__ src, int H, int W, DevState* st, double* partials) {
+    k_user_mean_body(src, H, W, st, partials, single_blk());
 }
 
 // xbar^K = (dL/dU - mean, 0, 0) into the residual planes
@@ -588,13 +624,12 @@ k_adj_init(Planes P, StencilArgs a, const float* __restrict__ dLdU, const DevSta
 
 // Adjoint solve set-up for step k: W^k, D^k from the checkpoint V^k, x = 0, r = xbar (already
 // in the residual planes); ||r||^2 is the scale of the relative stopping test.
-__global__ void __launch_bounds__(kThreads)
-k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
+__device__ __forceinline__ void k_adj_setup_body(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
             const float* __restrict__ Cv, const float* __restrict__ Ch, DevState* st,
-            double* partials) {
+            double* partials, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
     const float it = a.inv_tau, d2 = a.delta * a.delta;
     float rr = 0.f, rzv = 0.f, su = 0.f;
     if (j < W) {
@@ -621,7 +656,7 @@ k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float*
         }
     }
     double v[3] = {(double)rr, (double)rzv, (double)su}, tot[3];
-    if (grid_reduce<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[2], a.H, a.W);
         st->rr = rr_range;
         st->rz_v = tot[1];
@@ -631,6 +666,13 @@ k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float*
         st->p_fresh = 1;
         st->done = (rr_range <= 0.0 || a.cg_max <= 0) ? 1 : 0;
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
+            const float* __restrict__ Cv, const float* __restrict__ Ch, DevState* st,
+            double* partials) {
+    k_adj_setup_body(P, a, Vkv, Vkh, Cv, Ch, st, partials, single_blk());
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -698,6 +740,82 @@ k_adj_final(Planes P, StencilArgs a, const float* __restrict__ Gbv, const float*
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Batched launches: one grid over the blocks of every image; each block finds its image by a
+// binary search over the images' first-block indices and runs the single-image body with its
+// own coordinates, state and scratch.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_tile(const TileRec* __restrict__ r, int T, int bid, bool vec) {
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b0 = vec ? r[mid].vblk0 : r[mid].sblk0;
+        if (b0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ Blk tile_blk(const TileRec& r, int bid, bool vec) {
+    Blk b;
+    const int gx = vec ? r.vgx : r.sgx, gy = vec ? r.vgy : r.sgy;
+    const int local = bid - (vec ? r.vblk0 : r.sblk0);
+    b.bx = local % gx;
+    b.by = local / gx;
+    b.nblk = (unsigned)(gx * gy);
+    b.bid = (unsigned)local;
+    return b;
+}
+
+__global__ void __launch_bounds__(kThreads) kb_init(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    k_init_body(r.X, r.coh, nullptr, nullptr, nullptr, nullptr, nullptr, r.P, r.a, r.st,
+                tile_blk(r, blockIdx.x, false));
+}
+
+__global__ void __launch_bounds__(kThreads) kb_bnorm(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    k_bnorm_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+}
+
+__global__ void __launch_bounds__(kThreads) kb_reweight(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    k_reweight_residual_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads) kb_direction(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, true)];
+    k_direction_pap_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, true));
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads) kb_update(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, true)];
+    k_update_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, true));
+}
+
+__global__ void __launch_bounds__(kThreads) kb_finalize(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    k_finalize_reduce_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+}
+
+__global__ void __launch_bounds__(kThreads) kb_subtract_mean(const TileRec* __restrict__ recs, int T) {
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    k_subtract_mean_body(r.P.U, r.a.H, r.a.W, r.a.ld, r.st, tile_blk(r, blockIdx.x, false));
+}
+
+// number of images whose CG run has not stopped
+__global__ void k_count_active(const DevState* __restrict__ states, int T, int* out) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) c += states[t].done ? 0 : 1;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = cnt;
+}
+
 __global__ void k_copy_out(const float* __restrict__ src, int rows, int cols, int ld,
                            float* __restrict__ dst) {
     const size_t n = (size_t)rows * cols;
@@ -754,6 +872,56 @@ dim3 vec_grid(int H, int W) {
 }
 
 }  // namespace
+
+void strip_dims(int H, int W, int& gx, int& gy) {
+    dim3 g = strip_grid(H, W);
+    gx = (int)g.x;
+    gy = (int)g.y;
+}
+
+void vec_dims(int H, int W, int& gx, int& gy) {
+    dim3 g = vec_grid(H, W);
+    gx = (int)g.x;
+    gy = (int)g.y;
+}
+
+cudaError_t launch_init_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_init<<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_bnorm<<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_reweight<<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direction_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_direction<kVRows><<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_update<kVRows><<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
+    kb_finalize<<<total, kThreads, 0, s>>>(recs, T);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kb_subtract_mean<<<total, kThreads, 0, s>>>(recs, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStream_t s) {
+    k_count_active<<<1, 256, 0, s>>>(states, T, out);
+    return cudaGetLastError();
+}
 
 int stencil_grid_blocks(int H, int W) {
     dim3 g = strip_grid(H, W), v = vec_grid(H, W);

@@ -47,21 +47,32 @@ def l1_float32_floor(ref):
     return abs(O.l1_objective(U32, pb.Gv, pb.Gh, pb.Cv, pb.Ch) - l1)
 
 
-def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None):
+def edge_residuals(ref):
+    pb = ref["problem"]
+    U = ref["U"]
+    e = np.concatenate([np.abs(O.S_op(U) - pb.Gv).ravel(), np.abs(O.T_op(U) - pb.Gh).ravel()])
+    c = np.concatenate([pb.Cv.ravel(), pb.Ch.ravel()])
+    return e, c
+
+
+def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None, eps=1e-5):
+    """U within atol (both zero-mean), integer maps equal on >= 99.9 %, and the L1 objective
+    within l1_rtol relative plus 4 x the float32 floor of the oracle's own U.  Where edges whose
+    residual is below float32 trajectory noise (eps = 1e-5 rad) carry more of the objective than
+    the relative bar (2 eps sum_{|e|<eps} C > l1_rtol L1), |.| is not locally linear there and
+    no float32 trajectory can meet the bar: those edges get the bound the U agreement implies,
+    2 max|dU| sum C over the edges with |e| < max(eps, 2 max|dU|)."""
     Ug = Ug - Ug.mean()
     Uo = Uo - Uo.mean()
     err = np.abs(Ug - Uo).max()
     assert err <= atol, f"max |U_gpu - U_oracle| = {err}"
     tol = l1_rtol * max(abs(l1o), 1e-12) + 1e-9
     if ref is not None:
-        floor = l1_float32_floor(ref)
-        tol += 4.0 * floor
-        if floor >= 0.01 * abs(l1o):
-            # an objective at the float32 noise level (near-perfect unwrap): the relative bar has
-            # no meaning there, and the agreement of U bounds the objective's difference by the
-            # triangle inequality, |dL1| <= 2 max|dU| sum C
-            pb = ref["problem"]
-            tol += 2.0 * err * (pb.Cv.sum() + pb.Ch.sum())
+        tol += 4.0 * l1_float32_floor(ref)
+        e, c = edge_residuals(ref)
+        if 2.0 * eps * c[e < eps].sum() > l1_rtol * abs(l1o):
+            thr = max(eps, 2.0 * err)
+            tol += 2.0 * err * c[e < thr].sum()
     assert abs(l1g - l1o) <= tol, (l1g, l1o, tol)
     assert k_agreement(Ug, Uo, X) >= 0.999
 
