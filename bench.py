@@ -241,7 +241,10 @@ def main():
             "reweight_residual": args.outer * args.steps}
     bytes_px = {"direction_pap": 44.0, "reweight_residual": 56.0 + (2.0 if prec != "fp32" else 0),
                 "update": 68.0 + (2.0 if prec != "fp32" else 0) + (4.0 if flexible else 0)}
-    dct_flops = 4.0 * Hp * Wp * (n + n)
+    folded = plan.folded
+    # multiply-adds the preconditioner performs per application: four n^3 products in the direct
+    # form; the folded form runs each stage as half-size products (half of that)
+    dct_flops = 4.0 * Hp * Wp * (n + n) * (0.5 if folded else 1.0)
     dom = max(("direction_pap", "update", "dct_precond", "reweight_residual"),
               key=lambda c: per_cls[c]["ms"])
     avg_s = per_cls[dom]["ms"] / 1e3 / max(live[dom], 1)
@@ -256,7 +259,8 @@ def main():
             sus = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             passes = 3 if prec == "bf16x3" else 1
             alg = dct_flops / avg_s / 1e12
-            roof = {"kernel": f"dct_precond (4 tcgen05 GEMMs, {prec})", "bound": "tensor",
+            form = "folded even/odd" if folded else "direct"
+            roof = {"kernel": f"dct_precond (4 tcgen05 GEMMs, {form}, {prec})", "bound": "tensor",
                     "achieved": alg, "peak": sus / passes, "unit": "TFLOP/s",
                     "peak_source": (f"bf16_tflops_sustained ({peak_src}) / {passes}: the split "
                                     "product issues three bf16 MMAs per multiply-add"
@@ -270,7 +274,7 @@ def main():
     roof["traffic"] = None
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
-                         "dct_precond": 4, "finalize": 2}
+                         "dct_precond": 5 if folded else 4, "finalize": 2}
     gpu_launches = sum(per_cls[c]["launches"] * kernels_per_class[c] for c in classes)
     gpu_launches += args.steps  # copy-out of U
 
@@ -316,6 +320,8 @@ def main():
             "config": {"workload": workload_name(n, prec), "size": [n, n],
                        "outer_iters": args.outer, "delta": DELTA, "tau": TAU, "cg_tol": CG_TOL,
                        "precision": prec, "flexible_cg": bool(flexible),
+                       "dct_form": "folded" if folded else ("direct" if prec != "fp32" else
+                                                            "fp32 simt"),
                        "cg_iters_total": cg_total, "l1_objective": stats[-1]["l1_obj"][-1],
                        "cg_iters_per_outer": stats[-1]["cg_iters"],
                        "parallelism": f"replicas x{world}",

@@ -54,6 +54,12 @@ extern "C" {
 #define IRLS_PREC_BF16X3 2  /* split bfloat16: x = hi + lo, three tcgen05 products per GEMM   */
                             /* (hi*hi + hi*lo + lo*hi), float32 accumulation                  */
 
+/* Form of the tensor-core preconditioner (split precision only). */
+#define IRLS_DCT_AUTO   0   /* folded where allowed, else direct                                  */
+#define IRLS_DCT_DIRECT 1   /* four full-size products per application                            */
+#define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds; needs
+                             * precision IRLS_PREC_BF16X3 and H, W multiples of 256               */
+
 #define IRLS_MAX_OUTER 256
 
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
@@ -62,7 +68,7 @@ typedef struct irls_batch_s* irls_batch; /* opaque: a batched solve of many imag
 
 /* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
- * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1. */
+ * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1, dct_form = IRLS_DCT_AUTO. */
 typedef struct {
     float tau;          /* penalty tau of problem (soft constraints), Sec. 3.1; > 0            */
     float delta;        /* smoothing delta of F_delta, Sec. 3.1; > 0                           */
@@ -72,6 +78,7 @@ typedef struct {
     int   precision;    /* IRLS_PREC_*                                                         */
     int   flexible_cg;  /* 0: beta = rho_new / rho (Alg. 2); 1: Polak-Ribiere (flexible) beta  */
     int   warm_start;   /* 1: CG starts from the current (U, V); 0: from zero each outer step  */
+    int   dct_form;     /* IRLS_DCT_*; IRLS_DCT_FOLDED where not allowed: IRLS_ERR_UNSUPPORTED  */
 } irls_opts;
 
 /* Per-call statistics (host struct filled by the library). */
@@ -105,6 +112,12 @@ int irls_plan_destroy(irls_plan plan);
  * the precision the plan was created with (IRLS_ERR_UNSUPPORTED otherwise). */
 int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
 
+/* Preconditioner form the plan runs with its current options: IRLS_DCT_FOLDED or
+ * IRLS_DCT_DIRECT for the tensor-core precisions, IRLS_DCT_AUTO for IRLS_PREC_FP32 (no tensor
+ * cores); IRLS_ERR_ARG for a NULL plan.  The paper has no counterpart (an implementation
+ * choice of this library). */
+int irls_plan_dct_form(irls_plan plan);
+
 /* Simple form: unwrap d_X (H x W) into d_U (H x W, zero mean) with weights from d_coherence
  * (H x W, may be NULL for uniform weights), delta = eps, the given number of IRLS iterations
  * and CG tolerance, and the remaining options at their defaults (tau = 1e-2).  Edge weights from
@@ -136,7 +149,9 @@ int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
  * d_X[t], d_coherence[t] (the array may be NULL for uniform weights; entries may be NULL),
  * d_U[t]; per_tile (nullable) receives ntiles statistics.  Synchronous with respect to the host;
  * `stream` is ordered before and after the batch.  irls_unwrap_batched is create + run +
- * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist. */
+ * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist.
+ * The grouped preconditioner runs in the direct form (dct_form IRLS_DCT_FOLDED is
+ * IRLS_ERR_UNSUPPORTED). */
 int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* opts,
                       irls_batch* out);
 int irls_batch_destroy(irls_batch batch);

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 
-from ._binding import (IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
+from ._binding import (DCT_FORMS, IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
                        lib)
 
 __all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
@@ -56,6 +56,11 @@ class Plan:
         self._h = h
 
     @property
+    def folded(self):
+        """True when the preconditioner runs in the folded (even / odd) form."""
+        return lib().irls_plan_dct_form(self.handle) == DCT_FORMS["folded"]
+
+    @property
     def handle(self):
         if self._h is None:
             raise RuntimeError("plan destroyed")
@@ -66,6 +71,8 @@ class Plan:
         for k, v in kw.items():
             if k == "precision" and isinstance(v, str):
                 v = PRECISIONS[v]
+            if k == "dct_form" and isinstance(v, str):
+                v = DCT_FORMS[v]
             setattr(o, k, v)
         check(lib().irls_plan_set_opts(self.handle, ctypes.byref(o)), "irls_plan_set_opts")
         self.opts = o

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libirls.so")
 
 IRLS_MAX_OUTER = 256
+DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
 STATUS = {
@@ -32,6 +33,7 @@ class Opts(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("flexible_cg", ctypes.c_int),
         ("warm_start", ctypes.c_int),
+        ("dct_form", ctypes.c_int),
     ]
 
 
@@ -72,6 +74,7 @@ SIGNATURES = {
     "irls_plan_create": (_I, [_I, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "irls_plan_destroy": (_I, [_P]),
     "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
+    "irls_plan_dct_form": (_I, [_P]),
     "irls_unwrap": (_I, [_P, _P, _I, _I, _F, _I, _F, _P, _P]),
     "irls_unwrap_ex": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "irls_unwrap_forward_record": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(_P),
@@ -139,5 +142,7 @@ def default_opts(**kw):
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "dct_form" and isinstance(v, str):
+            v = DCT_FORMS[v]
         setattr(o, k, v)
     return o

@@ -24,6 +24,7 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
                            int skip_if_done, cudaStream_t s);
 size_t umma_dct_bytes(int H, int W, int split);
 cudaError_t umma_dct_setup(DctPlan& d, char* mem);
+void umma_dct_release(DctPlan& d);
 
 namespace {
 
@@ -242,6 +243,8 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) 
     }
     return e;
 }
+
+void dct_release(DctPlan& d) { umma_dct_release(d); }
 
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,

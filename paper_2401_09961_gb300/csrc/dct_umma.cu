@@ -46,12 +46,23 @@ constexpr int UBM = 128, UBK = 64;
 constexpr int kUThreads = 128;
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (about 2 s at 2 GHz)
 
-enum UEpi : int { UE_STORE16 = 0, UE_EIG16 = 1, UE_ZU = 2, UE_ZU_RHO = 3 };
+enum UEpi : int {
+    UE_STORE16 = 0, UE_EIG16 = 1, UE_ZU = 2, UE_ZU_RHO = 3,
+    // folded (even/odd) forms, two accumulators
+    UE_FOLD16 = 4,        // out+ = acc0 + mirror(acc1), out- = acc0 - mirror(acc1)
+    UE_UNFOLD16 = 5,      // row m: acc0 + acc1, row mrows-1-m: acc0 - acc1
+    UE_UNFOLDZ = 6,       // col n: acc0 + acc1, col mcols-1-n: acc0 - acc1 (fp32)
+    UE_UNFOLDZ_RHO = 7    // same, plus r^T z and the CG ratio
+};
 
 struct UEpiArgs {
     void* C;             // bf16 output (STORE16 / EIG16) or float output (ZU)
     void* C_lo;          // bf16 low part of a split output, or null
+    void* C2;            // second bf16 output (FOLD16: the differences)
+    void* C2_lo;
     int ldc;
+    int mrows, mcols;    // mirror extents (UNFOLD16: rows; UNFOLDZ: columns)
+    int keep_origin;     // EIG16: keep the (0, 0) coefficient (a folded block that is not DC)
     int vm, vn;          // valid extents of the output
     const float* lam_m;
     const float* lam_n;
@@ -195,12 +206,57 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int BN, int EPI, int SA, int SB>
+// 32 consecutive values of one row as bf16 (hi) and, with a lo plane, bf16(v - hi)
+__device__ __forceinline__ void store_row32(void* hi, void* lo, size_t off, const float (&v)[32]) {
+    uint4* dh = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(hi) + off);
+    if (lo == nullptr) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 w;
+            w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+            w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+            w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+            w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+            dh[q] = w;
+        }
+        return;
+    }
+    uint4* dl = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(lo) + off);
+    float h[32], l[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        h[t] = __bfloat162float(__float2bfloat16_rn(v[t]));
+        l[t] = v[t] - h[t];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 w, wl;
+        w.x = pack_bf16(h[8 * q + 0], h[8 * q + 1]);
+        w.y = pack_bf16(h[8 * q + 2], h[8 * q + 3]);
+        w.z = pack_bf16(h[8 * q + 4], h[8 * q + 5]);
+        w.w = pack_bf16(h[8 * q + 6], h[8 * q + 7]);
+        wl.x = pack_bf16(l[8 * q + 0], l[8 * q + 1]);
+        wl.y = pack_bf16(l[8 * q + 2], l[8 * q + 3]);
+        wl.z = pack_bf16(l[8 * q + 4], l[8 * q + 5]);
+        wl.w = pack_bf16(l[8 * q + 6], l[8 * q + 7]);
+        dh[q] = w;
+        dl[q] = wl;
+    }
+}
+
+template <int BN, int EPI, int SA, int SB, int DUAL = 0>
 __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtensorMap* tmA1,
                                           const CUtensorMap* tmB0, const CUtensorMap* tmB1,
                                           int K, const UEpiArgs& ep, int m0, int n0,
-                                          unsigned nblk, unsigned bid) {
+                                          unsigned nblk, unsigned bid,
+                                          const CUtensorMap* tmA2 = nullptr,
+                                          const CUtensorMap* tmA3 = nullptr,
+                                          const CUtensorMap* tmB2 = nullptr,
+                                          const CUtensorMap* tmB3 = nullptr, int n0b1 = 0) {
+    // DUAL: a second operand set (A2/A3, B2/B3 at B row n0b1) accumulates into TMEM columns
+    // [BN, 2 BN); its K loop follows the first one through the same shared-memory ring
     using C = UCfg<BN, SA, SB>;
+    constexpr uint32_t kCols = DUAL ? 2 * C::kTmemCols : C::kTmemCols;
     if (ep.skip_if_done && ep.st->done) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -213,6 +269,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = K / UBK;
+    const int nkt = DUAL ? 2 * nkb : nkb;
 
     if (threadIdx.x == 0) {
         s_err = 0;
@@ -223,7 +280,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
         mbar_init(accf, 1);
         fence_mbar_init();
     }
-    if (warp == 2) tmem_alloc(tmem_slot, C::kTmemCols);
+    if (warp == 2) tmem_alloc(tmem_slot, kCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -231,26 +288,31 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int kb = 0; kb < nkt; ++kb) {
                 const int s = kb % C::kStages;
                 const uint32_t ph = (uint32_t)(kb / C::kStages) & 1u;
                 if (kb >= C::kStages && !mbar_wait(&empty[s], ph ^ 1u)) {
                     atomicExch(&s_err, 1);
                     break;
                 }
+                const bool second = DUAL && kb >= nkb;
+                const int kc = (second ? kb - nkb : kb) * UBK;
+                const int nb0 = second ? n0b1 : n0;
                 uint8_t* sa = smem + s * C::kStageBytes;
                 uint8_t* sb = sa + SA * C::kABytes;
                 mbar_expect_tx(&full[s], C::kStageBytes);
-                tma_load_2d(sa, tmA0, &full[s], kb * UBK, m0);
-                if constexpr (SA == 2) tma_load_2d(sa + C::kABytes, tmA1, &full[s], kb * UBK, m0);
-                tma_load_2d(sb, tmB0, &full[s], kb * UBK, n0);
-                if constexpr (SB == 2) tma_load_2d(sb + C::kBBytes, tmB1, &full[s], kb * UBK, n0);
+                tma_load_2d(sa, second ? tmA2 : tmA0, &full[s], kc, m0);
+                if constexpr (SA == 2)
+                    tma_load_2d(sa + C::kABytes, second ? tmA3 : tmA1, &full[s], kc, m0);
+                tma_load_2d(sb, second ? tmB2 : tmB0, &full[s], kc, nb0);
+                if constexpr (SB == 2)
+                    tma_load_2d(sb + C::kBBytes, second ? tmB3 : tmB1, &full[s], kc, nb0);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int kb = 0; kb < nkt; ++kb) {
                 const int s = kb % C::kStages;
                 const uint32_t ph = (uint32_t)(kb / C::kStages) & 1u;
                 if (!mbar_wait(&full[s], ph)) {
@@ -258,16 +320,19 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
                     break;
                 }
                 tc_fence_after();
+                const bool second = DUAL && kb >= nkb;
+                const int kk = second ? kb - nkb : kb;
+                const uint32_t td = tmem + (second ? (uint32_t)BN : 0u);
                 const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
                 const uint32_t sb = sa + SA * C::kABytes;
                 const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
                 const uint64_t dal = desc_sw128(sa + C::kABytes), dbl = desc_sw128(sb + C::kBBytes);
 #pragma unroll
                 for (int j = 0; j < UBK / 16; ++j) {   // K = 16 per MMA: +32 bytes (= 2 in >> 4)
-                    if constexpr (SB == 2) umma_bf16(tmem, da + 2 * j, dbl + 2 * j, C::kIdesc, (kb | j) != 0);
+                    if constexpr (SB == 2) umma_bf16(td, da + 2 * j, dbl + 2 * j, C::kIdesc, (kk | j) != 0);
                     if constexpr (SA == 2)
-                        umma_bf16(tmem, dal + 2 * j, db + 2 * j, C::kIdesc, SB == 2 || (kb | j) != 0);
-                    umma_bf16(tmem, da + 2 * j, db + 2 * j, C::kIdesc, SA == 2 || SB == 2 || (kb | j) != 0);
+                        umma_bf16(td, dal + 2 * j, db + 2 * j, C::kIdesc, SB == 2 || (kk | j) != 0);
+                    umma_bf16(td, da + 2 * j, db + 2 * j, C::kIdesc, SA == 2 || SB == 2 || (kk | j) != 0);
                 }
                 umma_commit(&empty[s]);
             }
@@ -293,7 +358,60 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
             const int nb = n0 + c * 32;
-            if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+            if constexpr (EPI == UE_FOLD16) {
+                // acc1 holds the mirrored tile: its column BN-1-x pairs with acc0's column x
+                uint32_t r1[32];
+                tmem_ld32(tl + (uint32_t)BN + (uint32_t)((BN / 32 - 1 - c) * 32), r1);
+                float pl[32], mi[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
+                    pl[t] = a + b;
+                    mi[t] = a - b;
+                }
+                store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
+                store_row32(ep.C2, ep.C2_lo, (size_t)m * ep.ldc + nb, mi);
+            } else if constexpr (EPI == UE_UNFOLD16) {
+                uint32_t r1[32];
+                tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+                float pl[32], mi[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[t]);
+                    pl[t] = a + b;
+                    mi[t] = a - b;
+                }
+                store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
+                store_row32(ep.C, ep.C_lo, (size_t)(ep.mrows - 1 - m) * ep.ldc + nb, mi);
+            } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
+                uint32_t r1[32];
+                tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+                float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
+                const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 w, wm;
+                    float* wp = &w.x;
+                    float* wmp = &wm.x;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = 4 * q + u;            // column nb + t
+                        const int tm = 31 - (4 * q + u);    // mirrored column mb + 4q + u
+                        wp[u] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);
+                        wmp[u] = __uint_as_float(r[tm]) - __uint_as_float(r1[tm]);
+                    }
+                    reinterpret_cast<float4*>(out + nb)[q] = w;
+                    reinterpret_cast<float4*>(out + mb)[q] = wm;
+                    if constexpr (EPI == UE_UNFOLDZ_RHO) {
+                        const float* rr = ep.rU + (size_t)m * ep.ldc;
+                        const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
+                        const float4 xm = reinterpret_cast<const float4*>(rr + mb)[q];
+                        part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
+                        part += xm.x * wm.x + xm.y * wm.y + xm.z * wm.z + xm.w * wm.w;
+                    }
+                }
+            } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
                 float v[32];
 #pragma unroll
                 for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
@@ -303,7 +421,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
 #pragma unroll
                     for (int t = 0; t < 32; ++t) {
                         const int n = nb + t;
-                        const bool keep = rowok && n < ep.vn && (m | n) != 0;
+                        const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
                         v[t] = keep ? ep.scale * v[t] / (lm + __ldg(&ep.lam_n[n])) : 0.f;
                     }
                 }
@@ -379,9 +497,9 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
     __syncthreads();
     if (warp == 2) {
         tc_fence_after();
-        tmem_dealloc(tmem, C::kTmemCols);
+        tmem_dealloc(tmem, kCols);
     }
-    if constexpr (EPI == UE_ZU_RHO) {
+    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
         double vv[1] = {(double)part}, tot[1];
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0) {
             DevState* st = ep.st;
@@ -416,15 +534,18 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
 // epilogue arguments and the index of its first CTA in the launch.
 struct alignas(64) GemmTile {
     CUtensorMap a0, a1, b0, b1;
+    CUtensorMap a2, a3, b2, b3;   // second operand set (dual-accumulator stages)
     UEpiArgs ep;
     int M, N, K;
     int blk0, gx;
+    int mirror_b1;                // second set's B rows mirrored: nb_rows - n0 - 128
+    int nb_rows;
 };
 
 // Grouped GEMM: one launch over the output tiles of every problem (BN = 128).  A CTA finds its
 // problem by a binary search over the first-CTA indices; problems whose CG run has stopped
 // return at once (the per-problem convergence mask).
-template <int EPI, int SA, int SB>
+template <int EPI, int SA, int SB, int DUAL = 0>
 __global__ void __launch_bounds__(kUThreads, 1)
 kb_umma_gemm(const GemmTile* __restrict__ tiles, int T) {
     int lo = 0, hi = T - 1;
@@ -436,8 +557,10 @@ kb_umma_gemm(const GemmTile* __restrict__ tiles, int T) {
     const GemmTile& g = tiles[lo];
     const int local = bid - g.blk0;
     const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * 128;
-    umma_body<128, EPI, SA, SB>(&g.a0, &g.a1, &g.b0, &g.b1, g.K, g.ep, m0, n0,
-                                (unsigned)((g.M / UBM) * g.gx), (unsigned)local);
+    umma_body<128, EPI, SA, SB, DUAL>(&g.a0, &g.a1, &g.b0, &g.b1, g.K, g.ep, m0, n0,
+                                      (unsigned)((g.M / UBM) * g.gx), (unsigned)local, &g.a2,
+                                      &g.a3, &g.b2, &g.b3,
+                                      g.mirror_b1 ? g.nb_rows - n0 - 128 : n0);
 }
 
 __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bfloat16* P16lo,
@@ -459,6 +582,68 @@ __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bf
             const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
             P16lo[(size_t)i * Np + k] = l;
             PT16lo[(size_t)k * Np + i] = l;
+        }
+    }
+}
+
+// Even / odd halves of the DCT basis of side n (n even), h = n / 2:
+//   Pe[a][b] = P[a][2b], Po[a][b] = P[a][2b+1] (a, b < h), their transposes, and the eigenvalues
+//   permuted to (even indices, odd indices).  P[n-1-a][k] = (-1)^k P[a][k] makes these enough.
+__global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat16* PeT,
+                               __nv_bfloat16* PoT, __nv_bfloat16* Pelo, __nv_bfloat16* Polo,
+                               __nv_bfloat16* PeTlo, __nv_bfloat16* PoTlo, float* lamP, int n) {
+    const int h = n / 2;
+    const size_t total = (size_t)h * h;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / h), b = (int)(t % h);
+        for (int par = 0; par < 2; ++par) {
+            const int k = 2 * b + par;
+            const long long mm = ((long long)(2 * a + 1) * k) % (4LL * n);
+            const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+            const double v = ck * cospi((double)mm / (2.0 * n));
+            const __nv_bfloat16 hv = __double2bfloat16(v);
+            const __nv_bfloat16 lv = __double2bfloat16(v - (double)__bfloat162float(hv));
+            __nv_bfloat16* P = par ? Po : Pe;
+            __nv_bfloat16* PT = par ? PoT : PeT;
+            P[(size_t)a * h + b] = hv;
+            PT[(size_t)b * h + a] = hv;
+            __nv_bfloat16* Pl = par ? Polo : Pelo;
+            __nv_bfloat16* PTl = par ? PoTlo : PeTlo;
+            if (Pl) {
+                Pl[(size_t)a * h + b] = lv;
+                PTl[(size_t)b * h + a] = lv;
+            }
+        }
+        if (a == 0) {
+            for (int par = 0; par < 2; ++par) {
+                const double sn = sinpi((double)(2 * b + par) / (2.0 * n));
+                lamP[par * h + b] = (float)(4.0 * sn * sn);
+            }
+        }
+    }
+}
+
+// Folded residual: Re[i][j] = r[i][j] + r[i][W-1-j], Ro[i][j] = r[i][j] - r[i][W-1-j] (j < W/2),
+// each split into bf16 hi + lo.
+__global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W,
+                         __nv_bfloat16* __restrict__ Re, __nv_bfloat16* __restrict__ Relo,
+                         __nv_bfloat16* __restrict__ Ro, __nv_bfloat16* __restrict__ Rolo,
+                         const DevState* st, int skip_if_done) {
+    if (skip_if_done && st->done) return;
+    const int h = W / 2;
+    const size_t total = (size_t)H * h;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / h), j = (int)(t % h);
+        const float a = rU[(size_t)i * ld + j], b = rU[(size_t)i * ld + (W - 1 - j)];
+        const float e = a + b, o = a - b;
+        const __nv_bfloat16 eh = __float2bfloat16_rn(e), oh = __float2bfloat16_rn(o);
+        Re[t] = eh;
+        Ro[t] = oh;
+        if (Relo) {
+            Relo[t] = __float2bfloat16_rn(e - __bfloat162float(eh));
+            Rolo[t] = __float2bfloat16_rn(o - __bfloat162float(oh));
         }
     }
 }
@@ -549,12 +734,249 @@ cudaError_t set_attrs() {
 
 }  // namespace
 
+bool foldable(int H, int W, int split) { return split && H % 256 == 0 && W % 256 == 0; }
+
+namespace {
+
+// Host-side record of the folded form's buffers and of the arguments its device tables were
+// last built for (the tables bake in the planes, the CG state and the epilogue flags).
+struct FoldBufs {
+    void *PeN[2], *PoN[2], *PeTN[2], *PoTN[2];   // [hi, lo]
+    void *PeM[2], *PoM[2], *PeTM[2], *PoTM[2];
+    float *lamPN, *lamPM;
+    void *Re[2], *Ro[2];                          // H x W/2
+    void* T1[4][2];                               // (x, sign) = (e+, e-, o+, o-), W/2 x H/2
+    void* T3[2][2];                               // x = e, o: H x W/2 (aliases T1)
+    void* T2[4][2];                               // (x, y) = ee, eo, oe, oo: W/2 x H/2
+    std::vector<GemmTile> tab[4];
+    bool bound = false;
+    const float* rU = nullptr;
+    float* zU = nullptr;
+    int ld = 0, flexible = 0, skip = 0;
+    DevState* st = nullptr;
+    double* partials = nullptr;
+    float tau = 0.f;
+};
+
+size_t fold_bytes(int H, int W) {
+    const size_t hN = H / 2, hM = W / 2;
+    size_t n = 4 * hN * hN + 3 * (size_t)H * W;   // basis halves; R e/o, T1 (= T3), T2
+    if (H != W) n += 4 * hM * hM;
+    return 2 * n * 2 + (size_t)(H + W) * 4 + 4 * 4 * sizeof(GemmTile) + 64 * 1024;
+}
+
+cudaError_t fold_setup(DctPlan& d, char* p) {
+    const int H = d.H, W = d.W;
+    const size_t hN = H / 2, hM = W / 2;
+    auto take = [&](size_t bytes) {
+        void* r = p;
+        p += rup(bytes, 1024);
+        return r;
+    };
+    FoldBufs* fp = new FoldBufs();
+    FoldBufs& f = *fp;
+    for (int q = 0; q < 2; ++q) {
+        f.PeN[q] = take(hN * hN * 2); f.PoN[q] = take(hN * hN * 2);
+        f.PeTN[q] = take(hN * hN * 2); f.PoTN[q] = take(hN * hN * 2);
+    }
+    f.lamPN = static_cast<float*>(take((size_t)H * 4));
+    if (H != W) {
+        for (int q = 0; q < 2; ++q) {
+            f.PeM[q] = take(hM * hM * 2); f.PoM[q] = take(hM * hM * 2);
+            f.PeTM[q] = take(hM * hM * 2); f.PoTM[q] = take(hM * hM * 2);
+        }
+        f.lamPM = static_cast<float*>(take((size_t)W * 4));
+    } else {
+        for (int q = 0; q < 2; ++q) {
+            f.PeM[q] = f.PeN[q]; f.PoM[q] = f.PoN[q]; f.PeTM[q] = f.PeTN[q]; f.PoTM[q] = f.PoTN[q];
+        }
+        f.lamPM = f.lamPN;
+    }
+    for (int q = 0; q < 2; ++q) {
+        f.Re[q] = take((size_t)H * hM * 2);
+        f.Ro[q] = take((size_t)H * hM * 2);
+    }
+    for (int q = 0; q < 2; ++q) {
+        char* region = static_cast<char*>(take((size_t)H * W * 2));
+        for (int b = 0; b < 4; ++b) f.T1[b][q] = region + (size_t)b * hM * hN * 2;
+        for (int x = 0; x < 2; ++x) f.T3[x][q] = region + (size_t)x * H * hM * 2;
+    }
+    for (int q = 0; q < 2; ++q)
+        for (int b = 0; b < 4; ++b) f.T2[b][q] = take(hM * hN * 2);
+    for (int st = 0; st < 4; ++st) d.fold_tiles[st] = take(4 * sizeof(GemmTile));
+    d.fold_host = fp;
+    d.Re = f.Re[0]; d.Relo = f.Re[1]; d.Ro = f.Ro[0]; d.Rolo = f.Ro[1];
+    using B = __nv_bfloat16;
+    auto bf = [](void* x) { return static_cast<B*>(x); };
+    k_build_fold16<<<1024, 256>>>(bf(f.PeN[0]), bf(f.PoN[0]), bf(f.PeTN[0]), bf(f.PoTN[0]),
+                                  bf(f.PeN[1]), bf(f.PoN[1]), bf(f.PeTN[1]), bf(f.PoTN[1]),
+                                  f.lamPN, H);
+    if (H != W)
+        k_build_fold16<<<1024, 256>>>(bf(f.PeM[0]), bf(f.PoM[0]), bf(f.PeTM[0]), bf(f.PoTM[0]),
+                                      bf(f.PeM[1]), bf(f.PoM[1]), bf(f.PeTM[1]), bf(f.PoTM[1]),
+                                      f.lamPM, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // problems per stage and their CTA counts depend on the shape only
+    const int tiles_g_hN = (int)((hM / UBM) * (hN / 128));
+    const int cnt[4] = {2, 4, 2, 1};
+    const int per[4] = {tiles_g_hN, tiles_g_hN, (int)((hN / UBM) * (hM / 128)),
+                        (int)((H / UBM) * (hM / 128))};
+    for (int k = 0; k < 4; ++k) {
+        d.fold_count[k] = cnt[k];
+        d.fold_ctas[k] = cnt[k] * per[k];
+    }
+    using C22 = UCfg<128, 2, 2>;
+    for (auto fn : {kb_umma_gemm<UE_FOLD16, 2, 2, 1>, kb_umma_gemm<UE_EIG16, 2, 2, 0>,
+                    kb_umma_gemm<UE_UNFOLD16, 2, 2, 1>, kb_umma_gemm<UE_UNFOLDZ, 2, 2, 1>,
+                    kb_umma_gemm<UE_UNFOLDZ_RHO, 2, 2, 1>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C22::kSmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// (Re)builds the four stage tables of the folded form for the given planes, state and flags and
+// copies them in stream order (kernels still reading the previous tables finish first).
+cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU, int ld,
+                      DevState* st, double* partials, int flexible, int skip, cudaStream_t s) {
+    const int H = d.H, W = d.W, hN = H / 2, hM = W / 2;
+    bool ok = true;
+    UEpiArgs base{};
+    base.st = st;
+    base.partials = partials;
+    base.flexible = flexible;
+    base.skip_if_done = skip;
+    auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
+        ok &= make_map(&g.a0, A[0], ar, ac, UBM);
+        ok &= make_map(&g.a1, A[1], ar, ac, UBM);
+        ok &= make_map(&g.b0, Bm[0], br, bc, 128);
+        ok &= make_map(&g.b1, Bm[1], br, bc, 128);
+        g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
+    };
+    auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
+        ok &= make_map(&g.a2, A[0], ar, ac, UBM);
+        ok &= make_map(&g.a3, A[1], ar, ac, UBM);
+        ok &= make_map(&g.b2, Bm[0], br, bc, 128);
+        ok &= make_map(&g.b3, Bm[1], br, bc, 128);
+    };
+    for (auto& t : f.tab) t.clear();
+    // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
+    // the second operand set reads the B rows mirrored
+    for (int x = 0; x < 2; ++x) {
+        GemmTile g{};
+        set0(g, x ? f.PoTM : f.PeTM, hM, hM, x ? f.Ro : f.Re, H, hM);
+        g.mirror_b1 = 1;
+        g.nb_rows = H;
+        g.M = hM; g.N = hN; g.K = hM;
+        g.ep = base;
+        g.ep.C = f.T1[2 * x][0]; g.ep.C_lo = f.T1[2 * x][1];
+        g.ep.C2 = f.T1[2 * x + 1][0]; g.ep.C2_lo = f.T1[2 * x + 1][1];
+        g.ep.ldc = hN;
+        f.tab[0].push_back(g);
+    }
+    // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
+    // divided by the eigenvalue sum at frequencies (2k' + y, 2l' + x)
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            GemmTile g{};
+            set0(g, f.T1[2 * x + y], hM, hN, y ? f.PoTN : f.PeTN, hN, hN);
+            g.M = hM; g.N = hN; g.K = hN;
+            g.ep = base;
+            g.ep.C = f.T2[2 * x + y][0]; g.ep.C_lo = f.T2[2 * x + y][1]; g.ep.ldc = hN;
+            g.ep.vm = hM; g.ep.vn = hN;
+            g.ep.lam_m = f.lamPM + x * hM;
+            g.ep.lam_n = f.lamPN + y * hN;
+            g.ep.scale = d.tau;
+            g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
+            f.tab[1].push_back(g);
+        }
+    // stage 3 (x): with E from the even and O from the odd frequencies along i,
+    // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O
+    for (int x = 0; x < 2; ++x) {
+        GemmTile g{};
+        set0(g, f.PeN, hN, hN, f.T2[2 * x], hM, hN);
+        set1(g, f.PoN, hN, hN, f.T2[2 * x + 1], hM, hN);
+        g.M = hN; g.N = hM; g.K = hN;
+        g.ep = base;
+        g.ep.C = f.T3[x][0]; g.ep.C_lo = f.T3[x][1]; g.ep.ldc = hM; g.ep.mrows = H;
+        f.tab[2].push_back(g);
+    }
+    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O, E from T3e, O from T3o
+    {
+        GemmTile g{};
+        set0(g, f.T3[0], H, hM, f.PeM, hM, hM);
+        set1(g, f.T3[1], H, hM, f.PoM, hM, hM);
+        g.M = H; g.N = hM; g.K = hM;
+        g.ep = base;
+        g.ep.C = zU; g.ep.ldc = ld; g.ep.mcols = W; g.ep.rU = rU;
+        f.tab[3].push_back(g);
+    }
+    if (!ok) return cudaErrorNotSupported;
+    for (int k = 0; k < 4; ++k) {
+        int cta = 0;
+        for (auto& g : f.tab[k]) {
+            g.gx = g.N / 128;
+            g.blk0 = cta;
+            cta += (g.M / UBM) * g.gx;
+        }
+        if ((int)f.tab[k].size() != d.fold_count[k] || cta != d.fold_ctas[k])
+            return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemcpyAsync(d.fold_tiles[k], f.tab[k].data(),
+                                        f.tab[k].size() * sizeof(GemmTile),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    f.bound = true;
+    f.rU = rU; f.zU = zU; f.ld = ld; f.st = st; f.partials = partials;
+    f.flexible = flexible; f.skip = skip; f.tau = d.tau;
+    return cudaSuccess;
+}
+
+cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
+                       int reduce_rho, int flexible, double* partials, int skip_if_done,
+                       cudaStream_t s) {
+    FoldBufs& f = *static_cast<FoldBufs*>(d.fold_host);
+    if (!f.bound || f.rU != rU || f.zU != zU || f.ld != ld || f.st != st ||
+        f.partials != partials || f.flexible != flexible || f.skip != skip_if_done ||
+        f.tau != d.tau) {
+        cudaError_t e = fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, s);
+        if (e != cudaSuccess) return e;
+    }
+    using C22 = UCfg<128, 2, 2>;
+    using B = __nv_bfloat16;
+    const size_t n = (size_t)d.H * (d.W / 2);
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, static_cast<B*>(d.Re), static_cast<B*>(d.Relo),
+                                    static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
+                                    skip_if_done);
+    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
+    kb_umma_gemm<UE_FOLD16, 2, 2, 1><<<d.fold_ctas[0], kUThreads, C22::kSmem, s>>>(tab(0), d.fold_count[0]);
+    kb_umma_gemm<UE_EIG16, 2, 2, 0><<<d.fold_ctas[1], kUThreads, C22::kSmem, s>>>(tab(1), d.fold_count[1]);
+    kb_umma_gemm<UE_UNFOLD16, 2, 2, 1><<<d.fold_ctas[2], kUThreads, C22::kSmem, s>>>(tab(2), d.fold_count[2]);
+    if (reduce_rho)
+        kb_umma_gemm<UE_UNFOLDZ_RHO, 2, 2, 1><<<d.fold_ctas[3], kUThreads, C22::kSmem, s>>>(tab(3), d.fold_count[3]);
+    else
+        kb_umma_gemm<UE_UNFOLDZ, 2, 2, 1><<<d.fold_ctas[3], kUThreads, C22::kSmem, s>>>(tab(3), d.fold_count[3]);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void umma_dct_release(DctPlan& d) {
+    delete static_cast<FoldBufs*>(d.fold_host);
+    d.fold_host = nullptr;
+    d.fold = d.fold_ready = 0;
+}
+
 size_t umma_dct_bytes(int H, int W, int split) {
     const size_t Hp = rup(H, 128), Wp = rup(W, 128);
     size_t n = 2 * Hp * Hp + 3 * Hp * Wp;
     if (H != W) n += 2 * Wp * Wp;
     if (split) n *= 2;
-    return n * 2 + 32 * 1024;
+    size_t bytes = n * 2 + 32 * 1024;
+    if (foldable(H, W, split)) bytes += fold_bytes(H, W);
+    return bytes;
 }
 
 cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
@@ -585,6 +1007,12 @@ cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
     take2(Hp * Wp, d.R16, d.R16lo);
     take2(Hp * Wp, d.S16a, d.S16alo);
     take2(Hp * Wp, d.S16b, d.S16blo);
+    umma_dct_release(d);
+    if (foldable(d.H, d.W, split)) {
+        cudaError_t ef = fold_setup(d, p);
+        if (ef != cudaSuccess) return ef;
+        d.fold = d.fold_ready = 1;
+    }
     using B = __nv_bfloat16;
     k_build_basis16<<<1024, 256>>>(static_cast<B*>(d.PN16), static_cast<B*>(d.PNT16),
                                    static_cast<B*>(d.PN16lo), static_cast<B*>(d.PNT16lo), d.H, d.Hp);
@@ -633,6 +1061,7 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
                            int reduce_rho, const StencilArgs& a, double* partials,
                            int skip_if_done, cudaStream_t s) {
     if (!d.umma_ok) return cudaErrorNotSupported;
+    if (d.fold) return fold_apply(d, rU, zU, ld, st, reduce_rho, a.flexible, partials, skip_if_done, s);
     const TmapSet& ts = *reinterpret_cast<const TmapSet*>(d.tmap_storage);
     const int Hp = d.Hp, Wp = d.Wp;
     const int mk = d.split;

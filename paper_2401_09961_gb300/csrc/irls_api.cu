@@ -53,6 +53,7 @@ bool opts_valid(const irls_opts& o) {
     if (o.outer_iters < 0 || o.outer_iters > IRLS_MAX_OUTER) return false;
     if (o.cg_max_iter < 0) return false;
     if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_BF16X3) return false;
+    if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FOLDED) return false;
     return true;
 }
 
@@ -196,8 +197,20 @@ StencilArgs make_args(const irls_plan_s* p) {
     // the residual carries a lo part when the first product splits its data operand
     a.r16lo = (p->opts.precision == IRLS_PREC_BF16X3 && (p->dct.split & 2)) ? p->dct.R16lo
                                                                              : nullptr;
+    // the folded form makes its own bf16 operands from r_U (sums and differences of mirrored
+    // columns), so the stencil kernels emit none
+    if (p->opts.precision == IRLS_PREC_BF16X3 && p->dct.fold) a.r16 = a.r16lo = nullptr;
     a.ld16 = p->dct.Wp;
     return a;
+}
+
+// Folded preconditioner on or off for the given options; false when IRLS_DCT_FOLDED is asked for
+// and the plan has no folded form (a shape or precision that does not allow it).
+bool select_dct_form(irls_plan_s* p, const irls_opts& o) {
+    const bool ready = p->dct.fold_ready && o.precision == IRLS_PREC_BF16X3;
+    if (o.dct_form == IRLS_DCT_FOLDED && !ready) return false;
+    p->dct.fold = ready && o.dct_form != IRLS_DCT_DIRECT;
+    return true;
 }
 
 void destroy_plan(irls_plan_s* p) {
@@ -206,6 +219,7 @@ void destroy_plan(irls_plan_s* p) {
     cudaGetDevice(&cur);
     cudaSetDevice(p->dev);
     cudaDeviceSynchronize();
+    dct_release(p->dct);
     if (p->mem) cudaFree(p->mem);
     if (p->h_flag) cudaFreeHost(p->h_flag);
     for (auto& e : p->ev)
@@ -520,6 +534,7 @@ int irls_opts_default(irls_opts* o) {
     o->precision = IRLS_PREC_FP32;
     o->flexible_cg = 0;
     o->warm_start = 1;
+    o->dct_form = IRLS_DCT_AUTO;
     return IRLS_OK;
 }
 
@@ -571,6 +586,10 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
         p->st = reinterpret_cast<DevState*>(p->mem + p->L.state);
         p->partials = reinterpret_cast<double*>(p->mem + p->L.partials);
         ck(dct_setup(p->dct, H, W, o.precision, o.tau, p->mem + p->L.dct));
+        if (!select_dct_form(p, o)) {
+            destroy_plan(p);
+            return IRLS_ERR_UNSUPPORTED;
+        }
         ck(cudaHostAlloc(&p->h_flag, 2 * sizeof(int), cudaHostAllocDefault));
         for (auto& ev : p->ev) ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         ck(cudaDeviceSynchronize());
@@ -580,6 +599,12 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
     }
     *out = p;
     return IRLS_OK;
+}
+
+int irls_plan_dct_form(irls_plan p) {
+    if (!p) return IRLS_ERR_ARG;
+    if (p->opts.precision == IRLS_PREC_FP32) return IRLS_DCT_AUTO;
+    return p->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
 }
 
 int irls_plan_destroy(irls_plan p) {
@@ -593,6 +618,7 @@ int irls_plan_set_opts(irls_plan p, const irls_opts* opts) {
     if (opts->precision != p->opts.precision && opts->precision != IRLS_PREC_FP32 &&
         opts->precision != p->prec_alloc)
         return IRLS_ERR_UNSUPPORTED;
+    if (!select_dct_form(p, *opts)) return IRLS_ERR_UNSUPPORTED;
     if (opts->tau != p->opts.tau) {
         p->dct.tau = opts->tau;
     }
@@ -748,6 +774,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     if (opts) o = *opts;
     if (!opts_valid(o)) return IRLS_ERR_ARG;
     if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
+    if (o.dct_form == IRLS_DCT_FOLDED) return IRLS_ERR_UNSUPPORTED;   // grouped form is direct
     for (int t = 0; t < ntiles; ++t)
         if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
     irls_batch_s* b = new (std::nothrow) irls_batch_s();

@@ -97,6 +97,14 @@ struct DctPlan {
     void *R16lo, *S16alo, *S16blo;  // lo parts
     int split;
     int umma_ok;
+    // folded (even/odd) form for H, W multiples of 256: half-size products on r_U(j) +- r_U(W-1-j)
+    int fold;                  // folded form in use
+    int fold_ready;            // folded form built (memory, bases)
+    void* fold_tiles[4];       // device tables of grouped-GEMM problems per stage
+    int fold_count[4];         // problems per stage (2, 4, 2, 1)
+    int fold_ctas[4];
+    void *Re, *Relo, *Ro, *Rolo;   // folded residual, H x W/2 each
+    void* fold_host;               // host-side record of the folded form (owned)
     alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
 };
 
@@ -182,6 +190,7 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
 // z_U = L^+ (tau r_U) from the plane rU (pitch ld) into zU (pitch ld).  `st` (never null)
 // receives error flags; with reduce_rho the last GEMM also forms rho = r_U^T z_U + st->rz_v
 // and the next beta (Alg. 2).  With skip_if_done the launches return at once once CG stopped.
+void dct_release(DctPlan& d);
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
                       cudaStream_t s);

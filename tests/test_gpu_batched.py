@@ -26,6 +26,8 @@ def cuda(a):
 
 
 OPTS = dict(tau=1e-2, delta=1e-3, outer_iters=5, cg_tol=1e-6, cg_max_iter=1000)
+# single-image plans in the grouped form's (direct) preconditioner, for bit-identical comparisons
+DIRECT = dict(OPTS, dct_form="direct")
 
 
 def test_batched_equals_single_image_path(irls):
@@ -40,7 +42,7 @@ def test_batched_equals_single_image_path(irls):
         assert b.uses_graphs
         Us2, st2 = b.unwrap(Xs, Cs)   # a second call on the same batch (graph replay)
     for t, (h, w) in enumerate(shapes):
-        with irls.Plan(h, w, precision="bf16x3", **OPTS) as p:
+        with irls.Plan(h, w, precision="bf16x3", **DIRECT) as p:
             U, s1 = p.unwrap(Xs[t], Cs[t])
         assert torch.equal(Us[t], U), t
         assert torch.equal(Us2[t], U), t
@@ -62,7 +64,7 @@ def test_batched_per_image_convergence_masks(irls):
     assert st[0]["cg_iters"] == [0] * 5 and float(Us[0].abs().max()) == 0.0
     assert sum(st[1]["cg_iters"]) > 5 * sum(st[2]["cg_iters"])
     for t, (h, w) in enumerate(shapes):
-        with irls.Plan(h, w, precision="bf16x3", **OPTS) as p:
+        with irls.Plan(h, w, precision="bf16x3", **DIRECT) as p:
             U, s1 = p.unwrap(Xs[t], Cs[t])
         assert torch.equal(Us[t], U) and st[t]["cg_iters"] == s1["cg_iters"]
 
@@ -80,6 +82,12 @@ def test_batched_matches_oracle(irls):
                              ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref)
 
 
+def test_batched_rejects_folded_form(irls):
+    with pytest.raises(irls.IrlsError) as e:
+        irls.Batch([(256, 256)], precision="bf16x3", dct_form="folded", **OPTS)
+    assert e.value.code == -8
+
+
 def test_batched_64_uneven_tiles(irls):
     """The 64-tile workload: sides drawn from {256, 384, ..., 1536}, one batch; a few tiles are
     re-solved alone and must agree bit for bit."""
@@ -93,6 +101,6 @@ def test_batched_64_uneven_tiles(irls):
     assert all(s["outer_done"] == 3 for s in st)
     for t in (0, 17, 63):
         h, w = shapes[t]
-        with irls.Plan(h, w, precision="bf16x3", **opts) as p:
+        with irls.Plan(h, w, precision="bf16x3", dct_form="direct", **opts) as p:
             U, _ = p.unwrap(Xs[t], Cs[t])
         assert torch.equal(Us[t], U), t

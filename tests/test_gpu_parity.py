@@ -108,8 +108,10 @@ def parity_atol(env):
 # ------------------------------------------------------------------------------------------
 # single operators
 # ------------------------------------------------------------------------------------------
+# (256, 256), (512, 256), (256, 768) and (1024, 512) take the folded tensor-core form in bf16x3
+# (both sides multiples of 256); the others the direct one
 PRECOND_SHAPES = [(64, 48), (130, 257), (256, 256), (384, 256), (256, 640), (1, 200), (300, 1),
-                  (3, 3)]
+                  (3, 3), (512, 256), (256, 768), (1024, 512), (2048, 2048), (1920, 2048)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
@@ -117,7 +119,9 @@ PRECOND_SHAPES = [(64, 48), (130, 257), (256, 256), (384, 256), (256, 640), (1, 
 def test_precond_laplacian_matches_oracle(irls, H, W, prec):
     """Sec. 3.3 Sylvester solve in the DCT eigenbasis.  fp32: float32 GEMMs, bound 2e-5 of the
     largest output.  bf16: operands rounded to bfloat16 (relative 2^-9) in each of the four
-    products, float32 accumulation; the error is a few 1e-3 in the l2 sense.  bf16x3: operands
+    products, float32 accumulation; the error is 2^-9 times the amplification tau / (l_i + m_j)
+    of the lowest frequencies, which grows with the side: about 2e-2 in the l2 sense at sides up to
+    1024 (bound 4e-2, one-sided form only).  bf16x3: operands
     split into two bfloat16 parts (split residual and dropped lo*lo term about 2^-17 relative per
     product), bound 1e-4 of the largest output."""
     rng = np.random.default_rng(H * 1000 + W)
@@ -136,7 +140,73 @@ def test_precond_laplacian_matches_oracle(irls, H, W, prec):
         assert rel2 <= 5e-5 and np.abs(Z - z_ref).max() <= 1e-4 * scale, rel2
     else:
         rel2 = np.linalg.norm(Z - z_ref) / (np.linalg.norm(z_ref) + 1e-30)
-        assert rel2 <= 1.5e-2 and np.abs(Z - z_ref).max() <= 3e-2 * scale, rel2
+        assert rel2 <= 4e-2 and np.abs(Z - z_ref).max() <= 6e-2 * scale, rel2
+
+
+def test_folded_and_direct_forms_agree(irls):
+    """The folded form (sums and differences of mirrored rows and columns, half-size products
+    with the even and odd halves of the DCT basis) and the direct form compute the same Sec. 3.3
+    solve; both within the split-precision bound of the oracle and of each other."""
+    H, W = 512, 768
+    R = np.random.default_rng(11).standard_normal((H, W)).astype(np.float32)
+    z_ref = O.precond_apply((R.astype(np.float64), np.zeros((H - 1, W)), np.zeros((H, W - 1))),
+                            np.zeros((H - 1, W)), np.zeros((H, W - 1)), 1e-2, O.dct_basis(H),
+                            O.dct_basis(W))[0]
+    scale = np.abs(z_ref).max()
+    with irls.Plan(H, W, precision="bf16x3") as plan:
+        assert plan.folded
+        Zf = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+        plan.set_opts(dct_form="direct")
+        assert not plan.folded
+        Zd = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+        plan.set_opts(dct_form="auto")
+        assert plan.folded
+    for Z in (Zf, Zd):
+        assert np.abs(Z - z_ref).max() <= 1e-4 * scale
+    assert np.abs(Zf - Zd).max() <= 2e-4 * scale
+    X = synthetic.config_small(4, H=256, W=512)["X"]
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=6, cg_tol=1e-6, cg_max=1000)
+    ref = O.irls_unwrap(X, None, **kw)
+    for form in ("folded", "direct"):
+        U, st = irls.unwrap(cuda(X), None, eps=1e-3, outer_iters=6, cg_tol=1e-6,
+                            precision="bf16x3", return_stats=True,
+                            plan=irls.Plan(256, 512, tau=1e-2, delta=1e-3, outer_iters=6,
+                                           cg_tol=1e-6, precision="bf16x3", dct_form=form))
+        assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], X,
+                             ref=ref)
+
+
+def test_folded_form_only_where_allowed(irls):
+    """IRLS_DCT_FOLDED needs split precision and both sides multiples of 256."""
+    for H, W, prec in ((384, 256, "bf16x3"), (256, 256, "bf16"), (256, 256, "fp32")):
+        with pytest.raises(irls.IrlsError) as e:
+            irls.Plan(H, W, precision=prec, dct_form="folded")
+        assert e.value.code == -8
+    with irls.Plan(384, 256, precision="bf16x3") as plan:
+        assert not plan.folded
+        with pytest.raises(irls.IrlsError):
+            plan.set_opts(dct_form="folded")
+    with irls.Plan(256, 256, precision="bf16x3") as plan:
+        assert plan.folded
+        plan.set_opts(precision="fp32")
+        assert not plan.folded
+
+
+def test_precond_repeatable_around_unwrap(irls):
+    """The folded form binds its device tables to the planes and flags of the call; a solve on the
+    same plan in between (other flags) must leave a repeated preconditioner call bit-identical."""
+    H, W = 256, 512
+    R = np.random.default_rng(3).standard_normal((H, W)).astype(np.float32)
+    X = synthetic.config_small(2, H=H, W=W)["X"]
+    with irls.Plan(H, W, precision="bf16x3", outer_iters=2, cg_tol=1e-5) as plan:
+        Z1 = irls.precond_laplacian(plan, cuda(R)).cpu().numpy()
+        plan.unwrap(cuda(X))
+        Z2 = irls.precond_laplacian(plan, cuda(R)).cpu().numpy()
+        plan.set_opts(tau=2e-2)
+        Z3 = irls.precond_laplacian(plan, cuda(R)).cpu().numpy()
+    assert np.array_equal(Z1, Z2)
+    # tau scales the solve linearly (Sec. 3.3)
+    assert np.allclose(Z3, 2.0 * Z1, rtol=1e-5, atol=1e-6 * np.abs(Z1).max())
 
 
 @pytest.mark.parametrize("H,W", [(37, 53), (1, 64), (64, 1), (256, 256), (129, 130)])
@@ -267,17 +337,22 @@ def test_unwrap_line_images(irls):
                              ref=ref)
 
 
-def test_unwrap_2048_first_outer_matches_oracle(irls):
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_unwrap_2048_first_outer_matches_oracle(irls, prec):
     """2048 x 2048 coherence-weighted workload: one outer step with 4 CG iterations compared
-    element by element (the oracle finishes that in seconds)."""
+    element by element (the oracle finishes that in seconds); bf16x3 runs the folded form."""
     d = synthetic.config_2048(seed=10)
     kw = dict(tau=1e-2, delta=1e-3, outer_iters=1, cg_tol=1e-6, cg_max=4)
     ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
     U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=1,
-                        cg_tol=1e-6, cg_max_iter=4, return_stats=True)
+                        cg_tol=1e-6, cg_max_iter=4, precision=prec, return_stats=True)
     assert st["cg_iters"] == [4]
+    # A truncated CG iterate is a fixed polynomial in the preconditioned operator, so the
+    # preconditioner's own relative error (split form: below 5e-5 in l2, tested above up to
+    # 2048) reaches U about once per iteration: 4 x 5e-5 x max|U|
+    atol = 1e-3 if prec == "fp32" else max(1e-3, 4 * 5e-5 * np.abs(ref["U"]).max())
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         ref=ref)
+                         atol=atol, ref=ref)
 
 
 def test_unwrap_2048_invariants(irls):
