@@ -191,6 +191,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // Shared-memory matrix descriptor of a K-major tile written by TMA with 128-byte swizzling:
 // rows of 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset), descriptor version 1,
 // layout code 2 (SWIZZLE_128B).  The leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr);
+
+// The same for a tile written with 64-byte swizzling (rows of 64 bytes = 32 bf16 of K, 8-row
+// atoms 512 bytes apart, layout code 4).
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+template <int KB>
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
+    static_assert(KB == 64 || KB == 32, "K per stage");
+    if constexpr (KB == 64) return desc_sw128(saddr);
+    else return desc_sw64(saddr);
+}
+
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -244,10 +265,176 @@ __device__ __forceinline__ void store_row32(void* hi, void* lo, size_t off, cons
     }
 }
 
+// rho = r_U^T z_U + r_V^T z_V and the CG ratio beta (Alg. 2), by the last block of the launch.
+__device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u) {
+    DevState* st = ep.st;
+    const double rho_new = rz_u + st->rz_v;
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        // rho <= 0 is a breakdown unless the residual is already at the accuracy rounding
+        // allows (relative 1e-3 and below)
+        if (st->rel > 1e-3 || !isfinite(rho_new)) st->status |= ST_BREAKDOWN;
+        st->done = 1;
+    } else if (st->p_fresh) {
+        st->rho = rho_new;
+        st->beta = 0.0;
+    } else {
+        const double num = ep.flexible ? rho_new - st->rz_old : rho_new;
+        st->beta = num / st->rho;
+        st->rho = rho_new;
+    }
+}
+
+// Epilogue of one 128 x BN output tile for the accumulator row this thread holds: tl is the
+// tensor-memory address of its lane at the accumulator's first column (a second accumulator, if
+// any, starts BN columns later), m its output row, n0 the tile's first column.  ZU_RHO forms
+// add their share of r^T z to `part`.
+template <int BN, int EPI>
+__device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m, int n0,
+                                         float& part) {
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tl + (uint32_t)(c * 32), r);
+        const int nb = n0 + c * 32;
+        if constexpr (EPI == UE_FOLD16) {
+            // acc1 holds the mirrored tile: its column BN-1-x pairs with acc0's column x
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)((BN / 32 - 1 - c) * 32), r1);
+            float pl[32], mi[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
+                pl[t] = a + b;
+                mi[t] = a - b;
+            }
+            store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
+            store_row32(ep.C2, ep.C2_lo, (size_t)m * ep.ldc + nb, mi);
+        } else if constexpr (EPI == UE_UNFOLD16) {
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+            float pl[32], mi[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[t]);
+                pl[t] = a + b;
+                mi[t] = a - b;
+            }
+            store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
+            store_row32(ep.C, ep.C_lo, (size_t)(ep.mrows - 1 - m) * ep.ldc + nb, mi);
+        } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+            float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
+            const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float4 w, wm;
+                float* wp = &w.x;
+                float* wmp = &wm.x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = 4 * q + u;            // column nb + t
+                    const int tm = 31 - (4 * q + u);    // mirrored column mb + 4q + u
+                    wp[u] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);
+                    wmp[u] = __uint_as_float(r[tm]) - __uint_as_float(r1[tm]);
+                }
+                reinterpret_cast<float4*>(out + nb)[q] = w;
+                reinterpret_cast<float4*>(out + mb)[q] = wm;
+                if constexpr (EPI == UE_UNFOLDZ_RHO) {
+                    const float* rr = ep.rU + (size_t)m * ep.ldc;
+                    const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
+                    const float4 xm = reinterpret_cast<const float4*>(rr + mb)[q];
+                    part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
+                    part += xm.x * wm.x + xm.y * wm.y + xm.z * wm.z + xm.w * wm.w;
+                }
+            }
+        } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+            float v[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+            if constexpr (EPI == UE_EIG16) {
+                const bool rowok = m < ep.vm;
+                const float lm = rowok ? ep.lam_m[m] : 0.f;
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int n = nb + t;
+                    const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
+                    v[t] = keep ? __fdividef(ep.scale * v[t], lm + __ldg(&ep.lam_n[n])) : 0.f;
+                }
+            }
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C) +
+                                                  (size_t)m * ep.ldc + nb);
+            if (ep.C_lo == nullptr) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 w;
+                    w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                    w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                    w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                    w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                    dst[q] = w;
+                }
+            } else {
+                uint4* dlo = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C_lo) +
+                                                      (size_t)m * ep.ldc + nb);
+                float lo[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const float h = __bfloat162float(__float2bfloat16_rn(v[t]));
+                    lo[t] = v[t] - h;
+                    v[t] = h;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 w, wl;
+                    w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                    w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                    w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                    w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                    wl.x = pack_bf16(lo[8 * q + 0], lo[8 * q + 1]);
+                    wl.y = pack_bf16(lo[8 * q + 2], lo[8 * q + 3]);
+                    wl.z = pack_bf16(lo[8 * q + 4], lo[8 * q + 5]);
+                    wl.w = pack_bf16(lo[8 * q + 6], lo[8 * q + 7]);
+                    dst[q] = w;
+                    dlo[q] = wl;
+                }
+            }
+        } else {
+            if (m < ep.vm) {
+                float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
+                const float* rr = ep.rU + (size_t)m * ep.ldc;
+                if (nb + 32 <= ep.vn) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 w = make_float4(__uint_as_float(r[4 * q]),
+                                               __uint_as_float(r[4 * q + 1]),
+                                               __uint_as_float(r[4 * q + 2]),
+                                               __uint_as_float(r[4 * q + 3]));
+                        reinterpret_cast<float4*>(out + nb)[q] = w;
+                        if constexpr (EPI == UE_ZU_RHO) {
+                            const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
+                            part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        if (nb + t < ep.vn) {
+                            const float z = __uint_as_float(r[t]);
+                            out[nb + t] = z;
+                            if constexpr (EPI == UE_ZU_RHO) part += rr[nb + t] * z;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int BN, int EPI, int SA, int SB, int DUAL = 0>
 __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtensorMap* tmA1,
                                           const CUtensorMap* tmB0, const CUtensorMap* tmB1,
-                                          int K, const UEpiArgs& ep, int m0, int n0,
+                                          int K, const UEpiArgs& ep_ref, int m0, int n0,
                                           unsigned nblk, unsigned bid,
                                           const CUtensorMap* tmA2 = nullptr,
                                           const CUtensorMap* tmA3 = nullptr,
@@ -257,6 +444,9 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
     // [BN, 2 BN); its K loop follows the first one through the same shared-memory ring
     using C = UCfg<BN, SA, SB>;
     constexpr uint32_t kCols = DUAL ? 2 * C::kTmemCols : C::kTmemCols;
+    // a register copy: the epilogue's stores could alias a table in global memory, which would
+    // force a reload of every argument after each store
+    const UEpiArgs ep = ep_ref;
     if (ep.skip_if_done && ep.st->done) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -352,147 +542,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
     }
     const int m = m0 + warp * 32 + lane;
     float part = 0.f;
-    if (good) {
-#pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-            const int nb = n0 + c * 32;
-            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-            if constexpr (EPI == UE_FOLD16) {
-                // acc1 holds the mirrored tile: its column BN-1-x pairs with acc0's column x
-                uint32_t r1[32];
-                tmem_ld32(tl + (uint32_t)BN + (uint32_t)((BN / 32 - 1 - c) * 32), r1);
-                float pl[32], mi[32];
-#pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
-                    pl[t] = a + b;
-                    mi[t] = a - b;
-                }
-                store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
-                store_row32(ep.C2, ep.C2_lo, (size_t)m * ep.ldc + nb, mi);
-            } else if constexpr (EPI == UE_UNFOLD16) {
-                uint32_t r1[32];
-                tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
-                float pl[32], mi[32];
-#pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[t]);
-                    pl[t] = a + b;
-                    mi[t] = a - b;
-                }
-                store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
-                store_row32(ep.C, ep.C_lo, (size_t)(ep.mrows - 1 - m) * ep.ldc + nb, mi);
-            } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
-                uint32_t r1[32];
-                tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
-                float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
-                const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float4 w, wm;
-                    float* wp = &w.x;
-                    float* wmp = &wm.x;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int t = 4 * q + u;            // column nb + t
-                        const int tm = 31 - (4 * q + u);    // mirrored column mb + 4q + u
-                        wp[u] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);
-                        wmp[u] = __uint_as_float(r[tm]) - __uint_as_float(r1[tm]);
-                    }
-                    reinterpret_cast<float4*>(out + nb)[q] = w;
-                    reinterpret_cast<float4*>(out + mb)[q] = wm;
-                    if constexpr (EPI == UE_UNFOLDZ_RHO) {
-                        const float* rr = ep.rU + (size_t)m * ep.ldc;
-                        const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
-                        const float4 xm = reinterpret_cast<const float4*>(rr + mb)[q];
-                        part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
-                        part += xm.x * wm.x + xm.y * wm.y + xm.z * wm.z + xm.w * wm.w;
-                    }
-                }
-            } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
-                float v[32];
-#pragma unroll
-                for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
-                if constexpr (EPI == UE_EIG16) {
-                    const bool rowok = m < ep.vm;
-                    const float lm = rowok ? ep.lam_m[m] : 0.f;
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const int n = nb + t;
-                        const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
-                        v[t] = keep ? ep.scale * v[t] / (lm + __ldg(&ep.lam_n[n])) : 0.f;
-                    }
-                }
-                uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C) +
-                                                      (size_t)m * ep.ldc + nb);
-                if (ep.C_lo == nullptr) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 w;
-                        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-                        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-                        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-                        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-                        dst[q] = w;
-                    }
-                } else {
-                    uint4* dlo = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(ep.C_lo) +
-                                                          (size_t)m * ep.ldc + nb);
-                    float lo[32];
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const float h = __bfloat162float(__float2bfloat16_rn(v[t]));
-                        lo[t] = v[t] - h;
-                        v[t] = h;
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 w, wl;
-                        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-                        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-                        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-                        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-                        wl.x = pack_bf16(lo[8 * q + 0], lo[8 * q + 1]);
-                        wl.y = pack_bf16(lo[8 * q + 2], lo[8 * q + 3]);
-                        wl.z = pack_bf16(lo[8 * q + 4], lo[8 * q + 5]);
-                        wl.w = pack_bf16(lo[8 * q + 6], lo[8 * q + 7]);
-                        dst[q] = w;
-                        dlo[q] = wl;
-                    }
-                }
-            } else {
-                if (m < ep.vm) {
-                    float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
-                    const float* rr = ep.rU + (size_t)m * ep.ldc;
-                    if (nb + 32 <= ep.vn) {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            float4 w = make_float4(__uint_as_float(r[4 * q]),
-                                                   __uint_as_float(r[4 * q + 1]),
-                                                   __uint_as_float(r[4 * q + 2]),
-                                                   __uint_as_float(r[4 * q + 3]));
-                            reinterpret_cast<float4*>(out + nb)[q] = w;
-                            if constexpr (EPI == UE_ZU_RHO) {
-                                const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
-                                part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < 32; ++t) {
-                            if (nb + t < ep.vn) {
-                                const float z = __uint_as_float(r[t]);
-                                out[nb + t] = z;
-                                if constexpr (EPI == UE_ZU_RHO) part += rr[nb + t] * z;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-    }
+    if (good) epi_tile<BN, EPI>(tmem + ((uint32_t)(warp * 32) << 16), ep, m, n0, part);
     tc_fence_before();
     __syncthreads();
     if (warp == 2) {
@@ -501,23 +551,8 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
     }
     if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
         double vv[1] = {(double)part}, tot[1];
-        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0) {
-            DevState* st = ep.st;
-            const double rho_new = tot[0] + st->rz_v;
-            if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-                // rho <= 0 is a breakdown unless the residual is already at the accuracy
-                // rounding allows (relative 1e-3 and below)
-                if (st->rel > 1e-3 || !isfinite(rho_new)) st->status |= ST_BREAKDOWN;
-                st->done = 1;
-            } else if (st->p_fresh) {
-                st->rho = rho_new;
-                st->beta = 0.0;
-            } else {
-                const double num = ep.flexible ? rho_new - st->rz_old : rho_new;
-                st->beta = num / st->rho;
-                st->rho = rho_new;
-            }
-        }
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0)
+            finish_rho(ep, tot[0]);
     }
 }
 
@@ -561,6 +596,227 @@ kb_umma_gemm(const GemmTile* __restrict__ tiles, int T) {
                                       (unsigned)((g.M / UBM) * g.gx), (unsigned)local, &g.a2,
                                       &g.a3, &g.b2, &g.b3,
                                       g.mirror_b1 ? g.nb_rows - n0 - 128 : n0);
+}
+
+// ------------------------------------------------------------------------------------------
+// persistent form
+// ------------------------------------------------------------------------------------------
+constexpr int kPThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has flagged an error.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int* err) {
+    const uint32_t a = smem_u32(bar);
+    if (mbar_try_wait(a, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(a, parity)) {
+        if (*(volatile int*)err) return false;
+        if (clock64() - t0 > kWaitBudget) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ const GemmTile& tile_problem(const GemmTile* tiles, int T, int t) {
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tiles[mid].blk0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return tiles[lo];
+}
+
+// Persistent, warp-specialised grouped GEMM (128 x 128 tiles, split operands: hi + lo parts of
+// A and B).  gridDim.x CTAs (at most one per SM) walk the output tiles of every problem of the
+// launch, CTA c taking tiles c, c + gridDim.x, ...:
+//   warp 0 lane 0   TMA producer: the k-blocks of the CTA's tiles through the shared-memory ring;
+//   warp 1 lane 0   MMA issuer into one of two tensor-memory accumulator buffers, alternating
+//                   per tile, so that one tile's epilogue overlaps the next tile's products;
+//                   warp 1 also owns the tensor-memory allocation;
+//   warps 2..5      epilogue: warp w drains accumulator lanes 32 (w mod 4) .. + 31 of a buffer,
+//                   then frees it for the MMA issuer.
+// DUAL problems accumulate a second operand set in the next BN columns of the same buffer.
+// Every wait is bounded and gives up once any role has flagged an error; before exit the
+// producer waits (bounded) for its copies in flight and the issuer for its MMAs.  The ZU_RHO
+// forms need a launch with a single problem: the r^T z reduction runs over the whole grid.
+// Shared-memory ring of the persistent kernel: KB columns of K per stage (64 with 128-byte
+// swizzling, 32 with 64-byte swizzling), hi and lo parts of a 128-row A and a 128-row B tile.
+template <int KB>
+struct PCfg {
+    static constexpr int kABytes = UBM * KB * 2;
+    static constexpr int kBBytes = 128 * KB * 2;
+    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr uint32_t kIdesc = UCfg<128, 2, 2>::kIdesc;
+};
+
+template <int EPI, int DUAL, int KB>
+__global__ void __launch_bounds__(kPThreads, 1)
+kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
+    using C = PCfg<KB>;
+    constexpr int BN = 128;
+    constexpr uint32_t kAcc = DUAL ? 2 * BN : BN;
+    constexpr uint32_t kCols = 2 * kAcc;
+    constexpr int S = C::kStages;
+    DevState* st0 = tiles[0].ep.st;
+    if (tiles[0].ep.skip_if_done && st0->done) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;     // [2] accumulator buffer ready for the epilogue
+    uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    __shared__ int s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    float part = 0.f;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool bad = false;
+            for (int t = blockIdx.x; t < total_tiles && !bad; t += gridDim.x) {
+                const GemmTile& g = tile_problem(tiles, T, t);
+                const int local = t - g.blk0;
+                const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * BN;
+                const int n0b1 = g.mirror_b1 ? g.nb_rows - n0 - BN : n0;
+                const int nkb = g.K / KB, nkt = DUAL ? 2 * nkb : nkb;
+                for (int kb = 0; kb < nkt; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (it >= S && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_err)) {
+                        bad = true;
+                        break;
+                    }
+                    const bool second = DUAL && kb >= nkb;
+                    const int kc = (second ? kb - nkb : kb) * KB;
+                    const int nb = second ? n0b1 : n0;
+                    uint8_t* sa = smem + s * C::kStageBytes;
+                    uint8_t* sb = sa + 2 * C::kABytes;
+                    mbar_expect_tx(&full[s], C::kStageBytes);
+                    tma_load_2d(sa, second ? &g.a2 : &g.a0, &full[s], kc, m0);
+                    tma_load_2d(sa + C::kABytes, second ? &g.a3 : &g.a1, &full[s], kc, m0);
+                    tma_load_2d(sb, second ? &g.b2 : &g.b0, &full[s], kc, nb);
+                    tma_load_2d(sb + C::kBBytes, second ? &g.b3 : &g.b1, &full[s], kc, nb);
+                }
+            }
+            // copies in flight land before the CTA may exit (immediate on the normal path)
+            for (int j = it - S < 0 ? 0 : it - S; j < it; ++j)
+                if (!mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) atomicExch(&s_err, 1);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, j = 0;
+            bool bad = false;
+            for (int t = blockIdx.x; t < total_tiles && !bad; t += gridDim.x, ++j) {
+                const GemmTile& g = tile_problem(tiles, T, t);
+                const int nkb = g.K / KB, nkt = DUAL ? 2 * nkb : nkb;
+                const int b = j & 1, u = j >> 1;
+                if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
+                    bad = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + (uint32_t)b * kAcc;
+                for (int kb = 0; kb < nkt; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (!mbar_wait_or_abort(&full[s], ph, &s_err)) {
+                        bad = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const bool second = DUAL && kb >= nkb;
+                    const int kk = second ? kb - nkb : kb;
+                    const uint32_t td = base + (second ? (uint32_t)BN : 0u);
+                    const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
+                    const uint32_t sb = sa + 2 * C::kABytes;
+                    const uint64_t da = desc_kmajor<KB>(sa), db = desc_kmajor<KB>(sb);
+                    const uint64_t dal = desc_kmajor<KB>(sa + C::kABytes);
+                    const uint64_t dbl = desc_kmajor<KB>(sb + C::kBBytes);
+#pragma unroll
+                    for (int q = 0; q < KB / 16; ++q) {   // K = 16 per MMA: +32 bytes
+                        umma_bf16(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
+                        umma_bf16(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                        umma_bf16(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (!bad) umma_commit(&tfull[b]);
+            }
+            if (it > 0) {
+                umma_commit(drain);
+                if (!mbar_wait(drain, 0)) atomicExch(&s_err, 1);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++j) {
+            const GemmTile& g = tile_problem(tiles, T, t);
+            const int local = t - g.blk0;
+            const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * BN;
+            const int b = j & 1, u = j >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const UEpiArgs ep = g.ep;   // register copy (see umma_body)
+            epi_tile<BN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
+                              m0 + q * 32 + lane, n0, part);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+    if (threadIdx.x == 0 && *(volatile int*)&s_err) {
+        atomicOr(&st0->status, ST_TIMEOUT);
+        st0->done = 1;
+    }
+    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
+        const UEpiArgs& ep = tiles[0].ep;
+        double vv[1] = {(double)part}, tot[1];
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
+            threadIdx.x == 0)
+            finish_rho(ep, tot[0]);
+    }
 }
 
 __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bfloat16* P16lo,
@@ -625,25 +881,39 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
 }
 
 // Folded residual: Re[i][j] = r[i][j] + r[i][W-1-j], Ro[i][j] = r[i][j] - r[i][W-1-j] (j < W/2),
-// each split into bf16 hi + lo.
+// each split into bf16 hi + lo.  Four columns per thread: the float4 at j and the float4 ending
+// at W-1-j (reversed); W is a multiple of 256 and the pitch a multiple of 4 floats.
 __global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W,
                          __nv_bfloat16* __restrict__ Re, __nv_bfloat16* __restrict__ Relo,
                          __nv_bfloat16* __restrict__ Ro, __nv_bfloat16* __restrict__ Rolo,
                          const DevState* st, int skip_if_done) {
     if (skip_if_done && st->done) return;
-    const int h = W / 2;
-    const size_t total = (size_t)H * h;
+    const int h = W / 2, h4 = h / 4;
+    const size_t total = (size_t)H * h4;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / h), j = (int)(t % h);
-        const float a = rU[(size_t)i * ld + j], b = rU[(size_t)i * ld + (W - 1 - j)];
-        const float e = a + b, o = a - b;
-        const __nv_bfloat16 eh = __float2bfloat16_rn(e), oh = __float2bfloat16_rn(o);
-        Re[t] = eh;
-        Ro[t] = oh;
+        const int i = (int)(t / h4), j = (int)(t % h4) * 4;
+        const float4 a = *reinterpret_cast<const float4*>(rU + (size_t)i * ld + j);
+        const float4 bm = *reinterpret_cast<const float4*>(rU + (size_t)i * ld + (W - 4 - j));
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {bm.w, bm.z, bm.y, bm.x};   // r[W-1-j-k], k = 0..3
+        float e[4], o[4], el[4], ol[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float se = av[k] + bv[k], so = av[k] - bv[k];
+            e[k] = __bfloat162float(__float2bfloat16_rn(se));
+            o[k] = __bfloat162float(__float2bfloat16_rn(so));
+            el[k] = se - e[k];
+            ol[k] = so - o[k];
+        }
+        const size_t off = (size_t)i * h + j;
+        *reinterpret_cast<uint2*>(Re + off) = make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
+        *reinterpret_cast<uint2*>(Ro + off) = make_uint2(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]));
         if (Relo) {
-            Relo[t] = __float2bfloat16_rn(e - __bfloat162float(eh));
-            Rolo[t] = __float2bfloat16_rn(o - __bfloat162float(oh));
+            *reinterpret_cast<uint2*>(Relo + off) =
+                make_uint2(pack_bf16(el[0], el[1]), pack_bf16(el[2], el[3]));
+            *reinterpret_cast<uint2*>(Rolo + off) =
+                make_uint2(pack_bf16(ol[0], ol[1]), pack_bf16(ol[2], ol[3]));
         }
     }
 }
@@ -673,15 +943,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // row-major bf16 matrix rows x cols (cols contiguous), box = 64 columns x box_rows rows
-bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+// kb = 64: box 64 columns with 128-byte swizzling; kb = 32: box 32 columns, 64-byte swizzling
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows, int kb = UBK) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)UBK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)kb, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
-                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -756,6 +1028,8 @@ struct FoldBufs {
     DevState* st = nullptr;
     double* partials = nullptr;
     float tau = 0.f;
+    int n_sm = 0;          // SMs of the device: persistent grid size
+    int persistent = 1;    // persistent GEMM kernels (else one CTA per tile)
 };
 
 size_t fold_bytes(int H, int W) {
@@ -833,6 +1107,16 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C22::kSmem);
         if (e != cudaSuccess) return e;
     }
+    for (auto fn : {kp_umma_gemm<UE_FOLD16, 1, 64>, kp_umma_gemm<UE_EIG16, 0, 64>,
+                    kp_umma_gemm<UE_UNFOLD16, 1, 64>, kp_umma_gemm<UE_UNFOLDZ, 1, 64>,
+                    kp_umma_gemm<UE_UNFOLDZ_RHO, 1, 64>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PCfg<64>::kSmem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&f.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
@@ -847,18 +1131,21 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     base.partials = partials;
     base.flexible = flexible;
     base.skip_if_done = skip;
+    // 64 columns of K per stage: measured faster than 32-column stages with 64-byte swizzling
+    // (twice the stages, but twice the TMA boxes and barrier round trips per multiply-add)
+    const int kb = UBK;
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a0, A[0], ar, ac, UBM);
-        ok &= make_map(&g.a1, A[1], ar, ac, UBM);
-        ok &= make_map(&g.b0, Bm[0], br, bc, 128);
-        ok &= make_map(&g.b1, Bm[1], br, bc, 128);
+        ok &= make_map(&g.a0, A[0], ar, ac, UBM, kb);
+        ok &= make_map(&g.a1, A[1], ar, ac, UBM, kb);
+        ok &= make_map(&g.b0, Bm[0], br, bc, 128, kb);
+        ok &= make_map(&g.b1, Bm[1], br, bc, 128, kb);
         g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
     };
     auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a2, A[0], ar, ac, UBM);
-        ok &= make_map(&g.a3, A[1], ar, ac, UBM);
-        ok &= make_map(&g.b2, Bm[0], br, bc, 128);
-        ok &= make_map(&g.b3, Bm[1], br, bc, 128);
+        ok &= make_map(&g.a2, A[0], ar, ac, UBM, kb);
+        ok &= make_map(&g.a3, A[1], ar, ac, UBM, kb);
+        ok &= make_map(&g.b2, Bm[0], br, bc, 128, kb);
+        ok &= make_map(&g.b3, Bm[1], br, bc, 128, kb);
     };
     for (auto& t : f.tab) t.clear();
     // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
@@ -933,6 +1220,22 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     return cudaSuccess;
 }
 
+template <int KB>
+cudaError_t fold_launch_persistent(const DctPlan& d, const FoldBufs& f, int reduce_rho,
+                                   cudaStream_t s) {
+    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
+    auto grid = [&](int k) { return std::min(d.fold_ctas[k], f.n_sm); };
+    const int sm = PCfg<KB>::kSmem;
+    kp_umma_gemm<UE_FOLD16, 1, KB><<<grid(0), kPThreads, sm, s>>>(tab(0), d.fold_count[0], d.fold_ctas[0]);
+    kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), d.fold_count[1], d.fold_ctas[1]);
+    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), d.fold_count[2], d.fold_ctas[2]);
+    if (reduce_rho)
+        kp_umma_gemm<UE_UNFOLDZ_RHO, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), d.fold_count[3], d.fold_ctas[3]);
+    else
+        kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), d.fold_count[3], d.fold_ctas[3]);
+    return cudaGetLastError();
+}
+
 cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                        int reduce_rho, int flexible, double* partials, int skip_if_done,
                        cudaStream_t s) {
@@ -945,12 +1248,15 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
     }
     using C22 = UCfg<128, 2, 2>;
     using B = __nv_bfloat16;
-    const size_t n = (size_t)d.H * (d.W / 2);
-    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    const size_t n = (size_t)d.H * (d.W / 8);
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
     k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, static_cast<B*>(d.Re), static_cast<B*>(d.Relo),
                                     static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
                                     skip_if_done);
     auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
+    if (f.persistent) {
+        return fold_launch_persistent<64>(d, f, reduce_rho, s);
+    }
     kb_umma_gemm<UE_FOLD16, 2, 2, 1><<<d.fold_ctas[0], kUThreads, C22::kSmem, s>>>(tab(0), d.fold_count[0]);
     kb_umma_gemm<UE_EIG16, 2, 2, 0><<<d.fold_ctas[1], kUThreads, C22::kSmem, s>>>(tab(1), d.fold_count[1]);
     kb_umma_gemm<UE_UNFOLD16, 2, 2, 1><<<d.fold_ctas[2], kUThreads, C22::kSmem, s>>>(tab(2), d.fold_count[2]);
