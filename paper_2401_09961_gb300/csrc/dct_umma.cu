@@ -819,6 +819,303 @@ kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// CTA-pair form: tcgen05.mma.cta_group::2 over two SMs of a TPC
+// ------------------------------------------------------------------------------------------
+// A pair of CTAs (a cluster of two) computes 256-row output tiles: each CTA stages its own 128
+// rows of A and its half of B's rows, the even CTA issues M = 256 MMAs that read both CTAs'
+// shared memory, and each CTA's tensor memory receives its own 128 accumulator rows.  Per SM
+// this halves the B bytes streamed per multiply-add against the one-SM form.
+constexpr int k2Threads = 192;
+
+template <int DUAL>
+struct Q2Cfg {
+    static constexpr int kBRows = DUAL ? 64 : 128;    // B rows per CTA (per operand set)
+    static constexpr int kMmaN = 2 * kBRows;           // N of one MMA: both CTAs' B rows
+    static constexpr int kABytes = UBM * UBK * 2;      // one bf16 part of this CTA's A rows
+    static constexpr int kBBytes = kBRows * UBK * 2;
+    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    // kind::f16, D f32, A and B bf16 K-major, N = kMmaN, M = 256
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                       ((uint32_t)(kMmaN >> 3) << 17) |
+                                       ((uint32_t)(256 >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA load into this CTA's shared memory that signals an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// arrive on the mbarrier at this offset in both CTAs once the issuer's MMAs so far complete
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+                 : "memory");
+}
+
+// Tensor memory of both CTAs of the pair, allocated and released collectively (one warp of each
+// CTA issues the instruction; both receive the same column address).
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// Output tile width of a pair-form problem: DUAL problems and mirrored-B problems pair two
+// 128-column halves (two operand sets, or a tile and its mirror); the others are 256 wide.
+__device__ __forceinline__ int pair_tile_n(const GemmTile& g, int dual) {
+    return (dual || g.mirror_b1) ? 128 : 256;
+}
+
+// Persistent CTA-pair grouped GEMM.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
+// p + gridDim.x / 2, ...; roles as in kp_umma_gemm, with the MMA issuer in the even CTA only:
+//   non-DUAL: one M = 256, N = 256 accumulator; CTA r stages B rows n0 + 128 r, or for a
+//             mirrored problem rows n0 (even CTA) and nb_rows - n0 - 128 (odd CTA), so that
+//             accumulator columns [128, 256) hold the mirrored tile;
+//   DUAL:     two M = 256, N = 128 accumulators (operand sets), 64 B rows per CTA each.
+// The even CTA's full barriers count both CTAs' bytes; the issuer's commits arrive in both CTAs;
+// both CTAs' epilogue warps release an accumulator buffer on the even CTA's barrier.  All waits
+// are bounded; the two CTAs take every branch that has a cluster barrier together.
+template <int EPI, int DUAL, int EBN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
+k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
+    using C = Q2Cfg<DUAL>;
+    constexpr int S = C::kStages;
+    constexpr uint32_t kAcc = 256;           // tensor-memory columns per accumulator buffer
+    constexpr uint32_t kCols = 2 * kAcc;
+    DevState* st0 = tiles[0].ep.st;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;     // [2] accumulator buffer ready (both CTAs)
+    uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained (even CTA: 8 warps)
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    __shared__ int s_err;
+    __shared__ int s_skip;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        s_skip = (tiles[0].ep.skip_if_done && st0->done) ? 1 : 0;
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    cluster_sync_all();
+    {
+        // both CTAs skip, or neither: a stopped CG run read by only one of them must not split
+        // the pair across the cluster barriers below
+        int peer;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];"
+                     : "=r"(peer)
+                     : "r"(mapa_shared(smem_u32(&s_skip), rank ^ 1u))
+                     : "memory");
+        if (s_skip | peer) {
+            cluster_sync_all();
+            return;
+        }
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    float part = 0.f;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t full0 = mapa_shared(smem_u32(full), 0);
+            int it = 0;
+            bool bad = false;
+            for (int t = pair; t < total_tiles && !bad; t += npairs) {
+                const GemmTile& g = tile_problem(tiles, T, t);
+                const int local = t - g.blk0;
+                const int tn = pair_tile_n(g, DUAL);
+                const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
+                const int n0 = (local % g.gx) * tn;
+                const int nb = DUAL ? n0 + C::kBRows * (int)rank
+                                    : (rank == 0 ? n0
+                                                 : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + 128));
+                const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
+                for (int kb = 0; kb < nkt; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (it >= S && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_err)) {
+                        bad = true;
+                        break;
+                    }
+                    const bool second = DUAL && kb >= nkb;
+                    const int kc = (second ? kb - nkb : kb) * UBK;
+                    uint8_t* sa = smem + s * C::kStageBytes;
+                    uint8_t* sb = sa + 2 * C::kABytes;
+                    if (rank == 0) mbar_expect_tx(&full[s], 2 * C::kStageBytes);
+                    const uint32_t fb = full0 + 8u * (uint32_t)s;
+                    tma_load_2d_pair(sa, second ? &g.a2 : &g.a0, fb, kc, m0);
+                    tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
+                    tma_load_2d_pair(sb, second ? &g.b2 : &g.b0, fb, kc, nb);
+                    tma_load_2d_pair(sb + C::kBBytes, second ? &g.b3 : &g.b1, fb, kc, nb);
+                }
+            }
+            if (rank == 0) {
+                // both CTAs' copies of the last stages have landed (immediate on the normal path)
+                for (int j = it - S < 0 ? 0 : it - S; j < it; ++j)
+                    if (!mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) atomicExch(&s_err, 1);
+            } else if (bad) {
+                // the odd CTA's copies signal the even CTA's barriers: give them time to land
+                const long long t0 = clock64();
+                while (clock64() - t0 < (1LL << 22)) {
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (rank == 0 && lane == 0) {
+            int it = 0, j = 0;
+            bool bad = false;
+            for (int t = pair; t < total_tiles && !bad; t += npairs, ++j) {
+                const GemmTile& g = tile_problem(tiles, T, t);
+                const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
+                const int b = j & 1, u = j >> 1;
+                if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
+                    bad = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + (uint32_t)b * kAcc;
+                for (int kb = 0; kb < nkt; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (!mbar_wait_or_abort(&full[s], ph, &s_err)) {
+                        bad = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const bool second = DUAL && kb >= nkb;
+                    const int kk = second ? kb - nkb : kb;
+                    const uint32_t td = base + (second ? 128u : 0u);
+                    const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
+                    const uint32_t sb = sa + 2 * C::kABytes;
+                    const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
+                    const uint64_t dal = desc_sw128(sa + C::kABytes);
+                    const uint64_t dbl = desc_sw128(sb + C::kBBytes);
+#pragma unroll
+                    for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
+                        umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
+                        umma_bf16_pair(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                        umma_bf16_pair(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                    }
+                    umma_commit_pair(&empty[s]);
+                }
+                if (!bad) umma_commit_pair(&tfull[b]);
+            }
+            umma_commit_pair(drain);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
+        int j = 0;
+        for (int t = pair; t < total_tiles; t += npairs, ++j) {
+            const GemmTile& g = tile_problem(tiles, T, t);
+            const int local = t - g.blk0;
+            const int tn = pair_tile_n(g, DUAL);
+            const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
+            const int n0 = (local % g.gx) * tn;
+            const int b = j & 1, u = j >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const UEpiArgs ep = g.ep;   // register copy (see umma_body)
+            epi_tile<EBN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
+                               m0 + q * 32 + lane, n0, part);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(te0 + 8u * (uint32_t)b);
+        }
+    }
+
+    // every MMA of the pair has completed before the tensor memory is released
+    if (warp == 1 && lane == 0 && !mbar_wait(drain, 0)) atomicExch(&s_err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, kCols);
+    }
+    if (threadIdx.x == 0 && *(volatile int*)&s_err) {
+        atomicOr(&st0->status, ST_TIMEOUT);
+        st0->done = 1;
+    }
+    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
+        const UEpiArgs& ep = tiles[0].ep;
+        double vv[1] = {(double)part}, tot[1];
+        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
+            threadIdx.x == 0)
+            finish_rho(ep, tot[0]);
+    }
+    cluster_sync_all();
+}
+
 __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bfloat16* P16lo,
                                 __nv_bfloat16* PT16lo, int N, int Np) {
     const size_t total = (size_t)Np * Np;
@@ -1010,6 +1307,10 @@ bool foldable(int H, int W, int split) { return split && H % 256 == 0 && W % 256
 
 namespace {
 
+// Persistent GEMM form of the folded stages: one CTA per SM (sides multiples of 256), or CTA
+// pairs with 256-row tiles (sides multiples of 512).
+constexpr int kFoldOneSm = 1, kFoldPair = 2;
+
 // Host-side record of the folded form's buffers and of the arguments its device tables were
 // last built for (the tables bake in the planes, the CG state and the epilogue flags).
 struct FoldBufs {
@@ -1029,7 +1330,8 @@ struct FoldBufs {
     double* partials = nullptr;
     float tau = 0.f;
     int n_sm = 0;          // SMs of the device: persistent grid size
-    int persistent = 1;    // persistent GEMM kernels (else one CTA per tile)
+    int mode = 1;          // kFoldOneSm or kFoldPair
+    int tiles[4] = {0, 0, 0, 0};   // output tiles per stage in that form
 };
 
 size_t fold_bytes(int H, int W) {
@@ -1091,26 +1393,22 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
                                       f.lamPM, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // problems per stage and their CTA counts depend on the shape only
-    const int tiles_g_hN = (int)((hM / UBM) * (hN / 128));
-    const int cnt[4] = {2, 4, 2, 1};
-    const int per[4] = {tiles_g_hN, tiles_g_hN, (int)((hN / UBM) * (hM / 128)),
-                        (int)((H / UBM) * (hM / 128))};
-    for (int k = 0; k < 4; ++k) {
-        d.fold_count[k] = cnt[k];
-        d.fold_ctas[k] = cnt[k] * per[k];
-    }
-    using C22 = UCfg<128, 2, 2>;
-    for (auto fn : {kb_umma_gemm<UE_FOLD16, 2, 2, 1>, kb_umma_gemm<UE_EIG16, 2, 2, 0>,
-                    kb_umma_gemm<UE_UNFOLD16, 2, 2, 1>, kb_umma_gemm<UE_UNFOLDZ, 2, 2, 1>,
-                    kb_umma_gemm<UE_UNFOLDZ_RHO, 2, 2, 1>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C22::kSmem);
-        if (e != cudaSuccess) return e;
-    }
+    const int cnt[4] = {2, 4, 2, 1};   // problems per stage
+    for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
+    f.mode = (H % 512 == 0 && W % 512 == 0) ? kFoldPair : kFoldOneSm;
     for (auto fn : {kp_umma_gemm<UE_FOLD16, 1, 64>, kp_umma_gemm<UE_EIG16, 0, 64>,
                     kp_umma_gemm<UE_UNFOLD16, 1, 64>, kp_umma_gemm<UE_UNFOLDZ, 1, 64>,
                     kp_umma_gemm<UE_UNFOLDZ_RHO, 1, 64>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PCfg<64>::kSmem);
+        if (e != cudaSuccess) return e;
+    }
+    for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
+        if (e != cudaSuccess) return e;
+    }
+    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 128>, k2_umma_gemm<UE_UNFOLDZ, 1, 128>,
+                    k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 128>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<1>::kSmem);
         if (e != cudaSuccess) return e;
     }
     int dev = 0;
@@ -1134,18 +1432,20 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     // 64 columns of K per stage: measured faster than 32-column stages with 64-byte swizzling
     // (twice the stages, but twice the TMA boxes and barrier round trips per multiply-add)
     const int kb = UBK;
+    // B box height: 128 rows, except the two-accumulator stages of the pair form (64 rows per CTA)
+    int bbox = 128;
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a0, A[0], ar, ac, UBM, kb);
         ok &= make_map(&g.a1, A[1], ar, ac, UBM, kb);
-        ok &= make_map(&g.b0, Bm[0], br, bc, 128, kb);
-        ok &= make_map(&g.b1, Bm[1], br, bc, 128, kb);
+        ok &= make_map(&g.b0, Bm[0], br, bc, bbox, kb);
+        ok &= make_map(&g.b1, Bm[1], br, bc, bbox, kb);
         g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
     };
     auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a2, A[0], ar, ac, UBM, kb);
         ok &= make_map(&g.a3, A[1], ar, ac, UBM, kb);
-        ok &= make_map(&g.b2, Bm[0], br, bc, 128, kb);
-        ok &= make_map(&g.b3, Bm[1], br, bc, 128, kb);
+        ok &= make_map(&g.b2, Bm[0], br, bc, bbox, kb);
+        ok &= make_map(&g.b3, Bm[1], br, bc, bbox, kb);
     };
     for (auto& t : f.tab) t.clear();
     // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
@@ -1178,6 +1478,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             f.tab[1].push_back(g);
         }
+    if (f.mode == kFoldPair) bbox = 64;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
     // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O
     for (int x = 0; x < 2; ++x) {
@@ -1201,14 +1502,19 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     }
     if (!ok) return cudaErrorNotSupported;
     for (int k = 0; k < 4; ++k) {
-        int cta = 0;
+        // output tiles: 128 x 128 (one-SM form); 256 rows x 128 columns for two-accumulator or
+        // mirrored stages and 256 x 256 otherwise (pair form)
+        const int tm = f.mode == kFoldPair ? 256 : UBM;
+        int tiles = 0;
         for (auto& g : f.tab[k]) {
-            g.gx = g.N / 128;
-            g.blk0 = cta;
-            cta += (g.M / UBM) * g.gx;
+            const int tn = (f.mode == kFoldPair && k == 1) ? 256 : 128;
+            if (g.M % tm != 0 || g.N % tn != 0) return cudaErrorInvalidValue;
+            g.gx = g.N / tn;
+            g.blk0 = tiles;
+            tiles += (g.M / tm) * g.gx;
         }
-        if ((int)f.tab[k].size() != d.fold_count[k] || cta != d.fold_ctas[k])
-            return cudaErrorInvalidValue;
+        if ((int)f.tab[k].size() != d.fold_count[k]) return cudaErrorInvalidValue;
+        f.tiles[k] = tiles;
         cudaError_t e = cudaMemcpyAsync(d.fold_tiles[k], f.tab[k].data(),
                                         f.tab[k].size() * sizeof(GemmTile),
                                         cudaMemcpyHostToDevice, s);
@@ -1224,15 +1530,33 @@ template <int KB>
 cudaError_t fold_launch_persistent(const DctPlan& d, const FoldBufs& f, int reduce_rho,
                                    cudaStream_t s) {
     auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
-    auto grid = [&](int k) { return std::min(d.fold_ctas[k], f.n_sm); };
+    auto grid = [&](int k) { return std::min(f.tiles[k], f.n_sm); };
     const int sm = PCfg<KB>::kSmem;
-    kp_umma_gemm<UE_FOLD16, 1, KB><<<grid(0), kPThreads, sm, s>>>(tab(0), d.fold_count[0], d.fold_ctas[0]);
-    kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), d.fold_count[1], d.fold_ctas[1]);
-    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), d.fold_count[2], d.fold_ctas[2]);
+    const int* c = d.fold_count;
+    const int* t = f.tiles;
+    kp_umma_gemm<UE_FOLD16, 1, KB><<<grid(0), kPThreads, sm, s>>>(tab(0), c[0], t[0]);
+    kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
+    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), c[2], t[2]);
     if (reduce_rho)
-        kp_umma_gemm<UE_UNFOLDZ_RHO, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), d.fold_count[3], d.fold_ctas[3]);
+        kp_umma_gemm<UE_UNFOLDZ_RHO, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
     else
-        kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), d.fold_count[3], d.fold_ctas[3]);
+        kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
+    return cudaGetLastError();
+}
+
+cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho, cudaStream_t s) {
+    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
+    auto grid = [&](int k) { return 2 * std::min(f.tiles[k], f.n_sm / 2); };
+    const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1>::kSmem;
+    const int* c = d.fold_count;
+    const int* t = f.tiles;
+    k2_umma_gemm<UE_FOLD16, 0, 128><<<grid(0), k2Threads, s0, s>>>(tab(0), c[0], t[0]);
+    k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
+    k2_umma_gemm<UE_UNFOLD16, 1, 128><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
+    if (reduce_rho)
+        k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 128><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+    else
+        k2_umma_gemm<UE_UNFOLDZ, 1, 128><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
 }
 
@@ -1246,25 +1570,14 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
         cudaError_t e = fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, s);
         if (e != cudaSuccess) return e;
     }
-    using C22 = UCfg<128, 2, 2>;
     using B = __nv_bfloat16;
     const size_t n = (size_t)d.H * (d.W / 8);
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
     k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, static_cast<B*>(d.Re), static_cast<B*>(d.Relo),
                                     static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
                                     skip_if_done);
-    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
-    if (f.persistent) {
-        return fold_launch_persistent<64>(d, f, reduce_rho, s);
-    }
-    kb_umma_gemm<UE_FOLD16, 2, 2, 1><<<d.fold_ctas[0], kUThreads, C22::kSmem, s>>>(tab(0), d.fold_count[0]);
-    kb_umma_gemm<UE_EIG16, 2, 2, 0><<<d.fold_ctas[1], kUThreads, C22::kSmem, s>>>(tab(1), d.fold_count[1]);
-    kb_umma_gemm<UE_UNFOLD16, 2, 2, 1><<<d.fold_ctas[2], kUThreads, C22::kSmem, s>>>(tab(2), d.fold_count[2]);
-    if (reduce_rho)
-        kb_umma_gemm<UE_UNFOLDZ_RHO, 2, 2, 1><<<d.fold_ctas[3], kUThreads, C22::kSmem, s>>>(tab(3), d.fold_count[3]);
-    else
-        kb_umma_gemm<UE_UNFOLDZ, 2, 2, 1><<<d.fold_ctas[3], kUThreads, C22::kSmem, s>>>(tab(3), d.fold_count[3]);
-    return cudaGetLastError();
+    if (f.mode == kFoldPair) return fold_launch_pair(d, f, reduce_rho, s);
+    return fold_launch_persistent<64>(d, f, reduce_rho, s);
 }
 
 }  // namespace

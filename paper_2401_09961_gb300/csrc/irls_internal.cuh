@@ -102,7 +102,6 @@ struct DctPlan {
     int fold_ready;            // folded form built (memory, bases)
     void* fold_tiles[4];       // device tables of grouped-GEMM problems per stage
     int fold_count[4];         // problems per stage (2, 4, 2, 1)
-    int fold_ctas[4];
     void *Re, *Relo, *Ro, *Rolo;   // folded residual, H x W/2 each
     void* fold_host;               // host-side record of the folded form (owned)
     alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
