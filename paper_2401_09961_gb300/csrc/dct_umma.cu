@@ -290,9 +290,9 @@ __device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u) {
 // add their share of r^T z to `part`.
 template <int BN, int EPI>
 __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m, int n0,
-                                         float& part) {
+                                         float& part, int c_begin = 0, int c_end = BN / 32) {
 #pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
+    for (int c = c_begin; c < c_end; ++c) {
         uint32_t r[32];
         tmem_ld32(tl + (uint32_t)(c * 32), r);
         const int nb = n0 + c * 32;
@@ -427,6 +427,145 @@ __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m,
                     }
                 }
             }
+        }
+    }
+}
+
+// Per-warp shared-memory block for the coalesced epilogue: 32 rows x 32 columns (padded).
+struct WarpScratch {
+    float v[32][33];
+};
+
+// Each lane holds one row of a 32 x 32 block (32 consecutive columns); after this call row r is
+// readable as s.v[r][column] by any lane of the warp.
+__device__ __forceinline__ void scr_put(WarpScratch& s, const float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) s.v[lane][t] = v[t];
+    __syncwarp();
+}
+
+// The block in `s` as bf16 (hi) and, with a lo plane, bf16(x - hi): two rows per instruction,
+// each lane one bf16 pair, row r of the block at element offset row_off(r) + col0.
+template <typename RowOff>
+__device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void* lo, int col0,
+                                            RowOff row_off) {
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane >> 4, col = 2 * (lane & 15);
+#pragma unroll 4
+    for (int rr = 0; rr < 32; rr += 2) {
+        const int row = rr + rsub;
+        const float x0 = s.v[row][col], x1 = s.v[row][col + 1];
+        const size_t off = row_off(row) + col0 + col;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(hi) + off) = h;
+        if (lo) {
+            const float2 hf = __bfloat1622float2(h);
+            *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(lo) + off) =
+                __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+        }
+    }
+}
+
+// The block in `s` as float32 rows at out + row_off(r) + col0 (four rows per instruction, one
+// float4 per lane); with rU, adds rU . z over the block to `part`.
+template <typename RowOff>
+__device__ __forceinline__ void scr_store32(const WarpScratch& s, float* out, const float* rU,
+                                            int col0, RowOff row_off, float& part) {
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane >> 3, col = 4 * (lane & 7);
+#pragma unroll 2
+    for (int rr = 0; rr < 32; rr += 4) {
+        const int row = rr + rsub;
+        const float4 z = make_float4(s.v[row][col], s.v[row][col + 1], s.v[row][col + 2],
+                                     s.v[row][col + 3]);
+        const size_t off = row_off(row) + col0 + col;
+        *reinterpret_cast<float4*>(out + off) = z;
+        if (rU) {
+            const float4 x = *reinterpret_cast<const float4*>(rU + off);
+            part += x.x * z.x + x.y * z.y + x.z * z.z + x.w * z.w;
+        }
+    }
+}
+
+// Epilogue of the persistent kernels: as epi_tile, for the warp's 32 accumulator rows starting
+// at output row m0w (this lane's row is m0w + lane), with coalesced stores through `s`.
+template <int BN, int EPI>
+__device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int m0w, int n0,
+                                           float& part, int c_begin, int c_end, WarpScratch& s) {
+    const int lane = threadIdx.x & 31;
+    const int m = m0w + lane;
+    const size_t ldc = (size_t)ep.ldc;
+    auto rows = [&](int r) { return (size_t)(m0w + r) * ldc; };
+#pragma unroll 1
+    for (int c = c_begin; c < c_end; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tl + (uint32_t)(c * 32), r);
+        const int nb = n0 + c * 32;
+        if constexpr (EPI == UE_FOLD16) {
+            // acc1 holds the mirrored tile: its column BN-1-x pairs with acc0's column x
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)((BN / 32 - 1 - c) * 32), r1);
+            float pl[32], mi[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
+                pl[t] = a + b;
+                mi[t] = a - b;
+            }
+            scr_put(s, pl);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+            scr_put(s, mi);
+            scr_store16(s, ep.C2, ep.C2_lo, nb, rows);
+        } else if constexpr (EPI == UE_UNFOLD16) {
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+            float pl[32], mi[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[t]);
+                pl[t] = a + b;
+                mi[t] = a - b;
+            }
+            scr_put(s, pl);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+            scr_put(s, mi);
+            const int mr = ep.mrows - 1 - m0w;
+            scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; });
+        } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
+            uint32_t r1[32];
+            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
+            const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
+            float pl[32], mi[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                pl[t] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);                // nb + t
+                mi[t] = __uint_as_float(r[31 - t]) - __uint_as_float(r1[31 - t]);     // mb + t
+            }
+            const float* rr = EPI == UE_UNFOLDZ_RHO ? ep.rU : nullptr;
+            scr_put(s, pl);
+            scr_store32(s, static_cast<float*>(ep.C), rr, nb, rows, part);
+            scr_put(s, mi);
+            scr_store32(s, static_cast<float*>(ep.C), rr, mb, rows, part);
+        } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+            float v[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+            if constexpr (EPI == UE_EIG16) {
+                const bool rowok = m < ep.vm;
+                const float lm = rowok ? ep.lam_m[m] : 0.f;
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int n = nb + t;
+                    const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
+                    v[t] = keep ? __fdividef(ep.scale * v[t], lm + __ldg(&ep.lam_n[n])) : 0.f;
+                }
+            }
+            scr_put(s, v);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+        } else {
+            static_assert(EPI == UE_STORE16, "persistent kernels: folded and eigenvalue forms");
         }
     }
 }
@@ -567,7 +706,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CU
 
 // One problem of a grouped GEMM launch: its TMA descriptors (in global memory), shape,
 // epilogue arguments and the index of its first CTA in the launch.
-struct alignas(64) GemmTile {
+struct GemmTile {
     CUtensorMap a0, a1, b0, b1;
     CUtensorMap a2, a3, b2, b3;   // second operand set (dual-accumulator stages)
     UEpiArgs ep;
@@ -651,8 +790,9 @@ struct PCfg {
     static constexpr int kABytes = UBM * KB * 2;
     static constexpr int kBBytes = 128 * KB * 2;
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr int kStages = (192 * 1024) / kStageBytes > 8 ? 8 : (192 * 1024) / kStageBytes;
+    // ring, 1024-byte alignment slack, barriers (256 bytes), four epilogue warps' scratch
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + 4 * (int)sizeof(WarpScratch);
     static constexpr uint32_t kIdesc = UCfg<128, 2, 2>::kIdesc;
 };
 
@@ -675,6 +815,7 @@ kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
     __shared__ int s_err;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -792,8 +933,8 @@ kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             if (!ok) break;
             tc_fence_after();
             const UEpiArgs ep = g.ep;   // register copy (see umma_body)
-            epi_tile<BN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
-                              m0 + q * 32 + lane, n0, part);
+            epi_tile_t<BN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
+                                m0 + q * 32, n0, part, 0, BN / 32, scratch[warp - 2]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
@@ -826,20 +967,28 @@ kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
 // rows of A and its half of B's rows, the even CTA issues M = 256 MMAs that read both CTAs'
 // shared memory, and each CTA's tensor memory receives its own 128 accumulator rows.  Per SM
 // this halves the B bytes streamed per multiply-add against the one-SM form.
-constexpr int k2Threads = 192;
+constexpr int k2EpiWarps = 8;
+constexpr int k2Threads = 64 + 32 * k2EpiWarps;
 
+// Every MMA is M = 256 (two CTAs), N = 256: each CTA stages 128 rows of A and 128 rows of B.
+// Measured on this part, N = 128 MMAs keep the tensor pipe busy at most ~77 % of the time and
+// N = 256 ones ~99 %, so two-operand-set (DUAL) problems use two N = 256 accumulators (all 512
+// tensor-memory columns, one buffer) instead of two N = 128 ones (double-buffered).
 template <int DUAL>
 struct Q2Cfg {
-    static constexpr int kBRows = DUAL ? 64 : 128;    // B rows per CTA (per operand set)
-    static constexpr int kMmaN = 2 * kBRows;           // N of one MMA: both CTAs' B rows
+    static constexpr int kBRows = 128;                 // B rows per CTA (per operand set)
     static constexpr int kABytes = UBM * UBK * 2;      // one bf16 part of this CTA's A rows
     static constexpr int kBBytes = kBRows * UBK * 2;
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
-    // kind::f16, D f32, A and B bf16 K-major, N = kMmaN, M = 256
+    static constexpr int kStages = (192 * 1024) / kStageBytes > 8 ? 8 : (192 * 1024) / kStageBytes;
+    // ring, 1024-byte alignment slack, barriers (256 bytes), the epilogue warps' scratch
+    static constexpr int kSmem =
+        kStages * kStageBytes + 1024 + 256 + k2EpiWarps * (int)sizeof(WarpScratch);
+    static constexpr uint32_t kAcc = DUAL ? 512 : 256;   // tensor-memory columns per buffer
+    static constexpr int kBufs = DUAL ? 1 : 2;
+    // kind::f16, D f32, A and B bf16 K-major, N = 256, M = 256
     static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                       ((uint32_t)(kMmaN >> 3) << 17) |
+                                       ((uint32_t)(256 >> 3) << 17) |
                                        ((uint32_t)(256 >> 4) << 24);
 };
 
@@ -907,18 +1056,17 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
 
-// Output tile width of a pair-form problem: DUAL problems and mirrored-B problems pair two
-// 128-column halves (two operand sets, or a tile and its mirror); the others are 256 wide.
-__device__ __forceinline__ int pair_tile_n(const GemmTile& g, int dual) {
-    return (dual || g.mirror_b1) ? 128 : 256;
-}
+// Output tile width of a pair-form problem: a mirrored-B problem pairs a 128-column tile with
+// its mirror in one N = 256 accumulator; the others are 256 wide.
+__device__ __forceinline__ int pair_tile_n(const GemmTile& g) { return g.mirror_b1 ? 128 : 256; }
 
 // Persistent CTA-pair grouped GEMM.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
-// p + gridDim.x / 2, ...; roles as in kp_umma_gemm, with the MMA issuer in the even CTA only:
-//   non-DUAL: one M = 256, N = 256 accumulator; CTA r stages B rows n0 + 128 r, or for a
-//             mirrored problem rows n0 (even CTA) and nb_rows - n0 - 128 (odd CTA), so that
-//             accumulator columns [128, 256) hold the mirrored tile;
-//   DUAL:     two M = 256, N = 128 accumulators (operand sets), 64 B rows per CTA each.
+// p + gridDim.x / 2, ...; roles as in kp_umma_gemm (eight epilogue warps, two per accumulator
+// lane quarter, splitting the columns), with the MMA issuer in the even CTA only:
+//   non-DUAL: one M = 256, N = 256 accumulator, two buffers; CTA r stages B rows n0 + 128 r, or
+//             for a mirrored problem rows n0 (even CTA) and nb_rows - n0 - 128 (odd CTA), so
+//             that accumulator columns [128, 256) hold the mirrored tile;
+//   DUAL:     two M = 256, N = 256 accumulators (operand sets) in one 512-column buffer.
 // The even CTA's full barriers count both CTAs' bytes; the issuer's commits arrive in both CTAs;
 // both CTAs' epilogue warps release an accumulator buffer on the even CTA's barrier.  All waits
 // are bounded; the two CTAs take every branch that has a cluster barrier together.
@@ -927,8 +1075,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
 k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     using C = Q2Cfg<DUAL>;
     constexpr int S = C::kStages;
-    constexpr uint32_t kAcc = 256;           // tensor-memory columns per accumulator buffer
-    constexpr uint32_t kCols = 2 * kAcc;
+    constexpr uint32_t kAcc = C::kAcc;
+    constexpr int NB = C::kBufs;
+    constexpr uint32_t kCols = 512;
     DevState* st0 = tiles[0].ep.st;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -936,9 +1085,11 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;     // [2] accumulator buffer ready (both CTAs)
-    uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained (even CTA: 8 warps)
+    uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained (even CTA: all epilogue
+                                     //     warps of both CTAs)
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
     __shared__ int s_err;
     __shared__ int s_skip;
 
@@ -953,7 +1104,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 8);
+            mbar_init(&tempty[b], 2 * k2EpiWarps);
         }
         mbar_init(drain, 1);
         fence_mbar_init();
@@ -988,12 +1139,10 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             for (int t = pair; t < total_tiles && !bad; t += npairs) {
                 const GemmTile& g = tile_problem(tiles, T, t);
                 const int local = t - g.blk0;
-                const int tn = pair_tile_n(g, DUAL);
+                const int tn = pair_tile_n(g);
                 const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
                 const int n0 = (local % g.gx) * tn;
-                const int nb = DUAL ? n0 + C::kBRows * (int)rank
-                                    : (rank == 0 ? n0
-                                                 : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + 128));
+                const int nb = rank == 0 ? n0 : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + 128);
                 const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
                 for (int kb = 0; kb < nkt; ++kb, ++it) {
                     const int s = it % S;
@@ -1033,7 +1182,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             for (int t = pair; t < total_tiles && !bad; t += npairs, ++j) {
                 const GemmTile& g = tile_problem(tiles, T, t);
                 const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
-                const int b = j & 1, u = j >> 1;
+                const int b = j % NB, u = j / NB;
                 if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
                     bad = true;
                     break;
@@ -1050,7 +1199,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
                     tc_fence_after();
                     const bool second = DUAL && kb >= nkb;
                     const int kk = second ? kb - nkb : kb;
-                    const uint32_t td = base + (second ? 128u : 0u);
+                    const uint32_t td = base + (second ? 256u : 0u);
                     const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
                     const uint32_t sb = sa + 2 * C::kABytes;
                     const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
@@ -1070,24 +1219,26 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         }
         __syncwarp();
     } else {
-        const int q = warp & 3;
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        constexpr int kChunks = EBN / 32;
+        const int c_begin = half * (kChunks / 2), c_end = c_begin + kChunks / 2;
         const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
         int j = 0;
         for (int t = pair; t < total_tiles; t += npairs, ++j) {
             const GemmTile& g = tile_problem(tiles, T, t);
             const int local = t - g.blk0;
-            const int tn = pair_tile_n(g, DUAL);
+            const int tn = pair_tile_n(g);
             const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
             const int n0 = (local % g.gx) * tn;
-            const int b = j & 1, u = j >> 1;
+            const int b = j % NB, u = j / NB;
             int ok = 1;
             if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
             const UEpiArgs ep = g.ep;   // register copy (see umma_body)
-            epi_tile<EBN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
-                               m0 + q * 32 + lane, n0, part);
+            epi_tile_t<EBN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
+                                 m0 + q * 32, n0, part, c_begin, c_end, scratch[warp - 2]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(te0 + 8u * (uint32_t)b);
@@ -1406,8 +1557,8 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
         if (e != cudaSuccess) return e;
     }
-    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 128>, k2_umma_gemm<UE_UNFOLDZ, 1, 128>,
-                    k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 128>}) {
+    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 256>, k2_umma_gemm<UE_UNFOLDZ, 1, 256>,
+                    k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 256>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<1>::kSmem);
         if (e != cudaSuccess) return e;
     }
@@ -1432,8 +1583,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     // 64 columns of K per stage: measured faster than 32-column stages with 64-byte swizzling
     // (twice the stages, but twice the TMA boxes and barrier round trips per multiply-add)
     const int kb = UBK;
-    // B box height: 128 rows, except the two-accumulator stages of the pair form (64 rows per CTA)
-    int bbox = 128;
+    const int bbox = 128;
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a0, A[0], ar, ac, UBM, kb);
         ok &= make_map(&g.a1, A[1], ar, ac, UBM, kb);
@@ -1478,7 +1628,6 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             f.tab[1].push_back(g);
         }
-    if (f.mode == kFoldPair) bbox = 64;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
     // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O
     for (int x = 0; x < 2; ++x) {
@@ -1502,12 +1651,12 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     }
     if (!ok) return cudaErrorNotSupported;
     for (int k = 0; k < 4; ++k) {
-        // output tiles: 128 x 128 (one-SM form); 256 rows x 128 columns for two-accumulator or
-        // mirrored stages and 256 x 256 otherwise (pair form)
+        // output tiles: 128 x 128 (one-SM form); 256 rows x 128 columns for the mirrored stage 1
+        // and 256 x 256 otherwise (pair form)
         const int tm = f.mode == kFoldPair ? 256 : UBM;
         int tiles = 0;
         for (auto& g : f.tab[k]) {
-            const int tn = (f.mode == kFoldPair && k == 1) ? 256 : 128;
+            const int tn = (f.mode == kFoldPair && k != 0) ? 256 : 128;
             if (g.M % tm != 0 || g.N % tn != 0) return cudaErrorInvalidValue;
             g.gx = g.N / tn;
             g.blk0 = tiles;
@@ -1552,11 +1701,11 @@ cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho
     const int* t = f.tiles;
     k2_umma_gemm<UE_FOLD16, 0, 128><<<grid(0), k2Threads, s0, s>>>(tab(0), c[0], t[0]);
     k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
-    k2_umma_gemm<UE_UNFOLD16, 1, 128><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
+    k2_umma_gemm<UE_UNFOLD16, 1, 256><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
     if (reduce_rho)
-        k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 128><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+        k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     else
-        k2_umma_gemm<UE_UNFOLDZ, 1, 128><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+        k2_umma_gemm<UE_UNFOLDZ, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
 }
 
