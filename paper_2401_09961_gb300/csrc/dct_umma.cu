@@ -52,7 +52,8 @@ enum UEpi : int {
     UE_FOLD16 = 4,        // out+ = acc0 + mirror(acc1), out- = acc0 - mirror(acc1)
     UE_UNFOLD16 = 5,      // row m: acc0 + acc1, row mrows-1-m: acc0 - acc1
     UE_UNFOLDZ = 6,       // col n: acc0 + acc1, col mcols-1-n: acc0 - acc1 (fp32)
-    UE_UNFOLDZ_RHO = 7    // same, plus r^T z and the CG ratio
+    UE_UNFOLDZ_RHO = 7,   // same, plus r^T z and the CG ratio
+    UE_EIG16_RHO = 8      // EIG16, plus r^T z formed from the spectral coefficients
 };
 
 struct UEpiArgs {
@@ -548,18 +549,21 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
             scr_store32(s, static_cast<float*>(ep.C), rr, nb, rows, part);
             scr_put(s, mi);
             scr_store32(s, static_cast<float*>(ep.C), rr, mb, rows, part);
-        } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+        } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16 || EPI == UE_EIG16_RHO) {
             float v[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
-            if constexpr (EPI == UE_EIG16) {
+            if constexpr (EPI == UE_EIG16 || EPI == UE_EIG16_RHO) {
                 const bool rowok = m < ep.vm;
                 const float lm = rowok ? ep.lam_m[m] : 0.f;
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const int n = nb + t;
                     const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
-                    v[t] = keep ? __fdividef(ep.scale * v[t], lm + __ldg(&ep.lam_n[n])) : 0.f;
+                    const float f = v[t];
+                    v[t] = keep ? __fdividef(ep.scale * f, lm + __ldg(&ep.lam_n[n])) : 0.f;
+                    // r^T z = sum over frequencies of F * (tau F / eig) (P_N, P_M orthogonal)
+                    if constexpr (EPI == UE_EIG16_RHO) part += f * v[t];
                 }
             }
             scr_put(s, v);
@@ -951,7 +955,7 @@ kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         atomicOr(&st0->status, ST_TIMEOUT);
         st0->done = 1;
     }
-    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
+    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO || EPI == UE_EIG16_RHO) {
         const UEpiArgs& ep = tiles[0].ep;
         double vv[1] = {(double)part}, tot[1];
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
@@ -1257,7 +1261,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         atomicOr(&st0->status, ST_TIMEOUT);
         st0->done = 1;
     }
-    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
+    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO || EPI == UE_EIG16_RHO) {
         const UEpiArgs& ep = tiles[0].ep;
         double vv[1] = {(double)part}, tot[1];
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
@@ -1548,17 +1552,17 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
     f.mode = (H % 512 == 0 && W % 512 == 0) ? kFoldPair : kFoldOneSm;
     for (auto fn : {kp_umma_gemm<UE_FOLD16, 1, 64>, kp_umma_gemm<UE_EIG16, 0, 64>,
-                    kp_umma_gemm<UE_UNFOLD16, 1, 64>, kp_umma_gemm<UE_UNFOLDZ, 1, 64>,
-                    kp_umma_gemm<UE_UNFOLDZ_RHO, 1, 64>}) {
+                    kp_umma_gemm<UE_EIG16_RHO, 0, 64>, kp_umma_gemm<UE_UNFOLD16, 1, 64>,
+                    kp_umma_gemm<UE_UNFOLDZ, 1, 64>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PCfg<64>::kSmem);
         if (e != cudaSuccess) return e;
     }
-    for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>}) {
+    for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>,
+                    k2_umma_gemm<UE_EIG16_RHO, 0, 256>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
         if (e != cudaSuccess) return e;
     }
-    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 256>, k2_umma_gemm<UE_UNFOLDZ, 1, 256>,
-                    k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 256>}) {
+    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 256>, k2_umma_gemm<UE_UNFOLDZ, 1, 256>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<1>::kSmem);
         if (e != cudaSuccess) return e;
     }
@@ -1683,13 +1687,14 @@ cudaError_t fold_launch_persistent(const DctPlan& d, const FoldBufs& f, int redu
     const int sm = PCfg<KB>::kSmem;
     const int* c = d.fold_count;
     const int* t = f.tiles;
+    // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
     kp_umma_gemm<UE_FOLD16, 1, KB><<<grid(0), kPThreads, sm, s>>>(tab(0), c[0], t[0]);
-    kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
-    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), c[2], t[2]);
     if (reduce_rho)
-        kp_umma_gemm<UE_UNFOLDZ_RHO, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
+        kp_umma_gemm<UE_EIG16_RHO, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
     else
-        kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
+        kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
+    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), c[2], t[2]);
+    kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
 }
 
@@ -1699,13 +1704,14 @@ cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho
     const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1>::kSmem;
     const int* c = d.fold_count;
     const int* t = f.tiles;
+    // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
     k2_umma_gemm<UE_FOLD16, 0, 128><<<grid(0), k2Threads, s0, s>>>(tab(0), c[0], t[0]);
-    k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
-    k2_umma_gemm<UE_UNFOLD16, 1, 256><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
     if (reduce_rho)
-        k2_umma_gemm<UE_UNFOLDZ_RHO, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+        k2_umma_gemm<UE_EIG16_RHO, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
     else
-        k2_umma_gemm<UE_UNFOLDZ, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+        k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
+    k2_umma_gemm<UE_UNFOLD16, 1, 256><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
+    k2_umma_gemm<UE_UNFOLDZ, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
 }
 
