@@ -978,9 +978,9 @@ constexpr int k2Threads = 64 + 32 * k2EpiWarps;
 // Measured on this part, N = 128 MMAs keep the tensor pipe busy at most ~77 % of the time and
 // N = 256 ones ~99 %, so two-operand-set (DUAL) problems use two N = 256 accumulators (all 512
 // tensor-memory columns, one buffer) instead of two N = 128 ones (double-buffered).
-template <int DUAL>
+template <int DUAL, int SETN = 256>
 struct Q2Cfg {
-    static constexpr int kBRows = 128;                 // B rows per CTA (per operand set)
+    static constexpr int kBRows = SETN / 2;            // B rows per CTA (per operand set)
     static constexpr int kABytes = UBM * UBK * 2;      // one bf16 part of this CTA's A rows
     static constexpr int kBBytes = kBRows * UBK * 2;
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
@@ -988,11 +988,11 @@ struct Q2Cfg {
     // ring, 1024-byte alignment slack, barriers (256 bytes), the epilogue warps' scratch
     static constexpr int kSmem =
         kStages * kStageBytes + 1024 + 256 + k2EpiWarps * (int)sizeof(WarpScratch);
-    static constexpr uint32_t kAcc = DUAL ? 512 : 256;   // tensor-memory columns per buffer
-    static constexpr int kBufs = DUAL ? 1 : 2;
-    // kind::f16, D f32, A and B bf16 K-major, N = 256, M = 256
+    static constexpr uint32_t kAcc = DUAL ? 2 * SETN : SETN;   // tensor-memory columns per buffer
+    static constexpr int kBufs = 512 / kAcc;
+    // kind::f16, D f32, A and B bf16 K-major, N = SETN, M = 256
     static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                       ((uint32_t)(256 >> 3) << 17) |
+                                       ((uint32_t)(SETN >> 3) << 17) |
                                        ((uint32_t)(256 >> 4) << 24);
 };
 
@@ -1060,9 +1060,12 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
 
-// Output tile width of a pair-form problem: a mirrored-B problem pairs a 128-column tile with
-// its mirror in one N = 256 accumulator; the others are 256 wide.
-__device__ __forceinline__ int pair_tile_n(const GemmTile& g) { return g.mirror_b1 ? 128 : 256; }
+// Output tile width of a pair-form problem: a DUAL problem's set width; a mirrored-B problem
+// pairs a 128-column tile with its mirror in one N = 256 accumulator; the others are 256 wide.
+template <int DUAL, int SETN>
+__device__ __forceinline__ int pair_tile_n(const GemmTile& g) {
+    return DUAL ? SETN : (g.mirror_b1 ? 128 : 256);
+}
 
 // Persistent CTA-pair grouped GEMM.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
 // p + gridDim.x / 2, ...; roles as in kp_umma_gemm (eight epilogue warps, two per accumulator
@@ -1077,7 +1080,8 @@ __device__ __forceinline__ int pair_tile_n(const GemmTile& g) { return g.mirror_
 template <int EPI, int DUAL, int EBN>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
 k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
-    using C = Q2Cfg<DUAL>;
+    constexpr int SETN = DUAL ? EBN : 256;     // N of one MMA (one operand set)
+    using C = Q2Cfg<DUAL, SETN>;
     constexpr int S = C::kStages;
     constexpr uint32_t kAcc = C::kAcc;
     constexpr int NB = C::kBufs;
@@ -1143,10 +1147,11 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             for (int t = pair; t < total_tiles && !bad; t += npairs) {
                 const GemmTile& g = tile_problem(tiles, T, t);
                 const int local = t - g.blk0;
-                const int tn = pair_tile_n(g);
+                const int tn = pair_tile_n<DUAL, SETN>(g);
                 const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
                 const int n0 = (local % g.gx) * tn;
-                const int nb = rank == 0 ? n0 : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + 128);
+                const int nb = rank == 0 ? n0
+                                         : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + C::kBRows);
                 const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
                 for (int kb = 0; kb < nkt; ++kb, ++it) {
                     const int s = it % S;
@@ -1203,7 +1208,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
                     tc_fence_after();
                     const bool second = DUAL && kb >= nkb;
                     const int kk = second ? kb - nkb : kb;
-                    const uint32_t td = base + (second ? 256u : 0u);
+                    const uint32_t td = base + (second ? (uint32_t)SETN : 0u);
                     const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
                     const uint32_t sb = sa + 2 * C::kABytes;
                     const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
@@ -1231,7 +1236,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         for (int t = pair; t < total_tiles; t += npairs, ++j) {
             const GemmTile& g = tile_problem(tiles, T, t);
             const int local = t - g.blk0;
-            const int tn = pair_tile_n(g);
+            const int tn = pair_tile_n<DUAL, SETN>(g);
             const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
             const int n0 = (local % g.gx) * tn;
             const int b = j % NB, u = j / NB;
@@ -1465,6 +1470,9 @@ namespace {
 // Persistent GEMM form of the folded stages: one CTA per SM (sides multiples of 256), or CTA
 // pairs with 256-row tiles (sides multiples of 512).
 constexpr int kFoldOneSm = 1, kFoldPair = 2;
+// N of each operand set in the pair form's two-set stages (3 and 4): 256 (two accumulators
+// fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
+constexpr int kPairDualN = 256;
 
 // Host-side record of the folded form's buffers and of the arguments its device tables were
 // last built for (the tables bake in the planes, the CG state and the epilogue flags).
@@ -1562,8 +1570,9 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
         if (e != cudaSuccess) return e;
     }
-    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, 256>, k2_umma_gemm<UE_UNFOLDZ, 1, 256>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<1>::kSmem);
+    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN>, k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Q2Cfg<1, kPairDualN>::kSmem);
         if (e != cudaSuccess) return e;
     }
     int dev = 0;
@@ -1587,7 +1596,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     // 64 columns of K per stage: measured faster than 32-column stages with 64-byte swizzling
     // (twice the stages, but twice the TMA boxes and barrier round trips per multiply-add)
     const int kb = UBK;
-    const int bbox = 128;
+    int bbox = 128;
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a0, A[0], ar, ac, UBM, kb);
         ok &= make_map(&g.a1, A[1], ar, ac, UBM, kb);
@@ -1632,6 +1641,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             f.tab[1].push_back(g);
         }
+    if (f.mode == kFoldPair) bbox = kPairDualN / 2;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
     // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O
     for (int x = 0; x < 2; ++x) {
@@ -1660,7 +1670,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
         const int tm = f.mode == kFoldPair ? 256 : UBM;
         int tiles = 0;
         for (auto& g : f.tab[k]) {
-            const int tn = (f.mode == kFoldPair && k != 0) ? 256 : 128;
+            const int tn = f.mode != kFoldPair ? 128 : (k == 0 ? 128 : (k == 1 ? 256 : kPairDualN));
             if (g.M % tm != 0 || g.N % tn != 0) return cudaErrorInvalidValue;
             g.gx = g.N / tn;
             g.blk0 = tiles;
@@ -1701,7 +1711,7 @@ cudaError_t fold_launch_persistent(const DctPlan& d, const FoldBufs& f, int redu
 cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho, cudaStream_t s) {
     auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
     auto grid = [&](int k) { return 2 * std::min(f.tiles[k], f.n_sm / 2); };
-    const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1>::kSmem;
+    const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1, kPairDualN>::kSmem;
     const int* c = d.fold_count;
     const int* t = f.tiles;
     // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
@@ -1710,8 +1720,8 @@ cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho
         k2_umma_gemm<UE_EIG16_RHO, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
     else
         k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
-    k2_umma_gemm<UE_UNFOLD16, 1, 256><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
-    k2_umma_gemm<UE_UNFOLDZ, 1, 256><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
+    k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
+    k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
 }
 
