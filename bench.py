@@ -271,7 +271,12 @@ def main():
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per preconditioner application (dram__bytes_read.sum + dram__bytes_write.sum
+    # over k_fold_r and the four k2_umma_gemm stages, one ncu capture of the current kernels at
+    # 4096 x 4096, bf16x3, folded pair form); null for any other configuration
+    measured_traffic = {(4096, "bf16x3", True): 807.1e6}
+    roof["traffic"] = (measured_traffic.get((n, prec, bool(folded)))
+                       if dom == "dct_precond" else None)
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
                          "dct_precond": 5 if folded else 4, "finalize": 2}
