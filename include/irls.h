@@ -60,6 +60,10 @@ extern "C" {
 #define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds; needs
                              * precision IRLS_PREC_BF16X3 and H, W multiples of 256               */
 
+/* Inner-solve budget (Sec. 4.3). */
+#define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
+#define IRLS_CG_PAPER 1     /* the adaptive budget m_CG(k) and IRLS stop of Sec. 4.3            */
+
 #define IRLS_MAX_OUTER 256
 
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
@@ -68,7 +72,9 @@ typedef struct irls_batch_s* irls_batch; /* opaque: a batched solve of many imag
 
 /* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
- * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1, dct_form = IRLS_DCT_AUTO. */
+ * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1, dct_form = IRLS_DCT_AUTO,
+ * cg_schedule = IRLS_CG_FIXED, cg_m0 = 5, cg_eps_tol = 1e-3, cg_alpha = 1.7 (the values of
+ * Sec. 4.3). */
 typedef struct {
     float tau;          /* penalty tau of problem (soft constraints), Sec. 3.1; > 0            */
     float delta;        /* smoothing delta of F_delta, Sec. 3.1; > 0                           */
@@ -79,6 +85,17 @@ typedef struct {
     int   flexible_cg;  /* 0: beta = rho_new / rho (Alg. 2); 1: Polak-Ribiere (flexible) beta  */
     int   warm_start;   /* 1: CG starts from the current (U, V); 0: from zero each outer step  */
     int   dct_form;     /* IRLS_DCT_*; IRLS_DCT_FOLDED where not allowed: IRLS_ERR_UNSUPPORTED  */
+    /* IRLS_CG_PAPER (Sec. 4.3): solve k is capped at min(m_CG(k), cg_max_iter), m_CG(0) = cg_m0.
+     * For k >= 1, with Delta = (H_delta(x^k, W^{k-1}) - H_delta(x^k, W^k)) / H_delta(x^k,
+     * W^{k-1}): Delta > cg_eps_tol keeps m_CG; otherwise the run stops and returns U^k if m_CG
+     * was raised at k-1, else m_CG(k) = floor(cg_alpha * m_CG(k-1)).  outer_iters bounds the
+     * number of IRLS iterations.  Reaching a planned budget is not a warning; reaching
+     * cg_max_iter is.  Single-image solves only (the batched and recorded forms return
+     * IRLS_ERR_UNSUPPORTED). */
+    int   cg_schedule;  /* IRLS_CG_FIXED or IRLS_CG_PAPER                                      */
+    int   cg_m0;        /* m_CG(0) >= 1                                                         */
+    float cg_eps_tol;   /* epsilon_tol of Sec. 4.3 (not NaN)                                   */
+    float cg_alpha;     /* alpha > 1 of Sec. 4.3                                               */
 } irls_opts;
 
 /* Per-call statistics (host struct filled by the library). */
@@ -91,6 +108,10 @@ typedef struct {
     double l1_obj[IRLS_MAX_OUTER];      /* objective of problem (main) at U^{k+1}             */
     double h_delta[IRLS_MAX_OUTER];     /* H_delta(U^{k+1}, V^{k+1}, W^k), problem (alt1)     */
     double f_delta[IRLS_MAX_OUTER];     /* F_delta(U^k, V^k) = H_delta(x^k, W^k) before solve */
+    int    cg_cap[IRLS_MAX_OUTER];      /* cap of each inner solve (IRLS_CG_PAPER: m_CG(k))   */
+    int    schedule_stop;               /* 1: the Sec. 4.3 rule ended the run before outer_iters;
+                                           f_delta[outer_done] then holds the F_delta(x^k) it
+                                           read at that iteration                          */
 } irls_stats;
 
 /* Fill *opts with the defaults above.  Returns IRLS_ERR_ARG if opts is NULL. */

@@ -34,7 +34,7 @@ __all__ = [
     "TWO_PI_F32", "PI_F32", "wrap_f32", "wrapped_gradients", "edge_weights",
     "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
     "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
-    "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "k_map",
+    "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "paper_cg_cap", "k_map",
     "best_shift_error", "dense_operators", "Problem", "irls_adjoint",
 ]
 
@@ -193,7 +193,8 @@ def _stored(v, storage):
     return tuple(np.asarray(a, dtype=storage).astype(np.float64) for a in v)
 
 
-def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None):
+def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None,
+        precond_rounding=None):
     """Preconditioned CG (Alg. 2) on A x = b from the warm start x0.
 
     Stops when ||r|| / ||b|| <= tol or after cg_max products with A.  ``beta_rule`` 'fr' is the
@@ -201,8 +202,20 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
     r_{l+1}^T (z_{l+1} - z_l) / rho_l, which equals it in exact arithmetic.  ``storage`` (None or
     a numpy dtype such as float32) rounds the vectors x, r, z, p to that type after every update:
     another valid floating-point execution of the same algorithm, used to measure how far such
-    executions spread; the arithmetic itself stays float64.
+    executions spread; the arithmetic itself stays float64.  ``precond_rounding`` (None or
+    (rel, seed)) multiplies each preconditioner output by 1 + rel * N(0, 1) elementwise (seeded):
+    a model of the preconditioner evaluated at finite precision, for the same purpose.
     Returns (x, iterations, final relative residual, status); status -5 flags a breakdown."""
+    if precond_rounding is not None:
+        rel_pc, seed_pc = precond_rounding
+        rng_pc = np.random.default_rng(seed_pc)
+
+    def precond(rr):
+        z = precond_apply(rr, dv, dh, tau, basis_N, basis_M)
+        if precond_rounding is None:
+            return z
+        return tuple(zi * (1.0 + rel_pc * rng_pc.standard_normal(zi.shape)) for zi in z)
+
     x = _stored(tuple(np.array(a, dtype=np.float64) for a in x0), storage)
     bnorm = math.sqrt(_dot(b, b))
     r = tuple(bi - qi for bi, qi in zip(b, apply_A(x, dv, dh, tau)))
@@ -210,7 +223,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
     if bnorm == 0.0 or rel <= tol or cg_max <= 0:
         return x, 0, rel, 0
     r = _stored(r, storage)
-    z = _stored(precond_apply(r, dv, dh, tau, basis_N, basis_M), storage)
+    z = _stored(precond(r), storage)
     p = z
     rho = _dot(r, z)
     it = 0
@@ -226,7 +239,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
         rel = math.sqrt(_dot(r, r)) / bnorm
         if rel <= tol or it >= cg_max:
             return x, it, rel, 0
-        z_new = _stored(precond_apply(r, dv, dh, tau, basis_N, basis_M), storage)
+        z_new = _stored(precond(r), storage)
         rho_new = _dot(r, z_new)
         if beta_rule == "pr":
             beta = (rho_new - _dot(r, z)) / rho
@@ -307,15 +320,43 @@ class Problem:
         self.basis_M = self.basis_N if self.M == self.N else dct_basis(self.M)
 
 
+def paper_cg_cap(delta_rel, m_prev, raised_prev, eps_tol, alpha):
+    """One step of the CG-budget rule of Sec. 4.3, taken at IRLS iteration k >= 1 once the
+    weights W^k are known.  delta_rel = Delta_{k-1,k}, the relative drop of H_delta at x^k when
+    the weights go from W^{k-1} to W^k; m_prev = m_CG(k-1); raised_prev tells whether
+    m_CG(k-1) != m_CG(k-2).  Returns (m_CG(k), raised) or (None, raised_prev) for "stop and
+    return U^k":
+      Delta > eps_tol                    -> keep the budget;
+      Delta <= eps_tol, raised last time -> stop;
+      Delta <= eps_tol, not raised       -> budget times alpha.
+    Readings: m_CG(-1) = m_CG(0) (nothing was raised before k = 1), and the scaled budget is
+    rounded down to an integer number of iterations."""
+    if delta_rel > eps_tol:
+        return m_prev, False
+    if raised_prev:
+        return None, raised_prev
+    return int(np.floor(alpha * m_prev)), True
+
+
 def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
-                cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None):
-    """Alg. 1 with Alg. 2 as the inner solver, for a fixed number of outer iterations.
+                cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None,
+                cg_schedule="fixed", m0=5, eps_tol=1e-3, alpha=1.7, precond_rounding=None):
+    """Alg. 1 with Alg. 2 as the inner solver.
+
+    cg_schedule "fixed": outer_iters IRLS iterations, every inner solve capped at cg_max.
+    cg_schedule "paper": the CG budget m_CG(k) and the IRLS stop of Sec. 4.3 (paper_cg_cap,
+    m_CG(0) = m0), at most outer_iters iterations, each solve capped at min(m_CG(k), cg_max).
 
     Returns a dict with U (zero mean), Vv, Vh, and per-outer statistics: cg_iters, rel_res,
     l1_obj (problem (main) at U^{k+1}), h_delta (H_delta(x^{k+1}, W^k)), h_before
-    (H_delta(x^k, W^k)), h_after_rw (H_delta(x^{k+1}, W^{k+1})), f_delta, status.  With
-    ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
-    ``storage`` is passed to pcg (float64 arithmetic with rounded vector storage)."""
+    (H_delta(x^k, W^k)), h_after_rw (H_delta(x^{k+1}, W^{k+1})), f_delta, cg_cap (the cap of
+    each solve), delta_rel (Delta_{k-1,k} for k >= 1, "paper" only), schedule_stop and h_stop
+    (H_delta(x^k, W^k) at the iteration where the rule stopped the run), status.
+    With ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
+    ``storage`` and ``precond_rounding`` are passed to pcg (other valid floating-point executions;
+    the latter's seed advances with the outer iteration)."""
+    if cg_schedule not in ("fixed", "paper"):
+        raise ValueError("cg_schedule is 'fixed' or 'paper'")
     pb = Problem(X, coherence, Cv, Ch, tau)
     N, M = pb.N, pb.M
     if x0 is None:
@@ -325,21 +366,40 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
     else:
         U, Vv, Vh = (np.array(a, dtype=np.float64) for a in x0)
     st = {k: [] for k in ("cg_iters", "rel_res", "l1_obj", "h_delta", "h_before", "h_after_rw",
-                          "f_delta")}
+                          "f_delta", "cg_cap", "delta_rel")}
     rec = {"W": [], "x": []}
     status = 0
+    m_cg, raised, stop, h_stop = m0, False, False, None
     for k in range(outer_iters):
         Wv, Wh = reweight(Vv, Vh, pb.Cv, pb.Ch, delta)
         dv, dh = diag_d(pb.Cv, pb.Ch, Wv, Wh)
+        h_before = H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
+        cap = cg_max
+        if cg_schedule == "paper":
+            if k >= 1:
+                # Delta_{k-1,k} = (H(x^k, W^{k-1}) - H(x^k, W^k)) / H(x^k, W^{k-1})
+                d = (st["h_delta"][-1] - h_before) / st["h_delta"][-1]
+                st["delta_rel"].append(d)
+                m_next, raised = paper_cg_cap(d, m_cg, raised, eps_tol, alpha)
+                if m_next is None:
+                    stop = True
+                    h_stop = h_before
+                    break
+                m_cg = m_next
+            cap = min(m_cg, cg_max)
         if record:
             rec["W"].append((Wv, Wh))
             rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
-        st["h_before"].append(H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
+        st["h_before"].append(h_before)
+        st["cg_cap"].append(cap)
+        pr = None if precond_rounding is None else (precond_rounding[0],
+                                                    precond_rounding[1] + 7919 * k)
         (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
-                                      cg_tol, cg_max, beta_rule, storage)
+                                      cg_tol, cap, beta_rule, storage, pr)
         if s < 0:
             status = s
-        elif it >= cg_max and rel > cg_tol and status == 0:
+        elif it >= cap and cap >= cg_max and rel > cg_tol and status == 0:
+            # the hard cap ended a solve short of cg_tol (a planned budget of Sec. 4.3 does not)
             status = 1
         U = U - U.mean()
         st["cg_iters"].append(it)
@@ -351,7 +411,8 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
         st["f_delta"].append(F_delta_value(U, Vv, Vh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta))
         if s < 0:
             break
-    out = {"U": U, "Vv": Vv, "Vh": Vh, "status": status, "problem": pb, **st}
+    out = {"U": U, "Vv": Vv, "Vh": Vh, "status": status, "problem": pb, "schedule_stop": stop,
+           "h_stop": h_stop, **st}
     if record:
         rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         out["record"] = rec

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libirls.so")
 
 IRLS_MAX_OUTER = 256
 DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2}
+CG_SCHEDULES = {"fixed": 0, "paper": 1}
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
 STATUS = {
@@ -34,6 +35,10 @@ class Opts(ctypes.Structure):
         ("flexible_cg", ctypes.c_int),
         ("warm_start", ctypes.c_int),
         ("dct_form", ctypes.c_int),
+        ("cg_schedule", ctypes.c_int),
+        ("cg_m0", ctypes.c_int),
+        ("cg_eps_tol", ctypes.c_float),
+        ("cg_alpha", ctypes.c_float),
     ]
 
 
@@ -47,6 +52,8 @@ class Stats(ctypes.Structure):
         ("l1_obj", ctypes.c_double * IRLS_MAX_OUTER),
         ("h_delta", ctypes.c_double * IRLS_MAX_OUTER),
         ("f_delta", ctypes.c_double * IRLS_MAX_OUTER),
+        ("cg_cap", ctypes.c_int * IRLS_MAX_OUTER),
+        ("schedule_stop", ctypes.c_int),
     ]
 
     def to_dict(self):
@@ -60,6 +67,10 @@ class Stats(ctypes.Structure):
             "l1_obj": list(self.l1_obj[:n]),
             "h_delta": list(self.h_delta[:n]),
             "f_delta": list(self.f_delta[:n]),
+            "cg_cap": list(self.cg_cap[:n]),
+            "schedule_stop": bool(self.schedule_stop),
+            "f_delta_stop": (self.f_delta[n] if self.schedule_stop and n < IRLS_MAX_OUTER
+                             else None),
         }
 
 
@@ -144,5 +155,7 @@ def default_opts(**kw):
             v = PRECISIONS[v]
         if k == "dct_form" and isinstance(v, str):
             v = DCT_FORMS[v]
+        if k == "cg_schedule" and isinstance(v, str):
+            v = CG_SCHEDULES[v]
         setattr(o, k, v)
     return o

@@ -54,6 +54,10 @@ bool opts_valid(const irls_opts& o) {
     if (o.cg_max_iter < 0) return false;
     if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_BF16X3) return false;
     if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FOLDED) return false;
+    if (o.cg_schedule != IRLS_CG_FIXED && o.cg_schedule != IRLS_CG_PAPER) return false;
+    if (o.cg_schedule == IRLS_CG_PAPER &&
+        (o.cg_m0 < 1 || !(o.cg_alpha > 1.f) || std::isnan(o.cg_eps_tol)))
+        return false;
     return true;
 }
 
@@ -162,6 +166,9 @@ struct irls_plan_s {
     double* partials = nullptr;
     DctPlan dct{};
     int* h_flag = nullptr;     // pinned, 2 slots
+    double* h_pair = nullptr;  // pinned, 2 doubles: H_delta values read by the Sec. 4.3 rule
+    std::vector<int> caps;     // cap of each inner solve of the last run
+    int schedule_stop = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profiler prof;
 };
@@ -190,6 +197,7 @@ StencilArgs make_args(const irls_plan_s* p) {
     a.delta = p->opts.delta;
     a.tol2 = (double)p->opts.cg_tol * (double)p->opts.cg_tol;
     a.cg_max = p->opts.cg_max_iter;
+    a.cap_warn = 1;
     a.flexible = p->opts.flexible_cg;
     a.warm_start = p->opts.warm_start;
     a.prec = p->opts.precision;
@@ -222,6 +230,7 @@ void destroy_plan(irls_plan_s* p) {
     dct_release(p->dct);
     if (p->mem) cudaFree(p->mem);
     if (p->h_flag) cudaFreeHost(p->h_flag);
+    if (p->h_pair) cudaFreeHost(p->h_pair);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(cur);
@@ -252,12 +261,16 @@ int fetch_stats(irls_plan_s* p, cudaStream_t s, irls_stats* stats) {
         stats->cg_total = h.cg_total;
         const int n = std::min(h.outer, IRLS_MAX_OUTER);
         for (int k = 0; k < n; ++k) {
+            stats->cg_cap[k] = k < (int)p->caps.size() ? p->caps[k] : 0;
             stats->cg_iters[k] = h.cg_iters[k];
             stats->rel_res[k] = h.rel_res[k];
             stats->l1_obj[k] = h.l1_obj[k];
             stats->h_delta[k] = h.h_delta[k];
             stats->f_delta[k] = h.f_delta[k];
         }
+        stats->schedule_stop = p->schedule_stop;
+        // the rule's last input: F_delta(x^k) at the iteration where it stopped the run
+        if (p->schedule_stop && n < IRLS_MAX_OUTER) stats->f_delta[n] = h.f_delta[n];
         stats->status = status_to_code(h.status);
         return h.status;
     }
@@ -274,8 +287,8 @@ void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s) 
     int issued = 0, slot = 0;
     bool pending = false;
     size_t mark[2] = {0, 0};
-    while (issued < p->opts.cg_max_iter) {
-        const int n = std::min(kChunk, p->opts.cg_max_iter - issued);
+    while (issued < a.cg_max) {
+        const int n = std::min(kChunk, a.cg_max - issued);
         for (int c = 0; c < n; ++c) {
             t0 = pf.begin(s);
             ck(launch_direction_pap(p->P, a, st, p->partials, s));
@@ -332,16 +345,49 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
         copy_plane(tape->Vv[0], p->P.Vv, pb, s); copy_plane(tape->Vh[0], p->P.Vh, pb, s);
     }
 
+    // inner-solve budget: fixed, or the adaptive rule of Sec. 4.3
+    const bool sched = p->opts.cg_schedule == IRLS_CG_PAPER;
+    int m_cg = p->opts.cg_m0;
+    bool raised = false;
+    p->caps.assign(p->opts.outer_iters, 0);
+    p->schedule_stop = 0;
     for (int k = 0; k < p->opts.outer_iters; ++k) {
         t0 = pf.begin(s);
         ck(launch_reweight_residual(p->P, a, st, p->partials, s));
         pf.end(PC_REWEIGHT, t0, s);
+        StencilArgs ak = a;
+        if (sched) {
+            if (k >= 1 && k < IRLS_MAX_OUTER) {
+                // Delta_{k-1,k} from H_delta(x^k, W^{k-1}) (the previous finalize) and
+                // H_delta(x^k, W^k) = F_delta(x^k) (this reweight)
+                ck(cudaMemcpyAsync(&p->h_pair[0], &st->h_delta[k - 1], sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+                ck(cudaMemcpyAsync(&p->h_pair[1], &st->f_delta[k], sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+                ck(cudaStreamSynchronize(s));
+                const double hp = p->h_pair[0], hk = p->h_pair[1];
+                const double d = (hp - hk) / hp;
+                if (d > (double)p->opts.cg_eps_tol) {
+                    raised = false;
+                } else if (raised) {
+                    p->schedule_stop = 1;   // return U^k
+                    break;
+                } else {
+                    m_cg = (int)std::floor((double)p->opts.cg_alpha * (double)m_cg);
+                    raised = true;
+                }
+            }
+            ak.cg_max = std::min(m_cg, p->opts.cg_max_iter);
+            // a planned budget is not a warning; the hard cap is
+            ak.cap_warn = ak.cg_max >= p->opts.cg_max_iter ? 1 : 0;
+        }
+        p->caps[k] = ak.cg_max;
         t0 = pf.begin(s);
-        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
+        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, ak, p->partials, 1, s));
         pf.end(PC_DCT, t0, s);
-        run_cg(p, a, st, s);
+        run_cg(p, ak, st, s);
         t0 = pf.begin(s);
-        ck(launch_finalize(p->P, a, st, p->partials, s));
+        ck(launch_finalize(p->P, ak, st, p->partials, s));
         pf.end(PC_FINALIZE, t0, s);
         if (tape) {
             copy_plane(tape->Vv[k + 1], p->P.Vv, pb, s);
@@ -535,6 +581,10 @@ int irls_opts_default(irls_opts* o) {
     o->flexible_cg = 0;
     o->warm_start = 1;
     o->dct_form = IRLS_DCT_AUTO;
+    o->cg_schedule = IRLS_CG_FIXED;
+    o->cg_m0 = 5;
+    o->cg_eps_tol = 1e-3f;
+    o->cg_alpha = 1.7f;
     return IRLS_OK;
 }
 
@@ -591,6 +641,7 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
             return IRLS_ERR_UNSUPPORTED;
         }
         ck(cudaHostAlloc(&p->h_flag, 2 * sizeof(int), cudaHostAllocDefault));
+        ck(cudaHostAlloc(&p->h_pair, 2 * sizeof(double), cudaHostAllocDefault));
         for (auto& ev : p->ev) ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         ck(cudaDeviceSynchronize());
     } catch (Fail&) {
@@ -658,6 +709,8 @@ int irls_unwrap_forward_record(irls_plan p, const float* X, const float* coh, co
     if (!p || !X || !U || !out) return IRLS_ERR_ARG;
     *out = nullptr;
     if ((Cv == nullptr) != (Ch == nullptr)) return IRLS_ERR_ARG;
+    // the adjoint differentiates through converged inner solves: no planned budgets
+    if (p->opts.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     irls_tape_s* t = new (std::nothrow) irls_tape_s();
     if (!t) return IRLS_ERR_OOM;
@@ -775,6 +828,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     if (!opts_valid(o)) return IRLS_ERR_ARG;
     if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
     if (o.dct_form == IRLS_DCT_FOLDED) return IRLS_ERR_UNSUPPORTED;   // grouped form is direct
+    if (o.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;  // images run in lockstep
     for (int t = 0; t < ntiles; ++t)
         if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
     irls_batch_s* b = new (std::nothrow) irls_batch_s();
@@ -850,6 +904,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             a.tau = o.tau; a.inv_tau = 1.0f / o.tau; a.delta = o.delta;
             a.tol2 = (double)o.cg_tol * (double)o.cg_tol;
             a.cg_max = o.cg_max_iter;
+            a.cap_warn = 1;
             a.flexible = o.flexible_cg;
             a.warm_start = o.warm_start;
             a.prec = o.precision;

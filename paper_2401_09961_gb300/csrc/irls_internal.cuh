@@ -71,6 +71,7 @@ struct StencilArgs {
     float tau, inv_tau, delta;
     double tol2;        // cg_tol^2
     int cg_max;
+    int cap_warn;       // 1: a run ended by cg_max short of the tolerance sets ST_CGMAX
     int flexible;
     int warm_start;
     int cur;            // which pU/pVv/pVh buffer holds the newest direction

@@ -557,7 +557,8 @@ __device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, 
             st->rel_res[k] = st->rel;
         }
         st->cg_total += st->iter;
-        if (st->iter >= a.cg_max && st->rel * st->rel > a.tol2) st->status |= ST_CGMAX;
+        if (a.cap_warn && st->iter >= a.cg_max && st->rel * st->rel > a.tol2)
+            st->status |= ST_CGMAX;
         st->outer = k + 1;
     }
 }

@@ -527,6 +527,76 @@ def test_paper_parameters_fixture():
 
 
 # ------------------------------------------------------------------------------------------
+# Sec. 4.3: CG budget and IRLS stop
+# ------------------------------------------------------------------------------------------
+def test_paper_cg_cap_rules():
+    """The three cases of Sec. 4.3, with its parameters m_CG(0) = 5, eps_tol = 1e-3, alpha = 1.7,
+    on a hand-worked sequence of relative improvements."""
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    m0, tol, a = g["max_iter_CG_start"], g["rel_improvement_tol"], g["increase_CG_iteration_factor"]
+    # case 1: significant improvement keeps the budget
+    assert O.paper_cg_cap(0.5, 5, False, tol, a) == (5, False)
+    assert O.paper_cg_cap(0.5, 8, True, tol, a) == (8, False)
+    # case 3: not significant, budget not raised last time -> times alpha (5 * 1.7 = 8.5 -> 8)
+    assert O.paper_cg_cap(1e-4, 5, False, tol, a) == (8, True)
+    assert O.paper_cg_cap(tol, 13, False, tol, a) == (22, True)      # boundary: Delta <= tol
+    # case 2: not significant right after a raise -> stop
+    assert O.paper_cg_cap(1e-4, 8, True, tol, a)[0] is None
+    # a whole run: Delta_{k-1,k} for k = 1..6
+    deltas = [0.5, 0.1, 5e-4, 0.2, 5e-4, 5e-4]
+    m, raised, caps = m0, False, [m0]
+    for d in deltas:
+        m_next, raised = O.paper_cg_cap(d, m, raised, tol, a)
+        if m_next is None:
+            break
+        m = m_next
+        caps.append(m)
+    assert caps == [5, 5, 5, 8, 8, 13] and m_next is None
+
+
+@pytest.fixture(scope="module")
+def schedule_case():
+    d = synthetic.config_small(3, H=24, W=20)
+    return d["X"], dict(tau=1e-2, delta=1e-3, outer_iters=12, cg_tol=1e-10, cg_max=1000)
+
+
+def test_paper_schedule_special_cases(schedule_case):
+    """eps_tol < 0 never finds an improvement insignificant: the run is the fixed schedule with
+    every solve capped at m_CG(0).  eps_tol = inf finds every improvement insignificant: the
+    budget is raised once at k = 1 (5 -> 8) and the run stops at k = 2, returning U^2."""
+    X, kw = schedule_case
+    keep = O.irls_unwrap(X, None, cg_schedule="paper", eps_tol=-1.0, **kw)
+    fixed = O.irls_unwrap(X, None, **dict(kw, cg_max=5))
+    assert keep["cg_cap"] == [5] * kw["outer_iters"] and not keep["schedule_stop"]
+    assert np.array_equal(keep["U"], fixed["U"])
+    stop = O.irls_unwrap(X, None, cg_schedule="paper", eps_tol=np.inf, **kw)
+    assert stop["cg_cap"] == [5, 8] and stop["schedule_stop"]
+    assert len(stop["cg_iters"]) == 2 and stop["cg_iters"][1] <= 8
+
+
+def test_paper_schedule_follows_the_rule(schedule_case):
+    """With the paper's parameters, the caps and the stop follow the rule applied to the run's
+    own Delta_{k-1,k} = (H(x^k, W^{k-1}) - H(x^k, W^k)) / H(x^k, W^{k-1}), and every Delta is
+    >= 0 (reweighting minimises H over W, Sec. 3.1)."""
+    X, kw = schedule_case
+    r = O.irls_unwrap(X, None, cg_schedule="paper", **kw)
+    assert r["cg_cap"][0] == 5
+    assert all(d >= -1e-12 for d in r["delta_rel"])
+    h_now = r["h_before"] + ([r["h_stop"]] if r["schedule_stop"] else [])
+    for k, d in enumerate(r["delta_rel"], start=1):
+        ref = (r["h_delta"][k - 1] - h_now[k]) / r["h_delta"][k - 1]
+        assert d == ref
+    m, raised = 5, False
+    for k, d in enumerate(r["delta_rel"], start=1):
+        m, raised = O.paper_cg_cap(d, m, raised, 1e-3, 1.7)
+        if m is None:
+            assert r["schedule_stop"] and len(r["cg_cap"]) == k
+            break
+        assert r["cg_cap"][k] == m
+    assert all(it <= cap for it, cap in zip(r["cg_iters"], r["cg_cap"]))
+
+
+# ------------------------------------------------------------------------------------------
 # Adjoint of the IRLS map: central differences of the oracle's own forward map
 # ------------------------------------------------------------------------------------------
 def _adjoint_case():
