@@ -36,9 +36,11 @@ CG_TOTAL_REFERENCE = {4096: 5000, 2048: 3000}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
-def workload_name(n, prec):
-    return (f"irls_unwrap_{n}x{n}: synthetic interferogram (ramp 0-{800 * n // 4096} rad, "
-            f"{max(1, round(80 * n / 4096))} bumps, 20% low-coherence patches, two 3pi steps), "
+def workload_name(n, prec, w=None):
+    w = n if w is None else w
+    m = max(n, w)
+    return (f"irls_unwrap_{n}x{w}: synthetic interferogram (ramp 0-{800 * m // 4096} rad, "
+            f"{max(1, round(80 * m / 4096))} bumps, 20% low-coherence patches, two 3pi steps), "
             f"coherence weights, {OUTER} IRLS iterations, delta {DELTA:g}, tau {TAU:g}, "
             f"cg_tol {CG_TOL:g}, DCT preconditioner {prec}")
 
@@ -138,9 +140,9 @@ def cpu_threads():
         return os.cpu_count()
 
 
-def extrapolated_oracle_rate(n, t_setup, t_outer, t_iter, cg_total, outer=OUTER):
+def extrapolated_oracle_rate(n, t_setup, t_outer, t_iter, cg_total, outer=OUTER, w=None):
     t_full = t_setup + outer * t_outer + cg_total * t_iter
-    return (n * n / 1e6) / t_full, t_full
+    return (n * (n if w is None else w) / 1e6) / t_full, t_full
 
 
 # ------------------------------------------------------------------------------------------
@@ -151,6 +153,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--width", type=int, default=None,
+                    help="image width (default: --size, a square image); e.g. --size 4000 "
+                         "--width 16000 for the paper's 4000 x M scaling shapes")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -186,11 +191,12 @@ def main():
     import synthetic
     import ctypes
 
-    d = synthetic.config_4096_mixed(seed=20 + rank, H=n, W=n)
+    wd = args.width or n
+    d = synthetic.config_4096_mixed(seed=20 + rank, H=n, W=wd)
     X = torch.as_tensor(d["X"]).cuda()
     C = torch.as_tensor(d["coherence"]).cuda()
     flexible = 1 if prec == "bf16" else 0
-    plan = irls.Plan(n, n, tau=TAU, delta=DELTA, outer_iters=args.outer, cg_tol=CG_TOL,
+    plan = irls.Plan(n, wd, tau=TAU, delta=DELTA, outer_iters=args.outer, cg_tol=CG_TOL,
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible,
                      cg_schedule=args.cg_schedule)
     stream = torch.cuda.current_stream()
@@ -229,13 +235,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_step = ms / args.steps
-    mpix_step = n * n / 1e6
+    mpix_step = n * wd / 1e6
     value = world * mpix_step * args.steps / (ms / 1e3)
 
     # ---- roofline of the dominant kernel class ----
     peaks, peak_src = load_peaks()
-    P = n * n
-    Hp = Wp = (n + 127) // 128 * 128
+    P = n * wd
     cg_total = stats[-1]["cg_total"]
     outer_done = stats[-1]["outer_done"]
     classes = ["init", "reweight_residual", "direction_pap", "update", "dct_precond", "finalize"]
@@ -249,7 +254,7 @@ def main():
     folded = plan.folded
     # multiply-adds the preconditioner performs per application: four n^3 products in the direct
     # form; the folded form runs each stage as half-size products (half of that)
-    dct_flops = 4.0 * Hp * Wp * (n + n) * (0.5 if folded else 1.0)
+    dct_flops = 4.0 * n * wd * (n + wd) * (0.5 if folded else 1.0)
     dom = max(("direction_pap", "update", "dct_precond", "reweight_residual"),
               key=lambda c: per_cls[c]["ms"])
     avg_s = per_cls[dom]["ms"] / 1e3 / max(live[dom], 1)
@@ -279,8 +284,8 @@ def main():
     # DRAM bytes per preconditioner application (dram__bytes_read.sum + dram__bytes_write.sum
     # over k_fold_r and the four k2_umma_gemm stages, one ncu capture of the current kernels at
     # 4096 x 4096, bf16x3, folded pair form); null for any other configuration
-    measured_traffic = {(4096, "bf16x3", True): 807.1e6}
-    roof["traffic"] = (measured_traffic.get((n, prec, bool(folded)))
+    measured_traffic = {(4096, 4096, "bf16x3", True): 807.1e6}
+    roof["traffic"] = (measured_traffic.get((n, wd, prec, bool(folded)))
                        if dom == "dct_precond" else None)
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
@@ -312,9 +317,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ts, to, ti = oracle_sample(d["X"], d["coherence"])
-        rate, tfull = extrapolated_oracle_rate(n, ts, to, ti, cg_total, outer_done)
+        rate, tfull = extrapolated_oracle_rate(n, ts, to, ti, cg_total, outer_done, wd)
         cpu = {"value": rate, "unit": "Mpix/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": (f"FP64 NumPy oracle on the full {n}x{n} image: set-up + one outer step "
+               "sample": (f"FP64 NumPy oracle on the full {n}x{wd} image: set-up + one outer step "
                           f"+ 2 PCG iterations timed ({ts:.1f} s, {to:.1f} s, {ti:.2f} s/iter), "
                           f"extrapolated to a full unwrap with this run's {cg_total} CG "
                           f"iterations: {tfull:.0f} s"),
@@ -329,7 +334,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else
             f"f32+{prec}-tensor-core-dct", "data": "synthetic",
-            "config": {"workload": workload_name(n, prec), "size": [n, n],
+            "config": {"workload": workload_name(n, prec, wd), "size": [n, wd],
                        "outer_iters": args.outer, "outer_done": outer_done,
                        "cg_schedule": args.cg_schedule, "delta": DELTA, "tau": TAU,
                        "cg_tol": CG_TOL,

@@ -223,6 +223,22 @@ int irls_apply_A(irls_plan plan, const float* d_U, const float* d_Vv, const floa
                  const float* d_Dv, const float* d_Dh, float* d_qU, float* d_qVv, float* d_qVh,
                  void* stream);
 
+/* "Rounded IRLS" (Sec. 4.5): moves an unwrapped image d_U (H x W, the plan's shape) to the
+ * nearest image 2pi-congruent to the input phase d_X.  The global offset of U is free (the model
+ * is shift invariant), so U is first aligned with X by the circular mean
+ * c = arg sum exp(i (U - X)) (FP64 sums); then, per pixel in float32 (one rounded operation at a
+ * time), K = rint(((U - c) - X) / 2pi) and U_round = X + 2pi K.  d_Uround (float, H x W) and d_K
+ * (int32, H x W) may each be NULL; h_offset (host, nullable) receives c.  Uses the plan's
+ * device state (not during a solve on another stream).  Synchronous. */
+int irls_round_congruent(irls_plan plan, const float* d_U, const float* d_X, float* d_Uround,
+                         int* d_K, double* h_offset, void* stream);
+
+/* Best-shift error of Sec. 4.5 against a reference unwrapping d_Xu (H x W):
+ * alpha = mean(Xu - U) (FP64), E = (Xu - U) - alpha (float32, d_E nullable), and the RMS of E
+ * (FP64).  h_alpha, h_rms: host, nullable.  Synchronous. */
+int irls_best_shift_error(irls_plan plan, const float* d_U, const float* d_Xu, float* d_E,
+                          double* h_alpha, double* h_rms, void* stream);
+
 /* Allocation-free Laplacian preconditioner.  The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory - plug-ins whose host framework owns every
  * device byte through its own allocator, and latency-critical code that must never meet

@@ -35,6 +35,7 @@ __all__ = [
     "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
     "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
     "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "paper_cg_cap", "k_map",
+    "round_congruent",
     "best_shift_error", "dense_operators", "Problem", "irls_adjoint",
 ]
 
@@ -426,6 +427,27 @@ def best_shift_error(U, Xu):
     """E(U, Xu) = Xu - (U + alpha), alpha = mean(Xu - U) (Sec. 4.5)."""
     alpha = float(np.mean(Xu - U))
     return Xu - (U + alpha)
+
+
+def round_congruent(U, X, c=None):
+    """'Rounded IRLS' (Sec. 4.5): the output moved to the nearest image that is 2pi-congruent to
+    the input.  The global offset of U is free (the model is shift invariant), so U is first
+    aligned with X by the circular mean c = arg sum exp(i (U - X)) (float64); then
+    K = rint((U - c - X) / 2pi) and U_round = X + 2pi K.  The integer K is decided in float32,
+    one correctly rounded operation at a time (the precision of the library's kernel):
+    t = (U - c) - X, q = t / 2pi, K = rint(q), U_round = X + (2pi * K).  Returns
+    (U_round float32, K int64, c)."""
+    U32 = np.asarray(U, dtype=np.float32)
+    X32 = np.asarray(X, dtype=np.float32)
+    if c is None:
+        d = U32.astype(np.float64) - X32.astype(np.float64)
+        c = float(math.atan2(np.sum(np.sin(d)), np.sum(np.cos(d))))
+    c32 = np.float32(c)
+    t = ((U32 - c32).astype(np.float32) - X32).astype(np.float32)
+    q = (t / TWO_PI_F32).astype(np.float32)
+    K = np.rint(q).astype(np.float32)
+    Ur = (X32 + (TWO_PI_F32 * K).astype(np.float32)).astype(np.float32)
+    return Ur, K.astype(np.int64), c
 
 
 def k_map(U, X):

@@ -13,7 +13,8 @@ import ctypes
 from ._binding import (CG_SCHEDULES, DCT_FORMS, IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
                        lib)
 
-__all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "default_opts", "lib", "IrlsError",
+__all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "round_congruent",
+           "best_shift_error", "default_opts", "lib", "IrlsError",
            "Opts", "Stats", "PRECISIONS", "unwrap_differentiable"]
 
 
@@ -234,6 +235,29 @@ def precond_laplacian(plan, R, stream=None):
     check(lib().irls_precond_laplacian(plan.handle, _ptr(R), _ptr(Z), _stream(stream)),
           "irls_precond_laplacian")
     return Z
+
+
+def round_congruent(plan, U, X, stream=None):
+    """'Rounded IRLS' (Sec. 4.5): (U_round, K, c) with U_round = X + 2pi K the image
+    2pi-congruent to X nearest to U aligned by its circular-mean offset c (device tensors)."""
+    torch = _torch()
+    Ur = torch.empty_like(U)
+    K = torch.empty(U.shape, device=U.device, dtype=torch.int32)
+    c = ctypes.c_double()
+    check(lib().irls_round_congruent(plan.handle, _ptr(U), _ptr(X), _ptr(Ur),
+                                     ctypes.c_void_p(K.data_ptr()), ctypes.byref(c),
+                                     _stream(stream)), "irls_round_congruent")
+    return Ur, K, c.value
+
+
+def best_shift_error(plan, U, Xu, stream=None):
+    """Best-shift error of Sec. 4.5: (E, alpha, rms) with E = (Xu - U) - alpha on the device."""
+    torch = _torch()
+    E = torch.empty_like(U)
+    a, r = ctypes.c_double(), ctypes.c_double()
+    check(lib().irls_best_shift_error(plan.handle, _ptr(U), _ptr(Xu), _ptr(E), ctypes.byref(a),
+                                      ctypes.byref(r), _stream(stream)), "irls_best_shift_error")
+    return E, a.value, r.value
 
 
 def apply_A(plan, U, Vv, Vh, Dv, Dh, stream=None):

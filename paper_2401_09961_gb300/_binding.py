@@ -86,6 +86,9 @@ SIGNATURES = {
     "irls_plan_destroy": (_I, [_P]),
     "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
     "irls_plan_dct_form": (_I, [_P]),
+    "irls_round_congruent": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "irls_best_shift_error": (_I, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), _P]),
     "irls_unwrap": (_I, [_P, _P, _I, _I, _F, _I, _F, _P, _P]),
     "irls_unwrap_ex": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     "irls_unwrap_forward_record": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(_P),

@@ -991,6 +991,46 @@ int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) 
     return IRLS_OK;
 }
 
+int irls_round_congruent(irls_plan p, const float* U, const float* X, float* Ur, int* K,
+                         double* offset, void* stream) {
+    if (!p || !U || !X) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        DeviceGuard g(p->dev);
+        const size_t n = (size_t)p->H * p->W;
+        ck(cudaMemsetAsync(&p->st->counter, 0, sizeof(unsigned int), s));
+        ck(launch_round_congruent(U, X, n, p->st, p->partials, p->L.max_blocks, Ur, K, s));
+        double h = 0.0;
+        ck(cudaMemcpyAsync(p->h_pair, &p->st->aux[0], sizeof(double), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        h = p->h_pair[0];
+        if (offset) *offset = h;
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return IRLS_OK;
+}
+
+int irls_best_shift_error(irls_plan p, const float* U, const float* Xu, float* E, double* alpha,
+                          double* rms, void* stream) {
+    if (!p || !U || !Xu) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        DeviceGuard g(p->dev);
+        const size_t n = (size_t)p->H * p->W;
+        ck(cudaMemsetAsync(&p->st->counter, 0, sizeof(unsigned int), s));
+        ck(launch_best_shift(U, Xu, n, p->st, p->partials, p->L.max_blocks, E, s));
+        ck(cudaMemcpyAsync(p->h_pair, &p->st->aux[1], 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           s));
+        ck(cudaStreamSynchronize(s));
+        if (alpha) *alpha = p->h_pair[0];
+        if (rms) *rms = std::sqrt(p->h_pair[1] / (double)n);
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return IRLS_OK;
+}
+
 int irls_apply_A(irls_plan p, const float* U, const float* Vv, const float* Vh, const float* Dv,
                  const float* Dh, float* qU, float* qVv, float* qVh, void* stream) {
     if (!p || !U || !qU) return IRLS_ERR_ARG;

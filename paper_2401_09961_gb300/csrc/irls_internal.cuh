@@ -50,6 +50,7 @@ struct DevState {
     double l1_obj[kMaxOuter];
     double h_delta[kMaxOuter];
     double f_delta[kMaxOuter];
+    double aux[4];   // post-processing results: circular offset, best shift, sum of E^2
 };
 
 // Image-shaped planes.  Every plane is H rows x ld floats (ld a multiple of 32); the vertical
@@ -191,6 +192,11 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
 // receives error flags; with reduce_rho the last GEMM also forms rho = r_U^T z_U + st->rz_v
 // and the next beta (Alg. 2).  With skip_if_done the launches return at once once CG stopped.
 void dct_release(DctPlan& d);
+cudaError_t launch_round_congruent(const float* U, const float* X, size_t n, DevState* st,
+                                   double* partials, int max_blocks, float* Ur, int* K,
+                                   cudaStream_t s);
+cudaError_t launch_best_shift(const float* U, const float* Xu, size_t n, DevState* st,
+                              double* partials, int max_blocks, float* E, cudaStream_t s);
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
                       cudaStream_t s);

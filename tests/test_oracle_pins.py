@@ -597,6 +597,53 @@ def test_paper_schedule_follows_the_rule(schedule_case):
 
 
 # ------------------------------------------------------------------------------------------
+# Sec. 4.5: rounded IRLS and the best-shift error
+# ------------------------------------------------------------------------------------------
+def test_round_congruent_recovers_planted_integers():
+    """U = X + 2pi K0 + c0 + small noise: the planted K0 and offset come back exactly, and the
+    rounded image is X + 2pi K0 (congruent to X to float32 rounding)."""
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-np.pi, np.pi, (40, 30)).astype(np.float32)
+    K0 = rng.integers(-20, 21, (40, 30))
+    c0 = 1.234
+    U = (X + 2 * np.pi * K0 + c0 + 0.3 * rng.standard_normal(X.shape)).astype(np.float32)
+    Ur, K, c = O.round_congruent(U, X)
+    assert abs(c - c0) < 0.1
+    assert np.array_equal(K, K0)
+    assert np.abs(Ur.astype(np.float64) - X - 2 * np.pi * K0).max() <= 4e-6 * np.abs(Ur).max()
+    # a multiple of 2pi added to U moves K by the same integer; a constant shift moves only c
+    _, K2, _ = O.round_congruent((U + np.float32(2 * np.pi) * 3).astype(np.float32), X)
+    assert np.array_equal(K2, K0 + 3)
+    _, K3, c3 = O.round_congruent((U + np.float32(0.5)).astype(np.float32), X)
+    assert np.array_equal(K3, K0) and abs(c3 - c - 0.5) < 1e-6
+
+
+def test_rounded_irls_matches_true_ambiguities_on_an_easy_image():
+    """On a low-noise smooth phase the unwrapped output rounds to the true integer map (the
+    planted phase's own ambiguities), up to one global integer."""
+    d = synthetic.make_phase(48, 40, 9, ramp=30.0, n_bumps=2, noise=0.05)
+    r = O.irls_unwrap(d["X"], None, tau=1e-2, delta=1e-3, outer_iters=8, cg_tol=1e-9)
+    _, K, _ = O.round_congruent(r["U"], d["X"])
+    # the planted phase's own ambiguities (its constant offset aligned the same way)
+    _, Ktrue, _ = O.round_congruent(d["phi_true"], d["X"])
+    diff = K - Ktrue
+    assert np.all(diff == diff.flat[0])
+
+
+def test_best_shift_error_definition():
+    """E = Xu - (U + alpha) with alpha the least-squares shift (Sec. 4.5): E has zero mean, and
+    no other shift gives a smaller norm."""
+    rng = np.random.default_rng(5)
+    Xu = rng.standard_normal((20, 16)) * 5
+    U = Xu + 3.7 + 0.1 * rng.standard_normal(Xu.shape)
+    E = O.best_shift_error(U, Xu)
+    assert abs(E.mean()) < 1e-12
+    n0 = np.linalg.norm(E)
+    for s in (-1e-3, 1e-3):
+        assert np.linalg.norm(E - s) > n0
+
+
+# ------------------------------------------------------------------------------------------
 # Adjoint of the IRLS map: central differences of the oracle's own forward map
 # ------------------------------------------------------------------------------------------
 def _adjoint_case():
