@@ -35,7 +35,8 @@ __all__ = [
     "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
     "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
     "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "paper_cg_cap", "k_map",
-    "round_congruent",
+    "round_congruent", "schur_weights", "schur_matvec", "schur_rhs", "schur_recover_v",
+    "pcg_schur",
     "best_shift_error", "dense_operators", "Problem", "irls_adjoint",
 ]
 
@@ -252,6 +253,77 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
 
 
 # --------------------------------------------------------------------------------------------
+# U-only (Schur complement) form of the same linear system
+# --------------------------------------------------------------------------------------------
+# The V rows of the system of Sec. 3.1 give (D + 1/tau) V = (D U - G) / tau edge by edge, i.e.
+# V = (D U - G) / (1 + tau D).  Substituted into the U row:  S^T Om_v (S U - Gv) +
+# (U T - Gh) Om_h T^T = 0  with  Om = D / (1 + tau D)  per edge.
+def schur_weights(dv, dh, tau):
+    """Om = D / (1 + tau D) on the vertical and horizontal edges."""
+    return dv / (1.0 + tau * dv), dh / (1.0 + tau * dh)
+
+
+def schur_matvec(U, Ov, Oh):
+    """L_Om U = S^T (Om_v o S U) + (Om_h o U T) T^T."""
+    N, M = U.shape
+    return St_op(Ov * S_op(U), N) + Tt_op(Oh * T_op(U), M)
+
+
+def schur_rhs(Gv, Gh, Ov, Oh, N, M):
+    """f = S^T (Om_v o Gv) + (Om_h o Gh) T^T."""
+    return St_op(Ov * Gv, N) + Tt_op(Oh * Gh, M)
+
+
+def schur_recover_v(U, Gv, Gh, dv, dh, tau):
+    """V = (D U - G) / (1 + tau D), the V rows solved for the given U."""
+    return (S_op(U) - Gv) / (1.0 + tau * dv), (T_op(U) - Gh) / (1.0 + tau * dh)
+
+
+def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None):
+    """Alg. 2 on L_Om U = f from the warm start U0, preconditioned by the Laplacian block of
+    Sec. 3.3 (z = P_S [(P_S^T tau r P_T) / (lam_i + mu_j)] P_T^T, zero frequency dropped; Om <=
+    1/tau, so (1/tau) times the Laplacian is its upper bound).  Stops when ||r|| / ||f|| <= tol
+    or after cg_max products with L_Om.  Returns (U, iterations, relative residual, status)."""
+    N, M = f.shape
+    zeros_v, zeros_h = np.zeros((N - 1, M)), np.zeros((N, M - 1))
+
+    def prec(r):
+        return precond_apply((r, zeros_v, zeros_h), zeros_v, zeros_h, tau, basis_N, basis_M)[0]
+
+    def keep(a):
+        return a if storage is None else np.asarray(a, dtype=storage).astype(np.float64)
+
+    U = keep(np.array(U0, dtype=np.float64))
+    fnorm = float(np.linalg.norm(f))
+    r = f - schur_matvec(U, Ov, Oh)
+    rel = float(np.linalg.norm(r)) / fnorm if fnorm > 0 else 0.0
+    if fnorm == 0.0 or rel <= tol or cg_max <= 0:
+        return U, 0, rel, 0
+    r = keep(r)
+    z = keep(prec(r))
+    p = z
+    rho = float(np.vdot(r, z))
+    it = 0
+    while True:
+        q = schur_matvec(p, Ov, Oh)
+        pq = float(np.vdot(p, q))
+        if not (pq > 0.0 and rho > 0.0):
+            return U, it, rel, -5
+        alpha = rho / pq
+        U = keep(U + alpha * p)
+        r = keep(r - alpha * q)
+        it += 1
+        rel = float(np.linalg.norm(r)) / fnorm
+        if rel <= tol or it >= cg_max:
+            return U, it, rel, 0
+        z_new = keep(prec(r))
+        rho_new = float(np.vdot(r, z_new))
+        beta = (rho_new - float(np.vdot(r, z))) / rho if beta_rule == "pr" else rho_new / rho
+        rho, z = rho_new, z_new
+        p = keep(z_new + beta * p)
+
+
+# --------------------------------------------------------------------------------------------
 # Objectives: problem (main), F (soft constraints), F_delta, H_delta (problem alt1)
 # --------------------------------------------------------------------------------------------
 def l1_objective(U, Gv, Gh, Cv, Ch):
@@ -341,7 +413,8 @@ def paper_cg_cap(delta_rel, m_prev, raised_prev, eps_tol, alpha):
 
 def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
                 cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None,
-                cg_schedule="fixed", m0=5, eps_tol=1e-3, alpha=1.7, precond_rounding=None):
+                cg_schedule="fixed", m0=5, eps_tol=1e-3, alpha=1.7, precond_rounding=None,
+                system="full"):
     """Alg. 1 with Alg. 2 as the inner solver.
 
     cg_schedule "fixed": outer_iters IRLS iterations, every inner solve capped at cg_max.
@@ -355,7 +428,13 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
     (H_delta(x^k, W^k) at the iteration where the rule stopped the run), status.
     With ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
     ``storage`` and ``precond_rounding`` are passed to pcg (other valid floating-point executions;
-    the latter's seed advances with the outer iteration)."""
+    the latter's seed advances with the outer iteration).
+    system "full": Alg. 2 on the (U, Vv, Vh) system of Sec. 3.1 with the block-diagonal
+    preconditioner (the paper's method).  system "schur": Alg. 2 on the U-only system obtained
+    by eliminating V (pcg_schur), then V = (D U - G) / (1 + tau D); the same outer loop, stopping
+    rule on the U-only residual (with precond_rounding unsupported)."""
+    if system not in ("full", "schur"):
+        raise ValueError("system is 'full' or 'schur'")
     if cg_schedule not in ("fixed", "paper"):
         raise ValueError("cg_schedule is 'fixed' or 'paper'")
     pb = Problem(X, coherence, Cv, Ch, tau)
@@ -393,10 +472,17 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
             rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         st["h_before"].append(h_before)
         st["cg_cap"].append(cap)
-        pr = None if precond_rounding is None else (precond_rounding[0],
-                                                    precond_rounding[1] + 7919 * k)
-        (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
-                                      cg_tol, cap, beta_rule, storage, pr)
+        if system == "schur":
+            Ov, Oh = schur_weights(dv, dh, tau)
+            f = schur_rhs(pb.Gv, pb.Gh, Ov, Oh, N, M)
+            U, it, rel, s = pcg_schur(U, f, Ov, Oh, tau, pb.basis_N, pb.basis_M, cg_tol, cap,
+                                      beta_rule, storage)
+            Vv, Vh = schur_recover_v(U, pb.Gv, pb.Gh, dv, dh, tau)
+        else:
+            pr = None if precond_rounding is None else (precond_rounding[0],
+                                                        precond_rounding[1] + 7919 * k)
+            (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
+                                          cg_tol, cap, beta_rule, storage, pr)
         if s < 0:
             status = s
         elif it >= cap and cap >= cg_max and rel > cg_tol and status == 0:

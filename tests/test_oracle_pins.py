@@ -421,6 +421,64 @@ def test_schur_complement_equivalence():
     np.testing.assert_allclose(U_full - U_full.mean(), u - u.mean(), atol=1e-10)
 
 
+def test_schur_operators_equal_kronecker_forms():
+    """schur_matvec = D^T diag(Om) D and schur_rhs = D^T diag(Om) g with D = [I (x) S; T^T (x) I]
+    from the element definitions, Om = C^2 / (W + tau C^2) = D_w / (1 + tau D_w), and the V
+    recovered from U solves the V rows of the full system."""
+    N, M, tau = 6, 5, 1e-2
+    rng = np.random.default_rng(18)
+    pb = rand_problem(N, M, rng, tau)
+    Wv = rng.uniform(1e-3, 1.0, size=(N - 1, M))
+    Wh = rng.uniform(1e-3, 1.0, size=(N, M - 1))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+    Ov, Oh = O.schur_weights(dv, dh, tau)
+    np.testing.assert_allclose(Ov, pb.Cv ** 2 / (Wv + tau * pb.Cv ** 2), rtol=1e-13)
+    S, T, _ = O.dense_operators(N, M)
+    D = np.vstack([np.kron(np.eye(M), S), np.kron(T.T, np.eye(N))])
+    Om = np.concatenate([vecF(Ov), vecF(Oh)])
+    U = rng.standard_normal((N, M))
+    np.testing.assert_allclose(vecF(O.schur_matvec(U, Ov, Oh)), D.T @ (Om * (D @ vecF(U))),
+                               atol=1e-12)
+    g = np.concatenate([vecF(pb.Gv), vecF(pb.Gh)])
+    np.testing.assert_allclose(vecF(O.schur_rhs(pb.Gv, pb.Gh, Ov, Oh, N, M)), D.T @ (Om * g),
+                               atol=1e-12)
+    Vv, Vh = O.schur_recover_v(U, pb.Gv, pb.Gh, dv, dh, tau)
+    q = dense_A(N, M, dv, dh, tau) @ pack((U, Vv, Vh)) - pack(pb.b)
+    nu = N * M
+    assert np.abs(q[nu:]).max() < 1e-9 * np.abs(pack(pb.b)).max()
+
+
+def test_pcg_schur_matches_lstsq():
+    N, M, tau = 7, 6, 1e-2
+    rng = np.random.default_rng(19)
+    pb = rand_problem(N, M, rng, tau)
+    Wv = rng.uniform(1e-2, 1.0, size=(N - 1, M))
+    Wh = rng.uniform(1e-2, 1.0, size=(N, M - 1))
+    dv, dh = O.diag_d(pb.Cv, pb.Ch, Wv, Wh)
+    Ov, Oh = O.schur_weights(dv, dh, tau)
+    f = O.schur_rhs(pb.Gv, pb.Gh, Ov, Oh, N, M)
+    U, it, rel, st = O.pcg_schur(np.zeros((N, M)), f, Ov, Oh, tau, O.dct_basis(N), O.dct_basis(M),
+                                 1e-13, 500)
+    S, T, _ = O.dense_operators(N, M)
+    D = np.vstack([np.kron(np.eye(M), S), np.kron(T.T, np.eye(N))])
+    Om = np.concatenate([vecF(Ov), vecF(Oh)])
+    u = np.linalg.lstsq(D.T @ (Om[:, None] * D), vecF(f), rcond=None)[0].reshape((N, M), order="F")
+    assert st == 0 and rel <= 1e-13
+    np.testing.assert_allclose(U - U.mean(), u - u.mean(), atol=1e-9)
+
+
+def test_schur_irls_equals_full_irls_with_converged_solves():
+    """With every inner solve converged, the U-only form and the paper's (U, V) form follow the
+    same IRLS trajectory (the Schur complement is exact): same U, same objectives."""
+    d = synthetic.make_phase(20, 18, 3, ramp=10.0, n_bumps=2, noise=0.6, coherence=True)
+    kw = dict(tau=1e-2, delta=1e-2, outer_iters=5, cg_tol=1e-13, cg_max=5000)
+    full = O.irls_unwrap(d["X"], d["coherence"], **kw)
+    schur = O.irls_unwrap(d["X"], d["coherence"], system="schur", **kw)
+    np.testing.assert_allclose(schur["U"], full["U"], atol=1e-7)
+    np.testing.assert_allclose(schur["l1_obj"], full["l1_obj"], rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(schur["h_delta"], full["h_delta"], rtol=1e-8, atol=1e-9)
+
+
 # ------------------------------------------------------------------------------------------
 # Invariances
 # ------------------------------------------------------------------------------------------
