@@ -165,6 +165,9 @@ def main():
     ap.add_argument("--outer", type=int, default=OUTER,
                     help="IRLS iterations per unwrap (short profiling runs only; the benchmark "
                          "workload is 20); with --cg-schedule paper, the most it may take")
+    ap.add_argument("--system", default="full", choices=["full", "schur"],
+                    help="full: the paper's (U, V) system (the benchmark); schur: the U-only "
+                         "system left after eliminating V")
     ap.add_argument("--cg-schedule", default="fixed", choices=["fixed", "paper"],
                     help="fixed: every solve capped at 1000 CG iterations (the benchmark); paper: "
                          "the adaptive CG budget and IRLS stop of Sec. 4.3")
@@ -198,7 +201,7 @@ def main():
     flexible = 1 if prec == "bf16" else 0
     plan = irls.Plan(n, wd, tau=TAU, delta=DELTA, outer_iters=args.outer, cg_tol=CG_TOL,
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible,
-                     cg_schedule=args.cg_schedule)
+                     cg_schedule=args.cg_schedule, system=args.system)
     stream = torch.cuda.current_stream()
     U = torch.empty_like(X)
     for _ in range(args.warmup):
@@ -249,9 +252,17 @@ def main():
     live = {"direction_pap": cg_total * args.steps, "update": cg_total * args.steps,
             "dct_precond": (cg_total + outer_done) * args.steps,
             "reweight_residual": outer_done * args.steps}
-    bytes_px = {"direction_pap": 44.0, "reweight_residual": 56.0 + (2.0 if prec != "fp32" else 0),
-                "update": 68.0 + (2.0 if prec != "fp32" else 0) + (4.0 if flexible else 0)}
     folded = plan.folded
+    # bf16 copy of r_U written for the direct tensor-core forms (hi, plus lo in split precision)
+    emit = 0.0 if (prec == "fp32" or folded) else (4.0 if prec == "bf16x3" else 2.0)
+    if args.system == "schur":
+        # U-only kernels: direction reads z, p_old, D (2), writes p; update reads p, D (2), U,
+        # r and writes U, r; reweighting reads U, V (2), C (2), G (2) and writes W (2), D (2), r
+        bytes_px = {"direction_pap": 20.0, "reweight_residual": 48.0 + emit,
+                    "update": 28.0 + emit + (4.0 if flexible else 0)}
+    else:
+        bytes_px = {"direction_pap": 44.0, "reweight_residual": 56.0 + emit,
+                    "update": 68.0 + emit + (4.0 if flexible else 0)}
     # multiply-adds the preconditioner performs per application: four n^3 products in the direct
     # form; the folded form runs each stage as half-size products (half of that)
     dct_flops = 4.0 * n * wd * (n + wd) * (0.5 if folded else 1.0)
@@ -336,7 +347,8 @@ def main():
             f"f32+{prec}-tensor-core-dct", "data": "synthetic",
             "config": {"workload": workload_name(n, prec, wd), "size": [n, wd],
                        "outer_iters": args.outer, "outer_done": outer_done,
-                       "cg_schedule": args.cg_schedule, "delta": DELTA, "tau": TAU,
+                       "cg_schedule": args.cg_schedule, "system": args.system,
+                       "delta": DELTA, "tau": TAU,
                        "cg_tol": CG_TOL,
                        "precision": prec, "flexible_cg": bool(flexible),
                        "dct_form": "folded" if folded else ("direct" if prec != "fp32" else

@@ -64,6 +64,16 @@ extern "C" {
 #define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
 #define IRLS_CG_PAPER 1     /* the adaptive budget m_CG(k) and IRLS stop of Sec. 4.3            */
 
+/* Linear system of each outer step. */
+#define IRLS_SYS_FULL  0    /* the (U, Vv, Vh) system of Sec. 3.1 with the block-diagonal
+                             * preconditioner of Sec. 3.3 (the paper's method)                    */
+#define IRLS_SYS_SCHUR 1    /* the U-only system left after eliminating V (exact algebraically):
+                             * S^T Om_v (S U - Gv) + (U T - Gh) Om_h T^T = 0, Om = D/(1 + tau D),
+                             * Alg. 2 with the Laplacian block of Sec. 3.3 as the preconditioner,
+                             * then V = (D U - G)/(1 + tau D); the stopping rule uses the U-only
+                             * residual, so the trajectory differs from IRLS_SYS_FULL unless the
+                             * solves converge                                                    */
+
 #define IRLS_MAX_OUTER 256
 
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
@@ -74,7 +84,7 @@ typedef struct irls_batch_s* irls_batch; /* opaque: a batched solve of many imag
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
  * precision = IRLS_PREC_FP32, flexible_cg = 0, warm_start = 1, dct_form = IRLS_DCT_AUTO,
  * cg_schedule = IRLS_CG_FIXED, cg_m0 = 5, cg_eps_tol = 1e-3, cg_alpha = 1.7 (the values of
- * Sec. 4.3). */
+ * Sec. 4.3), system = IRLS_SYS_FULL. */
 typedef struct {
     float tau;          /* penalty tau of problem (soft constraints), Sec. 3.1; > 0            */
     float delta;        /* smoothing delta of F_delta, Sec. 3.1; > 0                           */
@@ -96,6 +106,8 @@ typedef struct {
     int   cg_m0;        /* m_CG(0) >= 1                                                         */
     float cg_eps_tol;   /* epsilon_tol of Sec. 4.3 (not NaN)                                   */
     float cg_alpha;     /* alpha > 1 of Sec. 4.3                                               */
+    int   system;       /* IRLS_SYS_FULL or IRLS_SYS_SCHUR (single-image solves; the batched and
+                           recorded forms return IRLS_ERR_UNSUPPORTED for IRLS_SYS_SCHUR)      */
 } irls_opts;
 
 /* Per-call statistics (host struct filled by the library). */

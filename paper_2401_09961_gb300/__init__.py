@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 
-from ._binding import (CG_SCHEDULES, DCT_FORMS, IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
+from ._binding import (CG_SCHEDULES, DCT_FORMS, SYSTEMS, IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
                        lib)
 
 __all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "round_congruent",
@@ -76,6 +76,8 @@ class Plan:
                 v = DCT_FORMS[v]
             if k == "cg_schedule" and isinstance(v, str):
                 v = CG_SCHEDULES[v]
+            if k == "system" and isinstance(v, str):
+                v = SYSTEMS[v]
             setattr(o, k, v)
         check(lib().irls_plan_set_opts(self.handle, ctypes.byref(o)), "irls_plan_set_opts")
         self.opts = o
@@ -132,14 +134,14 @@ class Plan:
 
 def unwrap(X, coherence=None, *, eps=1e-3, outer_iters=20, cg_tol=1e-6, tau=1e-2,
            cg_max_iter=1000, precision="fp32", flexible_cg=None, Cv=None, Ch=None,
-           return_stats=False, plan=None, cg_schedule="fixed"):
+           return_stats=False, plan=None, cg_schedule="fixed", system="full"):
     """Unwrap the wrapped phase X (H x W float32) with the L1 IRLS method.
 
     X and the optional coherence / Cv / Ch may be CUDA tensors (the result stays on the device)
     or host arrays / CPU tensors (they are copied to the current CUDA device and U is copied
     back).  eps is the smoothing delta of F_delta (Sec. 3.1).  cg_schedule "paper" runs the
     adaptive CG budget and IRLS stop of Sec. 4.3 (outer_iters then bounds the number of IRLS
-    iterations)."""
+    iterations); system "schur" solves the U-only system left after eliminating V."""
     torch = _torch()
     import numpy as np
     host = not (isinstance(X, torch.Tensor) and X.is_cuda)
@@ -160,7 +162,7 @@ def unwrap(X, coherence=None, *, eps=1e-3, outer_iters=20, cg_tol=1e-6, tau=1e-2
     if own:
         plan = Plan(H, W, tau=tau, delta=eps, outer_iters=outer_iters, cg_tol=cg_tol,
                     cg_max_iter=cg_max_iter, precision=precision, flexible_cg=flexible_cg,
-                    cg_schedule=cg_schedule)
+                    cg_schedule=cg_schedule, system=system)
     try:
         U, stats = plan.unwrap(Xd, dev(coherence), Cv=dev(Cv), Ch=dev(Ch))
     finally:

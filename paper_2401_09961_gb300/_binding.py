@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libirls.so")
 IRLS_MAX_OUTER = 256
 DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2}
 CG_SCHEDULES = {"fixed": 0, "paper": 1}
+SYSTEMS = {"full": 0, "schur": 1}
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
 STATUS = {
@@ -39,6 +40,7 @@ class Opts(ctypes.Structure):
         ("cg_m0", ctypes.c_int),
         ("cg_eps_tol", ctypes.c_float),
         ("cg_alpha", ctypes.c_float),
+        ("system", ctypes.c_int),
     ]
 
 
@@ -160,5 +162,7 @@ def default_opts(**kw):
             v = DCT_FORMS[v]
         if k == "cg_schedule" and isinstance(v, str):
             v = CG_SCHEDULES[v]
+        if k == "system" and isinstance(v, str):
+            v = SYSTEMS[v]
         setattr(o, k, v)
     return o

@@ -55,6 +55,7 @@ bool opts_valid(const irls_opts& o) {
     if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_BF16X3) return false;
     if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FOLDED) return false;
     if (o.cg_schedule != IRLS_CG_FIXED && o.cg_schedule != IRLS_CG_PAPER) return false;
+    if (o.system != IRLS_SYS_FULL && o.system != IRLS_SYS_SCHUR) return false;
     if (o.cg_schedule == IRLS_CG_PAPER &&
         (o.cg_m0 < 1 || !(o.cg_alpha > 1.f) || std::isnan(o.cg_eps_tol)))
         return false;
@@ -289,12 +290,15 @@ void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s) 
     size_t mark[2] = {0, 0};
     while (issued < a.cg_max) {
         const int n = std::min(kChunk, a.cg_max - issued);
+        const bool schur = p->opts.system == IRLS_SYS_SCHUR;
         for (int c = 0; c < n; ++c) {
             t0 = pf.begin(s);
-            ck(launch_direction_pap(p->P, a, st, p->partials, s));
+            if (schur) ck(launch_schur_direction(p->P, a, st, p->partials, s));
+            else ck(launch_direction_pap(p->P, a, st, p->partials, s));
             pf.end(PC_DIRECTION, t0, s);
             t0 = pf.begin(s);
-            ck(launch_update(p->P, a, st, p->partials, s));
+            if (schur) ck(launch_schur_update(p->P, a, st, p->partials, s));
+            else ck(launch_update(p->P, a, st, p->partials, s));
             pf.end(PC_UPDATE, t0, s);
             t0 = pf.begin(s);
             ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
@@ -351,9 +355,11 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
     bool raised = false;
     p->caps.assign(p->opts.outer_iters, 0);
     p->schedule_stop = 0;
+    const bool schur = p->opts.system == IRLS_SYS_SCHUR;
     for (int k = 0; k < p->opts.outer_iters; ++k) {
         t0 = pf.begin(s);
-        ck(launch_reweight_residual(p->P, a, st, p->partials, s));
+        if (schur) ck(launch_schur_reweight(p->P, a, st, p->partials, s));
+        else ck(launch_reweight_residual(p->P, a, st, p->partials, s));
         pf.end(PC_REWEIGHT, t0, s);
         StencilArgs ak = a;
         if (sched) {
@@ -387,6 +393,7 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
         pf.end(PC_DCT, t0, s);
         run_cg(p, ak, st, s);
         t0 = pf.begin(s);
+        if (schur) ck(launch_schur_recover_v(p->P, ak, s));
         ck(launch_finalize(p->P, ak, st, p->partials, s));
         pf.end(PC_FINALIZE, t0, s);
         if (tape) {
@@ -585,6 +592,7 @@ int irls_opts_default(irls_opts* o) {
     o->cg_m0 = 5;
     o->cg_eps_tol = 1e-3f;
     o->cg_alpha = 1.7f;
+    o->system = IRLS_SYS_FULL;
     return IRLS_OK;
 }
 
@@ -710,7 +718,8 @@ int irls_unwrap_forward_record(irls_plan p, const float* X, const float* coh, co
     *out = nullptr;
     if ((Cv == nullptr) != (Ch == nullptr)) return IRLS_ERR_ARG;
     // the adjoint differentiates through converged inner solves: no planned budgets
-    if (p->opts.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;
+    if (p->opts.cg_schedule != IRLS_CG_FIXED || p->opts.system != IRLS_SYS_FULL)
+        return IRLS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     irls_tape_s* t = new (std::nothrow) irls_tape_s();
     if (!t) return IRLS_ERR_OOM;
@@ -829,6 +838,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
     if (o.dct_form == IRLS_DCT_FOLDED) return IRLS_ERR_UNSUPPORTED;   // grouped form is direct
     if (o.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;  // images run in lockstep
+    if (o.system != IRLS_SYS_FULL) return IRLS_ERR_UNSUPPORTED;
     for (int t = 0; t < ntiles; ++t)
         if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
     irls_batch_s* b = new (std::nothrow) irls_batch_s();

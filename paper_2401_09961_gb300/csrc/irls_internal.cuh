@@ -192,6 +192,13 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
 // receives error flags; with reduce_rho the last GEMM also forms rho = r_U^T z_U + st->rz_v
 // and the next beta (Alg. 2).  With skip_if_done the launches return at once once CG stopped.
 void dct_release(DctPlan& d);
+cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
+                                  double* partials, cudaStream_t s);
+cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
+                                   double* partials, cudaStream_t s);
+cudaError_t launch_schur_update(const Planes& P, const StencilArgs& a, DevState* st,
+                                double* partials, cudaStream_t s);
+cudaError_t launch_schur_recover_v(const Planes& P, const StencilArgs& a, cudaStream_t s);
 cudaError_t launch_round_congruent(const float* U, const float* X, size_t n, DevState* st,
                                    double* partials, int max_blocks, float* Ur, int* K,
                                    cudaStream_t s);

@@ -858,6 +858,334 @@ __global__ void k_record_step(DevState* st) {
     st->outer = k + 1;
 }
 
+// ------------------------------------------------------------------------------------------
+// U-only (Schur complement) form of the same linear system.  The V rows of the system of
+// Sec. 3.1 give V = (D U - G) / (1 + tau D) edge by edge; the U row becomes
+//     L_Om U = f,   L_Om U = S^T (Om_v o S U) + (Om_h o U T) T^T,
+//     f = S^T (Om_v o Gv) + (Om_h o Gh) T^T,   Om = D / (1 + tau D)
+// solved by Alg. 2 with the Laplacian block of Sec. 3.3 as the preconditioner.  The planes dv,
+// dh keep D (Om is formed where it is used); the CG state and stopping rule are those of the
+// (U, V) form with r = r_U only (r_V, z_V and their products are zero).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float omega_of(float d, float tau) { return d / (1.f + tau * d); }
+
+// Start of an outer step: W = sqrt(C^2 V^2 + delta^2), D = C^2 / W, the Schur right-hand side
+// f and its norm, the initial residual r = f - L_Om U^k (warm start) or f (cold start), and
+// F_delta(x^k) (the same statistic as the (U, V) form).
+__device__ __forceinline__ void k_schur_reweight_body(Planes P, StencilArgs a, DevState* st,
+                                                      double* partials, const Blk& blk) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
+    const bool col = j < W, hh = j + 1 < W;
+    const float it = a.inv_tau, tau = a.tau, d2 = a.delta * a.delta;
+    const bool warm = a.warm_start != 0;
+    // vertical edge (i, j): omega and the edge terms Om (S U - Gv) and Om Gv
+    auto vedge = [&](int i, float& flux, float& fg) {
+        const size_t o = (size_t)i * ld + j;
+        const float cv = P.Cv[o], vv = P.Vv[o], gv = P.Gv[o];
+        const float wv = sqrtf(cv * cv * vv * vv + d2);
+        const float om = omega_of(cv * cv / wv, tau);
+        const float su = warm ? (P.U[o + ld] - P.U[o]) : 0.f;
+        flux = om * (su - gv);
+        fg = om * gv;
+    };
+    float rr = 0.f, bb = 0.f, fd = 0.f, su_r = 0.f;
+    float uc = col ? P.U[(size_t)i0 * ld + j] : 0.f;
+    float flux_up = 0.f, fg_up = 0.f;   // vertical edge (i - 1, j)
+    if (col && i0 > 0) vedge(i0 - 1, flux_up, fg_up);
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        const bool hv = i + 1 < H;
+        float vv = 0.f, vh = 0.f, cv = 0.f, ch = 0.f, gv = 0.f, gh = 0.f, un = 0.f;
+        if (col) {
+            vv = P.Vv[o]; vh = P.Vh[o]; cv = P.Cv[o]; ch = P.Ch[o]; gv = P.Gv[o]; gh = P.Gh[o];
+            if (hv) un = P.U[o + ld];
+        }
+        float ur = __shfl_down_sync(kFull, uc, 1);
+        if (lane == 31 && col && hh) ur = P.U[o + 1];
+        float wv = 0.f, wh = 0.f, dv = 0.f, dh = 0.f;
+        if (col && hv) { wv = sqrtf(cv * cv * vv * vv + d2); dv = cv * cv / wv; }
+        if (col && hh) { wh = sqrtf(ch * ch * vh * vh + d2); dh = ch * ch / wh; }
+        const float ov = omega_of(dv, tau), oh = omega_of(dh, tau);
+        const float sv = (col && hv && warm) ? (un - uc) : 0.f;
+        const float sh = (col && hh && warm) ? (ur - uc) : 0.f;
+        const float flux_v = (col && hv) ? ov * (sv - gv) : 0.f;
+        const float flux_h = (col && hh) ? oh * (sh - gh) : 0.f;
+        const float fgv = (col && hv) ? ov * gv : 0.f;
+        const float fgh = (col && hh) ? oh * gh : 0.f;
+        float flux_l = __shfl_up_sync(kFull, flux_h, 1);
+        float fg_l = __shfl_up_sync(kFull, fgh, 1);
+        if (lane == 0) {
+            flux_l = 0.f;
+            fg_l = 0.f;
+            if (col && j > 0) {
+                const float c = P.Ch[o - 1], v = P.Vh[o - 1], g = P.Gh[o - 1];
+                const float w = sqrtf(c * c * v * v + d2);
+                const float om = omega_of(c * c / w, tau);
+                const float s = warm ? (uc - P.U[o - 1]) : 0.f;
+                flux_l = om * (s - g);
+                fg_l = om * g;
+            }
+        }
+        if (col) {
+            // r = -(S^T flux_v + flux_h T^T),  f = S^T (Om Gv) + (Om Gh) T^T
+            const float ru = -(flux_up - flux_v + flux_l - flux_h);
+            const float fu = fg_up - fgv + fg_l - fgh;
+            P.Wv[o] = wv; P.Wh[o] = wh; P.dv[o] = dv; P.dh[o] = dh;
+            P.rU[o] = ru;
+            if (!warm) P.U[o] = 0.f;
+            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
+            rr += ru * ru;
+            su_r += ru;
+            bb += fu * fu;
+            // F_delta(x^k) with the edge residuals S U - V - G at the iterate
+            const float evk = hv ? (un - uc - vv - gv) : 0.f;
+            const float ehk = hh ? (ur - uc - vh - gh) : 0.f;
+            fd += wv + wh + 0.5f * it * (evk * evk + ehk * ehk);
+        }
+        flux_up = flux_v;
+        fg_up = fgv;
+        uc = un;
+    }
+    double v[4] = {(double)rr, (double)bb, (double)fd, (double)su_r}, tot[4];
+    if (grid_reduce<4>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[3], a.H, a.W);
+        st->rr = rr_range;
+        st->bb = tot[1];
+        st->rz_v = 0.0;
+        st->rz_old = 0.0;
+        st->rnorm_u = sqrt(tot[0]);
+        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
+        st->rel = rel;
+        st->iter = 0;
+        st->p_fresh = 1;
+        st->done = (rel * rel <= a.tol2 || a.cg_max <= 0 || st->bb <= 0.0) ? 1 : 0;
+        const int k = st->outer;
+        if (k < kMaxOuter) st->f_delta[k] = tot[2];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_schur_reweight(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_schur_reweight_body(P, a, st, partials, single_blk());
+}
+
+// p = z + beta p_old and p^T L_Om p = sum Om_v (S p)^2 + Om_h (p T)^2; alpha = rho / p^T L p.
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
+    const Blk blk = single_blk();
+    if (st->done) return;
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
+    const float tau = a.tau;
+    const int cur = st->pbuf, nxt = cur ^ 1;
+    const bool fresh = st->p_fresh != 0;
+    const float beta = fresh ? 0.f : (float)st->beta;
+    const float* __restrict__ pUo = P.pU[cur];
+    float* __restrict__ pUn = P.pU[nxt];
+    const float* __restrict__ zU = P.zU;
+    const float* __restrict__ Dv = P.dv;
+    const float* __restrict__ Dh = P.dh;
+    bool hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
+    auto dir_u = [&](size_t o, float (&pu)[4]) {
+        float z[4];
+        ld4(zU + o, z);
+        if (fresh) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pu[e] = z[e];
+        } else {
+            float q[4];
+            ld4(pUo + o, q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pu[e] = z[e] + beta * q[e];
+        }
+    };
+    float cu[4] = {0, 0, 0, 0}, nu[4] = {0, 0, 0, 0};
+    if (act) {
+        const size_t o = (size_t)i0 * ld + j0;
+        dir_u(o, cu);
+        if (i0 + 1 < H) dir_u(o + ld, nu);
+    }
+    float acc = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j0;
+        const bool hv = i + 1 < H;
+        float mu[4] = {0, 0, 0, 0}, dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0};
+        if (act) {
+            ld4(Dv + o, dv);
+            ld4(Dh + o, dh);
+            if (i + 1 < i1 && i + 2 < H) dir_u(o + 2 * (size_t)ld, mu);
+        }
+        float right = __shfl_down_sync(kFull, cu[0], 1);
+        if (lane == 31) {
+            right = 0.f;
+            if (act && j0 + kVec < W) {
+                const float z = zU[o + kVec];
+                right = fresh ? z : z + beta * pUo[o + kVec];
+            }
+        }
+        if (act) {
+            st4(pUn + o, cu);
+            const float pr[4] = {cu[1], cu[2], cu[3], right};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float yh = hh[e] ? (pr[e] - cu[e]) : 0.f;
+                const float yv = hv ? (nu[e] - cu[e]) : 0.f;
+                acc += omega_of(dv[e], tau) * yv * yv + omega_of(dh[e], tau) * yh * yh;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            cu[e] = nu[e];
+            nu[e] = mu[e];
+        }
+    }
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        st->pq = pq;
+        st->pbuf = nxt;
+        st->p_fresh = 0;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            st->alpha = 0.0;
+            if (st->rel > kBreakdownRel || !isfinite(pq)) st->status |= ST_BREAKDOWN;
+            st->done = 1;
+        } else {
+            st->alpha = st->rho / pq;
+        }
+    }
+}
+
+// U += alpha p, r -= alpha L_Om p, ||r||^2 (range part), r_new^T z_old for the flexible ratio.
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
+    const Blk blk = single_blk();
+    if (st->done) return;
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
+    const float tau = a.tau;
+    const int cur = st->pbuf;
+    const float alpha = (float)st->alpha;
+    const bool flex = a.flexible != 0;
+    const float* __restrict__ pU = P.pU[cur];
+    const float* __restrict__ Dv = P.dv;
+    const float* __restrict__ Dh = P.dh;
+    const float* __restrict__ Zu = P.zU;
+    float* __restrict__ U = P.U;
+    float* __restrict__ rU = P.rU;
+    bool hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
+    float cu[4] = {0, 0, 0, 0}, nu[4] = {0, 0, 0, 0};
+    float yvp[4] = {0, 0, 0, 0};   // Om_v (S p) on the vertical edge above
+    if (act) {
+        const size_t o = (size_t)i0 * ld + j0;
+        ld4(pU + o, cu);
+        if (i0 > 0) {
+            float q[4], d[4];
+            ld4(pU + o - ld, q);
+            ld4(Dv + o - ld, d);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) yvp[e] = omega_of(d[e], tau) * (cu[e] - q[e]);
+        }
+        if (i0 + 1 < H) ld4(pU + o + ld, nu);
+    }
+    float rr = 0.f, rzo = 0.f, su = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j0;
+        const bool hv = i + 1 < H;
+        float dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0}, u[4] = {0, 0, 0, 0};
+        float r0[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0}, mu[4] = {0, 0, 0, 0};
+        if (act) {
+            ld4(Dv + o, dv);
+            ld4(Dh + o, dh);
+            ld4(U + o, u);
+            ld4(rU + o, r0);
+            if (flex) ld4(Zu + o, z);
+            if (i + 1 < i1 && i + 2 < H) ld4(pU + o + 2 * (size_t)ld, mu);
+        }
+        float yv[4], yh[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) yv[e] = hv ? omega_of(dv[e], tau) * (nu[e] - cu[e]) : 0.f;
+        float right = __shfl_down_sync(kFull, cu[0], 1);
+        if (lane == 31) right = (act && j0 + kVec < W) ? pU[o + kVec] : 0.f;
+        const float pr[4] = {cu[1], cu[2], cu[3], right};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) yh[e] = hh[e] ? omega_of(dh[e], tau) * (pr[e] - cu[e]) : 0.f;
+        float left = __shfl_up_sync(kFull, yh[3], 1);
+        if (lane == 0)
+            left = (act && j0 > 0) ? omega_of(Dh[o - 1], tau) * (cu[0] - pU[o - 1]) : 0.f;
+        const float yl[4] = {left, yh[0], yh[1], yh[2]};
+        if (act) {
+            float n0[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                // (L_Om p) = S^T (Om_v S p) + (Om_h p T) T^T at this pixel
+                const float q = yvp[e] - yv[e] + yl[e] - yh[e];
+                u[e] += alpha * cu[e];
+                n0[e] = r0[e] - alpha * q;
+                rr += n0[e] * n0[e];
+                su += n0[e];
+                if (flex) rzo += n0[e] * z[e];
+            }
+            st4(U + o, u);
+            st4(rU + o, n0);
+            if (a.r16 != nullptr) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j0 + e < W) emit16(a.r16, a.r16lo, a.ld16, i, j0 + e, n0[e]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            yvp[e] = yv[e];
+            cu[e] = nu[e];
+            nu[e] = mu[e];
+        }
+    }
+    double v[3] = {(double)rr, (double)rzo, (double)su}, tot[3];
+    if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[2], a.H, a.W);
+        st->rr = rr_range;
+        st->rz_v = 0.0;
+        st->rz_old = tot[1];
+        st->rnorm_u = sqrt(tot[0]);
+        const int itn = st->iter + 1;
+        st->iter = itn;
+        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
+        st->rel = rel;
+        if (rel * rel <= a.tol2 || itn >= a.cg_max || !isfinite(rel)) st->done = 1;
+        if (!isfinite(rel)) st->status |= ST_NONFINITE;
+    }
+}
+
+// After the solve: V = (D U - G) / (1 + tau D) on every edge (the V rows of the system).
+__global__ void __launch_bounds__(kThreads)
+k_schur_recover_v(Planes P, StencilArgs a) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    if (j >= W) return;
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        const float u = P.U[o];
+        if (i + 1 < H) P.Vv[o] = (P.U[o + ld] - u - P.Gv[o]) / (1.f + a.tau * P.dv[o]);
+        if (j + 1 < W) P.Vh[o] = (P.U[o + 1] - u - P.Gh[o]) / (1.f + a.tau * P.dh[o]);
+    }
+}
+
 __global__ void k_prepare_matvec(DevState* st) {
     st->done = 0;
     st->iter = 0;
@@ -958,6 +1286,29 @@ cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState
 cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                           cudaStream_t s) {
     k_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
+                                  double* partials, cudaStream_t s) {
+    k_schur_reweight<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
+                                   double* partials, cudaStream_t s) {
+    k_schur_direction<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_update(const Planes& P, const StencilArgs& a, DevState* st,
+                                double* partials, cudaStream_t s) {
+    k_schur_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_recover_v(const Planes& P, const StencilArgs& a, cudaStream_t s) {
+    k_schur_recover_v<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a);
     return cudaGetLastError();
 }
 
