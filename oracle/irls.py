@@ -196,7 +196,7 @@ def _stored(v, storage):
 
 
 def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None,
-        precond_rounding=None):
+        precond_rounding=None, scalar_rounding=None):
     """Preconditioned CG (Alg. 2) on A x = b from the warm start x0.
 
     Stops when ||r|| / ||b|| <= tol or after cg_max products with A.  ``beta_rule`` 'fr' is the
@@ -207,7 +207,14 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
     executions spread; the arithmetic itself stays float64.  ``precond_rounding`` (None or
     (rel, seed)) multiplies each preconditioner output by 1 + rel * N(0, 1) elementwise (seeded):
     a model of the preconditioner evaluated at finite precision, for the same purpose.
+    ``scalar_rounding`` (None or (rel, seed)) multiplies alpha and beta by 1 + rel * N(0, 1): a
+    model of the inner products summed from float32 partial sums.
     Returns (x, iterations, final relative residual, status); status -5 flags a breakdown."""
+    rng_sc = None if scalar_rounding is None else np.random.default_rng(scalar_rounding[1])
+
+    def scal(v):
+        return v if rng_sc is None else v * (1.0 + scalar_rounding[0] * rng_sc.standard_normal())
+
     if precond_rounding is not None:
         rel_pc, seed_pc = precond_rounding
         rng_pc = np.random.default_rng(seed_pc)
@@ -234,7 +241,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
         pq = _dot(p, q)
         if not (pq > 0.0 and rho > 0.0):
             return x, it, rel, -5
-        alpha = rho / pq
+        alpha = scal(rho / pq)
         x = _stored(_axpy(alpha, p, x), storage)
         r = _stored(_axpy(-alpha, q, r), storage)
         it += 1
@@ -244,9 +251,9 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
         z_new = _stored(precond(r), storage)
         rho_new = _dot(r, z_new)
         if beta_rule == "pr":
-            beta = (rho_new - _dot(r, z)) / rho
+            beta = scal((rho_new - _dot(r, z)) / rho)
         else:
-            beta = rho_new / rho
+            beta = scal(rho_new / rho)
         rho = rho_new
         z = z_new
         p = _stored(tuple(zi + beta * pi for zi, pi in zip(z_new, p)), storage)
@@ -279,12 +286,19 @@ def schur_recover_v(U, Gv, Gh, dv, dh, tau):
     return (S_op(U) - Gv) / (1.0 + tau * dv), (T_op(U) - Gh) / (1.0 + tau * dh)
 
 
-def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None):
+def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None,
+              scalar_rounding=None):
     """Alg. 2 on L_Om U = f from the warm start U0, preconditioned by the Laplacian block of
     Sec. 3.3 (z = P_S [(P_S^T tau r P_T) / (lam_i + mu_j)] P_T^T, zero frequency dropped; Om <=
     1/tau, so (1/tau) times the Laplacian is its upper bound).  Stops when ||r|| / ||f|| <= tol
-    or after cg_max products with L_Om.  Returns (U, iterations, relative residual, status)."""
+    or after cg_max products with L_Om.  storage and scalar_rounding as in pcg.
+    Returns (U, iterations, relative residual, status)."""
     N, M = f.shape
+    rng_sc = None if scalar_rounding is None else np.random.default_rng(scalar_rounding[1])
+
+    def scal(v):
+        return v if rng_sc is None else v * (1.0 + scalar_rounding[0] * rng_sc.standard_normal())
+
     zeros_v, zeros_h = np.zeros((N - 1, M)), np.zeros((N, M - 1))
 
     def prec(r):
@@ -309,7 +323,7 @@ def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr",
         pq = float(np.vdot(p, q))
         if not (pq > 0.0 and rho > 0.0):
             return U, it, rel, -5
-        alpha = rho / pq
+        alpha = scal(rho / pq)
         U = keep(U + alpha * p)
         r = keep(r - alpha * q)
         it += 1
@@ -318,7 +332,7 @@ def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr",
             return U, it, rel, 0
         z_new = keep(prec(r))
         rho_new = float(np.vdot(r, z_new))
-        beta = (rho_new - float(np.vdot(r, z))) / rho if beta_rule == "pr" else rho_new / rho
+        beta = scal((rho_new - float(np.vdot(r, z))) / rho if beta_rule == "pr" else rho_new / rho)
         rho, z = rho_new, z_new
         p = keep(z_new + beta * p)
 
@@ -414,7 +428,7 @@ def paper_cg_cap(delta_rel, m_prev, raised_prev, eps_tol, alpha):
 def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
                 cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None,
                 cg_schedule="fixed", m0=5, eps_tol=1e-3, alpha=1.7, precond_rounding=None,
-                system="full"):
+                system="full", scalar_rounding=None, cg_caps=None):
     """Alg. 1 with Alg. 2 as the inner solver.
 
     cg_schedule "fixed": outer_iters IRLS iterations, every inner solve capped at cg_max.
@@ -427,8 +441,10 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
     each solve), delta_rel (Delta_{k-1,k} for k >= 1, "paper" only), schedule_stop and h_stop
     (H_delta(x^k, W^k) at the iteration where the rule stopped the run), status.
     With ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
-    ``storage`` and ``precond_rounding`` are passed to pcg (other valid floating-point executions;
-    the latter's seed advances with the outer iteration).
+    ``storage``, ``precond_rounding`` and ``scalar_rounding`` are passed to pcg (other valid
+    floating-point executions; the seeds advance with the outer iteration).  ``cg_caps`` (a list)
+    caps solve k at cg_caps[k] (with cg_tol = 0: exactly that many iterations), to replay another
+    execution's stopping decisions.
     system "full": Alg. 2 on the (U, Vv, Vh) system of Sec. 3.1 with the block-diagonal
     preconditioner (the paper's method).  system "schur": Alg. 2 on the U-only system obtained
     by eliminating V (pcg_schur), then V = (D U - G) / (1 + tau D); the same outer loop, stopping
@@ -454,7 +470,7 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
         Wv, Wh = reweight(Vv, Vh, pb.Cv, pb.Ch, delta)
         dv, dh = diag_d(pb.Cv, pb.Ch, Wv, Wh)
         h_before = H_delta_value(U, Vv, Vh, Wv, Wh, pb.Gv, pb.Gh, pb.Cv, pb.Ch, tau, delta)
-        cap = cg_max
+        cap = cg_max if cg_caps is None else cg_caps[k]
         if cg_schedule == "paper":
             if k >= 1:
                 # Delta_{k-1,k} = (H(x^k, W^{k-1}) - H(x^k, W^k)) / H(x^k, W^{k-1})
@@ -472,17 +488,19 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
             rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         st["h_before"].append(h_before)
         st["cg_cap"].append(cap)
+        sr = None if scalar_rounding is None else (scalar_rounding[0],
+                                                   scalar_rounding[1] + 7919 * k)
         if system == "schur":
             Ov, Oh = schur_weights(dv, dh, tau)
             f = schur_rhs(pb.Gv, pb.Gh, Ov, Oh, N, M)
             U, it, rel, s = pcg_schur(U, f, Ov, Oh, tau, pb.basis_N, pb.basis_M, cg_tol, cap,
-                                      beta_rule, storage)
+                                      beta_rule, storage, sr)
             Vv, Vh = schur_recover_v(U, pb.Gv, pb.Gh, dv, dh, tau)
         else:
             pr = None if precond_rounding is None else (precond_rounding[0],
                                                         precond_rounding[1] + 7919 * k)
             (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
-                                          cg_tol, cap, beta_rule, storage, pr)
+                                          cg_tol, cap, beta_rule, storage, pr, sr)
         if s < 0:
             status = s
         elif it >= cap and cap >= cg_max and rel > cg_tol and status == 0:

@@ -421,7 +421,7 @@ struct irls_batch_s {
     std::vector<TileRec> recs;
     TileRec* d_recs = nullptr;
     DevState* states = nullptr;
-    int total_strip = 0, total_vec = 0;
+    int total_strip = 0, total_vec = 0, total_upd = 0;
     BatchDctPlan dct;
     int* d_count = nullptr;          // device, 2 slots
     int* h_count = nullptr;          // pinned, 2 slots
@@ -457,7 +457,7 @@ void destroy_batch(irls_batch_s* b) {
 void issue_chunk(irls_batch_s* b, int n, int slot, cudaStream_t s) {
     for (int c = 0; c < n; ++c) {
         ck(launch_direction_batched(b->d_recs, b->T, b->total_vec, s));
-        ck(launch_update_batched(b->d_recs, b->T, b->total_vec, s));
+        ck(launch_update_batched(b->d_recs, b->T, b->total_upd, s));
         ck(batch_dct_apply(b->dct, s));
     }
     ck(launch_count_active(b->states, b->T, b->d_count + slot, s));
@@ -905,7 +905,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
         }
         ck(batch_dct_setup(b->dct, H, W, T, o.precision, o.tau, o.flexible_cg, b->mem + dct_off,
                            rU.data(), zU.data(), b->ld.data(), b->states, parts.data()));
-        int sblk = 0, vblk = 0;
+        int sblk = 0, vblk = 0, ublk = 0;
         for (int t = 0; t < T; ++t) {
             TileRec& r = b->recs[t];
             StencilArgs& a = r.a;
@@ -922,14 +922,17 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             a.r16lo = b->dct.split ? b->dct.r16lo[t] : nullptr;
             a.ld16 = b->dct.ld16[t];
             strip_dims(H[t], W[t], r.sgx, r.sgy);
-            vec_dims(H[t], W[t], r.vgx, r.vgy);
+            vec_dims(H[t], W[t], r.vgx, r.vgy, r.ugy);
             r.sblk0 = sblk;
             r.vblk0 = vblk;
+            r.ublk0 = ublk;
             sblk += r.sgx * r.sgy;
             vblk += r.vgx * r.vgy;
+            ublk += r.vgx * r.ugy;
         }
         b->total_strip = sblk;
         b->total_vec = vblk;
+        b->total_upd = ublk;
         ck(cudaMemcpy(b->d_recs, b->recs.data(), (size_t)T * sizeof(TileRec), cudaMemcpyHostToDevice));
         ck(cudaHostAlloc(&b->h_count, 2 * sizeof(int), cudaHostAllocDefault));
         for (auto& e : b->ev) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

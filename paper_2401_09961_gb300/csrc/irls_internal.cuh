@@ -120,7 +120,8 @@ struct TileRec {
     const float* X;
     const float* coh;
     int sblk0, sgx, sgy;
-    int vblk0, vgx, vgy;
+    int vblk0, vgx, vgy;       // direction kernel's blocks
+    int ublk0, ugy;            // update kernel's blocks (same columns, its own rows per block)
 };
 
 // Tensor-core preconditioner of a batched solve: per-stage device arrays of grouped-GEMM
@@ -176,7 +177,7 @@ cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float*
 // batched launches over a device array of TileRec (one launch for all images; images whose CG
 // run has stopped return at once)
 void strip_dims(int H, int W, int& gx, int& gy);
-void vec_dims(int H, int W, int& gx, int& gy);
+void vec_dims(int H, int W, int& gx, int& gy_dir, int& gy_upd);
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);

@@ -231,7 +231,11 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
 // values stay zero) and only the edge masks hh[] exclude the edges that do not exist.
 // ------------------------------------------------------------------------------------------
 constexpr int kVec = 4;
-constexpr int kVRows = 16;
+// rows per block of the float4-lane kernels, measured at 4096 x 4096 (16, 24 and 32 tried):
+// direction 24, update 32; the U-only kernels 24
+constexpr int kDirRows = 24;
+constexpr int kUpdRows = 32;
+constexpr int kSchurRows = 24;
 
 __device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4]) {
     const float4 t = *reinterpret_cast<const float4*>(p);
@@ -746,20 +750,27 @@ k_adj_final(Planes P, StencilArgs a, const float* __restrict__ Gbv, const float*
 // binary search over the images' first-block indices and runs the single-image body with its
 // own coordinates, state and scratch.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int find_tile(const TileRec* __restrict__ r, int T, int bid, bool vec) {
+// grid of a batched launch: the strip kernels, the direction kernel, the update kernel
+enum GridKind : int { GK_STRIP = 0, GK_DIR = 1, GK_UPD = 2 };
+
+__device__ __forceinline__ int grid_blk0(const TileRec& r, int kind) {
+    return kind == GK_STRIP ? r.sblk0 : (kind == GK_DIR ? r.vblk0 : r.ublk0);
+}
+
+__device__ __forceinline__ int find_tile(const TileRec* __restrict__ r, int T, int bid, int kind) {
     int lo = 0, hi = T - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int b0 = vec ? r[mid].vblk0 : r[mid].sblk0;
-        if (b0 <= bid) lo = mid; else hi = mid - 1;
+        if (grid_blk0(r[mid], kind) <= bid) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ Blk tile_blk(const TileRec& r, int bid, bool vec) {
+__device__ __forceinline__ Blk tile_blk(const TileRec& r, int bid, int kind) {
     Blk b;
-    const int gx = vec ? r.vgx : r.sgx, gy = vec ? r.vgy : r.sgy;
-    const int local = bid - (vec ? r.vblk0 : r.sblk0);
+    const int gx = kind == GK_STRIP ? r.sgx : r.vgx;
+    const int gy = kind == GK_STRIP ? r.sgy : (kind == GK_DIR ? r.vgy : r.ugy);
+    const int local = bid - grid_blk0(r, kind);
     b.bx = local % gx;
     b.by = local / gx;
     b.nblk = (unsigned)(gx * gy);
@@ -768,41 +779,41 @@ __device__ __forceinline__ Blk tile_blk(const TileRec& r, int bid, bool vec) {
 }
 
 __global__ void __launch_bounds__(kThreads) kb_init(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
     k_init_body(r.X, r.coh, nullptr, nullptr, nullptr, nullptr, nullptr, r.P, r.a, r.st,
-                tile_blk(r, blockIdx.x, false));
+                tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_bnorm(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
-    k_bnorm_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
+    k_bnorm_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_reweight(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
-    k_reweight_residual_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
+    k_reweight_residual_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
 template <int ROWS>
 __global__ void __launch_bounds__(kThreads) kb_direction(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, true)];
-    k_direction_pap_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, true));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_DIR)];
+    k_direction_pap_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_DIR));
 }
 
 template <int ROWS>
 __global__ void __launch_bounds__(kThreads) kb_update(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, true)];
-    k_update_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, true));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_UPD)];
+    k_update_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_finalize(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
-    k_finalize_reduce_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, false));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
+    k_finalize_reduce_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_subtract_mean(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, false)];
-    k_subtract_mean_body(r.P.U, r.a.H, r.a.W, r.a.ld, r.st, tile_blk(r, blockIdx.x, false));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
+    k_subtract_mean_body(r.P.U, r.a.H, r.a.W, r.a.ld, r.st, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
 // number of images whose CG run has not stopped
@@ -1196,8 +1207,8 @@ __global__ void k_prepare_matvec(DevState* st) {
 
 dim3 strip_grid(int H, int W) { return dim3((W + kThreads - 1) / kThreads, (H + kRows - 1) / kRows); }
 
-dim3 vec_grid(int H, int W) {
-    return dim3((W + kThreads * kVec - 1) / (kThreads * kVec), (H + kVRows - 1) / kVRows);
+dim3 vec_grid(int H, int W, int rows) {
+    return dim3((W + kThreads * kVec - 1) / (kThreads * kVec), (H + rows - 1) / rows);
 }
 
 }  // namespace
@@ -1208,10 +1219,11 @@ void strip_dims(int H, int W, int& gx, int& gy) {
     gy = (int)g.y;
 }
 
-void vec_dims(int H, int W, int& gx, int& gy) {
-    dim3 g = vec_grid(H, W);
+void vec_dims(int H, int W, int& gx, int& gy_dir, int& gy_upd) {
+    dim3 g = vec_grid(H, W, kDirRows);
     gx = (int)g.x;
-    gy = (int)g.y;
+    gy_dir = (int)g.y;
+    gy_upd = (int)vec_grid(H, W, kUpdRows).y;
 }
 
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
@@ -1230,12 +1242,12 @@ cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total, cudaS
 }
 
 cudaError_t launch_direction_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_direction<kVRows><<<total, kThreads, 0, s>>>(recs, T);
+    kb_direction<kDirRows><<<total, kThreads, 0, s>>>(recs, T);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_update<kVRows><<<total, kThreads, 0, s>>>(recs, T);
+    kb_update<kUpdRows><<<total, kThreads, 0, s>>>(recs, T);
     return cudaGetLastError();
 }
 
@@ -1253,7 +1265,7 @@ cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStr
 }
 
 int stencil_grid_blocks(int H, int W) {
-    dim3 g = strip_grid(H, W), v = vec_grid(H, W);
+    dim3 g = strip_grid(H, W), v = vec_grid(H, W, std::min({kDirRows, kUpdRows, kSchurRows}));
     return (int)std::max(g.x * g.y, v.x * v.y);
 }
 
@@ -1279,13 +1291,13 @@ cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevS
 
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
                                  double* partials, cudaStream_t s) {
-    k_direction_pap<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_direction_pap<kDirRows><<<vec_grid(a.H, a.W, kDirRows), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                           cudaStream_t s) {
-    k_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_update<kUpdRows><<<vec_grid(a.H, a.W, kUpdRows), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
@@ -1297,13 +1309,15 @@ cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevStat
 
 cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
                                    double* partials, cudaStream_t s) {
-    k_schur_direction<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_schur_direction<kSchurRows><<<vec_grid(a.H, a.W, kSchurRows), kThreads, 0, s>>>(P, a, st,
+                                                                                      partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_schur_update(const Planes& P, const StencilArgs& a, DevState* st,
                                 double* partials, cudaStream_t s) {
-    k_schur_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    k_schur_update<kSchurRows><<<vec_grid(a.H, a.W, kSchurRows), kThreads, 0, s>>>(P, a, st,
+                                                                                   partials);
     return cudaGetLastError();
 }
 
@@ -1395,7 +1409,7 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
     b.r16lo = nullptr;
     b.cg_max = 1 << 30;
     b.tol2 = -1.0;
-    k_update<kVRows><<<vec_grid(a.H, a.W), kThreads, 0, s>>>(P, b, st, partials);
+    k_update<kUpdRows><<<vec_grid(a.H, a.W, kUpdRows), kThreads, 0, s>>>(P, b, st, partials);
     return cudaGetLastError();
 }
 

@@ -81,7 +81,8 @@ def oracle_with_envelope(X, coh, kw, Cv=None, Ch=None):
     """The oracle's result plus the spread between equally valid floating-point executions of
     the same algorithm: the algebraically identical Polak-Ribiere ratio instead of the
     Fletcher-Reeves one of Alg. 2, the CG vectors stored in float32 (the library's storage type,
-    arithmetic still float64), and the weights perturbed at float32 level (relative 1e-7).
+    arithmetic still float64), CG's scalars perturbed at the level of float32 partial sums, and
+    the weights perturbed at float32 level (relative 1e-7).
     Where the truncated CG solves leave U weakly determined this spread is what any float32
     trajectory can promise; where it is small the 1e-3 rad bar applies unchanged."""
     base = O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, **kw)
@@ -89,6 +90,11 @@ def oracle_with_envelope(X, coh, kw, Cv=None, Ch=None):
     runs = [O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, beta_rule="pr", **kw),
             O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, **kw),
             O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, beta_rule="pr", **kw)]
+    # CG's scalars from inner products summed out of float32 partial sums (relative 1e-7 and
+    # 1e-6): on ill-conditioned solves this moves the iteration at which ||r|| crosses cg_tol
+    for rel, sd in ((1e-7, 1), (1e-6, 2)):
+        runs.append(O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32,
+                                  scalar_rounding=(rel, sd), **kw))
     for s in (0, 1):
         rng = np.random.default_rng(100 + s)
         if Cv is not None:
