@@ -448,15 +448,17 @@ __device__ __forceinline__ void scr_put(WarpScratch& s, const float (&v)[32]) {
 }
 
 // The block in `s` as bf16 (hi) and, with a lo plane, bf16(x - hi): two rows per instruction,
-// each lane one bf16 pair, row r of the block at element offset row_off(r) + col0.
+// each lane one bf16 pair, row r of the block at element offset row_off(r) + col0; rows at or
+// beyond nrows are not written.
 template <typename RowOff>
 __device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void* lo, int col0,
-                                            RowOff row_off) {
+                                            RowOff row_off, int nrows = 32) {
     const int lane = threadIdx.x & 31;
     const int rsub = lane >> 4, col = 2 * (lane & 15);
 #pragma unroll 4
     for (int rr = 0; rr < 32; rr += 2) {
         const int row = rr + rsub;
+        if (row >= nrows) continue;
         const float x0 = s.v[row][col], x1 = s.v[row][col + 1];
         const size_t off = row_off(row) + col0 + col;
         const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
@@ -470,22 +472,37 @@ __device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void
 }
 
 // The block in `s` as float32 rows at out + row_off(r) + col0 (four rows per instruction, one
-// float4 per lane); with rU, adds rU . z over the block to `part`.
+// float4 per lane); with rU, adds rU . z over the block to `part`.  Only rows < nrows and block
+// columns in [c_lo, c_hi) are written.  row_off(r) must be a multiple of 4 floats; groups that
+// are partial, or not 16-byte aligned (col0 not a multiple of 4: the mirrored columns of an
+// image whose width is not a multiple of 4), go element by element.
 template <typename RowOff>
 __device__ __forceinline__ void scr_store32(const WarpScratch& s, float* out, const float* rU,
-                                            int col0, RowOff row_off, float& part) {
+                                            int col0, RowOff row_off, float& part, int nrows = 32,
+                                            int c_lo = 0, int c_hi = 32) {
     const int lane = threadIdx.x & 31;
     const int rsub = lane >> 3, col = 4 * (lane & 7);
+    const bool full = (col0 & 3) == 0 && col >= c_lo && col + 4 <= c_hi;
 #pragma unroll 2
     for (int rr = 0; rr < 32; rr += 4) {
         const int row = rr + rsub;
-        const float4 z = make_float4(s.v[row][col], s.v[row][col + 1], s.v[row][col + 2],
-                                     s.v[row][col + 3]);
+        if (row >= nrows) continue;
         const size_t off = row_off(row) + col0 + col;
-        *reinterpret_cast<float4*>(out + off) = z;
-        if (rU) {
-            const float4 x = *reinterpret_cast<const float4*>(rU + off);
-            part += x.x * z.x + x.y * z.y + x.z * z.z + x.w * z.w;
+        if (full) {
+            const float4 z = make_float4(s.v[row][col], s.v[row][col + 1], s.v[row][col + 2],
+                                         s.v[row][col + 3]);
+            *reinterpret_cast<float4*>(out + off) = z;
+            if (rU) {
+                const float4 x = *reinterpret_cast<const float4*>(rU + off);
+                part += x.x * z.x + x.y * z.y + x.z * z.z + x.w * z.w;
+            }
+        } else {
+            for (int e = 0; e < 4; ++e) {
+                if (col + e < c_lo || col + e >= c_hi) continue;
+                const float z = s.v[row][col + e];
+                out[off + e] = z;
+                if (rU) part += rU[off + e] * z;
+            }
         }
     }
 }
@@ -512,8 +529,10 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
                 const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
-                pl[t] = a + b;
-                mi[t] = a - b;
+                // columns beyond the half side (padding of a ragged half) are zero
+                const bool ok = nb + t < ep.vn;
+                pl[t] = ok ? a + b : 0.f;
+                mi[t] = ok ? a - b : 0.f;
             }
             scr_put(s, pl);
             scr_store16(s, ep.C, ep.C_lo, nb, rows);
@@ -529,11 +548,13 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 pl[t] = a + b;
                 mi[t] = a - b;
             }
+            // rows at or beyond the half side (padding) have no mirror partner: not written
+            const int nr = min(max(ep.vm - m0w, 0), 32);
             scr_put(s, pl);
-            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows, nr);
             scr_put(s, mi);
             const int mr = ep.mrows - 1 - m0w;
-            scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; });
+            scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; }, nr);
         } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
             uint32_t r1[32];
             tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
@@ -545,10 +566,14 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 mi[t] = __uint_as_float(r[31 - t]) - __uint_as_float(r1[31 - t]);     // mb + t
             }
             const float* rr = EPI == UE_UNFOLDZ_RHO ? ep.rU : nullptr;
+            // rows beyond the image and columns beyond the half side (padding) are not written;
+            // the mirrored block holds column nb + t at position 31 - t
+            const int nr = min(max(ep.vm - m0w, 0), 32);
+            const int nc = min(max(ep.vn - nb, 0), 32);
             scr_put(s, pl);
-            scr_store32(s, static_cast<float*>(ep.C), rr, nb, rows, part);
+            scr_store32(s, static_cast<float*>(ep.C), rr, nb, rows, part, nr, 0, nc);
             scr_put(s, mi);
-            scr_store32(s, static_cast<float*>(ep.C), rr, mb, rows, part);
+            scr_store32(s, static_cast<float*>(ep.C), rr, mb, rows, part, nr, 32 - nc, 32);
         } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16 || EPI == UE_EIG16_RHO) {
             float v[32];
 #pragma unroll
@@ -1302,50 +1327,79 @@ __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bf
 // Even / odd halves of the DCT basis of side n (n even), h = n / 2:
 //   Pe[a][b] = P[a][2b], Po[a][b] = P[a][2b+1] (a, b < h), their transposes, and the eigenvalues
 //   permuted to (even indices, odd indices).  P[n-1-a][k] = (-1)^k P[a][k] makes these enough.
+// Stored hp x hp (hp >= h, pitch hp) with zeros outside the h x h block; lamP[par * hp + b].
 __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat16* PeT,
                                __nv_bfloat16* PoT, __nv_bfloat16* Pelo, __nv_bfloat16* Polo,
-                               __nv_bfloat16* PeTlo, __nv_bfloat16* PoTlo, float* lamP, int n) {
+                               __nv_bfloat16* PeTlo, __nv_bfloat16* PoTlo, float* lamP, int n,
+                               int hp) {
     const int h = n / 2;
-    const size_t total = (size_t)h * h;
+    const size_t total = (size_t)hp * hp;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
-        const int a = (int)(t / h), b = (int)(t % h);
+        const int a = (int)(t / hp), b = (int)(t % hp);
         for (int par = 0; par < 2; ++par) {
             const int k = 2 * b + par;
-            const long long mm = ((long long)(2 * a + 1) * k) % (4LL * n);
-            const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
-            const double v = ck * cospi((double)mm / (2.0 * n));
+            double v = 0.0;
+            if (a < h && b < h) {
+                const long long mm = ((long long)(2 * a + 1) * k) % (4LL * n);
+                const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+                v = ck * cospi((double)mm / (2.0 * n));
+            }
             const __nv_bfloat16 hv = __double2bfloat16(v);
             const __nv_bfloat16 lv = __double2bfloat16(v - (double)__bfloat162float(hv));
             __nv_bfloat16* P = par ? Po : Pe;
             __nv_bfloat16* PT = par ? PoT : PeT;
-            P[(size_t)a * h + b] = hv;
-            PT[(size_t)b * h + a] = hv;
+            P[(size_t)a * hp + b] = hv;
+            PT[(size_t)b * hp + a] = hv;
             __nv_bfloat16* Pl = par ? Polo : Pelo;
             __nv_bfloat16* PTl = par ? PoTlo : PeTlo;
             if (Pl) {
-                Pl[(size_t)a * h + b] = lv;
-                PTl[(size_t)b * h + a] = lv;
+                Pl[(size_t)a * hp + b] = lv;
+                PTl[(size_t)b * hp + a] = lv;
             }
         }
         if (a == 0) {
             for (int par = 0; par < 2; ++par) {
-                const double sn = sinpi((double)(2 * b + par) / (2.0 * n));
-                lamP[par * h + b] = (float)(4.0 * sn * sn);
+                double lam = 0.0;
+                if (b < h) {
+                    const double sn = sinpi((double)(2 * b + par) / (2.0 * n));
+                    lam = 4.0 * sn * sn;
+                }
+                lamP[par * hp + b] = (float)lam;
             }
         }
     }
 }
 
 // Folded residual: Re[i][j] = r[i][j] + r[i][W-1-j], Ro[i][j] = r[i][j] - r[i][W-1-j] (j < W/2),
-// each split into bf16 hi + lo.  Four columns per thread: the float4 at j and the float4 ending
-// at W-1-j (reversed); W is a multiple of 256 and the pitch a multiple of 4 floats.
-__global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W,
+// each split into bf16 hi + lo, pitch ldo (columns W/2 .. ldo-1 are left alone: zero).  W a
+// multiple of 8: four columns per thread, the float4 at j and the float4 ending at W-1-j
+// (reversed; the pitch ld is a multiple of 4 floats); otherwise one column per thread.
+__global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W, int ldo,
                          __nv_bfloat16* __restrict__ Re, __nv_bfloat16* __restrict__ Relo,
                          __nv_bfloat16* __restrict__ Ro, __nv_bfloat16* __restrict__ Rolo,
                          const DevState* st, int skip_if_done) {
     if (skip_if_done && st->done) return;
-    const int h = W / 2, h4 = h / 4;
+    const int h = W / 2;
+    if (W % 8 != 0) {
+        const size_t total = (size_t)H * h;
+        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+             t += (size_t)gridDim.x * blockDim.x) {
+            const int i = (int)(t / h), j = (int)(t % h);
+            const float a = rU[(size_t)i * ld + j], b = rU[(size_t)i * ld + (W - 1 - j)];
+            const float se = a + b, so = a - b;
+            const __nv_bfloat16 eh = __float2bfloat16_rn(se), oh = __float2bfloat16_rn(so);
+            const size_t off = (size_t)i * ldo + j;
+            Re[off] = eh;
+            Ro[off] = oh;
+            if (Relo) {
+                Relo[off] = __float2bfloat16_rn(se - __bfloat162float(eh));
+                Rolo[off] = __float2bfloat16_rn(so - __bfloat162float(oh));
+            }
+        }
+        return;
+    }
+    const int h4 = h / 4;
     const size_t total = (size_t)H * h4;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
@@ -1363,7 +1417,7 @@ __global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W,
             el[k] = se - e[k];
             ol[k] = so - o[k];
         }
-        const size_t off = (size_t)i * h + j;
+        const size_t off = (size_t)i * ldo + j;
         *reinterpret_cast<uint2*>(Re + off) = make_uint2(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]));
         *reinterpret_cast<uint2*>(Ro + off) = make_uint2(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]));
         if (Relo) {
@@ -1463,12 +1517,30 @@ cudaError_t set_attrs() {
 
 }  // namespace
 
-bool foldable(int H, int W, int split) { return split && H % 256 == 0 && W % 256 == 0; }
+// The folded form needs even sides (the mirror pairs); halves that are not multiples of 256 are
+// padded to them.  Below 256 per side the padding would dominate: the direct form runs there.
+bool foldable(int H, int W, int split) {
+    return split && H % 2 == 0 && W % 2 == 0 && H >= 256 && W >= 256;
+}
+
+// padded extents of the folded operands: the halves and the full height, multiples of 256
+struct FoldDims {
+    int hN, hM, hNp, hMp, Hp;
+};
+FoldDims fold_dims(int H, int W) {
+    FoldDims f;
+    f.hN = H / 2;
+    f.hM = W / 2;
+    f.hNp = (int)rup(f.hN, 256);
+    f.hMp = (int)rup(f.hM, 256);
+    f.Hp = (int)rup(H, 256);
+    return f;
+}
 
 namespace {
 
-// Persistent GEMM form of the folded stages: one CTA per SM (sides multiples of 256), or CTA
-// pairs with 256-row tiles (sides multiples of 512).
+// Persistent GEMM form of the folded stages: one CTA per SM (128-row tiles), or CTA pairs with
+// 256-row tiles (every padded extent is a multiple of 256, so the pair form always applies).
 constexpr int kFoldOneSm = 1, kFoldPair = 2;
 // N of each operand set in the pair form's two-set stages (3 and 4): 256 (two accumulators
 // fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
@@ -1480,10 +1552,11 @@ struct FoldBufs {
     void *PeN[2], *PoN[2], *PeTN[2], *PoTN[2];   // [hi, lo]
     void *PeM[2], *PoM[2], *PeTM[2], *PoTM[2];
     float *lamPN, *lamPM;
-    void *Re[2], *Ro[2];                          // H x W/2
-    void* T1[4][2];                               // (x, sign) = (e+, e-, o+, o-), W/2 x H/2
-    void* T3[2][2];                               // x = e, o: H x W/2 (aliases T1)
-    void* T2[4][2];                               // (x, y) = ee, eo, oe, oo: W/2 x H/2
+    void *Re[2], *Ro[2];                          // H x hMp
+    void* T1[4][2];                               // (x, sign) = (e+, e-, o+, o-), hMp x hNp
+    void* T3[2][2];                               // x = e, o: Hp x hMp (aliases T1)
+    void* T2[4][2];                               // (x, y) = ee, eo, oe, oo: hMp x hNp
+    FoldDims dim{};
     std::vector<GemmTile> tab[4];
     bool bound = false;
     const float* rU = nullptr;
@@ -1498,15 +1571,19 @@ struct FoldBufs {
 };
 
 size_t fold_bytes(int H, int W) {
-    const size_t hN = H / 2, hM = W / 2;
-    size_t n = 4 * hN * hN + 3 * (size_t)H * W;   // basis halves; R e/o, T1 (= T3), T2
-    if (H != W) n += 4 * hM * hM;
-    return 2 * n * 2 + (size_t)(H + W) * 4 + 4 * 4 * sizeof(GemmTile) + 64 * 1024;
+    const FoldDims fd = fold_dims(H, W);
+    const size_t hNp = fd.hNp, hMp = fd.hMp;
+    // basis halves (4 per side), folded residual (2), T1 = T3 region (4), T2 (4)
+    size_t n = 4 * hNp * hNp + 2 * (size_t)H * hMp + 8 * hMp * hNp;
+    if (H != W) n += 4 * hMp * hMp;
+    return 2 * n * 2 + (size_t)(2 * hNp + 2 * hMp) * 4 + 4 * 4 * sizeof(GemmTile) + 64 * 1024;
 }
 
 cudaError_t fold_setup(DctPlan& d, char* p) {
     const int H = d.H, W = d.W;
-    const size_t hN = H / 2, hM = W / 2;
+    const FoldDims fd = fold_dims(H, W);
+    const size_t hNp = fd.hNp, hMp = fd.hMp;
+    char* const p_begin = p;
     auto take = [&](size_t bytes) {
         void* r = p;
         p += rup(bytes, 1024);
@@ -1514,17 +1591,18 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     };
     FoldBufs* fp = new FoldBufs();
     FoldBufs& f = *fp;
+    f.dim = fd;
     for (int q = 0; q < 2; ++q) {
-        f.PeN[q] = take(hN * hN * 2); f.PoN[q] = take(hN * hN * 2);
-        f.PeTN[q] = take(hN * hN * 2); f.PoTN[q] = take(hN * hN * 2);
+        f.PeN[q] = take(hNp * hNp * 2); f.PoN[q] = take(hNp * hNp * 2);
+        f.PeTN[q] = take(hNp * hNp * 2); f.PoTN[q] = take(hNp * hNp * 2);
     }
-    f.lamPN = static_cast<float*>(take((size_t)H * 4));
+    f.lamPN = static_cast<float*>(take(2 * hNp * 4));
     if (H != W) {
         for (int q = 0; q < 2; ++q) {
-            f.PeM[q] = take(hM * hM * 2); f.PoM[q] = take(hM * hM * 2);
-            f.PeTM[q] = take(hM * hM * 2); f.PoTM[q] = take(hM * hM * 2);
+            f.PeM[q] = take(hMp * hMp * 2); f.PoM[q] = take(hMp * hMp * 2);
+            f.PeTM[q] = take(hMp * hMp * 2); f.PoTM[q] = take(hMp * hMp * 2);
         }
-        f.lamPM = static_cast<float*>(take((size_t)W * 4));
+        f.lamPM = static_cast<float*>(take(2 * hMp * 4));
     } else {
         for (int q = 0; q < 2; ++q) {
             f.PeM[q] = f.PeN[q]; f.PoM[q] = f.PoN[q]; f.PeTM[q] = f.PeTN[q]; f.PoTM[q] = f.PoTN[q];
@@ -1532,33 +1610,38 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
         f.lamPM = f.lamPN;
     }
     for (int q = 0; q < 2; ++q) {
-        f.Re[q] = take((size_t)H * hM * 2);
-        f.Ro[q] = take((size_t)H * hM * 2);
+        f.Re[q] = take((size_t)H * hMp * 2);
+        f.Ro[q] = take((size_t)H * hMp * 2);
     }
     for (int q = 0; q < 2; ++q) {
-        char* region = static_cast<char*>(take((size_t)H * W * 2));
-        for (int b = 0; b < 4; ++b) f.T1[b][q] = region + (size_t)b * hM * hN * 2;
-        for (int x = 0; x < 2; ++x) f.T3[x][q] = region + (size_t)x * H * hM * 2;
+        // T1 (four hMp x hNp blocks) and, after stage 2 has read it, T3 (two Hp x hMp blocks;
+        // Hp <= 2 hNp)
+        char* region = static_cast<char*>(take(4 * hMp * hNp * 2));
+        for (int b = 0; b < 4; ++b) f.T1[b][q] = region + (size_t)b * hMp * hNp * 2;
+        for (int x = 0; x < 2; ++x) f.T3[x][q] = region + (size_t)x * fd.Hp * hMp * 2;
     }
     for (int q = 0; q < 2; ++q)
-        for (int b = 0; b < 4; ++b) f.T2[b][q] = take(hM * hN * 2);
+        for (int b = 0; b < 4; ++b) f.T2[b][q] = take(hMp * hNp * 2);
     for (int st = 0; st < 4; ++st) d.fold_tiles[st] = take(4 * sizeof(GemmTile));
+    // padding (columns hM.. of the folded residual, which nothing else writes) stays zero
+    cudaError_t e = cudaMemset(p_begin, 0, (size_t)(p - p_begin));
+    if (e != cudaSuccess) return e;
     d.fold_host = fp;
     d.Re = f.Re[0]; d.Relo = f.Re[1]; d.Ro = f.Ro[0]; d.Rolo = f.Ro[1];
     using B = __nv_bfloat16;
     auto bf = [](void* x) { return static_cast<B*>(x); };
     k_build_fold16<<<1024, 256>>>(bf(f.PeN[0]), bf(f.PoN[0]), bf(f.PeTN[0]), bf(f.PoTN[0]),
                                   bf(f.PeN[1]), bf(f.PoN[1]), bf(f.PeTN[1]), bf(f.PoTN[1]),
-                                  f.lamPN, H);
+                                  f.lamPN, H, fd.hNp);
     if (H != W)
         k_build_fold16<<<1024, 256>>>(bf(f.PeM[0]), bf(f.PoM[0]), bf(f.PeTM[0]), bf(f.PoTM[0]),
                                       bf(f.PeM[1]), bf(f.PoM[1]), bf(f.PeTM[1]), bf(f.PoTM[1]),
-                                      f.lamPM, W);
-    cudaError_t e = cudaGetLastError();
+                                      f.lamPM, W, fd.hMp);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int cnt[4] = {2, 4, 2, 1};   // problems per stage
     for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
-    f.mode = (H % 512 == 0 && W % 512 == 0) ? kFoldPair : kFoldOneSm;
+    f.mode = kFoldPair;
     for (auto fn : {kp_umma_gemm<UE_FOLD16, 1, 64>, kp_umma_gemm<UE_EIG16, 0, 64>,
                     kp_umma_gemm<UE_EIG16_RHO, 0, 64>, kp_umma_gemm<UE_UNFOLD16, 1, 64>,
                     kp_umma_gemm<UE_UNFOLDZ, 1, 64>}) {
@@ -1586,7 +1669,9 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
 // copies them in stream order (kernels still reading the previous tables finish first).
 cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU, int ld,
                       DevState* st, double* partials, int flexible, int skip, cudaStream_t s) {
-    const int H = d.H, W = d.W, hN = H / 2, hM = W / 2;
+    const int H = d.H, W = d.W;
+    const FoldDims fd = f.dim;
+    const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
     bool ok = true;
     UEpiArgs base{};
     base.st = st;
@@ -1611,18 +1696,21 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
         ok &= make_map(&g.b3, Bm[1], br, bc, bbox, kb);
     };
     for (auto& t : f.tab) t.clear();
+    // Every operand is stored padded (extents hNp, hMp, Hp, multiples of 256); padding rows and
+    // columns of the bases are zero, and the epilogues mask what lies beyond the half sides.
     // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
-    // the second operand set reads the B rows mirrored
+    // the second operand set reads the B rows mirrored (a negative start row reads zeros)
     for (int x = 0; x < 2; ++x) {
         GemmTile g{};
-        set0(g, x ? f.PoTM : f.PeTM, hM, hM, x ? f.Ro : f.Re, H, hM);
+        set0(g, x ? f.PoTM : f.PeTM, hMp, hMp, x ? f.Ro : f.Re, H, hMp);
         g.mirror_b1 = 1;
         g.nb_rows = H;
-        g.M = hM; g.N = hN; g.K = hM;
+        g.M = hMp; g.N = hNp; g.K = hMp;
         g.ep = base;
         g.ep.C = f.T1[2 * x][0]; g.ep.C_lo = f.T1[2 * x][1];
         g.ep.C2 = f.T1[2 * x + 1][0]; g.ep.C2_lo = f.T1[2 * x + 1][1];
-        g.ep.ldc = hN;
+        g.ep.ldc = hNp;
+        g.ep.vn = hN;
         f.tab[0].push_back(g);
     }
     // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
@@ -1630,37 +1718,39 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     for (int x = 0; x < 2; ++x)
         for (int y = 0; y < 2; ++y) {
             GemmTile g{};
-            set0(g, f.T1[2 * x + y], hM, hN, y ? f.PoTN : f.PeTN, hN, hN);
-            g.M = hM; g.N = hN; g.K = hN;
+            set0(g, f.T1[2 * x + y], hMp, hNp, y ? f.PoTN : f.PeTN, hNp, hNp);
+            g.M = hMp; g.N = hNp; g.K = hNp;
             g.ep = base;
-            g.ep.C = f.T2[2 * x + y][0]; g.ep.C_lo = f.T2[2 * x + y][1]; g.ep.ldc = hN;
+            g.ep.C = f.T2[2 * x + y][0]; g.ep.C_lo = f.T2[2 * x + y][1]; g.ep.ldc = hNp;
             g.ep.vm = hM; g.ep.vn = hN;
-            g.ep.lam_m = f.lamPM + x * hM;
-            g.ep.lam_n = f.lamPN + y * hN;
+            g.ep.lam_m = f.lamPM + x * hMp;
+            g.ep.lam_n = f.lamPN + y * hNp;
             g.ep.scale = d.tau;
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             f.tab[1].push_back(g);
         }
     if (f.mode == kFoldPair) bbox = kPairDualN / 2;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
-    // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O
+    // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O (i' < hN)
     for (int x = 0; x < 2; ++x) {
         GemmTile g{};
-        set0(g, f.PeN, hN, hN, f.T2[2 * x], hM, hN);
-        set1(g, f.PoN, hN, hN, f.T2[2 * x + 1], hM, hN);
-        g.M = hN; g.N = hM; g.K = hN;
+        set0(g, f.PeN, hNp, hNp, f.T2[2 * x], hMp, hNp);
+        set1(g, f.PoN, hNp, hNp, f.T2[2 * x + 1], hMp, hNp);
+        g.M = hNp; g.N = hMp; g.K = hNp;
         g.ep = base;
-        g.ep.C = f.T3[x][0]; g.ep.C_lo = f.T3[x][1]; g.ep.ldc = hM; g.ep.mrows = H;
+        g.ep.C = f.T3[x][0]; g.ep.C_lo = f.T3[x][1]; g.ep.ldc = hMp; g.ep.mrows = H;
+        g.ep.vm = hN;
         f.tab[2].push_back(g);
     }
-    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O, E from T3e, O from T3o
+    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O (i < H, j' < hM), E from T3e, O from T3o
     {
         GemmTile g{};
-        set0(g, f.T3[0], H, hM, f.PeM, hM, hM);
-        set1(g, f.T3[1], H, hM, f.PoM, hM, hM);
-        g.M = H; g.N = hM; g.K = hM;
+        set0(g, f.T3[0], fd.Hp, hMp, f.PeM, hMp, hMp);
+        set1(g, f.T3[1], fd.Hp, hMp, f.PoM, hMp, hMp);
+        g.M = fd.Hp; g.N = hMp; g.K = hMp;
         g.ep = base;
         g.ep.C = zU; g.ep.ldc = ld; g.ep.mcols = W; g.ep.rU = rU;
+        g.ep.vm = H; g.ep.vn = hM;
         f.tab[3].push_back(g);
     }
     if (!ok) return cudaErrorNotSupported;
@@ -1736,9 +1826,10 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
         if (e != cudaSuccess) return e;
     }
     using B = __nv_bfloat16;
-    const size_t n = (size_t)d.H * (d.W / 8);
+    const size_t n = (size_t)d.H * (d.W % 8 == 0 ? d.W / 8 : d.W / 2);
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
-    k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, static_cast<B*>(d.Re), static_cast<B*>(d.Relo),
+    k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, f.dim.hMp, static_cast<B*>(d.Re),
+                                    static_cast<B*>(d.Relo),
                                     static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
                                     skip_if_done);
     if (f.mode == kFoldPair) return fold_launch_pair(d, f, reduce_rho, s);

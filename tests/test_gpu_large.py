@@ -1,6 +1,6 @@
-"""Large non-square images 4000 x M (the paper's scaling shapes, Sec. 4.4): the direct
-(padded, non-folded) tensor-core preconditioner on sides that are not multiples of 128 or 256,
-against the oracle where it finishes in seconds and against invariants beyond that."""
+"""Large non-square images 4000 x M (the paper's scaling shapes, Sec. 4.4): the folded
+tensor-core preconditioner with halves padded to multiples of 256 (and the direct form on
+request), against the oracle where it finishes in seconds and against invariants beyond that."""
 import numpy as np
 import pytest
 
@@ -26,14 +26,17 @@ def cuda(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def test_4000x2000_first_outer_matches_oracle(irls):
+@pytest.mark.parametrize("form", ["folded", "direct"])
+def test_4000x2000_first_outer_matches_oracle(irls, form):
     """4000 x 2000 (8 Mpix), split-bf16: one outer step of 4 CG iterations element by element
-    (bound as for the 2048 x 2048 truncated run: 4 x 5e-5 x max|U|)."""
+    (bound as for the 2048 x 2048 truncated run: 4 x 5e-5 x max|U|), both preconditioner forms."""
     d = synthetic.config_4096_mixed(seed=40, H=4000, W=2000)
     kw = dict(tau=1e-2, delta=1e-3, outer_iters=1, cg_tol=1e-6, cg_max=4)
     ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
-    U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=1,
-                        cg_tol=1e-6, cg_max_iter=4, precision="bf16x3", return_stats=True)
+    with irls.Plan(4000, 2000, delta=1e-3, outer_iters=1, cg_tol=1e-6, cg_max_iter=4,
+                   precision="bf16x3", dct_form=form) as p:
+        assert p.folded == (form == "folded")
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
     assert st["cg_iters"] == [4]
     atol = max(1e-3, 4 * 5e-5 * np.abs(ref["U"]).max())
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
@@ -42,12 +45,12 @@ def test_4000x2000_first_outer_matches_oracle(irls):
 
 @pytest.mark.parametrize("W", [8000, 16000])
 def test_4000xM_invariants(irls, W):
-    """4000 x 8000 and 4000 x 16000 (64 Mpix, about 11 GB of device memory): three outer steps;
+    """4000 x 8000 and 4000 x 16000 (64 Mpix, about 12 GB of device memory): three outer steps;
     the monotone quantities of Sec. 3.1 hold on the device statistics, U has zero mean, the plan
-    runs the direct form (4000 is not a multiple of 256), and the solve reports no error."""
+    runs the folded form with padded halves (2000 -> 2048), and the solve reports no error."""
     d = synthetic.config_4096_mixed(seed=41, H=4000, W=W)
     with irls.Plan(4000, W, delta=1e-3, outer_iters=3, cg_tol=1e-6, precision="bf16x3") as p:
-        assert not p.folded
+        assert p.folded
         U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
     assert st["return_code"] in (0, 1)
     f, h = st["f_delta"], st["h_delta"]

@@ -114,10 +114,12 @@ def parity_atol(env):
 # ------------------------------------------------------------------------------------------
 # single operators
 # ------------------------------------------------------------------------------------------
-# (256, 256), (512, 256), (256, 768) and (1024, 512) take the folded tensor-core form in bf16x3
-# (both sides multiples of 256); the others the direct one
+# in bf16x3 the even shapes with both sides >= 256 take the folded tensor-core form (halves
+# padded to multiples of 256 where they are not: 384 x 256, 256 x 640, 1920 x 2048, 4000 x 2002);
+# the others the direct one
 PRECOND_SHAPES = [(64, 48), (130, 257), (256, 256), (384, 256), (256, 640), (1, 200), (300, 1),
-                  (3, 3), (512, 256), (256, 768), (1024, 512), (2048, 2048), (1920, 2048)]
+                  (3, 3), (512, 256), (256, 768), (1024, 512), (2048, 2048), (1920, 2048),
+                  (4000, 2002), (258, 260)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
@@ -183,12 +185,15 @@ def test_folded_and_direct_forms_agree(irls):
 
 
 def test_folded_form_only_where_allowed(irls):
-    """IRLS_DCT_FOLDED needs split precision and both sides multiples of 256."""
-    for H, W, prec in ((384, 256, "bf16x3"), (256, 256, "bf16"), (256, 256, "fp32")):
+    """IRLS_DCT_FOLDED needs split precision and even sides of at least 256."""
+    for H, W, prec in ((200, 256, "bf16x3"), (256, 257, "bf16x3"), (256, 256, "bf16"),
+                       (256, 256, "fp32")):
         with pytest.raises(irls.IrlsError) as e:
             irls.Plan(H, W, precision=prec, dct_form="folded")
         assert e.value.code == -8
     with irls.Plan(384, 256, precision="bf16x3") as plan:
+        assert plan.folded
+    with irls.Plan(256, 257, precision="bf16x3") as plan:
         assert not plan.folded
         with pytest.raises(irls.IrlsError):
             plan.set_opts(dct_form="folded")
