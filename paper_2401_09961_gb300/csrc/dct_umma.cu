@@ -9,7 +9,12 @@
 //   stage 3: T3[i][l] = sum_k PN[i][k] T2[l][k]                     (= P_S Z')
 //   stage 4: Z[i][j]  = sum_l T3[i][l] PM[j][l]                     (= P_S Z' P_T^T)
 //
-// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
+// Two forms share the building blocks below.  The direct form (any side; operands padded to
+// multiples of 128) and the grouped batched form run one output tile per CTA, structured as
+// follows.  The folded form (even sides >= 256) runs persistent CTA-pair kernels
+// (k2_umma_gemm, tcgen05.mma.cta_group::2, further down), which take half the multiply-adds.
+//
+// Kernel structure of the direct form (one 128 x BN output tile per CTA, 128 threads):
 //   warp 0 lane 0  TMA producer: cp.async.bulk.tensor 2-D loads (128-byte swizzle) of the
 //                  128 x 64 A tile and the BN x 64 B tile into a ring of shared-memory stages,
 //                  each guarded by a full / empty mbarrier pair;
@@ -285,10 +290,10 @@ __device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u) {
     }
 }
 
-// Epilogue of one 128 x BN output tile for the accumulator row this thread holds: tl is the
-// tensor-memory address of its lane at the accumulator's first column (a second accumulator, if
-// any, starts BN columns later), m its output row, n0 the tile's first column.  ZU_RHO forms
-// add their share of r^T z to `part`.
+// Epilogue of one 128 x BN output tile of the one-tile-per-CTA kernels (the direct form and the
+// grouped batched form), for the accumulator row this thread holds: tl is the tensor-memory
+// address of its lane at the accumulator's first column, m its output row, n0 the tile's first
+// column.  ZU_RHO adds this thread's share of r^T z to `part`.
 template <int BN, int EPI>
 __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m, int n0,
                                          float& part, int c_begin = 0, int c_end = BN / 32) {
@@ -297,59 +302,9 @@ __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m,
         uint32_t r[32];
         tmem_ld32(tl + (uint32_t)(c * 32), r);
         const int nb = n0 + c * 32;
-        if constexpr (EPI == UE_FOLD16) {
-            // acc1 holds the mirrored tile: its column BN-1-x pairs with acc0's column x
-            uint32_t r1[32];
-            tmem_ld32(tl + (uint32_t)BN + (uint32_t)((BN / 32 - 1 - c) * 32), r1);
-            float pl[32], mi[32];
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
-                pl[t] = a + b;
-                mi[t] = a - b;
-            }
-            store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
-            store_row32(ep.C2, ep.C2_lo, (size_t)m * ep.ldc + nb, mi);
-        } else if constexpr (EPI == UE_UNFOLD16) {
-            uint32_t r1[32];
-            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
-            float pl[32], mi[32];
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[t]);
-                pl[t] = a + b;
-                mi[t] = a - b;
-            }
-            store_row32(ep.C, ep.C_lo, (size_t)m * ep.ldc + nb, pl);
-            store_row32(ep.C, ep.C_lo, (size_t)(ep.mrows - 1 - m) * ep.ldc + nb, mi);
-        } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
-            uint32_t r1[32];
-            tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
-            float* out = static_cast<float*>(ep.C) + (size_t)m * ep.ldc;
-            const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float4 w, wm;
-                float* wp = &w.x;
-                float* wmp = &wm.x;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = 4 * q + u;            // column nb + t
-                    const int tm = 31 - (4 * q + u);    // mirrored column mb + 4q + u
-                    wp[u] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);
-                    wmp[u] = __uint_as_float(r[tm]) - __uint_as_float(r1[tm]);
-                }
-                reinterpret_cast<float4*>(out + nb)[q] = w;
-                reinterpret_cast<float4*>(out + mb)[q] = wm;
-                if constexpr (EPI == UE_UNFOLDZ_RHO) {
-                    const float* rr = ep.rU + (size_t)m * ep.ldc;
-                    const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
-                    const float4 xm = reinterpret_cast<const float4*>(rr + mb)[q];
-                    part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
-                    part += xm.x * wm.x + xm.y * wm.y + xm.z * wm.z + xm.w * wm.w;
-                }
-            }
-        } else if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
+        static_assert(EPI == UE_STORE16 || EPI == UE_EIG16 || EPI == UE_ZU || EPI == UE_ZU_RHO,
+                      "one-tile-per-CTA kernels: direct-form epilogues");
+        if constexpr (EPI == UE_STORE16 || EPI == UE_EIG16) {
             float v[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
@@ -767,10 +722,8 @@ kb_umma_gemm(const GemmTile* __restrict__ tiles, int T) {
 }
 
 // ------------------------------------------------------------------------------------------
-// persistent form
+// helpers of the persistent (CTA-pair) form
 // ------------------------------------------------------------------------------------------
-constexpr int kPThreads = 192;
-
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -812,183 +765,6 @@ __device__ __forceinline__ const GemmTile& tile_problem(const GemmTile* tiles, i
 // Every wait is bounded and gives up once any role has flagged an error; before exit the
 // producer waits (bounded) for its copies in flight and the issuer for its MMAs.  The ZU_RHO
 // forms need a launch with a single problem: the r^T z reduction runs over the whole grid.
-// Shared-memory ring of the persistent kernel: KB columns of K per stage (64 with 128-byte
-// swizzling, 32 with 64-byte swizzling), hi and lo parts of a 128-row A and a 128-row B tile.
-template <int KB>
-struct PCfg {
-    static constexpr int kABytes = UBM * KB * 2;
-    static constexpr int kBBytes = 128 * KB * 2;
-    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = (192 * 1024) / kStageBytes > 8 ? 8 : (192 * 1024) / kStageBytes;
-    // ring, 1024-byte alignment slack, barriers (256 bytes), four epilogue warps' scratch
-    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + 4 * (int)sizeof(WarpScratch);
-    static constexpr uint32_t kIdesc = UCfg<128, 2, 2>::kIdesc;
-};
-
-template <int EPI, int DUAL, int KB>
-__global__ void __launch_bounds__(kPThreads, 1)
-kp_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
-    using C = PCfg<KB>;
-    constexpr int BN = 128;
-    constexpr uint32_t kAcc = DUAL ? 2 * BN : BN;
-    constexpr uint32_t kCols = 2 * kAcc;
-    constexpr int S = C::kStages;
-    DevState* st0 = tiles[0].ep.st;
-    if (tiles[0].ep.skip_if_done && st0->done) return;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                               ~static_cast<uintptr_t>(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * C::kStageBytes);
-    uint64_t* empty = full + S;
-    uint64_t* tfull = empty + S;     // [2] accumulator buffer ready for the epilogue
-    uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained
-    uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
-    __shared__ int s_err;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        s_err = 0;
-        for (int i = 0; i < S; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
-        }
-        mbar_init(drain, 1);
-        fence_mbar_init();
-    }
-    if (warp == 1) tmem_alloc(tmem_slot, kCols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    float part = 0.f;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            int it = 0;
-            bool bad = false;
-            for (int t = blockIdx.x; t < total_tiles && !bad; t += gridDim.x) {
-                const GemmTile& g = tile_problem(tiles, T, t);
-                const int local = t - g.blk0;
-                const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * BN;
-                const int n0b1 = g.mirror_b1 ? g.nb_rows - n0 - BN : n0;
-                const int nkb = g.K / KB, nkt = DUAL ? 2 * nkb : nkb;
-                for (int kb = 0; kb < nkt; ++kb, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    if (it >= S && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_err)) {
-                        bad = true;
-                        break;
-                    }
-                    const bool second = DUAL && kb >= nkb;
-                    const int kc = (second ? kb - nkb : kb) * KB;
-                    const int nb = second ? n0b1 : n0;
-                    uint8_t* sa = smem + s * C::kStageBytes;
-                    uint8_t* sb = sa + 2 * C::kABytes;
-                    mbar_expect_tx(&full[s], C::kStageBytes);
-                    tma_load_2d(sa, second ? &g.a2 : &g.a0, &full[s], kc, m0);
-                    tma_load_2d(sa + C::kABytes, second ? &g.a3 : &g.a1, &full[s], kc, m0);
-                    tma_load_2d(sb, second ? &g.b2 : &g.b0, &full[s], kc, nb);
-                    tma_load_2d(sb + C::kBBytes, second ? &g.b3 : &g.b1, &full[s], kc, nb);
-                }
-            }
-            // copies in flight land before the CTA may exit (immediate on the normal path)
-            for (int j = it - S < 0 ? 0 : it - S; j < it; ++j)
-                if (!mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) atomicExch(&s_err, 1);
-        }
-        __syncwarp();
-    } else if (warp == 1) {
-        if (lane == 0) {
-            int it = 0, j = 0;
-            bool bad = false;
-            for (int t = blockIdx.x; t < total_tiles && !bad; t += gridDim.x, ++j) {
-                const GemmTile& g = tile_problem(tiles, T, t);
-                const int nkb = g.K / KB, nkt = DUAL ? 2 * nkb : nkb;
-                const int b = j & 1, u = j >> 1;
-                if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
-                    bad = true;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t base = tmem + (uint32_t)b * kAcc;
-                for (int kb = 0; kb < nkt; ++kb, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    if (!mbar_wait_or_abort(&full[s], ph, &s_err)) {
-                        bad = true;
-                        break;
-                    }
-                    tc_fence_after();
-                    const bool second = DUAL && kb >= nkb;
-                    const int kk = second ? kb - nkb : kb;
-                    const uint32_t td = base + (second ? (uint32_t)BN : 0u);
-                    const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
-                    const uint32_t sb = sa + 2 * C::kABytes;
-                    const uint64_t da = desc_kmajor<KB>(sa), db = desc_kmajor<KB>(sb);
-                    const uint64_t dal = desc_kmajor<KB>(sa + C::kABytes);
-                    const uint64_t dbl = desc_kmajor<KB>(sb + C::kBBytes);
-#pragma unroll
-                    for (int q = 0; q < KB / 16; ++q) {   // K = 16 per MMA: +32 bytes
-                        umma_bf16(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
-                        umma_bf16(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
-                        umma_bf16(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
-                    }
-                    umma_commit(&empty[s]);
-                }
-                if (!bad) umma_commit(&tfull[b]);
-            }
-            if (it > 0) {
-                umma_commit(drain);
-                if (!mbar_wait(drain, 0)) atomicExch(&s_err, 1);
-            }
-        }
-        __syncwarp();
-    } else {
-        const int q = warp & 3;
-        int j = 0;
-        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++j) {
-            const GemmTile& g = tile_problem(tiles, T, t);
-            const int local = t - g.blk0;
-            const int m0 = (local / g.gx) * UBM, n0 = (local % g.gx) * BN;
-            const int b = j & 1, u = j >> 1;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
-            const UEpiArgs ep = g.ep;   // register copy (see umma_body)
-            epi_tile_t<BN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
-                                m0 + q * 32, n0, part, 0, BN / 32, scratch[warp - 2]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kCols);
-    }
-    if (threadIdx.x == 0 && *(volatile int*)&s_err) {
-        atomicOr(&st0->status, ST_TIMEOUT);
-        st0->done = 1;
-    }
-    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO || EPI == UE_EIG16_RHO) {
-        const UEpiArgs& ep = tiles[0].ep;
-        double vv[1] = {(double)part}, tot[1];
-        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
-            threadIdx.x == 0)
-            finish_rho(ep, tot[0]);
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // CTA-pair form: tcgen05.mma.cta_group::2 over two SMs of a TPC
 // ------------------------------------------------------------------------------------------
@@ -1093,8 +869,15 @@ __device__ __forceinline__ int pair_tile_n(const GemmTile& g) {
 }
 
 // Persistent CTA-pair grouped GEMM.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
-// p + gridDim.x / 2, ...; roles as in kp_umma_gemm (eight epilogue warps, two per accumulator
-// lane quarter, splitting the columns), with the MMA issuer in the even CTA only:
+// p + gridDim.x / 2, ... of every problem of the launch.  Warp roles in each CTA:
+//   warp 0 lane 0   TMA producer: this CTA's A and B rows of each k-block through the
+//                   shared-memory ring (the even CTA's full barriers count both CTAs' bytes);
+//   warp 1          tensor-memory allocation (both CTAs, collectively); in the even CTA lane 0
+//                   also issues the MMAs, into one of the accumulator buffers, so that one
+//                   tile's epilogue overlaps the next tile's products where two buffers fit;
+//   warps 2..9      epilogue: two warps per accumulator lane quarter split the columns and drain
+//                   their CTA's 128 accumulator rows, then release the buffer.
+// Per operand set:
 //   non-DUAL: one M = 256, N = 256 accumulator, two buffers; CTA r stages B rows n0 + 128 r, or
 //             for a mirrored problem rows n0 (even CTA) and nb_rows - n0 - 128 (odd CTA), so
 //             that accumulator columns [128, 256) hold the mirrored tile;
@@ -1539,10 +1322,8 @@ FoldDims fold_dims(int H, int W) {
 
 namespace {
 
-// Persistent GEMM form of the folded stages: one CTA per SM (128-row tiles), or CTA pairs with
-// 256-row tiles (every padded extent is a multiple of 256, so the pair form always applies).
-constexpr int kFoldOneSm = 1, kFoldPair = 2;
-// N of each operand set in the pair form's two-set stages (3 and 4): 256 (two accumulators
+// The folded stages run as persistent CTA-pair GEMMs with 256-row tiles (every padded extent is
+// a multiple of 256).  N of each operand set in the pair form's two-set stages (3 and 4): 256 (two accumulators
 // fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
 constexpr int kPairDualN = 256;
 
@@ -1566,7 +1347,6 @@ struct FoldBufs {
     double* partials = nullptr;
     float tau = 0.f;
     int n_sm = 0;          // SMs of the device: persistent grid size
-    int mode = 1;          // kFoldOneSm or kFoldPair
     int tiles[4] = {0, 0, 0, 0};   // output tiles per stage in that form
 };
 
@@ -1641,13 +1421,6 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     if (e != cudaSuccess) return e;
     const int cnt[4] = {2, 4, 2, 1};   // problems per stage
     for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
-    f.mode = kFoldPair;
-    for (auto fn : {kp_umma_gemm<UE_FOLD16, 1, 64>, kp_umma_gemm<UE_EIG16, 0, 64>,
-                    kp_umma_gemm<UE_EIG16_RHO, 0, 64>, kp_umma_gemm<UE_UNFOLD16, 1, 64>,
-                    kp_umma_gemm<UE_UNFOLDZ, 1, 64>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, PCfg<64>::kSmem);
-        if (e != cudaSuccess) return e;
-    }
     for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>,
                     k2_umma_gemm<UE_EIG16_RHO, 0, 256>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
@@ -1729,7 +1502,7 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             f.tab[1].push_back(g);
         }
-    if (f.mode == kFoldPair) bbox = kPairDualN / 2;
+    bbox = kPairDualN / 2;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
     // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O (i' < hN)
     for (int x = 0; x < 2; ++x) {
@@ -1755,12 +1528,12 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     }
     if (!ok) return cudaErrorNotSupported;
     for (int k = 0; k < 4; ++k) {
-        // output tiles: 128 x 128 (one-SM form); 256 rows x 128 columns for the mirrored stage 1
-        // and 256 x 256 otherwise (pair form)
-        const int tm = f.mode == kFoldPair ? 256 : UBM;
+        // output tiles: 256 rows x 128 columns for the mirrored stage 1, 256 x kPairDualN for the
+        // two-set stages, 256 x 256 for stage 2
+        const int tm = 256;
         int tiles = 0;
         for (auto& g : f.tab[k]) {
-            const int tn = f.mode != kFoldPair ? 128 : (k == 0 ? 128 : (k == 1 ? 256 : kPairDualN));
+            const int tn = k == 0 ? 128 : (k == 1 ? 256 : kPairDualN);
             if (g.M % tm != 0 || g.N % tn != 0) return cudaErrorInvalidValue;
             g.gx = g.N / tn;
             g.blk0 = tiles;
@@ -1777,25 +1550,6 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     f.rU = rU; f.zU = zU; f.ld = ld; f.st = st; f.partials = partials;
     f.flexible = flexible; f.skip = skip; f.tau = d.tau;
     return cudaSuccess;
-}
-
-template <int KB>
-cudaError_t fold_launch_persistent(const DctPlan& d, const FoldBufs& f, int reduce_rho,
-                                   cudaStream_t s) {
-    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
-    auto grid = [&](int k) { return std::min(f.tiles[k], f.n_sm); };
-    const int sm = PCfg<KB>::kSmem;
-    const int* c = d.fold_count;
-    const int* t = f.tiles;
-    // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
-    kp_umma_gemm<UE_FOLD16, 1, KB><<<grid(0), kPThreads, sm, s>>>(tab(0), c[0], t[0]);
-    if (reduce_rho)
-        kp_umma_gemm<UE_EIG16_RHO, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
-    else
-        kp_umma_gemm<UE_EIG16, 0, KB><<<grid(1), kPThreads, sm, s>>>(tab(1), c[1], t[1]);
-    kp_umma_gemm<UE_UNFOLD16, 1, KB><<<grid(2), kPThreads, sm, s>>>(tab(2), c[2], t[2]);
-    kp_umma_gemm<UE_UNFOLDZ, 1, KB><<<grid(3), kPThreads, sm, s>>>(tab(3), c[3], t[3]);
-    return cudaGetLastError();
 }
 
 cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho, cudaStream_t s) {
@@ -1832,8 +1586,7 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
                                     static_cast<B*>(d.Relo),
                                     static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
                                     skip_if_done);
-    if (f.mode == kFoldPair) return fold_launch_pair(d, f, reduce_rho, s);
-    return fold_launch_persistent<64>(d, f, reduce_rho, s);
+    return fold_launch_pair(d, f, reduce_rho, s);
 }
 
 }  // namespace
