@@ -151,6 +151,52 @@ def test_precond_laplacian_matches_oracle(irls, H, W, prec):
         assert rel2 <= 4e-2 and np.abs(Z - z_ref).max() <= 6e-2 * scale, rel2
 
 
+def precond_reference_fft(R, tau):
+    """The Sec. 3.3 solve through the orthonormal DCT-II of scipy.fft (P^T x = dct(x, 2, 'ortho')),
+    float64: the oracle's definition at sizes where its dense products would take minutes."""
+    from scipy.fft import dctn, idctn
+    H, W = R.shape
+    F = dctn(R.astype(np.float64), type=2, norm="ortho")
+    lam = 2.0 - 2.0 * np.cos(np.pi * np.arange(H) / H)
+    mu = 2.0 - 2.0 * np.cos(np.pi * np.arange(W) / W)
+    den = lam[:, None] + mu[None, :]
+    den[0, 0] = 1.0
+    G = tau * F / den
+    G[0, 0] = 0.0
+    return idctn(G, type=2, norm="ortho")
+
+
+def test_fft_reference_equals_oracle():
+    R = np.random.default_rng(2).standard_normal((48, 40))
+    z = O.precond_apply((R, np.zeros((47, 40)), np.zeros((48, 39))), np.zeros((47, 40)),
+                        np.zeros((48, 39)), 1e-2, O.dct_basis(48), O.dct_basis(40))[0]
+    assert np.abs(precond_reference_fft(R, 1e-2) - z).max() <= 1e-12 * np.abs(z).max()
+
+
+@pytest.mark.parametrize("H,W", [(4096, 4096), (2048, 4096), (4000, 16000)])
+def test_precond_large(irls, H, W):
+    """The folded preconditioner at the benchmarked size and at large non-square shapes (more
+    output tiles than CTA pairs, several rounds per pair), against the float64 reference.  The
+    split-bf16 error grows with the side (the lowest frequencies' amplification
+    tau / (l_i + m_j) grows as n^2): bound 5e-5 in l2 up to 4096 as for the small shapes, and at
+    any size no worse than the direct (unfolded) form's own error x 1.25."""
+    R = np.random.default_rng(H + W).standard_normal((H, W)).astype(np.float32)
+    with irls.Plan(H, W, tau=1e-2, precision="bf16x3") as plan:
+        assert plan.folded
+        Z = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+        Z2 = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+        plan.set_opts(dct_form="direct")
+        Zd = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+    z_ref = precond_reference_fft(R, 1e-2)
+    nz = np.linalg.norm(z_ref)
+    rel2 = np.linalg.norm(Z - z_ref) / nz
+    rel2_direct = np.linalg.norm(Zd - z_ref) / nz
+    assert rel2 <= 1.25 * rel2_direct, (rel2, rel2_direct)
+    if max(H, W) <= 4096:
+        assert rel2 <= 5e-5 and np.abs(Z - z_ref).max() <= 1e-4 * np.abs(z_ref).max(), rel2
+    assert np.array_equal(Z, Z2)   # deterministic: fixed tile order, fixed summation order
+
+
 def test_folded_and_direct_forms_agree(irls):
     """The folded form (sums and differences of mirrored rows and columns, half-size products
     with the even and odd halves of the DCT basis) and the direct form compute the same Sec. 3.3
