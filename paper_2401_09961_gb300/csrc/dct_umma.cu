@@ -78,6 +78,9 @@ struct UEpiArgs {
     double* partials;
     int flexible;
     int skip_if_done;
+    // EIG16_RHO in the CTA-pair kernels: the index of this problem's first tile among its
+    // image's tiles, and the image's tile count (its problems are consecutive in the table)
+    int rho_base, rho_count;
 };
 
 template <int BN, int SA, int SB>
@@ -743,6 +746,36 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
     return true;
 }
 
+// Arrive-and-wait of the CTA's epilogue warps on an mbarrier (count = epilogue warps), bounded;
+// `n` counts the uses so far (the phase parity).  False on timeout or another role's error.
+__device__ __forceinline__ bool epi_sync(uint64_t* bar, int& n, int* err) {
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive(bar);
+        ok = mbar_wait_or_abort(bar, (uint32_t)n & 1u, err);
+    }
+    ++n;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// A problem whose CG run has stopped (per-image mask of a batched launch) contributes no tiles.
+__device__ __forceinline__ bool problem_live(const GemmTile& g) {
+    return !(g.ep.skip_if_done && *(volatile int*)&g.ep.st->done);
+}
+
+// problem_live, read once per image while the image does not change (no image's flag changes
+// during a launch: a run stops between launches)
+__device__ __forceinline__ bool problem_live_cached(const GemmTile& g, const DevState*& st,
+                                                    bool& live) {
+    if (g.ep.st != st) {
+        st = g.ep.st;
+        live = problem_live(g);
+    }
+    return live;
+}
+
 __device__ __forceinline__ const GemmTile& tile_problem(const GemmTile* tiles, int T, int t) {
     int lo = 0, hi = T - 1;
     while (lo < hi) {
@@ -904,16 +937,21 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained (even CTA: all epilogue
                                      //     warps of both CTAs)
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* epibar = drain + 1;    // the CTA's epilogue warps (per-image r^T z sums)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epibar + 1);
     WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
     __shared__ int s_err;
     __shared__ int s_skip;
+    __shared__ double s_red[2][k2EpiWarps];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     if (threadIdx.x == 0) {
         s_err = 0;
-        s_skip = (tiles[0].ep.skip_if_done && st0->done) ? 1 : 0;
+        // the whole launch returns when every problem's run has stopped
+        int all_done = 1;
+        for (int i = 0; i < T; ++i) all_done &= problem_live(tiles[i]) ? 0 : 1;
+        s_skip = all_done;
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
@@ -923,6 +961,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             mbar_init(&tempty[b], 2 * k2EpiWarps);
         }
         mbar_init(drain, 1);
+        mbar_init(epibar, k2EpiWarps);
         fence_mbar_init();
     }
     cluster_sync_all();
@@ -946,6 +985,8 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     const uint32_t tmem = *tmem_slot;
     const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
     float part = 0.f;
+    const DevState* lst = nullptr;
+    bool llive = true;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -954,6 +995,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             bool bad = false;
             for (int t = pair; t < total_tiles && !bad; t += npairs) {
                 const GemmTile& g = tile_problem(tiles, T, t);
+                if (!problem_live_cached(g, lst, llive)) continue;
                 const int local = t - g.blk0;
                 const int tn = pair_tile_n<DUAL, SETN>(g);
                 const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
@@ -996,10 +1038,12 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         if (rank == 0 && lane == 0) {
             int it = 0, j = 0;
             bool bad = false;
-            for (int t = pair; t < total_tiles && !bad; t += npairs, ++j) {
+            for (int t = pair; t < total_tiles && !bad; t += npairs) {
                 const GemmTile& g = tile_problem(tiles, T, t);
+                if (!problem_live_cached(g, lst, llive)) continue;
                 const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
                 const int b = j % NB, u = j / NB;
+                ++j;
                 if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
                     bad = true;
                     break;
@@ -1040,14 +1084,16 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         constexpr int kChunks = EBN / 32;
         const int c_begin = half * (kChunks / 2), c_end = c_begin + kChunks / 2;
         const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
-        int j = 0;
-        for (int t = pair; t < total_tiles; t += npairs, ++j) {
+        int j = 0, nsync = 0;
+        for (int t = pair; t < total_tiles; t += npairs) {
             const GemmTile& g = tile_problem(tiles, T, t);
+            if (!problem_live_cached(g, lst, llive)) continue;
             const int local = t - g.blk0;
             const int tn = pair_tile_n<DUAL, SETN>(g);
             const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
             const int n0 = (local % g.gx) * tn;
             const int b = j % NB, u = j / NB;
+            ++j;
             int ok = 1;
             if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -1059,6 +1105,52 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(te0 + 8u * (uint32_t)b);
+            if constexpr (EPI == UE_EIG16_RHO) {
+                // r^T z of an image: a CTA meets the image's tiles as one run (t - a < npairs
+                // apart in the image's consecutive range [a, b)); at the end of its run it adds
+                // its epilogue warps' sums in a fixed order into the image's slot for (first tile
+                // of the run, CTA); the warp that fills the image's last slot adds the
+                // 2 min(npairs, b - a) slots in a fixed order and forms rho and beta
+                const int a = g.blk0 - ep.rho_base, b = a + ep.rho_count;
+                const int tn_ = t + npairs;
+                const bool run_end = tn_ >= b || tn_ >= total_tiles;
+                if (run_end) {
+                    double v = (double)part;
+                    part = 0.f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    const int buf = nsync & 1;
+                    if (lane == 0) s_red[buf][warp - 2] = v;
+                    if (!epi_sync(epibar, nsync, &s_err)) break;
+                    if (warp == 2) {
+                        const int first = a + ((pair - a) % npairs + npairs) % npairs;
+                        const int nslot = 2 * min(npairs, b - a);
+                        unsigned last = 0;
+                        if (lane == 0) {
+                            double sum = 0.0;
+                            for (int w = 0; w < k2EpiWarps; ++w) sum += s_red[buf][w];
+                            ep.partials[(first - a) * 2 + (int)rank] = sum;
+                            __threadfence();
+                            const unsigned prev = atomicAdd(&ep.st->counter, 1u);
+                            last = prev == (unsigned)nslot - 1u;
+                        }
+                        last = __shfl_sync(0xffffffffu, last, 0);
+                        if (last) {
+                            __threadfence();
+                            double tot = 0.0;
+                            for (int i = lane; i < nslot; i += 32) tot += __ldcg(&ep.partials[i]);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1)
+                                tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                            if (lane == 0) {
+                                finish_rho(ep, tot);
+                                ep.st->counter = 0u;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
         }
     }
 
@@ -1074,13 +1166,7 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         atomicOr(&st0->status, ST_TIMEOUT);
         st0->done = 1;
     }
-    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO || EPI == UE_EIG16_RHO) {
-        const UEpiArgs& ep = tiles[0].ep;
-        double vv[1] = {(double)part}, tot[1];
-        if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, gridDim.x, blockIdx.x) &&
-            threadIdx.x == 0)
-            finish_rho(ep, tot[0]);
-    }
+    static_assert(EPI != UE_ZU_RHO && EPI != UE_UNFOLDZ_RHO, "r^T z: the per-tile form only");
     cluster_sync_all();
 }
 
@@ -1323,104 +1409,189 @@ FoldDims fold_dims(int H, int W) {
 namespace {
 
 // The folded stages run as persistent CTA-pair GEMMs with 256-row tiles (every padded extent is
-// a multiple of 256).  N of each operand set in the pair form's two-set stages (3 and 4): 256 (two accumulators
-// fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
+// a multiple of 256).  N of each operand set in the pair form's two-set stages (3 and 4): 256
+// (two accumulators fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
 constexpr int kPairDualN = 256;
 
-// Host-side record of the folded form's buffers and of the arguments its device tables were
-// last built for (the tables bake in the planes, the CG state and the epilogue flags).
-struct FoldBufs {
-    void *PeN[2], *PoN[2], *PeTN[2], *PoTN[2];   // [hi, lo]
-    void *PeM[2], *PoM[2], *PeTM[2], *PoTM[2];
-    float *lamPN, *lamPM;
-    void *Re[2], *Ro[2];                          // H x hMp
-    void* T1[4][2];                               // (x, sign) = (e+, e-, o+, o-), hMp x hNp
-    void* T3[2][2];                               // x = e, o: Hp x hMp (aliases T1)
-    void* T2[4][2];                               // (x, y) = ee, eo, oe, oo: hMp x hNp
-    FoldDims dim{};
-    std::vector<GemmTile> tab[4];
-    bool bound = false;
-    const float* rU = nullptr;
-    float* zU = nullptr;
-    int ld = 0, flexible = 0, skip = 0;
-    DevState* st = nullptr;
-    double* partials = nullptr;
-    float tau = 0.f;
-    int n_sm = 0;          // SMs of the device: persistent grid size
-    int tiles[4] = {0, 0, 0, 0};   // output tiles per stage in that form
+// Even / odd basis halves of one side length n (hi and lo parts), padded to hp = rup(n/2, 256).
+struct FoldSide {
+    int n = 0, hp = 0;
+    void *Pe[2], *Po[2], *PeT[2], *PoT[2];
+    float* lamP;
 };
 
-size_t fold_bytes(int H, int W) {
-    const FoldDims fd = fold_dims(H, W);
-    const size_t hNp = fd.hNp, hMp = fd.hMp;
-    // basis halves (4 per side), folded residual (2), T1 = T3 region (4), T2 (4)
-    size_t n = 4 * hNp * hNp + 2 * (size_t)H * hMp + 8 * hMp * hNp;
-    if (H != W) n += 4 * hMp * hMp;
-    return 2 * n * 2 + (size_t)(2 * hNp + 2 * hMp) * 4 + 4 * 4 * sizeof(GemmTile) + 64 * 1024;
+// One image's folded operands and intermediates (hi and lo parts).
+struct FoldImage {
+    FoldDims dim{};
+    void *Re[2], *Ro[2];   // H x hMp
+    void* T1[4][2];        // (x, sign) = (e+, e-, o+, o-), hMp x hNp
+    void* T3[2][2];        // x = e, o: Hp x hMp (aliases T1)
+    void* T2[4][2];        // (x, y) = ee, eo, oe, oo: hMp x hNp
+};
+
+size_t fold_side_bytes(int n) {
+    const size_t hp = rup(n / 2, 256);
+    return 2 * 4 * rup(hp * hp * 2, 1024) + rup(2 * hp * 4, 1024);
 }
 
-cudaError_t fold_setup(DctPlan& d, char* p) {
-    const int H = d.H, W = d.W;
+size_t fold_image_bytes(int H, int W) {
     const FoldDims fd = fold_dims(H, W);
     const size_t hNp = fd.hNp, hMp = fd.hMp;
-    char* const p_begin = p;
-    auto take = [&](size_t bytes) {
-        void* r = p;
-        p += rup(bytes, 1024);
-        return r;
-    };
-    FoldBufs* fp = new FoldBufs();
-    FoldBufs& f = *fp;
-    f.dim = fd;
+    return 2 * (2 * rup((size_t)H * hMp * 2, 1024) + rup(4 * hMp * hNp * 2, 1024) +
+                4 * rup(hMp * hNp * 2, 1024));
+}
+
+template <typename Take>
+void carve_fold_side(FoldSide& sd, int n, Take take) {
+    sd.n = n;
+    sd.hp = (int)rup(n / 2, 256);
+    const size_t e = (size_t)sd.hp * sd.hp * 2;
     for (int q = 0; q < 2; ++q) {
-        f.PeN[q] = take(hNp * hNp * 2); f.PoN[q] = take(hNp * hNp * 2);
-        f.PeTN[q] = take(hNp * hNp * 2); f.PoTN[q] = take(hNp * hNp * 2);
+        sd.Pe[q] = take(e); sd.Po[q] = take(e); sd.PeT[q] = take(e); sd.PoT[q] = take(e);
     }
-    f.lamPN = static_cast<float*>(take(2 * hNp * 4));
-    if (H != W) {
-        for (int q = 0; q < 2; ++q) {
-            f.PeM[q] = take(hMp * hMp * 2); f.PoM[q] = take(hMp * hMp * 2);
-            f.PeTM[q] = take(hMp * hMp * 2); f.PoTM[q] = take(hMp * hMp * 2);
-        }
-        f.lamPM = static_cast<float*>(take(2 * hMp * 4));
-    } else {
-        for (int q = 0; q < 2; ++q) {
-            f.PeM[q] = f.PeN[q]; f.PoM[q] = f.PoN[q]; f.PeTM[q] = f.PeTN[q]; f.PoTM[q] = f.PoTN[q];
-        }
-        f.lamPM = f.lamPN;
-    }
+    sd.lamP = static_cast<float*>(take(2 * (size_t)sd.hp * 4));
+}
+
+void build_fold_side(const FoldSide& sd) {
+    using B = __nv_bfloat16;
+    auto bf = [](void* x) { return static_cast<B*>(x); };
+    k_build_fold16<<<1024, 256>>>(bf(sd.Pe[0]), bf(sd.Po[0]), bf(sd.PeT[0]), bf(sd.PoT[0]),
+                                  bf(sd.Pe[1]), bf(sd.Po[1]), bf(sd.PeT[1]), bf(sd.PoT[1]),
+                                  sd.lamP, sd.n, sd.hp);
+}
+
+template <typename Take>
+void carve_fold_image(FoldImage& im, int H, int W, Take take) {
+    const FoldDims fd = fold_dims(H, W);
+    im.dim = fd;
+    const size_t hNp = fd.hNp, hMp = fd.hMp;
     for (int q = 0; q < 2; ++q) {
-        f.Re[q] = take((size_t)H * hMp * 2);
-        f.Ro[q] = take((size_t)H * hMp * 2);
+        im.Re[q] = take((size_t)H * hMp * 2);
+        im.Ro[q] = take((size_t)H * hMp * 2);
     }
     for (int q = 0; q < 2; ++q) {
         // T1 (four hMp x hNp blocks) and, after stage 2 has read it, T3 (two Hp x hMp blocks;
         // Hp <= 2 hNp)
         char* region = static_cast<char*>(take(4 * hMp * hNp * 2));
-        for (int b = 0; b < 4; ++b) f.T1[b][q] = region + (size_t)b * hMp * hNp * 2;
-        for (int x = 0; x < 2; ++x) f.T3[x][q] = region + (size_t)x * fd.Hp * hMp * 2;
+        for (int b = 0; b < 4; ++b) im.T1[b][q] = region + (size_t)b * hMp * hNp * 2;
+        for (int x = 0; x < 2; ++x) im.T3[x][q] = region + (size_t)x * fd.Hp * hMp * 2;
     }
     for (int q = 0; q < 2; ++q)
-        for (int b = 0; b < 4; ++b) f.T2[b][q] = take(hMp * hNp * 2);
-    for (int st = 0; st < 4; ++st) d.fold_tiles[st] = take(4 * sizeof(GemmTile));
-    // padding (columns hM.. of the folded residual, which nothing else writes) stays zero
-    cudaError_t e = cudaMemset(p_begin, 0, (size_t)(p - p_begin));
-    if (e != cudaSuccess) return e;
-    d.fold_host = fp;
-    d.Re = f.Re[0]; d.Relo = f.Re[1]; d.Ro = f.Ro[0]; d.Rolo = f.Ro[1];
-    using B = __nv_bfloat16;
-    auto bf = [](void* x) { return static_cast<B*>(x); };
-    k_build_fold16<<<1024, 256>>>(bf(f.PeN[0]), bf(f.PoN[0]), bf(f.PeTN[0]), bf(f.PoTN[0]),
-                                  bf(f.PeN[1]), bf(f.PoN[1]), bf(f.PeTN[1]), bf(f.PoTN[1]),
-                                  f.lamPN, H, fd.hNp);
-    if (H != W)
-        k_build_fold16<<<1024, 256>>>(bf(f.PeM[0]), bf(f.PoM[0]), bf(f.PeTM[0]), bf(f.PoTM[0]),
-                                      bf(f.PeM[1]), bf(f.PoM[1]), bf(f.PeTM[1]), bf(f.PoTM[1]),
-                                      f.lamPM, W, fd.hMp);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int cnt[4] = {2, 4, 2, 1};   // problems per stage
-    for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
+        for (int b = 0; b < 4; ++b) im.T2[b][q] = take(hMp * hNp * 2);
+}
+
+// Appends one image's nine problems (2, 4, 2 and 1 per stage) to the stage tables.
+bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
+                          const FoldSide& sN, const FoldSide& sM, int H, int W, const float* rU,
+                          float* zU, int ld, DevState* st, double* partials, int flexible,
+                          int skip, float tau) {
+    const FoldDims fd = im.dim;
+    const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
+    bool ok = true;
+    UEpiArgs base{};
+    base.st = st;
+    base.partials = partials;
+    base.flexible = flexible;
+    base.skip_if_done = skip;
+    int bbox = 128;
+    auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
+        ok &= make_map(&g.a0, A[0], ar, ac, UBM);
+        ok &= make_map(&g.a1, A[1], ar, ac, UBM);
+        ok &= make_map(&g.b0, Bm[0], br, bc, bbox);
+        ok &= make_map(&g.b1, Bm[1], br, bc, bbox);
+        g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
+    };
+    auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
+        ok &= make_map(&g.a2, A[0], ar, ac, UBM);
+        ok &= make_map(&g.a3, A[1], ar, ac, UBM);
+        ok &= make_map(&g.b2, Bm[0], br, bc, bbox);
+        ok &= make_map(&g.b3, Bm[1], br, bc, bbox);
+    };
+    // Every operand is stored padded (extents hNp, hMp, Hp, multiples of 256); padding rows and
+    // columns of the bases are zero, and the epilogues mask what lies beyond the half sides.
+    // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
+    // the second operand set reads the B rows mirrored (a negative start row reads zeros)
+    for (int x = 0; x < 2; ++x) {
+        GemmTile g{};
+        set0(g, x ? sM.PoT : sM.PeT, hMp, hMp, x ? im.Ro : im.Re, H, hMp);
+        g.mirror_b1 = 1;
+        g.nb_rows = H;
+        g.M = hMp; g.N = hNp; g.K = hMp;
+        g.ep = base;
+        g.ep.C = im.T1[2 * x][0]; g.ep.C_lo = im.T1[2 * x][1];
+        g.ep.C2 = im.T1[2 * x + 1][0]; g.ep.C2_lo = im.T1[2 * x + 1][1];
+        g.ep.ldc = hNp;
+        g.ep.vn = hN;
+        tab[0].push_back(g);
+    }
+    // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
+    // divided by the eigenvalue sum at frequencies (2k' + y, 2l' + x); r^T z from the spectral
+    // coefficients, two per-tile slots (one per CTA) per 256 x 256 tile of the image
+    const int tiles2 = (hMp / 256) * (hNp / 256);
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            GemmTile g{};
+            set0(g, im.T1[2 * x + y], hMp, hNp, y ? sN.PoT : sN.PeT, hNp, hNp);
+            g.M = hMp; g.N = hNp; g.K = hNp;
+            g.ep = base;
+            g.ep.C = im.T2[2 * x + y][0]; g.ep.C_lo = im.T2[2 * x + y][1]; g.ep.ldc = hNp;
+            g.ep.vm = hM; g.ep.vn = hN;
+            g.ep.lam_m = sM.lamP + x * hMp;
+            g.ep.lam_n = sN.lamP + y * hNp;
+            g.ep.scale = tau;
+            g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
+            g.ep.rho_base = (2 * x + y) * tiles2;
+            g.ep.rho_count = 2 * 4 * tiles2;
+            tab[1].push_back(g);
+        }
+    bbox = kPairDualN / 2;
+    // stage 3 (x): with E from the even and O from the odd frequencies along i,
+    // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O (i' < hN)
+    for (int x = 0; x < 2; ++x) {
+        GemmTile g{};
+        set0(g, sN.Pe, hNp, hNp, im.T2[2 * x], hMp, hNp);
+        set1(g, sN.Po, hNp, hNp, im.T2[2 * x + 1], hMp, hNp);
+        g.M = hNp; g.N = hMp; g.K = hNp;
+        g.ep = base;
+        g.ep.C = im.T3[x][0]; g.ep.C_lo = im.T3[x][1]; g.ep.ldc = hMp; g.ep.mrows = H;
+        g.ep.vm = hN;
+        tab[2].push_back(g);
+    }
+    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O (i < H, j' < hM), E from T3e, O from T3o
+    {
+        GemmTile g{};
+        set0(g, im.T3[0], fd.Hp, hMp, sM.Pe, hMp, hMp);
+        set1(g, im.T3[1], fd.Hp, hMp, sM.Po, hMp, hMp);
+        g.M = fd.Hp; g.N = hMp; g.K = hMp;
+        g.ep = base;
+        g.ep.C = zU; g.ep.ldc = ld; g.ep.mcols = W; g.ep.rU = rU;
+        g.ep.vm = H; g.ep.vn = hM;
+        tab[3].push_back(g);
+    }
+    return ok;
+}
+
+// Tile grid of every problem (256 rows x 128 columns for the mirrored stage 1, 256 x kPairDualN
+// for the two-set stages, 256 x 256 for stage 2) and each problem's first tile in its launch.
+bool number_fold_tiles(std::vector<GemmTile> (&tab)[4], int (&tiles)[4]) {
+    for (int k = 0; k < 4; ++k) {
+        int n = 0;
+        for (auto& g : tab[k]) {
+            const int tn = k == 0 ? 128 : (k == 1 ? 256 : kPairDualN);
+            if (g.M % 256 != 0 || g.N % tn != 0) return false;
+            g.gx = g.N / tn;
+            g.blk0 = n;
+            n += (g.M / 256) * g.gx;
+        }
+        tiles[k] = n;
+    }
+    return true;
+}
+
+cudaError_t set_fold_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e;
     for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>,
                     k2_umma_gemm<UE_EIG16_RHO, 0, 256>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
@@ -1431,133 +1602,25 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
                                  Q2Cfg<1, kPairDualN>::kSmem);
         if (e != cudaSuccess) return e;
     }
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&f.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return e;
+    done = true;
     return cudaSuccess;
 }
 
-// (Re)builds the four stage tables of the folded form for the given planes, state and flags and
-// copies them in stream order (kernels still reading the previous tables finish first).
-cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU, int ld,
-                      DevState* st, double* partials, int flexible, int skip, cudaStream_t s) {
-    const int H = d.H, W = d.W;
-    const FoldDims fd = f.dim;
-    const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
-    bool ok = true;
-    UEpiArgs base{};
-    base.st = st;
-    base.partials = partials;
-    base.flexible = flexible;
-    base.skip_if_done = skip;
-    // 64 columns of K per stage: measured faster than 32-column stages with 64-byte swizzling
-    // (twice the stages, but twice the TMA boxes and barrier round trips per multiply-add)
-    const int kb = UBK;
-    int bbox = 128;
-    auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a0, A[0], ar, ac, UBM, kb);
-        ok &= make_map(&g.a1, A[1], ar, ac, UBM, kb);
-        ok &= make_map(&g.b0, Bm[0], br, bc, bbox, kb);
-        ok &= make_map(&g.b1, Bm[1], br, bc, bbox, kb);
-        g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
-    };
-    auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a2, A[0], ar, ac, UBM, kb);
-        ok &= make_map(&g.a3, A[1], ar, ac, UBM, kb);
-        ok &= make_map(&g.b2, Bm[0], br, bc, bbox, kb);
-        ok &= make_map(&g.b3, Bm[1], br, bc, bbox, kb);
-    };
-    for (auto& t : f.tab) t.clear();
-    // Every operand is stored padded (extents hNp, hMp, Hp, multiples of 256); padding rows and
-    // columns of the bases are zero, and the epilogues mask what lies beyond the half sides.
-    // stage 1 (x = e, o): T1x+-[l'][i'] = Y(i') +- Y(H-1-i') with Y(i) = sum_j' PxT_M[l'][j'] Rx[i][j'];
-    // the second operand set reads the B rows mirrored (a negative start row reads zeros)
-    for (int x = 0; x < 2; ++x) {
-        GemmTile g{};
-        set0(g, x ? f.PoTM : f.PeTM, hMp, hMp, x ? f.Ro : f.Re, H, hMp);
-        g.mirror_b1 = 1;
-        g.nb_rows = H;
-        g.M = hMp; g.N = hNp; g.K = hMp;
-        g.ep = base;
-        g.ep.C = f.T1[2 * x][0]; g.ep.C_lo = f.T1[2 * x][1];
-        g.ep.C2 = f.T1[2 * x + 1][0]; g.ep.C2_lo = f.T1[2 * x + 1][1];
-        g.ep.ldc = hNp;
-        g.ep.vn = hN;
-        f.tab[0].push_back(g);
-    }
-    // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
-    // divided by the eigenvalue sum at frequencies (2k' + y, 2l' + x)
-    for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 2; ++y) {
-            GemmTile g{};
-            set0(g, f.T1[2 * x + y], hMp, hNp, y ? f.PoTN : f.PeTN, hNp, hNp);
-            g.M = hMp; g.N = hNp; g.K = hNp;
-            g.ep = base;
-            g.ep.C = f.T2[2 * x + y][0]; g.ep.C_lo = f.T2[2 * x + y][1]; g.ep.ldc = hNp;
-            g.ep.vm = hM; g.ep.vn = hN;
-            g.ep.lam_m = f.lamPM + x * hMp;
-            g.ep.lam_n = f.lamPN + y * hNp;
-            g.ep.scale = d.tau;
-            g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
-            f.tab[1].push_back(g);
-        }
-    bbox = kPairDualN / 2;
-    // stage 3 (x): with E from the even and O from the odd frequencies along i,
-    // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O (i' < hN)
-    for (int x = 0; x < 2; ++x) {
-        GemmTile g{};
-        set0(g, f.PeN, hNp, hNp, f.T2[2 * x], hMp, hNp);
-        set1(g, f.PoN, hNp, hNp, f.T2[2 * x + 1], hMp, hNp);
-        g.M = hNp; g.N = hMp; g.K = hNp;
-        g.ep = base;
-        g.ep.C = f.T3[x][0]; g.ep.C_lo = f.T3[x][1]; g.ep.ldc = hMp; g.ep.mrows = H;
-        g.ep.vm = hN;
-        f.tab[2].push_back(g);
-    }
-    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O (i < H, j' < hM), E from T3e, O from T3o
-    {
-        GemmTile g{};
-        set0(g, f.T3[0], fd.Hp, hMp, f.PeM, hMp, hMp);
-        set1(g, f.T3[1], fd.Hp, hMp, f.PoM, hMp, hMp);
-        g.M = fd.Hp; g.N = hMp; g.K = hMp;
-        g.ep = base;
-        g.ep.C = zU; g.ep.ldc = ld; g.ep.mcols = W; g.ep.rU = rU;
-        g.ep.vm = H; g.ep.vn = hM;
-        f.tab[3].push_back(g);
-    }
-    if (!ok) return cudaErrorNotSupported;
-    for (int k = 0; k < 4; ++k) {
-        // output tiles: 256 rows x 128 columns for the mirrored stage 1, 256 x kPairDualN for the
-        // two-set stages, 256 x 256 for stage 2
-        const int tm = 256;
-        int tiles = 0;
-        for (auto& g : f.tab[k]) {
-            const int tn = k == 0 ? 128 : (k == 1 ? 256 : kPairDualN);
-            if (g.M % tm != 0 || g.N % tn != 0) return cudaErrorInvalidValue;
-            g.gx = g.N / tn;
-            g.blk0 = tiles;
-            tiles += (g.M / tm) * g.gx;
-        }
-        if ((int)f.tab[k].size() != d.fold_count[k]) return cudaErrorInvalidValue;
-        f.tiles[k] = tiles;
-        cudaError_t e = cudaMemcpyAsync(d.fold_tiles[k], f.tab[k].data(),
-                                        f.tab[k].size() * sizeof(GemmTile),
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
-    f.bound = true;
-    f.rU = rU; f.zU = zU; f.ld = ld; f.st = st; f.partials = partials;
-    f.flexible = flexible; f.skip = skip; f.tau = d.tau;
-    return cudaSuccess;
+int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
 }
 
-cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho, cudaStream_t s) {
-    auto tab = [&](int k) { return static_cast<const GemmTile*>(d.fold_tiles[k]); };
-    auto grid = [&](int k) { return 2 * std::min(f.tiles[k], f.n_sm / 2); };
+// The four stage launches over a set of tables (one image, or every image of a batch).
+cudaError_t launch_fold_stages(void* const (&d_tab)[4], const int (&count)[4],
+                               const int (&tiles)[4], int n_sm, int reduce_rho, cudaStream_t s) {
+    auto tab = [&](int k) { return static_cast<const GemmTile*>(d_tab[k]); };
+    auto grid = [&](int k) { return 2 * std::max(1, std::min(tiles[k], n_sm / 2)); };
     const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1, kPairDualN>::kSmem;
-    const int* c = d.fold_count;
-    const int* t = f.tiles;
+    const int* c = count;
+    const int* t = tiles;
     // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
     k2_umma_gemm<UE_FOLD16, 0, 128><<<grid(0), k2Threads, s0, s>>>(tab(0), c[0], t[0]);
     if (reduce_rho)
@@ -1567,6 +1630,83 @@ cudaError_t fold_launch_pair(const DctPlan& d, const FoldBufs& f, int reduce_rho
     k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
     k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
+}
+
+// Host-side record of a single-image plan's folded form and of the arguments its device tables
+// were last built for (the tables bake in the planes, the CG state and the epilogue flags).
+struct FoldBufs {
+    FoldSide sN, sM;
+    FoldImage img;
+    FoldDims dim{};
+    std::vector<GemmTile> tab[4];
+    bool bound = false;
+    const float* rU = nullptr;
+    float* zU = nullptr;
+    int ld = 0, flexible = 0, skip = 0;
+    DevState* st = nullptr;
+    double* partials = nullptr;
+    float tau = 0.f;
+    int n_sm = 0;                  // SMs of the device: persistent grid size
+    int tiles[4] = {0, 0, 0, 0};   // output tiles per stage
+};
+
+size_t fold_bytes(int H, int W) {
+    size_t b = fold_side_bytes(H) + fold_image_bytes(H, W);
+    if (H != W) b += fold_side_bytes(W);
+    return b + 4 * rup(4 * sizeof(GemmTile), 1024) + 64 * 1024;
+}
+
+cudaError_t fold_setup(DctPlan& d, char* p) {
+    const int H = d.H, W = d.W;
+    char* const p_begin = p;
+    auto take = [&](size_t bytes) {
+        void* r = p;
+        p += rup(bytes, 1024);
+        return r;
+    };
+    FoldBufs* fp = new FoldBufs();
+    FoldBufs& f = *fp;
+    d.fold_host = fp;
+    carve_fold_side(f.sN, H, take);
+    if (H != W) carve_fold_side(f.sM, W, take);
+    else f.sM = f.sN;
+    carve_fold_image(f.img, H, W, take);
+    f.dim = f.img.dim;
+    for (int st = 0; st < 4; ++st) d.fold_tiles[st] = take(4 * sizeof(GemmTile));
+    // padding (columns hM.. of the folded residual, which nothing else writes) stays zero
+    cudaError_t e = cudaMemset(p_begin, 0, (size_t)(p - p_begin));
+    if (e != cudaSuccess) return e;
+    d.Re = f.img.Re[0]; d.Relo = f.img.Re[1]; d.Ro = f.img.Ro[0]; d.Rolo = f.img.Ro[1];
+    build_fold_side(f.sN);
+    if (H != W) build_fold_side(f.sM);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int cnt[4] = {2, 4, 2, 1};   // problems per stage
+    for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
+    if ((e = set_fold_attrs()) != cudaSuccess) return e;
+    f.n_sm = device_sms();
+    return f.n_sm > 1 ? cudaSuccess : cudaErrorInvalidDevice;
+}
+
+// (Re)builds the four stage tables of the folded form for the given planes, state and flags and
+// copies them in stream order (kernels still reading the previous tables finish first).
+cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU, int ld,
+                      DevState* st, double* partials, int flexible, int skip, cudaStream_t s) {
+    for (auto& t : f.tab) t.clear();
+    if (!append_fold_problems(f.tab, f.img, f.sN, f.sM, d.H, d.W, rU, zU, ld, st, partials,
+                              flexible, skip, d.tau))
+        return cudaErrorNotSupported;
+    if (!number_fold_tiles(f.tab, f.tiles)) return cudaErrorInvalidValue;
+    for (int k = 0; k < 4; ++k) {
+        if ((int)f.tab[k].size() != d.fold_count[k]) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemcpyAsync(d.fold_tiles[k], f.tab[k].data(),
+                                        f.tab[k].size() * sizeof(GemmTile),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    f.bound = true;
+    f.rU = rU; f.zU = zU; f.ld = ld; f.st = st; f.partials = partials;
+    f.flexible = flexible; f.skip = skip; f.tau = d.tau;
+    return cudaSuccess;
 }
 
 cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
@@ -1583,10 +1723,10 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
     const size_t n = (size_t)d.H * (d.W % 8 == 0 ? d.W / 8 : d.W / 2);
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
     k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, f.dim.hMp, static_cast<B*>(d.Re),
-                                    static_cast<B*>(d.Relo),
-                                    static_cast<B*>(d.Ro), static_cast<B*>(d.Rolo), st,
-                                    skip_if_done);
-    return fold_launch_pair(d, f, reduce_rho, s);
+                                    static_cast<B*>(d.Relo), static_cast<B*>(d.Ro),
+                                    static_cast<B*>(d.Rolo), st, skip_if_done);
+    void* const tabs[4] = {d.fold_tiles[0], d.fold_tiles[1], d.fold_tiles[2], d.fold_tiles[3]};
+    return launch_fold_stages(tabs, d.fold_count, f.tiles, f.n_sm, reduce_rho, s);
 }
 
 }  // namespace
