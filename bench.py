@@ -158,6 +158,8 @@ def main():
                          "--width 16000 for the paper's 4000 x M scaling shapes")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dct-form", default="auto", choices=["auto", "direct", "folded"],
+                    help="preconditioner form (auto: folded where allowed)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batched"],
                     help="single: one 4096 x 4096 image per step (the benchmark); batched: 64 "
@@ -201,7 +203,7 @@ def main():
     flexible = 1 if prec == "bf16" else 0
     plan = irls.Plan(n, wd, tau=TAU, delta=DELTA, outer_iters=args.outer, cg_tol=CG_TOL,
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible,
-                     cg_schedule=args.cg_schedule, system=args.system)
+                     cg_schedule=args.cg_schedule, system=args.system, dct_form=args.dct_form)
     stream = torch.cuda.current_stream()
     U = torch.empty_like(X)
     for _ in range(args.warmup):
@@ -386,7 +388,8 @@ def batched_arm(args, rank, world, local):
     mpix = sum(h * w for h, w in shapes) / 1e6
     prec = args.precision if args.precision != "fp32" else "bf16x3"
     b = irls.Batch(shapes, precision=prec, tau=TAU, delta=DELTA, outer_iters=args.outer,
-                   cg_tol=CG_TOL, cg_max_iter=1000, flexible_cg=1 if prec == "bf16" else 0)
+                   cg_tol=CG_TOL, cg_max_iter=1000, flexible_cg=1 if prec == "bf16" else 0,
+                   dct_form=args.dct_form)
     for _ in range(args.warmup):
         b.unwrap(Xs, Cs)
     torch.cuda.synchronize()
@@ -407,7 +410,8 @@ def batched_arm(args, rank, world, local):
     if not args.no_e2e:
         for X, C, (h, w) in zip(Xs, Cs, shapes):
             with irls.Plan(h, w, precision=prec, tau=TAU, delta=DELTA, outer_iters=args.outer,
-                           cg_tol=CG_TOL, cg_max_iter=1000) as p:
+                           cg_tol=CG_TOL, cg_max_iter=1000,
+                           flexible_cg=1 if prec == "bf16" else 0, dct_form=args.dct_form) as p:
                 p.unwrap(X, C)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -426,6 +430,7 @@ def batched_arm(args, rank, world, local):
                                    f"delta {DELTA:g}, tau {TAU:g}, cg_tol {CG_TOL:g}, {prec}",
                        "cg_iters_total": sum(x["cg_total"] for x in st),
                        "cg_iters_max_tile": max(x["cg_total"] for x in st),
+                       "dct_form": "folded" if b.folded else "direct",
                        "uses_graphs": b.uses_graphs},
             "single_image_sequential_mpix_s": (mpix / t_single) if t_single else None,
             "clocks": clk,

@@ -183,8 +183,12 @@ int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
  * d_U[t]; per_tile (nullable) receives ntiles statistics.  Synchronous with respect to the host;
  * `stream` is ordered before and after the batch.  irls_unwrap_batched is create + run +
  * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist.
- * The grouped preconditioner runs in the direct form (dct_form IRLS_DCT_FOLDED is
- * IRLS_ERR_UNSUPPORTED). */
+ * Preconditioner form: with dct_form IRLS_DCT_AUTO the batch runs the folded form (four
+ * persistent CTA-pair GEMM launches over every image's tiles, plus one fold of r_U) when every
+ * image allows it (IRLS_PREC_BF16X3, even sides >= 256), else the direct grouped form;
+ * IRLS_DCT_FOLDED where some image does not allow it is IRLS_ERR_UNSUPPORTED.  An image's
+ * results do not depend on the batch it runs in: they equal, bit for bit, a single-image plan
+ * in the same form.  irls_batch_dct_form returns IRLS_DCT_FOLDED or IRLS_DCT_DIRECT. */
 int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* opts,
                       irls_batch* out);
 int irls_batch_destroy(irls_batch batch);
@@ -195,6 +199,7 @@ int irls_unwrap_batched(int ntiles, const int* H, const int* W, const float* con
                         const float* const* d_coherence, float* const* d_U, const irls_opts* opts,
                         irls_stats* per_tile, void* stream);
 int irls_batch_uses_graphs(irls_batch batch);
+int irls_batch_dct_form(irls_batch batch);
 
 /* Forward solve that records what the adjoint needs (the reverse sweep below):
  * the wrapped gradients G and weights C it used, and V^k of every outer step k = 0..K (the

@@ -210,6 +210,11 @@ class Batch:
     def uses_graphs(self):
         return lib().irls_batch_uses_graphs(self._h) == 1
 
+    @property
+    def folded(self):
+        """True when the batch's preconditioner runs in the folded (even / odd) form."""
+        return lib().irls_batch_dct_form(self._h) == DCT_FORMS["folded"]
+
     def unwrap(self, Xs, cohs=None, outs=None, stream=None):
         """Xs, cohs: lists of contiguous float32 CUDA tensors; returns (list of U, list of stats)."""
         torch = _torch()

@@ -106,6 +106,7 @@ SIGNATURES = {
                                  ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(Opts),
                                  ctypes.POINTER(Stats), _P]),
     "irls_batch_uses_graphs": (_I, [_P]),
+    "irls_batch_dct_form": (_I, [_P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),

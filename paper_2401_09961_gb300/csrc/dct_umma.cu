@@ -927,7 +927,6 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     constexpr uint32_t kAcc = C::kAcc;
     constexpr int NB = C::kBufs;
     constexpr uint32_t kCols = 512;
-    DevState* st0 = tiles[0].ep.st;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -942,7 +941,8 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
     __shared__ int s_err;
     __shared__ int s_skip;
-    __shared__ double s_red[2][k2EpiWarps];
+    __shared__ double s_tot[k2EpiWarps];
+    __shared__ int s_last;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
@@ -1106,48 +1106,42 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(te0 + 8u * (uint32_t)b);
             if constexpr (EPI == UE_EIG16_RHO) {
-                // r^T z of an image: a CTA meets the image's tiles as one run (t - a < npairs
-                // apart in the image's consecutive range [a, b)); at the end of its run it adds
-                // its epilogue warps' sums in a fixed order into the image's slot for (first tile
-                // of the run, CTA); the warp that fills the image's last slot adds the
-                // 2 min(npairs, b - a) slots in a fixed order and forms rho and beta
+                // r^T z of an image, in an order fixed by the image's own tile numbering (the same
+                // alone or in a batch): each epilogue warp stores its sum over the tile into slot
+                // ((tile, CTA), warp); a CTA meets the image's consecutive tile range [a, b) as
+                // one run, and at the end of it counts itself done; the CTA that completes the
+                // count adds all the image's slots and forms rho and beta
+                double v = (double)part;
+                part = 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0)
+                    ep.partials[((ep.rho_base + local) * 2 + (int)rank) * k2EpiWarps + (warp - 2)] = v;
                 const int a = g.blk0 - ep.rho_base, b = a + ep.rho_count;
-                const int tn_ = t + npairs;
-                const bool run_end = tn_ >= b || tn_ >= total_tiles;
-                if (run_end) {
-                    double v = (double)part;
-                    part = 0.f;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    const int buf = nsync & 1;
-                    if (lane == 0) s_red[buf][warp - 2] = v;
+                if (t + npairs >= b || t + npairs >= total_tiles) {
+                    if (lane == 0) __threadfence();
                     if (!epi_sync(epibar, nsync, &s_err)) break;
-                    if (warp == 2) {
-                        const int first = a + ((pair - a) % npairs + npairs) % npairs;
-                        const int nslot = 2 * min(npairs, b - a);
-                        unsigned last = 0;
-                        if (lane == 0) {
-                            double sum = 0.0;
-                            for (int w = 0; w < k2EpiWarps; ++w) sum += s_red[buf][w];
-                            ep.partials[(first - a) * 2 + (int)rank] = sum;
-                            __threadfence();
-                            const unsigned prev = atomicAdd(&ep.st->counter, 1u);
-                            last = prev == (unsigned)nslot - 1u;
-                        }
-                        last = __shfl_sync(0xffffffffu, last, 0);
-                        if (last) {
-                            __threadfence();
-                            double tot = 0.0;
-                            for (int i = lane; i < nslot; i += 32) tot += __ldcg(&ep.partials[i]);
+                    if (warp == 2 && lane == 0) {
+                        const unsigned prev = atomicAdd(&ep.st->counter, 1u);
+                        s_last = prev == (unsigned)(2 * min(npairs, b - a)) - 1u;
+                    }
+                    if (!epi_sync(epibar, nsync, &s_err)) break;
+                    if (s_last) {
+                        __threadfence();
+                        const int n = ep.rho_count * 2 * k2EpiWarps;
+                        const int e = threadIdx.x - 64;
+                        double tot = 0.0;
+                        for (int i = e; i < n; i += 32 * k2EpiWarps) tot += __ldcg(&ep.partials[i]);
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1)
-                                tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                            if (lane == 0) {
-                                finish_rho(ep, tot);
-                                ep.st->counter = 0u;
-                            }
+                        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+                        if (lane == 0) s_tot[warp - 2] = tot;
+                        if (!epi_sync(epibar, nsync, &s_err)) break;
+                        if (warp == 2 && lane == 0) {
+                            double sum = 0.0;
+                            for (int w = 0; w < k2EpiWarps; ++w) sum += s_tot[w];
+                            finish_rho(ep, sum);
+                            ep.st->counter = 0u;
                         }
-                        __syncwarp();
                     }
                 }
             }
@@ -1163,8 +1157,12 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         tmem_dealloc_pair(tmem, kCols);
     }
     if (threadIdx.x == 0 && *(volatile int*)&s_err) {
-        atomicOr(&st0->status, ST_TIMEOUT);
-        st0->done = 1;
+        // a wait gave up: every image of the launch stops with the timeout status
+        for (int i = 0; i < T; ++i) {
+            DevState* sti = tiles[i].ep.st;
+            atomicOr(&sti->status, ST_TIMEOUT);
+            sti->done = 1;
+        }
     }
     static_assert(EPI != UE_ZU_RHO && EPI != UE_UNFOLDZ_RHO, "r^T z: the per-tile form only");
     cluster_sync_all();
@@ -1244,16 +1242,29 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
 // each split into bf16 hi + lo, pitch ldo (columns W/2 .. ldo-1 are left alone: zero).  W a
 // multiple of 8: four columns per thread, the float4 at j and the float4 ending at W-1-j
 // (reversed; the pitch ld is a multiple of 4 floats); otherwise one column per thread.
-__global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W, int ldo,
-                         __nv_bfloat16* __restrict__ Re, __nv_bfloat16* __restrict__ Relo,
-                         __nv_bfloat16* __restrict__ Ro, __nv_bfloat16* __restrict__ Rolo,
-                         const DevState* st, int skip_if_done) {
-    if (skip_if_done && st->done) return;
+// One image's even / odd column folds of r_U for the folded preconditioner (hi and lo bf16
+// parts, row pitch ldo): Re[i][j'] = r[i][j'] + r[i][W-1-j'], Ro[i][j'] = r[i][j'] - r[i][W-1-j'],
+// j' < W/2.  Each element is formed on its own, so the result does not depend on the launch.
+struct FoldRRec {
+    const float* rU;
+    int ld, H, W, ldo;
+    __nv_bfloat16 *Re, *Relo, *Ro, *Rolo;
+    const DevState* st;
+    int blk0, nblk;   // the image's blocks in a batched launch
+};
+
+__device__ __forceinline__ void fold_r_body(const FoldRRec& f, int bid, int nblk) {
+    const float* __restrict__ rU = f.rU;
+    const int ld = f.ld, H = f.H, W = f.W, ldo = f.ldo;
+    __nv_bfloat16* __restrict__ Re = f.Re;
+    __nv_bfloat16* __restrict__ Relo = f.Relo;
+    __nv_bfloat16* __restrict__ Ro = f.Ro;
+    __nv_bfloat16* __restrict__ Rolo = f.Rolo;
     const int h = W / 2;
     if (W % 8 != 0) {
         const size_t total = (size_t)H * h;
-        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-             t += (size_t)gridDim.x * blockDim.x) {
+        for (size_t t = bid * (size_t)blockDim.x + threadIdx.x; t < total;
+             t += (size_t)nblk * blockDim.x) {
             const int i = (int)(t / h), j = (int)(t % h);
             const float a = rU[(size_t)i * ld + j], b = rU[(size_t)i * ld + (W - 1 - j)];
             const float se = a + b, so = a - b;
@@ -1270,8 +1281,8 @@ __global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W, int
     }
     const int h4 = h / 4;
     const size_t total = (size_t)H * h4;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-         t += (size_t)gridDim.x * blockDim.x) {
+    for (size_t t = bid * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)nblk * blockDim.x) {
         const int i = (int)(t / h4), j = (int)(t % h4) * 4;
         const float4 a = *reinterpret_cast<const float4*>(rU + (size_t)i * ld + j);
         const float4 bm = *reinterpret_cast<const float4*>(rU + (size_t)i * ld + (W - 4 - j));
@@ -1296,6 +1307,30 @@ __global__ void k_fold_r(const float* __restrict__ rU, int ld, int H, int W, int
                 make_uint2(pack_bf16(ol[0], ol[1]), pack_bf16(ol[2], ol[3]));
         }
     }
+}
+
+__global__ void k_fold_r(FoldRRec f, int skip_if_done) {
+    if (skip_if_done && f.st->done) return;
+    fold_r_body(f, blockIdx.x, gridDim.x);
+}
+
+// Batched: each image's blocks fold its own r_U; images whose CG run has stopped return at once.
+__global__ void k_fold_r_batched(const FoldRRec* __restrict__ recs, int T) {
+    int lo = 0, hi = T - 1;
+    const int bid = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (recs[mid].blk0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    const FoldRRec f = recs[lo];
+    if (f.st->done) return;
+    fold_r_body(f, bid - f.blk0, f.nblk);
+}
+
+// blocks of one image's fold (a grid-stride loop over rows x quads, at most 8192 blocks)
+int fold_r_blocks(int H, int W) {
+    const size_t n = (size_t)H * (W % 8 == 0 ? W / 8 : W / 2);
+    return (int)std::min<size_t>((n + 255) / 256, 8192);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1526,7 +1561,7 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
     }
     // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
     // divided by the eigenvalue sum at frequencies (2k' + y, 2l' + x); r^T z from the spectral
-    // coefficients, two per-tile slots (one per CTA) per 256 x 256 tile of the image
+    // coefficients, numbered by the image's own 256 x 256 tiles (tiles2 per problem)
     const int tiles2 = (hMp / 256) * (hNp / 256);
     for (int x = 0; x < 2; ++x)
         for (int y = 0; y < 2; ++y) {
@@ -1541,7 +1576,7 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
             g.ep.scale = tau;
             g.ep.keep_origin = (x == 0 && y == 0) ? 0 : 1;
             g.ep.rho_base = (2 * x + y) * tiles2;
-            g.ep.rho_count = 2 * 4 * tiles2;
+            g.ep.rho_count = 4 * tiles2;
             tab[1].push_back(g);
         }
     bbox = kPairDualN / 2;
@@ -1584,6 +1619,19 @@ bool number_fold_tiles(std::vector<GemmTile> (&tab)[4], int (&tiles)[4]) {
             n += (g.M / 256) * g.gx;
         }
         tiles[k] = n;
+    }
+    // stage 2 numbers an image's r^T z slots by its own tiles: its four problems are consecutive,
+    // problem q starts at tile rho_base = q * tiles2 of the image, rho_count = 4 * tiles2
+    if (tab[1].size() % 4 != 0) return false;
+    for (size_t i = 0; i < tab[1].size(); i += 4) {
+        const int a = tab[1][i].blk0;
+        for (int q = 0; q < 4; ++q) {
+            const GemmTile& g = tab[1][i + q];
+            const int nt = (g.M / 256) * g.gx;
+            if (g.ep.rho_base != q * nt || g.ep.rho_count != 4 * nt || g.blk0 != a + q * nt ||
+                g.ep.st != tab[1][i].ep.st)
+                return false;
+        }
     }
     return true;
 }
@@ -1630,6 +1678,17 @@ cudaError_t launch_fold_stages(void* const (&d_tab)[4], const int (&count)[4],
     k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
     k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
     return cudaGetLastError();
+}
+
+FoldRRec fold_r_rec(const FoldImage& im, const float* rU, int ld, int H, int W,
+                    const DevState* st) {
+    using B = __nv_bfloat16;
+    FoldRRec r{};
+    r.rU = rU; r.ld = ld; r.H = H; r.W = W; r.ldo = im.dim.hMp;
+    r.Re = static_cast<B*>(im.Re[0]); r.Relo = static_cast<B*>(im.Re[1]);
+    r.Ro = static_cast<B*>(im.Ro[0]); r.Rolo = static_cast<B*>(im.Ro[1]);
+    r.st = st;
+    return r;
 }
 
 // Host-side record of a single-image plan's folded form and of the arguments its device tables
@@ -1719,12 +1778,8 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
         cudaError_t e = fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, s);
         if (e != cudaSuccess) return e;
     }
-    using B = __nv_bfloat16;
-    const size_t n = (size_t)d.H * (d.W % 8 == 0 ? d.W / 8 : d.W / 2);
-    const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
-    k_fold_r<<<blocks, 256, 0, s>>>(rU, ld, d.H, d.W, f.dim.hMp, static_cast<B*>(d.Re),
-                                    static_cast<B*>(d.Relo), static_cast<B*>(d.Ro),
-                                    static_cast<B*>(d.Rolo), st, skip_if_done);
+    k_fold_r<<<fold_r_blocks(d.H, d.W), 256, 0, s>>>(fold_r_rec(f.img, rU, ld, d.H, d.W, st),
+                                                      skip_if_done);
     void* const tabs[4] = {d.fold_tiles[0], d.fold_tiles[1], d.fold_tiles[2], d.fold_tiles[3]};
     return launch_fold_stages(tabs, d.fold_count, f.tiles, f.n_sm, reduce_rho, s);
 }
@@ -1887,8 +1942,21 @@ struct BatchLayout {
     size_t side_bytes = 0, image_bytes = 0, tiles_bytes = 0, total = 0;
 };
 
-BatchLayout batch_layout(const int* H, const int* W, int T, int prec) {
+BatchLayout batch_layout(const int* H, const int* W, int T, int prec, int fold) {
     BatchLayout L;
+    if (fold) {
+        for (int t = 0; t < T; ++t)
+            for (int n : {H[t], W[t]})
+                if (std::find(L.sides.begin(), L.sides.end(), n) == L.sides.end())
+                    L.sides.push_back(n);
+        for (int n : L.sides) L.side_bytes += fold_side_bytes(n);
+        for (int t = 0; t < T; ++t) L.image_bytes += fold_image_bytes(H[t], W[t]);
+        // problems per image and stage: 2, 4, 2, 1; then the fold records
+        L.tiles_bytes = (2 + 4 + 2 + 1 + 4) * rup((size_t)T * sizeof(GemmTile), 1024) +
+                        rup((size_t)T * sizeof(FoldRRec), 1024);
+        L.total = L.side_bytes + L.image_bytes + L.tiles_bytes + 4096;
+        return L;
+    }
     const size_t mult = prec == IRLS_PREC_BF16X3 ? 2 : 1;
     for (int t = 0; t < T; ++t)
         for (int n : {H[t], W[t]})
@@ -1906,18 +1974,90 @@ BatchLayout batch_layout(const int* H, const int* W, int T, int prec) {
 
 }  // namespace
 
-size_t batch_dct_bytes(const int* H, const int* W, int T, int prec) {
-    return batch_layout(H, W, T, prec).total;
+// Per-tile r^T z slots of the folded form's stage 2: 16 per 256 x 256 tile (two CTAs x eight
+// epilogue warps), four quarter problems of rup(H/2, 256) x rup(W/2, 256)
+size_t dct_rho_slots(int H, int W) {
+    return (size_t)(rup(H / 2, 256) / 256) * (rup(W / 2, 256) / 256) * 4 * 2 * k2EpiWarps;
 }
 
+size_t batch_dct_bytes(const int* H, const int* W, int T, int prec, int fold) {
+    return batch_layout(H, W, T, prec, fold).total;
+}
+
+namespace {
+
+// Folded form of a batch: bases per distinct side, each image's operands, and the four stage
+// tables holding every image's problems in image order (an image's problems are consecutive,
+// as its per-tile r^T z slots need).  The workspace arrives zeroed (padding stays zero).
+cudaError_t batch_fold_setup(BatchDctPlan& bd, const int* H, const int* W, int T,
+                             const BatchLayout& L, char* p, float tau, int flexible,
+                             const float* const* rU, float* const* zU, const int* ld,
+                             DevState* states, double* const* partials) {
+    auto take = [&](size_t bytes) {
+        void* r = p;
+        p += rup(bytes, 1024);
+        return r;
+    };
+    std::vector<FoldSide> sides(L.sides.size());
+    for (size_t i = 0; i < L.sides.size(); ++i) {
+        carve_fold_side(sides[i], L.sides[i], take);
+        build_fold_side(sides[i]);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto side = [&](int n) -> const FoldSide& {
+        for (const auto& sd : sides)
+            if (sd.n == n) return sd;
+        return sides[0];
+    };
+    std::vector<GemmTile> tab[4];
+    std::vector<FoldRRec> recs(T);
+    int blk = 0;
+    for (int t = 0; t < T; ++t) {
+        FoldImage im;
+        carve_fold_image(im, H[t], W[t], take);
+        if (!append_fold_problems(tab, im, side(H[t]), side(W[t]), H[t], W[t], rU[t], zU[t], ld[t],
+                                  states + t, partials[t], flexible, 1, tau))
+            return cudaErrorNotSupported;
+        recs[t] = fold_r_rec(im, rU[t], ld[t], H[t], W[t], states + t);
+        recs[t].blk0 = blk;
+        recs[t].nblk = fold_r_blocks(H[t], W[t]);
+        blk += recs[t].nblk;
+    }
+    int tiles[4];
+    if (!number_fold_tiles(tab, tiles)) return cudaErrorInvalidValue;
+    for (int k = 0; k < 4; ++k) {
+        bd.d_tiles[k] = take(tab[k].size() * sizeof(GemmTile));
+        bd.total_ctas[k] = tiles[k];
+        bd.count[k] = (int)tab[k].size();
+        e = cudaMemcpy(bd.d_tiles[k], tab[k].data(), tab[k].size() * sizeof(GemmTile),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    bd.d_frec = take((size_t)T * sizeof(FoldRRec));
+    bd.frec_blocks = blk;
+    e = cudaMemcpy(bd.d_frec, recs.data(), (size_t)T * sizeof(FoldRRec), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    if ((e = set_fold_attrs()) != cudaSuccess) return e;
+    bd.n_sm = device_sms();
+    return bd.n_sm > 1 ? cudaSuccess : cudaErrorInvalidDevice;
+}
+
+}  // namespace
+
 cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T, int prec,
-                            float tau, int flexible, char* mem, const float* const* rU,
+                            int fold, float tau, int flexible, char* mem, const float* const* rU,
                             float* const* zU, const int* ld, DevState* states,
                             double* const* partials) {
     const bool split = prec == IRLS_PREC_BF16X3;
-    bd.T = T; bd.prec = prec; bd.split = split ? 1 : 0; bd.tau = tau;
-    BatchLayout L = batch_layout(H, W, T, prec);
+    bd.T = T; bd.prec = prec; bd.split = split ? 1 : 0; bd.tau = tau; bd.fold = fold ? 1 : 0;
+    BatchLayout L = batch_layout(H, W, T, prec, fold);
     char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(mem) + 1023) & ~uintptr_t(1023));
+    if (fold) {
+        for (int t = 0; t < T; ++t)
+            if (!foldable(H[t], W[t], split)) return cudaErrorInvalidValue;
+        return batch_fold_setup(bd, H, W, T, L, p, tau, flexible, rU, zU, ld, states, partials);
+    }
     auto take = [&](size_t bytes) {
         void* r = p;
         p += rup(bytes, 1024);
@@ -2028,6 +2168,11 @@ cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s) {
     using C22 = UCfg<128, 2, 2>;
     using C11 = UCfg<128, 1, 1>;
     const int T = bd.T;
+    if (bd.fold) {
+        k_fold_r_batched<<<bd.frec_blocks, 256, 0, s>>>(static_cast<const FoldRRec*>(bd.d_frec), T);
+        void* const tabs[4] = {bd.d_tiles[0], bd.d_tiles[1], bd.d_tiles[2], bd.d_tiles[3]};
+        return launch_fold_stages(tabs, bd.count, bd.total_ctas, bd.n_sm, 1, s);
+    }
     auto tiles = [&](int k) { return static_cast<const GemmTile*>(bd.d_tiles[k]); };
     if (bd.split) {
         kb_umma_gemm<UE_STORE16, 2, 2><<<bd.total_ctas[0], kUThreads, C22::kSmem, s>>>(tiles(0), T);

@@ -73,6 +73,12 @@ struct Layout {
     int max_blocks;
 };
 
+// reduction slots: eight per block of the widest grid-reduced launch, or the folded
+// preconditioner's per-tile slots
+size_t partial_count(int H, int W, int max_blocks) {
+    return std::max((size_t)8 * max_blocks, dct_rho_slots(H, W));
+}
+
 Layout layout(int H, int W, int prec) {
     Layout L{};
     const int ld = row_pitch(W);
@@ -81,7 +87,7 @@ Layout layout(int H, int W, int prec) {
     L.state = L.planes + kPlanes * L.plane_bytes;
     L.partials = L.state + align_up(sizeof(DevState), 256);
     L.max_blocks = std::max(stencil_grid_blocks(H, W), dct_max_blocks(H, W));
-    L.dct = L.partials + align_up((size_t)8 * L.max_blocks * sizeof(double), 1024);
+    L.dct = L.partials + align_up(partial_count(H, W, L.max_blocks) * sizeof(double), 1024);
     L.total = L.dct + align_up(dct_bytes(H, W, prec), 1024) + 1024;
     return L;
 }
@@ -836,11 +842,16 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     if (opts) o = *opts;
     if (!opts_valid(o)) return IRLS_ERR_ARG;
     if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
-    if (o.dct_form == IRLS_DCT_FOLDED) return IRLS_ERR_UNSUPPORTED;   // grouped form is direct
     if (o.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;  // images run in lockstep
     if (o.system != IRLS_SYS_FULL) return IRLS_ERR_UNSUPPORTED;
     for (int t = 0; t < ntiles; ++t)
         if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
+    // folded preconditioner when every image allows it (split precision, even sides >= 256)
+    bool all_fold = true;
+    for (int t = 0; t < ntiles; ++t)
+        all_fold &= foldable(H[t], W[t], o.precision == IRLS_PREC_BF16X3 ? 1 : 0);
+    if (o.dct_form == IRLS_DCT_FOLDED && !all_fold) return IRLS_ERR_UNSUPPORTED;
+    const int fold = all_fold && o.dct_form != IRLS_DCT_DIRECT ? 1 : 0;
     irls_batch_s* b = new (std::nothrow) irls_batch_s();
     if (!b) return IRLS_ERR_OOM;
     try {
@@ -857,14 +868,14 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             b->ld.push_back(ld);
             plane_bytes[t] = align_up((size_t)H[t] * ld * sizeof(float), 256);
             const int nb = std::max(stencil_grid_blocks(H[t], W[t]), dct_max_blocks(H[t], W[t]));
-            part_bytes[t] = align_up((size_t)8 * nb * sizeof(double), 256);
+            part_bytes[t] = align_up(partial_count(H[t], W[t], nb) * sizeof(double), 256);
             total += kPlanes * plane_bytes[t] + part_bytes[t];
         }
         const size_t state_off = align_up(total, 1024);
         const size_t recs_off = align_up(state_off + (size_t)T * sizeof(DevState), 1024);
         const size_t count_off = align_up(recs_off + (size_t)T * sizeof(TileRec), 256);
         const size_t dct_off = align_up(count_off + 256, 1024);
-        const size_t all = dct_off + batch_dct_bytes(H, W, T, o.precision);
+        const size_t all = dct_off + batch_dct_bytes(H, W, T, o.precision, fold);
         if (cudaMalloc(&b->mem, all) != cudaSuccess) {
             cudaGetLastError();
             b->mem = nullptr;
@@ -903,7 +914,8 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             r.st = b->states + t;
             r.partials = parts[t];
         }
-        ck(batch_dct_setup(b->dct, H, W, T, o.precision, o.tau, o.flexible_cg, b->mem + dct_off,
+        ck(batch_dct_setup(b->dct, H, W, T, o.precision, fold, o.tau, o.flexible_cg,
+                           b->mem + dct_off,
                            rU.data(), zU.data(), b->ld.data(), b->states, parts.data()));
         int sblk = 0, vblk = 0, ublk = 0;
         for (int t = 0; t < T; ++t) {
@@ -918,9 +930,13 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             a.flexible = o.flexible_cg;
             a.warm_start = o.warm_start;
             a.prec = o.precision;
-            a.r16 = b->dct.r16[t];
-            a.r16lo = b->dct.split ? b->dct.r16lo[t] : nullptr;
-            a.ld16 = b->dct.ld16[t];
+            // the direct form reads the update kernel's bf16 copy of r_U; the folded form folds
+            // r_U itself
+            if (!fold) {
+                a.r16 = b->dct.r16[t];
+                a.r16lo = b->dct.split ? b->dct.r16lo[t] : nullptr;
+                a.ld16 = b->dct.ld16[t];
+            }
             strip_dims(H[t], W[t], r.sgx, r.sgy);
             vec_dims(H[t], W[t], r.vgx, r.vgy, r.ugy);
             r.sblk0 = sblk;
@@ -950,6 +966,11 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
 int irls_batch_destroy(irls_batch b) {
     destroy_batch(b);
     return IRLS_OK;
+}
+
+int irls_batch_dct_form(irls_batch b) {
+    if (!b) return IRLS_ERR_ARG;
+    return b->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
 }
 
 int irls_batch_uses_graphs(irls_batch b) {

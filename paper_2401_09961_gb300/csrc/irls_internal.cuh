@@ -125,13 +125,19 @@ struct TileRec {
 };
 
 // Tensor-core preconditioner of a batched solve: per-stage device arrays of grouped-GEMM
-// problems (one per image), the images' bf16 copies of r_U, and the DCT bases cached per
-// distinct side length.
+// problems, and the DCT bases cached per distinct side length.  Direct form: one problem per
+// image and stage, the images' bf16 copies of r_U (written by the update kernel).  Folded form
+// (fold = 1): each image's nine problems of the four CTA-pair stages, and the images' fold
+// records (the fold of r_U runs as its own batched launch).
 struct BatchDctPlan {
-    int T = 0, prec = 0, split = 0;
+    int T = 0, prec = 0, split = 0, fold = 0;
     float tau = 0.f;
     void* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
-    int total_ctas[4] = {0, 0, 0, 0};
+    int total_ctas[4] = {0, 0, 0, 0};   // direct: CTAs per stage; folded: output tiles
+    int count[4] = {0, 0, 0, 0};        // problems per stage
+    void* d_frec = nullptr;             // folded: T fold records
+    int frec_blocks = 0;
+    int n_sm = 0;
     std::vector<void*> r16, r16lo;
     std::vector<int> ld16;
 };
@@ -209,10 +215,12 @@ cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevS
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
                       cudaStream_t s);
 int dct_max_blocks(int H, int W);
+size_t dct_rho_slots(int H, int W);
 // batched form (dct_umma.cu): memory for T images of sizes H[t] x W[t], set-up, application
-size_t batch_dct_bytes(const int* H, const int* W, int T, int prec);
+bool foldable(int H, int W, int split);
+size_t batch_dct_bytes(const int* H, const int* W, int T, int prec, int fold);
 cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T, int prec,
-                            float tau, int flexible, char* mem, const float* const* rU,
+                            int fold, float tau, int flexible, char* mem, const float* const* rU,
                             float* const* zU, const int* ld, DevState* states,
                             double* const* partials);
 cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s);

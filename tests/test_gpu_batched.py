@@ -82,25 +82,97 @@ def test_batched_matches_oracle(irls):
                              ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref)
 
 
-def test_batched_rejects_folded_form(irls):
-    with pytest.raises(irls.IrlsError) as e:
-        irls.Batch([(256, 256)], precision="bf16x3", dct_form="folded", **OPTS)
-    assert e.value.code == -8
+def test_batched_folded_form_only_where_every_image_allows_it(irls):
+    """The folded form needs the split precision and even sides >= 256 in every image."""
+    for shapes, prec in (([(256, 256), (256, 250)], "bf16x3"), ([(256, 256), (255, 256)], "bf16x3"),
+                         ([(256, 256)], "bf16")):
+        with pytest.raises(irls.IrlsError) as e:
+            irls.Batch(shapes, precision=prec, dct_form="folded", **OPTS)
+        assert e.value.code == -8
+    with irls.Batch([(256, 256), (256, 250)], precision="bf16x3", **OPTS) as b:
+        assert not b.folded    # auto: direct, one image does not allow the fold
+    with irls.Batch([(256, 256), (258, 512)], precision="bf16x3", **OPTS) as b:
+        assert b.folded
+    with irls.Batch([(256, 256)], precision="bf16x3", **DIRECT) as b:
+        assert not b.folded
 
 
-def test_batched_64_uneven_tiles(irls):
-    """The 64-tile workload: sides drawn from {256, 384, ..., 1536}, one batch; a few tiles are
-    re-solved alone and must agree bit for bit."""
+# sides even and >= 256: halves padded to multiples of 256 (129 -> 256, 150 -> 256, 384 -> 512),
+# non-square, one side shared by several images, one shape twice
+FOLD_SHAPES = [(256, 256), (258, 300), (512, 384), (384, 768), (256, 256), (1024, 512)]
+
+
+def test_batched_folded_equals_single_image_path(irls):
+    """Folded preconditioner over all images in four launches: per image the same tiles, the same
+    per-tile r^T z slots and the same reduction order as a plan of its own, so bit-identical."""
+    tiles = [synthetic.config_2048(seed=300 + t, H=h, W=w) for t, (h, w) in enumerate(FOLD_SHAPES)]
+    Xs = [cuda(d["X"]) for d in tiles]
+    Cs = [cuda(d["coherence"]) for d in tiles]
+    with irls.Batch(FOLD_SHAPES, precision="bf16x3", **OPTS) as b:
+        assert b.folded
+        Us, st = b.unwrap(Xs, Cs)
+        Us = [u.clone() for u in Us]
+        Us2, st2 = b.unwrap(Xs, Cs)
+    for t, (h, w) in enumerate(FOLD_SHAPES):
+        with irls.Plan(h, w, precision="bf16x3", **OPTS) as p:
+            assert p.folded
+            U, s1 = p.unwrap(Xs[t], Cs[t])
+        assert torch.equal(Us[t], U), t
+        assert torch.equal(Us2[t], U), t
+        assert st[t]["cg_iters"] == s1["cg_iters"] == st2[t]["cg_iters"], t
+        assert st[t]["l1_obj"] == s1["l1_obj"], t
+
+
+def test_batched_folded_per_image_masks(irls):
+    """A constant image stops at once and an easy one early, while a hard one runs on: the
+    stopped images' tiles drop out of the pair GEMMs and their fold."""
+    shapes = [(256, 256), (512, 512), (256, 384)]
+    flat = np.full((256, 256), 0.5, dtype=np.float32)
+    hard = synthetic.config_4096_mixed(seed=8, H=512, W=512)
+    easy = synthetic.config_small(seed=4, H=256, W=384)
+    Xs = [cuda(flat), cuda(hard["X"]), cuda(easy["X"])]
+    Cs = [cuda(np.ones((256, 256), np.float32)), cuda(hard["coherence"]),
+          cuda(np.ones((256, 384), np.float32))]
+    with irls.Batch(shapes, precision="bf16x3", **OPTS) as b:
+        assert b.folded
+        Us, st = b.unwrap(Xs, Cs)
+    assert st[0]["cg_iters"] == [0] * 5 and float(Us[0].abs().max()) == 0.0
+    assert sum(st[1]["cg_iters"]) > 3 * sum(st[2]["cg_iters"])
+    for t, (h, w) in enumerate(shapes):
+        with irls.Plan(h, w, precision="bf16x3", **OPTS) as p:
+            U, s1 = p.unwrap(Xs[t], Cs[t])
+        assert torch.equal(Us[t], U) and st[t]["cg_iters"] == s1["cg_iters"], t
+
+
+def test_batched_folded_matches_oracle(irls):
+    shapes = [(256, 256), (256, 320)]
+    tiles = [synthetic.config_2048(seed=400 + t, H=h, W=w) for t, (h, w) in enumerate(shapes)]
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6, cg_max=1000)
+    with irls.Batch(shapes, precision="bf16x3", tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6,
+                    cg_max_iter=1000) as b:
+        assert b.folded
+        Us, st = b.unwrap([cuda(d["X"]) for d in tiles], [cuda(d["coherence"]) for d in tiles])
+    for t, d in enumerate(tiles):
+        ref, env = oracle_with_envelope(d["X"], d["coherence"], kw)
+        assert_unwrap_parity(Us[t].cpu().numpy(), ref["U"], st[t]["l1_obj"][-1],
+                             ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref)
+
+
+@pytest.mark.parametrize("form", ["auto", "direct"])
+def test_batched_64_uneven_tiles(irls, form):
+    """The 64-tile workload: sides drawn from {256, 384, ..., 1536}, one batch (folded where every
+    image allows it, else direct); a few tiles are re-solved alone and must agree bit for bit."""
     tiles = synthetic.batched_tiles(n=64)
     shapes = [d["X"].shape for d in tiles]
     Xs = [cuda(d["X"]) for d in tiles]
     Cs = [cuda(d["coherence"]) for d in tiles]
-    opts = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6, cg_max_iter=1000)
+    opts = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6, cg_max_iter=1000, dct_form=form)
     with irls.Batch(shapes, precision="bf16x3", **opts) as b:
+        assert b.folded == (form == "auto")
         Us, st = b.unwrap(Xs, Cs)
     assert all(s["outer_done"] == 3 for s in st)
     for t in (0, 17, 63):
         h, w = shapes[t]
-        with irls.Plan(h, w, precision="bf16x3", dct_form="direct", **opts) as p:
+        with irls.Plan(h, w, precision="bf16x3", **opts) as p:
             U, _ = p.unwrap(Xs[t], Cs[t])
         assert torch.equal(Us[t], U), t
