@@ -282,8 +282,9 @@ def main():
             sus = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             passes = 3 if prec == "bf16x3" else 1
             alg = dct_flops / avg_s / 1e12
-            form = "folded even/odd" if folded else "direct"
-            roof = {"kernel": f"dct_precond (4 tcgen05 GEMMs, {form}, {prec})", "bound": "tensor",
+            form = ("k_fold_r + k2_fold_fused: the four folded even/odd stages in one persistent "
+                    "CTA-pair launch" if folded else "four grouped tcgen05 GEMMs, direct form")
+            roof = {"kernel": f"dct_precond ({form}, {prec})", "bound": "tensor",
                     "achieved": alg, "peak": sus / passes, "unit": "TFLOP/s",
                     "peak_source": (f"bf16_tflops_sustained ({peak_src}) / {passes}: the split "
                                     "product issues three bf16 MMAs per multiply-add"
@@ -295,14 +296,14 @@ def main():
                 "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # DRAM bytes per preconditioner application (dram__bytes_read.sum + dram__bytes_write.sum
-    # over k_fold_r and the four k2_umma_gemm stages, one ncu capture of the current kernels at
-    # 4096 x 4096, bf16x3, folded pair form); null for any other configuration
-    measured_traffic = {(4096, 4096, "bf16x3", True): 807.1e6}
+    # over k_fold_r and k2_fold_fused, one ncu capture of the current kernels at 4096 x 4096,
+    # bf16x3, folded form); null for any other configuration
+    measured_traffic = {(4096, 4096, "bf16x3", True): 874.9e6}
     roof["traffic"] = (measured_traffic.get((n, wd, prec, bool(folded)))
                        if dom == "dct_precond" else None)
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
-                         "dct_precond": 5 if folded else 4, "finalize": 2}
+                         "dct_precond": 2 if folded else 4, "finalize": 2}
     gpu_launches = sum(per_cls[c]["launches"] * kernels_per_class[c] for c in classes)
     gpu_launches += args.steps  # copy-out of U
 

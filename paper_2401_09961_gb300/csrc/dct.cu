@@ -25,6 +25,7 @@ cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld,
 size_t umma_dct_bytes(int H, int W, int split);
 cudaError_t umma_dct_setup(DctPlan& d, char* mem);
 void umma_dct_release(DctPlan& d);
+cudaError_t umma_dct_reset(const DctPlan& d, cudaStream_t s);
 
 namespace {
 
@@ -245,6 +246,7 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) 
 }
 
 void dct_release(DctPlan& d) { umma_dct_release(d); }
+cudaError_t dct_reset(const DctPlan& d, cudaStream_t s) { return umma_dct_reset(d, s); }
 
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,

@@ -11,8 +11,8 @@
 //
 // Two forms share the building blocks below.  The direct form (any side; operands padded to
 // multiples of 128) and the grouped batched form run one output tile per CTA, structured as
-// follows.  The folded form (even sides >= 256) runs persistent CTA-pair kernels
-// (k2_umma_gemm, tcgen05.mma.cta_group::2, further down), which take half the multiply-adds.
+// follows.  The folded form (even sides >= 256) runs one persistent CTA-pair kernel over all four
+// stages (k2_fold_fused, tcgen05.mma.cta_group::2, further down), with half the multiply-adds.
 //
 // Kernel structure of the direct form (one 128 x BN output tile per CTA, 128 threads):
 //   warp 0 lane 0  TMA producer: cp.async.bulk.tensor 2-D loads (128-byte swizzle) of the
@@ -275,14 +275,17 @@ __device__ __forceinline__ void store_row32(void* hi, void* lo, size_t off, cons
 }
 
 // rho = r_U^T z_U + r_V^T z_V and the CG ratio beta (Alg. 2), by the last block of the launch.
-__device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u) {
+// `defer`: a launch whose later tiles still test the stop flag records the stop in stop_next,
+// which the launch's last CTA moves to done once every tile has run.
+__device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u, bool defer = false) {
     DevState* st = ep.st;
     const double rho_new = rz_u + st->rz_v;
     if (!(rho_new > 0.0) || !isfinite(rho_new)) {
         // rho <= 0 is a breakdown unless the residual is already at the accuracy rounding
         // allows (relative 1e-3 and below)
         if (st->rel > 1e-3 || !isfinite(rho_new)) st->status |= ST_BREAKDOWN;
-        st->done = 1;
+        if (defer) st->stop_next = 1;
+        else st->done = 1;
     } else if (st->p_fresh) {
         st->rho = rho_new;
         st->beta = 0.0;
@@ -701,6 +704,7 @@ struct GemmTile {
     int blk0, gx;
     int mirror_b1;                // second set's B rows mirrored: nb_rows - n0 - 128
     int nb_rows;
+    int epi, dual;                // fused folded launch: the problem's epilogue and operand sets
 };
 
 // Grouped GEMM: one launch over the output tiles of every problem (BN = 128).  A CTA finds its
@@ -763,26 +767,6 @@ __device__ __forceinline__ bool epi_sync(uint64_t* bar, int& n, int* err) {
 // A problem whose CG run has stopped (per-image mask of a batched launch) contributes no tiles.
 __device__ __forceinline__ bool problem_live(const GemmTile& g) {
     return !(g.ep.skip_if_done && *(volatile int*)&g.ep.st->done);
-}
-
-// problem_live, read once per image while the image does not change (no image's flag changes
-// during a launch: a run stops between launches)
-__device__ __forceinline__ bool problem_live_cached(const GemmTile& g, const DevState*& st,
-                                                    bool& live) {
-    if (g.ep.st != st) {
-        st = g.ep.st;
-        live = problem_live(g);
-    }
-    return live;
-}
-
-__device__ __forceinline__ const GemmTile& tile_problem(const GemmTile* tiles, int T, int t) {
-    int lo = 0, hi = T - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tiles[mid].blk0 <= t) lo = mid; else hi = mid - 1;
-    }
-    return tiles[lo];
 }
 
 // Persistent, warp-specialised grouped GEMM (128 x 128 tiles, split operands: hi + lo parts of
@@ -894,15 +878,8 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
 
-// Output tile width of a pair-form problem: a DUAL problem's set width; a mirrored-B problem
-// pairs a 128-column tile with its mirror in one N = 256 accumulator; the others are 256 wide.
-template <int DUAL, int SETN>
-__device__ __forceinline__ int pair_tile_n(const GemmTile& g) {
-    return DUAL ? SETN : (g.mirror_b1 ? 128 : 256);
-}
-
-// Persistent CTA-pair grouped GEMM.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
-// p + gridDim.x / 2, ... of every problem of the launch.  Warp roles in each CTA:
+// Persistent CTA-pair kernels.  Pair p (CTAs 2p, 2p+1) takes the 256-row tiles p,
+// p + gridDim.x / 2, ... of its work list.  Warp roles in each CTA:
 //   warp 0 lane 0   TMA producer: this CTA's A and B rows of each k-block through the
 //                   shared-memory ring (the even CTA's full barriers count both CTAs' bytes);
 //   warp 1          tensor-memory allocation (both CTAs, collectively); in the even CTA lane 0
@@ -918,15 +895,99 @@ __device__ __forceinline__ int pair_tile_n(const GemmTile& g) {
 // The even CTA's full barriers count both CTAs' bytes; the issuer's commits arrive in both CTAs;
 // both CTAs' epilogue warps release an accumulator buffer on the even CTA's barrier.  All waits
 // are bounded; the two CTAs take every branch that has a cluster barrier together.
-template <int EPI, int DUAL, int EBN>
+// ------------------------------------------------------------------------------------------
+// Folded preconditioner as one persistent launch: the four stages' tiles in one work list
+// ------------------------------------------------------------------------------------------
+// A stage's tile reads row panels of the previous stage's output (stage 2 a 256-row panel of
+// T1, stage 3 a panel of two T2 blocks, stage 4 the rows of T3 that its Z rows fold from).  Each
+// tile that produces such rows adds one per CTA to its panel's counter once its stores are
+// visible; a tile waits until the panels it reads are complete before its first copy.  The work
+// list holds every stage's tiles in stage order (a producer always before its consumers), pair p
+// takes items p, p + P, ..., so the first unfinished item can always run: with all P pairs
+// resident the launch cannot deadlock (and every wait is bounded regardless).
+constexpr int kMaxDeps = 8;
+
+struct FoldItem {
+    const DevState* st;   // the image's state (stop flag)
+    int skip;             // the problem honours the stop flag
+    int prob, local;      // problem (index into the launch's problem table) and its tile
+    int m0, n0;           // first output row (even CTA) and column of the tile
+    int nb1;              // first B row the odd CTA stages
+    int nkb, dual;        // k-blocks per operand set, operand sets - 1
+    int epi;
+    int sig;              // counter this tile completes (one add per CTA), or -1
+    int ndep;
+    int rho_end;          // stage 2: this pair's last tile of the image's stage-2 range
+    int rho_nslot;        // stage 2: CTA flushes that complete the image's r^T z
+    int dep[kMaxDeps];    // counters the tile waits for ...
+    int need[kMaxDeps];   // ... and the counts that mean complete
+};
+
+// Bounded acquire-wait until every counter the item reads has reached its count (all counters
+// loaded together: one round trip when they are complete); false on timeout or another role's
+// error.
+__device__ __forceinline__ bool wait_deps(const FoldItem& f, const unsigned* ctr, int* err) {
+    auto ready = [&]() {
+        unsigned v[kMaxDeps];
+#pragma unroll
+        for (int d = 0; d < kMaxDeps; ++d)
+            if (d < f.ndep)
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];"
+                             : "=r"(v[d])
+                             : "l"(ctr + f.dep[d])
+                             : "memory");
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < kMaxDeps; ++d)
+            if (d < f.ndep) ok &= v[d] >= (unsigned)f.need[d];
+        return ok;
+    };
+    if (ready()) return true;
+    const long long t0 = clock64();
+    while (!ready()) {
+        __nanosleep(128);
+        if (*(volatile int*)err) return false;
+        if (clock64() - t0 > kWaitBudget) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool item_live(const FoldItem& f, const DevState*& st, bool& live) {
+    if (f.st != st) {
+        st = f.st;
+        live = !(f.skip && *(volatile const int*)&f.st->done);
+    }
+    return live;
+}
+
+// Generic-proxy stores of other SMs (acquired above) become visible to this thread's TMA loads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <int EBN, int EPI>
+__device__ __forceinline__ void fused_epi(uint32_t tl, const UEpiArgs& ep, int m0w, int n0,
+                                          float& part, int half, WarpScratch& s) {
+    constexpr int kChunks = EBN / 32;
+    epi_tile_t<EBN, EPI>(tl, ep, m0w, n0, part, half * (kChunks / 2), (half + 1) * (kChunks / 2), s);
+}
+
+// Persistent CTA-pair kernel over the fused work list, with the warp roles and operand sets
+// described above; every MMA is M = N = 256.  An item with one operand set uses one 256-column
+// accumulator buffer (two buffers alternate); an item with two sets uses both (512 columns).  ctr[0 .. n_ctr) are the panel counters and ctr[n_ctr] counts exited
+// CTAs: the last CTA to exit zeroes them for the next launch and applies deferred stops.
+// sts[0 .. n_st) are the images' states; honour_stop: every problem skips a stopped image.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
-k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
-    constexpr int SETN = DUAL ? EBN : 256;     // N of one MMA (one operand set)
-    using C = Q2Cfg<DUAL, SETN>;
+k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ items,
+              int n_items, unsigned* __restrict__ ctr, int n_ctr, DevState* const* __restrict__ sts,
+              int n_st, int honour_stop) {
+    using C = Q2Cfg<0, 256>;
+    static_assert(Q2Cfg<1, 256>::kStageBytes == C::kStageBytes, "one ring for both forms");
     constexpr int S = C::kStages;
-    constexpr uint32_t kAcc = C::kAcc;
-    constexpr int NB = C::kBufs;
-    constexpr uint32_t kCols = 512;
+    constexpr uint32_t kCols = 512, kBuf = 256;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -936,22 +997,27 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
     uint64_t* tempty = tfull + 2;    // [2] accumulator buffer drained (even CTA: all epilogue
                                      //     warps of both CTAs)
     uint64_t* drain = tempty + 2;
-    uint64_t* epibar = drain + 1;    // the CTA's epilogue warps (per-image r^T z sums)
+    uint64_t* epibar = drain + 1;    // the CTA's epilogue warps
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epibar + 1);
     WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + S * C::kStageBytes + 256);
     __shared__ int s_err;
     __shared__ int s_skip;
-    __shared__ double s_tot[k2EpiWarps];
     __shared__ int s_last;
+    __shared__ int s_exit;
+    __shared__ double s_tot[k2EpiWarps];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
+    {
+        // no image's stop flag changes during the launch (stops found here are deferred)
+        int live = honour_stop ? 0 : 1;
+        for (int i = threadIdx.x; i < n_st && !live; i += blockDim.x)
+            live = *(volatile const int*)&sts[i]->done ? 0 : 1;
+        live = __syncthreads_or(live);
+        if (threadIdx.x == 0) s_skip = live ? 0 : 1;
+    }
     if (threadIdx.x == 0) {
         s_err = 0;
-        // the whole launch returns when every problem's run has stopped
-        int all_done = 1;
-        for (int i = 0; i < T; ++i) all_done &= problem_live(tiles[i]) ? 0 : 1;
-        s_skip = all_done;
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
@@ -965,206 +1031,274 @@ k2_umma_gemm(const GemmTile* __restrict__ tiles, int T, int total_tiles) {
         fence_mbar_init();
     }
     cluster_sync_all();
+    bool skip;
     {
-        // both CTAs skip, or neither: a stopped CG run read by only one of them must not split
-        // the pair across the cluster barriers below
+        // both CTAs of the pair skip, or neither
         int peer;
         asm volatile("ld.shared::cluster.u32 %0, [%1];"
                      : "=r"(peer)
                      : "r"(mapa_shared(smem_u32(&s_skip), rank ^ 1u))
                      : "memory");
-        if (s_skip | peer) {
-            cluster_sync_all();
-            return;
-        }
+        skip = (s_skip | peer) != 0;
     }
-    if (warp == 1) tmem_alloc_pair(tmem_slot, kCols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-    float part = 0.f;
-    const DevState* lst = nullptr;
-    bool llive = true;
+    cluster_sync_all();
+    if (!skip) {
+        if (warp == 1) tmem_alloc_pair(tmem_slot, kCols);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const uint32_t tmem = *tmem_slot;
+        const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+        const DevState* lst = nullptr;
+        bool llive = true;
 
-    if (warp == 0) {
-        if (lane == 0) {
-            const uint32_t full0 = mapa_shared(smem_u32(full), 0);
-            int it = 0;
-            bool bad = false;
-            for (int t = pair; t < total_tiles && !bad; t += npairs) {
-                const GemmTile& g = tile_problem(tiles, T, t);
-                if (!problem_live_cached(g, lst, llive)) continue;
-                const int local = t - g.blk0;
-                const int tn = pair_tile_n<DUAL, SETN>(g);
-                const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
-                const int n0 = (local % g.gx) * tn;
-                const int nb = rank == 0 ? n0
-                                         : (g.mirror_b1 ? g.nb_rows - n0 - 128 : n0 + C::kBRows);
-                const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
-                for (int kb = 0; kb < nkt; ++kb, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    if (it >= S && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_err)) {
-                        bad = true;
-                        break;
+        if (warp == 0) {
+            if (lane == 0) {
+                const uint32_t full0 = mapa_shared(smem_u32(full), 0);
+                int it = 0;
+                bool bad = false;
+                // the next item's record is fetched while this item's copies are issued
+                FoldItem f;
+                if (pair < n_items) f = items[pair];
+                for (int t = pair; t < n_items && !bad; t += npairs) {
+                    FoldItem fn;
+                    if (t + npairs < n_items) fn = items[t + npairs];
+                    if (!item_live(f, lst, llive)) {
+                        f = fn;
+                        continue;
                     }
-                    const bool second = DUAL && kb >= nkb;
-                    const int kc = (second ? kb - nkb : kb) * UBK;
-                    uint8_t* sa = smem + s * C::kStageBytes;
-                    uint8_t* sb = sa + 2 * C::kABytes;
-                    if (rank == 0) mbar_expect_tx(&full[s], 2 * C::kStageBytes);
-                    const uint32_t fb = full0 + 8u * (uint32_t)s;
-                    tma_load_2d_pair(sa, second ? &g.a2 : &g.a0, fb, kc, m0);
-                    tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
-                    tma_load_2d_pair(sb, second ? &g.b2 : &g.b0, fb, kc, nb);
-                    tma_load_2d_pair(sb + C::kBBytes, second ? &g.b3 : &g.b1, fb, kc, nb);
+                    const GemmTile& g = probs[f.prob];
+                    // the rows this tile reads are complete (other SMs' stores, then a proxy fence
+                    // so that the tensor copies below observe them)
+                    if (f.ndep > 0) {
+                        if (!wait_deps(f, ctr, &s_err)) {
+                            bad = true;
+                            break;
+                        }
+                        fence_proxy_async_global();
+                    }
+                    const int dual = f.dual;
+                    const int m0 = f.m0 + 128 * (int)rank;
+                    const int nb = rank == 0 ? f.n0 : f.nb1;
+                    const int nkb = f.nkb, nkt = dual ? 2 * nkb : nkb;
+                    for (int kb = 0; kb < nkt; ++kb, ++it) {
+                        const int s = it % S;
+                        const uint32_t ph = (uint32_t)(it / S) & 1u;
+                        if (it >= S && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_err)) {
+                            bad = true;
+                            break;
+                        }
+                        const bool second = dual && kb >= nkb;
+                        const int kc = (second ? kb - nkb : kb) * UBK;
+                        uint8_t* sa = smem + s * C::kStageBytes;
+                        uint8_t* sb = sa + 2 * C::kABytes;
+                        if (rank == 0) mbar_expect_tx(&full[s], 2 * C::kStageBytes);
+                        const uint32_t fb = full0 + 8u * (uint32_t)s;
+                        tma_load_2d_pair(sa, second ? &g.a2 : &g.a0, fb, kc, m0);
+                        tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
+                        tma_load_2d_pair(sb, second ? &g.b2 : &g.b0, fb, kc, nb);
+                        tma_load_2d_pair(sb + C::kBBytes, second ? &g.b3 : &g.b1, fb, kc, nb);
+                    }
+                    f = fn;
+                }
+                if (rank == 0) {
+                    for (int j = it - S < 0 ? 0 : it - S; j < it; ++j)
+                        if (!mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) atomicExch(&s_err, 1);
+                } else if (bad) {
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < (1LL << 22)) {
+                    }
                 }
             }
-            if (rank == 0) {
-                // both CTAs' copies of the last stages have landed (immediate on the normal path)
-                for (int j = it - S < 0 ? 0 : it - S; j < it; ++j)
-                    if (!mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) atomicExch(&s_err, 1);
-            } else if (bad) {
-                // the odd CTA's copies signal the even CTA's barriers: give them time to land
-                const long long t0 = clock64();
-                while (clock64() - t0 < (1LL << 22)) {
-                }
-            }
-        }
-        __syncwarp();
-    } else if (warp == 1) {
-        if (rank == 0 && lane == 0) {
-            int it = 0, j = 0;
-            bool bad = false;
-            for (int t = pair; t < total_tiles && !bad; t += npairs) {
-                const GemmTile& g = tile_problem(tiles, T, t);
-                if (!problem_live_cached(g, lst, llive)) continue;
-                const int nkb = g.K / UBK, nkt = DUAL ? 2 * nkb : nkb;
-                const int b = j % NB, u = j / NB;
-                ++j;
-                if (u >= 1 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(u - 1) & 1u, &s_err)) {
-                    bad = true;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t base = tmem + (uint32_t)b * kAcc;
-                for (int kb = 0; kb < nkt; ++kb, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (uint32_t)(it / S) & 1u;
-                    if (!mbar_wait_or_abort(&full[s], ph, &s_err)) {
-                        bad = true;
-                        break;
-                    }
-                    tc_fence_after();
-                    const bool second = DUAL && kb >= nkb;
-                    const int kk = second ? kb - nkb : kb;
-                    const uint32_t td = base + (second ? (uint32_t)SETN : 0u);
-                    const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
-                    const uint32_t sb = sa + 2 * C::kABytes;
-                    const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
-                    const uint64_t dal = desc_sw128(sa + C::kABytes);
-                    const uint64_t dbl = desc_sw128(sb + C::kBBytes);
-#pragma unroll
-                    for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
-                        umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
-                        umma_bf16_pair(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
-                        umma_bf16_pair(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
-                    }
-                    umma_commit_pair(&empty[s]);
-                }
-                if (!bad) umma_commit_pair(&tfull[b]);
-            }
-            umma_commit_pair(drain);
-        }
-        __syncwarp();
-    } else {
-        const int q = warp & 3, half = (warp - 2) >> 2;
-        constexpr int kChunks = EBN / 32;
-        const int c_begin = half * (kChunks / 2), c_end = c_begin + kChunks / 2;
-        const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
-        int j = 0, nsync = 0;
-        for (int t = pair; t < total_tiles; t += npairs) {
-            const GemmTile& g = tile_problem(tiles, T, t);
-            if (!problem_live_cached(g, lst, llive)) continue;
-            const int local = t - g.blk0;
-            const int tn = pair_tile_n<DUAL, SETN>(g);
-            const int m0 = (local / g.gx) * 256 + 128 * (int)rank;
-            const int n0 = (local % g.gx) * tn;
-            const int b = j % NB, u = j / NB;
-            ++j;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)u & 1u, &s_err);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
-            const UEpiArgs ep = g.ep;   // register copy (see umma_body)
-            epi_tile_t<EBN, EPI>(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16), ep,
-                                 m0 + q * 32, n0, part, c_begin, c_end, scratch[warp - 2]);
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(te0 + 8u * (uint32_t)b);
-            if constexpr (EPI == UE_EIG16_RHO) {
-                // r^T z of an image, in an order fixed by the image's own tile numbering (the same
-                // alone or in a batch): each epilogue warp stores its sum over the tile into slot
-                // ((tile, CTA), warp); a CTA meets the image's consecutive tile range [a, b) as
-                // one run, and at the end of it counts itself done; the CTA that completes the
-                // count adds all the image's slots and forms rho and beta
-                double v = (double)part;
-                part = 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0)
-                    ep.partials[((ep.rho_base + local) * 2 + (int)rank) * k2EpiWarps + (warp - 2)] = v;
-                const int a = g.blk0 - ep.rho_base, b = a + ep.rho_count;
-                if (t + npairs >= b || t + npairs >= total_tiles) {
-                    if (lane == 0) __threadfence();
-                    if (!epi_sync(epibar, nsync, &s_err)) break;
-                    if (warp == 2 && lane == 0) {
-                        const unsigned prev = atomicAdd(&ep.st->counter, 1u);
-                        s_last = prev == (unsigned)(2 * min(npairs, b - a)) - 1u;
+        } else if (warp == 1) {
+            if (rank == 0 && lane == 0) {
+                int it = 0, nbuf = 0;
+                int use[2] = {0, 0};
+                bool bad = false;
+                FoldItem f;
+                if (pair < n_items) f = items[pair];
+                for (int t = pair; t < n_items && !bad; t += npairs) {
+                    FoldItem fn;
+                    if (t + npairs < n_items) fn = items[t + npairs];
+                    if (!item_live(f, lst, llive)) {
+                        f = fn;
+                        continue;
                     }
-                    if (!epi_sync(epibar, nsync, &s_err)) break;
-                    if (s_last) {
-                        __threadfence();
-                        const int n = ep.rho_count * 2 * k2EpiWarps;
-                        const int e = threadIdx.x - 64;
-                        double tot = 0.0;
-                        for (int i = e; i < n; i += 32 * k2EpiWarps) tot += __ldcg(&ep.partials[i]);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-                        if (lane == 0) s_tot[warp - 2] = tot;
+                    const int dual = f.dual;
+                    const int b0 = dual ? 0 : nbuf, nbu = dual ? 2 : 1;
+                    if (!dual) nbuf ^= 1;
+                    for (int k = 0; k < nbu && !bad; ++k) {
+                        const int b = b0 + k;
+                        if (use[b] >= 1 &&
+                            !mbar_wait_or_abort(&tempty[b], (uint32_t)(use[b] - 1) & 1u, &s_err))
+                            bad = true;
+                        ++use[b];
+                    }
+                    if (bad) break;
+                    tc_fence_after();
+                    const uint32_t base = tmem + (uint32_t)b0 * kBuf;
+                    const int nkb = f.nkb, nkt = dual ? 2 * nkb : nkb;
+                    for (int kb = 0; kb < nkt; ++kb, ++it) {
+                        const int s = it % S;
+                        const uint32_t ph = (uint32_t)(it / S) & 1u;
+                        if (!mbar_wait_or_abort(&full[s], ph, &s_err)) {
+                            bad = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const bool second = dual && kb >= nkb;
+                        const int kk = second ? kb - nkb : kb;
+                        const uint32_t td = base + (second ? kBuf : 0u);
+                        const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
+                        const uint32_t sb = sa + 2 * C::kABytes;
+                        const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
+                        const uint64_t dal = desc_sw128(sa + C::kABytes);
+                        const uint64_t dbl = desc_sw128(sb + C::kBBytes);
+    #pragma unroll
+                        for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
+                            umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
+                            umma_bf16_pair(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                            umma_bf16_pair(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                        }
+                        umma_commit_pair(&empty[s]);
+                    }
+                    if (!bad)
+                        for (int k = 0; k < nbu; ++k) umma_commit_pair(&tfull[b0 + k]);
+                    f = fn;
+                }
+                umma_commit_pair(drain);
+            }
+            __syncwarp();
+        } else {
+            const int q = warp & 3, half = (warp - 2) >> 2;
+            const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
+            int nbuf = 0, nsync = 0;
+            int use[2] = {0, 0};
+            float part = 0.f;
+            for (int t = pair; t < n_items; t += npairs) {
+                const FoldItem& f = items[t];
+                if (!item_live(f, lst, llive)) continue;
+                const GemmTile& g = probs[f.prob];
+                const int dual = f.dual;
+                const int b0 = dual ? 0 : nbuf, nbu = dual ? 2 : 1;
+                if (!dual) nbuf ^= 1;
+                int ok = 1;
+                for (int k = 0; k < nbu; ++k) {
+                    const int b = b0 + k;
+                    if (lane == 0 && ok) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)use[b] & 1u, &s_err);
+                    ++use[b];
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                tc_fence_after();
+                const int m0 = f.m0 + 128 * (int)rank;
+                const int n0 = f.n0;
+                const UEpiArgs ep = g.ep;
+                const uint32_t tl = tmem + (uint32_t)b0 * kBuf + ((uint32_t)(q * 32) << 16);
+                WarpScratch& sc = scratch[warp - 2];
+                switch (f.epi) {
+                    case UE_FOLD16: fused_epi<128, UE_FOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
+                    case UE_EIG16: fused_epi<256, UE_EIG16>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
+                    case UE_EIG16_RHO:
+                        fused_epi<256, UE_EIG16_RHO>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        break;
+                    case UE_UNFOLD16:
+                        fused_epi<256, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        break;
+                    default: fused_epi<256, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    for (int k = 0; k < nbu; ++k) mbar_arrive_cluster(te0 + 8u * (uint32_t)(b0 + k));
+                if (f.epi == UE_EIG16_RHO) {
+                    // r^T z of an image, in an order fixed by the image's own tile numbering (the same
+                    // alone or in a batch): each epilogue warp stores its sum over the tile into slot
+                    // ((tile, CTA), warp); at the end of its run of the image's stage-2 tiles (marked
+                    // by the host) a CTA counts itself done, and the CTA that completes the count adds
+                    // all the image's slots and forms rho and beta
+                    double v = (double)part;
+                    part = 0.f;
+    #pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    if (lane == 0)
+                        ep.partials[((ep.rho_base + f.local) * 2 + (int)rank) * k2EpiWarps + (warp - 2)] = v;
+                    if (f.rho_end) {
+                        if (lane == 0) __threadfence();
                         if (!epi_sync(epibar, nsync, &s_err)) break;
                         if (warp == 2 && lane == 0) {
-                            double sum = 0.0;
-                            for (int w = 0; w < k2EpiWarps; ++w) sum += s_tot[w];
-                            finish_rho(ep, sum);
-                            ep.st->counter = 0u;
+                            const unsigned prev = atomicAdd(&ep.st->counter, 1u);
+                            s_last = prev == (unsigned)f.rho_nslot - 1u;
+                        }
+                        if (!epi_sync(epibar, nsync, &s_err)) break;
+                        if (s_last) {
+                            __threadfence();
+                            const int n = ep.rho_count * 2 * k2EpiWarps;
+                            const int e = threadIdx.x - 64;
+                            double tot = 0.0;
+                            for (int i = e; i < n; i += 32 * k2EpiWarps) tot += __ldcg(&ep.partials[i]);
+    #pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+                            if (lane == 0) s_tot[warp - 2] = tot;
+                            if (!epi_sync(epibar, nsync, &s_err)) break;
+                            if (warp == 2 && lane == 0) {
+                                double sum = 0.0;
+                                for (int w = 0; w < k2EpiWarps; ++w) sum += s_tot[w];
+                                finish_rho(ep, sum, true);
+                                ep.st->counter = 0u;
+                            }
                         }
                     }
                 }
+                if (f.sig >= 0) {
+                    // this CTA's rows of the tile are stored: the epilogue warps' barrier orders
+                    // every lane's stores before one release-add (cumulative) per CTA
+                    if (!epi_sync(epibar, nsync, &s_err)) break;
+                    if (warp == 2 && lane == 0)
+                        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctr[f.sig])
+                                     : "memory");
+                }
             }
         }
-    }
 
-    // every MMA of the pair has completed before the tensor memory is released
-    if (warp == 1 && lane == 0 && !mbar_wait(drain, 0)) atomicExch(&s_err, 1);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc_pair(tmem, kCols);
-    }
-    if (threadIdx.x == 0 && *(volatile int*)&s_err) {
-        // a wait gave up: every image of the launch stops with the timeout status
-        for (int i = 0; i < T; ++i) {
-            DevState* sti = tiles[i].ep.st;
-            atomicOr(&sti->status, ST_TIMEOUT);
-            sti->done = 1;
+        // every MMA of the pair has completed before the tensor memory is released
+        if (warp == 1 && lane == 0 && !mbar_wait(drain, 0)) atomicExch(&s_err, 1);
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 1) {
+            tc_fence_after();
+            tmem_dealloc_pair(tmem, kCols);
         }
     }
-    static_assert(EPI != UE_ZU_RHO && EPI != UE_UNFOLDZ_RHO, "r^T z: the per-tile form only");
+    __syncthreads();
+    if (*(volatile int*)&s_err) {
+        // a wait gave up: every image of the launch stops with the timeout status
+        for (int i = threadIdx.x; i < n_st; i += blockDim.x) {
+            atomicOr(&sts[i]->status, ST_TIMEOUT);
+            sts[i]->done = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_exit = atomicAdd(&ctr[n_ctr], 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (s_exit) {
+        // every other CTA has exited: reset the counters and apply the stops found in the launch
+        __threadfence();
+        for (int i = threadIdx.x; i < n_ctr; i += blockDim.x) ctr[i] = 0u;
+        for (int i = threadIdx.x; i < n_st; i += blockDim.x) {
+            DevState* sti = sts[i];
+            if (sti->stop_next) {
+                sti->done = 1;
+                sti->stop_next = 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ctr[n_ctr] = 0u;
+    }
     cluster_sync_all();
 }
 
@@ -1443,9 +1577,9 @@ FoldDims fold_dims(int H, int W) {
 
 namespace {
 
-// The folded stages run as persistent CTA-pair GEMMs with 256-row tiles (every padded extent is
-// a multiple of 256).  N of each operand set in the pair form's two-set stages (3 and 4): 256
-// (two accumulators fill the tensor memory, one buffer) or 128 (two buffers, epilogue overlapped)
+// The folded stages run as CTA-pair GEMMs with 256-row tiles (every padded extent is a multiple
+// of 256); the two-set stages (3 and 4) use N = 256 per operand set (two accumulators fill the
+// tensor memory), the width the fused kernel's accumulator buffers assume.
 constexpr int kPairDualN = 256;
 
 // Even / odd basis halves of one side length n (hi and lo parts), padded to hp = rup(n/2, 256).
@@ -1460,7 +1594,7 @@ struct FoldImage {
     FoldDims dim{};
     void *Re[2], *Ro[2];   // H x hMp
     void* T1[4][2];        // (x, sign) = (e+, e-, o+, o-), hMp x hNp
-    void* T3[2][2];        // x = e, o: Hp x hMp (aliases T1)
+    void* T3[2][2];        // x = e, o: Hp x hMp
     void* T2[4][2];        // (x, y) = ee, eo, oe, oo: hMp x hNp
 };
 
@@ -1472,8 +1606,8 @@ size_t fold_side_bytes(int n) {
 size_t fold_image_bytes(int H, int W) {
     const FoldDims fd = fold_dims(H, W);
     const size_t hNp = fd.hNp, hMp = fd.hMp;
-    return 2 * (2 * rup((size_t)H * hMp * 2, 1024) + rup(4 * hMp * hNp * 2, 1024) +
-                4 * rup(hMp * hNp * 2, 1024));
+    return 2 * (2 * rup((size_t)H * hMp * 2, 1024) + 4 * rup(hMp * hNp * 2, 1024) +
+                4 * rup(hMp * hNp * 2, 1024) + 2 * rup((size_t)fd.Hp * hMp * 2, 1024));
 }
 
 template <typename Take>
@@ -1504,15 +1638,13 @@ void carve_fold_image(FoldImage& im, int H, int W, Take take) {
         im.Re[q] = take((size_t)H * hMp * 2);
         im.Ro[q] = take((size_t)H * hMp * 2);
     }
-    for (int q = 0; q < 2; ++q) {
-        // T1 (four hMp x hNp blocks) and, after stage 2 has read it, T3 (two Hp x hMp blocks;
-        // Hp <= 2 hNp)
-        char* region = static_cast<char*>(take(4 * hMp * hNp * 2));
-        for (int b = 0; b < 4; ++b) im.T1[b][q] = region + (size_t)b * hMp * hNp * 2;
-        for (int x = 0; x < 2; ++x) im.T3[x][q] = region + (size_t)x * fd.Hp * hMp * 2;
-    }
+    for (int q = 0; q < 2; ++q)
+        for (int b = 0; b < 4; ++b) im.T1[b][q] = take(hMp * hNp * 2);
     for (int q = 0; q < 2; ++q)
         for (int b = 0; b < 4; ++b) im.T2[b][q] = take(hMp * hNp * 2);
+    // T3 rows H .. Hp-1 are read as A rows of stage 4 (masked there) and never written: zero
+    for (int q = 0; q < 2; ++q)
+        for (int x = 0; x < 2; ++x) im.T3[x][q] = take((size_t)fd.Hp * hMp * 2);
 }
 
 // Appends one image's nine problems (2, 4, 2 and 1 per stage) to the stage tables.
@@ -1636,20 +1768,241 @@ bool number_fold_tiles(std::vector<GemmTile> (&tab)[4], int (&tiles)[4]) {
     return true;
 }
 
+// ---- fused launch: problem table, work list with panel dependencies ----------------------
+struct FusedDev {
+    GemmTile* probs = nullptr;
+    FoldItem* items = nullptr;
+    unsigned* ctr = nullptr;     // n_ctr panel counters and the exit counter
+    DevState** sts = nullptr;    // the images' states
+    int n_probs = 0, n_items = 0, n_ctr = 0, n_st = 0, pairs = 0, honour_stop = 1;
+};
+
+// Items and panel counters of one image's four stages.
+void fused_counts(int H, int W, int& items, int& ctrs) {
+    const FoldDims d = fold_dims(H, W);
+    const int mb = d.hMp / 256, nb = d.hNp / 256;
+    items = 2 * mb * (d.hNp / 128) + 4 * mb * nb + 2 * nb * mb + (d.Hp / 256) * mb;
+    ctrs = 2 * mb + 4 * mb + 2 * nb;
+}
+
+size_t fused_bytes(int n_img, int items, int ctrs) {
+    return rup((size_t)9 * n_img * sizeof(GemmTile), 1024) +
+           rup((size_t)items * sizeof(FoldItem), 1024) + rup((size_t)(ctrs + 1) * 4, 1024) +
+           rup((size_t)n_img * sizeof(DevState*), 1024);
+}
+
+template <typename Take>
+void carve_fused(FusedDev& fd, int n_img, int items, int ctrs, Take take) {
+    fd.probs = static_cast<GemmTile*>(take((size_t)9 * n_img * sizeof(GemmTile)));
+    fd.items = static_cast<FoldItem*>(take((size_t)items * sizeof(FoldItem)));
+    fd.ctr = static_cast<unsigned*>(take((size_t)(ctrs + 1) * 4));
+    fd.sts = static_cast<DevState**>(take((size_t)n_img * sizeof(DevState*)));
+    fd.n_st = n_img;
+    fd.n_probs = 9 * n_img;
+    fd.n_items = items;
+    fd.n_ctr = ctrs;
+}
+
+// From the per-stage tables (every image's problems in image order, tiles numbered): one problem
+// table and the work list, stage after stage.  Stage-2 tiles of an image stay consecutive (its
+// r^T z run flags assume that); stage-4 tiles of an image are ordered by the last stage-3 panel
+// they read.  `pairs` is the launch's pair count (the static item -> pair assignment).
+bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& Hs,
+                 int pairs, int reduce_rho, std::vector<GemmTile>& probs,
+                 std::vector<FoldItem>& items, int& n_ctr) {
+    const int n_img = (int)Hs.size();
+    if ((int)tab[0].size() != 2 * n_img || (int)tab[1].size() != 4 * n_img ||
+        (int)tab[2].size() != 2 * n_img || (int)tab[3].size() != n_img)
+        return false;
+    probs.clear();
+    items.clear();
+    int off[4];
+    for (int k = 0; k < 4; ++k) {
+        off[k] = (int)probs.size();
+        for (GemmTile g : tab[k]) {
+            g.epi = k == 0 ? UE_FOLD16
+                           : k == 1 ? (reduce_rho ? UE_EIG16_RHO : UE_EIG16)
+                                    : k == 2 ? UE_UNFOLD16 : UE_UNFOLDZ;
+            g.dual = k >= 2 ? 1 : 0;
+            probs.push_back(g);
+        }
+    }
+    // counters: per image, stage-1 panels (x, l'-block), stage-2 panels (xy, l'-block), stage-3
+    // panels (x, i'-block)
+    std::vector<int> c1(n_img), c2(n_img), c3(n_img), mbs(n_img), nbs(n_img);
+    int n = 0;
+    for (int i = 0; i < n_img; ++i) {
+        mbs[i] = tab[1][4 * i].M / 256;
+        nbs[i] = tab[2][2 * i].M / 256;
+        c1[i] = n; n += 2 * mbs[i];
+        c2[i] = n; n += 4 * mbs[i];
+        c3[i] = n; n += 2 * nbs[i];
+    }
+    n_ctr = n;
+    auto ntiles = [](const GemmTile& g) { return (g.M / 256) * g.gx; };
+    // stage 1: no dependencies (the folded residual comes from the previous launch)
+    for (int i = 0; i < n_img; ++i)
+        for (int x = 0; x < 2; ++x) {
+            const GemmTile& g = tab[0][2 * i + x];
+            for (int l = 0; l < ntiles(g); ++l) {
+                FoldItem f{};
+                f.prob = off[0] + 2 * i + x;
+                f.local = l;
+                f.sig = c1[i] + x * mbs[i] + l / g.gx;
+                items.push_back(f);
+            }
+        }
+    // stage 2 (x, y): the stage-1 panel of T1x at the same l'-block
+    std::vector<int> r2a(n_img), r2b(n_img);
+    for (int i = 0; i < n_img; ++i) {
+        r2a[i] = (int)items.size();
+        for (int q = 0; q < 4; ++q) {
+            const GemmTile& g = tab[1][4 * i + q];
+            const int x = q >> 1;
+            const int need = 2 * tab[0][2 * i + x].gx;
+            for (int l = 0; l < ntiles(g); ++l) {
+                FoldItem f{};
+                f.prob = off[1] + 4 * i + q;
+                f.local = l;
+                f.sig = c2[i] + q * mbs[i] + l / g.gx;
+                f.ndep = 1;
+                f.dep[0] = c1[i] + x * mbs[i] + l / g.gx;
+                f.need[0] = need;
+                items.push_back(f);
+            }
+        }
+        r2b[i] = (int)items.size();
+    }
+    // stage 3 (x): B rows = the l'-block of T2(x, e) and T2(x, o)
+    for (int i = 0; i < n_img; ++i)
+        for (int x = 0; x < 2; ++x) {
+            const GemmTile& g = tab[2][2 * i + x];
+            const int need = 2 * tab[1][4 * i].gx;
+            for (int l = 0; l < ntiles(g); ++l) {
+                const int m = l / g.gx, nn = l % g.gx;
+                FoldItem f{};
+                f.prob = off[2] + 2 * i + x;
+                f.local = l;
+                f.sig = c3[i] + x * nbs[i] + m;
+                f.ndep = 2;
+                f.dep[0] = c2[i] + (2 * x) * mbs[i] + nn;
+                f.dep[1] = c2[i] + (2 * x + 1) * mbs[i] + nn;
+                f.need[0] = f.need[1] = need;
+                items.push_back(f);
+            }
+        }
+    // stage 4: A rows r of T3e and T3o come from i' = r (r < hN) or i' = H - 1 - r (r >= hN)
+    for (int i = 0; i < n_img; ++i) {
+        const GemmTile& g = tab[3][i];
+        const int H = Hs[i], hN = H / 2;
+        const int need = 2 * tab[2][2 * i].gx;
+        std::vector<std::pair<int, FoldItem>> st4;
+        for (int l = 0; l < ntiles(g); ++l) {
+            const int m = l / g.gx;
+            const int lo = 256 * m, hi = std::min(256 * m + 256, H);   // rows [lo, hi)
+            std::vector<int> m3;
+            auto add = [&](int ip) {
+                const int b = ip / 256;
+                if (std::find(m3.begin(), m3.end(), b) == m3.end()) m3.push_back(b);
+            };
+            for (int r = lo; r < hi; r += 1) {
+                if (r < hN) add(r);
+                else add(H - 1 - r);
+            }
+            FoldItem f{};
+            f.prob = off[3] + i;
+            f.local = l;
+            f.sig = -1;
+            int key = -1;
+            for (int x = 0; x < 2; ++x)
+                for (int b : m3) {
+                    if (f.ndep >= kMaxDeps) return false;
+                    f.dep[f.ndep] = c3[i] + x * nbs[i] + b;
+                    f.need[f.ndep] = need;
+                    ++f.ndep;
+                    key = std::max(key, b);
+                }
+            st4.push_back({key, f});
+        }
+        std::stable_sort(st4.begin(), st4.end(),
+                         [](const std::pair<int, FoldItem>& a, const std::pair<int, FoldItem>& b) {
+                             return a.first < b.first;
+                         });
+        for (auto& e : st4) items.push_back(e.second);
+    }
+    // tile coordinates and the stop flag, so that the kernel's producer and issuer need only the
+    // item record
+    for (FoldItem& f : items) {
+        const GemmTile& g = probs[f.prob];
+        const int tn = g.dual ? 256 : (g.mirror_b1 ? 128 : 256);
+        f.st = g.ep.st;
+        f.skip = g.ep.skip_if_done;
+        f.m0 = (f.local / g.gx) * 256;
+        f.n0 = (f.local % g.gx) * tn;
+        f.nb1 = g.mirror_b1 ? g.nb_rows - f.n0 - 128 : f.n0 + 128;
+        f.nkb = g.K / UBK;
+        f.dual = g.dual;
+        f.epi = g.epi;
+    }
+    // r^T z run flags of stage 2 (item t runs on pair t mod pairs)
+    for (int i = 0; i < n_img; ++i) {
+        const int a = r2a[i], b = r2b[i];
+        for (int t = a; t < b; ++t) {
+            items[t].rho_end = t + pairs >= b ? 1 : 0;
+            items[t].rho_nslot = 2 * std::min(pairs, b - a);
+        }
+    }
+    return true;
+}
+
+// Copies the tables; the images' states are the stage-4 problems' (one per image).
+cudaError_t upload_fused(FusedDev& fd, const std::vector<GemmTile>& probs,
+                         const std::vector<FoldItem>& items, int n_ctr, cudaStream_t s) {
+    if ((int)probs.size() != fd.n_probs || (int)items.size() != fd.n_items || n_ctr != fd.n_ctr)
+        return cudaErrorInvalidValue;
+    std::vector<DevState*> sts;
+    fd.honour_stop = 1;
+    for (const GemmTile& g : probs) {
+        if (g.epi == UE_UNFOLDZ) sts.push_back(g.ep.st);
+        if (!g.ep.skip_if_done) fd.honour_stop = 0;
+    }
+    if ((int)sts.size() != fd.n_st) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(fd.probs, probs.data(), probs.size() * sizeof(GemmTile),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(fd.sts, sts.data(), sts.size() * sizeof(DevState*),
+                        cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(fd.items, items.data(), items.size() * sizeof(FoldItem),
+                           cudaMemcpyHostToDevice, s);
+}
+
+// Pairs of the fused launch: every pair must be resident at once (tiles wait on other pairs).
+int fused_pairs(int n_sm) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_sm);
+    cfg.blockDim = dim3(k2Threads);
+    cfg.dynamicSmemBytes = Q2Cfg<0>::kSmem;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k2_fold_fused, &cfg) != cudaSuccess || nc < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::min(n_sm / 2, nc);
+}
+
+cudaError_t launch_fused(const FusedDev& fd, cudaStream_t s) {
+    k2_fold_fused<<<2 * fd.pairs, k2Threads, Q2Cfg<0>::kSmem, s>>>(
+        fd.probs, fd.items, fd.n_items, fd.ctr, fd.n_ctr, fd.sts, fd.n_st, fd.honour_stop);
+    return cudaGetLastError();
+}
+
 cudaError_t set_fold_attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e;
-    for (auto fn : {k2_umma_gemm<UE_FOLD16, 0, 128>, k2_umma_gemm<UE_EIG16, 0, 256>,
-                    k2_umma_gemm<UE_EIG16_RHO, 0, 256>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
-        if (e != cudaSuccess) return e;
-    }
-    for (auto fn : {k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN>, k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Q2Cfg<1, kPairDualN>::kSmem);
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = cudaFuncSetAttribute(
+        k2_fold_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, Q2Cfg<0>::kSmem);
+    if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
 }
@@ -1659,25 +2012,6 @@ int device_sms() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     return n;
-}
-
-// The four stage launches over a set of tables (one image, or every image of a batch).
-cudaError_t launch_fold_stages(void* const (&d_tab)[4], const int (&count)[4],
-                               const int (&tiles)[4], int n_sm, int reduce_rho, cudaStream_t s) {
-    auto tab = [&](int k) { return static_cast<const GemmTile*>(d_tab[k]); };
-    auto grid = [&](int k) { return 2 * std::max(1, std::min(tiles[k], n_sm / 2)); };
-    const int s0 = Q2Cfg<0>::kSmem, s1 = Q2Cfg<1, kPairDualN>::kSmem;
-    const int* c = count;
-    const int* t = tiles;
-    // r^T z is reduced in stage 2 from the spectral coefficients (no re-read of r_U in stage 4)
-    k2_umma_gemm<UE_FOLD16, 0, 128><<<grid(0), k2Threads, s0, s>>>(tab(0), c[0], t[0]);
-    if (reduce_rho)
-        k2_umma_gemm<UE_EIG16_RHO, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
-    else
-        k2_umma_gemm<UE_EIG16, 0, 256><<<grid(1), k2Threads, s0, s>>>(tab(1), c[1], t[1]);
-    k2_umma_gemm<UE_UNFOLD16, 1, kPairDualN><<<grid(2), k2Threads, s1, s>>>(tab(2), c[2], t[2]);
-    k2_umma_gemm<UE_UNFOLDZ, 1, kPairDualN><<<grid(3), k2Threads, s1, s>>>(tab(3), c[3], t[3]);
-    return cudaGetLastError();
 }
 
 FoldRRec fold_r_rec(const FoldImage& im, const float* rU, int ld, int H, int W,
@@ -1705,14 +2039,17 @@ struct FoldBufs {
     DevState* st = nullptr;
     double* partials = nullptr;
     float tau = 0.f;
-    int n_sm = 0;                  // SMs of the device: persistent grid size
-    int tiles[4] = {0, 0, 0, 0};   // output tiles per stage
+    int rho = -1;                  // r^T z formed in stage 2 (the tables' stage-2 epilogue)
+    int n_sm = 0;                  // SMs of the device
+    FusedDev fused;
 };
 
 size_t fold_bytes(int H, int W) {
     size_t b = fold_side_bytes(H) + fold_image_bytes(H, W);
     if (H != W) b += fold_side_bytes(W);
-    return b + 4 * rup(4 * sizeof(GemmTile), 1024) + 64 * 1024;
+    int items = 0, ctrs = 0;
+    fused_counts(H, W, items, ctrs);
+    return b + fused_bytes(1, items, ctrs) + 64 * 1024;
 }
 
 cudaError_t fold_setup(DctPlan& d, char* p) {
@@ -1731,7 +2068,11 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     else f.sM = f.sN;
     carve_fold_image(f.img, H, W, take);
     f.dim = f.img.dim;
-    for (int st = 0; st < 4; ++st) d.fold_tiles[st] = take(4 * sizeof(GemmTile));
+    {
+        int items = 0, ctrs = 0;
+        fused_counts(H, W, items, ctrs);
+        carve_fused(f.fused, 1, items, ctrs, take);
+    }
     // padding (columns hM.. of the folded residual, which nothing else writes) stays zero
     cudaError_t e = cudaMemset(p_begin, 0, (size_t)(p - p_begin));
     if (e != cudaSuccess) return e;
@@ -1739,32 +2080,34 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     build_fold_side(f.sN);
     if (H != W) build_fold_side(f.sM);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int cnt[4] = {2, 4, 2, 1};   // problems per stage
-    for (int k = 0; k < 4; ++k) d.fold_count[k] = cnt[k];
     if ((e = set_fold_attrs()) != cudaSuccess) return e;
     f.n_sm = device_sms();
-    return f.n_sm > 1 ? cudaSuccess : cudaErrorInvalidDevice;
+    f.fused.pairs = fused_pairs(f.n_sm);
+    return f.n_sm > 1 && f.fused.pairs > 0 ? cudaSuccess : cudaErrorInvalidDevice;
 }
 
-// (Re)builds the four stage tables of the folded form for the given planes, state and flags and
-// copies them in stream order (kernels still reading the previous tables finish first).
+// (Re)builds the fused launch's problem table and work list for the given planes, state and
+// flags and copies them in stream order (a launch still reading the previous tables finishes
+// first).
 cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU, int ld,
-                      DevState* st, double* partials, int flexible, int skip, cudaStream_t s) {
+                      DevState* st, double* partials, int flexible, int skip, int rho,
+                      cudaStream_t s) {
     for (auto& t : f.tab) t.clear();
     if (!append_fold_problems(f.tab, f.img, f.sN, f.sM, d.H, d.W, rU, zU, ld, st, partials,
                               flexible, skip, d.tau))
         return cudaErrorNotSupported;
-    if (!number_fold_tiles(f.tab, f.tiles)) return cudaErrorInvalidValue;
-    for (int k = 0; k < 4; ++k) {
-        if ((int)f.tab[k].size() != d.fold_count[k]) return cudaErrorInvalidValue;
-        cudaError_t e = cudaMemcpyAsync(d.fold_tiles[k], f.tab[k].data(),
-                                        f.tab[k].size() * sizeof(GemmTile),
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
+    int tiles[4];
+    if (!number_fold_tiles(f.tab, tiles)) return cudaErrorInvalidValue;
+    std::vector<GemmTile> probs;
+    std::vector<FoldItem> items;
+    int n_ctr = 0;
+    if (!build_fused(f.tab, std::vector<int>{d.H}, f.fused.pairs, rho, probs, items, n_ctr))
+        return cudaErrorInvalidValue;
+    cudaError_t e = upload_fused(f.fused, probs, items, n_ctr, s);
+    if (e != cudaSuccess) return e;
     f.bound = true;
     f.rU = rU; f.zU = zU; f.ld = ld; f.st = st; f.partials = partials;
-    f.flexible = flexible; f.skip = skip; f.tau = d.tau;
+    f.flexible = flexible; f.skip = skip; f.tau = d.tau; f.rho = rho;
     return cudaSuccess;
 }
 
@@ -1774,17 +2117,25 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
     FoldBufs& f = *static_cast<FoldBufs*>(d.fold_host);
     if (!f.bound || f.rU != rU || f.zU != zU || f.ld != ld || f.st != st ||
         f.partials != partials || f.flexible != flexible || f.skip != skip_if_done ||
-        f.tau != d.tau) {
-        cudaError_t e = fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, s);
+        f.tau != d.tau || f.rho != reduce_rho) {
+        cudaError_t e =
+            fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, reduce_rho, s);
         if (e != cudaSuccess) return e;
     }
     k_fold_r<<<fold_r_blocks(d.H, d.W), 256, 0, s>>>(fold_r_rec(f.img, rU, ld, d.H, d.W, st),
                                                       skip_if_done);
-    void* const tabs[4] = {d.fold_tiles[0], d.fold_tiles[1], d.fold_tiles[2], d.fold_tiles[3]};
-    return launch_fold_stages(tabs, d.fold_count, f.tiles, f.n_sm, reduce_rho, s);
+    return launch_fused(f.fused, s);
 }
 
 }  // namespace
+
+// Zeroes the fused launch's counters (each launch leaves them zero; this recovers from a launch
+// that stopped on a timeout).
+cudaError_t umma_dct_reset(const DctPlan& d, cudaStream_t s) {
+    if (!d.fold_host) return cudaSuccess;
+    const FusedDev& fd = static_cast<const FoldBufs*>(d.fold_host)->fused;
+    return cudaMemsetAsync(fd.ctr, 0, (size_t)(fd.n_ctr + 1) * 4, s);
+}
 
 void umma_dct_release(DctPlan& d) {
     delete static_cast<FoldBufs*>(d.fold_host);
@@ -1951,9 +2302,15 @@ BatchLayout batch_layout(const int* H, const int* W, int T, int prec, int fold) 
                     L.sides.push_back(n);
         for (int n : L.sides) L.side_bytes += fold_side_bytes(n);
         for (int t = 0; t < T; ++t) L.image_bytes += fold_image_bytes(H[t], W[t]);
-        // problems per image and stage: 2, 4, 2, 1; then the fold records
-        L.tiles_bytes = (2 + 4 + 2 + 1 + 4) * rup((size_t)T * sizeof(GemmTile), 1024) +
-                        rup((size_t)T * sizeof(FoldRRec), 1024);
+        // the fold records and the fused launch's tables
+        int items = 0, ctrs = 0;
+        for (int t = 0; t < T; ++t) {
+            int it = 0, ct = 0;
+            fused_counts(H[t], W[t], it, ct);
+            items += it;
+            ctrs += ct;
+        }
+        L.tiles_bytes = rup((size_t)T * sizeof(FoldRRec), 1024) + fused_bytes(T, items, ctrs);
         L.total = L.side_bytes + L.image_bytes + L.tiles_bytes + 4096;
         return L;
     }
@@ -2026,21 +2383,36 @@ cudaError_t batch_fold_setup(BatchDctPlan& bd, const int* H, const int* W, int T
     }
     int tiles[4];
     if (!number_fold_tiles(tab, tiles)) return cudaErrorInvalidValue;
-    for (int k = 0; k < 4; ++k) {
-        bd.d_tiles[k] = take(tab[k].size() * sizeof(GemmTile));
-        bd.total_ctas[k] = tiles[k];
-        bd.count[k] = (int)tab[k].size();
-        e = cudaMemcpy(bd.d_tiles[k], tab[k].data(), tab[k].size() * sizeof(GemmTile),
-                       cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return e;
+    if ((e = set_fold_attrs()) != cudaSuccess) return e;
+    bd.n_sm = device_sms();
+    FusedDev fd;
+    fd.pairs = fused_pairs(bd.n_sm);
+    if (bd.n_sm < 2 || fd.pairs < 1) return cudaErrorInvalidDevice;
+    {
+        int items = 0, ctrs = 0;
+        for (int t = 0; t < T; ++t) {
+            int it = 0, ct = 0;
+            fused_counts(H[t], W[t], it, ct);
+            items += it;
+            ctrs += ct;
+        }
+        carve_fused(fd, T, items, ctrs, take);
+        std::vector<GemmTile> probs;
+        std::vector<FoldItem> fitems;
+        int n_ctr = 0;
+        if (!build_fused(tab, std::vector<int>(H, H + T), fd.pairs, 1, probs, fitems, n_ctr))
+            return cudaErrorInvalidValue;
+        if ((e = upload_fused(fd, probs, fitems, n_ctr, 0)) != cudaSuccess) return e;
+        if ((e = cudaMemset(fd.ctr, 0, (size_t)(fd.n_ctr + 1) * 4)) != cudaSuccess) return e;
     }
+    bd.d_probs = fd.probs; bd.d_items = fd.items; bd.d_ctr = fd.ctr; bd.d_sts = fd.sts;
+    bd.n_probs = fd.n_probs; bd.n_items = fd.n_items; bd.n_ctr = fd.n_ctr; bd.pairs = fd.pairs;
+    bd.n_st = fd.n_st; bd.honour_stop = fd.honour_stop;
     bd.d_frec = take((size_t)T * sizeof(FoldRRec));
     bd.frec_blocks = blk;
     e = cudaMemcpy(bd.d_frec, recs.data(), (size_t)T * sizeof(FoldRRec), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    if ((e = set_fold_attrs()) != cudaSuccess) return e;
-    bd.n_sm = device_sms();
-    return bd.n_sm > 1 ? cudaSuccess : cudaErrorInvalidDevice;
+    return cudaDeviceSynchronize();
 }
 
 }  // namespace
@@ -2164,14 +2536,25 @@ cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T,
     return cudaSuccess;
 }
 
+cudaError_t batch_dct_reset(const BatchDctPlan& bd, cudaStream_t s) {
+    if (!bd.fold) return cudaSuccess;
+    return cudaMemsetAsync(bd.d_ctr, 0, (size_t)(bd.n_ctr + 1) * 4, s);
+}
+
 cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s) {
     using C22 = UCfg<128, 2, 2>;
     using C11 = UCfg<128, 1, 1>;
     const int T = bd.T;
     if (bd.fold) {
         k_fold_r_batched<<<bd.frec_blocks, 256, 0, s>>>(static_cast<const FoldRRec*>(bd.d_frec), T);
-        void* const tabs[4] = {bd.d_tiles[0], bd.d_tiles[1], bd.d_tiles[2], bd.d_tiles[3]};
-        return launch_fold_stages(tabs, bd.count, bd.total_ctas, bd.n_sm, 1, s);
+        FusedDev fd;
+        fd.probs = static_cast<GemmTile*>(bd.d_probs);
+        fd.items = static_cast<FoldItem*>(bd.d_items);
+        fd.ctr = static_cast<unsigned*>(bd.d_ctr);
+        fd.sts = static_cast<DevState**>(bd.d_sts);
+        fd.n_probs = bd.n_probs; fd.n_items = bd.n_items; fd.n_ctr = bd.n_ctr; fd.pairs = bd.pairs;
+        fd.n_st = bd.n_st; fd.honour_stop = bd.honour_stop;
+        return launch_fused(fd, s);
     }
     auto tiles = [&](int k) { return static_cast<const GemmTile*>(bd.d_tiles[k]); };
     if (bd.split) {

@@ -340,6 +340,7 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
     const size_t pb = p->L.plane_bytes;
     cudaEvent_t t0;
     ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    ck(dct_reset(p->dct, s));
     t0 = pf.begin(s);
     ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
     ck(launch_bnorm(p->P, a, st, p->partials, s));
@@ -520,6 +521,7 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
     ck(cudaMemcpyAsync(b->d_recs, b->recs.data(), (size_t)T * sizeof(TileRec),
                        cudaMemcpyHostToDevice, s));
     ck(cudaMemsetAsync(b->states, 0, (size_t)T * sizeof(DevState), s));
+    ck(batch_dct_reset(b->dct, s));
     ck(launch_init_batched(b->d_recs, T, b->total_strip, s));
     ck(launch_bnorm_batched(b->d_recs, T, b->total_strip, s));
     std::vector<DevState> h(T);
@@ -786,6 +788,7 @@ int irls_unwrap_backward(irls_tape t, const float* dLdU, float* dLdX, float* dLd
         DevState* st = p->st;
         const size_t pb = t->plane_bytes;
         ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+        ck(dct_reset(p->dct, s));
         for (float* z : {t->Gbv, t->Gbh, t->Cbv, t->Cbh}) ck(cudaMemsetAsync(z, 0, pb, s));
         ck(launch_adj_init(p->P, a, dLdU, st, p->partials, s));
         for (int k = t->K - 1; k >= 0; --k) {
@@ -1017,6 +1020,7 @@ int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) 
         ck(cudaMemsetAsync(p->P.rU, 0, p->L.plane_bytes, s));
         ck(launch_copy_in(R, p->H, p->W, p->P.rU, p->ld, s));
         if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.r16lo, a.ld16, s));
+        ck(dct_reset(p->dct, s));
         ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, p->st, 0, a, p->partials, 0, s));
         ck(launch_copy_out(p->P.zU, p->H, p->W, p->ld, Z, s));
     } catch (Fail&) {

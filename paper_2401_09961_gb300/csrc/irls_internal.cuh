@@ -45,6 +45,7 @@ struct DevState {
     int cg_total;
     unsigned int counter;   // last-block-done ticket for the deterministic reductions
     int pbuf;        // which ping-pong buffer holds the newest search direction
+    int stop_next;   // a stop found inside a launch whose tiles still test done (set at its end)
     int cg_iters[kMaxOuter];
     double rel_res[kMaxOuter];
     double l1_obj[kMaxOuter];
@@ -102,8 +103,6 @@ struct DctPlan {
     // folded (even/odd) form for H, W multiples of 256: half-size products on r_U(j) +- r_U(W-1-j)
     int fold;                  // folded form in use
     int fold_ready;            // folded form built (memory, bases)
-    void* fold_tiles[4];       // device tables of grouped-GEMM problems per stage
-    int fold_count[4];         // problems per stage (2, 4, 2, 1)
     void *Re, *Relo, *Ro, *Rolo;   // folded residual, H x W/2 each
     void* fold_host;               // host-side record of the folded form (owned)
     alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
@@ -124,20 +123,26 @@ struct TileRec {
     int ublk0, ugy;            // update kernel's blocks (same columns, its own rows per block)
 };
 
-// Tensor-core preconditioner of a batched solve: per-stage device arrays of grouped-GEMM
-// problems, and the DCT bases cached per distinct side length.  Direct form: one problem per
-// image and stage, the images' bf16 copies of r_U (written by the update kernel).  Folded form
-// (fold = 1): each image's nine problems of the four CTA-pair stages, and the images' fold
-// records (the fold of r_U runs as its own batched launch).
+// Tensor-core preconditioner of a batched solve, with the DCT bases cached per distinct side
+// length.  Direct form: per-stage device arrays of grouped-GEMM problems (one per image and
+// stage) and the images' bf16 copies of r_U (written by the update kernel).  Folded form
+// (fold = 1): one problem table holding each image's nine problems of the four stages, the
+// fused launch's work list and panel counters, and the images' fold records (the fold of r_U
+// runs as its own batched launch).
 struct BatchDctPlan {
     int T = 0, prec = 0, split = 0, fold = 0;
     float tau = 0.f;
-    void* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
-    int total_ctas[4] = {0, 0, 0, 0};   // direct: CTAs per stage; folded: output tiles
-    int count[4] = {0, 0, 0, 0};        // problems per stage
+    void* d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};   // direct: problems per stage
+    int total_ctas[4] = {0, 0, 0, 0};                         // direct: CTAs per stage
     void* d_frec = nullptr;             // folded: T fold records
     int frec_blocks = 0;
     int n_sm = 0;
+    // folded: the fused launch's problem table, work list and panel counters
+    void* d_probs = nullptr;
+    void* d_items = nullptr;
+    void* d_ctr = nullptr;
+    void* d_sts = nullptr;
+    int n_probs = 0, n_items = 0, n_ctr = 0, pairs = 0, n_st = 0, honour_stop = 1;
     std::vector<void*> r16, r16lo;
     std::vector<int> ld16;
 };
@@ -199,6 +204,8 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
 // receives error flags; with reduce_rho the last GEMM also forms rho = r_U^T z_U + st->rz_v
 // and the next beta (Alg. 2).  With skip_if_done the launches return at once once CG stopped.
 void dct_release(DctPlan& d);
+// zeroes the folded form's launch counters (recovery after a launch that timed out)
+cudaError_t dct_reset(const DctPlan& d, cudaStream_t s);
 cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
                                   double* partials, cudaStream_t s);
 cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
@@ -224,5 +231,6 @@ cudaError_t batch_dct_setup(BatchDctPlan& bd, const int* H, const int* W, int T,
                             float* const* zU, const int* ld, DevState* states,
                             double* const* partials);
 cudaError_t batch_dct_apply(const BatchDctPlan& bd, cudaStream_t s);
+cudaError_t batch_dct_reset(const BatchDctPlan& bd, cudaStream_t s);
 
 }  // namespace irls
