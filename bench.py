@@ -158,6 +158,8 @@ def main():
                          "--width 16000 for the paper's 4000 x M scaling shapes")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default stencil tile shapes (no timing pass before warm-up)")
     ap.add_argument("--dct-form", default="auto", choices=["auto", "direct", "folded"],
                     help="preconditioner form (auto: folded where allowed)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -205,6 +207,8 @@ def main():
                      cg_max_iter=1000, precision=prec, flexible_cg=flexible,
                      cg_schedule=args.cg_schedule, system=args.system, dct_form=args.dct_form)
     stream = torch.cuda.current_stream()
+    # stencil tile shapes timed on this GPU before the warm-up (outside the timed region)
+    tune = None if (args.no_autotune or args.system != "full") else plan.autotune()
     U = torch.empty_like(X)
     for _ in range(args.warmup):
         _, st = plan.unwrap(X, C, out=U)
@@ -356,6 +360,9 @@ def main():
                        "precision": prec, "flexible_cg": bool(flexible),
                        "dct_form": "folded" if folded else ("direct" if prec != "fp32" else
                                                             "fp32 simt"),
+                       "stencil_tiles": {"direction_rows": plan.tiles[0],
+                                         "update_rows": plan.tiles[1],
+                                         "autotuned": tune is not None},
                        "cg_iters_total": cg_total, "l1_objective": stats[-1]["l1_obj"][-1],
                        "cg_iters_per_outer": stats[-1]["cg_iters"],
                        **({"cg_caps": stats[-1]["cg_cap"]} if args.cg_schedule == "paper"
@@ -391,6 +398,8 @@ def batched_arm(args, rank, world, local):
     b = irls.Batch(shapes, precision=prec, tau=TAU, delta=DELTA, outer_iters=args.outer,
                    cg_tol=CG_TOL, cg_max_iter=1000, flexible_cg=1 if prec == "bf16" else 0,
                    dct_form=args.dct_form)
+    # stencil tile shapes timed on this GPU before the warm-up (outside the timed region)
+    tune = None if args.no_autotune else b.autotune()
     for _ in range(args.warmup):
         b.unwrap(Xs, Cs)
     torch.cuda.synchronize()
@@ -432,6 +441,8 @@ def batched_arm(args, rank, world, local):
                        "cg_iters_total": sum(x["cg_total"] for x in st),
                        "cg_iters_max_tile": max(x["cg_total"] for x in st),
                        "dct_form": "folded" if b.folded else "direct",
+                       "stencil_tiles": {"direction_rows": b.tiles[0], "update_rows": b.tiles[1],
+                                         "autotuned": tune is not None},
                        "uses_graphs": b.uses_graphs},
             "single_image_sequential_mpix_s": (mpix / t_single) if t_single else None,
             "clocks": clk,

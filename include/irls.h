@@ -151,6 +151,22 @@ int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
  * choice of this library). */
 int irls_plan_dct_form(irls_plan plan);
 
+/* Tile shapes of the CG direction and update kernels (Alg. 2's two stencil passes per
+ * iteration, both bound by HBM bandwidth): image rows per thread block, one of 8, 16, 24, 32
+ * (defaults 24 and 32).  They change the block decomposition, so results change within
+ * rounding (the reductions' summation order follows the blocks), never the method.
+ * irls_plan_set_tiles sets them (0 keeps a value; anything else not in the list is
+ * IRLS_ERR_ARG); irls_plan_get_tiles reads the values in use.  irls_plan_autotune times each
+ * allowed value of each kernel on the plan's workspace (ten launches each, after two warm-up
+ * launches, CUDA events on `stream`) and keeps the fastest; h_ms (NULL allowed) receives the
+ * eight mean times in ms: direction for 8, 16, 24, 32 rows, then update.  It overwrites the
+ * plan's scratch planes and state: call it between solves, not between a forward record and
+ * its backward sweep.  Synchronous with respect to the host.  The batched form keeps
+ * the defaults.  No counterpart in the paper (an implementation choice of this library). */
+int irls_plan_set_tiles(irls_plan plan, int dir_rows, int upd_rows);
+int irls_plan_get_tiles(irls_plan plan, int* dir_rows, int* upd_rows);
+int irls_plan_autotune(irls_plan plan, float* h_ms, void* stream);
+
 /* Simple form: unwrap d_X (H x W) into d_U (H x W, zero mean) with weights from d_coherence
  * (H x W, may be NULL for uniform weights), delta = eps, the given number of IRLS iterations
  * and CG tolerance, and the remaining options at their defaults (tau = 1e-2).  Edge weights from
@@ -200,6 +216,18 @@ int irls_unwrap_batched(int ntiles, const int* H, const int* W, const float* con
                         irls_stats* per_tile, void* stream);
 int irls_batch_uses_graphs(irls_batch batch);
 int irls_batch_dct_form(irls_batch batch);
+
+/* Tile shapes of the batched CG direction and update launches (one value per batch, the same
+ * meaning and allowed values as irls_plan_set_tiles; defaults 24 and 32).  An image's blocks,
+ * and so its results, are those of a single-image plan with the same tile shapes.
+ * irls_batch_autotune times each allowed value of each kernel over the whole batch (ten
+ * launches each after two warm-up launches, CUDA events) and keeps the fastest; h_ms as for
+ * irls_plan_autotune.  Both overwrite the batch's scratch and states: call them between runs;
+ * the CG chunk graphs are captured again on the next run.  Ordered after `stream`; synchronous
+ * with respect to the host. */
+int irls_batch_set_tiles(irls_batch batch, int dir_rows, int upd_rows);
+int irls_batch_get_tiles(irls_batch batch, int* dir_rows, int* upd_rows);
+int irls_batch_autotune(irls_batch batch, float* h_ms, void* stream);
 
 /* Forward solve that records what the adjoint needs (the reverse sweep below):
  * the wrapped gradients G and weights C it used, and V^k of every outer step k = 0..K (the

@@ -67,6 +67,39 @@ class Plan:
             raise RuntimeError("plan destroyed")
         return self._h
 
+    @property
+    def tiles(self):
+        """(direction, update) image rows per block of the CG stencil kernels in use."""
+        d, u = ctypes.c_int(), ctypes.c_int()
+        check(lib().irls_plan_get_tiles(self.handle, ctypes.byref(d), ctypes.byref(u)),
+              "irls_plan_get_tiles")
+        return d.value, u.value
+
+    def set_tiles(self, dir_rows=0, upd_rows=0):
+        """Sets the stencil tile shapes (one of 8, 16, 24, 32; 0 keeps the current value)."""
+        check(lib().irls_plan_set_tiles(self.handle, int(dir_rows), int(upd_rows)),
+              "irls_plan_set_tiles")
+
+    def autotune(self, cache=None, stream=None):
+        """Times the stencil kernels' tile shapes on this GPU and keeps the fastest.  With
+        `cache` (a JSON file path) a result stored for the same size, precision, system and GPU
+        is applied without timing, and a new result is stored.  Returns a dict with the tiles in
+        use, the eight timings in ms (None when cached) and whether the cache answered."""
+        from . import tuning
+        torch = _torch()
+        key = tuning.tuning_key(self.H, self.W, self.opts.precision, self.opts.system,
+                                torch.cuda.get_device_name())
+        hit = tuning.cache_get(cache, key) if cache else None
+        if hit is not None:
+            self.set_tiles(*hit)
+            return {"tiles": self.tiles, "ms": None, "cached": True}
+        ms = (ctypes.c_float * 8)()
+        check(lib().irls_plan_autotune(self.handle, ms, _stream(stream)), "irls_plan_autotune")
+        tiles = self.tiles
+        if cache:
+            tuning.cache_put(cache, key, tiles, list(ms))
+        return {"tiles": tiles, "ms": list(ms), "cached": False}
+
     def set_opts(self, **kw):
         o = Opts.from_buffer_copy(self.opts)
         for k, v in kw.items():
@@ -214,6 +247,36 @@ class Batch:
     def folded(self):
         """True when the batch's preconditioner runs in the folded (even / odd) form."""
         return lib().irls_batch_dct_form(self._h) == DCT_FORMS["folded"]
+
+    @property
+    def tiles(self):
+        """(direction, update) image rows per block of the batched CG stencil launches."""
+        d, u = ctypes.c_int(), ctypes.c_int()
+        check(lib().irls_batch_get_tiles(self._h, ctypes.byref(d), ctypes.byref(u)),
+              "irls_batch_get_tiles")
+        return d.value, u.value
+
+    def set_tiles(self, dir_rows=0, upd_rows=0):
+        """Sets the stencil tile shapes (one of 8, 16, 24, 32; 0 keeps the current value)."""
+        check(lib().irls_batch_set_tiles(self._h, int(dir_rows), int(upd_rows)),
+              "irls_batch_set_tiles")
+
+    def autotune(self, cache=None, stream=None):
+        """As Plan.autotune, for the batch's launches; the cache key holds the batch's shapes."""
+        from . import tuning
+        torch = _torch()
+        key = tuning.batch_key(self.shapes, self.opts.precision, self.opts.system,
+                               torch.cuda.get_device_name())
+        hit = tuning.cache_get(cache, key) if cache else None
+        if hit is not None:
+            self.set_tiles(*hit)
+            return {"tiles": self.tiles, "ms": None, "cached": True}
+        ms = (ctypes.c_float * 8)()
+        check(lib().irls_batch_autotune(self._h, ms, _stream(stream)), "irls_batch_autotune")
+        tiles = self.tiles
+        if cache:
+            tuning.cache_put(cache, key, tiles, list(ms))
+        return {"tiles": tiles, "ms": list(ms), "cached": False}
 
     def unwrap(self, Xs, cohs=None, outs=None, stream=None):
         """Xs, cohs: lists of contiguous float32 CUDA tensors; returns (list of U, list of stats)."""

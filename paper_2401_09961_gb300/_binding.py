@@ -88,6 +88,9 @@ SIGNATURES = {
     "irls_plan_destroy": (_I, [_P]),
     "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
     "irls_plan_dct_form": (_I, [_P]),
+    "irls_plan_set_tiles": (_I, [_P, _I, _I]),
+    "irls_plan_get_tiles": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "irls_plan_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
     "irls_round_congruent": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "irls_best_shift_error": (_I, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), _P]),
@@ -107,6 +110,9 @@ SIGNATURES = {
                                  ctypes.POINTER(Stats), _P]),
     "irls_batch_uses_graphs": (_I, [_P]),
     "irls_batch_dct_form": (_I, [_P]),
+    "irls_batch_set_tiles": (_I, [_P, _I, _I]),
+    "irls_batch_get_tiles": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "irls_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),

@@ -176,6 +176,7 @@ struct irls_plan_s {
     double* h_pair = nullptr;  // pinned, 2 doubles: H_delta values read by the Sec. 4.3 rule
     std::vector<int> caps;     // cap of each inner solve of the last run
     int schedule_stop = 0;
+    int dir_rows = 0, upd_rows = 0;   // stencil tile shapes (0: the defaults)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profiler prof;
 };
@@ -216,6 +217,8 @@ StencilArgs make_args(const irls_plan_s* p) {
     // columns), so the stencil kernels emit none
     if (p->opts.precision == IRLS_PREC_BF16X3 && p->dct.fold) a.r16 = a.r16lo = nullptr;
     a.ld16 = p->dct.Wp;
+    a.dir_rows = p->dir_rows ? p->dir_rows : kDefaultDirRows;
+    a.upd_rows = p->upd_rows ? p->upd_rows : kDefaultUpdRows;
     return a;
 }
 
@@ -429,6 +432,7 @@ struct irls_batch_s {
     TileRec* d_recs = nullptr;
     DevState* states = nullptr;
     int total_strip = 0, total_vec = 0, total_upd = 0;
+    int dir_rows = kDefaultDirRows, upd_rows = kDefaultUpdRows;   // stencil tile shapes
     BatchDctPlan dct;
     int* d_count = nullptr;          // device, 2 slots
     int* h_count = nullptr;          // pinned, 2 slots
@@ -460,11 +464,37 @@ void destroy_batch(irls_batch_s* b) {
     delete b;
 }
 
+// Each image's blocks in the batched direction and update launches for the batch's tile shapes
+// (host records; uploaded with the image pointers at the start of every run).
+void layout_vec_blocks(irls_batch_s* b) {
+    int vblk = 0, ublk = 0;
+    for (int t = 0; t < b->T; ++t) {
+        TileRec& r = b->recs[t];
+        vec_dims(b->H[t], b->W[t], b->dir_rows, b->upd_rows, r.vgx, r.vgy, r.ugy);
+        r.vblk0 = vblk;
+        r.ublk0 = ublk;
+        vblk += r.vgx * r.vgy;
+        ublk += r.vgx * r.ugy;
+    }
+    b->total_vec = vblk;
+    b->total_upd = ublk;
+}
+
+// The CG chunk graphs bake in the launches' grids and kernels: captured again on the next run.
+void drop_graphs(irls_batch_s* b) {
+    for (auto& g : b->chunk)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->graphs_tried = false;
+}
+
 // one chunk of n batched CG iterations followed by the count of images still iterating
 void issue_chunk(irls_batch_s* b, int n, int slot, cudaStream_t s) {
     for (int c = 0; c < n; ++c) {
-        ck(launch_direction_batched(b->d_recs, b->T, b->total_vec, s));
-        ck(launch_update_batched(b->d_recs, b->T, b->total_upd, s));
+        ck(launch_direction_batched(b->d_recs, b->T, b->total_vec, b->dir_rows, s));
+        ck(launch_update_batched(b->d_recs, b->T, b->total_upd, b->upd_rows, s));
         ck(batch_dct_apply(b->dct, s));
     }
     ck(launch_count_active(b->states, b->T, b->d_count + slot, s));
@@ -672,6 +702,79 @@ int irls_plan_dct_form(irls_plan p) {
     if (!p) return IRLS_ERR_ARG;
     if (p->opts.precision == IRLS_PREC_FP32) return IRLS_DCT_AUTO;
     return p->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
+}
+
+int irls_plan_set_tiles(irls_plan p, int dir_rows, int upd_rows) {
+    if (!p) return IRLS_ERR_ARG;
+    if ((dir_rows != 0 && !tile_rows_ok(dir_rows)) || (upd_rows != 0 && !tile_rows_ok(upd_rows)))
+        return IRLS_ERR_ARG;
+    if (dir_rows) p->dir_rows = dir_rows;
+    if (upd_rows) p->upd_rows = upd_rows;
+    return IRLS_OK;
+}
+
+int irls_plan_get_tiles(irls_plan p, int* dir_rows, int* upd_rows) {
+    if (!p || !dir_rows || !upd_rows) return IRLS_ERR_ARG;
+    const StencilArgs a = make_args(p);
+    *dir_rows = a.dir_rows;
+    *upd_rows = a.upd_rows;
+    return IRLS_OK;
+}
+
+int irls_plan_autotune(irls_plan p, float* h_ms, void* stream) {
+    if (!p) return IRLS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = IRLS_OK;
+    try {
+        DeviceGuard g(p->dev);
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        StencilArgs a = make_args(p);
+        // a run that never stops on its own: the kernels do their full traffic every launch
+        a.cg_max = 1 << 30;
+        a.tol2 = -1.0;
+        a.cap_warn = 0;
+        constexpr int kWarm = 2, kReps = 10;
+        float ms[2][4];
+        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < 4; ++i) {
+                StencilArgs b = a;
+                if (k == 0) b.dir_rows = kTileRows[i];
+                else b.upd_rows = kTileRows[i];
+                float tot = 0.f;
+                for (int r = 0; r < kWarm + kReps; ++r) {
+                    // a fresh state per launch (a stopped run's kernels return at once)
+                    ck(cudaMemsetAsync(p->st, 0, sizeof(DevState), s));
+                    ck(cudaEventRecord(e0, s));
+                    if (k == 0) ck(launch_direction_pap(p->P, b, p->st, p->partials, s));
+                    else ck(launch_update(p->P, b, p->st, p->partials, s));
+                    ck(cudaEventRecord(e1, s));
+                    ck(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    ck(cudaEventElapsedTime(&t, e0, e1));
+                    if (r >= kWarm) tot += t;
+                }
+                ms[k][i] = tot / kReps;
+            }
+        int bd = 0, bu = 0;
+        for (int i = 1; i < 4; ++i) {
+            if (ms[0][i] < ms[0][bd]) bd = i;
+            if (ms[1][i] < ms[1][bu]) bu = i;
+        }
+        p->dir_rows = kTileRows[bd];
+        p->upd_rows = kTileRows[bu];
+        if (h_ms)
+            for (int k = 0; k < 2; ++k)
+                for (int i = 0; i < 4; ++i) h_ms[4 * k + i] = ms[k][i];
+        ck(cudaMemsetAsync(p->st, 0, sizeof(DevState), s));
+        ck(cudaStreamSynchronize(s));
+    } catch (Fail&) {
+        rc = IRLS_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
 }
 
 int irls_plan_destroy(irls_plan p) {
@@ -941,17 +1044,11 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
                 a.ld16 = b->dct.ld16[t];
             }
             strip_dims(H[t], W[t], r.sgx, r.sgy);
-            vec_dims(H[t], W[t], r.vgx, r.vgy, r.ugy);
             r.sblk0 = sblk;
-            r.vblk0 = vblk;
-            r.ublk0 = ublk;
             sblk += r.sgx * r.sgy;
-            vblk += r.vgx * r.vgy;
-            ublk += r.vgx * r.ugy;
         }
         b->total_strip = sblk;
-        b->total_vec = vblk;
-        b->total_upd = ublk;
+        layout_vec_blocks(b);
         ck(cudaMemcpy(b->d_recs, b->recs.data(), (size_t)T * sizeof(TileRec), cudaMemcpyHostToDevice));
         ck(cudaHostAlloc(&b->h_count, 2 * sizeof(int), cudaHostAllocDefault));
         for (auto& e : b->ev) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -974,6 +1071,96 @@ int irls_batch_destroy(irls_batch b) {
 int irls_batch_dct_form(irls_batch b) {
     if (!b) return IRLS_ERR_ARG;
     return b->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
+}
+
+int irls_batch_set_tiles(irls_batch b, int dir_rows, int upd_rows) {
+    if (!b) return IRLS_ERR_ARG;
+    if ((dir_rows != 0 && !tile_rows_ok(dir_rows)) || (upd_rows != 0 && !tile_rows_ok(upd_rows)))
+        return IRLS_ERR_ARG;
+    const int d = dir_rows ? dir_rows : b->dir_rows, u = upd_rows ? upd_rows : b->upd_rows;
+    if (d == b->dir_rows && u == b->upd_rows) return IRLS_OK;
+    try {
+        DeviceGuard g(b->dev);
+        ck(cudaStreamSynchronize(b->stream));
+        b->dir_rows = d;
+        b->upd_rows = u;
+        layout_vec_blocks(b);
+        ck(cudaMemcpy(b->d_recs, b->recs.data(), (size_t)b->T * sizeof(TileRec),
+                      cudaMemcpyHostToDevice));
+        drop_graphs(b);
+    } catch (Fail&) {
+        return IRLS_ERR_CUDA;
+    }
+    return IRLS_OK;
+}
+
+int irls_batch_get_tiles(irls_batch b, int* dir_rows, int* upd_rows) {
+    if (!b || !dir_rows || !upd_rows) return IRLS_ERR_ARG;
+    *dir_rows = b->dir_rows;
+    *upd_rows = b->upd_rows;
+    return IRLS_OK;
+}
+
+int irls_batch_autotune(irls_batch b, float* h_ms, void* stream) {
+    if (!b) return IRLS_ERR_ARG;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = IRLS_OK;
+    try {
+        DeviceGuard g(b->dev);
+        cudaStream_t s = b->stream;
+        ck(cudaEventRecord(b->join, static_cast<cudaStream_t>(stream)));
+        ck(cudaStreamWaitEvent(s, b->join, 0));
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        constexpr int kWarm = 2, kReps = 10;
+        float ms[2][4];
+        const int d0 = b->dir_rows, u0 = b->upd_rows;
+        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < 4; ++i) {
+                b->dir_rows = k == 0 ? kTileRows[i] : d0;
+                b->upd_rows = k == 1 ? kTileRows[i] : u0;
+                layout_vec_blocks(b);
+                ck(cudaMemcpyAsync(b->d_recs, b->recs.data(), (size_t)b->T * sizeof(TileRec),
+                                   cudaMemcpyHostToDevice, s));
+                float tot = 0.f;
+                for (int r = 0; r < kWarm + kReps; ++r) {
+                    // fresh states per launch (a stopped image's blocks return at once)
+                    ck(cudaMemsetAsync(b->states, 0, (size_t)b->T * sizeof(DevState), s));
+                    ck(cudaEventRecord(e0, s));
+                    if (k == 0)
+                        ck(launch_direction_batched(b->d_recs, b->T, b->total_vec, b->dir_rows, s));
+                    else
+                        ck(launch_update_batched(b->d_recs, b->T, b->total_upd, b->upd_rows, s));
+                    ck(cudaEventRecord(e1, s));
+                    ck(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    ck(cudaEventElapsedTime(&t, e0, e1));
+                    if (r >= kWarm) tot += t;
+                }
+                ms[k][i] = tot / kReps;
+            }
+        int bd = 0, bu = 0;
+        for (int i = 1; i < 4; ++i) {
+            if (ms[0][i] < ms[0][bd]) bd = i;
+            if (ms[1][i] < ms[1][bu]) bu = i;
+        }
+        b->dir_rows = kTileRows[bd];
+        b->upd_rows = kTileRows[bu];
+        layout_vec_blocks(b);
+        ck(cudaMemcpyAsync(b->d_recs, b->recs.data(), (size_t)b->T * sizeof(TileRec),
+                           cudaMemcpyHostToDevice, s));
+        ck(cudaMemsetAsync(b->states, 0, (size_t)b->T * sizeof(DevState), s));
+        ck(cudaStreamSynchronize(s));
+        drop_graphs(b);
+        if (h_ms)
+            for (int k = 0; k < 2; ++k)
+                for (int i = 0; i < 4; ++i) h_ms[4 * k + i] = ms[k][i];
+    } catch (Fail&) {
+        rc = IRLS_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
 }
 
 int irls_batch_uses_graphs(irls_batch b) {

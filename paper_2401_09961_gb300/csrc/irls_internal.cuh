@@ -82,7 +82,16 @@ struct StencilArgs {
     void* r16lo;        // same shape or nullptr: bf16(r_U - bf16(r_U)) for split precision
     int ld16;
     int prec;           // IRLS_PREC_*
+    // image rows per block of the CG direction and update kernels (single-image launches; one of
+    // kTileRows), set per plan by irls_plan_set_tiles / irls_plan_autotune
+    int dir_rows, upd_rows;
 };
+
+// Image rows per block the CG direction and update kernels are built for, and the defaults
+// (measured fastest at 4096 x 4096).
+constexpr int kTileRows[4] = {8, 16, 24, 32};
+constexpr int kDefaultDirRows = 24, kDefaultUpdRows = 32;
+inline bool tile_rows_ok(int r) { return r == 8 || r == 16 || r == 24 || r == 32; }
 
 // DCT-preconditioner resources owned by a plan.
 struct DctPlan {
@@ -188,12 +197,14 @@ cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float*
 // batched launches over a device array of TileRec (one launch for all images; images whose CG
 // run has stopped return at once)
 void strip_dims(int H, int W, int& gx, int& gy);
-void vec_dims(int H, int W, int& gx, int& gy_dir, int& gy_upd);
+void vec_dims(int H, int W, int dir_rows, int upd_rows, int& gx, int& gy_dir, int& gy_upd);
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
-cudaError_t launch_direction_batched(const TileRec* recs, int T, int total_vec, cudaStream_t s);
-cudaError_t launch_update_batched(const TileRec* recs, int T, int total_vec, cudaStream_t s);
+cudaError_t launch_direction_batched(const TileRec* recs, int T, int total_vec, int rows,
+                                     cudaStream_t s);
+cudaError_t launch_update_batched(const TileRec* recs, int T, int total_upd, int rows,
+                                  cudaStream_t s);
 cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStream_t s);
 

@@ -233,8 +233,8 @@ k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
 constexpr int kVec = 4;
 // rows per block of the float4-lane kernels, measured at 4096 x 4096 (16, 24 and 32 tried):
 // direction 24, update 32; the U-only kernels 24
-constexpr int kDirRows = 24;
-constexpr int kUpdRows = 32;
+constexpr int kDirRows = kDefaultDirRows;
+constexpr int kUpdRows = kDefaultUpdRows;
 constexpr int kSchurRows = 24;
 
 __device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4]) {
@@ -1219,11 +1219,11 @@ void strip_dims(int H, int W, int& gx, int& gy) {
     gy = (int)g.y;
 }
 
-void vec_dims(int H, int W, int& gx, int& gy_dir, int& gy_upd) {
-    dim3 g = vec_grid(H, W, kDirRows);
+void vec_dims(int H, int W, int dir_rows, int upd_rows, int& gx, int& gy_dir, int& gy_upd) {
+    dim3 g = vec_grid(H, W, dir_rows);
     gx = (int)g.x;
     gy_dir = (int)g.y;
-    gy_upd = (int)vec_grid(H, W, kUpdRows).y;
+    gy_upd = (int)vec_grid(H, W, upd_rows).y;
 }
 
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
@@ -1241,13 +1241,27 @@ cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_direction_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_direction<kDirRows><<<total, kThreads, 0, s>>>(recs, T);
+cudaError_t launch_direction_batched(const TileRec* recs, int T, int total, int rows,
+                                     cudaStream_t s) {
+    switch (rows) {
+        case 8: kb_direction<8><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 16: kb_direction<16><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 24: kb_direction<24><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 32: kb_direction<32><<<total, kThreads, 0, s>>>(recs, T); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_update<kUpdRows><<<total, kThreads, 0, s>>>(recs, T);
+cudaError_t launch_update_batched(const TileRec* recs, int T, int total, int rows,
+                                  cudaStream_t s) {
+    switch (rows) {
+        case 8: kb_update<8><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 16: kb_update<16><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 24: kb_update<24><<<total, kThreads, 0, s>>>(recs, T); break;
+        case 32: kb_update<32><<<total, kThreads, 0, s>>>(recs, T); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -1265,9 +1279,44 @@ cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStr
 }
 
 int stencil_grid_blocks(int H, int W) {
-    dim3 g = strip_grid(H, W), v = vec_grid(H, W, std::min({kDirRows, kUpdRows, kSchurRows}));
+    dim3 g = strip_grid(H, W), v = vec_grid(H, W, std::min({kDirRows, kUpdRows, kSchurRows,
+                                                           kTileRows[0]}));
     return (int)std::max(g.x * g.y, v.x * v.y);
 }
+
+namespace {
+
+// The direction and update kernels for a runtime row count (one of kTileRows; the defaults
+// otherwise).
+template <template <int> class K, typename... Args>
+cudaError_t launch_rows(int rows, int H, int W, cudaStream_t s, Args... args) {
+    switch (rows) {
+        case 8: K<8>::go(vec_grid(H, W, 8), s, args...); break;
+        case 16: K<16>::go(vec_grid(H, W, 16), s, args...); break;
+        case 24: K<24>::go(vec_grid(H, W, 24), s, args...); break;
+        case 32: K<32>::go(vec_grid(H, W, 32), s, args...); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int R>
+struct DirK {
+    static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
+        k_direction_pap<R><<<g, kThreads, 0, s>>>(P, a, st, pa);
+    }
+};
+
+template <int R>
+struct UpdK {
+    static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
+        k_update<R><<<g, kThreads, 0, s>>>(P, a, st, pa);
+    }
+};
+
+int rows_or(int r, int dflt) { return tile_rows_ok(r) ? r : dflt; }
+
+}  // namespace
 
 cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, const float* Ch_in,
                         const float* U0, const float* Vv0, const float* Vh0, const Planes& P,
@@ -1291,14 +1340,12 @@ cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevS
 
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
                                  double* partials, cudaStream_t s) {
-    k_direction_pap<kDirRows><<<vec_grid(a.H, a.W, kDirRows), kThreads, 0, s>>>(P, a, st, partials);
-    return cudaGetLastError();
+    return launch_rows<DirK>(rows_or(a.dir_rows, kDirRows), a.H, a.W, s, P, a, st, partials);
 }
 
 cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                           cudaStream_t s) {
-    k_update<kUpdRows><<<vec_grid(a.H, a.W, kUpdRows), kThreads, 0, s>>>(P, a, st, partials);
-    return cudaGetLastError();
+    return launch_rows<UpdK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st, partials);
 }
 
 cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
@@ -1409,8 +1456,7 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
     b.r16lo = nullptr;
     b.cg_max = 1 << 30;
     b.tol2 = -1.0;
-    k_update<kUpdRows><<<vec_grid(a.H, a.W, kUpdRows), kThreads, 0, s>>>(P, b, st, partials);
-    return cudaGetLastError();
+    return launch_update(P, b, st, partials, s);
 }
 
 }  // namespace irls
