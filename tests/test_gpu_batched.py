@@ -103,7 +103,7 @@ FOLD_SHAPES = [(256, 256), (258, 300), (512, 384), (384, 768), (256, 256), (1024
 
 
 def test_batched_folded_equals_single_image_path(irls):
-    """Folded preconditioner over all images in four launches: per image the same tiles, the same
+    """Folded preconditioner over all images in one fused launch: per image the same tiles, the same
     per-tile r^T z slots and the same reduction order as a plan of its own, so bit-identical."""
     tiles = [synthetic.config_2048(seed=300 + t, H=h, W=w) for t, (h, w) in enumerate(FOLD_SHAPES)]
     Xs = [cuda(d["X"]) for d in tiles]
