@@ -146,6 +146,28 @@ def extrapolated_oracle_rate(n, t_setup, t_outer, t_iter, cg_total, outer=OUTER,
 
 
 # ------------------------------------------------------------------------------------------
+def rank_max(x, world, device="cuda"):
+    """x maximised over the ranks of the process group (the slowest rank's time); x at N = 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_sum(x, world, device="cuda"):
+    """x summed over the ranks (the units every rank processed); x at N = 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -239,13 +261,11 @@ def main():
     prof_n = (ctypes.c_longlong * 6)()
     L.irls_plan_profile(plan.handle, prof_ms, prof_n, 6)
     L.irls_plan_set_profiling(plan.handle, 0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(ms, world)
     ms_step = ms / args.steps
     mpix_step = n * wd / 1e6
-    value = world * mpix_step * args.steps / (ms / 1e3)
+    # every rank unwraps its own n x wd image: the whole job's pixels over the slowest rank's time
+    value = rank_sum(mpix_step, world) * args.steps / (ms / 1e3)
 
     # ---- roofline of the dominant kernel class ----
     peaks, peak_src = load_peaks()
@@ -323,11 +343,8 @@ def main():
             Uh = irls.unwrap(Xh, Ch, plan=plan)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * mpix_step * args.steps / t_e2e, "unit": "Mpix/s",
+        t_e2e = rank_max(t_e2e, world)
+        e2e = {"value": rank_sum(mpix_step, world) * args.steps / t_e2e, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
                "d2h_bytes_per_step": int(Uh.numel() * 4)}
 
@@ -386,9 +403,12 @@ def batched_arm(args, rank, world, local):
     """64 uneven tiles (sides from {256, ..., 1536}, tile t seeded 1000 + t) unwrapped together:
     one step = one batched solve of all tiles, 20 outer steps each, split-bf16 preconditioner."""
     import torch
+    import torch.distributed as dist
     import paper_2401_09961_gb300 as irls
     import synthetic
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     tiles = synthetic.batched_tiles(n=64, seed_base=1000 + 64 * rank)
     shapes = [d["X"].shape for d in tiles]
     Xs = [torch.as_tensor(d["X"]).cuda() for d in tiles]
@@ -404,6 +424,9 @@ def batched_arm(args, rank, world, local):
         b.unwrap(Xs, Cs)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks.start()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -413,8 +436,12 @@ def batched_arm(args, rank, world, local):
         _, st = b.unwrap(Xs, Cs)
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    # each rank solves its own 64 tiles (its own seeds, so its own pixel count)
+    ms = rank_max(e0.elapsed_time(e1), world) / args.steps
+    mpix_all = rank_sum(mpix, world)
     # the same tiles one at a time through single-image plans, for comparison
     t_single = 0.0
     if not args.no_e2e:
@@ -431,11 +458,11 @@ def batched_arm(args, rank, world, local):
     if rank == 0:
         out = {
             "metric": "Mpix/s per batched IRLS unwrap of 64 uneven tiles",
-            "value": world * mpix / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world,
+            "value": mpix_all / (ms / 1e3), "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": f"f32+{prec}-tensor-core-dct", "data": "synthetic",
-            "config": {"workload": f"64 tiles, sides in {{256,...,1536}} (non-square), "
+            "config": {"workload": f"64 tiles per rank, sides in {{256,...,1536}} (non-square), "
                                    f"{mpix:.1f} Mpix total, {args.outer} IRLS iterations, "
                                    f"delta {DELTA:g}, tau {TAU:g}, cg_tol {CG_TOL:g}, {prec}",
                        "cg_iters_total": sum(x["cg_total"] for x in st),
@@ -449,6 +476,8 @@ def batched_arm(args, rank, world, local):
         }
         print(json.dumps(out))
     b.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def reference_arm(args, rank, world, n, prec):
