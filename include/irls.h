@@ -164,6 +164,15 @@ int irls_plan_dct_form(irls_plan plan);
  * its backward sweep.  Synchronous with respect to the host.  The batched form keeps
  * the defaults.  No counterpart in the paper (an implementation choice of this library). */
 int irls_plan_set_tiles(irls_plan plan, int dir_rows, int upd_rows);
+
+/* Test hook for failure detection: with on = 1, every stage-2 tile of the plan's folded
+ * preconditioner launch waits for a row panel count one higher than the panel ever reaches.
+ * Each such wait gives up after its bounded budget (about 2 s); the launch then finishes with
+ * every image's state marked IRLS_ERR_TIMEOUT and stopped, its tensor memory freed, and the
+ * context usable; a solve returns IRLS_ERR_TIMEOUT.  on = 0 restores the normal tables (the
+ * next solve is unaffected).  IRLS_ERR_UNSUPPORTED when the plan does not run the folded form.
+ * Not for production use. */
+int irls_debug_stall_fold(irls_plan plan, int on);
 int irls_plan_get_tiles(irls_plan plan, int* dir_rows, int* upd_rows);
 int irls_plan_autotune(irls_plan plan, float* h_ms, void* stream);
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "irls_plan_set_opts": (_I, [_P, ctypes.POINTER(Opts)]),
     "irls_plan_dct_form": (_I, [_P]),
     "irls_plan_set_tiles": (_I, [_P, _I, _I]),
+    "irls_debug_stall_fold": (_I, [_P, _I]),
     "irls_plan_get_tiles": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "irls_plan_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
     "irls_round_congruent": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),

@@ -26,6 +26,7 @@ size_t umma_dct_bytes(int H, int W, int split);
 cudaError_t umma_dct_setup(DctPlan& d, char* mem);
 void umma_dct_release(DctPlan& d);
 cudaError_t umma_dct_reset(const DctPlan& d, cudaStream_t s);
+bool umma_dct_stall(DctPlan& d, int on);
 
 namespace {
 
@@ -247,6 +248,7 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) 
 
 void dct_release(DctPlan& d) { umma_dct_release(d); }
 cudaError_t dct_reset(const DctPlan& d, cudaStream_t s) { return umma_dct_reset(d, s); }
+bool dct_stall(DctPlan& d, int on) { return umma_dct_stall(d, on); }
 
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,

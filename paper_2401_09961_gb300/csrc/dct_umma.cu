@@ -1807,9 +1807,11 @@ void carve_fused(FusedDev& fd, int n_img, int items, int ctrs, Take take) {
 // table and the work list, stage after stage.  Stage-2 tiles of an image stay consecutive (its
 // r^T z run flags assume that); stage-4 tiles of an image are ordered by the last stage-3 panel
 // they read.  `pairs` is the launch's pair count (the static item -> pair assignment).
+// `stall` (a test hook): every stage-2 tile waits for one count more than its panel reaches, so
+// that the bounded wait runs out and the launch ends with the timeout status.
 bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& Hs,
                  int pairs, int reduce_rho, std::vector<GemmTile>& probs,
-                 std::vector<FoldItem>& items, int& n_ctr) {
+                 std::vector<FoldItem>& items, int& n_ctr, int stall = 0) {
     const int n_img = (int)Hs.size();
     if ((int)tab[0].size() != 2 * n_img || (int)tab[1].size() != 4 * n_img ||
         (int)tab[2].size() != 2 * n_img || (int)tab[3].size() != n_img)
@@ -1867,7 +1869,7 @@ bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& 
                 f.sig = c2[i] + q * mbs[i] + l / g.gx;
                 f.ndep = 1;
                 f.dep[0] = c1[i] + x * mbs[i] + l / g.gx;
-                f.need[0] = need;
+                f.need[0] = need + (stall ? 1 : 0);
                 items.push_back(f);
             }
         }
@@ -2040,6 +2042,7 @@ struct FoldBufs {
     double* partials = nullptr;
     float tau = 0.f;
     int rho = -1;                  // r^T z formed in stage 2 (the tables' stage-2 epilogue)
+    int stall = 0;                 // test hook: stage-2 waits that run out (see build_fused)
     int n_sm = 0;                  // SMs of the device
     FusedDev fused;
 };
@@ -2101,7 +2104,8 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
     std::vector<GemmTile> probs;
     std::vector<FoldItem> items;
     int n_ctr = 0;
-    if (!build_fused(f.tab, std::vector<int>{d.H}, f.fused.pairs, rho, probs, items, n_ctr))
+    if (!build_fused(f.tab, std::vector<int>{d.H}, f.fused.pairs, rho, probs, items, n_ctr,
+                     f.stall))
         return cudaErrorInvalidValue;
     cudaError_t e = upload_fused(f.fused, probs, items, n_ctr, s);
     if (e != cudaSuccess) return e;
@@ -2135,6 +2139,16 @@ cudaError_t umma_dct_reset(const DctPlan& d, cudaStream_t s) {
     if (!d.fold_host) return cudaSuccess;
     const FusedDev& fd = static_cast<const FoldBufs*>(d.fold_host)->fused;
     return cudaMemsetAsync(fd.ctr, 0, (size_t)(fd.n_ctr + 1) * 4, s);
+}
+
+// Test hook: the folded launch's stage-2 waits run out (on) or not (off); false without a
+// folded form.
+bool umma_dct_stall(DctPlan& d, int on) {
+    if (!d.fold_host || !d.fold) return false;
+    FoldBufs& f = *static_cast<FoldBufs*>(d.fold_host);
+    f.stall = on ? 1 : 0;
+    f.bound = false;   // the tables are rebuilt on the next application
+    return true;
 }
 
 void umma_dct_release(DctPlan& d) {

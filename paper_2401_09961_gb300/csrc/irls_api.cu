@@ -704,6 +704,11 @@ int irls_plan_dct_form(irls_plan p) {
     return p->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
 }
 
+int irls_debug_stall_fold(irls_plan p, int on) {
+    if (!p) return IRLS_ERR_ARG;
+    return dct_stall(p->dct, on) ? IRLS_OK : IRLS_ERR_UNSUPPORTED;
+}
+
 int irls_plan_set_tiles(irls_plan p, int dir_rows, int upd_rows) {
     if (!p) return IRLS_ERR_ARG;
     if ((dir_rows != 0 && !tile_rows_ok(dir_rows)) || (upd_rows != 0 && !tile_rows_ok(upd_rows)))

@@ -217,6 +217,8 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem);
 void dct_release(DctPlan& d);
 // zeroes the folded form's launch counters (recovery after a launch that timed out)
 cudaError_t dct_reset(const DctPlan& d, cudaStream_t s);
+// test hook: the folded launch's dependency waits run out (IRLS_ERR_TIMEOUT path)
+bool dct_stall(DctPlan& d, int on);
 cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
                                   double* partials, cudaStream_t s);
 cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
