@@ -277,8 +277,10 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
 #pragma unroll
     for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
 
-    // direction at (row, j0..j0+3): U part only, or all three parts with the diagonals
-    auto dir_u = [&](size_t o, float (&pu)[4]) {
+    // direction at (row, j0..j0+3): U part only, or all three parts with the diagonals; lane 31
+    // also forms the U part at column j0 + 4 (the next warp's first column: its right neighbour),
+    // loaded with the rest of the row two rows ahead of its use
+    auto dir_u = [&](size_t o, float (&pu)[4], float& rh) {
         float z[4];
         ld4(zU + o, z);
         if (fresh) {
@@ -289,6 +291,11 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
             ld4(pUo + o, q);
 #pragma unroll
             for (int e = 0; e < 4; ++e) pu[e] = z[e] + beta * q[e];
+        }
+        rh = 0.f;
+        if (lane == 31 && j0 + kVec < W) {
+            const float zr = zU[o + kVec];
+            rh = fresh ? zr : zr + beta * pUo[o + kVec];
         }
     };
     auto dir_v = [&](size_t o, float (&pvv)[4], float (&pvh)[4], float (&dv)[4], float (&dh)[4]) {
@@ -312,12 +319,13 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
     float cdv[4] = {0, 0, 0, 0}, cdh[4] = {0, 0, 0, 0};
     float nu[4] = {0, 0, 0, 0}, nvv[4] = {0, 0, 0, 0}, nvh[4] = {0, 0, 0, 0};
     float ndv[4] = {0, 0, 0, 0}, ndh[4] = {0, 0, 0, 0};
+    float rcu = 0.f, rnu = 0.f;
     if (act) {
         const size_t o = (size_t)i0 * ld + j0;
-        dir_u(o, cu);
+        dir_u(o, cu, rcu);
         dir_v(o, cvv, cvh, cdv, cdh);
         if (i0 + 1 < H) {
-            dir_u(o + ld, nu);
+            dir_u(o + ld, nu, rnu);
             if (i0 + 1 < i1) dir_v(o + ld, nvv, nvh, ndv, ndh);
         }
     }
@@ -328,18 +336,13 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
         // direction of row i + 2 (its U part closes row i + 1's vertical edges)
         float mu[4] = {0, 0, 0, 0}, mvv[4] = {0, 0, 0, 0}, mvh[4] = {0, 0, 0, 0};
         float mdv[4] = {0, 0, 0, 0}, mdh[4] = {0, 0, 0, 0};
+        float rmu = 0.f;
         if (act && i + 1 < i1 && i + 2 < H) {
-            dir_u(o + 2 * (size_t)ld, mu);
+            dir_u(o + 2 * (size_t)ld, mu, rmu);
             if (i + 2 < i1) dir_v(o + 2 * (size_t)ld, mvv, mvh, mdv, mdh);
         }
         float right = __shfl_down_sync(kFull, cu[0], 1);
-        if (lane == 31) {
-            right = 0.f;
-            if (act && j0 + kVec < W) {
-                float z = zU[o + kVec];
-                right = fresh ? z : z + beta * pUo[o + kVec];
-            }
-        }
+        if (lane == 31) right = rcu;
         if (act) {
             st4(pUn + o, cu); st4(pVvn + o, cvv); st4(pVhn + o, cvh);
             const float pr[4] = {cu[1], cu[2], cu[3], right};
@@ -355,6 +358,8 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
             cu[e] = nu[e]; cvv[e] = nvv[e]; cvh[e] = nvh[e]; cdv[e] = ndv[e]; cdh[e] = ndh[e];
             nu[e] = mu[e]; nvv[e] = mvv[e]; nvh[e] = mvh[e]; ndv[e] = mdv[e]; ndh[e] = mdh[e];
         }
+        rcu = rnu;
+        rnu = rmu;
     }
     double v[1] = {(double)acc}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
