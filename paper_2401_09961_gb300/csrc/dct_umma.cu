@@ -705,6 +705,7 @@ struct GemmTile {
     int mirror_b1;                // second set's B rows mirrored: nb_rows - n0 - 128
     int nb_rows;
     int epi, dual;                // fused folded launch: the problem's epilogue and operand sets
+    CUtensorMap bh0, bh1, bh2, bh3;   // two-set problems: B maps with 64-row boxes (half tiles)
 };
 
 // Grouped GEMM: one launch over the output tiles of every problem (BN = 128).  A CTA finds its
@@ -914,6 +915,7 @@ struct FoldItem {
     int m0, n0;           // first output row (even CTA) and column of the tile
     int nb1;              // first B row the odd CTA stages
     int nkb, dual;        // k-blocks per operand set, operand sets - 1
+    int half;             // a two-set tile of half width (N = 128 per set, one accumulator buffer)
     int epi;
     int sig;              // counter this tile completes (one add per CTA), or -1
     int ndep;
@@ -988,6 +990,8 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
     static_assert(Q2Cfg<1, 256>::kStageBytes == C::kStageBytes, "one ring for both forms");
     constexpr int S = C::kStages;
     constexpr uint32_t kCols = 512, kBuf = 256;
+    // N = 128 per operand set (half-width two-set tiles), otherwise as C::kIdesc
+    constexpr uint32_t kIdescHalf = (C::kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(128 >> 3) << 17);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -1077,10 +1081,12 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         }
                         fence_proxy_async_global();
                     }
-                    const int dual = f.dual;
+                    const int dual = f.dual, half = f.half;
                     const int m0 = f.m0 + 128 * (int)rank;
                     const int nb = rank == 0 ? f.n0 : f.nb1;
                     const int nkb = f.nkb, nkt = dual ? 2 * nkb : nkb;
+                    // a half-width tile stages 64 B rows per CTA instead of 128
+                    const uint32_t tx = half ? 2u * (2 * C::kABytes + C::kBBytes) : 2u * C::kStageBytes;
                     for (int kb = 0; kb < nkt; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -1092,12 +1098,16 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         const int kc = (second ? kb - nkb : kb) * UBK;
                         uint8_t* sa = smem + s * C::kStageBytes;
                         uint8_t* sb = sa + 2 * C::kABytes;
-                        if (rank == 0) mbar_expect_tx(&full[s], 2 * C::kStageBytes);
+                        if (rank == 0) mbar_expect_tx(&full[s], tx);
                         const uint32_t fb = full0 + 8u * (uint32_t)s;
                         tma_load_2d_pair(sa, second ? &g.a2 : &g.a0, fb, kc, m0);
                         tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
-                        tma_load_2d_pair(sb, second ? &g.b2 : &g.b0, fb, kc, nb);
-                        tma_load_2d_pair(sb + C::kBBytes, second ? &g.b3 : &g.b1, fb, kc, nb);
+                        const CUtensorMap* bm0 = half ? (second ? &g.bh2 : &g.bh0)
+                                                      : (second ? &g.b2 : &g.b0);
+                        const CUtensorMap* bm1 = half ? (second ? &g.bh3 : &g.bh1)
+                                                      : (second ? &g.b3 : &g.b1);
+                        tma_load_2d_pair(sb, bm0, fb, kc, nb);
+                        tma_load_2d_pair(sb + C::kBBytes, bm1, fb, kc, nb);
                     }
                     f = fn;
                 }
@@ -1125,9 +1135,12 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         f = fn;
                         continue;
                     }
-                    const int dual = f.dual;
-                    const int b0 = dual ? 0 : nbuf, nbu = dual ? 2 : 1;
-                    if (!dual) nbuf ^= 1;
+                    const int dual = f.dual, half = f.half;
+                    const bool two = dual && !half;   // both accumulator buffers
+                    const int b0 = two ? 0 : nbuf, nbu = two ? 2 : 1;
+                    if (!two) nbuf ^= 1;
+                    const uint32_t idesc = half ? kIdescHalf : C::kIdesc;
+                    const uint32_t set1 = half ? 128u : kBuf;
                     for (int k = 0; k < nbu && !bad; ++k) {
                         const int b = b0 + k;
                         if (use[b] >= 1 &&
@@ -1149,7 +1162,7 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         tc_fence_after();
                         const bool second = dual && kb >= nkb;
                         const int kk = second ? kb - nkb : kb;
-                        const uint32_t td = base + (second ? kBuf : 0u);
+                        const uint32_t td = base + (second ? set1 : 0u);
                         const uint32_t sa = smem_u32(smem + s * C::kStageBytes);
                         const uint32_t sb = sa + 2 * C::kABytes;
                         const uint64_t da = desc_sw128(sa), db = desc_sw128(sb);
@@ -1157,9 +1170,9 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         const uint64_t dbl = desc_sw128(sb + C::kBBytes);
     #pragma unroll
                         for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
-                            umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, C::kIdesc, (kk | q) != 0);
-                            umma_bf16_pair(td, dal + 2 * q, db + 2 * q, C::kIdesc, 1u);
-                            umma_bf16_pair(td, da + 2 * q, db + 2 * q, C::kIdesc, 1u);
+                            umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, idesc, (kk | q) != 0);
+                            umma_bf16_pair(td, dal + 2 * q, db + 2 * q, idesc, 1u);
+                            umma_bf16_pair(td, da + 2 * q, db + 2 * q, idesc, 1u);
                         }
                         umma_commit_pair(&empty[s]);
                     }
@@ -1180,9 +1193,9 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                 const FoldItem& f = items[t];
                 if (!item_live(f, lst, llive)) continue;
                 const GemmTile& g = probs[f.prob];
-                const int dual = f.dual;
-                const int b0 = dual ? 0 : nbuf, nbu = dual ? 2 : 1;
-                if (!dual) nbuf ^= 1;
+                const bool two = f.dual && !f.half;
+                const int b0 = two ? 0 : nbuf, nbu = two ? 2 : 1;
+                if (!two) nbuf ^= 1;
                 int ok = 1;
                 for (int k = 0; k < nbu; ++k) {
                     const int b = b0 + k;
@@ -1204,9 +1217,13 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         fused_epi<256, UE_EIG16_RHO>(tl, ep, m0 + q * 32, n0, part, half, sc);
                         break;
                     case UE_UNFOLD16:
-                        fused_epi<256, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        if (f.half) fused_epi<128, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        else fused_epi<256, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
                         break;
-                    default: fused_epi<256, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
+                    default:
+                        if (f.half) fused_epi<128, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        else fused_epi<256, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        break;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -1661,18 +1678,30 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
     base.flexible = flexible;
     base.skip_if_done = skip;
     int bbox = 128;
+    bool halves = false;   // two-set stages: also B maps with 64-row boxes (half-width tiles)
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a0, A[0], ar, ac, UBM);
         ok &= make_map(&g.a1, A[1], ar, ac, UBM);
         ok &= make_map(&g.b0, Bm[0], br, bc, bbox);
         ok &= make_map(&g.b1, Bm[1], br, bc, bbox);
         g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
+        if (halves) {
+            ok &= make_map(&g.bh0, Bm[0], br, bc, 64);
+            ok &= make_map(&g.bh1, Bm[1], br, bc, 64);
+        } else {
+            g.bh0 = g.b0; g.bh1 = g.b1;
+        }
+        g.bh2 = g.bh0; g.bh3 = g.bh1;
     };
     auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
         ok &= make_map(&g.a2, A[0], ar, ac, UBM);
         ok &= make_map(&g.a3, A[1], ar, ac, UBM);
         ok &= make_map(&g.b2, Bm[0], br, bc, bbox);
         ok &= make_map(&g.b3, Bm[1], br, bc, bbox);
+        if (halves) {
+            ok &= make_map(&g.bh2, Bm[0], br, bc, 64);
+            ok &= make_map(&g.bh3, Bm[1], br, bc, 64);
+        }
     };
     // Every operand is stored padded (extents hNp, hMp, Hp, multiples of 256); padding rows and
     // columns of the bases are zero, and the epilogues mask what lies beyond the half sides.
@@ -1712,6 +1741,7 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
             tab[1].push_back(g);
         }
     bbox = kPairDualN / 2;
+    halves = true;
     // stage 3 (x): with E from the even and O from the odd frequencies along i,
     // T3x[i'][l'] = E + O and T3x[H-1-i'][l'] = E - O (i' < hN)
     for (int x = 0; x < 2; ++x) {
@@ -1774,7 +1804,7 @@ struct FusedDev {
     FoldItem* items = nullptr;
     unsigned* ctr = nullptr;     // n_ctr panel counters and the exit counter
     DevState** sts = nullptr;    // the images' states
-    int n_probs = 0, n_items = 0, n_ctr = 0, n_st = 0, pairs = 0, honour_stop = 1;
+    int n_probs = 0, n_items = 0, cap_items = 0, n_ctr = 0, n_st = 0, pairs = 0, honour_stop = 1;
 };
 
 // Items and panel counters of one image's four stages.
@@ -1785,14 +1815,19 @@ void fused_counts(int H, int W, int& items, int& ctrs) {
     ctrs = 2 * mb + 4 * mb + 2 * nb;
 }
 
+// Work-list capacity: the tiles plus up to kMaxSplit two-set tiles split into halves.
+constexpr int kMaxSplit = 1024;
+
 size_t fused_bytes(int n_img, int items, int ctrs) {
     return rup((size_t)9 * n_img * sizeof(GemmTile), 1024) +
-           rup((size_t)items * sizeof(FoldItem), 1024) + rup((size_t)(ctrs + 1) * 4, 1024) +
+           rup((size_t)(items + kMaxSplit) * sizeof(FoldItem), 1024) +
+           rup((size_t)(ctrs + 1) * 4, 1024) +
            rup((size_t)n_img * sizeof(DevState*), 1024);
 }
 
 template <typename Take>
 void carve_fused(FusedDev& fd, int n_img, int items, int ctrs, Take take) {
+    items += kMaxSplit;
     fd.probs = static_cast<GemmTile*>(take((size_t)9 * n_img * sizeof(GemmTile)));
     fd.items = static_cast<FoldItem*>(take((size_t)items * sizeof(FoldItem)));
     fd.ctr = static_cast<unsigned*>(take((size_t)(ctrs + 1) * 4));
@@ -1800,6 +1835,7 @@ void carve_fused(FusedDev& fd, int n_img, int items, int ctrs, Take take) {
     fd.n_st = n_img;
     fd.n_probs = 9 * n_img;
     fd.n_items = items;
+    fd.cap_items = items;
     fd.n_ctr = ctrs;
 }
 
@@ -1946,6 +1982,45 @@ bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& 
         f.dual = g.dual;
         f.epi = g.epi;
     }
+    // Half-width tail: the last two-set tiles (stage 4, no consumers) may be split into two
+    // N = 128 halves each, so that the last wave fills the pairs that would otherwise idle.  The
+    // count is chosen by the makespan of the static assignment (item t on pair t mod pairs),
+    // counting a tile's k-blocks per operand set, a half tile at 1/0.77 of its size (N = 128 MMAs
+    // ran at ~77 % of the N = 256 rate).  The arithmetic of every output element is unchanged.
+    {
+        int n_tail = 0;   // trailing stage-4 tiles
+        for (int t = (int)items.size() - 1; t >= 0 && items[t].epi == UE_UNFOLDZ; --t) ++n_tail;
+        const int max_split = std::min({n_tail, pairs, kMaxSplit});
+        auto dur = [](const FoldItem& f) { return (double)f.nkb * (f.dual ? 2 : 1); };
+        const int n = (int)items.size();
+        std::vector<double> base(pairs, 0.0);
+        int best_x = 0;
+        double best = 0.0;
+        for (int x = 0; x <= max_split; ++x) {
+            std::fill(base.begin(), base.end(), 0.0);
+            int t = 0;
+            for (int i = 0; i < n - x; ++i, ++t) base[t % pairs] += dur(items[i]);
+            for (int i = n - x; i < n; ++i)
+                for (int h = 0; h < 2; ++h, ++t) base[t % pairs] += items[i].nkb / 0.77;
+            const double mk = *std::max_element(base.begin(), base.end());
+            if (x == 0 || mk < best - 1e-9) {
+                best = mk;
+                best_x = x;
+            }
+        }
+        if (best_x > 0) {
+            std::vector<FoldItem> tail(items.end() - best_x, items.end());
+            items.resize(items.size() - best_x);
+            for (const FoldItem& f : tail)
+                for (int h = 0; h < 2; ++h) {
+                    FoldItem g = f;
+                    g.half = 1;
+                    g.n0 = f.n0 + 128 * h;
+                    g.nb1 = g.n0 + 64;
+                    items.push_back(g);
+                }
+        }
+    }
     // r^T z run flags of stage 2 (item t runs on pair t mod pairs)
     for (int i = 0; i < n_img; ++i) {
         const int a = r2a[i], b = r2b[i];
@@ -1960,8 +2035,9 @@ bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& 
 // Copies the tables; the images' states are the stage-4 problems' (one per image).
 cudaError_t upload_fused(FusedDev& fd, const std::vector<GemmTile>& probs,
                          const std::vector<FoldItem>& items, int n_ctr, cudaStream_t s) {
-    if ((int)probs.size() != fd.n_probs || (int)items.size() != fd.n_items || n_ctr != fd.n_ctr)
+    if ((int)probs.size() != fd.n_probs || (int)items.size() > fd.cap_items || n_ctr != fd.n_ctr)
         return cudaErrorInvalidValue;
+    fd.n_items = (int)items.size();
     std::vector<DevState*> sts;
     fd.honour_stop = 1;
     for (const GemmTile& g : probs) {

@@ -1011,7 +1011,8 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
     bool hh[kVec];
 #pragma unroll
     for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
-    auto dir_u = [&](size_t o, float (&pu)[4]) {
+    // p_U of a row (and, in lane 31, at column j0 + 4: the right neighbour), two rows ahead
+    auto dir_u = [&](size_t o, float (&pu)[4], float& rh) {
         float z[4];
         ld4(zU + o, z);
         if (fresh) {
@@ -1023,31 +1024,35 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) pu[e] = z[e] + beta * q[e];
         }
+        rh = 0.f;
+        if (lane == 31 && j0 + kVec < W) {
+            const float zr = zU[o + kVec];
+            rh = fresh ? zr : zr + beta * pUo[o + kVec];
+        }
     };
     float cu[4] = {0, 0, 0, 0}, nu[4] = {0, 0, 0, 0};
+    float dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0};   // D of the current row, one row ahead
+    float rcu = 0.f, rnu = 0.f;
     if (act) {
         const size_t o = (size_t)i0 * ld + j0;
-        dir_u(o, cu);
-        if (i0 + 1 < H) dir_u(o + ld, nu);
+        dir_u(o, cu, rcu);
+        ld4(Dv + o, dv);
+        ld4(Dh + o, dh);
+        if (i0 + 1 < H) dir_u(o + ld, nu, rnu);
     }
     float acc = 0.f;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
-        float mu[4] = {0, 0, 0, 0}, dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0};
-        if (act) {
-            ld4(Dv + o, dv);
-            ld4(Dh + o, dh);
-            if (i + 1 < i1 && i + 2 < H) dir_u(o + 2 * (size_t)ld, mu);
+        float mu[4] = {0, 0, 0, 0}, ndv[4] = {0, 0, 0, 0}, ndh[4] = {0, 0, 0, 0};
+        float rmu = 0.f;
+        if (act && i + 1 < i1) {
+            ld4(Dv + o + ld, ndv);
+            ld4(Dh + o + ld, ndh);
+            if (i + 2 < H) dir_u(o + 2 * (size_t)ld, mu, rmu);
         }
         float right = __shfl_down_sync(kFull, cu[0], 1);
-        if (lane == 31) {
-            right = 0.f;
-            if (act && j0 + kVec < W) {
-                const float z = zU[o + kVec];
-                right = fresh ? z : z + beta * pUo[o + kVec];
-            }
-        }
+        if (lane == 31) right = rcu;
         if (act) {
             st4(pUn + o, cu);
             const float pr[4] = {cu[1], cu[2], cu[3], right};
@@ -1062,7 +1067,11 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
         for (int e = 0; e < 4; ++e) {
             cu[e] = nu[e];
             nu[e] = mu[e];
+            dv[e] = ndv[e];
+            dh[e] = ndh[e];
         }
+        rcu = rnu;
+        rnu = rmu;
     }
     double v[1] = {(double)acc}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
