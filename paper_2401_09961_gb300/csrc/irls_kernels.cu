@@ -1127,31 +1127,48 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
         if (i0 + 1 < H) ld4(pU + o + ld, nu);
     }
+    // the row's own data and its neighbour halos (lane 31: p_U at column j0 + 4; lane 0: p_U
+    // and D_h at column j0 - 1), loaded one row ahead of their use
+    struct SRow {
+        float dv[4], dh[4], u[4], r0[4], z[4];
+        float rgt, lpu, ldh;
+    };
+    auto load_row = [&](size_t o, SRow& d) {
+        ld4(Dv + o, d.dv);
+        ld4(Dh + o, d.dh);
+        ld4(U + o, d.u);
+        ld4(rU + o, d.r0);
+        if (flex) ld4(Zu + o, d.z);
+        d.rgt = d.lpu = d.ldh = 0.f;
+        if (lane == 31 && j0 + kVec < W) d.rgt = pU[o + kVec];
+        if (lane == 0 && j0 > 0) {
+            d.lpu = pU[o - 1];
+            d.ldh = Dh[o - 1];
+        }
+    };
+    SRow rc;
+    if (act) load_row((size_t)i0 * ld + j0, rc);
     float rr = 0.f, rzo = 0.f, su = 0.f;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
-        float dv[4] = {0, 0, 0, 0}, dh[4] = {0, 0, 0, 0}, u[4] = {0, 0, 0, 0};
-        float r0[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0}, mu[4] = {0, 0, 0, 0};
+        float mu[4] = {0, 0, 0, 0};
+        SRow rn;
         if (act) {
-            ld4(Dv + o, dv);
-            ld4(Dh + o, dh);
-            ld4(U + o, u);
-            ld4(rU + o, r0);
-            if (flex) ld4(Zu + o, z);
+            if (i + 1 < i1) load_row(o + ld, rn);
             if (i + 1 < i1 && i + 2 < H) ld4(pU + o + 2 * (size_t)ld, mu);
         }
+        float (&dv)[4] = rc.dv, (&dh)[4] = rc.dh, (&u)[4] = rc.u, (&r0)[4] = rc.r0, (&z)[4] = rc.z;
         float yv[4], yh[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) yv[e] = hv ? omega_of(dv[e], tau) * (nu[e] - cu[e]) : 0.f;
         float right = __shfl_down_sync(kFull, cu[0], 1);
-        if (lane == 31) right = (act && j0 + kVec < W) ? pU[o + kVec] : 0.f;
+        if (lane == 31) right = rc.rgt;
         const float pr[4] = {cu[1], cu[2], cu[3], right};
 #pragma unroll
         for (int e = 0; e < 4; ++e) yh[e] = hh[e] ? omega_of(dh[e], tau) * (pr[e] - cu[e]) : 0.f;
         float left = __shfl_up_sync(kFull, yh[3], 1);
-        if (lane == 0)
-            left = (act && j0 > 0) ? omega_of(Dh[o - 1], tau) * (cu[0] - pU[o - 1]) : 0.f;
+        if (lane == 0) left = (act && j0 > 0) ? omega_of(rc.ldh, tau) * (cu[0] - rc.lpu) : 0.f;
         const float yl[4] = {left, yh[0], yh[1], yh[2]};
         if (act) {
             float n0[4];
@@ -1179,6 +1196,7 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
             cu[e] = nu[e];
             nu[e] = mu[e];
         }
+        rc = rn;
     }
     double v[3] = {(double)rr, (double)rzo, (double)su}, tot[3];
     if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
