@@ -57,8 +57,9 @@ extern "C" {
 /* Form of the tensor-core preconditioner (split precision only). */
 #define IRLS_DCT_AUTO   0   /* folded where allowed, else direct                                  */
 #define IRLS_DCT_DIRECT 1   /* four full-size products per application                            */
-#define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds; needs
-                             * precision IRLS_PREC_BF16X3 and H, W multiples of 256               */
+#define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds, all four
+                             * stages in one persistent launch; needs precision IRLS_PREC_BF16X3
+                             * and even H, W >= 256                                              */
 
 /* Inner-solve budget (Sec. 4.3). */
 #define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
@@ -197,8 +198,8 @@ int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
 /* Batched solve: ntiles independent images of their own sizes H[t] x W[t] (non-square allowed),
  * each unwrapped as by irls_unwrap_ex with the options `opts`, with one GPU launch per phase of
  * Alg. 1 / Alg. 2 for all images together (the stencil kernels over the union of the images'
- * blocks, the preconditioner as one grouped tensor-core GEMM per DCT stage over all images'
- * tiles).  Each image keeps its own CG scalars and stopping test: an image whose CG run has
+ * blocks, the preconditioner over all images' tiles: one launch for the folded form, one
+ * grouped tensor-core GEMM per DCT stage for the direct form).  Each image keeps its own CG scalars and stopping test: an image whose CG run has
  * stopped drops out of later launches of the same outer step (its blocks return at once).  The
  * inner CG iterations are replayed from CUDA graphs captured once per batch.  Precision must be
  * IRLS_PREC_BF16X3 or IRLS_PREC_BF16 (IRLS_ERR_UNSUPPORTED for IRLS_PREC_FP32).
@@ -208,9 +209,10 @@ int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
  * d_U[t]; per_tile (nullable) receives ntiles statistics.  Synchronous with respect to the host;
  * `stream` is ordered before and after the batch.  irls_unwrap_batched is create + run +
  * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist.
- * Preconditioner form: with dct_form IRLS_DCT_AUTO the batch runs the folded form (four
- * persistent CTA-pair GEMM launches over every image's tiles, plus one fold of r_U) when every
- * image allows it (IRLS_PREC_BF16X3, even sides >= 256), else the direct grouped form;
+ * Preconditioner form: with dct_form IRLS_DCT_AUTO the batch runs the folded form (one
+ * persistent CTA-pair launch over every image's tiles of all four stages, plus one fold of
+ * r_U) when every image allows it (IRLS_PREC_BF16X3, even sides >= 256), else the direct
+ * grouped form;
  * IRLS_DCT_FOLDED where some image does not allow it is IRLS_ERR_UNSUPPORTED.  An image's
  * results do not depend on the batch it runs in: they equal, bit for bit, a single-image plan
  * in the same form.  irls_batch_dct_form returns IRLS_DCT_FOLDED or IRLS_DCT_DIRECT. */
@@ -319,7 +321,7 @@ int irls_precond_laplacian_noalloc(const float* d_R, float* d_Z, int H, int W, f
  * per kernel class; turning it on (or off) clears the totals.  Classes, in order:
  *   0 gradients/weights/||b|| (once per solve)   1 reweight + initial residual (per outer)
  *   2 search direction + p^T A p (per CG iter)    3 CG update x, r (per CG iter)
- *   4 Laplacian preconditioner, all four GEMMs    5 end-of-outer reductions and U -= mean
+ *   4 Laplacian preconditioner (all its launches) 5 end-of-outer reductions and U -= mean
  * irls_plan_profile copies min(n, classes) totals (milliseconds) and launch counts and returns
  * the number of classes (6); launches skipped on the device after CG stopped are counted too. */
 int irls_plan_set_profiling(irls_plan plan, int on);
