@@ -59,7 +59,7 @@ extern "C" {
 #define IRLS_DCT_DIRECT 1   /* four full-size products per application                            */
 #define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds, all four
                              * stages in one persistent launch; needs precision IRLS_PREC_BF16X3
-                             * and even H, W >= 256                                              */
+                             * and H, W >= 256 (odd or even)                                     */
 
 /* Inner-solve budget (Sec. 4.3). */
 #define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
@@ -211,7 +211,7 @@ int irls_unwrap_ex(irls_plan plan, const float* d_X, const float* d_coherence,
  * destroy in one call.  irls_batch_uses_graphs returns 1 once the CG chunk graphs exist.
  * Preconditioner form: with dct_form IRLS_DCT_AUTO the batch runs the folded form (one
  * persistent CTA-pair launch over every image's tiles of all four stages, plus one fold of
- * r_U) when every image allows it (IRLS_PREC_BF16X3, even sides >= 256), else the direct
+ * r_U) when every image allows it (IRLS_PREC_BF16X3, sides >= 256), else the direct
  * grouped form;
  * IRLS_DCT_FOLDED where some image does not allow it is IRLS_ERR_UNSUPPORTED.  An image's
  * results do not depend on the batch it runs in: they equal, bit for bit, a single-image plan

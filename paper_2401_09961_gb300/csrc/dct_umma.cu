@@ -81,6 +81,9 @@ struct UEpiArgs {
     // EIG16_RHO in the CTA-pair kernels: the index of this problem's first tile among its
     // image's tiles, and the image's tile count (its problems are consecutive in the table)
     int rho_base, rho_count;
+    // FOLD16 with an odd number of B rows: the middle row pairs with itself (its sum is the row
+    // itself, not twice it); -1 otherwise
+    int mid;
 };
 
 template <int BN, int SA, int SB>
@@ -492,8 +495,9 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 const float a = __uint_as_float(r[t]), b = __uint_as_float(r1[31 - t]);
                 // columns beyond the half side (padding of a ragged half) are zero
                 const bool ok = nb + t < ep.vn;
-                pl[t] = ok ? a + b : 0.f;
-                mi[t] = ok ? a - b : 0.f;
+                const bool self = nb + t == ep.mid;
+                pl[t] = ok ? (self ? a : a + b) : 0.f;
+                mi[t] = ok && !self ? a - b : 0.f;
             }
             scr_put(s, pl);
             scr_store16(s, ep.C, ep.C_lo, nb, rows);
@@ -1350,7 +1354,11 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
                                __nv_bfloat16* PoT, __nv_bfloat16* Pelo, __nv_bfloat16* Polo,
                                __nv_bfloat16* PeTlo, __nv_bfloat16* PoTlo, float* lamP, int n,
                                int hp) {
-    const int h = n / 2;
+    // spatial half: (n + 1) / 2 rows (for odd n the middle row is its own mirror); frequencies:
+    // (n + 1) / 2 even ones, n / 2 odd ones.  On the middle row every odd-frequency entry is
+    // exactly 0 (P[(n-1)/2][k] = (-1)^k P[(n-1)/2][k]), so the two mirrored writes of that row in
+    // the inverse stages carry the same value.
+    const int hs = (n + 1) / 2;
     const size_t total = (size_t)hp * hp;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
@@ -1358,7 +1366,7 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
         for (int par = 0; par < 2; ++par) {
             const int k = 2 * b + par;
             double v = 0.0;
-            if (a < h && b < h) {
+            if (a < hs && k < n && !(par == 1 && 2 * a + 1 == n)) {
                 const long long mm = ((long long)(2 * a + 1) * k) % (4LL * n);
                 const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
                 v = ck * cospi((double)mm / (2.0 * n));
@@ -1379,7 +1387,7 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
         if (a == 0) {
             for (int par = 0; par < 2; ++par) {
                 double lam = 0.0;
-                if (b < h) {
+                if (2 * b + par < n) {
                     const double sn = sinpi((double)(2 * b + par) / (2.0 * n));
                     lam = 4.0 * sn * sn;
                 }
@@ -1411,14 +1419,18 @@ __device__ __forceinline__ void fold_r_body(const FoldRRec& f, int bid, int nblk
     __nv_bfloat16* __restrict__ Relo = f.Relo;
     __nv_bfloat16* __restrict__ Ro = f.Ro;
     __nv_bfloat16* __restrict__ Rolo = f.Rolo;
-    const int h = W / 2;
     if (W % 8 != 0) {
+        // (W + 1) / 2 columns: for odd W the middle column is its own mirror (sum: the column
+        // itself; difference: 0)
+        const int h = (W + 1) / 2;
         const size_t total = (size_t)H * h;
         for (size_t t = bid * (size_t)blockDim.x + threadIdx.x; t < total;
              t += (size_t)nblk * blockDim.x) {
             const int i = (int)(t / h), j = (int)(t % h);
-            const float a = rU[(size_t)i * ld + j], b = rU[(size_t)i * ld + (W - 1 - j)];
-            const float se = a + b, so = a - b;
+            const bool self = 2 * j + 1 == W;
+            const float a = rU[(size_t)i * ld + j];
+            const float b = self ? 0.f : rU[(size_t)i * ld + (W - 1 - j)];
+            const float se = a + b, so = self ? 0.f : a - b;
             const __nv_bfloat16 eh = __float2bfloat16_rn(se), oh = __float2bfloat16_rn(so);
             const size_t off = (size_t)i * ldo + j;
             Re[off] = eh;
@@ -1430,7 +1442,7 @@ __device__ __forceinline__ void fold_r_body(const FoldRRec& f, int bid, int nblk
         }
         return;
     }
-    const int h4 = h / 4;
+    const int h4 = W / 8;
     const size_t total = (size_t)H * h4;
     for (size_t t = bid * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)nblk * blockDim.x) {
@@ -1480,7 +1492,7 @@ __global__ void k_fold_r_batched(const FoldRRec* __restrict__ recs, int T) {
 
 // blocks of one image's fold (a grid-stride loop over rows x quads, at most 8192 blocks)
 int fold_r_blocks(int H, int W) {
-    const size_t n = (size_t)H * (W % 8 == 0 ? W / 8 : W / 2);
+    const size_t n = (size_t)H * (W % 8 == 0 ? W / 8 : (W + 1) / 2);
     return (int)std::min<size_t>((n + 255) / 256, 8192);
 }
 
@@ -1572,20 +1584,22 @@ cudaError_t set_attrs() {
 
 }  // namespace
 
-// The folded form needs even sides (the mirror pairs); halves that are not multiples of 256 are
-// padded to them.  Below 256 per side the padding would dominate: the direct form runs there.
+// The folded form pairs mirrored rows and columns (for an odd side the middle one pairs with
+// itself); halves that are not multiples of 256 are padded to them.  Below 256 per side the
+// padding would dominate: the direct form runs there.
 bool foldable(int H, int W, int split) {
-    return split && H % 2 == 0 && W % 2 == 0 && H >= 256 && W >= 256;
+    return split && H >= 256 && W >= 256;
 }
 
 // padded extents of the folded operands: the halves and the full height, multiples of 256
 struct FoldDims {
     int hN, hM, hNp, hMp, Hp;
 };
+// hN, hM: the spatial half sides, (n + 1) / 2 (odd n: the middle row / column counted once)
 FoldDims fold_dims(int H, int W) {
     FoldDims f;
-    f.hN = H / 2;
-    f.hM = W / 2;
+    f.hN = (H + 1) / 2;
+    f.hM = (W + 1) / 2;
     f.hNp = (int)rup(f.hN, 256);
     f.hMp = (int)rup(f.hM, 256);
     f.Hp = (int)rup(H, 256);
@@ -1616,7 +1630,7 @@ struct FoldImage {
 };
 
 size_t fold_side_bytes(int n) {
-    const size_t hp = rup(n / 2, 256);
+    const size_t hp = rup((n + 1) / 2, 256);
     return 2 * 4 * rup(hp * hp * 2, 1024) + rup(2 * hp * 4, 1024);
 }
 
@@ -1630,7 +1644,7 @@ size_t fold_image_bytes(int H, int W) {
 template <typename Take>
 void carve_fold_side(FoldSide& sd, int n, Take take) {
     sd.n = n;
-    sd.hp = (int)rup(n / 2, 256);
+    sd.hp = (int)rup((n + 1) / 2, 256);
     const size_t e = (size_t)sd.hp * sd.hp * 2;
     for (int q = 0; q < 2; ++q) {
         sd.Pe[q] = take(e); sd.Po[q] = take(e); sd.PeT[q] = take(e); sd.PoT[q] = take(e);
@@ -1671,6 +1685,8 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
                           int skip, float tau) {
     const FoldDims fd = im.dim;
     const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
+    // the bases' padded sides are the operands' (every tensor map below assumes it)
+    if (sN.hp != hNp || sM.hp != hMp || sN.n != H || sM.n != W) return false;
     bool ok = true;
     UEpiArgs base{};
     base.st = st;
@@ -1718,6 +1734,7 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
         g.ep.C2 = im.T1[2 * x + 1][0]; g.ep.C2_lo = im.T1[2 * x + 1][1];
         g.ep.ldc = hNp;
         g.ep.vn = hN;
+        g.ep.mid = (H % 2 == 1) ? H / 2 : -1;
         tab[0].push_back(g);
     }
     // stage 2 (x, y): T2xy[l'][k'] = tau sum_i' T1x(+ for y = e, - for y = o)[l'][i'] PyT_N[k'][i']
@@ -1731,7 +1748,9 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
             g.M = hMp; g.N = hNp; g.K = hNp;
             g.ep = base;
             g.ep.C = im.T2[2 * x + y][0]; g.ep.C_lo = im.T2[2 * x + y][1]; g.ep.ldc = hNp;
-            g.ep.vm = hM; g.ep.vn = hN;
+            // valid frequencies of each parity: (n + 1) / 2 even, n / 2 odd
+            g.ep.vm = x ? W / 2 : hM;
+            g.ep.vn = y ? H / 2 : hN;
             g.ep.lam_m = sM.lamP + x * hMp;
             g.ep.lam_n = sN.lamP + y * hNp;
             g.ep.scale = tau;
@@ -1932,7 +1951,7 @@ bool build_fused(const std::vector<GemmTile> (&tab)[4], const std::vector<int>& 
     // stage 4: A rows r of T3e and T3o come from i' = r (r < hN) or i' = H - 1 - r (r >= hN)
     for (int i = 0; i < n_img; ++i) {
         const GemmTile& g = tab[3][i];
-        const int H = Hs[i], hN = H / 2;
+        const int H = Hs[i], hN = (H + 1) / 2;
         const int need = 2 * tab[2][2 * i].gx;
         std::vector<std::pair<int, FoldItem>> st4;
         for (int l = 0; l < ntiles(g); ++l) {
@@ -2424,7 +2443,8 @@ BatchLayout batch_layout(const int* H, const int* W, int T, int prec, int fold) 
 // Per-tile r^T z slots of the folded form's stage 2: 16 per 256 x 256 tile (two CTAs x eight
 // epilogue warps), four quarter problems of rup(H/2, 256) x rup(W/2, 256)
 size_t dct_rho_slots(int H, int W) {
-    return (size_t)(rup(H / 2, 256) / 256) * (rup(W / 2, 256) / 256) * 4 * 2 * k2EpiWarps;
+    return (size_t)(rup((H + 1) / 2, 256) / 256) * (rup((W + 1) / 2, 256) / 256) * 4 * 2 *
+           k2EpiWarps;
 }
 
 size_t batch_dct_bytes(const int* H, const int* W, int T, int prec, int fold) {

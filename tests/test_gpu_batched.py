@@ -97,9 +97,11 @@ def test_batched_folded_form_only_where_every_image_allows_it(irls):
         assert not b.folded
 
 
-# sides even and >= 256: halves padded to multiples of 256 (129 -> 256, 150 -> 256, 384 -> 512),
-# non-square, one side shared by several images, one shape twice
-FOLD_SHAPES = [(256, 256), (258, 300), (512, 384), (384, 768), (256, 256), (1024, 512)]
+# sides >= 256: halves padded to multiples of 256 (129 -> 256, 150 -> 256, 384 -> 512), odd sides
+# (middle row or column its own mirror), non-square, one side shared by several images, one
+# shape twice
+FOLD_SHAPES = [(256, 256), (258, 300), (512, 384), (384, 768), (256, 256), (1024, 512),
+               (257, 301), (511, 256)]
 
 
 def test_batched_folded_equals_single_image_path(irls):

@@ -119,7 +119,7 @@ def parity_atol(env):
 # the others the direct one
 PRECOND_SHAPES = [(64, 48), (130, 257), (256, 256), (384, 256), (256, 640), (1, 200), (300, 1),
                   (3, 3), (512, 256), (256, 768), (1024, 512), (2048, 2048), (1920, 2048),
-                  (4000, 2002), (258, 260)]
+                  (4000, 2002), (258, 260), (257, 301), (511, 1025), (1023, 257), (2047, 1999)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
@@ -173,7 +173,7 @@ def test_fft_reference_equals_oracle():
     assert np.abs(precond_reference_fft(R, 1e-2) - z).max() <= 1e-12 * np.abs(z).max()
 
 
-@pytest.mark.parametrize("H,W", [(4096, 4096), (2048, 4096), (4000, 16000)])
+@pytest.mark.parametrize("H,W", [(4096, 4096), (2048, 4096), (4000, 16000), (4095, 4097)])
 def test_precond_large(irls, H, W):
     """The folded preconditioner at the benchmarked size and at large non-square shapes (more
     output tiles than CTA pairs, several rounds per pair), against the float64 reference.  The
@@ -197,11 +197,12 @@ def test_precond_large(irls, H, W):
     assert np.array_equal(Z, Z2)   # deterministic: fixed tile order, fixed summation order
 
 
-def test_folded_and_direct_forms_agree(irls):
+@pytest.mark.parametrize("H,W", [(512, 768), (511, 769)])
+def test_folded_and_direct_forms_agree(irls, H, W):
     """The folded form (sums and differences of mirrored rows and columns, half-size products
-    with the even and odd halves of the DCT basis) and the direct form compute the same Sec. 3.3
-    solve; both within the split-precision bound of the oracle and of each other."""
-    H, W = 512, 768
+    with the even and odd halves of the DCT basis; for an odd side the middle row or column is
+    its own mirror) and the direct form compute the same Sec. 3.3 solve; both within the
+    split-precision bound of the oracle and of each other."""
     R = np.random.default_rng(11).standard_normal((H, W)).astype(np.float32)
     z_ref = O.precond_apply((R.astype(np.float64), np.zeros((H - 1, W)), np.zeros((H, W - 1))),
                             np.zeros((H - 1, W)), np.zeros((H, W - 1)), 1e-2, O.dct_basis(H),
@@ -218,28 +219,31 @@ def test_folded_and_direct_forms_agree(irls):
     for Z in (Zf, Zd):
         assert np.abs(Z - z_ref).max() <= 1e-4 * scale
     assert np.abs(Zf - Zd).max() <= 2e-4 * scale
-    X = synthetic.config_small(4, H=256, W=512)["X"]
+    Hu, Wu = (256, 512) if H % 2 == 0 else (257, 383)
+    X = synthetic.config_small(4, H=Hu, W=Wu)["X"]
     kw = dict(tau=1e-2, delta=1e-3, outer_iters=6, cg_tol=1e-6, cg_max=1000)
     ref = O.irls_unwrap(X, None, **kw)
     for form in ("folded", "direct"):
         U, st = irls.unwrap(cuda(X), None, eps=1e-3, outer_iters=6, cg_tol=1e-6,
                             precision="bf16x3", return_stats=True,
-                            plan=irls.Plan(256, 512, tau=1e-2, delta=1e-3, outer_iters=6,
+                            plan=irls.Plan(Hu, Wu, tau=1e-2, delta=1e-3, outer_iters=6,
                                            cg_tol=1e-6, precision="bf16x3", dct_form=form))
         assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], X,
                              ref=ref)
 
 
 def test_folded_form_only_where_allowed(irls):
-    """IRLS_DCT_FOLDED needs split precision and even sides of at least 256."""
-    for H, W, prec in ((200, 256, "bf16x3"), (256, 257, "bf16x3"), (256, 256, "bf16"),
+    """IRLS_DCT_FOLDED needs split precision and sides of at least 256 (odd or even)."""
+    for H, W, prec in ((200, 256, "bf16x3"), (256, 255, "bf16x3"), (256, 256, "bf16"),
                        (256, 256, "fp32")):
         with pytest.raises(irls.IrlsError) as e:
             irls.Plan(H, W, precision=prec, dct_form="folded")
         assert e.value.code == -8
     with irls.Plan(384, 256, precision="bf16x3") as plan:
         assert plan.folded
-    with irls.Plan(256, 257, precision="bf16x3") as plan:
+    with irls.Plan(257, 301, precision="bf16x3") as plan:
+        assert plan.folded
+    with irls.Plan(256, 255, precision="bf16x3") as plan:
         assert not plan.folded
         with pytest.raises(irls.IrlsError):
             plan.set_opts(dct_form="folded")
