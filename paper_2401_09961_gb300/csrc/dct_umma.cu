@@ -57,7 +57,6 @@ enum UEpi : int {
     UE_FOLD16 = 4,        // out+ = acc0 + mirror(acc1), out- = acc0 - mirror(acc1)
     UE_UNFOLD16 = 5,      // row m: acc0 + acc1, row mrows-1-m: acc0 - acc1
     UE_UNFOLDZ = 6,       // col n: acc0 + acc1, col mcols-1-n: acc0 - acc1 (fp32)
-    UE_UNFOLDZ_RHO = 7,   // same, plus r^T z and the CG ratio
     UE_EIG16_RHO = 8      // EIG16, plus r^T z formed from the spectral coefficients
 };
 
@@ -520,7 +519,7 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
             scr_put(s, mi);
             const int mr = ep.mrows - 1 - m0w;
             scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; }, nr);
-        } else if constexpr (EPI == UE_UNFOLDZ || EPI == UE_UNFOLDZ_RHO) {
+        } else if constexpr (EPI == UE_UNFOLDZ) {
             uint32_t r1[32];
             tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
             const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
@@ -530,7 +529,7 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 pl[t] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);                // nb + t
                 mi[t] = __uint_as_float(r[31 - t]) - __uint_as_float(r1[31 - t]);     // mb + t
             }
-            const float* rr = EPI == UE_UNFOLDZ_RHO ? ep.rU : nullptr;
+            const float* rr = nullptr;   // r^T z is formed in stage 2
             // rows beyond the image and columns beyond the half side (padding) are not written;
             // the mirrored block holds column nb + t at position 31 - t
             const int nr = min(max(ep.vm - m0w, 0), 32);
@@ -682,7 +681,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
         tc_fence_after();
         tmem_dealloc(tmem, kCols);
     }
-    if constexpr (EPI == UE_ZU_RHO || EPI == UE_UNFOLDZ_RHO) {
+    if constexpr (EPI == UE_ZU_RHO) {
         double vv[1] = {(double)part}, tot[1];
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0)
             finish_rho(ep, tot[0]);
@@ -767,11 +766,6 @@ __device__ __forceinline__ bool epi_sync(uint64_t* bar, int& n, int* err) {
     }
     ++n;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-// A problem whose CG run has stopped (per-image mask of a batched launch) contributes no tiles.
-__device__ __forceinline__ bool problem_live(const GemmTile& g) {
-    return !(g.ep.skip_if_done && *(volatile int*)&g.ep.st->done);
 }
 
 // Persistent, warp-specialised grouped GEMM (128 x 128 tiles, split operands: hi + lo parts of
