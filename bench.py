@@ -33,7 +33,7 @@ OUTER, DELTA, TAU, CG_TOL = 20, 1e-3, 1e-2, 1e-6
 # follows the same trajectory); used only to extrapolate the oracle's timed sample when no GPU
 # run is available in the same process (the reference arm).
 # CG iterations of the full unwrap the reference arm extrapolates to: 4096 x 4096 is the count
-# measured for this workload (20 outer steps, cg_tol 1e-6: 4466 in float32 and split bf16 alike);
+# measured for this workload (20 outer steps, cg_tol 1e-6: 4466 in split bf16, 4472 in float32);
 # other sizes take a round figure
 CG_TOTAL_REFERENCE = {4096: 4466, 2048: 3000}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
