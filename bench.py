@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--width", type=int, default=None,
                     help="image width (default: --size, a square image); e.g. --size 4000 "
                          "--width 16000 for the paper's 4000 x M scaling shapes")
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "fp16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default stencil tile shapes (no timing pass before warm-up)")
@@ -315,7 +315,10 @@ def main():
                     "achieved": alg, "peak": sus / passes, "unit": "TFLOP/s",
                     "peak_source": (f"bf16_tflops_sustained ({peak_src}) / {passes}: the split "
                                     "product issues three bf16 MMAs per multiply-add"
-                                    if passes == 3 else f"bf16_tflops_sustained ({peak_src})"),
+                                    if passes == 3 else
+                                    f"bf16_tflops_sustained ({peak_src}); float16 and bf16 "
+                                    "have the same dense tensor rate" if prec == "fp16" else
+                                    f"bf16_tflops_sustained ({peak_src})"),
                     "tensor_pipe_frac_of_bf16_peak": alg * passes / sus}
     else:
         achieved = bytes_px[dom] * P / avg_s / 1e9

@@ -53,6 +53,11 @@ extern "C" {
 #define IRLS_PREC_BF16   1  /* bfloat16 operands, float32 accumulation (tcgen05), one pass    */
 #define IRLS_PREC_BF16X3 2  /* split bfloat16: x = hi + lo, three tcgen05 products per GEMM   */
                             /* (hi*hi + hi*lo + lo*hi), float32 accumulation                  */
+#define IRLS_PREC_FP16   3  /* float16 operands, one tcgen05 product, float32 accumulation;   */
+                            /* folded form only (single-image plans, sides >= 256): r_U is   */
+                            /* scaled by sqrt(H W) / ||r_U||, each row of the eigenvalue      */
+                            /* stage by (mu + lambda_1) / tau, undone by a pre-scaled basis   */
+                            /* in the last stage; not for batches or the adjoint              */
 
 /* Form of the tensor-core preconditioner (split precision only). */
 #define IRLS_DCT_AUTO   0   /* folded where allowed, else direct                                  */

@@ -16,7 +16,7 @@ IRLS_MAX_OUTER = 256
 DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2}
 CG_SCHEDULES = {"fixed": 0, "paper": 1}
 SYSTEMS = {"full": 0, "schur": 1}
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16": 3}
 
 STATUS = {
     0: "IRLS_OK", 1: "IRLS_WARN_CG_MAX", -1: "IRLS_ERR_ARG", -2: "IRLS_ERR_SHAPE",

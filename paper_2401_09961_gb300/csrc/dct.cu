@@ -22,7 +22,7 @@ namespace irls {
 cudaError_t umma_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                            int reduce_rho, const StencilArgs& a, double* partials,
                            int skip_if_done, cudaStream_t s);
-size_t umma_dct_bytes(int H, int W, int split);
+size_t umma_dct_bytes(int H, int W, int prec);
 cudaError_t umma_dct_setup(DctPlan& d, char* mem);
 void umma_dct_release(DctPlan& d);
 cudaError_t umma_dct_reset(const DctPlan& d, cudaStream_t s);
@@ -214,7 +214,7 @@ size_t dct_bytes(int H, int W, int prec) {
     size_t n = 2 * Hp * Hp + Hp + Wp + 2 * Hp * Wp;
     if (H != W) n += 2 * Wp * Wp;
     size_t bytes = n * sizeof(float) + 4096;
-    if (prec != IRLS_PREC_FP32) bytes += umma_dct_bytes(H, W, prec == IRLS_PREC_BF16X3);
+    if (prec != IRLS_PREC_FP32) bytes += umma_dct_bytes(H, W, prec);
     return bytes;
 }
 

@@ -83,7 +83,20 @@ struct UEpiArgs {
     // FOLD16 with an odd number of B rows: the middle row pairs with itself (its sum is the row
     // itself, not twice it); -1 otherwise
     int mid;
+    // float16 operands (folded form): bf16 stores become float16 stores; stage 2 writes its
+    // coefficients scaled per row by (mu_m + lam1) / tau (lam1: the smallest nonzero eigenvalue
+    // of the other side), which cancels the division's growth; stage 4 (whose basis is scaled
+    // by the inverse) undoes the residual's scale sqrt(H W) / ||r_U|| (inv_sqrt_n = 1/sqrt(H W))
+    int f16;
+    float lam1, inv_sqrt_n;
 };
+
+// 1 / (the residual's float16 scale) of the current application: ||r_U|| / sqrt(H W), or 1 for
+// r_U = 0.  The kernel that produced r_U set ||r_U||; it does not change during the application.
+__device__ __forceinline__ float f16_inv_scale(const UEpiArgs& ep) {
+    const double rn = *(volatile const double*)&ep.st->rnorm_u;
+    return rn > 0.0 ? (float)(rn * (double)ep.inv_sqrt_n) : 1.f;
+}
 
 template <int BN, int SA, int SB>
 struct UCfg {
@@ -415,7 +428,7 @@ __device__ __forceinline__ void scr_put(WarpScratch& s, const float (&v)[32]) {
 // beyond nrows are not written.
 template <typename RowOff>
 __device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void* lo, int col0,
-                                            RowOff row_off, int nrows = 32) {
+                                            RowOff row_off, int nrows = 32, int f16 = 0) {
     const int lane = threadIdx.x & 31;
     const int rsub = lane >> 4, col = 2 * (lane & 15);
 #pragma unroll 4
@@ -424,6 +437,10 @@ __device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void
         if (row >= nrows) continue;
         const float x0 = s.v[row][col], x1 = s.v[row][col + 1];
         const size_t off = row_off(row) + col0 + col;
+        if (f16) {   // float16, one part
+            *reinterpret_cast<__half2*>(static_cast<__half*>(hi) + off) = __floats2half2_rn(x0, x1);
+            continue;
+        }
         const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
         *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(hi) + off) = h;
         if (lo) {
@@ -499,9 +516,9 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 mi[t] = ok && !self ? a - b : 0.f;
             }
             scr_put(s, pl);
-            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows, 32, ep.f16);
             scr_put(s, mi);
-            scr_store16(s, ep.C2, ep.C2_lo, nb, rows);
+            scr_store16(s, ep.C2, ep.C2_lo, nb, rows, 32, ep.f16);
         } else if constexpr (EPI == UE_UNFOLD16) {
             uint32_t r1[32];
             tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
@@ -515,19 +532,21 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
             // rows at or beyond the half side (padding) have no mirror partner: not written
             const int nr = min(max(ep.vm - m0w, 0), 32);
             scr_put(s, pl);
-            scr_store16(s, ep.C, ep.C_lo, nb, rows, nr);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows, nr, ep.f16);
             scr_put(s, mi);
             const int mr = ep.mrows - 1 - m0w;
-            scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; }, nr);
+            scr_store16(s, ep.C, ep.C_lo, nb, [&](int rr) { return (size_t)(mr - rr) * ldc; }, nr,
+                        ep.f16);
         } else if constexpr (EPI == UE_UNFOLDZ) {
             uint32_t r1[32];
             tmem_ld32(tl + (uint32_t)BN + (uint32_t)(c * 32), r1);
             const int mb = ep.mcols - 32 - nb;   // first column of the mirrored 32
+            const float us = ep.f16 ? f16_inv_scale(ep) : 1.f;
             float pl[32], mi[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
-                pl[t] = __uint_as_float(r[t]) + __uint_as_float(r1[t]);                // nb + t
-                mi[t] = __uint_as_float(r[31 - t]) - __uint_as_float(r1[31 - t]);     // mb + t
+                pl[t] = (__uint_as_float(r[t]) + __uint_as_float(r1[t])) * us;            // nb + t
+                mi[t] = (__uint_as_float(r[31 - t]) - __uint_as_float(r1[31 - t])) * us;  // mb + t
             }
             const float* rr = nullptr;   // r^T z is formed in stage 2
             // rows beyond the image and columns beyond the half side (padding) are not written;
@@ -546,17 +565,21 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                 const bool rowok = m < ep.vm;
                 const float lm = rowok ? ep.lam_m[m] : 0.f;
 #pragma unroll
+                // float16: the row's coefficients times (lm + lam1) / tau (see UEpiArgs)
+                const float rs = ep.f16 ? __fdividef(lm + ep.lam1, ep.scale) : 1.f;
                 for (int t = 0; t < 32; ++t) {
                     const int n = nb + t;
                     const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
                     const float f = v[t];
-                    v[t] = keep ? __fdividef(ep.scale * f, lm + __ldg(&ep.lam_n[n])) : 0.f;
-                    // r^T z = sum over frequencies of F * (tau F / eig) (P_N, P_M orthogonal)
-                    if constexpr (EPI == UE_EIG16_RHO) part += f * v[t];
+                    const float g = keep ? __fdividef(ep.scale * f, lm + __ldg(&ep.lam_n[n])) : 0.f;
+                    v[t] = g * rs;
+                    // r^T z = sum over frequencies of F * (tau F / eig) (P_N, P_M orthogonal);
+                    // with float16 F and G carry the residual's scale, removed when rho is formed
+                    if constexpr (EPI == UE_EIG16_RHO) part += f * g;
                 }
             }
             scr_put(s, v);
-            scr_store16(s, ep.C, ep.C_lo, nb, rows);
+            scr_store16(s, ep.C, ep.C_lo, nb, rows, 32, ep.f16);
         } else {
             static_assert(EPI == UE_STORE16, "persistent kernels: folded and eigenvalue forms");
         }
@@ -983,13 +1006,15 @@ __device__ __forceinline__ void fused_epi(uint32_t tl, const UEpiArgs& ep, int m
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
 k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ items,
               int n_items, unsigned* __restrict__ ctr, int n_ctr, DevState* const* __restrict__ sts,
-              int n_st, int honour_stop) {
+              int n_st, int honour_stop, int f16) {
     using C = Q2Cfg<0, 256>;
     static_assert(Q2Cfg<1, 256>::kStageBytes == C::kStageBytes, "one ring for both forms");
     constexpr int S = C::kStages;
     constexpr uint32_t kCols = 512, kBuf = 256;
     // N = 128 per operand set (half-width two-set tiles), otherwise as C::kIdesc
     constexpr uint32_t kIdescHalf = (C::kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(128 >> 3) << 17);
+    // float16 operands: A and B format fields 0 (float16) instead of 1 (bf16)
+    constexpr uint32_t kFmtBits = (7u << 7) | (7u << 10);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -1083,8 +1108,10 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                     const int m0 = f.m0 + 128 * (int)rank;
                     const int nb = rank == 0 ? f.n0 : f.nb1;
                     const int nkb = f.nkb, nkt = dual ? 2 * nkb : nkb;
-                    // a half-width tile stages 64 B rows per CTA instead of 128
-                    const uint32_t tx = half ? 2u * (2 * C::kABytes + C::kBBytes) : 2u * C::kStageBytes;
+                    // a half-width tile stages 64 B rows per CTA instead of 128; float16 operands have
+                    // one part (no lo planes)
+                    const uint32_t parts = f16 ? 1u : 2u;
+                    const uint32_t tx = 2u * parts * (C::kABytes + (half ? C::kBBytes / 2 : C::kBBytes));
                     for (int kb = 0; kb < nkt; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -1099,13 +1126,15 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         if (rank == 0) mbar_expect_tx(&full[s], tx);
                         const uint32_t fb = full0 + 8u * (uint32_t)s;
                         tma_load_2d_pair(sa, second ? &g.a2 : &g.a0, fb, kc, m0);
-                        tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
                         const CUtensorMap* bm0 = half ? (second ? &g.bh2 : &g.bh0)
                                                       : (second ? &g.b2 : &g.b0);
-                        const CUtensorMap* bm1 = half ? (second ? &g.bh3 : &g.bh1)
-                                                      : (second ? &g.b3 : &g.b1);
                         tma_load_2d_pair(sb, bm0, fb, kc, nb);
-                        tma_load_2d_pair(sb + C::kBBytes, bm1, fb, kc, nb);
+                        if (!f16) {
+                            tma_load_2d_pair(sa + C::kABytes, second ? &g.a3 : &g.a1, fb, kc, m0);
+                            const CUtensorMap* bm1 = half ? (second ? &g.bh3 : &g.bh1)
+                                                          : (second ? &g.b3 : &g.b1);
+                            tma_load_2d_pair(sb + C::kBBytes, bm1, fb, kc, nb);
+                        }
                     }
                     f = fn;
                 }
@@ -1137,7 +1166,7 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                     const bool two = dual && !half;   // both accumulator buffers
                     const int b0 = two ? 0 : nbuf, nbu = two ? 2 : 1;
                     if (!two) nbuf ^= 1;
-                    const uint32_t idesc = half ? kIdescHalf : C::kIdesc;
+                    const uint32_t idesc = (half ? kIdescHalf : C::kIdesc) & (f16 ? ~kFmtBits : ~0u);
                     const uint32_t set1 = half ? 128u : kBuf;
                     for (int k = 0; k < nbu && !bad; ++k) {
                         const int b = b0 + k;
@@ -1167,10 +1196,17 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                         const uint64_t dal = desc_sw128(sa + C::kABytes);
                         const uint64_t dbl = desc_sw128(sb + C::kBBytes);
     #pragma unroll
-                        for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
-                            umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, idesc, (kk | q) != 0);
-                            umma_bf16_pair(td, dal + 2 * q, db + 2 * q, idesc, 1u);
-                            umma_bf16_pair(td, da + 2 * q, db + 2 * q, idesc, 1u);
+                        if (f16) {
+#pragma unroll
+                            for (int q = 0; q < UBK / 16; ++q)   // one float16 product per K = 16
+                                umma_bf16_pair(td, da + 2 * q, db + 2 * q, idesc, (kk | q) != 0);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < UBK / 16; ++q) {   // K = 16 per MMA: +32 bytes
+                                umma_bf16_pair(td, da + 2 * q, dbl + 2 * q, idesc, (kk | q) != 0);
+                                umma_bf16_pair(td, dal + 2 * q, db + 2 * q, idesc, 1u);
+                                umma_bf16_pair(td, da + 2 * q, db + 2 * q, idesc, 1u);
+                            }
                         }
                         umma_commit_pair(&empty[s]);
                     }
@@ -1260,6 +1296,10 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                             if (warp == 2 && lane == 0) {
                                 double sum = 0.0;
                                 for (int w = 0; w < k2EpiWarps; ++w) sum += s_tot[w];
+                                if (ep.f16) {
+                                    const double us = (double)f16_inv_scale(ep);
+                                    sum *= us * us;
+                                }
                                 finish_rho(ep, sum, true);
                                 ep.st->counter = 0u;
                             }
@@ -1347,7 +1387,7 @@ __global__ void k_build_basis16(__nv_bfloat16* P16, __nv_bfloat16* PT16, __nv_bf
 __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat16* PeT,
                                __nv_bfloat16* PoT, __nv_bfloat16* Pelo, __nv_bfloat16* Polo,
                                __nv_bfloat16* PeTlo, __nv_bfloat16* PoTlo, float* lamP, int n,
-                               int hp) {
+                               int hp, int f16) {
     // spatial half: (n + 1) / 2 rows (for odd n the middle row is its own mirror); frequencies:
     // (n + 1) / 2 even ones, n / 2 odd ones.  On the middle row every odd-frequency entry is
     // exactly 0 (P[(n-1)/2][k] = (-1)^k P[(n-1)/2][k]), so the two mirrored writes of that row in
@@ -1365,10 +1405,16 @@ __global__ void k_build_fold16(__nv_bfloat16* Pe, __nv_bfloat16* Po, __nv_bfloat
                 const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
                 v = ck * cospi((double)mm / (2.0 * n));
             }
-            const __nv_bfloat16 hv = __double2bfloat16(v);
-            const __nv_bfloat16 lv = __double2bfloat16(v - (double)__bfloat162float(hv));
             __nv_bfloat16* P = par ? Po : Pe;
             __nv_bfloat16* PT = par ? PoT : PeT;
+            if (f16) {   // float16, one part (the lo planes stay unused)
+                const __half hh = __double2half(v);
+                reinterpret_cast<__half*>(P)[(size_t)a * hp + b] = hh;
+                reinterpret_cast<__half*>(PT)[(size_t)b * hp + a] = hh;
+                continue;
+            }
+            const __nv_bfloat16 hv = __double2bfloat16(v);
+            const __nv_bfloat16 lv = __double2bfloat16(v - (double)__bfloat162float(hv));
             P[(size_t)a * hp + b] = hv;
             PT[(size_t)b * hp + a] = hv;
             __nv_bfloat16* Pl = par ? Polo : Pelo;
@@ -1404,11 +1450,32 @@ struct FoldRRec {
     __nv_bfloat16 *Re, *Relo, *Ro, *Rolo;
     const DevState* st;
     int blk0, nblk;   // the image's blocks in a batched launch
+    int f16;          // float16 planes (Re, Ro only), scaled by sqrt(H W) / ||r_U||
+    float inv_sqrt_n;
 };
 
 __device__ __forceinline__ void fold_r_body(const FoldRRec& f, int bid, int nblk) {
     const float* __restrict__ rU = f.rU;
     const int ld = f.ld, H = f.H, W = f.W, ldo = f.ldo;
+    if (f.f16) {
+        const double rn = f.st->rnorm_u;
+        const float sc = rn > 0.0 ? (float)(1.0 / (rn * (double)f.inv_sqrt_n)) : 1.f;
+        __half* __restrict__ Eh = reinterpret_cast<__half*>(f.Re);
+        __half* __restrict__ Oh = reinterpret_cast<__half*>(f.Ro);
+        const int h = (W + 1) / 2;
+        const size_t total = (size_t)H * h;
+        for (size_t t = bid * (size_t)blockDim.x + threadIdx.x; t < total;
+             t += (size_t)nblk * blockDim.x) {
+            const int i = (int)(t / h), j = (int)(t % h);
+            const bool self = 2 * j + 1 == W;
+            const float a = rU[(size_t)i * ld + j];
+            const float b = self ? 0.f : rU[(size_t)i * ld + (W - 1 - j)];
+            const size_t off = (size_t)i * ldo + j;
+            Eh[off] = __float2half_rn((a + b) * sc);
+            Oh[off] = __float2half_rn(self ? 0.f : (a - b) * sc);
+        }
+        return;
+    }
     __nv_bfloat16* __restrict__ Re = f.Re;
     __nv_bfloat16* __restrict__ Relo = f.Relo;
     __nv_bfloat16* __restrict__ Ro = f.Ro;
@@ -1485,9 +1552,35 @@ __global__ void k_fold_r_batched(const FoldRRec* __restrict__ recs, int T) {
 }
 
 // blocks of one image's fold (a grid-stride loop over rows x quads, at most 8192 blocks)
-int fold_r_blocks(int H, int W) {
-    const size_t n = (size_t)H * (W % 8 == 0 ? W / 8 : (W + 1) / 2);
+int fold_r_blocks(int H, int W, int f16 = 0) {
+    const size_t n = (size_t)H * ((W % 8 == 0 && !f16) ? W / 8 : (W + 1) / 2);
     return (int)std::min<size_t>((n + 255) / 256, 8192);
+}
+
+// Float16 form, stage 4's B operand: the even / odd basis halves of side W with column (frequency)
+// k scaled by tau / (mu_k + lam1), the inverse of the row scale stage 2 gives its coefficients
+// (mu_k: this side's eigenvalues, lam1: the other side's smallest nonzero one).  P4e[a][b] for
+// frequency 2b, P4o[a][b] for 2b + 1, hp x hp, zero outside the valid block.  Largest entry about
+// sqrt(2 / W) tau / lam1 (~ 4e2 at 4096 x 4096): within float16.
+__global__ void k_build_fold_stage4_f16(__half* P4e, __half* P4o, int n, int hp, double lam1,
+                                        double tau) {
+    const int hs = (n + 1) / 2;
+    const size_t total = (size_t)hp * hp;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / hp), b = (int)(t % hp);
+        for (int par = 0; par < 2; ++par) {
+            const int k = 2 * b + par;
+            double v = 0.0;
+            if (a < hs && k < n && !(par == 1 && 2 * a + 1 == n)) {
+                const long long mm = ((long long)(2 * a + 1) * k) % (4LL * n);
+                const double ck = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+                const double sn = sinpi((double)k / (2.0 * n));
+                v = ck * cospi((double)mm / (2.0 * n)) * tau / (4.0 * sn * sn + lam1);
+            }
+            (par ? P4o : P4e)[(size_t)a * hp + b] = __double2half(v);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1580,9 +1673,10 @@ cudaError_t set_attrs() {
 
 // The folded form pairs mirrored rows and columns (for an odd side the middle one pairs with
 // itself); halves that are not multiples of 256 are padded to them.  Below 256 per side the
-// padding would dominate: the direct form runs there.
-bool foldable(int H, int W, int split) {
-    return split && H >= 256 && W >= 256;
+// padding would dominate: the direct form runs there.  `tc`: a precision the folded form runs in
+// (split bf16 or float16).
+bool foldable(int H, int W, int tc) {
+    return tc && H >= 256 && W >= 256;
 }
 
 // padded extents of the folded operands: the halves and the full height, multiples of 256
@@ -1610,6 +1704,7 @@ constexpr int kPairDualN = 256;
 // Even / odd basis halves of one side length n (hi and lo parts), padded to hp = rup(n/2, 256).
 struct FoldSide {
     int n = 0, hp = 0;
+    int f16 = 0;   // float16 bases (one part) instead of bf16 hi / lo
     void *Pe[2], *Po[2], *PeT[2], *PoT[2];
     float* lamP;
 };
@@ -1620,6 +1715,7 @@ struct FoldImage {
     void *Re[2], *Ro[2];   // H x hMp
     void* T1[4][2];        // (x, sign) = (e+, e-, o+, o-), hMp x hNp
     void* T3[2][2];        // x = e, o: Hp x hMp
+    void* P4[2];           // float16 form: stage 4's scaled basis halves (even, odd), hMp x hMp
     void* T2[4][2];        // (x, y) = ee, eo, oe, oo: hMp x hNp
 };
 
@@ -1632,12 +1728,14 @@ size_t fold_image_bytes(int H, int W) {
     const FoldDims fd = fold_dims(H, W);
     const size_t hNp = fd.hNp, hMp = fd.hMp;
     return 2 * (2 * rup((size_t)H * hMp * 2, 1024) + 4 * rup(hMp * hNp * 2, 1024) +
-                4 * rup(hMp * hNp * 2, 1024) + 2 * rup((size_t)fd.Hp * hMp * 2, 1024));
+                4 * rup(hMp * hNp * 2, 1024) + 2 * rup((size_t)fd.Hp * hMp * 2, 1024)) +
+           2 * rup(hMp * hMp * 2, 1024);
 }
 
 template <typename Take>
-void carve_fold_side(FoldSide& sd, int n, Take take) {
+void carve_fold_side(FoldSide& sd, int n, Take take, int f16 = 0) {
     sd.n = n;
+    sd.f16 = f16;
     sd.hp = (int)rup((n + 1) / 2, 256);
     const size_t e = (size_t)sd.hp * sd.hp * 2;
     for (int q = 0; q < 2; ++q) {
@@ -1651,7 +1749,7 @@ void build_fold_side(const FoldSide& sd) {
     auto bf = [](void* x) { return static_cast<B*>(x); };
     k_build_fold16<<<1024, 256>>>(bf(sd.Pe[0]), bf(sd.Po[0]), bf(sd.PeT[0]), bf(sd.PoT[0]),
                                   bf(sd.Pe[1]), bf(sd.Po[1]), bf(sd.PeT[1]), bf(sd.PoT[1]),
-                                  sd.lamP, sd.n, sd.hp);
+                                  sd.lamP, sd.n, sd.hp, sd.f16);
 }
 
 template <typename Take>
@@ -1670,13 +1768,14 @@ void carve_fold_image(FoldImage& im, int H, int W, Take take) {
     // T3 rows H .. Hp-1 are read as A rows of stage 4 (masked there) and never written: zero
     for (int q = 0; q < 2; ++q)
         for (int x = 0; x < 2; ++x) im.T3[x][q] = take((size_t)fd.Hp * hMp * 2);
+    for (int x = 0; x < 2; ++x) im.P4[x] = take(hMp * hMp * 2);
 }
 
 // Appends one image's nine problems (2, 4, 2 and 1 per stage) to the stage tables.
 bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
                           const FoldSide& sN, const FoldSide& sM, int H, int W, const float* rU,
                           float* zU, int ld, DevState* st, double* partials, int flexible,
-                          int skip, float tau) {
+                          int skip, float tau, int f16 = 0) {
     const FoldDims fd = im.dim;
     const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
     // the bases' padded sides are the operands' (every tensor map below assumes it)
@@ -1687,6 +1786,12 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
     base.partials = partials;
     base.flexible = flexible;
     base.skip_if_done = skip;
+    base.f16 = f16;
+    {
+        const double sn = std::sin(3.14159265358979323846 / (2.0 * H));
+        base.lam1 = (float)(4.0 * sn * sn);   // the smallest nonzero eigenvalue of side H
+        base.inv_sqrt_n = (float)(1.0 / std::sqrt((double)H * (double)W));
+    }
     int bbox = 128;
     bool halves = false;   // two-set stages: also B maps with 64-row boxes (half-width tiles)
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
@@ -1767,11 +1872,14 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
         g.ep.vm = hN;
         tab[2].push_back(g);
     }
-    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O (i < H, j' < hM), E from T3e, O from T3o
+    // stage 4: Z[i][j'] = E + O, Z[i][W-1-j'] = E - O (i < H, j' < hM), E from T3e, O from T3o;
+    // the float16 form's B is the basis scaled per frequency (the inverse of stage 2's row scale)
     {
         GemmTile g{};
-        set0(g, im.T3[0], fd.Hp, hMp, sM.Pe, hMp, hMp);
-        set1(g, im.T3[1], fd.Hp, hMp, sM.Po, hMp, hMp);
+        void* const p4e[2] = {im.P4[0], im.P4[0]};
+        void* const p4o[2] = {im.P4[1], im.P4[1]};
+        set0(g, im.T3[0], fd.Hp, hMp, f16 ? p4e : sM.Pe, hMp, hMp);
+        set1(g, im.T3[1], fd.Hp, hMp, f16 ? p4o : sM.Po, hMp, hMp);
         g.M = fd.Hp; g.N = hMp; g.K = hMp;
         g.ep = base;
         g.ep.C = zU; g.ep.ldc = ld; g.ep.mcols = W; g.ep.rU = rU;
@@ -1818,6 +1926,7 @@ struct FusedDev {
     unsigned* ctr = nullptr;     // n_ctr panel counters and the exit counter
     DevState** sts = nullptr;    // the images' states
     int n_probs = 0, n_items = 0, cap_items = 0, n_ctr = 0, n_st = 0, pairs = 0, honour_stop = 1;
+    int f16 = 0;                 // float16 operands (one MMA per K step)
 };
 
 // Items and panel counters of one image's four stages.
@@ -2084,7 +2193,7 @@ int fused_pairs(int n_sm) {
 
 cudaError_t launch_fused(const FusedDev& fd, cudaStream_t s) {
     k2_fold_fused<<<2 * fd.pairs, k2Threads, Q2Cfg<0>::kSmem, s>>>(
-        fd.probs, fd.items, fd.n_items, fd.ctr, fd.n_ctr, fd.sts, fd.n_st, fd.honour_stop);
+        fd.probs, fd.items, fd.n_items, fd.ctr, fd.n_ctr, fd.sts, fd.n_st, fd.honour_stop, fd.f16);
     return cudaGetLastError();
 }
 
@@ -2106,13 +2215,15 @@ int device_sms() {
 }
 
 FoldRRec fold_r_rec(const FoldImage& im, const float* rU, int ld, int H, int W,
-                    const DevState* st) {
+                    const DevState* st, int f16 = 0) {
     using B = __nv_bfloat16;
     FoldRRec r{};
     r.rU = rU; r.ld = ld; r.H = H; r.W = W; r.ldo = im.dim.hMp;
     r.Re = static_cast<B*>(im.Re[0]); r.Relo = static_cast<B*>(im.Re[1]);
     r.Ro = static_cast<B*>(im.Ro[0]); r.Rolo = static_cast<B*>(im.Ro[1]);
     r.st = st;
+    r.f16 = f16;
+    r.inv_sqrt_n = (float)(1.0 / std::sqrt((double)H * (double)W));
     return r;
 }
 
@@ -2155,11 +2266,13 @@ cudaError_t fold_setup(DctPlan& d, char* p) {
     FoldBufs* fp = new FoldBufs();
     FoldBufs& f = *fp;
     d.fold_host = fp;
-    carve_fold_side(f.sN, H, take);
-    if (H != W) carve_fold_side(f.sM, W, take);
+    const int f16 = d.prec == IRLS_PREC_FP16 ? 1 : 0;
+    carve_fold_side(f.sN, H, take, f16);
+    if (H != W) carve_fold_side(f.sM, W, take, f16);
     else f.sM = f.sN;
     carve_fold_image(f.img, H, W, take);
     f.dim = f.img.dim;
+    f.fused.f16 = f16;
     {
         int items = 0, ctrs = 0;
         fused_counts(H, W, items, ctrs);
@@ -2186,8 +2299,17 @@ cudaError_t fold_bind(const DctPlan& d, FoldBufs& f, const float* rU, float* zU,
                       cudaStream_t s) {
     for (auto& t : f.tab) t.clear();
     if (!append_fold_problems(f.tab, f.img, f.sN, f.sM, d.H, d.W, rU, zU, ld, st, partials,
-                              flexible, skip, d.tau))
+                              flexible, skip, d.tau, f.fused.f16))
         return cudaErrorNotSupported;
+    if (f.fused.f16) {
+        // stage 4's basis, scaled per frequency by tau / (mu + lambda_1): depends on tau
+        const double sn = std::sin(3.14159265358979323846 / (2.0 * d.H));
+        k_build_fold_stage4_f16<<<1024, 256, 0, s>>>(static_cast<__half*>(f.img.P4[0]),
+                                                     static_cast<__half*>(f.img.P4[1]), d.W,
+                                                     f.dim.hMp, 4.0 * sn * sn, (double)d.tau);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     int tiles[4];
     if (!number_fold_tiles(f.tab, tiles)) return cudaErrorInvalidValue;
     std::vector<GemmTile> probs;
@@ -2215,8 +2337,8 @@ cudaError_t fold_apply(const DctPlan& d, const float* rU, float* zU, int ld, Dev
             fold_bind(d, f, rU, zU, ld, st, partials, flexible, skip_if_done, reduce_rho, s);
         if (e != cudaSuccess) return e;
     }
-    k_fold_r<<<fold_r_blocks(d.H, d.W), 256, 0, s>>>(fold_r_rec(f.img, rU, ld, d.H, d.W, st),
-                                                      skip_if_done);
+    k_fold_r<<<fold_r_blocks(d.H, d.W, f.fused.f16), 256, 0, s>>>(
+        fold_r_rec(f.img, rU, ld, d.H, d.W, st, f.fused.f16), skip_if_done);
     return launch_fused(f.fused, s);
 }
 
@@ -2246,13 +2368,14 @@ void umma_dct_release(DctPlan& d) {
     d.fold = d.fold_ready = 0;
 }
 
-size_t umma_dct_bytes(int H, int W, int split) {
+size_t umma_dct_bytes(int H, int W, int prec) {
+    const bool split = prec == IRLS_PREC_BF16X3;
     const size_t Hp = rup(H, 128), Wp = rup(W, 128);
     size_t n = 2 * Hp * Hp + 3 * Hp * Wp;
     if (H != W) n += 2 * Wp * Wp;
     if (split) n *= 2;
     size_t bytes = n * 2 + 32 * 1024;
-    if (foldable(H, W, split)) bytes += fold_bytes(H, W);
+    if (foldable(H, W, split || prec == IRLS_PREC_FP16)) bytes += fold_bytes(H, W);
     return bytes;
 }
 
@@ -2285,7 +2408,7 @@ cudaError_t umma_dct_setup(DctPlan& d, char* mem) {
     take2(Hp * Wp, d.S16a, d.S16alo);
     take2(Hp * Wp, d.S16b, d.S16blo);
     umma_dct_release(d);
-    if (foldable(d.H, d.W, split)) {
+    if (foldable(d.H, d.W, split || d.prec == IRLS_PREC_FP16)) {
         cudaError_t ef = fold_setup(d, p);
         if (ef != cudaSuccess) return ef;
         d.fold = d.fold_ready = 1;

@@ -52,7 +52,7 @@ bool opts_valid(const irls_opts& o) {
     if (!(o.cg_tol >= 0.f)) return false;
     if (o.outer_iters < 0 || o.outer_iters > IRLS_MAX_OUTER) return false;
     if (o.cg_max_iter < 0) return false;
-    if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_BF16X3) return false;
+    if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_FP16) return false;
     if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FOLDED) return false;
     if (o.cg_schedule != IRLS_CG_FIXED && o.cg_schedule != IRLS_CG_PAPER) return false;
     if (o.system != IRLS_SYS_FULL && o.system != IRLS_SYS_SCHUR) return false;
@@ -215,7 +215,9 @@ StencilArgs make_args(const irls_plan_s* p) {
                                                                              : nullptr;
     // the folded form makes its own bf16 operands from r_U (sums and differences of mirrored
     // columns), so the stencil kernels emit none
-    if (p->opts.precision == IRLS_PREC_BF16X3 && p->dct.fold) a.r16 = a.r16lo = nullptr;
+    if ((p->opts.precision == IRLS_PREC_BF16X3 || p->opts.precision == IRLS_PREC_FP16) &&
+        p->dct.fold)
+        a.r16 = a.r16lo = nullptr;
     a.ld16 = p->dct.Wp;
     a.dir_rows = p->dir_rows ? p->dir_rows : kDefaultDirRows;
     a.upd_rows = p->upd_rows ? p->upd_rows : kDefaultUpdRows;
@@ -225,8 +227,11 @@ StencilArgs make_args(const irls_plan_s* p) {
 // Folded preconditioner on or off for the given options; false when IRLS_DCT_FOLDED is asked for
 // and the plan has no folded form (a shape or precision that does not allow it).
 bool select_dct_form(irls_plan_s* p, const irls_opts& o) {
-    const bool ready = p->dct.fold_ready && o.precision == IRLS_PREC_BF16X3;
+    const bool ready = p->dct.fold_ready &&
+                       (o.precision == IRLS_PREC_BF16X3 || o.precision == IRLS_PREC_FP16);
     if (o.dct_form == IRLS_DCT_FOLDED && !ready) return false;
+    // float16 runs in the folded form only
+    if (o.precision == IRLS_PREC_FP16 && (!ready || o.dct_form == IRLS_DCT_DIRECT)) return false;
     p->dct.fold = ready && o.dct_form != IRLS_DCT_DIRECT;
     return true;
 }
@@ -833,8 +838,10 @@ int irls_unwrap_forward_record(irls_plan p, const float* X, const float* coh, co
     if (!p || !X || !U || !out) return IRLS_ERR_ARG;
     *out = nullptr;
     if ((Cv == nullptr) != (Ch == nullptr)) return IRLS_ERR_ARG;
-    // the adjoint differentiates through converged inner solves: no planned budgets
-    if (p->opts.cg_schedule != IRLS_CG_FIXED || p->opts.system != IRLS_SYS_FULL)
+    // the adjoint differentiates through converged inner solves: no planned budgets; its
+    // right-hand sides carry no norm for the float16 scale
+    if (p->opts.cg_schedule != IRLS_CG_FIXED || p->opts.system != IRLS_SYS_FULL ||
+        p->opts.precision == IRLS_PREC_FP16)
         return IRLS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     irls_tape_s* t = new (std::nothrow) irls_tape_s();
@@ -952,7 +959,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     irls_opts_default(&o);
     if (opts) o = *opts;
     if (!opts_valid(o)) return IRLS_ERR_ARG;
-    if (o.precision == IRLS_PREC_FP32) return IRLS_ERR_UNSUPPORTED;
+    if (o.precision == IRLS_PREC_FP32 || o.precision == IRLS_PREC_FP16) return IRLS_ERR_UNSUPPORTED;
     if (o.cg_schedule != IRLS_CG_FIXED) return IRLS_ERR_UNSUPPORTED;  // images run in lockstep
     if (o.system != IRLS_SYS_FULL) return IRLS_ERR_UNSUPPORTED;
     for (int t = 0; t < ntiles; ++t)
@@ -1212,6 +1219,9 @@ int irls_precond_laplacian(irls_plan p, const float* R, float* Z, void* stream) 
         ck(cudaMemsetAsync(p->P.rU, 0, p->L.plane_bytes, s));
         ck(launch_copy_in(R, p->H, p->W, p->P.rU, p->ld, s));
         if (a.r16) ck(launch_emit16(p->P.rU, p->H, p->W, p->ld, a.r16, a.r16lo, a.ld16, s));
+        // the float16 form scales its input by ||r_U||, which no solve kernel produced here
+        if (p->opts.precision == IRLS_PREC_FP16)
+            ck(launch_norm_u(p->P, a, p->st, p->partials, s));
         ck(dct_reset(p->dct, s));
         ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, p->st, 0, a, p->partials, 0, s));
         ck(launch_copy_out(p->P.zU, p->H, p->W, p->ld, Z, s));

@@ -162,6 +162,8 @@ cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, co
                         const StencilArgs& a, DevState* st, double* partials, cudaStream_t s);
 cudaError_t launch_bnorm(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                          cudaStream_t s);
+cudaError_t launch_norm_u(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                          cudaStream_t s);
 cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevState* st,
                                      double* partials, cudaStream_t s);
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,

@@ -126,6 +126,25 @@ k_bnorm(Planes P, StencilArgs a, DevState* st, double* partials) {
     k_bnorm_body(P, a, st, partials, single_blk());
 }
 
+// ||r_U|| of the residual plane (deterministic grid reduction) into the state: the norm the
+// float16 preconditioner scales its input by, for a residual no solve kernel has produced.
+__global__ void __launch_bounds__(kThreads)
+k_norm_u(Planes P, StencilArgs a, DevState* st, double* partials) {
+    const Blk blk = single_blk();
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
+    float acc = 0.f;
+    if (j < W)
+        for (int i = i0; i < i1; ++i) {
+            const float r = P.rU[(size_t)i * ld + j];
+            acc += r * r;
+        }
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0)
+        st->rnorm_u = sqrt(tot[0]);
+}
+
 // ------------------------------------------------------------------------------------------
 // Start of an outer step: reweighting (Alg. 1, closed form W = sqrt(C^2 V^2 + delta^2)),
 // D = C^2 / W, and the initial CG residual r = b - A x of the warm start (Alg. 2).
@@ -1361,6 +1380,12 @@ cudaError_t launch_init(const float* X, const float* coh, const float* Cv_in, co
 cudaError_t launch_bnorm(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                          cudaStream_t s) {
     k_bnorm<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_u(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                          cudaStream_t s) {
+    k_norm_u<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
