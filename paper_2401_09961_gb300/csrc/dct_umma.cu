@@ -1,6 +1,6 @@
 // Tensor-core form of the Laplacian preconditioner block (Sec. 3.3 of arXiv 2401.09961): the
 // four dense products P_S^T R P_T and P_S Z' P_T^T on sm_103a tcgen05 tensor cores, bfloat16
-// operands with float32 accumulation in tensor memory.
+// (or float16) operands with float32 accumulation in tensor memory.
 //
 // Every stage is a "TN" GEMM  D[m][n] = sum_k A[m][k] B[n][k]  with both operands K-contiguous,
 // arranged so that each stage's output is again K-contiguous for the next one:
@@ -11,7 +11,7 @@
 //
 // Two forms share the building blocks below.  The direct form (any side; operands padded to
 // multiples of 128) and the grouped batched form run one output tile per CTA, structured as
-// follows.  The folded form (even sides >= 256) runs one persistent CTA-pair kernel over all four
+// follows.  The folded form (sides >= 256) runs one persistent CTA-pair kernel over all four
 // stages (k2_fold_fused, tcgen05.mma.cta_group::2, further down), with half the multiply-adds.
 //
 // Kernel structure of the direct form (one 128 x BN output tile per CTA, 128 threads):
@@ -33,6 +33,12 @@
 // and the residual of the split are below 2^-16 relative).  A single bfloat16 pass rounds at
 // 2^-9, and that error, leaked into the lowest frequencies by the forward transform, is
 // amplified by tau / (l_i + m_j) (about 1e4 at 4096 x 4096): the inner CG then stalls.
+//
+// Float16 (IRLS_PREC_FP16, folded form only): one product per multiply-add on float16 operands
+// (rounding 2^-11).  Its range is kept by scales known before each stage runs: the residual by
+// sqrt(H W) / ||r_U||, stage 2's coefficient rows by (m_l + l_1) / tau (l_1 the smallest nonzero
+// eigenvalue of the other side), which cancels the division's growth, and stage 4's basis by
+// the inverse; see UEpiArgs.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
