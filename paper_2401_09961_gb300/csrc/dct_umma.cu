@@ -1005,10 +1005,12 @@ __device__ __forceinline__ void fused_epi(uint32_t tl, const UEpiArgs& ep, int m
 }
 
 // Persistent CTA-pair kernel over the fused work list, with the warp roles and operand sets
-// described above; every MMA is M = N = 256.  An item with one operand set uses one 256-column
-// accumulator buffer (two buffers alternate); an item with two sets uses both (512 columns).  ctr[0 .. n_ctr) are the panel counters and ctr[n_ctr] counts exited
-// CTAs: the last CTA to exit zeroes them for the next launch and applies deferred stops.
-// sts[0 .. n_st) are the images' states; honour_stop: every problem skips a stopped image.
+// described above; every MMA is M = 256, N = 256 (N = 128 per set for a half-width tile).  An
+// item with one operand set uses one 256-column accumulator buffer (two buffers alternate); an
+// item with two sets uses both (512 columns).  ctr[0 .. n_ctr) are the panel counters and
+// ctr[n_ctr] counts exited CTAs: the last CTA to exit zeroes them for the next launch and applies
+// deferred stops.  sts[0 .. n_st) are the images' states; honour_stop: every problem skips a
+// stopped image.  f16: float16 operands, one product per multiply-add (no lo parts).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(k2Threads, 1)
 k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ items,
               int n_items, unsigned* __restrict__ ctr, int n_ctr, DevState* const* __restrict__ sts,
@@ -1239,7 +1241,8 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                 int ok = 1;
                 for (int k = 0; k < nbu; ++k) {
                     const int b = b0 + k;
-                    if (lane == 0 && ok) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)use[b] & 1u, &s_err);
+                    if (lane == 0 && ok)
+                        ok = mbar_wait_or_abort(&tfull[b], (uint32_t)use[b] & 1u, &s_err);
                     ++use[b];
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -1251,18 +1254,26 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                 const uint32_t tl = tmem + (uint32_t)b0 * kBuf + ((uint32_t)(q * 32) << 16);
                 WarpScratch& sc = scratch[warp - 2];
                 switch (f.epi) {
-                    case UE_FOLD16: fused_epi<128, UE_FOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
-                    case UE_EIG16: fused_epi<256, UE_EIG16>(tl, ep, m0 + q * 32, n0, part, half, sc); break;
+                    case UE_FOLD16:
+                        fused_epi<128, UE_FOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        break;
+                    case UE_EIG16:
+                        fused_epi<256, UE_EIG16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        break;
                     case UE_EIG16_RHO:
                         fused_epi<256, UE_EIG16_RHO>(tl, ep, m0 + q * 32, n0, part, half, sc);
                         break;
                     case UE_UNFOLD16:
-                        if (f.half) fused_epi<128, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
-                        else fused_epi<256, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        if (f.half)
+                            fused_epi<128, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        else
+                            fused_epi<256, UE_UNFOLD16>(tl, ep, m0 + q * 32, n0, part, half, sc);
                         break;
                     default:
-                        if (f.half) fused_epi<128, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
-                        else fused_epi<256, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        if (f.half)
+                            fused_epi<128, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
+                        else
+                            fused_epi<256, UE_UNFOLDZ>(tl, ep, m0 + q * 32, n0, part, half, sc);
                         break;
                 }
                 tc_fence_before();
@@ -1280,7 +1291,8 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
     #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                     if (lane == 0)
-                        ep.partials[((ep.rho_base + f.local) * 2 + (int)rank) * k2EpiWarps + (warp - 2)] = v;
+                        ep.partials[((ep.rho_base + f.local) * 2 + (int)rank) * k2EpiWarps +
+                                    (warp - 2)] = v;
                     if (f.rho_end) {
                         if (lane == 0) __threadfence();
                         if (!epi_sync(epibar, nsync, &s_err)) break;
@@ -1294,9 +1306,11 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                             const int n = ep.rho_count * 2 * k2EpiWarps;
                             const int e = threadIdx.x - 64;
                             double tot = 0.0;
-                            for (int i = e; i < n; i += 32 * k2EpiWarps) tot += __ldcg(&ep.partials[i]);
+                            for (int i = e; i < n; i += 32 * k2EpiWarps)
+                                tot += __ldcg(&ep.partials[i]);
     #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+                            for (int o = 16; o > 0; o >>= 1)
+                                tot += __shfl_down_sync(0xffffffffu, tot, o);
                             if (lane == 0) s_tot[warp - 2] = tot;
                             if (!epi_sync(epibar, nsync, &s_err)) break;
                             if (warp == 2 && lane == 0) {
