@@ -426,6 +426,8 @@ def batched_arm(args, rank, world, local):
     Cs = [torch.as_tensor(d["coherence"]).cuda() for d in tiles]
     mpix = sum(h * w for h, w in shapes) / 1e6
     prec = args.precision if args.precision != "fp32" else "bf16x3"
+    if prec == "fp16":
+        raise SystemExit("bench.py: the batched form runs bf16x3 or bf16 (float16 is single-image)")
     b = irls.Batch(shapes, precision=prec, tau=TAU, delta=DELTA, outer_iters=args.outer,
                    cg_tol=CG_TOL, cg_max_iter=1000, flexible_cg=1 if prec == "bf16" else 0,
                    dct_form=args.dct_form)
