@@ -99,3 +99,33 @@ def test_product_path_does_not_import_the_oracle():
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
                 assert "synthetic" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", txt,
                                                      flags=re.M), f
+
+
+def test_workspace_by_precision(L):
+    """Host-side sizing: the float16 plan holds the single-part direct buffers plus the folded
+    form's; split bf16 holds two parts of the direct buffers plus the folded form's."""
+    from paper_2401_09961_gb300 import _binding
+    n = {p: L.irls_workspace_bytes(512, 512, ctypes.byref(_binding.default_opts(precision=p)))
+         for p in ("fp32", "bf16", "fp16", "bf16x3")}
+    assert 0 < n["fp32"] < n["bf16"] < n["fp16"] < n["bf16x3"], n
+    bad = _binding.default_opts(precision=4)
+    assert L.irls_workspace_bytes(512, 512, ctypes.byref(bad)) == 0
+
+
+def test_new_entry_points_reject_null_handles(L):
+    from paper_2401_09961_gb300 import _binding
+    d, u = ctypes.c_int(), ctypes.c_int()
+    assert L.irls_plan_set_tiles(None, 8, 8) == -1
+    assert L.irls_plan_get_tiles(None, ctypes.byref(d), ctypes.byref(u)) == -1
+    assert L.irls_plan_autotune(None, None, None) == -1
+    assert L.irls_batch_set_tiles(None, 8, 8) == -1
+    assert L.irls_batch_get_tiles(None, ctypes.byref(d), ctypes.byref(u)) == -1
+    assert L.irls_batch_autotune(None, None, None) == -1
+    assert L.irls_batch_dct_form(None) == -1
+    assert L.irls_debug_stall_fold(None, 1) == -1
+    # float16 batches are refused before any device work
+    H = (ctypes.c_int * 1)(256)
+    W = (ctypes.c_int * 1)(256)
+    h = ctypes.c_void_p()
+    o = _binding.default_opts(precision="fp16")
+    assert L.irls_batch_create(1, H, W, ctypes.byref(o), ctypes.byref(h)) == -8
