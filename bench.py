@@ -10,7 +10,9 @@ between steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun every rank unwraps its own image (replicas: an unwrap does not shard) and the
-value is the total pixel rate over ranks, timed by the slowest rank.
+value is the total pixel rate over ranks, timed by the slowest rank.  With `--workload batched`
+the ranks split one set of 64 tiles per GPU by estimated cost (longest processing time first)
+and each unwraps its share as one batch.
 """
 from __future__ import annotations
 
@@ -411,16 +413,22 @@ def main():
 
 
 def batched_arm(args, rank, world, local):
-    """64 uneven tiles (sides from {256, ..., 1536}, tile t seeded 1000 + t) unwrapped together:
-    one step = one batched solve of all tiles, 20 outer steps each, split-bf16 preconditioner."""
+    """64 uneven tiles per GPU (sides from {256, ..., 1536}, tile t seeded 1000 + t) unwrapped
+    together: one step = one batched solve of the rank's tiles, 20 outer steps each,
+    split-bf16 preconditioner.  On N GPUs the job is the 64 N tiles 1000 ... 1000 + 64 N - 1,
+    split across the ranks by longest-processing-time-first on the estimated cost of a tile,
+    with no collective on the data path."""
     import torch
     import torch.distributed as dist
     import paper_2401_09961_gb300 as irls
+    from paper_2401_09961_gb300 import sharding
     import synthetic
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    tiles = synthetic.batched_tiles(n=64, seed_base=1000 + 64 * rank)
+    all_shapes = synthetic.batched_tile_shapes(n=64 * world, seed_base=1000)
+    mine = sharding.shard_tiles(all_shapes, rank, world)
+    tiles = synthetic.batched_tiles(n=64 * world, seed_base=1000, indices=mine)
     shapes = [d["X"].shape for d in tiles]
     Xs = [torch.as_tensor(d["X"]).cuda() for d in tiles]
     Cs = [torch.as_tensor(d["coherence"]).cuda() for d in tiles]
@@ -452,7 +460,7 @@ def batched_arm(args, rank, world, local):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    # each rank solves its own 64 tiles (its own seeds, so its own pixel count)
+    # each rank solves its own share of the tiles (its own pixel count)
     ms = rank_max(e0.elapsed_time(e1), world) / args.steps
     mpix_all = rank_sum(mpix, world)
     # the same tiles one at a time through single-image plans, for comparison
@@ -475,15 +483,17 @@ def batched_arm(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": f"f32+{prec}-tensor-core-dct", "data": "synthetic",
-            "config": {"workload": f"64 tiles per rank, sides in {{256,...,1536}} (non-square), "
-                                   f"{mpix:.1f} Mpix total, {args.outer} IRLS iterations, "
+            "config": {"workload": f"{64 * world} tiles, sides in {{256,...,1536}} (non-square), "
+                                   f"{mpix_all:.1f} Mpix total, {args.outer} IRLS iterations, "
                                    f"delta {DELTA:g}, tau {TAU:g}, cg_tol {CG_TOL:g}, {prec}",
                        "cg_iters_total": sum(x["cg_total"] for x in st),
                        "cg_iters_max_tile": max(x["cg_total"] for x in st),
                        "dct_form": "folded" if b.folded else "direct",
                        "stencil_tiles": {"direction_rows": b.tiles[0], "update_rows": b.tiles[1],
                                          "autotuned": tune is not None},
-                       "uses_graphs": b.uses_graphs},
+                       "uses_graphs": b.uses_graphs,
+                       "sharding": ("none" if world == 1 else
+                                    f"LPT over {world} ranks, rank 0 holds {len(mine)} tiles")},
             "single_image_sequential_mpix_s": (mpix / t_single) if t_single else None,
             "clocks": clk,
         }

@@ -180,16 +180,24 @@ def config_adjoint_1024(seed=30, H=1024, W=1024):
                       noise=0.5, coherence=True)
 
 
-def batched_tiles(n=64, seed_base=1000, sides=tuple(range(256, 1537, 128))):
-    """``n`` independent tiles with each side drawn uniformly from ``sides`` (non-square allowed),
-    tile t seeded with ``seed_base + t`` and drawn with the 2048 x 2048 law scaled to its size."""
-    tiles = []
+def batched_tile_shapes(n=64, seed_base=1000, sides=tuple(range(256, 1537, 128))):
+    """The (H, W) of each tile ``batched_tiles`` draws, without drawing the images."""
+    shapes = []
     for t in range(n):
         rng = np.random.default_rng(seed_base + t)
         H = int(rng.choice(sides))
         W = int(rng.choice(sides))
-        tiles.append(config_2048(seed=seed_base + t, H=H, W=W))
-    return tiles
+        shapes.append((H, W))
+    return shapes
+
+
+def batched_tiles(n=64, seed_base=1000, sides=tuple(range(256, 1537, 128)), indices=None):
+    """``n`` independent tiles with each side drawn uniformly from ``sides`` (non-square allowed),
+    tile t seeded with ``seed_base + t`` and drawn with the 2048 x 2048 law scaled to its size.
+    With ``indices``, only those tiles (in that order) are drawn."""
+    shapes = batched_tile_shapes(n, seed_base, sides)
+    idx = range(n) if indices is None else indices
+    return [config_2048(seed=seed_base + t, H=shapes[t][0], W=shapes[t][1]) for t in idx]
 
 
 def smooth_phase(H, W, seed, max_step=2.0):
