@@ -179,6 +179,27 @@ int irls_plan_set_tiles(irls_plan plan, int dir_rows, int upd_rows);
  * next solve is unaffected).  IRLS_ERR_UNSUPPORTED when the plan does not run the folded form.
  * Not for production use. */
 int irls_debug_stall_fold(irls_plan plan, int on);
+
+/* The folded preconditioner's persistent-launch work list (Sec. 3.3's four dense products in
+ * even / odd folded form, every tile of every stage in one list), as the launch's set-up builds
+ * it for n_img images of sizes H[t] x W[t] (host arrays) run by `pairs` CTA pairs, without any
+ * device work: for checking the schedule on a host without a GPU.  Writes the item count, the
+ * panel counter count and the launch's item capacity (all host pointers, non-NULL); with rec
+ * non-NULL and rec_items >= the item count, also IRLS_FOLD_SCHED_INTS ints per item in list
+ * order:
+ *   0 stage (0-3), 1 image, 2 tile within its problem, 3 first output row, 4 first column,
+ *   5 columns, 6 k-blocks per operand set, 7 two operand sets, 8 half-width split,
+ *   9 counter the tile completes (-1: none; each CTA of the pair adds one),
+ *   10 dependency count, 11-18 counters waited for (-1 unused), 19-26 counts waited for,
+ *   27 last tile of its pair in the image's stage-2 run, 28 r^T z slots of the image,
+ *   29-31 the problem's M, N, K, 32 the problem (index among its stage's problems, images in
+ *   order: 2 per image in stages 0 and 2, 4 in stage 1, 1 in stage 3).
+ * Pair p runs items p, p + pairs, p + 2 pairs, ... in order.  IRLS_ERR_ARG for a NULL pointer,
+ * n_img < 1, pairs < 1 or rec_items too small (the counts are still written); IRLS_ERR_SHAPE
+ * for a side below 256 (the folded form's minimum) or above 32768.  Not for production use. */
+#define IRLS_FOLD_SCHED_INTS 33
+int irls_debug_fold_schedule(int n_img, const int* H, const int* W, int pairs, int* n_items,
+                             int* n_ctr, int* cap_items, int* rec, int rec_items);
 int irls_plan_get_tiles(irls_plan plan, int* dir_rows, int* upd_rows);
 int irls_plan_autotune(irls_plan plan, float* h_ms, void* stream);
 

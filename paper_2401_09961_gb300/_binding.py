@@ -90,6 +90,8 @@ SIGNATURES = {
     "irls_plan_dct_form": (_I, [_P]),
     "irls_plan_set_tiles": (_I, [_P, _I, _I]),
     "irls_debug_stall_fold": (_I, [_P, _I]),
+    "irls_debug_fold_schedule": (_I, [_I, _P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                      ctypes.POINTER(_I), _P, _I]),
     "irls_plan_get_tiles": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "irls_plan_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
     "irls_round_congruent": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
@@ -174,3 +176,27 @@ def default_opts(**kw):
             v = SYSTEMS[v]
         setattr(o, k, v)
     return o
+
+
+FOLD_SCHED_INTS = 33
+FOLD_SCHED_FIELDS = (["stage", "image", "local", "m0", "n0", "width", "nkb", "dual", "half",
+                      "sig", "ndep"] + [f"dep{d}" for d in range(8)] +
+                     [f"need{d}" for d in range(8)] + ["rho_end", "rho_nslot", "M", "N", "K", "prob"])
+
+
+def fold_schedule(shapes, pairs):
+    """The folded preconditioner launch's work list for images of the given (H, W) shapes run
+    by `pairs` CTA pairs (host only, no device work): an int32 array with one row of
+    FOLD_SCHED_FIELDS per item in list order, the panel counter count and the item capacity."""
+    import numpy as np
+    T = len(shapes)
+    H = (ctypes.c_int * max(T, 1))(*[int(h) for h, _ in shapes])
+    W = (ctypes.c_int * max(T, 1))(*[int(w) for _, w in shapes])
+    ni, nc, cap = _I(), _I(), _I()
+    check(lib().irls_debug_fold_schedule(T, H, W, int(pairs), ctypes.byref(ni), ctypes.byref(nc),
+                                         ctypes.byref(cap), None, 0), "irls_debug_fold_schedule")
+    rec = np.zeros((ni.value, FOLD_SCHED_INTS), dtype=np.int32)
+    check(lib().irls_debug_fold_schedule(T, H, W, int(pairs), ctypes.byref(ni), ctypes.byref(nc),
+                                         ctypes.byref(cap), rec.ctypes.data, ni.value),
+          "irls_debug_fold_schedule")
+    return rec, nc.value, cap.value

@@ -1795,7 +1795,7 @@ void carve_fold_image(FoldImage& im, int H, int W, Take take) {
 bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
                           const FoldSide& sN, const FoldSide& sM, int H, int W, const float* rU,
                           float* zU, int ld, DevState* st, double* partials, int flexible,
-                          int skip, float tau, int f16 = 0) {
+                          int skip, float tau, int f16 = 0, bool encode = true) {
     const FoldDims fd = im.dim;
     const int hN = fd.hN, hM = fd.hM, hNp = fd.hNp, hMp = fd.hMp;
     // the bases' padded sides are the operands' (every tensor map below assumes it)
@@ -1814,28 +1814,32 @@ bool append_fold_problems(std::vector<GemmTile> (&tab)[4], const FoldImage& im,
     }
     int bbox = 128;
     bool halves = false;   // two-set stages: also B maps with 64-row boxes (half-width tiles)
+    // tensor maps (skipped when only the schedule is wanted: no driver call)
+    auto mm = [&](CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+        return encode ? make_map(m, ptr, rows, cols, box_rows) : true;
+    };
     auto set0 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a0, A[0], ar, ac, UBM);
-        ok &= make_map(&g.a1, A[1], ar, ac, UBM);
-        ok &= make_map(&g.b0, Bm[0], br, bc, bbox);
-        ok &= make_map(&g.b1, Bm[1], br, bc, bbox);
+        ok &= mm(&g.a0, A[0], ar, ac, UBM);
+        ok &= mm(&g.a1, A[1], ar, ac, UBM);
+        ok &= mm(&g.b0, Bm[0], br, bc, bbox);
+        ok &= mm(&g.b1, Bm[1], br, bc, bbox);
         g.a2 = g.a0; g.a3 = g.a1; g.b2 = g.b0; g.b3 = g.b1;
         if (halves) {
-            ok &= make_map(&g.bh0, Bm[0], br, bc, 64);
-            ok &= make_map(&g.bh1, Bm[1], br, bc, 64);
+            ok &= mm(&g.bh0, Bm[0], br, bc, 64);
+            ok &= mm(&g.bh1, Bm[1], br, bc, 64);
         } else {
             g.bh0 = g.b0; g.bh1 = g.b1;
         }
         g.bh2 = g.bh0; g.bh3 = g.bh1;
     };
     auto set1 = [&](GemmTile& g, void* const* A, int ar, int ac, void* const* Bm, int br, int bc) {
-        ok &= make_map(&g.a2, A[0], ar, ac, UBM);
-        ok &= make_map(&g.a3, A[1], ar, ac, UBM);
-        ok &= make_map(&g.b2, Bm[0], br, bc, bbox);
-        ok &= make_map(&g.b3, Bm[1], br, bc, bbox);
+        ok &= mm(&g.a2, A[0], ar, ac, UBM);
+        ok &= mm(&g.a3, A[1], ar, ac, UBM);
+        ok &= mm(&g.b2, Bm[0], br, bc, bbox);
+        ok &= mm(&g.b3, Bm[1], br, bc, bbox);
         if (halves) {
-            ok &= make_map(&g.bh2, Bm[0], br, bc, 64);
-            ok &= make_map(&g.bh3, Bm[1], br, bc, 64);
+            ok &= mm(&g.bh2, Bm[0], br, bc, 64);
+            ok &= mm(&g.bh3, Bm[1], br, bc, 64);
         }
     };
     // Every operand is stored padded (extents hNp, hMp, Hp, multiples of 256); padding rows and
@@ -2386,6 +2390,82 @@ void umma_dct_release(DctPlan& d) {
     delete static_cast<FoldBufs*>(d.fold_host);
     d.fold_host = nullptr;
     d.fold = d.fold_ready = 0;
+}
+
+// The fused folded launch's work list for images H[t] x W[t] run by `pairs` CTA pairs, built on
+// the host exactly as the launch's set-up builds it, but with no tensor maps and no device
+// memory (operand pointers are null).  Per item, kFoldSchedInts ints: stage (0-3), image, tile
+// within its problem, first row, first column, columns, k-blocks per operand set, two operand
+// sets, half width, counter completed (-1: none), dependency count, 8 counters waited for, 8
+// counts waited for, r^T z run end, r^T z slot count, the problem's M, N and K, the problem
+// among its stage's problems.  Also the counter count and the launch's item capacity.  False
+// on a side below 256 (the folded form's minimum) or above 32768, or on a table the builders
+// reject.
+bool fold_schedule(const int* H, const int* W, int T, int pairs, int& n_items, int& n_ctr,
+                   int& cap_items, std::vector<int>& rec) {
+    if (T < 1 || pairs < 1) return false;
+    std::vector<GemmTile> tab[4];
+    std::vector<std::vector<float>> lam(2 * T);
+    int est_items = 0, est_ctrs = 0;
+    for (int t = 0; t < T; ++t) {
+        if (H[t] < 256 || W[t] < 256 || H[t] > 32768 || W[t] > 32768) return false;
+        FoldImage im{};
+        im.dim = fold_dims(H[t], W[t]);
+        FoldSide sN{}, sM{};
+        sN.n = H[t];
+        sN.hp = im.dim.hNp;
+        sM.n = W[t];
+        sM.hp = im.dim.hMp;
+        lam[2 * t].assign(2 * (size_t)sN.hp, 0.f);
+        lam[2 * t + 1].assign(2 * (size_t)sM.hp, 0.f);
+        sN.lamP = lam[2 * t].data();
+        sM.lamP = lam[2 * t + 1].data();
+        if (!append_fold_problems(tab, im, sN, sM, H[t], W[t], nullptr, nullptr, W[t], nullptr,
+                                  nullptr, 0, 1, 1e-2f, 0, false))
+            return false;
+        int it = 0, ct = 0;
+        fused_counts(H[t], W[t], it, ct);
+        est_items += it;
+        est_ctrs += ct;
+    }
+    int tiles[4];
+    if (!number_fold_tiles(tab, tiles)) return false;
+    std::vector<GemmTile> probs;
+    std::vector<FoldItem> items;
+    if (!build_fused(tab, std::vector<int>(H, H + T), pairs, 1, probs, items, n_ctr)) return false;
+    if (n_ctr != est_ctrs) return false;
+    n_items = (int)items.size();
+    cap_items = est_items + kMaxSplit;
+    const int off[4] = {0, 2 * T, 6 * T, 8 * T}, per[4] = {2, 4, 2, 1};
+    rec.assign((size_t)n_items * kFoldSchedInts, 0);
+    for (int i = 0; i < n_items; ++i) {
+        const FoldItem& f = items[i];
+        const GemmTile& g = probs[f.prob];
+        const int k = f.epi == UE_FOLD16 ? 0 : f.epi == UE_UNFOLD16 ? 2 : f.epi == UE_UNFOLDZ ? 3 : 1;
+        int* r = rec.data() + (size_t)i * kFoldSchedInts;
+        r[0] = k;
+        r[1] = (f.prob - off[k]) / per[k];
+        r[2] = f.local;
+        r[3] = f.m0;
+        r[4] = f.n0;
+        r[5] = (f.half || k == 0) ? 128 : 256;
+        r[6] = f.nkb;
+        r[7] = f.dual;
+        r[8] = f.half;
+        r[9] = f.sig;
+        r[10] = f.ndep;
+        for (int d = 0; d < kMaxDeps; ++d) {
+            r[11 + d] = d < f.ndep ? f.dep[d] : -1;
+            r[19 + d] = d < f.ndep ? f.need[d] : 0;
+        }
+        r[27] = f.rho_end;
+        r[28] = f.rho_nslot;
+        r[29] = g.M;
+        r[30] = g.N;
+        r[31] = g.K;
+        r[32] = f.prob - off[k];
+    }
+    return true;
 }
 
 size_t umma_dct_bytes(int H, int W, int prec) {

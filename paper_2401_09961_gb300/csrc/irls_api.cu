@@ -714,6 +714,28 @@ int irls_debug_stall_fold(irls_plan p, int on) {
     return dct_stall(p->dct, on) ? IRLS_OK : IRLS_ERR_UNSUPPORTED;
 }
 
+int irls_debug_fold_schedule(int n_img, const int* H, const int* W, int pairs, int* n_items,
+                             int* n_ctr, int* cap_items, int* rec, int rec_items) {
+    if (n_img < 1 || pairs < 1 || !H || !W || !n_items || !n_ctr || !cap_items)
+        return IRLS_ERR_ARG;
+    for (int t = 0; t < n_img; ++t)
+        if (H[t] < 256 || W[t] < 256 || H[t] > 32768 || W[t] > 32768) return IRLS_ERR_SHAPE;
+    try {
+        std::vector<int> r;
+        int ni = 0, nc = 0, cap = 0;
+        if (!fold_schedule(H, W, n_img, pairs, ni, nc, cap, r)) return IRLS_ERR_SHAPE;
+        *n_items = ni;
+        *n_ctr = nc;
+        *cap_items = cap;
+        if (!rec) return IRLS_OK;
+        if (rec_items < ni) return IRLS_ERR_ARG;
+        std::copy(r.begin(), r.end(), rec);
+        return IRLS_OK;
+    } catch (...) {
+        return IRLS_ERR_OOM;
+    }
+}
+
 int irls_plan_set_tiles(irls_plan p, int dir_rows, int upd_rows) {
     if (!p) return IRLS_ERR_ARG;
     if ((dir_rows != 0 && !tile_rows_ok(dir_rows)) || (upd_rows != 0 && !tile_rows_ok(upd_rows)))

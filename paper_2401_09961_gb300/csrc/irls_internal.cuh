@@ -221,6 +221,10 @@ void dct_release(DctPlan& d);
 cudaError_t dct_reset(const DctPlan& d, cudaStream_t s);
 // test hook: the folded launch's dependency waits run out (IRLS_ERR_TIMEOUT path)
 bool dct_stall(DctPlan& d, int on);
+// host-only: the fused folded launch's work list, kFoldSchedInts ints per item (dct_umma.cu)
+constexpr int kFoldSchedInts = IRLS_FOLD_SCHED_INTS;
+bool fold_schedule(const int* H, const int* W, int T, int pairs, int& n_items, int& n_ctr,
+                   int& cap_items, std::vector<int>& rec);
 cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
                                   double* partials, cudaStream_t s);
 cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
