@@ -64,7 +64,8 @@ extern "C" {
 #define IRLS_DCT_DIRECT 1   /* four full-size products per application                            */
 #define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds, all four
                              * stages in one persistent launch; needs precision IRLS_PREC_BF16X3
-                             * and H, W >= 256 (odd or even)                                     */
+                             * or IRLS_PREC_FP16 (which always runs it) and H, W >= 256 (odd or
+                             * even); otherwise plan creation returns IRLS_ERR_UNSUPPORTED       */
 
 /* Inner-solve budget (Sec. 4.3). */
 #define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
