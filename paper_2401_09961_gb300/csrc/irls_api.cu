@@ -986,7 +986,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     if (o.system != IRLS_SYS_FULL) return IRLS_ERR_UNSUPPORTED;
     for (int t = 0; t < ntiles; ++t)
         if (!shape_valid(H[t], W[t])) return IRLS_ERR_SHAPE;
-    // folded preconditioner when every image allows it (split precision, even sides >= 256)
+    // folded preconditioner when every image allows it (split precision, sides >= 256, odd or even)
     bool all_fold = true;
     for (int t = 0; t < ntiles; ++t)
         all_fold &= foldable(H[t], W[t], o.precision == IRLS_PREC_BF16X3 ? 1 : 0);

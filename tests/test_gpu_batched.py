@@ -83,7 +83,7 @@ def test_batched_matches_oracle(irls):
 
 
 def test_batched_folded_form_only_where_every_image_allows_it(irls):
-    """The folded form needs the split precision and even sides >= 256 in every image."""
+    """The folded form needs the split precision and sides >= 256 in every image."""
     for shapes, prec in (([(256, 256), (256, 250)], "bf16x3"), ([(256, 256), (255, 256)], "bf16x3"),
                          ([(256, 256)], "bf16")):
         with pytest.raises(irls.IrlsError) as e:
