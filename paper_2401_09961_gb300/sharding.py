@@ -7,7 +7,8 @@ give each tile to the rank with the least load so far), whose makespan is within
 4/3 - 1/(3m) of the optimum on m ranks (Graham, 1969).  Every rank computes the same split
 from the same shape list, so no exchange is needed to agree on it.
 
-Plain host arithmetic, no device work.
+The split is plain host arithmetic; `unwrap_sharded` runs one rank's share through the batched
+solver.
 """
 from __future__ import annotations
 
@@ -79,3 +80,47 @@ def shard_tiles(shapes, rank, world):
 def part_loads(shapes, parts):
     """Estimated seconds per CG iteration of each part (sum of its tiles' costs)."""
     return [sum(tile_cost(*shapes[i]) for i in p) for p in parts]
+
+
+def unwrap_sharded(Xs, cohs=None, rank=None, world=None, device="cuda", batch=None, **opts):
+    """Unwraps this rank's share of the images `Xs` (2-D tensors; `cohs` their coherences or
+    None) as one batched solve on `device`.
+
+    `rank` and `world` default to those of the initialised torch.distributed process group
+    (0 and 1 without one).  Only this rank's images are copied to `device` (as contiguous
+    float32), so `Xs` may stay in host memory.  No collective is issued; a process that needs
+    every result gathers them itself.  `batch` builds the solver from the share's shapes and
+    `opts` (default: the package's Batch).  Returns (indices, Us, stats) for this rank's images,
+    in ascending index order; all three are empty when the rank has no image.
+    """
+    import torch
+    if rank is None or world is None:
+        r, w = 0, 1
+        if torch.distributed.is_available() and torch.distributed.is_initialized():
+            r, w = torch.distributed.get_rank(), torch.distributed.get_world_size()
+        rank = r if rank is None else rank
+        world = w if world is None else world
+    if cohs is not None and len(cohs) != len(Xs):
+        raise ValueError("one coherence per image")
+    shapes = []
+    for X in Xs:
+        if X.dim() != 2:
+            raise ValueError("images must be 2-D")
+        shapes.append((int(X.shape[0]), int(X.shape[1])))
+    mine = shard_tiles(shapes, rank, world)
+    if not mine:
+        return [], [], []
+    if batch is None:
+        from . import Batch as batch
+
+    def put(t):
+        return t.to(device=device, dtype=torch.float32).contiguous()
+
+    Xm = [put(Xs[i]) for i in mine]
+    Cm = None if cohs is None else [put(cohs[i]) for i in mine]
+    b = batch([shapes[i] for i in mine], **opts)
+    try:
+        Us, stats = b.unwrap(Xm, Cm)
+    finally:
+        b.close()
+    return mine, Us, stats

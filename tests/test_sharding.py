@@ -140,3 +140,92 @@ def test_two_gloo_ranks_agree_without_exchange():
     import synthetic
     shapes = synthetic.batched_tile_shapes(n=128, seed_base=1000)
     assert [m0, m1] == sharding.lpt_partition([sharding.tile_cost(*s) for s in shapes], 2)
+
+
+class FakeBatch:
+    """Stands in for the GPU batch: records what it was given and returns X + 1 as U."""
+    made = []
+
+    def __init__(self, shapes, **opts):
+        self.shapes, self.opts, self.closed = list(shapes), opts, False
+        FakeBatch.made.append(self)
+
+    def unwrap(self, Xs, cohs=None):
+        assert [tuple(X.shape) for X in Xs] == self.shapes
+        assert all(X.dtype.is_floating_point and X.is_contiguous() for X in Xs)
+        self.cohs = cohs
+        return [X + 1 for X in Xs], [{"cg_total": int(X.numel())} for X in Xs]
+
+    def close(self):
+        self.closed = True
+
+
+def _images(n=9, seed=0):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.integers(256, 700)), int(rng.integers(256, 700))) for _ in range(n)]
+    return [torch.full(s, float(i), dtype=torch.float64) for i, s in enumerate(shapes)]
+
+
+def test_unwrap_sharded_takes_this_ranks_share():
+    Xs = _images()
+    cohs = [X * 0 + 0.5 for X in Xs]
+    got = {}
+    for r in range(3):
+        FakeBatch.made.clear()
+        idx, Us, st = sharding.unwrap_sharded(Xs, cohs, rank=r, world=3, device="cpu",
+                                              batch=FakeBatch, precision="bf16x3")
+        assert idx == sharding.shard_tiles([tuple(X.shape) for X in Xs], r, 3)
+        b, = FakeBatch.made
+        assert b.closed and b.opts == {"precision": "bf16x3"} and len(b.cohs) == len(idx)
+        for i, U in zip(idx, Us):
+            assert U.dtype.is_floating_point and float(U[0, 0]) == i + 1
+            got[i] = U
+        assert [s["cg_total"] for s in st] == [Xs[i].numel() for i in idx]
+    assert sorted(got) == list(range(len(Xs)))
+
+
+def test_unwrap_sharded_edges():
+    Xs = _images(2)
+    idx, Us, st = sharding.unwrap_sharded(Xs, rank=3, world=4, device="cpu", batch=FakeBatch)
+    assert (idx, Us, st) == ([], [], [])
+    with pytest.raises(ValueError):
+        sharding.unwrap_sharded(Xs, [Xs[0]], rank=0, world=1, device="cpu", batch=FakeBatch)
+    with pytest.raises(ValueError):
+        sharding.unwrap_sharded([Xs[0][0]], rank=0, world=1, device="cpu", batch=FakeBatch)
+    # no process group: the whole list on one rank
+    idx, _, _ = sharding.unwrap_sharded(Xs, device="cpu", batch=FakeBatch)
+    assert idx == [0, 1]
+
+
+def _unwrap_rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        Xs = _images(11, seed=5)
+        idx, Us, _ = sharding.unwrap_sharded(Xs, device="cpu", batch=FakeBatch)
+        vals = [float(U[0, 0]) for U in Us]
+        out.put((rank, idx, vals))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_unwrap_sharded_under_two_gloo_ranks():
+    """rank and world come from the process group; the two shares cover every image once."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    port = _free_port()
+    procs = [ctx.Process(target=_unwrap_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get() for _ in range(2))
+    assert sorted(res[0][1] + res[1][1]) == list(range(11))
+    assert not set(res[0][1]) & set(res[1][1])
+    for _, idx, vals in res:
+        assert vals == [i + 1.0 for i in idx]
