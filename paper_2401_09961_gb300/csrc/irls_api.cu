@@ -342,17 +342,21 @@ void copy_plane(float* dst, const float* src, size_t bytes, cudaStream_t s) {
 int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv, const float* Ch,
               const float* U0, const float* Vv0, const float* Vh0, cudaStream_t s,
               irls_stats* stats, irls_tape_s* tape = nullptr) {
+    TraceRange trace("irls_unwrap");
     const StencilArgs a = make_args(p);
     DevState* st = p->st;
     Profiler& pf = p->prof;
     const size_t pb = p->L.plane_bytes;
     cudaEvent_t t0;
-    ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-    ck(dct_reset(p->dct, s));
-    t0 = pf.begin(s);
-    ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
-    ck(launch_bnorm(p->P, a, st, p->partials, s));
-    pf.end(PC_INIT, t0, s);
+    {
+        TraceRange r("irls_init");
+        ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+        ck(dct_reset(p->dct, s));
+        t0 = pf.begin(s);
+        ck(launch_init(X, coh, Cv, Ch, U0, Vv0, Vh0, p->P, a, st, p->partials, s));
+        ck(launch_bnorm(p->P, a, st, p->partials, s));
+        pf.end(PC_INIT, t0, s);
+    }
     // stop early on invalid input
     ck(cudaMemcpyAsync(&p->h_flag[0], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
@@ -372,9 +376,13 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
     p->schedule_stop = 0;
     const bool schur = p->opts.system == IRLS_SYS_SCHUR;
     for (int k = 0; k < p->opts.outer_iters; ++k) {
+        TraceRange r_outer("irls_outer");
         t0 = pf.begin(s);
-        if (schur) ck(launch_schur_reweight(p->P, a, st, p->partials, s));
-        else ck(launch_reweight_residual(p->P, a, st, p->partials, s));
+        {
+            TraceRange r("irls_reweight");
+            if (schur) ck(launch_schur_reweight(p->P, a, st, p->partials, s));
+            else ck(launch_reweight_residual(p->P, a, st, p->partials, s));
+        }
         pf.end(PC_REWEIGHT, t0, s);
         StencilArgs ak = a;
         if (sched) {
@@ -403,13 +411,19 @@ int run_solve(irls_plan_s* p, const float* X, const float* coh, const float* Cv,
             ak.cap_warn = ak.cg_max >= p->opts.cg_max_iter ? 1 : 0;
         }
         p->caps[k] = ak.cg_max;
+        {
+            TraceRange r("irls_pcg");
+            t0 = pf.begin(s);
+            ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, ak, p->partials, 1, s));
+            pf.end(PC_DCT, t0, s);
+            run_cg(p, ak, st, s);
+        }
         t0 = pf.begin(s);
-        ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, ak, p->partials, 1, s));
-        pf.end(PC_DCT, t0, s);
-        run_cg(p, ak, st, s);
-        t0 = pf.begin(s);
-        if (schur) ck(launch_schur_recover_v(p->P, ak, s));
-        ck(launch_finalize(p->P, ak, st, p->partials, s));
+        {
+            TraceRange r("irls_finalize");
+            if (schur) ck(launch_schur_recover_v(p->P, ak, s));
+            ck(launch_finalize(p->P, ak, st, p->partials, s));
+        }
         pf.end(PC_FINALIZE, t0, s);
         if (tape) {
             copy_plane(tape->Vv[k + 1], p->P.Vv, pb, s);
@@ -544,6 +558,7 @@ void prepare_graphs(irls_batch_s* b) {
 
 int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, float* const* U,
               irls_stats* stats, cudaStream_t user) {
+    TraceRange trace("irls_batch_unwrap");
     const int T = b->T;
     cudaStream_t s = b->stream;
     // order after the caller's stream
@@ -567,27 +582,32 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
     if (bad) return ST_NONFINITE;
     prepare_graphs(b);
     for (int k = 0; k < b->opts.outer_iters; ++k) {
+        TraceRange r_outer("irls_outer");
         ck(launch_reweight_batched(b->d_recs, T, b->total_strip, s));
-        ck(batch_dct_apply(b->dct, s));
-        int issued = 0, slot = 0;
-        bool pending = false;
-        while (issued < b->opts.cg_max_iter) {
-            const int n = std::min(kChunk, b->opts.cg_max_iter - issued);
-            if (n == kChunk && b->chunk[slot])
-                ck(cudaGraphLaunch(b->chunk[slot], s));
-            else
-                issue_chunk(b, n, slot, s);
-            issued += n;
-            ck(cudaMemcpyAsync(&b->h_count[slot], b->d_count + slot, sizeof(int),
-                               cudaMemcpyDeviceToHost, s));
-            ck(cudaEventRecord(b->ev[slot], s));
-            if (pending) {
-                ck(cudaEventSynchronize(b->ev[slot ^ 1]));
-                if (b->h_count[slot ^ 1] == 0) break;
+        {
+            TraceRange r_pcg("irls_pcg");
+            ck(batch_dct_apply(b->dct, s));
+            int issued = 0, slot = 0;
+            bool pending = false;
+            while (issued < b->opts.cg_max_iter) {
+                const int n = std::min(kChunk, b->opts.cg_max_iter - issued);
+                if (n == kChunk && b->chunk[slot])
+                    ck(cudaGraphLaunch(b->chunk[slot], s));
+                else
+                    issue_chunk(b, n, slot, s);
+                issued += n;
+                ck(cudaMemcpyAsync(&b->h_count[slot], b->d_count + slot, sizeof(int),
+                                   cudaMemcpyDeviceToHost, s));
+                ck(cudaEventRecord(b->ev[slot], s));
+                if (pending) {
+                    ck(cudaEventSynchronize(b->ev[slot ^ 1]));
+                    if (b->h_count[slot ^ 1] == 0) break;
+                }
+                pending = true;
+                slot ^= 1;
             }
-            pending = true;
-            slot ^= 1;
         }
+        TraceRange r_fin("irls_finalize");
         ck(launch_finalize_batched(b->d_recs, T, b->total_strip, s));
     }
     for (int t = 0; t < T; ++t)
@@ -927,8 +947,10 @@ int irls_unwrap_backward(irls_tape t, const float* dLdU, float* dLdX, float* dLd
         ck(cudaMemsetAsync(st, 0, sizeof(DevState), s));
         ck(dct_reset(p->dct, s));
         for (float* z : {t->Gbv, t->Gbh, t->Cbv, t->Cbh}) ck(cudaMemsetAsync(z, 0, pb, s));
+        TraceRange trace("irls_backward");
         ck(launch_adj_init(p->P, a, dLdU, st, p->partials, s));
         for (int k = t->K - 1; k >= 0; --k) {
+            TraceRange r_step("irls_backward_step");
             ck(launch_adj_setup(p->P, a, t->Vv[k], t->Vh[k], t->Cv, t->Ch, st, p->partials, s));
             ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
             run_cg(p, a, st, s);

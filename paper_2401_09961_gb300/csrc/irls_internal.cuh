@@ -8,9 +8,21 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/irls.h"
 
 namespace irls {
+
+// A named NVTX range over the host thread's span of a phase, so that Nsight tools can attribute
+// and filter the kernels launched in it (e.g. ncu --nvtx --nvtx-include "irls_unwrap/irls_pcg/").
+// Without an attached tool each push and pop is a no-op call.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 constexpr int kMaxOuter = IRLS_MAX_OUTER;
 
