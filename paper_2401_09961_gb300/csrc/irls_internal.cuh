@@ -8,7 +8,12 @@
 
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define IRLS_HAVE_NVTX 1
+#else
+#define IRLS_HAVE_NVTX 0
+#endif
 
 #include "../../include/irls.h"
 
@@ -16,10 +21,15 @@ namespace irls {
 
 // A named NVTX range over the host thread's span of a phase, so that Nsight tools can attribute
 // and filter the kernels launched in it (e.g. ncu --nvtx --nvtx-include "irls_unwrap/irls_pcg/").
-// Without an attached tool each push and pop is a no-op call.
+// Without an attached tool each push and pop is a no-op call; without the NVTX headers in the
+// toolkit the ranges are compiled out.
 struct TraceRange {
+#if IRLS_HAVE_NVTX
     explicit TraceRange(const char* name) { nvtxRangePushA(name); }
     ~TraceRange() { nvtxRangePop(); }
+#else
+    explicit TraceRange(const char*) {}
+#endif
     TraceRange(const TraceRange&) = delete;
     TraceRange& operator=(const TraceRange&) = delete;
 };
