@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "TWO_PI_F32", "PI_F32", "wrap_f32", "wrapped_gradients", "edge_weights",
-    "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d",
+    "S_op", "St_op", "T_op", "Tt_op", "rhs_b", "apply_A", "reweight", "diag_d", "dD_dV", "dD_dC",
     "dct_basis", "precond_apply", "pcg", "l1_objective", "F_value", "F_delta_value",
     "H_delta_value", "gradient_candidate", "smoothness_L", "irls_unwrap", "paper_cg_cap", "k_map",
     "round_congruent", "schur_weights", "schur_matvec", "schur_rhs", "schur_recover_v",
@@ -119,6 +119,18 @@ def diag_d(Cv, Ch, Wv, Wh):
     return Cv * Cv / Wv, Ch * Ch / Wh
 
 
+def dD_dV(C, V, W):
+    """Derivative of D = C^2 / W with W = sqrt(C^2 V^2 + delta^2) (Sec. 3.1) in V, per edge:
+    dD/dV = -C^2 / W^2 * dW/dV = -C^4 V / W^3."""
+    return -(C ** 4) * V / W ** 3
+
+
+def dD_dC(C, V, W):
+    """Derivative of D = C^2 / W in C, per edge: 2 C / W - C^2 / W^2 * dW/dC
+    = 2 C / W - C^3 V^2 / W^3."""
+    return 2.0 * C / W - C ** 3 * V ** 2 / W ** 3
+
+
 def rhs_b(Gv, Gh, tau):
     """b = (B1, B2, B3) with B1 = (S^T Gv + Gh T^T) / tau, B2 = -Gv / tau, B3 = -Gh / tau
     (Sec. 3.2, definition of B1, B2, B3)."""
@@ -196,7 +208,7 @@ def _stored(v, storage):
 
 
 def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None,
-        precond_rounding=None, scalar_rounding=None):
+        precond_rounding=None):
     """Preconditioned CG (Alg. 2) on A x = b from the warm start x0.
 
     Stops when ||r|| / ||b|| <= tol or after cg_max products with A.  ``beta_rule`` 'fr' is the
@@ -207,14 +219,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
     executions spread; the arithmetic itself stays float64.  ``precond_rounding`` (None or
     (rel, seed)) multiplies each preconditioner output by 1 + rel * N(0, 1) elementwise (seeded):
     a model of the preconditioner evaluated at finite precision, for the same purpose.
-    ``scalar_rounding`` (None or (rel, seed)) multiplies alpha and beta by 1 + rel * N(0, 1): a
-    model of the inner products summed from float32 partial sums.
     Returns (x, iterations, final relative residual, status); status -5 flags a breakdown."""
-    rng_sc = None if scalar_rounding is None else np.random.default_rng(scalar_rounding[1])
-
-    def scal(v):
-        return v if rng_sc is None else v * (1.0 + scalar_rounding[0] * rng_sc.standard_normal())
-
     if precond_rounding is not None:
         rel_pc, seed_pc = precond_rounding
         rng_pc = np.random.default_rng(seed_pc)
@@ -241,7 +246,7 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
         pq = _dot(p, q)
         if not (pq > 0.0 and rho > 0.0):
             return x, it, rel, -5
-        alpha = scal(rho / pq)
+        alpha = rho / pq
         x = _stored(_axpy(alpha, p, x), storage)
         r = _stored(_axpy(-alpha, q, r), storage)
         it += 1
@@ -251,9 +256,9 @@ def pcg(x0, b, dv, dh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", stora
         z_new = _stored(precond(r), storage)
         rho_new = _dot(r, z_new)
         if beta_rule == "pr":
-            beta = scal((rho_new - _dot(r, z)) / rho)
+            beta = (rho_new - _dot(r, z)) / rho
         else:
-            beta = scal(rho_new / rho)
+            beta = rho_new / rho
         rho = rho_new
         z = z_new
         p = _stored(tuple(zi + beta * pi for zi, pi in zip(z_new, p)), storage)
@@ -286,19 +291,13 @@ def schur_recover_v(U, Gv, Gh, dv, dh, tau):
     return (S_op(U) - Gv) / (1.0 + tau * dv), (T_op(U) - Gh) / (1.0 + tau * dh)
 
 
-def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None,
-              scalar_rounding=None):
+def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr", storage=None):
     """Alg. 2 on L_Om U = f from the warm start U0, preconditioned by the Laplacian block of
     Sec. 3.3 (z = P_S [(P_S^T tau r P_T) / (lam_i + mu_j)] P_T^T, zero frequency dropped; Om <=
     1/tau, so (1/tau) times the Laplacian is its upper bound).  Stops when ||r|| / ||f|| <= tol
-    or after cg_max products with L_Om.  storage and scalar_rounding as in pcg.
+    or after cg_max products with L_Om.  storage as in pcg.
     Returns (U, iterations, relative residual, status)."""
     N, M = f.shape
-    rng_sc = None if scalar_rounding is None else np.random.default_rng(scalar_rounding[1])
-
-    def scal(v):
-        return v if rng_sc is None else v * (1.0 + scalar_rounding[0] * rng_sc.standard_normal())
-
     zeros_v, zeros_h = np.zeros((N - 1, M)), np.zeros((N, M - 1))
 
     def prec(r):
@@ -323,7 +322,7 @@ def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr",
         pq = float(np.vdot(p, q))
         if not (pq > 0.0 and rho > 0.0):
             return U, it, rel, -5
-        alpha = scal(rho / pq)
+        alpha = rho / pq
         U = keep(U + alpha * p)
         r = keep(r - alpha * q)
         it += 1
@@ -332,7 +331,7 @@ def pcg_schur(U0, f, Ov, Oh, tau, basis_N, basis_M, tol, cg_max, beta_rule="fr",
             return U, it, rel, 0
         z_new = keep(prec(r))
         rho_new = float(np.vdot(r, z_new))
-        beta = scal((rho_new - float(np.vdot(r, z))) / rho if beta_rule == "pr" else rho_new / rho)
+        beta = (rho_new - float(np.vdot(r, z))) / rho if beta_rule == "pr" else rho_new / rho
         rho, z = rho_new, z_new
         p = keep(z_new + beta * p)
 
@@ -428,7 +427,7 @@ def paper_cg_cap(delta_rel, m_prev, raised_prev, eps_tol, alpha):
 def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, outer_iters=10,
                 cg_tol=1e-5, cg_max=1000, beta_rule="fr", x0=None, record=False, storage=None,
                 cg_schedule="fixed", m0=5, eps_tol=1e-3, alpha=1.7, precond_rounding=None,
-                system="full", scalar_rounding=None, cg_caps=None):
+                system="full", cg_caps=None):
     """Alg. 1 with Alg. 2 as the inner solver.
 
     cg_schedule "fixed": outer_iters IRLS iterations, every inner solve capped at cg_max.
@@ -441,8 +440,8 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
     each solve), delta_rel (Delta_{k-1,k} for k >= 1, "paper" only), schedule_stop and h_stop
     (H_delta(x^k, W^k) at the iteration where the rule stopped the run), status.
     With ``record`` the per-outer weights W^k and iterates are kept too (used by the adjoint).
-    ``storage``, ``precond_rounding`` and ``scalar_rounding`` are passed to pcg (other valid
-    floating-point executions; the seeds advance with the outer iteration).  ``cg_caps`` (a list)
+    ``storage`` and ``precond_rounding`` are passed to pcg (other valid floating-point
+    executions; the latter's seed advances with the outer iteration).  ``cg_caps`` (a list)
     caps solve k at cg_caps[k] (with cg_tol = 0: exactly that many iterations), to replay another
     execution's stopping decisions.
     system "full": Alg. 2 on the (U, Vv, Vh) system of Sec. 3.1 with the block-diagonal
@@ -488,19 +487,17 @@ def irls_unwrap(X, coherence=None, *, Cv=None, Ch=None, tau=1e-2, delta=1e-3, ou
             rec["x"].append((U.copy(), Vv.copy(), Vh.copy()))
         st["h_before"].append(h_before)
         st["cg_cap"].append(cap)
-        sr = None if scalar_rounding is None else (scalar_rounding[0],
-                                                   scalar_rounding[1] + 7919 * k)
         if system == "schur":
             Ov, Oh = schur_weights(dv, dh, tau)
             f = schur_rhs(pb.Gv, pb.Gh, Ov, Oh, N, M)
             U, it, rel, s = pcg_schur(U, f, Ov, Oh, tau, pb.basis_N, pb.basis_M, cg_tol, cap,
-                                      beta_rule, storage, sr)
+                                      beta_rule, storage)
             Vv, Vh = schur_recover_v(U, pb.Gv, pb.Gh, dv, dh, tau)
         else:
             pr = None if precond_rounding is None else (precond_rounding[0],
                                                         precond_rounding[1] + 7919 * k)
             (U, Vv, Vh), it, rel, s = pcg((U, Vv, Vh), pb.b, dv, dh, tau, pb.basis_N, pb.basis_M,
-                                          cg_tol, cap, beta_rule, storage, pr, sr)
+                                          cg_tol, cap, beta_rule, storage, pr)
         if s < 0:
             status = s
         elif it >= cap and cap >= cg_max and rel > cg_tol and status == 0:
@@ -640,10 +637,10 @@ def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, c
         Gbv += (S_op(lu) - lv) / tau
         Gbh += (T_op(lu) - lh) / tau
         Dbv, Dbh = -lv * Vv_n, -lh * Vh_n
-        Vbv = Dbv * (-(Cv ** 4) * Vv_k / Wv ** 3)
-        Vbh = Dbh * (-(Ch ** 4) * Vh_k / Wh ** 3)
-        Cbv += Dbv * (2.0 * Cv / Wv - Cv ** 3 * Vv_k ** 2 / Wv ** 3)
-        Cbh += Dbh * (2.0 * Ch / Wh - Ch ** 3 * Vh_k ** 2 / Wh ** 3)
+        Vbv = Dbv * dD_dV(Cv, Vv_k, Wv)
+        Vbh = Dbh * dD_dV(Ch, Vh_k, Wh)
+        Cbv += Dbv * dD_dC(Cv, Vv_k, Wv)
+        Cbh += Dbh * dD_dC(Ch, Vh_k, Wh)
         xbar = (np.zeros((N, M)), Vbv, Vbh)
     # V^0 = -G
     Gbv -= xbar[1]

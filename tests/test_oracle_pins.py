@@ -714,13 +714,13 @@ def _adjoint_case():
     return X, coh, Uref, kw
 
 
-def test_adjoint_matches_central_differences():
-    """dL/dX and dL/dcoherence of L = sum (U - U_ref)^2 through 3 IRLS steps with converged
-    solves.  X: Richardson-extrapolated central differences with steps 2e-2 and 1e-2 (the
-    float32 wrap rounds X +- h, so smaller steps only add noise; pixels whose incident wrapped
-    differences stay below pi - 0.05); coherence: steps of 1e-3."""
-    X, coh, Uref, kw = _adjoint_case()
-
+def _adjoint_fd_mismatches(X, coh, Uref, kw):
+    """Compares the oracle adjoint's dL/dX and dL/dcoherence (L = sum (U - U_ref)^2 through 3
+    IRLS steps with converged solves) with central differences of the oracle's own forward map.
+    X: Richardson-extrapolated central differences with steps 2e-2 and 1e-2 (the float32 wrap
+    rounds X +- h, so smaller steps only add noise; pixels whose incident wrapped differences
+    stay below pi - 0.05); coherence: steps of 1e-3.  Returns the pixels that disagree and the
+    number of X pixels checked."""
     def L(Xa, ca):
         return float(np.sum((O.irls_unwrap(Xa, ca, **kw)["U"] - Uref) ** 2))
 
@@ -728,7 +728,7 @@ def test_adjoint_matches_central_differences():
     gX, gC, _ = O.irls_adjoint(X, coh, 2 * (r0["U"] - Uref), **kw)
     Gv, Gh = O.wrapped_gradients(X)
     N, M = X.shape
-    checked = 0
+    checked, bad = 0, []
     for i, j in [(3, 4), (6, 2), (0, 0), (11, 9), (5, 5), (8, 1)]:
         inc = [abs(Gv[i - 1, j]) if i > 0 else 0, abs(Gv[i, j]) if i < N - 1 else 0,
                abs(Gh[i, j - 1]) if j > 0 else 0, abs(Gh[i, j]) if j < M - 1 else 0]
@@ -741,27 +741,124 @@ def test_adjoint_matches_central_differences():
             # Richardson extrapolation of steps 2e-2 and 1e-2 (cancels the O(h^2) term)
             fd = (4.0 * cd(1e-2) - cd(2e-2)) / 3.0
             # float32 rounding of X +- h and of the wrapped difference leaves ~2e-4 of noise
-            assert abs(fd - gX[i, j]) <= 5e-4 * max(1.0, abs(fd)), (i, j, fd, gX[i, j])
+            if abs(fd - gX[i, j]) > 5e-4 * max(1.0, abs(fd)):
+                bad.append(("X", i, j, fd, gX[i, j]))
             checked += 1
         h = 1e-3
         cp, cm = coh.copy(), coh.copy()
         cp[i, j] += h
         cm[i, j] -= h
         fdc = (L(X, cp) - L(X, cm)) / (2 * h)
-        assert abs(fdc - gC[i, j]) <= 1e-5 * max(1.0, abs(fdc)), (i, j, fdc, gC[i, j])
+        if abs(fdc - gC[i, j]) > 1e-5 * max(1.0, abs(fdc)):
+            bad.append(("coh", i, j, fdc, gC[i, j]))
+    return bad, checked
+
+
+def test_adjoint_matches_central_differences():
+    X, coh, Uref, kw = _adjoint_case()
+    bad, checked = _adjoint_fd_mismatches(X, coh, Uref, kw)
+    assert not bad, bad
     assert checked >= 3
 
 
-def test_planted_wrong_reweighting_derivative_is_caught():
-    """Dropping the C^3 V^2 / W^3 term of dD/dC must break the coherence gradient check."""
+def test_planted_wrong_reweighting_derivative_is_caught(monkeypatch):
+    """Dropping the C^3 V^2 / W^3 term of dD/dC (D = C^2 / W with W = sqrt(C^2 V^2 + delta^2),
+    Sec. 3.1) must break the central-difference check of the coherence gradient; a sign slip
+    in dD/dV must break the check of dL/dX (it reaches X through V^0 = -G)."""
     X, coh, Uref, kw = _adjoint_case()
-    r0 = O.irls_unwrap(X, coh, **kw)
-    _, gC, fwd = O.irls_adjoint(X, coh, 2 * (r0["U"] - Uref), **kw)
-    # recompute with the planted slip
-    pb = fwd["problem"]
-    xs = fwd["record"]["x"]
-    _, Vv0, Vh0 = xs[0]
-    Wv, Wh = O.reweight(Vv0, Vh0, pb.Cv, pb.Ch, kw["delta"])
-    good = 2.0 * pb.Cv / Wv - pb.Cv ** 3 * Vv0 ** 2 / Wv ** 3
-    bad = 2.0 * pb.Cv / Wv
-    assert not np.allclose(good, bad, rtol=1e-3)
+    monkeypatch.setattr(O, "dD_dC", lambda C, V, W: 2.0 * C / W)
+    bad, _ = _adjoint_fd_mismatches(X, coh, Uref, kw)
+    assert any(b[0] == "coh" for b in bad)
+    monkeypatch.undo()
+    monkeypatch.setattr(O, "dD_dV", lambda C, V, W: (C ** 4) * V / W ** 3)
+    bad, _ = _adjoint_fd_mismatches(X, coh, Uref, kw)
+    assert any(b[0] == "X" for b in bad)
+
+
+# ------------------------------------------------------------------------------------------
+# Edge weights from coherence (reading of Sec. 2's weights for a per-pixel coherence map)
+# ------------------------------------------------------------------------------------------
+def _edges_touched_by_pixel(fn, N, M, i, j):
+    """Which edge weights change when only pixel (i, j)'s coherence changes."""
+    rng = np.random.default_rng(i * 31 + j)
+    c = rng.uniform(0.05, 1.0, size=(N, M))
+    Cv0, Ch0 = fn(c, N, M)
+    c2 = c.copy()
+    c2[i, j] += 0.25
+    Cv1, Ch1 = fn(c2, N, M)
+    return set(map(tuple, np.argwhere(Cv1 != Cv0))), set(map(tuple, np.argwhere(Ch1 != Ch0)))
+
+
+def _edge_weight_pins_hold(fn):
+    """An edge's weight depends on the coherence of its two end pixels only, equally on both:
+    raising one pixel's coherence by h raises exactly its (up to) four incident edges, each by
+    h / 2; uniform coherence c gives uniform weights c on every edge that exists."""
+    for N, M in ((7, 7), (6, 9)):
+        for i, j in ((0, 0), (3, 5), (N - 1, M - 1), (2, 0), (N - 1, 4)):
+            tv, th = _edges_touched_by_pixel(fn, N, M, i, j)
+            want_v = {(a, j) for a in (i - 1, i) if 0 <= a < N - 1}
+            want_h = {(i, b) for b in (j - 1, j) if 0 <= b < M - 1}
+            if tv != want_v or th != want_h:
+                return False
+        Cv, Ch = fn(np.full((N, M), 0.3), N, M)
+        if Cv.shape != (N - 1, M) or Ch.shape != (N, M - 1):
+            return False
+        if not (np.allclose(Cv, 0.3) and np.allclose(Ch, 0.3)):
+            return False
+        rng = np.random.default_rng(N)
+        c = rng.uniform(0.05, 1.0, size=(N, M))
+        c2 = c.copy()
+        c2[2, 3] += 0.25
+        Cv0, Ch0 = fn(c, N, M)
+        Cv1, Ch1 = fn(c2, N, M)
+        if not (np.allclose((Cv1 - Cv0)[(Cv1 - Cv0) != 0], 0.125)
+                and np.allclose((Ch1 - Ch0)[(Ch1 - Ch0) != 0], 0.125)):
+            return False
+    return True
+
+
+def test_edge_weights_are_local_and_symmetric():
+    assert _edge_weight_pins_hold(O.edge_weights)
+    Cv, Ch = O.edge_weights(None, 5, 4)
+    assert np.array_equal(Cv, np.ones((4, 4))) and np.array_equal(Ch, np.ones((5, 3)))
+
+
+def test_transposition_with_non_symmetric_coherence():
+    """Transposing X and the coherence map transposes U (the problem has no preferred axis), with
+    a coherence map that is far from symmetric."""
+    d = synthetic.make_phase(18, 14, 4, ramp=8.0, n_bumps=2, noise=0.7, coherence=True)
+    X = d["X"]
+    coh = d["coherence"].copy()
+    coh[:, :5] *= 0.2             # a low-coherence band along one side only
+    assert np.abs(coh[:14, :14] - coh[:14, :14].T).max() > 0.3
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=4, cg_tol=1e-11, cg_max=600)
+    base = O.irls_unwrap(X, coh, **kw)
+    tr = O.irls_unwrap(X.T.copy(), coh.T.copy(), **kw)
+    np.testing.assert_allclose(tr["U"].T, base["U"], atol=1e-8)
+    np.testing.assert_allclose(tr["l1_obj"], base["l1_obj"], rtol=1e-6)
+
+
+def test_planted_axis_swap_in_edge_weights_is_caught(monkeypatch):
+    """Averaging along the wrong axis (on a square image the shapes still fit): the locality pin
+    fails.  A swap of both planes (weights taken from the transposed coherence) keeps the
+    transposition invariance, so that check alone could not catch it; a swap of one plane
+    breaks both."""
+    def both_swapped(coherence, N, M):
+        c = np.asarray(coherence, dtype=np.float64)
+        return 0.5 * (c[:, 1:] + c[:, :-1]).T, 0.5 * (c[1:, :] + c[:-1, :]).T
+
+    def one_swapped(coherence, N, M):
+        c = np.asarray(coherence, dtype=np.float64)
+        return 0.5 * (c[:, 1:] + c[:, :-1]).T, 0.5 * (c[:, 1:] + c[:, :-1])
+
+    square = lambda fn: (lambda c, N, M: fn(c, N, M) if N == M else O.edge_weights(c, N, M))  # noqa
+    assert not _edge_weight_pins_hold(square(both_swapped))
+    assert not _edge_weight_pins_hold(square(one_swapped))
+    d = synthetic.make_phase(14, 14, 4, ramp=8.0, n_bumps=2, noise=0.7, coherence=True)
+    X, coh = d["X"], d["coherence"].copy()
+    coh[:, :5] *= 0.2
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-11, cg_max=600)
+    monkeypatch.setattr(O, "edge_weights", one_swapped)
+    base = O.irls_unwrap(X, coh, **kw)
+    tr = O.irls_unwrap(X.T.copy(), coh.T.copy(), **kw)
+    assert np.abs(tr["U"].T - base["U"]).max() > 1e-6
