@@ -117,10 +117,11 @@ k_gemm_tn_f32(const float* __restrict__ A, int lda, int a_rows, const float* __r
         __syncthreads();
     }
 
-    float part = 0.f;
+    CSum part;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        float row = 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
@@ -134,13 +135,14 @@ k_gemm_tn_f32(const float* __restrict__ A, int lda, int a_rows, const float* __r
             } else {
                 if (m < ep.vm && n < ep.vn) {
                     ep.C[(size_t)m * ep.ldc + n] = v;
-                    if constexpr (EPI == EPI_ZU_RHO) part += ep.rU[(size_t)m * ep.ldc + n] * v;
+                    if constexpr (EPI == EPI_ZU_RHO) row += ep.rU[(size_t)m * ep.ldc + n] * v;
                 }
             }
         }
+        if constexpr (EPI == EPI_ZU_RHO) part.add(row);
     }
     if constexpr (EPI == EPI_ZU_RHO) {
-        double vv[1] = {(double)part}, tot[1];
+        double vv[1] = {part.value()}, tot[1];
         const Blk blk = single_blk();
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, blk.nblk, blk.bid) && tid == 0) {
             DevState* st = ep.st;

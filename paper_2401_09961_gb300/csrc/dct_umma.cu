@@ -323,7 +323,7 @@ __device__ __forceinline__ void finish_rho(const UEpiArgs& ep, double rz_u, bool
 // column.  ZU_RHO adds this thread's share of r^T z to `part`.
 template <int BN, int EPI>
 __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m, int n0,
-                                         float& part, int c_begin = 0, int c_end = BN / 32) {
+                                         CSum& part, int c_begin = 0, int c_end = BN / 32) {
 #pragma unroll 1
     for (int c = c_begin; c < c_end; ++c) {
         uint32_t r[32];
@@ -396,7 +396,7 @@ __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m,
                         reinterpret_cast<float4*>(out + nb)[q] = w;
                         if constexpr (EPI == UE_ZU_RHO) {
                             const float4 x = reinterpret_cast<const float4*>(rr + nb)[q];
-                            part += x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w;
+                            part.add(x.x * w.x + x.y * w.y + x.z * w.z + x.w * w.w);
                         }
                     }
                 } else {
@@ -405,7 +405,7 @@ __device__ __forceinline__ void epi_tile(uint32_t tl, const UEpiArgs& ep, int m,
                         if (nb + t < ep.vn) {
                             const float z = __uint_as_float(r[t]);
                             out[nb + t] = z;
-                            if constexpr (EPI == UE_ZU_RHO) part += rr[nb + t] * z;
+                            if constexpr (EPI == UE_ZU_RHO) part.add(rr[nb + t] * z);
                         }
                     }
                 }
@@ -464,7 +464,7 @@ __device__ __forceinline__ void scr_store16(const WarpScratch& s, void* hi, void
 // image whose width is not a multiple of 4), go element by element.
 template <typename RowOff>
 __device__ __forceinline__ void scr_store32(const WarpScratch& s, float* out, const float* rU,
-                                            int col0, RowOff row_off, float& part, int nrows = 32,
+                                            int col0, RowOff row_off, CSum& part, int nrows = 32,
                                             int c_lo = 0, int c_hi = 32) {
     const int lane = threadIdx.x & 31;
     const int rsub = lane >> 3, col = 4 * (lane & 7);
@@ -480,14 +480,14 @@ __device__ __forceinline__ void scr_store32(const WarpScratch& s, float* out, co
             *reinterpret_cast<float4*>(out + off) = z;
             if (rU) {
                 const float4 x = *reinterpret_cast<const float4*>(rU + off);
-                part += x.x * z.x + x.y * z.y + x.z * z.z + x.w * z.w;
+                part.add(x.x * z.x + x.y * z.y + x.z * z.z + x.w * z.w);
             }
         } else {
             for (int e = 0; e < 4; ++e) {
                 if (col + e < c_lo || col + e >= c_hi) continue;
                 const float z = s.v[row][col + e];
                 out[off + e] = z;
-                if (rU) part += rU[off + e] * z;
+                if (rU) part.add(rU[off + e] * z);
             }
         }
     }
@@ -497,7 +497,7 @@ __device__ __forceinline__ void scr_store32(const WarpScratch& s, float* out, co
 // at output row m0w (this lane's row is m0w + lane), with coalesced stores through `s`.
 template <int BN, int EPI>
 __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int m0w, int n0,
-                                           float& part, int c_begin, int c_end, WarpScratch& s) {
+                                           CSum& part, int c_begin, int c_end, WarpScratch& s) {
     const int lane = threadIdx.x & 31;
     const int m = m0w + lane;
     const size_t ldc = (size_t)ep.ldc;
@@ -573,6 +573,7 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
 #pragma unroll
                 // float16: the row's coefficients times (lm + lam1) / tau (see UEpiArgs)
                 const float rs = ep.f16 ? __fdividef(lm + ep.lam1, ep.scale) : 1.f;
+                float q4 = 0.f;
                 for (int t = 0; t < 32; ++t) {
                     const int n = nb + t;
                     const bool keep = rowok && n < ep.vn && (ep.keep_origin || (m | n) != 0);
@@ -580,8 +581,15 @@ __device__ __forceinline__ void epi_tile_t(uint32_t tl, const UEpiArgs& ep, int 
                     const float g = keep ? __fdividef(ep.scale * f, lm + __ldg(&ep.lam_n[n])) : 0.f;
                     v[t] = g * rs;
                     // r^T z = sum over frequencies of F * (tau F / eig) (P_N, P_M orthogonal);
-                    // with float16 F and G carry the residual's scale, removed when rho is formed
-                    if constexpr (EPI == UE_EIG16_RHO) part += f * g;
+                    // with float16 F and G carry the residual's scale, removed when rho is formed;
+                    // partials of four frequencies go into the compensated sum
+                    if constexpr (EPI == UE_EIG16_RHO) {
+                        q4 += f * g;
+                        if ((t & 3) == 3) {
+                            part.add(q4);
+                            q4 = 0.f;
+                        }
+                    }
                 }
             }
             scr_put(s, v);
@@ -702,7 +710,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
         ep.st->done = 1;
     }
     const int m = m0 + warp * 32 + lane;
-    float part = 0.f;
+    CSum part;
     if (good) epi_tile<BN, EPI>(tmem + ((uint32_t)(warp * 32) << 16), ep, m, n0, part);
     tc_fence_before();
     __syncthreads();
@@ -711,7 +719,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap* tmA0, const CUtenso
         tmem_dealloc(tmem, kCols);
     }
     if constexpr (EPI == UE_ZU_RHO) {
-        double vv[1] = {(double)part}, tot[1];
+        double vv[1] = {part.value()}, tot[1];
         if (grid_reduce<1>(vv, ep.partials, &ep.st->counter, tot, nblk, bid) && threadIdx.x == 0)
             finish_rho(ep, tot[0]);
     }
@@ -999,7 +1007,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 template <int EBN, int EPI>
 __device__ __forceinline__ void fused_epi(uint32_t tl, const UEpiArgs& ep, int m0w, int n0,
-                                          float& part, int half, WarpScratch& s) {
+                                          CSum& part, int half, WarpScratch& s) {
     constexpr int kChunks = EBN / 32;
     epi_tile_t<EBN, EPI>(tl, ep, m0w, n0, part, half * (kChunks / 2), (half + 1) * (kChunks / 2), s);
 }
@@ -1230,7 +1238,7 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
             const uint32_t te0 = mapa_shared(smem_u32(tempty), 0);
             int nbuf = 0, nsync = 0;
             int use[2] = {0, 0};
-            float part = 0.f;
+            CSum part;
             for (int t = pair; t < n_items; t += npairs) {
                 const FoldItem& f = items[t];
                 if (!item_live(f, lst, llive)) continue;
@@ -1286,8 +1294,8 @@ k2_fold_fused(const GemmTile* __restrict__ probs, const FoldItem* __restrict__ i
                     // ((tile, CTA), warp); at the end of its run of the image's stage-2 tiles (marked
                     // by the host) a CTA counts itself done, and the CTA that completes the count adds
                     // all the image's slots and forms rho and beta
-                    double v = (double)part;
-                    part = 0.f;
+                    double v = part.value();
+                    part = CSum();
     #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                     if (lane == 0)

@@ -296,7 +296,8 @@ int fetch_stats(irls_plan_s* p, cudaStream_t s, irls_stats* stats) {
 
 // PCG iterations (Alg. 2) after the first preconditioner application of a run: issued in chunks,
 // the device stopping flag polled one chunk behind.
-void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s) {
+void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s,
+            bool schur_system = false) {
     Profiler& pf = p->prof;
     cudaEvent_t t0;
     int issued = 0, slot = 0;
@@ -304,7 +305,7 @@ void run_cg(irls_plan_s* p, const StencilArgs& a, DevState* st, cudaStream_t s) 
     size_t mark[2] = {0, 0};
     while (issued < a.cg_max) {
         const int n = std::min(kChunk, a.cg_max - issued);
-        const bool schur = p->opts.system == IRLS_SYS_SCHUR;
+        const bool schur = schur_system || p->opts.system == IRLS_SYS_SCHUR;
         for (int c = 0; c < n; ++c) {
             t0 = pf.begin(s);
             if (schur) ck(launch_schur_direction(p->P, a, st, p->partials, s));
@@ -583,7 +584,7 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
     prepare_graphs(b);
     for (int k = 0; k < b->opts.outer_iters; ++k) {
         TraceRange r_outer("irls_outer");
-        ck(launch_reweight_batched(b->d_recs, T, b->total_strip, s));
+        ck(launch_reweight_batched(b->d_recs, T, b->total_upd, b->upd_rows, s));
         {
             TraceRange r_pcg("irls_pcg");
             ck(batch_dct_apply(b->dct, s));
@@ -608,7 +609,7 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
             }
         }
         TraceRange r_fin("irls_finalize");
-        ck(launch_finalize_batched(b->d_recs, T, b->total_strip, s));
+        ck(launch_finalize_batched(b->d_recs, T, b->total_strip, b->total_upd, b->upd_rows, s));
     }
     for (int t = 0; t < T; ++t)
         ck(launch_copy_out(b->recs[t].P.U, b->H[t], b->W[t], b->ld[t], U[t], s));
@@ -951,14 +952,19 @@ int irls_unwrap_backward(irls_tape t, const float* dLdU, float* dLdX, float* dLd
         ck(launch_adj_init(p->P, a, dLdU, st, p->partials, s));
         for (int k = t->K - 1; k >= 0; --k) {
             TraceRange r_step("irls_backward_step");
-            ck(launch_adj_setup(p->P, a, t->Vv[k], t->Vh[k], t->Cv, t->Ch, st, p->partials, s));
+            // lambda = A_k^+ xbar through the U-only system (V eliminated exactly), for the
+            // step's cotangent normalised to unit norm (its factor kept in FP64 on the device)
+            ck(launch_adj_norm(p->P, a, st, p->partials, s));
+            ck(launch_adj_setup_schur(p->P, a, t->Vv[k], t->Vh[k], t->Cv, t->Ch, st,
+                                      p->partials, s));
             ck(dct_apply(p->dct, p->P.rU, p->P.zU, p->ld, st, 1, a, p->partials, 1, s));
-            run_cg(p, a, st, s);
+            run_cg(p, a, st, s, true);
+            ck(launch_adj_recover_v(p->P, a, st, s));
             ck(launch_record_step(st, s));
             ck(launch_adj_accumulate(p->P, a, t->Vv[k], t->Vh[k], t->Vv[k + 1], t->Vh[k + 1],
-                                     t->Cv, t->Ch, t->Gbv, t->Gbh, t->Cbv, t->Cbh, s));
+                                     t->Cv, t->Ch, t->Gbv, t->Gbh, t->Cbv, t->Cbh, st, s));
         }
-        ck(launch_adj_final(p->P, a, t->Gbv, t->Gbh, t->Cbv, t->Cbh, dLdX, dLdcoh, s));
+        ck(launch_adj_final(p->P, a, t->Gbv, t->Gbh, t->Cbv, t->Cbh, dLdX, dLdcoh, st, s));
         status = fetch_stats(p, s, stats);
     } catch (Fail&) {
         return IRLS_ERR_CUDA;

@@ -74,6 +74,8 @@ struct DevState {
     double h_delta[kMaxOuter];
     double f_delta[kMaxOuter];
     double aux[4];   // post-processing results: circular offset, best shift, sum of E^2
+    double adj_scale;  // adjoint sweep: factor of the cotangent held in the residual planes
+    double adj_step;   // adjoint sweep: ||xbar|| of the current reverse step
 };
 
 // Image-shaped planes.  Every plane is H rows x ld floats (ld a multiple of 32); the vertical
@@ -207,16 +209,20 @@ int stencil_grid_blocks(int H, int W);
 cudaError_t launch_record_step(DevState* st, cudaStream_t s);
 cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* dLdU, DevState* st,
                             double* partials, cudaStream_t s);
-cudaError_t launch_adj_setup(const Planes& P, const StencilArgs& a, const float* Vkv,
-                             const float* Vkh, const float* Cv, const float* Ch, DevState* st,
-                             double* partials, cudaStream_t s);
+cudaError_t launch_adj_setup_schur(const Planes& P, const StencilArgs& a, const float* Vkv,
+                                   const float* Vkh, const float* Cv, const float* Ch,
+                                   DevState* st, double* partials, cudaStream_t s);
+cudaError_t launch_adj_recover_v(const Planes& P, const StencilArgs& a, const DevState* st,
+                                 cudaStream_t s);
+cudaError_t launch_adj_norm(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                            cudaStream_t s);
 cudaError_t launch_adj_accumulate(const Planes& P, const StencilArgs& a, const float* Vkv,
                                   const float* Vkh, const float* Vnv, const float* Vnh,
                                   const float* Cv, const float* Ch, float* Gbv, float* Gbh,
-                                  float* Cbv, float* Cbh, cudaStream_t s);
+                                  float* Cbv, float* Cbh, const DevState* st, cudaStream_t s);
 cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float* Gbv,
                              const float* Gbh, const float* Cbv, const float* Cbh, float* dX,
-                             float* dcoh, cudaStream_t s);
+                             float* dcoh, const DevState* st, cudaStream_t s);
 
 // batched launches over a device array of TileRec (one launch for all images; images whose CG
 // run has stopped return at once)
@@ -224,12 +230,14 @@ void strip_dims(int H, int W, int& gx, int& gy);
 void vec_dims(int H, int W, int dir_rows, int upd_rows, int& gx, int& gy_dir, int& gy_upd);
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
-cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_upd, int rows,
+                                    cudaStream_t s);
 cudaError_t launch_direction_batched(const TileRec* recs, int T, int total_vec, int rows,
                                      cudaStream_t s);
 cudaError_t launch_update_batched(const TileRec* recs, int T, int total_upd, int rows,
                                   cudaStream_t s);
-cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, int total_upd,
+                                    int rows, cudaStream_t s);
 cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStream_t s);
 
 // ---- DCT preconditioner (dct.cu) ------------------------------------------------------------

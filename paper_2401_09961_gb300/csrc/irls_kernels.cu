@@ -106,7 +106,7 @@ __device__ __forceinline__ void k_bnorm_body(Planes P, StencilArgs a, DevState* 
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blk.bx * kThreads + threadIdx.x;
     const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    float acc = 0.f;
+    CSum acc;
     if (j < W) {
         for (int i = i0; i < i1; ++i) {
             const size_t o = (size_t)i * ld + j;
@@ -114,10 +114,10 @@ __device__ __forceinline__ void k_bnorm_body(Planes P, StencilArgs a, DevState* 
             const float gv_up = i > 0 ? P.Gv[o - ld] : 0.f;
             const float gh_l = j > 0 ? P.Gh[o - 1] : 0.f;
             const float bu = a.inv_tau * (gv_up - gv + gh_l - gh);
-            acc += bu * bu + a.inv_tau * a.inv_tau * (gv * gv + gh * gh);
+            acc.add(bu * bu + a.inv_tau * a.inv_tau * (gv * gv + gh * gh));
         }
     }
-    double v[1] = {(double)acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) st->bb = tot[0];
 }
 
@@ -134,13 +134,13 @@ k_norm_u(Planes P, StencilArgs a, DevState* st, double* partials) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blk.bx * kThreads + threadIdx.x;
     const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    float acc = 0.f;
+    CSum acc;
     if (j < W)
         for (int i = i0; i < i1; ++i) {
             const float r = P.rU[(size_t)i * ld + j];
-            acc += r * r;
+            acc.add(r * r);
         }
-    double v[1] = {(double)acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0)
         st->rnorm_u = sqrt(tot[0]);
 }
@@ -163,85 +163,6 @@ __device__ __forceinline__ void emit16(void* r16, void* r16lo, int ld16, int i, 
             __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-__device__ __forceinline__ void k_reweight_residual_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
-    const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blk.bx * kThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    const bool col = j < W, hh = j + 1 < W;
-    const float it = a.inv_tau, d2 = a.delta * a.delta;
-    const bool warm = a.warm_start != 0;
-    float rr = 0.f, rzv = 0.f, fd = 0.f, ru2 = 0.f, su = 0.f;
-    float uc = col ? P.U[(size_t)i0 * ld + j] : 0.f;
-    float ev_prev = 0.f;          // residual-edge e_v of the row above
-    if (col && i0 > 0) {
-        const size_t o = (size_t)(i0 - 1) * ld + j;
-        ev_prev = warm ? (uc - P.U[o] - P.Vv[o] - P.Gv[o]) : -P.Gv[o];
-    }
-    for (int i = i0; i < i1; ++i) {
-        const size_t o = (size_t)i * ld + j;
-        const bool hv = i + 1 < H;
-        float vv = 0.f, vh = 0.f, cv = 0.f, ch = 0.f, gv = 0.f, gh = 0.f, un = 0.f;
-        if (col) {
-            vv = P.Vv[o]; vh = P.Vh[o]; cv = P.Cv[o]; ch = P.Ch[o]; gv = P.Gv[o]; gh = P.Gh[o];
-            if (hv) un = P.U[o + ld];
-        }
-        float ur = __shfl_down_sync(kFull, uc, 1);
-        if (lane == 31 && col && hh) ur = P.U[o + 1];
-        // edge residuals at the iterate x^k
-        const float evk = (col && hv) ? (un - uc - vv - gv) : 0.f;
-        const float ehk = (col && hh) ? (ur - uc - vh - gh) : 0.f;
-        // edge residuals of the CG starting point
-        const float ev = warm ? evk : ((col && hv) ? -gv : 0.f);
-        const float eh = warm ? ehk : ((col && hh) ? -gh : 0.f);
-        float eh_l = __shfl_up_sync(kFull, eh, 1);
-        if (lane == 0) {
-            eh_l = 0.f;
-            if (col && j > 0)
-                eh_l = warm ? (uc - P.U[o - 1] - P.Vh[o - 1] - P.Gh[o - 1]) : -P.Gh[o - 1];
-        }
-        if (col) {
-            float wv = 0.f, wh = 0.f, dv = 0.f, dh = 0.f;
-            if (hv) { wv = sqrtf(cv * cv * vv * vv + d2); dv = cv * cv / wv; }
-            if (hh) { wh = sqrtf(ch * ch * vh * vh + d2); dh = ch * ch / wh; }
-            const float xvv = warm ? vv : 0.f, xvh = warm ? vh : 0.f;
-            const float ru = -it * (ev_prev - ev + eh_l - eh);
-            const float rv = it * ev - dv * xvv;
-            const float rh = it * eh - dh * xvh;
-            P.Wv[o] = wv; P.Wh[o] = wh; P.dv[o] = dv; P.dh[o] = dh;
-            P.rU[o] = ru; P.rVv[o] = rv; P.rVh[o] = rh;
-            if (!warm) { P.U[o] = 0.f; P.Vv[o] = 0.f; P.Vh[o] = 0.f; }
-            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
-            rr += ru * ru + rv * rv + rh * rh;
-            ru2 += ru * ru;
-            su += ru;
-            rzv += rv * rv / (dv + it) + rh * rh / (dh + it);
-            fd += wv + wh + 0.5f * it * (evk * evk + ehk * ehk);
-        }
-        ev_prev = ev;
-        uc = un;
-    }
-    double v[5] = {(double)rr, (double)rzv, (double)fd, (double)ru2, (double)su}, tot[5];
-    if (grid_reduce<5>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
-        const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
-        st->rr = rr_range;
-        st->rz_v = tot[1];
-        st->rnorm_u = sqrt(tot[3]);
-        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
-        st->rel = rel;
-        st->iter = 0;
-        st->p_fresh = 1;
-        st->done = (rel * rel <= a.tol2 || a.cg_max <= 0 || st->bb <= 0.0) ? 1 : 0;
-        const int k = st->outer;
-        if (k < kMaxOuter) st->f_delta[k] = tot[2];
-    }
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
-    k_reweight_residual_body(P, a, st, partials, single_blk());
-}
-
 // ------------------------------------------------------------------------------------------
 // The two per-iteration kernels work on float4 lanes: a thread owns 4 consecutive columns, a
 // warp 128 and a block of 128 threads 512, so each warp moves 512-byte rows; the next row's
@@ -262,6 +183,145 @@ __device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4]) 
 }
 __device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+
+// Start of an outer step (see the comment above emit16), on float4 lanes with the update
+// kernel's block shape: a thread owns four columns; the horizontal neighbour of its last column
+// comes from the next lane (lane 31 loads it), the horizontal edge left of its first column from
+// the previous lane (lane 0 recomputes it).  Padding columns (>= W) get no W, D or r.
+template <int ROWS>
+__device__ __forceinline__ void k_reweight_residual_body(Planes P, StencilArgs a, DevState* st,
+                                                         double* partials, const Blk& blk) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
+    const float it = a.inv_tau, d2 = a.delta * a.delta;
+    const bool warm = a.warm_start != 0;
+    // not __restrict__: a cold start zeroes the iterate through P in the same pass
+    const float* U = P.U;
+    const float* Vv = P.Vv;
+    const float* Vh = P.Vh;
+    const float* __restrict__ Gv = P.Gv;
+    const float* __restrict__ Gh = P.Gh;
+    bool col[kVec], hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) {
+        col[e] = j0 + e < W;
+        hh[e] = j0 + e + 1 < W;
+    }
+    CSum rr, rzv, fd, ru2, su;
+    float uc[4] = {0, 0, 0, 0}, evp[4] = {0, 0, 0, 0};   // this row's U; e_v of the row above
+    if (act) {
+        ld4(U + (size_t)i0 * ld + j0, uc);
+        if (i0 > 0) {
+            const size_t o = (size_t)(i0 - 1) * ld + j0;
+            float uu[4], vu[4], gu[4];
+            ld4(U + o, uu); ld4(Vv + o, vu); ld4(Gv + o, gu);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) evp[e] = warm ? (uc[e] - uu[e] - vu[e] - gu[e]) : -gu[e];
+        }
+    }
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j0;
+        const bool hv = i + 1 < H;
+        float vv[4] = {0, 0, 0, 0}, vh[4] = {0, 0, 0, 0}, cv[4] = {0, 0, 0, 0};
+        float ch[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gh[4] = {0, 0, 0, 0};
+        float un[4] = {0, 0, 0, 0};
+        if (act) {
+            ld4(Vv + o, vv); ld4(Vh + o, vh); ld4(P.Cv + o, cv); ld4(P.Ch + o, ch);
+            ld4(Gv + o, gv); ld4(Gh + o, gh);
+            if (hv) ld4(U + o + ld, un);
+        }
+        float ur = __shfl_down_sync(kFull, uc[0], 1);
+        if (lane == 31) ur = (act && j0 + kVec < W) ? U[o + kVec] : 0.f;
+        const float pr[4] = {uc[1], uc[2], uc[3], ur};
+        // edge residuals at the iterate x^k, and of the CG starting point
+        float evk[4], ehk[4], ev[4], eh[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            evk[e] = hv ? (un[e] - uc[e] - vv[e] - gv[e]) : 0.f;
+            ehk[e] = hh[e] ? (pr[e] - uc[e] - vh[e] - gh[e]) : 0.f;
+            ev[e] = warm ? evk[e] : (hv ? -gv[e] : 0.f);
+            eh[e] = warm ? ehk[e] : (hh[e] ? -gh[e] : 0.f);
+        }
+        float ehl = __shfl_up_sync(kFull, eh[3], 1);
+        if (lane == 0) {
+            ehl = 0.f;
+            if (act && j0 > 0)
+                ehl = warm ? (uc[0] - U[o - 1] - Vh[o - 1] - Gh[o - 1]) : -Gh[o - 1];
+        }
+        const float el[4] = {ehl, eh[0], eh[1], eh[2]};
+        if (act) {
+            float wv[4], wh[4], dv[4], dh[4], ru[4], rv[4], rh[4];
+            float prr = 0.f, pru2 = 0.f, psu = 0.f, przv = 0.f, pfd = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool ve = hv && col[e];
+                wv[e] = ve ? sqrtf(cv[e] * cv[e] * vv[e] * vv[e] + d2) : 0.f;
+                dv[e] = ve ? cv[e] * cv[e] / wv[e] : 0.f;
+                wh[e] = hh[e] ? sqrtf(ch[e] * ch[e] * vh[e] * vh[e] + d2) : 0.f;
+                dh[e] = hh[e] ? ch[e] * ch[e] / wh[e] : 0.f;
+                const float xvv = warm ? vv[e] : 0.f, xvh = warm ? vh[e] : 0.f;
+                // r = b - A x with the cancelling terms carried as hi + lo pairs
+                float h, l;
+                sum4_scaled(-it, evp[e], -ev[e], el[e], -eh[e], h, l);
+                ru[e] = __fadd_rn(h, l);
+                diff_prod(dv[e], xvv, it, ev[e], h, l);
+                rv[e] = -__fadd_rn(h, l);
+                diff_prod(dh[e], xvh, it, eh[e], h, l);
+                rh[e] = -__fadd_rn(h, l);
+                prr += ru[e] * ru[e] + rv[e] * rv[e] + rh[e] * rh[e];
+                pru2 += ru[e] * ru[e];
+                psu += ru[e];
+                przv += rv[e] * rv[e] / (dv[e] + it) + rh[e] * rh[e] / (dh[e] + it);
+                pfd += wv[e] + wh[e] + 0.5f * it * (evk[e] * evk[e] + ehk[e] * ehk[e]);
+            }
+            st4(P.Wv + o, wv); st4(P.Wh + o, wh); st4(P.dv + o, dv); st4(P.dh + o, dh);
+            st4(P.rU + o, ru); st4(P.rVv + o, rv); st4(P.rVh + o, rh);
+            if (!warm) {
+                const float z[4] = {0.f, 0.f, 0.f, 0.f};
+                st4(P.U + o, z); st4(P.Vv + o, z); st4(P.Vh + o, z);
+            }
+            if (a.r16 != nullptr) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (col[e]) emit16(a.r16, a.r16lo, a.ld16, i, j0 + e, ru[e]);
+            }
+            rr.add(prr);
+            ru2.add(pru2);
+            su.add(psu);
+            rzv.add(przv);
+            fd.add(pfd);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            evp[e] = ev[e];
+            uc[e] = un[e];
+        }
+    }
+    double v[5] = {rr.value(), rzv.value(), fd.value(), ru2.value(), su.value()}, tot[5];
+    if (grid_reduce<5>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
+        st->rr = rr_range;
+        st->rz_v = tot[1];
+        st->rnorm_u = sqrt(tot[3]);
+        const double rel = st->bb > 0.0 ? sqrt(rr_range / st->bb) : 0.0;
+        st->rel = rel;
+        st->iter = 0;
+        st->p_fresh = 1;
+        st->done = (rel * rel <= a.tol2 || a.cg_max <= 0 || st->bb <= 0.0) ? 1 : 0;
+        const int k = st->outer;
+        if (k < kMaxOuter) st->f_delta[k] = tot[2];
+    }
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_reweight_residual(Planes P, StencilArgs a, DevState* st, double* partials) {
+    k_reweight_residual_body<ROWS>(P, a, st, partials, single_blk());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -348,7 +408,7 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
             if (i0 + 1 < i1) dir_v(o + ld, nvv, nvh, ndv, ndh);
         }
     }
-    float acc = 0.f;
+    CSum acc;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
@@ -365,12 +425,14 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
         if (act) {
             st4(pUn + o, cu); st4(pVvn + o, cvv); st4(pVhn + o, cvh);
             const float pr[4] = {cu[1], cu[2], cu[3], right};
+            float row = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const float yh = hh[e] ? (pr[e] - cu[e] - cvh[e]) : 0.f;
                 const float yv = hv ? (nu[e] - cu[e] - cvv[e]) : 0.f;
-                acc += it * (yh * yh + yv * yv) + cdv[e] * cvv[e] * cvv[e] + cdh[e] * cvh[e] * cvh[e];
+                row += it * (yh * yh + yv * yv) + cdv[e] * cvv[e] * cvv[e] + cdh[e] * cvh[e] * cvh[e];
             }
+            acc.add(row);
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -380,7 +442,7 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
         rcu = rnu;
         rnu = rmu;
     }
-    double v[1] = {(double)acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double pq = tot[0];
         st->pq = pq;
@@ -454,7 +516,7 @@ __device__ __forceinline__ void k_update_body(Planes P, StencilArgs a, DevState*
             if (i0 + 1 < i1) { ld4(pVv + o + ld, nvv); ld4(pVh + o + ld, nvh); }
         }
     }
-    float rr = 0.f, rzv = 0.f, rzo = 0.f, ru2 = 0.f, su = 0.f;
+    CSum rr, rzv, rzo, ru2, su;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
@@ -486,24 +548,33 @@ __device__ __forceinline__ void k_update_body(Planes P, StencilArgs a, DevState*
         const float yl[4] = {left, yh[0], yh[1], yh[2]};
         if (act) {
             float n0[4], n1[4], n2[4];
+            float prr = 0.f, pru2 = 0.f, psu = 0.f, przv = 0.f, przo = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float qu = it * (yvp[e] - yv[e] + yl[e] - yh[e]);
-                const float qv = dv[e] * cvv[e] - it * yv[e];
-                const float qh = dh[e] * cvh[e] - it * yh[e];
+                // A p with its cancelling terms as hi + lo pairs, subtracted from r with one
+                // rounding each (the residual is far smaller than the terms near convergence)
+                float quh, qul, qvh, qvl, qhh, qhl;
+                sum4_scaled(it, yvp[e], -yv[e], yl[e], -yh[e], quh, qul);
+                diff_prod(dv[e], cvv[e], it, yv[e], qvh, qvl);
+                diff_prod(dh[e], cvh[e], it, yh[e], qhh, qhl);
                 u[e] += alpha * cu[e];
                 vv[e] += alpha * cvv[e];
                 vh[e] += alpha * cvh[e];
-                n0[e] = r0[e] - alpha * qu;
-                n1[e] = r1[e] - alpha * qv;
-                n2[e] = r2[e] - alpha * qh;
+                n0[e] = __fmaf_rn(-alpha, qul, __fmaf_rn(-alpha, quh, r0[e]));
+                n1[e] = __fmaf_rn(-alpha, qvl, __fmaf_rn(-alpha, qvh, r1[e]));
+                n2[e] = __fmaf_rn(-alpha, qhl, __fmaf_rn(-alpha, qhh, r2[e]));
                 const float iv = 1.f / (dv[e] + it), ih = 1.f / (dh[e] + it);
-                rr += n0[e] * n0[e] + n1[e] * n1[e] + n2[e] * n2[e];
-                ru2 += n0[e] * n0[e];
-                su += n0[e];
-                rzv += n1[e] * n1[e] * iv + n2[e] * n2[e] * ih;
-                if (flex) rzo += n0[e] * z[e] + (n1[e] * r1[e]) * iv + (n2[e] * r2[e]) * ih;
+                prr += n0[e] * n0[e] + n1[e] * n1[e] + n2[e] * n2[e];
+                pru2 += n0[e] * n0[e];
+                psu += n0[e];
+                przv += n1[e] * n1[e] * iv + n2[e] * n2[e] * ih;
+                if (flex) przo += n0[e] * z[e] + (n1[e] * r1[e]) * iv + (n2[e] * r2[e]) * ih;
             }
+            rr.add(prr);
+            ru2.add(pru2);
+            su.add(psu);
+            rzv.add(przv);
+            if (flex) rzo.add(przo);
             st4(U + o, u); st4(Vv + o, vv); st4(Vh + o, vh);
             st4(rU + o, n0); st4(rVv + o, n1); st4(rVh + o, n2);
             if (a.r16 != nullptr) {
@@ -519,7 +590,7 @@ __device__ __forceinline__ void k_update_body(Planes P, StencilArgs a, DevState*
             nu[e] = mu[e]; nvv[e] = mvv[e]; nvh[e] = mvh[e];
         }
     }
-    double v[5] = {(double)rr, (double)rzv, (double)rzo, (double)ru2, (double)su}, tot[5];
+    double v[5] = {rr.value(), rzv.value(), rzo.value(), ru2.value(), su.value()}, tot[5];
     if (grid_reduce<5>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[4], a.H, a.W);
         st->rr = rr_range;
@@ -545,36 +616,77 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
 // End of an outer step: sum U (for U -= mean(U), Prop. 'minimising (alt1)'), the objective of
 // problem (main) and H_delta(x^{k+1}, W^k) of problem (alt1); then record the statistics.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, DevState* st, double* partials, const Blk& blk) {
+// On float4 lanes with the update kernel's block shape.  Per edge in float32: the difference
+// U_{i+1} - U_i and its residual e = (U_{i+1} - U_i) - G are formed with two-sums, so e is exact
+// up to one rounding of itself; C |e| and the H_delta term are each one or two roundings of
+// themselves, and all sums are compensated per thread, then FP64 across threads.
+__device__ __forceinline__ float edge_residual(float un, float u, float g) {
+    float d, dl, e, el;
+    two_sum(un, -u, d, dl);
+    two_sum(d, -g, e, el);
+    return __fadd_rn(e, __fadd_rn(el, dl));
+}
+
+template <int ROWS>
+__device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, DevState* st,
+                                                       double* partials, const Blk& blk) {
     const int H = a.H, W = a.W, ld = a.ld;
-    const int j = blk.bx * kThreads + threadIdx.x;
-    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    const double it = 1.0 / (double)a.tau, d2 = (double)a.delta * (double)a.delta;
-    // FP64 evaluation: the difference of two float32 values is exact in double, so the edge
-    // residuals of the objective carry no cancellation error of their own
-    double su = 0.0, l1 = 0.0, hd = 0.0;
-    if (j < W) {
-        for (int i = i0; i < i1; ++i) {
-            const size_t o = (size_t)i * ld + j;
-            const double u = P.U[o];
-            su += u;
-            if (i + 1 < H) {
-                const double e = ((double)P.U[o + ld] - u) - (double)P.Gv[o];
-                const double c = P.Cv[o], v = P.Vv[o], w = P.Wv[o];
-                l1 += c * fabs(e);
-                const double pe = e - v;
-                hd += 0.5 * ((c * c * v * v + d2) / w + w) + 0.5 * it * pe * pe;
+    const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const bool act = j0 < W;
+    const float it = a.inv_tau, d2 = a.delta * a.delta;
+    const float* __restrict__ U = P.U;
+    bool hh[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) hh[e] = j0 + e + 1 < W;
+    CSum su, l1, hd;
+    float uc[4] = {0, 0, 0, 0};
+    if (act) ld4(U + (size_t)i0 * ld + j0, uc);
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j0;
+        const bool hv = i + 1 < H;
+        float un[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gh[4] = {0, 0, 0, 0};
+        float cv[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0}, vv[4] = {0, 0, 0, 0};
+        float vh[4] = {0, 0, 0, 0}, wv[4] = {0, 0, 0, 0}, wh[4] = {0, 0, 0, 0};
+        if (act) {
+            if (hv) {
+                ld4(U + o + ld, un); ld4(P.Gv + o, gv); ld4(P.Cv + o, cv); ld4(P.Vv + o, vv);
+                ld4(P.Wv + o, wv);
             }
-            if (j + 1 < W) {
-                const double e = ((double)P.U[o + 1] - u) - (double)P.Gh[o];
-                const double c = P.Ch[o], v = P.Vh[o], w = P.Wh[o];
-                l1 += c * fabs(e);
-                const double pe = e - v;
-                hd += 0.5 * ((c * c * v * v + d2) / w + w) + 0.5 * it * pe * pe;
-            }
+            ld4(P.Gh + o, gh); ld4(P.Ch + o, ch); ld4(P.Vh + o, vh); ld4(P.Wh + o, wh);
         }
+        float ur = __shfl_down_sync(kFull, uc[0], 1);
+        if (lane == 31) ur = (act && j0 + kVec < W) ? U[o + kVec] : 0.f;
+        const float pr[4] = {uc[1], uc[2], uc[3], ur};
+        if (act) {
+            float psu = 0.f, pl1 = 0.f, phd = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                psu += uc[e];
+                if (hv && j0 + e < W) {
+                    const float r = edge_residual(un[e], uc[e], gv[e]);
+                    pl1 += cv[e] * fabsf(r);
+                    const float pe = r - vv[e];
+                    phd += 0.5f * ((cv[e] * cv[e] * vv[e] * vv[e] + d2) / wv[e] + wv[e]) +
+                           0.5f * it * pe * pe;
+                }
+                if (hh[e]) {
+                    const float r = edge_residual(pr[e], uc[e], gh[e]);
+                    pl1 += ch[e] * fabsf(r);
+                    const float pe = r - vh[e];
+                    phd += 0.5f * ((ch[e] * ch[e] * vh[e] * vh[e] + d2) / wh[e] + wh[e]) +
+                           0.5f * it * pe * pe;
+                }
+            }
+            su.add(psu);
+            l1.add(pl1);
+            hd.add(phd);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) uc[e] = un[e];
     }
-    double v[3] = {su, l1, hd}, tot[3];
+    double v[3] = {su.value(), l1.value(), hd.value()}, tot[3];
     if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         st->mean_u = tot[0] / ((double)H * (double)W);
         const int k = st->outer;
@@ -591,11 +703,13 @@ __device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, 
     }
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(kThreads)
 k_finalize_reduce(Planes P, StencilArgs a, DevState* st, double* partials) {
-    k_finalize_reduce_body(P, a, st, partials, single_blk());
+    k_finalize_reduce_body<ROWS>(P, a, st, partials, single_blk());
 }
 
+// U -= mean(U) with the mean the finalize kernel formed (Prop. 'minimising (alt1)').
 __device__ __forceinline__ void k_subtract_mean_body(float* U, int H, int W, int ld, const DevState* st, const Blk& blk) {
     const int j = blk.bx * kThreads + threadIdx.x;
     const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
@@ -622,10 +736,10 @@ k_subtract_mean(float* U, int H, int W, int ld, const DevState* st) {
 __device__ __forceinline__ void k_user_mean_body(const float* __restrict__ src, int H, int W, DevState* st, double* partials, const Blk& blk) {
     const int j = blk.bx * kThreads + threadIdx.x;
     const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    float acc = 0.f;
+    CSum acc;
     if (j < W)
-        for (int i = i0; i < i1; ++i) acc += src[(size_t)i * W + j];
-    double v[1] = {(double)acc}, tot[1];
+        for (int i = i0; i < i1; ++i) acc.add(src[(size_t)i * W + j]);
+    double v[1] = {acc.value()}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0)
         st->mean_u = tot[0] / ((double)H * (double)W);
 }
@@ -635,12 +749,20 @@ k_user_mean(const float* __restrict__ src, int H, int W, DevState* st, double* p
     k_user_mean_body(src, H, W, st, partials, single_blk());
 }
 
-// xbar^K = (dL/dU - mean, 0, 0) into the residual planes
+// xbar^K = (dL/dU - mean, 0, 0) into the residual planes, with factor 1.
+//
+// Scaling of the sweep: the cotangent shrinks by about the same factor at every reverse step (by
+// 1e-7 per step on the 1024^2 workload's law: 1e-89 after 15 steps), far below float32's range.
+// The residual planes therefore hold xbar' with xbar = adj_scale * xbar' (adj_scale in FP64);
+// each step solves with xbar' / ||xbar'|| and multiplies what it accumulates by the running
+// factor, so no plane ever underflows (contributions below float32's range become 0, as they
+// would in float32 arithmetic of the unscaled sweep).
 __global__ void __launch_bounds__(kThreads)
-k_adj_init(Planes P, StencilArgs a, const float* __restrict__ dLdU, const DevState* st) {
+k_adj_init(Planes P, StencilArgs a, const float* __restrict__ dLdU, DevState* st) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blockIdx.x * kThreads + threadIdx.x;
     const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->adj_scale = 1.0;
     if (j >= W) return;
     const float m = (float)st->mean_u;
     for (int i = i0; i < i1; ++i) {
@@ -651,44 +773,94 @@ k_adj_init(Planes P, StencilArgs a, const float* __restrict__ dLdU, const DevSta
     }
 }
 
-// Adjoint solve set-up for step k: W^k, D^k from the checkpoint V^k, x = 0, r = xbar (already
-// in the residual planes); ||r||^2 is the scale of the relative stopping test.
-__device__ __forceinline__ void k_adj_setup_body(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
-            const float* __restrict__ Cv, const float* __restrict__ Ch, DevState* st,
-            double* partials, const Blk& blk) {
+// The adjoint solve A_k lambda = xbar through the U-only (Schur) system: its V rows give
+//   lambda_V = (tau xbar_V + S lambda_U) / (1 + tau D)     per edge,
+// and the U row becomes L_Om lambda_U = f with Om = D / (1 + tau D) and
+//   f = xbar_U + S^T (xbar_Vv / (1 + tau Dv)) + (xbar_Vh / (1 + tau Dh)) T^T.
+// The elimination is exact; it keeps lambda_V accurate edge by edge where D is large (the
+// weights of nearly consistent edges, D ~ C^2 / delta), where a float32 solve of the full
+// system resolves lambda_V only to the rounding of the largest component, which the next
+// reverse step amplifies by up to 1 / delta.  Set-up: W, D from the checkpoint V^k, f into
+// r_U (xbar_V stays in r_Vv, r_Vh for the recovery), lambda = 0, the stopping scale ||f||.
+__device__ __forceinline__ float adj_wd(float c, float v, float d2, float& w) {
+    w = sqrtf(c * c * v * v + d2);
+    return c * c / w;
+}
+
+// ||xbar'|| of a reverse step into st->adj_step, and the step's factor adj_scale * ||xbar'||
+// into st->adj_scale (the factor of this step's solution and of the next cotangent).
+__global__ void __launch_bounds__(kThreads)
+k_adj_norm(Planes P, StencilArgs a, DevState* st, double* partials) {
+    const Blk blk = single_blk();
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blk.bx * kThreads + threadIdx.x;
     const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
-    const float it = a.inv_tau, d2 = a.delta * a.delta;
-    float rr = 0.f, rzv = 0.f, su = 0.f;
+    CSum acc;
+    if (j < W)
+        for (int i = i0; i < i1; ++i) {
+            const size_t o = (size_t)i * ld + j;
+            const float u = P.rU[o], v = P.rVv[o], h = P.rVh[o];
+            acc.add(u * u + v * v + h * h);
+        }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double s = sqrt(tot[0]);
+        st->adj_step = s;
+        st->adj_scale = st->adj_scale * s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_adj_setup_schur(Planes P, StencilArgs a, const float* __restrict__ Vkv,
+                  const float* __restrict__ Vkh, const float* __restrict__ Cv,
+                  const float* __restrict__ Ch, DevState* st, double* partials) {
+    const Blk blk = single_blk();
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blk.bx * kThreads + threadIdx.x;
+    const int i0 = blk.by * kRows, i1 = strip_rows(H, i0);
+    const float tau = a.tau, d2 = a.delta * a.delta;
+    // the step's right-hand side normalised: xbar' / ||xbar'||
+    const double sn = st->adj_step;
+    const float inv = sn > 0.0 ? (float)(1.0 / sn) : 0.f;
+    CSum rr, su;
     if (j < W) {
         for (int i = i0; i < i1; ++i) {
             const size_t o = (size_t)i * ld + j;
-            float wv = 0.f, wh = 0.f, dv = 0.f, dh = 0.f;
+            float wv = 0.f, wh = 0.f, dv = 0.f, dh = 0.f, gv = 0.f, gh = 0.f, gvu = 0.f, ghl = 0.f;
             if (i + 1 < H) {
-                const float c = Cv[o], v = Vkv[o];
-                wv = sqrtf(c * c * v * v + d2);
-                dv = c * c / wv;
+                dv = adj_wd(Cv[o], Vkv[o], d2, wv);
+                gv = inv * P.rVv[o] / (1.f + tau * dv);
             }
             if (j + 1 < W) {
-                const float c = Ch[o], v = Vkh[o];
-                wh = sqrtf(c * c * v * v + d2);
-                dh = c * c / wh;
+                dh = adj_wd(Ch[o], Vkh[o], d2, wh);
+                gh = inv * P.rVh[o] / (1.f + tau * dh);
+            }
+            if (i > 0) {
+                float w;
+                gvu = inv * P.rVv[o - ld] / (1.f + tau * adj_wd(Cv[o - ld], Vkv[o - ld], d2, w));
+            }
+            if (j > 0) {
+                float w;
+                ghl = inv * P.rVh[o - 1] / (1.f + tau * adj_wd(Ch[o - 1], Vkh[o - 1], d2, w));
             }
             P.Wv[o] = wv; P.Wh[o] = wh; P.dv[o] = dv; P.dh[o] = dh;
             P.U[o] = 0.f; P.Vv[o] = 0.f; P.Vh[o] = 0.f;
-            const float ru = P.rU[o], rv = P.rVv[o], rh = P.rVh[o];
-            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
-            rr += ru * ru + rv * rv + rh * rh;
-            su += ru;
-            rzv += rv * rv / (dv + it) + rh * rh / (dh + it);
+            float h, l;
+            sum4_scaled(1.f, gvu, -gv, ghl, -gh, h, l);
+            const float f = __fadd_rn(inv * P.rU[o], __fadd_rn(h, l));
+            P.rU[o] = f;
+            if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, f);
+            rr.add(f * f);
+            su.add(f);
         }
     }
-    double v[3] = {(double)rr, (double)rzv, (double)su}, tot[3];
-    if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
-        const double rr_range = range_part(tot[0], tot[2], a.H, a.W);
+    double v[2] = {rr.value(), su.value()}, tot[2];
+    if (grid_reduce<2>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
+        const double rr_range = range_part(tot[0], tot[1], a.H, a.W);
         st->rr = rr_range;
-        st->rz_v = tot[1];
+        st->rz_v = 0.0;
+        st->rz_old = 0.0;
+        st->rnorm_u = sqrt(tot[0]);
         st->bb = rr_range;
         st->rel = rr_range > 0.0 ? 1.0 : 0.0;
         st->iter = 0;
@@ -697,11 +869,24 @@ __device__ __forceinline__ void k_adj_setup_body(Planes P, StencilArgs a, const 
     }
 }
 
+// lambda_V = (tau xbar_V + S lambda_U) / (1 + tau D) after the U-only adjoint solve, with the
+// step's normalised right-hand side xbar' / ||xbar'||
 __global__ void __launch_bounds__(kThreads)
-k_adj_setup(Planes P, StencilArgs a, const float* __restrict__ Vkv, const float* __restrict__ Vkh,
-            const float* __restrict__ Cv, const float* __restrict__ Ch, DevState* st,
-            double* partials) {
-    k_adj_setup_body(P, a, Vkv, Vkh, Cv, Ch, st, partials, single_blk());
+k_adj_recover_v(Planes P, StencilArgs a, const DevState* st) {
+    const int H = a.H, W = a.W, ld = a.ld;
+    const int j = blockIdx.x * kThreads + threadIdx.x;
+    const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
+    if (j >= W) return;
+    const double sn = st->adj_step;
+    const float tau = a.tau * (sn > 0.0 ? (float)(1.0 / sn) : 0.f);
+    for (int i = i0; i < i1; ++i) {
+        const size_t o = (size_t)i * ld + j;
+        const float u = P.U[o];
+        if (i + 1 < H)
+            P.Vv[o] = (tau * P.rVv[o] + (P.U[o + ld] - u)) / (1.f + a.tau * P.dv[o]);
+        if (j + 1 < W)
+            P.Vh[o] = (tau * P.rVh[o] + (P.U[o + 1] - u)) / (1.f + a.tau * P.dh[o]);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -709,11 +894,15 @@ k_adj_accumulate(Planes P, StencilArgs a, const float* __restrict__ Vkv,
                  const float* __restrict__ Vkh, const float* __restrict__ Vnv,
                  const float* __restrict__ Vnh, const float* __restrict__ Cv,
                  const float* __restrict__ Ch, float* __restrict__ Gbv, float* __restrict__ Gbh,
-                 float* __restrict__ Cbv, float* __restrict__ Cbh) {
+                 float* __restrict__ Cbv, float* __restrict__ Cbh, const DevState* st) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blockIdx.x * kThreads + threadIdx.x;
     const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
-    const float it = a.inv_tau, d2 = a.delta * a.delta;
+    const float d2 = a.delta * a.delta;
+    // the step's factor: lambda = F lambda'' for the normalised solve (float32: 0 once the
+    // contribution is below float32's range)
+    const float F = (float)st->adj_scale;
+    const float it = a.inv_tau * F;
     if (j >= W) return;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j;
@@ -726,7 +915,7 @@ k_adj_accumulate(Planes P, StencilArgs a, const float* __restrict__ Vkv,
             const float w = sqrtf(c * c * v * v + d2);
             const float w3 = w * w * w;
             const float db = -lv * Vnv[o];
-            Cbv[o] += db * (2.f * c / w - c * c * c * v * v / w3);
+            Cbv[o] += F * db * (2.f * c / w - c * c * c * v * v / w3);
             nv = db * (-(c * c * c * c) * v / w3);
         }
         if (j + 1 < W) {
@@ -736,7 +925,7 @@ k_adj_accumulate(Planes P, StencilArgs a, const float* __restrict__ Vkv,
             const float w = sqrtf(c * c * v * v + d2);
             const float w3 = w * w * w;
             const float db = -lh * Vnh[o];
-            Cbh[o] += db * (2.f * c / w - c * c * c * v * v / w3);
+            Cbh[o] += F * db * (2.f * c / w - c * c * c * v * v / w3);
             nh = db * (-(c * c * c * c) * v / w3);
         }
         P.rU[o] = 0.f;
@@ -750,13 +939,14 @@ k_adj_accumulate(Planes P, StencilArgs a, const float* __restrict__ Vkv,
 __global__ void __launch_bounds__(kThreads)
 k_adj_final(Planes P, StencilArgs a, const float* __restrict__ Gbv, const float* __restrict__ Gbh,
             const float* __restrict__ Cbv, const float* __restrict__ Cbh, float* __restrict__ dX,
-            float* __restrict__ dcoh) {
+            float* __restrict__ dcoh, const DevState* st) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j = blockIdx.x * kThreads + threadIdx.x;
     const int i0 = blockIdx.y * kRows, i1 = strip_rows(H, i0);
     if (j >= W) return;
-    auto gv = [&](size_t o) { return Gbv[o] - P.rVv[o]; };
-    auto gh = [&](size_t o) { return Gbh[o] - P.rVh[o]; };
+    const float F = (float)st->adj_scale;   // factor of the cotangent left in the planes
+    auto gv = [&](size_t o) { return Gbv[o] - F * P.rVv[o]; };
+    auto gh = [&](size_t o) { return Gbh[o] - F * P.rVh[o]; };
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j;
         float x = 0.f, c = 0.f;
@@ -813,9 +1003,10 @@ __global__ void __launch_bounds__(kThreads) kb_bnorm(const TileRec* __restrict__
     k_bnorm_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(kThreads) kb_reweight(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
-    k_reweight_residual_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_UPD)];
+    k_reweight_residual_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
 }
 
 template <int ROWS>
@@ -830,9 +1021,10 @@ __global__ void __launch_bounds__(kThreads) kb_update(const TileRec* __restrict_
     k_update_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(kThreads) kb_finalize(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_STRIP)];
-    k_finalize_reduce_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_UPD)];
+    k_finalize_reduce_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_subtract_mean(const TileRec* __restrict__ recs, int T) {
@@ -926,7 +1118,7 @@ __device__ __forceinline__ void k_schur_reweight_body(Planes P, StencilArgs a, D
         flux = om * (su - gv);
         fg = om * gv;
     };
-    float rr = 0.f, bb = 0.f, fd = 0.f, su_r = 0.f;
+    CSum rr, bb, fd, su_r;
     float uc = col ? P.U[(size_t)i0 * ld + j] : 0.f;
     float flux_up = 0.f, fg_up = 0.f;   // vertical edge (i - 1, j)
     if (col && i0 > 0) vedge(i0 - 1, flux_up, fg_up);
@@ -972,19 +1164,19 @@ __device__ __forceinline__ void k_schur_reweight_body(Planes P, StencilArgs a, D
             P.rU[o] = ru;
             if (!warm) P.U[o] = 0.f;
             if (a.r16 != nullptr) emit16(a.r16, a.r16lo, a.ld16, i, j, ru);
-            rr += ru * ru;
-            su_r += ru;
-            bb += fu * fu;
+            rr.add(ru * ru);
+            su_r.add(ru);
+            bb.add(fu * fu);
             // F_delta(x^k) with the edge residuals S U - V - G at the iterate
             const float evk = hv ? (un - uc - vv - gv) : 0.f;
             const float ehk = hh ? (ur - uc - vh - gh) : 0.f;
-            fd += wv + wh + 0.5f * it * (evk * evk + ehk * ehk);
+            fd.add(wv + wh + 0.5f * it * (evk * evk + ehk * ehk));
         }
         flux_up = flux_v;
         fg_up = fgv;
         uc = un;
     }
-    double v[4] = {(double)rr, (double)bb, (double)fd, (double)su_r}, tot[4];
+    double v[4] = {rr.value(), bb.value(), fd.value(), su_r.value()}, tot[4];
     if (grid_reduce<4>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[3], a.H, a.W);
         st->rr = rr_range;
@@ -1059,7 +1251,7 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
         ld4(Dh + o, dh);
         if (i0 + 1 < H) dir_u(o + ld, nu, rnu);
     }
-    float acc = 0.f;
+    CSum acc;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
@@ -1075,12 +1267,14 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
         if (act) {
             st4(pUn + o, cu);
             const float pr[4] = {cu[1], cu[2], cu[3], right};
+            float row = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const float yh = hh[e] ? (pr[e] - cu[e]) : 0.f;
                 const float yv = hv ? (nu[e] - cu[e]) : 0.f;
-                acc += omega_of(dv[e], tau) * yv * yv + omega_of(dh[e], tau) * yh * yh;
+                row += omega_of(dv[e], tau) * yv * yv + omega_of(dh[e], tau) * yh * yh;
             }
+            acc.add(row);
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1092,7 +1286,7 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
         rcu = rnu;
         rnu = rmu;
     }
-    double v[1] = {(double)acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (grid_reduce<1>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double pq = tot[0];
         st->pq = pq;
@@ -1167,7 +1361,7 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
     };
     SRow rc;
     if (act) load_row((size_t)i0 * ld + j0, rc);
-    float rr = 0.f, rzo = 0.f, su = 0.f;
+    CSum rr, rzo, su;
     for (int i = i0; i < i1; ++i) {
         const size_t o = (size_t)i * ld + j0;
         const bool hv = i + 1 < H;
@@ -1191,16 +1385,20 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
         const float yl[4] = {left, yh[0], yh[1], yh[2]};
         if (act) {
             float n0[4];
+            float prr = 0.f, psu = 0.f, przo = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 // (L_Om p) = S^T (Om_v S p) + (Om_h p T) T^T at this pixel
                 const float q = yvp[e] - yv[e] + yl[e] - yh[e];
                 u[e] += alpha * cu[e];
                 n0[e] = r0[e] - alpha * q;
-                rr += n0[e] * n0[e];
-                su += n0[e];
-                if (flex) rzo += n0[e] * z[e];
+                prr += n0[e] * n0[e];
+                psu += n0[e];
+                if (flex) przo += n0[e] * z[e];
             }
+            rr.add(prr);
+            su.add(psu);
+            if (flex) rzo.add(przo);
             st4(U + o, u);
             st4(rU + o, n0);
             if (a.r16 != nullptr) {
@@ -1217,7 +1415,7 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
         }
         rc = rn;
     }
-    double v[3] = {(double)rr, (double)rzo, (double)su}, tot[3];
+    double v[3] = {rr.value(), rzo.value(), su.value()}, tot[3];
     if (grid_reduce<3>(v, partials, &st->counter, tot, blk.nblk, blk.bid) && threadIdx.x == 0) {
         const double rr_range = range_part(tot[0], tot[2], a.H, a.W);
         st->rr = rr_range;
@@ -1287,8 +1485,15 @@ cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_reweight<<<total, kThreads, 0, s>>>(recs, T);
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_upd, int rows,
+                                    cudaStream_t s) {
+    switch (rows) {
+        case 8: kb_reweight<8><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 16: kb_reweight<16><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 24: kb_reweight<24><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 32: kb_reweight<32><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -1316,8 +1521,15 @@ cudaError_t launch_update_batched(const TileRec* recs, int T, int total, int row
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total, cudaStream_t s) {
-    kb_finalize<<<total, kThreads, 0, s>>>(recs, T);
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total, int total_upd,
+                                    int rows, cudaStream_t s) {
+    switch (rows) {
+        case 8: kb_finalize<8><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 16: kb_finalize<16><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 24: kb_finalize<24><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        case 32: kb_finalize<32><<<total_upd, kThreads, 0, s>>>(recs, T); break;
+        default: return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     kb_subtract_mean<<<total, kThreads, 0, s>>>(recs, T);
@@ -1351,6 +1563,7 @@ cudaError_t launch_rows(int rows, int H, int W, cudaStream_t s, Args... args) {
     return cudaGetLastError();
 }
 
+
 template <int R>
 struct DirK {
     static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
@@ -1362,6 +1575,20 @@ template <int R>
 struct UpdK {
     static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
         k_update<R><<<g, kThreads, 0, s>>>(P, a, st, pa);
+    }
+};
+
+template <int R>
+struct RwK {
+    static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
+        k_reweight_residual<R><<<g, kThreads, 0, s>>>(P, a, st, pa);
+    }
+};
+
+template <int R>
+struct FinK {
+    static void go(dim3 g, cudaStream_t s, Planes P, StencilArgs a, DevState* st, double* pa) {
+        k_finalize_reduce<R><<<g, kThreads, 0, s>>>(P, a, st, pa);
     }
 };
 
@@ -1391,8 +1618,7 @@ cudaError_t launch_norm_u(const Planes& P, const StencilArgs& a, DevState* st, d
 
 cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevState* st,
                                      double* partials, cudaStream_t s) {
-    k_reweight_residual<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
-    return cudaGetLastError();
+    return launch_rows<RwK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st, partials);
 }
 
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
@@ -1432,8 +1658,8 @@ cudaError_t launch_schur_recover_v(const Planes& P, const StencilArgs& a, cudaSt
 
 cudaError_t launch_finalize(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                             cudaStream_t s) {
-    k_finalize_reduce<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_rows<FinK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st,
+                                      partials);
     if (e != cudaSuccess) return e;
     k_subtract_mean<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P.U, a.H, a.W, a.ld, st);
     return cudaGetLastError();
@@ -1479,26 +1705,39 @@ cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_setup(const Planes& P, const StencilArgs& a, const float* Vkv,
-                             const float* Vkh, const float* Cv, const float* Ch, DevState* st,
-                             double* partials, cudaStream_t s) {
-    k_adj_setup<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Vkv, Vkh, Cv, Ch, st, partials);
+cudaError_t launch_adj_setup_schur(const Planes& P, const StencilArgs& a, const float* Vkv,
+                                   const float* Vkh, const float* Cv, const float* Ch,
+                                   DevState* st, double* partials, cudaStream_t s) {
+    k_adj_setup_schur<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Vkv, Vkh, Cv, Ch, st,
+                                                                 partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_recover_v(const Planes& P, const StencilArgs& a, const DevState* st,
+                                 cudaStream_t s) {
+    k_adj_recover_v<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_norm(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
+                            cudaStream_t s) {
+    k_adj_norm<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_accumulate(const Planes& P, const StencilArgs& a, const float* Vkv,
                                   const float* Vkh, const float* Vnv, const float* Vnh,
                                   const float* Cv, const float* Ch, float* Gbv, float* Gbh,
-                                  float* Cbv, float* Cbh, cudaStream_t s) {
+                                  float* Cbv, float* Cbh, const DevState* st, cudaStream_t s) {
     k_adj_accumulate<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Vkv, Vkh, Vnv, Vnh, Cv, Ch,
-                                                               Gbv, Gbh, Cbv, Cbh);
+                                                               Gbv, Gbh, Cbv, Cbh, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_final(const Planes& P, const StencilArgs& a, const float* Gbv,
                              const float* Gbh, const float* Cbv, const float* Cbh, float* dX,
-                             float* dcoh, cudaStream_t s) {
-    k_adj_final<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Gbv, Gbh, Cbv, Cbh, dX, dcoh);
+                             float* dcoh, const DevState* st, cudaStream_t s) {
+    k_adj_final<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P, a, Gbv, Gbh, Cbv, Cbh, dX, dcoh, st);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,59 @@
 
 namespace irls {
 
+// Compensated float32 sum (Knuth's two-sum): hi + lo carries the running sum of the added terms
+// with an error that does not grow with their number, at seven float32 operations per added
+// term.  The per-thread partials of every inner product of the CG iteration are accumulated in
+// one (each added term is a single value or a partial of at most four values of one image row),
+// then carried into the FP64 warp, block and grid sums as (double)hi + (double)lo.  The
+// intrinsics keep the compiler from contracting or reordering the error terms.
+struct CSum {
+    float hi, lo;
+    __device__ __forceinline__ CSum() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Error-free transformations in float32: a + b = s + e and a * b = p + e exactly (Knuth's
+// two-sum; the product's error from one fused multiply-add).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// The terms of A x that cancel (Sec. 3.2, the vectorised A), carried as hi + lo pairs so that
+// the difference keeps the accuracy of its float32 operands:
+//   s * (y0 + y1 + y2 + y3)        (the U row: s = 1/tau times a sum of four edge terms)
+//   d * v - s * y                   (a V row: D V minus the penalty term)
+__device__ __forceinline__ void sum4_scaled(float s, float y0, float y1, float y2, float y3,
+                                            float& hi, float& lo) {
+    float t, e1, e2, e3;
+    two_sum(y0, y1, t, e1);
+    two_sum(t, y2, t, e2);
+    two_sum(t, y3, t, e3);
+    two_prod(s, t, hi, lo);
+    lo = __fmaf_rn(s, __fadd_rn(__fadd_rn(e1, e2), e3), lo);
+}
+__device__ __forceinline__ void diff_prod(float d, float v, float s, float y, float& hi,
+                                          float& lo) {
+    float p1, e1, p2, e2, e3;
+    two_prod(d, v, p1, e1);
+    two_prod(s, y, p2, e2);
+    two_sum(p1, -p2, hi, e3);
+    lo = __fadd_rn(e3, __fsub_rn(e1, e2));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
