@@ -79,7 +79,8 @@ def test_batched_matches_oracle(irls):
     for t, d in enumerate(tiles):
         ref, env = oracle_with_envelope(d["X"], d["coherence"], kw)
         assert_unwrap_parity(Us[t].cpu().numpy(), ref["U"], st[t]["l1_obj"][-1],
-                             ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref)
+                             ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref, env=env,
+                             case=f"batch of 2, image {t} {d['X'].shape} bf16x3 (direct) tol 1e-6")
 
 
 def test_batched_folded_form_only_where_every_image_allows_it(irls):
@@ -147,17 +148,25 @@ def test_batched_folded_per_image_masks(irls):
 
 
 def test_batched_folded_matches_oracle(irls):
+    """The folded batched form (the 64-tile workload's form) on two images of the coherence law
+    with solves tight enough (cg_tol 1e-8) that U is determined: no envelope, per-outer H_delta
+    history too.  (At cg_tol 1e-6 the oracle's own U on the 256 x 320 image moves by 1.9e-3 rad
+    between solves cut at 1e-6 and at 1e-8, so a truncated comparison would measure where a
+    solve stops, not the batched form.)"""
+    from test_gpu_parity import assert_history
     shapes = [(256, 256), (256, 320)]
     tiles = [synthetic.config_2048(seed=400 + t, H=h, W=w) for t, (h, w) in enumerate(shapes)]
-    kw = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6, cg_max=1000)
-    with irls.Batch(shapes, precision="bf16x3", tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-6,
-                    cg_max_iter=1000) as b:
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-8, cg_max=3000)
+    with irls.Batch(shapes, precision="bf16x3", tau=1e-2, delta=1e-3, outer_iters=3, cg_tol=1e-8,
+                    cg_max_iter=3000) as b:
         assert b.folded
         Us, st = b.unwrap([cuda(d["X"]) for d in tiles], [cuda(d["coherence"]) for d in tiles])
     for t, d in enumerate(tiles):
-        ref, env = oracle_with_envelope(d["X"], d["coherence"], kw)
+        ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
         assert_unwrap_parity(Us[t].cpu().numpy(), ref["U"], st[t]["l1_obj"][-1],
-                             ref["l1_obj"][-1], d["X"], atol=parity_atol(env), ref=ref)
+                             ref["l1_obj"][-1], d["X"], ref=ref, strict=True,
+                             case=f"batch of 2, image {t} {d['X'].shape} bf16x3 (folded) tol 1e-8")
+        assert_history(st[t], ref, l1=False)
 
 
 @pytest.mark.parametrize("form", ["auto", "direct"])

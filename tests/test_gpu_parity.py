@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from oracle import irls as O
+import parity_log
 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -30,8 +31,18 @@ def cuda(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def k_agreement(U1, U2, X):
+def k_agreement(U1, U2, X, margin=None):
+    """Fraction of pixels whose integer ambiguity maps agree up to one global integer.  With a
+    margin (radians), only over the pixels where U2's value lies farther than the margin from a
+    rounding boundary of its map (where an error below margin / 2 in U1, and so in its circular
+    offset, cannot change the integer)."""
     d = O.k_map(U1, X) - O.k_map(U2, X)
+    if margin is not None:
+        X64 = np.asarray(X, dtype=np.float64)
+        c = float(np.angle(np.sum(np.exp(1j * (U2 - X64)))))
+        q = (U2 - c - X64) / (2.0 * np.pi)
+        keep = np.abs(q - np.rint(q)) < 0.5 - margin / (2.0 * np.pi)
+        d = d[keep]
     vals, cnt = np.unique(d, return_counts=True)
     return cnt.max() / d.size
 
@@ -55,34 +66,103 @@ def edge_residuals(ref):
     return e, c
 
 
-def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None, eps=1e-5):
-    """U within atol (both zero-mean), integer maps equal on >= 99.9 %, and the L1 objective
-    within l1_rtol relative plus 4 x the float32 floor of the oracle's own U.  Where edges whose
-    residual is below float32 trajectory noise (eps = 1e-5 rad) carry more of the objective than
-    the relative bar (2 eps sum_{|e|<eps} C > l1_rtol L1), |.| is not locally linear there and
-    no float32 trajectory can meet the bar: those edges get the bound the U agreement implies,
-    2 max|dU| sum C over the edges with |e| < max(eps, 2 max|dU|)."""
+def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None, eps=1e-5,
+                         case=None, strict=False, env=None, truncated=False):
+    """The acceptance bars of a float32 unwrap against the FP64 oracle, with the achieved errors
+    recorded (tests/parity_log.py):
+
+      * U within atol, both zero-mean (1e-3 rad, or the envelope's bar where one is passed);
+      * the integer maps equal on >= 99.9 % of the pixels; for a solve truncated after a few CG
+        iterations (``truncated``: U is far from an unwrapping and its bar is the truncated-solve
+        bound), equal on every pixel whose oracle value lies farther than 2 atol from a rounding
+        boundary (where an error within atol cannot flip the integer), the raw agreement being
+        recorded;
+      * the L1 objective of problem (main) evaluated in FP64 on the GPU's own U (with the
+        oracle's G and C) within l1_rtol relative, plus 4 x the float32 floor of the oracle's U
+        (what rounding U* to float32 alone changes; from the oracle only).  Where edges whose
+        oracle residual is below float32 trajectory noise (eps = 1e-5 rad) carry more of the
+        objective than the relative bar (2 eps sum_{|e|<eps} C > l1_rtol L1), |.| is not locally
+        linear there and those edges get the bound the U agreement implies,
+        2 max|dU| sum C over the edges with |e| < max(eps, 2 max|dU|) (|L1(U) - L1(U*)| is at
+        most sum C |S(U - U*)| over any set of edges).  ``strict`` requires atol = 1e-3: no
+        envelope of other executions.
+      * the library's own L1 statistic l1g (formed from U before the float32 removal of its
+        mean) equals the FP64 evaluation within what that rounding can move: one rounding of
+        max|U| per edge end.
+    """
+    Ug = np.asarray(Ug, dtype=np.float64)
     Ug = Ug - Ug.mean()
     Uo = Uo - Uo.mean()
-    err = np.abs(Ug - Uo).max()
-    assert err <= atol, f"max |U_gpu - U_oracle| = {err}"
-    tol = l1_rtol * max(abs(l1o), 1e-12) + 1e-9
+    err = float(np.abs(Ug - Uo).max())
+    bars = []
     if ref is not None:
-        tol += 4.0 * l1_float32_floor(ref)
+        pb = ref["problem"]
+        l1_gpu = O.l1_objective(Ug, pb.Gv, pb.Gh, pb.Cv, pb.Ch)
+        floor = l1_float32_floor(ref)
+        tol = l1_rtol * max(abs(l1o), 1e-12) + 1e-9 + 4.0 * floor
+        bars.append(f"floor {4 * floor / max(abs(l1o), 1e-30):.1e}")
         e, c = edge_residuals(ref)
         if 2.0 * eps * c[e < eps].sum() > l1_rtol * abs(l1o):
             thr = max(eps, 2.0 * err)
-            tol += 2.0 * err * c[e < thr].sum()
-    assert abs(l1g - l1o) <= tol, (l1g, l1o, tol)
-    assert k_agreement(Ug, Uo, X) >= 0.999
+            extra = 2.0 * err * c[e < thr].sum()
+            tol += extra
+            bars.append(f"small-edge {extra / max(abs(l1o), 1e-30):.1e}")
+        # the library's statistic: same U before the float32 mean removal
+        n_c = float(pb.Cv.sum() + pb.Ch.sum())
+        lib_tol = 2.0 * 2.0 ** -24 * (np.abs(Ug).max() + abs(float(Uo.mean())) + np.pi) * n_c \
+            + 1e-9 * abs(l1_gpu)
+    else:
+        l1_gpu = l1g
+        tol = l1_rtol * max(abs(l1o), 1e-12) + 1e-9
+        lib_tol = None
+    if env is not None:
+        bars.append(f"envelope {env:.1e}")
+    if strict:
+        bars.append("strict")
+        assert atol <= 1e-3 and env is None
+    kag = k_agreement(Ug, Uo, X)
+    kdec = k_agreement(Ug, Uo, X, margin=2.0 * atol) if truncated else None
+    if truncated:
+        bars.append(f"K decided {kdec:.5f}")
+    parity_log.record(case=case or "unwrap", err_u=err, atol=atol,
+                      dl1_rel=abs(l1_gpu - l1o) / max(abs(l1o), 1e-30),
+                      l1_bar_rel=tol / max(abs(l1o), 1e-30), k_agree=kag, l1=l1o,
+                      bars=", ".join(bars) or "-")
+    assert err <= atol, f"max |U_gpu - U_oracle| = {err}"
+    assert abs(l1_gpu - l1o) <= tol, (l1_gpu, l1o, tol)
+    if lib_tol is not None:
+        assert abs(l1g - l1_gpu) <= lib_tol, ("library L1 statistic", l1g, l1_gpu, lib_tol)
+    if truncated:
+        assert kdec == 1.0, (kdec, kag)
+    else:
+        assert kag >= 0.999, kag
+
+
+def assert_history(st, ref, l1=True, l1_rtol=1e-4, h_rtol=1e-5):
+    """Per outer step, the library's H_delta(x^{k+1}, W^k) statistic against the oracle's within
+    h_rtol, and with ``l1`` its L1 statistic within l1_rtol (where the trajectory is determined:
+    solves tight enough that equally valid executions agree; the L1 history only on images whose
+    objective is carried by residues, not by edges at float32 noise)."""
+    n = len(ref["l1_obj"])
+    assert st["outer_done"] == n
+    l1g, l1o = np.array(st["l1_obj"]), np.array(ref["l1_obj"])
+    hg, ho = np.array(st["h_delta"]), np.array(ref["h_delta"])
+    dl1 = np.abs(l1g - l1o) / np.abs(l1o)
+    dh = np.abs(hg - ho) / np.abs(ho)
+    parity_log.record(case="  per-outer history", err_u=float("nan"), atol=float("nan"),
+                      dl1_rel=float(dl1.max()), l1_bar_rel=l1_rtol if l1 else float("nan"),
+                      k_agree=float("nan"), l1=float(l1o[-1]),
+                      bars=f"H_delta max rel {dh.max():.1e} (bar {h_rtol:.0e})")
+    if l1:
+        assert np.all(dl1 <= l1_rtol), (l1g, l1o)
+    assert np.all(dh <= h_rtol), (hg, ho)
 
 
 def oracle_with_envelope(X, coh, kw, Cv=None, Ch=None):
     """The oracle's result plus the spread between equally valid floating-point executions of
     the same algorithm: the algebraically identical Polak-Ribiere ratio instead of the
-    Fletcher-Reeves one of Alg. 2, the CG vectors stored in float32 (the library's storage type,
-    arithmetic still float64), CG's scalars perturbed at the level of float32 partial sums, and
-    the weights perturbed at float32 level (relative 1e-7).
+    Fletcher-Reeves one of Alg. 2, and the CG vectors stored in float32 (the library's storage
+    type; arithmetic still float64), alone and together.
     Where the truncated CG solves leave U weakly determined this spread is what any float32
     trajectory can promise; where it is small the 1e-3 rad bar applies unchanged."""
     base = O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, **kw)
@@ -90,19 +170,6 @@ def oracle_with_envelope(X, coh, kw, Cv=None, Ch=None):
     runs = [O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, beta_rule="pr", **kw),
             O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, **kw),
             O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32, beta_rule="pr", **kw)]
-    # CG's scalars from inner products summed out of float32 partial sums (relative 1e-7 and
-    # 1e-6): on ill-conditioned solves this moves the iteration at which ||r|| crosses cg_tol
-    for rel, sd in ((1e-7, 1), (1e-6, 2)):
-        runs.append(O.irls_unwrap(X, coh, Cv=Cv, Ch=Ch, storage=np.float32,
-                                  scalar_rounding=(rel, sd), **kw))
-    for s in (0, 1):
-        rng = np.random.default_rng(100 + s)
-        if Cv is not None:
-            runs.append(O.irls_unwrap(X, None, Cv=Cv * (1 + 1e-7 * rng.standard_normal(Cv.shape)),
-                                      Ch=Ch * (1 + 1e-7 * rng.standard_normal(Ch.shape)), **kw))
-        elif coh is not None:
-            c2 = coh.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(coh.shape))
-            runs.append(O.irls_unwrap(X, c2, **kw))
     env = max([0.0] + [np.abs((r["U"] - r["U"].mean()) - U0).max() for r in runs])
     return base, env
 
@@ -229,7 +296,7 @@ def test_folded_and_direct_forms_agree(irls, H, W):
                             plan=irls.Plan(Hu, Wu, tau=1e-2, delta=1e-3, outer_iters=6,
                                            cg_tol=1e-6, precision="bf16x3", dct_form=form))
         assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], X,
-                             ref=ref)
+                             ref=ref, case=f"{Hu}x{Wu} uniform bf16x3 ({form}) tol 1e-6")
 
 
 def test_folded_form_only_where_allowed(irls):
@@ -325,6 +392,9 @@ def test_apply_A_full_size_sampled(irls):
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", [0, 1])
 def test_unwrap_256_matches_oracle(irls, seed):
+    """The 256 x 256 uniform-weight workload (10 outer steps, cg_tol 1e-5): no envelope.  Its
+    unwraps are almost perfect (L1 objective ~1e-2, at the float32 resolution of U: rounding the
+    oracle's own U to float32 changes L1 by 80-600 %), so the L1 bar carries the float32 floor."""
     d = synthetic.config_small(seed)
     kw = dict(tau=1e-2, delta=1e-3, outer_iters=10, cg_tol=1e-5, cg_max=1000)
     ref = O.irls_unwrap(d["X"], None, **kw)
@@ -332,8 +402,7 @@ def test_unwrap_256_matches_oracle(irls, seed):
                         return_stats=True)
     assert st["outer_done"] == 10
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         ref=ref)
-
+                         ref=ref, case=f"256x256 uniform seed {seed} fp32 tol 1e-5", strict=True)
 
 
 @pytest.mark.parametrize("H,W,seed", [(100, 75, 3), (67, 131, 4)])
@@ -344,7 +413,8 @@ def test_unwrap_ragged_with_coherence_matches_oracle(irls, H, W, seed):
     U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=6,
                         cg_tol=1e-6, return_stats=True)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"{H}x{W} coherence fp32 tol 1e-6")
     # F_delta(x^k) = sum W + penalty is dominated by delta * (number of edges) at intermediate
     # iterates, so its trajectory is compared at 1e-3 and the converged value at 1e-5
     np.testing.assert_allclose(st["f_delta"], ref["h_before"], rtol=1e-3)
@@ -353,16 +423,19 @@ def test_unwrap_ragged_with_coherence_matches_oracle(irls, H, W, seed):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 def test_unwrap_ill_conditioned_within_oracle_envelope(irls, prec):
-    """Patches of low coherence and 3 pi steps (the 4096 x 4096 workload's law at 96 x 80):
-    L1 objective within 1e-4 relative and >= 99.9 % equal integer maps (unique quantities), and
-    U within max(1e-3, 2 x the spread of equally valid FP64 executions)."""
+    """Patches of low coherence and 3 pi steps (the 4096 x 4096 workload's law at 96 x 80), at the
+    benchmark's cg_tol 1e-6: L1 objective within 1e-4 relative and >= 99.9 % equal integer maps
+    (unique quantities), and U within max(1e-3, 2 x the spread of equally valid FP64 executions:
+    the Polak-Ribiere ratio, float32 storage), since the truncated solves leave U weakly
+    determined (the oracle's own U moves by 2.7e-3 rad between those executions)."""
     d = synthetic.config_4096_mixed(seed=12, H=96, W=80)
     kw = dict(tau=1e-2, delta=1e-3, outer_iters=4, cg_tol=1e-6, cg_max=1000)
     ref, env = oracle_with_envelope(d["X"], d["coherence"], kw)
     U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=4, cg_tol=1e-6,
                         precision=prec, return_stats=True)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"96x80 mixed-law {prec} tol 1e-6")
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
@@ -374,7 +447,8 @@ def test_unwrap_256_tensor_core_matches_oracle(irls, seed, prec):
     U, st = irls.unwrap(cuda(d["X"]), None, eps=1e-3, outer_iters=10, cg_tol=1e-5,
                         precision=prec, return_stats=True)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         ref=ref)
+                         ref=ref, case=f"256x256 uniform seed {seed} {prec} tol 1e-5",
+                         strict=True)
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
@@ -386,7 +460,49 @@ def test_unwrap_tensor_core_with_coherence_matches_oracle(irls, H, W, seed, prec
     U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), eps=1e-3, outer_iters=6,
                         cg_tol=1e-6, precision=prec, return_stats=True)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"{H}x{W} coherence {prec} tol 1e-6")
+
+
+# Determined trajectories: solves tight enough (cg_tol 1e-8) that U no longer depends on where a
+# truncated solve stops, compared with no envelope at the stated bars (1e-3 rad, L1 within 1e-4
+# relative evaluated in FP64 on the GPU's U, >= 99.9 % equal integer maps), with the per-outer
+# L1 and H_delta statistics.  One law per workload family: coherence weights (the 2048 x 2048
+# law), low-coherence patches and 3 pi steps (the 4096 x 4096 law).
+DETERMINED = dict(tau=1e-2, delta=1e-3, cg_tol=1e-8, cg_max=3000)
+_DET_REF = {}
+
+
+def determined_reference(law, H, W, seed, outer):
+    key = (law, H, W, seed, outer)
+    if key not in _DET_REF:
+        gen = synthetic.config_2048 if law == "coherence" else synthetic.config_4096_mixed
+        d = gen(seed=seed, H=H, W=W)
+        _DET_REF[key] = (d, O.irls_unwrap(d["X"], d["coherence"], outer_iters=outer,
+                                          **DETERMINED))
+    return _DET_REF[key]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16"])
+@pytest.mark.parametrize("law,H,W,seed,outer", [("coherence", 256, 384, 5, 6),
+                                                ("mixed", 96, 80, 12, 4),
+                                                ("mixed", 256, 256, 12, 4)])
+def test_unwrap_determined_matches_oracle(irls, law, H, W, seed, outer, prec):
+    """The coherence law's objective (about 40 at 256 x 384) sits mostly on edges at float32
+    noise, so its per-outer history is compared through H_delta only; the mixed law's (370 and
+    1900) is carried by residues and its L1 history is compared too."""
+    if prec == "fp16" and min(H, W) < 256:
+        pytest.skip("the float16 preconditioner runs the folded form (sides >= 256)")
+    d, ref = determined_reference(law, H, W, seed, outer)
+    with irls.Plan(H, W, precision=prec, tau=1e-2, delta=1e-3, outer_iters=outer, cg_tol=1e-8,
+                   cg_max_iter=3000) as p:
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+        form = "folded" if p.folded else "direct"
+    assert st["return_code"] == 0
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
+                         ref=ref, strict=True,
+                         case=f"{H}x{W} {law}-law {prec} ({form}) tol 1e-8")
+    assert_history(st, ref, l1=(law == "mixed"))
 
 
 def test_unwrap_line_images(irls):
@@ -395,7 +511,7 @@ def test_unwrap_line_images(irls):
         ref = O.irls_unwrap(X, None, tau=1e-2, delta=1e-3, outer_iters=4, cg_tol=1e-6)
         U, st = irls.unwrap(cuda(X), None, eps=1e-3, outer_iters=4, cg_tol=1e-6, return_stats=True)
         assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], X,
-                             ref=ref)
+                             ref=ref, case=f"{H}x{W} line image fp32 tol 1e-6")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -413,7 +529,8 @@ def test_unwrap_2048_first_outer_matches_oracle(irls, prec):
     # 2048) reaches U about once per iteration: 4 x 5e-5 x max|U|
     atol = 1e-3 if prec == "fp32" else max(1e-3, 4 * 5e-5 * np.abs(ref["U"]).max())
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=atol, ref=ref)
+                         atol=atol, ref=ref, case=f"2048x2048 coherence {prec} 1 step x 4 CG",
+                         truncated=True)
 
 
 def test_unwrap_2048_invariants(irls):
@@ -490,7 +607,8 @@ def test_user_edge_weights_take_precedence(irls):
     U, st = irls.unwrap(cuda(d["X"]), cuda(d["coherence"]), Cv=cuda(Cv ** 2), Ch=cuda(Ch ** 2),
                         eps=1e-3, outer_iters=4, cg_tol=1e-6, return_stats=True)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case="50x60 explicit edge weights fp32 tol 1e-6")
 
 
 def test_host_arrays_round_trip(irls):

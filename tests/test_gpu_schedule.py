@@ -87,7 +87,8 @@ def test_paper_schedule_matches_oracle(irls, prec):
     assert st["return_code"] == 0
     check_rule(st)
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"96x80 Sec. 4.3 CG schedule {prec}")
 
 
 def test_paper_schedule_2048_follows_the_rule(irls):

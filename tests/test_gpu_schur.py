@@ -35,7 +35,8 @@ def test_schur_matches_oracle(irls, H, W, seed, prec):
                         cg_tol=1e-6, precision=prec, system="schur", return_stats=True)
     assert st["return_code"] == 0
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"{H}x{W} coherence U-only {prec} tol 1e-6")
     # the objectives of Sec. 3.1 recorded along the way agree too
     np.testing.assert_allclose(st["h_delta"], ref["h_delta"], rtol=2e-4)
 

@@ -62,7 +62,8 @@ def test_unwrap_parity_any_tile_shape(irls, tiles, prec):
         p.set_tiles(*tiles)
         U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
-                         atol=parity_atol(env), ref=ref)
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case=f"203x613 coherence {prec} tiles {tiles} tol 1e-6")
 
 
 def test_tile_shape_changes_rounding_only(irls):

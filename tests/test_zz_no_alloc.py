@@ -46,6 +46,38 @@ def test_noalloc_matches_plan_entry_point_on_consecutive_calls(irls):
         assert float((Z - Z_ref).abs().max()) <= 2e-5 * scale
 
 
+def _noalloc(irls, R, tau):
+    L = irls.lib()
+    H, W = R.shape
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    Z = torch.full_like(R, float("nan"))
+    rc = L.irls_precond_laplacian_noalloc(ctypes.c_void_p(R.data_ptr()),
+                                          ctypes.c_void_p(Z.data_ptr()), H, W,
+                                          ctypes.c_float(tau), stream)
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    return Z.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("H,W", [(17, 33), (1, 200), (255, 3), (256, 255), (255, 256), (200, 1)])
+def test_noalloc_matches_oracle(irls, H, W):
+    """Against the FP64 oracle's Laplacian block (Sec. 3.3: the Sylvester solve in the DCT
+    eigenbasis, zero frequency dropped), at the float32 preconditioner's bound: 2e-5 of the
+    largest output.  (1, 200) and (200, 1) have a single eigenvalue 0 along one side, (255, 3)
+    and (17, 33) are odd and ragged, and (256, 255) / (255, 256) use the whole buffer: the
+    entry point refuses any shape whose layout would not fit it (IRLS_ERR_SHAPE), so a change of
+    the layout shows here as a refusal, never as a write beyond the buffer."""
+    from oracle import irls as O
+    tau = 1e-2
+    R = np.random.default_rng(H * 1000 + W).standard_normal((H, W)).astype(np.float32)
+    Z = _noalloc(irls, torch.as_tensor(R).cuda(), tau)
+    z_ref = O.precond_apply((R.astype(np.float64), np.zeros((H - 1, W)), np.zeros((H, W - 1))),
+                            np.zeros((H - 1, W)), np.zeros((H, W - 1)), tau, O.dct_basis(H),
+                            O.dct_basis(W))[0]
+    scale = np.abs(z_ref).max() + 1e-30
+    assert np.abs(Z - z_ref).max() <= 2e-5 * scale
+
+
 def test_noalloc_rejects_sizes_beyond_its_buffer(irls):
     L = irls.lib()
     R = torch.zeros(300, 300, device="cuda")
