@@ -86,6 +86,7 @@ extern "C" {
 typedef struct irls_plan_s* irls_plan;   /* opaque: device workspace, DCT bases, device state */
 typedef struct irls_tape_s* irls_tape;   /* opaque: checkpoints of a recorded forward solve   */
 typedef struct irls_batch_s* irls_batch; /* opaque: a batched solve of many images            */
+typedef struct irls_tiled_s* irls_tiled; /* opaque: a tiled solve of one large image          */
 
 /* Solver options.  Defaults (irls_opts_default): tau = 1e-2 and delta = 1e-6 (the paper's
  * model parameters, Sec. 4.4), outer_iters = 20, cg_tol = 1e-6, cg_max_iter = 1000,
@@ -255,6 +256,35 @@ int irls_unwrap_batched(int ntiles, const int* H, const int* W, const float* con
 int irls_batch_uses_graphs(irls_batch batch);
 int irls_batch_dct_form(irls_batch batch);
 
+/* Tiled unwrapping of one large image: the paper leaves very large images to future work
+ * (Sec. 5, after the 4000 x M study of Sec. 4.5); this is that step built on the batched form.
+ * The H x W image is cut into overlapping tiles of min(tile, H) x min(tile, W) pixels: along a
+ * side of n pixels the tiles start at 0, tile - overlap, 2 (tile - overlap), ... while a tile
+ * ends before n, and one more tile ends flush at n (one tile when n <= tile).  All tiles are
+ * solved as one batch (irls_batch_create with `opts`; the batched form's precision rules
+ * apply).  Each tile's solution is then shifted by a constant c_t: for every pair of
+ * neighbouring tiles (next column or next row of tiles) d_ts is the mean of U_t - U_s over
+ * their overlap, taken again over the pixels within pi of that first mean; c minimises
+ * sum n_ts (c_s - c_t - d_ts)^2 (n_ts: the pixels of that second mean) with c_0 = 0.  Each
+ * pixel of d_U takes U_t + c_t from the tile whose core holds it (consecutive tiles split their
+ * overlap at (start of the next + end of this) / 2, rounded down), and d_U is made zero-mean.
+ *   irls_tiled_create: 1 <= overlap < tile (IRLS_ERR_ARG otherwise); allocates the
+ *     batch and the tiles' inputs and outputs (3 floats per tile pixel).  Synchronous.
+ *   irls_tiled_info: the number of tiles, their height and width and the neighbour pairs
+ *     (host pointers, non-NULL).  irls_tiled_batch: the underlying batch (for its tile shapes
+ *     and autotuning; owned by the tiled handle).
+ *   irls_unwrap_tiled: d_X, d_coherence (NULL: uniform weights) and d_U are H x W device
+ *     arrays; per_tile (nullable) receives n_tiles statistics and h_constants (nullable)
+ *     n_tiles constants.  Synchronous with respect to the host; the status is the batch's.
+ * No paper counterpart for the stitching rule (the paper states no procedure). */
+int irls_tiled_create(int H, int W, int tile, int overlap, const irls_opts* opts,
+                      irls_tiled* out);
+int irls_tiled_destroy(irls_tiled tiled);
+int irls_tiled_info(irls_tiled tiled, int* n_tiles, int* tile_h, int* tile_w, int* n_pairs);
+int irls_tiled_batch(irls_tiled tiled, irls_batch* batch);
+int irls_unwrap_tiled(irls_tiled tiled, const float* d_X, const float* d_coherence, float* d_U,
+                      irls_stats* per_tile, double* h_constants, void* stream);
+
 /* Tile shapes of the batched CG direction and update launches (one value per batch, the same
  * meaning and allowed values as irls_plan_set_tiles; defaults 24 and 32).  An image's blocks,
  * and so its results, are those of a single-image plan with the same tile shapes.
@@ -333,9 +363,12 @@ int irls_best_shift_error(irls_plan plan, const float* d_U, const float* d_Xu, f
  *   d_R, d_Z  H x W float32 device arrays, row-major and contiguous, owned by the caller;
  *   tau       > 0 (the penalty of the plan-based form);
  *   returns   IRLS_ERR_SHAPE if H or W is < 1 or > IRLS_NOALLOC_MAX_SIDE, IRLS_ERR_ARG for a
- *             null pointer or tau <= 0, IRLS_ERR_CUDA if a launch fails; asynchronous on stream.
+ *             null pointer or tau <= 0, IRLS_ERR_UNSUPPORTED if the current device's ordinal is
+ *             64 or more, IRLS_ERR_CUDA if a launch fails; asynchronous on stream.
  * The first call on a device looks up the buffer's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the one
+ * that device current and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call the entry point on a device after cudaDeviceReset in the same
+ * process (the reset unloads the module, and the kept address would be stale).  All calls share the one
  * buffer and each call rewrites every part of it that it reads, so nothing needs clearing
  * between calls - but calls that overlap on the GPU (other streams or host threads without
  * ordering between them) race on the buffer and corrupt each other's results. */

@@ -38,6 +38,7 @@ __all__ = [
     "round_congruent", "schur_weights", "schur_matvec", "schur_rhs", "schur_recover_v",
     "pcg_schur",
     "best_shift_error", "dense_operators", "Problem", "irls_adjoint",
+    "tile_starts", "tile_cores", "overlap_offset", "stitch_tiles", "irls_unwrap_tiled",
 ]
 
 TWO_PI_F32 = np.float32(2.0 * np.pi)
@@ -655,3 +656,117 @@ def irls_adjoint(X, coherence, dL_dU, *, tau=1e-2, delta=1e-3, outer_iters=10, c
         cbar[:, 1:] += 0.5 * Cbh
     return Xbar, cbar, fwd
 
+
+
+# --------------------------------------------------------------------------------------------
+# Tiled unwrapping of a large image (the paper's future-work remark on very large images,
+# Sec. 5, with the 4000 x M images of Sec. 4.5): overlapping tiles solved independently by
+# Alg. 1, then each tile's free constant fixed by agreement on the overlaps.  The paper gives
+# no procedure; the readings are:
+#   * tile starts along a side of n pixels with tile t and overlap o: 0, t - o, 2 (t - o), ...
+#     while the tile ends before n, then a last tile ending flush at n (every tile is t long;
+#     one tile of n when n <= t);
+#   * the offset between tiles s and t that are neighbours in the tile grid (same row of tiles,
+#     next column, or same column, next row) is the mean of U_t - U_s over their overlap,
+#     taken again over the pixels within pi of that first mean (pixels where the two tiles
+#     unwrapped a different number of cycles do not pull it);
+#   * constants c minimising sum over neighbour pairs of n_st (c_s - c_t - d_ts)^2 with
+#     d_ts = offset(U_t - U_s) and c_0 = 0 (weights n_st: the pixels the second mean used);
+#   * each pixel is taken from the tile whose core holds it: consecutive tiles split their
+#     overlap at (start of the next + end of this) // 2; the stitched image is made zero-mean.
+# --------------------------------------------------------------------------------------------
+def tile_starts(n, t, o):
+    """Starts of the tiles along a side of n pixels (tile t, overlap o, 0 <= o < t)."""
+    if n <= t:
+        return [0]
+    s, out = t - o, []
+    a = 0
+    while a + t < n:
+        out.append(a)
+        a += s
+    out.append(n - t)
+    return out
+
+
+def tile_cores(starts, t, n):
+    """[lo, hi) of each tile's core along one side: consecutive tiles split their overlap at
+    (start of the next + end of this) // 2."""
+    t = min(t, n)
+    bounds = [0] + [(starts[a + 1] + starts[a] + t) // 2 for a in range(len(starts) - 1)] + [n]
+    return [(bounds[a], bounds[a + 1]) for a in range(len(starts))]
+
+
+def overlap_offset(Ut, Us):
+    """Robust mean of Ut - Us over an overlap (both arrays of the overlap's shape): the mean,
+    then the mean again over the pixels within pi of it.  Returns (offset, pixel count)."""
+    d = (Ut - Us).ravel()
+    m0 = float(d.mean())
+    keep = np.abs(d - m0) < np.pi
+    if not keep.any():
+        return m0, d.size
+    return float(d[keep].mean()), int(keep.sum())
+
+
+def stitch_tiles(sol, rs, cs, th, tw, H, W):
+    """Fixes the constants of tile solutions sol[t] (tile t = a * len(cs) + b at rows
+    rs[a]:rs[a]+th, columns cs[b]:cs[b]+tw) by least squares on the neighbour offsets and
+    stitches the cores into a zero-mean H x W image.  Returns (U, constants, pairs)."""
+    nc = len(cs)
+    pairs = []
+    for a in range(len(rs)):
+        for b in range(nc):
+            t = a * nc + b
+            for (a2, b2) in ((a, b + 1), (a + 1, b)):
+                if a2 >= len(rs) or b2 >= nc:
+                    continue
+                s = a2 * nc + b2
+                r0, c0 = max(rs[a], rs[a2]), max(cs[b], cs[b2])
+                r1, c1 = min(rs[a], rs[a2]) + th, min(cs[b], cs[b2]) + tw
+                if r1 <= r0 or c1 <= c0:
+                    continue
+                Ut = sol[t][r0 - rs[a]:r1 - rs[a], c0 - cs[b]:c1 - cs[b]]
+                Us = sol[s][r0 - rs[a2]:r1 - rs[a2], c0 - cs[b2]:c1 - cs[b2]]
+                d, n = overlap_offset(Ut, Us)
+                pairs.append((t, s, d, n))
+    T = len(rs) * nc
+    c = np.zeros(T)
+    if T > 1:
+        # normal equations of sum n (c_s - c_t - d)^2 with c_0 fixed at 0
+        A = np.zeros((T, T))
+        rhs = np.zeros(T)
+        for t, s, d, n in pairs:
+            A[t, t] += n
+            A[s, s] += n
+            A[t, s] -= n
+            A[s, t] -= n
+            rhs[s] += n * d
+            rhs[t] -= n * d
+        c[1:] = np.linalg.solve(A[1:, 1:], rhs[1:])
+    U = np.zeros((H, W))
+    rc, cc = tile_cores(rs, th, H), tile_cores(cs, tw, W)
+    for a, (lo_r, hi_r) in enumerate(rc):
+        for b, (lo_c, hi_c) in enumerate(cc):
+            t = a * nc + b
+            U[lo_r:hi_r, lo_c:hi_c] = (sol[t][lo_r - rs[a]:hi_r - rs[a], lo_c - cs[b]:hi_c - cs[b]]
+                                       + c[t])
+    U -= U.mean()
+    return U, c, pairs
+
+
+def irls_unwrap_tiled(X, coherence=None, *, tile=256, overlap=32, **kw):
+    """Unwraps X tile by tile (Alg. 1 on each overlapping tile, keyword arguments as in
+    irls_unwrap), fixes the tiles' constants by least squares on the neighbour offsets and
+    stitches the cores.  Returns a dict with U (zero mean), the tiles' solutions and constants."""
+    X = np.asarray(X, dtype=np.float32)
+    H, W = X.shape
+    rs, cs = tile_starts(H, tile, overlap), tile_starts(W, tile, overlap)
+    th, tw = min(tile, H), min(tile, W)
+    tiles = [(r, c) for r in rs for c in cs]
+    sol = []
+    for r, c in tiles:
+        co = None if coherence is None else np.asarray(coherence)[r:r + th, c:c + tw]
+        out = irls_unwrap(X[r:r + th, c:c + tw], co, **kw)
+        sol.append(out["U"])
+    U, c, pairs = stitch_tiles(sol, rs, cs, th, tw, H, W)
+    return {"U": U, "tiles": tiles, "tile_U": sol, "constants": c, "pairs": pairs,
+            "row_starts": rs, "col_starts": cs}

@@ -13,7 +13,7 @@ import ctypes
 from ._binding import (CG_SCHEDULES, DCT_FORMS, SYSTEMS, IRLS_MAX_OUTER, PRECISIONS, IrlsError, Opts, Stats, check, default_opts,
                        lib)
 
-__all__ = ["Plan", "Batch", "unwrap", "precond_laplacian", "apply_A", "round_congruent",
+__all__ = ["Plan", "Batch", "Tiled", "unwrap", "precond_laplacian", "apply_A", "round_congruent",
            "best_shift_error", "default_opts", "lib", "IrlsError",
            "Opts", "Stats", "PRECISIONS", "unwrap_differentiable"]
 
@@ -296,6 +296,65 @@ class Batch:
         rc = lib().irls_unwrap_batched_ex(self._h, xa, ca, ua, st, _stream(stream))
         check(rc, "irls_unwrap_batched_ex")
         return Us, [x.to_dict() for x in st]
+
+
+class Tiled:
+    """A tiled solve of one large H x W image (irls_tiled_*): overlapping tiles of side `tile`
+    with `overlap` pixels in common, solved as one batch, then stitched by constants fixed on
+    the overlaps.  Options as for Batch (precision bf16x3 by default)."""
+
+    def __init__(self, H, W, tile=1024, overlap=64, **opts):
+        if "precision" not in opts:
+            opts["precision"] = "bf16x3"
+        self.H, self.W, self.tile, self.overlap = int(H), int(W), int(tile), int(overlap)
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        check(lib().irls_tiled_create(self.H, self.W, self.tile, self.overlap,
+                                      ctypes.byref(self.opts), ctypes.byref(h)),
+              "irls_tiled_create")
+        self._h = h
+        n, th, tw, npair = (ctypes.c_int() for _ in range(4))
+        check(lib().irls_tiled_info(h, ctypes.byref(n), ctypes.byref(th), ctypes.byref(tw),
+                                    ctypes.byref(npair)), "irls_tiled_info")
+        self.n_tiles, self.tile_shape, self.n_pairs = n.value, (th.value, tw.value), npair.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().irls_tiled_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, stream=None):
+        """Times the batched stencil tile shapes on this solve's batch and keeps the fastest."""
+        b = ctypes.c_void_p()
+        check(lib().irls_tiled_batch(self._h, ctypes.byref(b)), "irls_tiled_batch")
+        ms = (ctypes.c_float * 8)()
+        check(lib().irls_batch_autotune(b, ms, _stream(stream)), "irls_batch_autotune")
+        return list(ms)
+
+    def unwrap(self, X, coherence=None, out=None, stream=None):
+        """X, coherence: H x W float32 CUDA tensors; returns (U, per-tile stats, constants)."""
+        torch = _torch()
+        if tuple(X.shape) != (self.H, self.W):
+            raise ValueError("image shape does not match the tiled solve")
+        U = out if out is not None else torch.empty_like(X)
+        st = (Stats * self.n_tiles)()
+        c = (ctypes.c_double * self.n_tiles)()
+        rc = lib().irls_unwrap_tiled(self._h, _ptr(X), _ptr(coherence), _ptr(U), st, c,
+                                     _stream(stream))
+        check(rc, "irls_unwrap_tiled")
+        return U, [x.to_dict() for x in st], list(c)
 
 
 def precond_laplacian(plan, R, stream=None):

@@ -116,6 +116,13 @@ SIGNATURES = {
     "irls_batch_set_tiles": (_I, [_P, _I, _I]),
     "irls_batch_get_tiles": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "irls_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
+    "irls_tiled_create": (_I, [_I, _I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "irls_tiled_destroy": (_I, [_P]),
+    "irls_tiled_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(_I)]),
+    "irls_tiled_batch": (_I, [_P, ctypes.POINTER(_P)]),
+    "irls_unwrap_tiled": (_I, [_P, _P, _P, _P, ctypes.POINTER(Stats),
+                               ctypes.POINTER(ctypes.c_double), _P]),
     "irls_precond_laplacian": (_I, [_P, _P, _P, _P]),
     "irls_apply_A": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "irls_precond_laplacian_noalloc": (_I, [_P, _P, _I, _I, _F, _P]),

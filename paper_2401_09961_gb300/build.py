@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libirls.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["irls_kernels.cu", "dct.cu", "dct_umma.cu", "irls_api.cu", "noalloc.cu", "post.cu"]
+SOURCES = ["irls_kernels.cu", "dct.cu", "dct_umma.cu", "irls_api.cu", "noalloc.cu", "post.cu",
+           "tiled.cu"]
 
 
 def _nvcc():
