@@ -374,16 +374,17 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["sm_mhz_median_timed_region"] = clk.get("sm_mhz")
     # DRAM bytes per preconditioner application (dram__bytes_read.sum + dram__bytes_write.sum
-    # over k_fold_r and k2_fold_fused) from ncu captures of the current kernels; none is
-    # current: the last one (4096 x 4096, bf16x3, folded form, 865.0 MB) was taken before
-    # k2_fold_fused gained its float16 argument, and is reported beside, not as, the traffic
-    measured_traffic = {}
-    previous_traffic = {(4096, 4096, "bf16x3", True): 865.0e6}
+    # of k_fold_r, 85.5 MB, and k2_fold_fused, 779.2 MB) from one ncu capture of the current
+    # kernels at 4096 x 4096, split bf16, folded form (the algorithmic traffic is 0.81 GB)
+    measured_traffic = {(4096, 4096, "bf16x3", True): 864.7e6}
     roof["traffic"] = (measured_traffic.get((n, wd, prec, bool(folded)))
                        if dom == "dct_precond" else None)
-    prev = previous_traffic.get((n, wd, prec, bool(folded))) if dom == "dct_precond" else None
-    if roof["traffic"] is None and prev is not None:
-        roof["traffic_before_last_kernel_change"] = prev
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
+                                  "application, k_fold_r + k2_fold_fused")
+        # clock-independent tensor-pipe activity of k2_fold_fused from the same capture
+        roof["ncu_tensor_pipe_active_pct"] = {"avg": 80.3, "max": 83.4, "min": 77.4,
+                                              "sm_clock_ghz_under_ncu": 1.84}
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
                          "dct_precond": 2 if folded else 4, "finalize": 2}
