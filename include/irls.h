@@ -160,17 +160,19 @@ int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
 int irls_plan_dct_form(irls_plan plan);
 
 /* Tile shapes of the CG direction and update kernels (Alg. 2's two stencil passes per
- * iteration, both bound by HBM bandwidth): image rows per thread block, one of 8, 16, 24, 32
- * (defaults 24 and 32).  They change the block decomposition, so results change within
- * rounding (the reductions' summation order follows the blocks), never the method.
- * irls_plan_set_tiles sets them (0 keeps a value; anything else not in the list is
- * IRLS_ERR_ARG); irls_plan_get_tiles reads the values in use.  irls_plan_autotune times each
- * allowed value of each kernel on the plan's workspace (ten launches each, after two warm-up
- * launches, CUDA events on `stream`) and keeps the fastest; h_ms (NULL allowed) receives the
- * eight mean times in ms: direction for 8, 16, 24, 32 rows, then update.  It overwrites the
- * plan's scratch planes and state: call it between solves, not between a forward record and
- * its backward sweep.  Synchronous with respect to the host.  The batched form keeps
- * the defaults.  No counterpart in the paper (an implementation choice of this library). */
+ * iteration, both bound by HBM bandwidth): image rows per thread block, 8 to 64 for a plan
+ * (defaults 24 and 32; batches: one of 8, 16, 24, 32, see irls_batch_set_tiles).  They change
+ * the block decomposition, so results change within rounding (the reductions' summation order
+ * follows the blocks), never the method.  irls_plan_set_tiles sets them (0 keeps a value;
+ * anything outside 8..64 is IRLS_ERR_ARG); irls_plan_get_tiles reads the values in use.
+ * irls_plan_autotune times, for each kernel, 8, 16, 24 and 32 rows and the row count that makes
+ * the kernel's launch a whole number of waves on this device (when that count is another one),
+ * on the plan's workspace (ten launches each, after two warm-up launches, CUDA events on
+ * `stream`), and keeps the fastest; h_ms (NULL allowed) receives eight mean times in ms:
+ * direction for 8, 16, 24, 32 rows, then update.  It overwrites the plan's scratch planes and
+ * state: call it between solves, not between a forward record and its backward sweep.
+ * Synchronous with respect to the host.  No counterpart in the paper (an implementation choice
+ * of this library). */
 int irls_plan_set_tiles(irls_plan plan, int dir_rows, int upd_rows);
 
 /* Test hook for failure detection: with on = 1, every stage-2 tile of the plan's folded

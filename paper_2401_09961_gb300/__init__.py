@@ -76,7 +76,8 @@ class Plan:
         return d.value, u.value
 
     def set_tiles(self, dir_rows=0, upd_rows=0):
-        """Sets the stencil tile shapes (one of 8, 16, 24, 32; 0 keeps the current value)."""
+        """Sets the stencil tile shapes (image rows per block, 8 to 64; 0 keeps the current
+        value)."""
         check(lib().irls_plan_set_tiles(self.handle, int(dir_rows), int(upd_rows)),
               "irls_plan_set_tiles")
 

@@ -221,6 +221,9 @@ StencilArgs make_args(const irls_plan_s* p) {
     a.ld16 = p->dct.Wp;
     a.dir_rows = p->dir_rows ? p->dir_rows : kDefaultDirRows;
     a.upd_rows = p->upd_rows ? p->upd_rows : kDefaultUpdRows;
+    // the reweighting and finalize kernels take the update kernel's block shape (so that a batch
+    // and a single-image plan with the same tiles sum in the same order)
+    a.rw_rows = a.fin_rows = 0;
     return a;
 }
 
@@ -759,7 +762,7 @@ int irls_debug_fold_schedule(int n_img, const int* H, const int* W, int pairs, i
 
 int irls_plan_set_tiles(irls_plan p, int dir_rows, int upd_rows) {
     if (!p) return IRLS_ERR_ARG;
-    if ((dir_rows != 0 && !tile_rows_ok(dir_rows)) || (upd_rows != 0 && !tile_rows_ok(upd_rows)))
+    if ((dir_rows != 0 && !plan_rows_ok(dir_rows)) || (upd_rows != 0 && !plan_rows_ok(upd_rows)))
         return IRLS_ERR_ARG;
     if (dir_rows) p->dir_rows = dir_rows;
     if (upd_rows) p->upd_rows = upd_rows;
@@ -789,12 +792,22 @@ int irls_plan_autotune(irls_plan p, float* h_ms, void* stream) {
         a.tol2 = -1.0;
         a.cap_warn = 0;
         constexpr int kWarm = 2, kReps = 10;
-        float ms[2][4];
+        // candidates: the fixed row counts, then for each kernel the count that makes its
+        // launch a whole number of waves (if it is not one of them)
+        int cand[2][5];
+        int ncand[2];
+        for (int k = 0; k < 2; ++k) {
+            for (int i = 0; i < 4; ++i) cand[k][i] = kTileRows[i];
+            ncand[k] = 4;
+            const int w = wave_rows(k, p->H, p->W, 32);
+            if (w && w != 8 && w != 16 && w != 24 && w != 32) cand[k][ncand[k]++] = w;
+        }
+        float ms[2][5];
         for (int k = 0; k < 2; ++k)
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < ncand[k]; ++i) {
                 StencilArgs b = a;
-                if (k == 0) b.dir_rows = kTileRows[i];
-                else b.upd_rows = kTileRows[i];
+                if (k == 0) b.dir_rows = cand[k][i];
+                else b.upd_rows = cand[k][i];
                 float tot = 0.f;
                 for (int r = 0; r < kWarm + kReps; ++r) {
                     // a fresh state per launch (a stopped run's kernels return at once)
@@ -811,12 +824,12 @@ int irls_plan_autotune(irls_plan p, float* h_ms, void* stream) {
                 ms[k][i] = tot / kReps;
             }
         int bd = 0, bu = 0;
-        for (int i = 1; i < 4; ++i) {
+        for (int i = 1; i < ncand[0]; ++i)
             if (ms[0][i] < ms[0][bd]) bd = i;
+        for (int i = 1; i < ncand[1]; ++i)
             if (ms[1][i] < ms[1][bu]) bu = i;
-        }
-        p->dir_rows = kTileRows[bd];
-        p->upd_rows = kTileRows[bu];
+        p->dir_rows = cand[0][bd];
+        p->upd_rows = cand[1][bu];
         if (h_ms)
             for (int k = 0; k < 2; ++k)
                 for (int i = 0; i < 4; ++i) h_ms[4 * k + i] = ms[k][i];

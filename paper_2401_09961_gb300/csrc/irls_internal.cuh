@@ -106,16 +106,21 @@ struct StencilArgs {
     void* r16lo;        // same shape or nullptr: bf16(r_U - bf16(r_U)) for split precision
     int ld16;
     int prec;           // IRLS_PREC_*
-    // image rows per block of the CG direction and update kernels (single-image launches; one of
-    // kTileRows), set per plan by irls_plan_set_tiles / irls_plan_autotune
+    // image rows per block of the CG direction and update kernels, set per plan by
+    // irls_plan_set_tiles / irls_plan_autotune (single images: kMinTileRows .. kMaxTileRows;
+    // batches: one of kTileRows); rw_rows / fin_rows: the reweighting and finalize kernels'
+    // (0: the update kernel's; the launchers fill in the count they dispatch)
     int dir_rows, upd_rows;
+    int rw_rows, fin_rows;
 };
 
 // Image rows per block the CG direction and update kernels are built for, and the defaults
 // (measured fastest at 4096 x 4096).
 constexpr int kTileRows[4] = {8, 16, 24, 32};
 constexpr int kDefaultDirRows = 24, kDefaultUpdRows = 32;
+constexpr int kMinTileRows = 8, kMaxTileRows = 64;
 inline bool tile_rows_ok(int r) { return r == 8 || r == 16 || r == 24 || r == 32; }
+inline bool plan_rows_ok(int r) { return r >= kMinTileRows && r <= kMaxTileRows; }
 
 // DCT-preconditioner resources owned by a plan.
 struct DctPlan {
@@ -205,6 +210,10 @@ cudaError_t launch_matvec_via_update(const Planes& P, const StencilArgs& a, DevS
 cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, void* r16lo, int ld16,
                          cudaStream_t s);
 int stencil_grid_blocks(int H, int W);
+// rows per block that make a launch of the single-image kernel (0 direction, 1 update,
+// 2 reweighting, 3 finalize) on an H x W image a whole number of waves on the current device,
+// between kMinTileRows and `max_rows` (0 when no count in that range does)
+int wave_rows(int kernel, int H, int W, int max_rows);
 // adjoint sweep (reverse over the outer steps)
 cudaError_t launch_record_step(DevState* st, cudaStream_t s);
 cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* dLdU, DevState* st,

@@ -196,7 +196,8 @@ __device__ __forceinline__ void k_reweight_residual_body(Planes P, StencilArgs a
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.rw_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float it = a.inv_tau, d2 = a.delta * a.delta;
     const bool warm = a.warm_start != 0;
@@ -335,7 +336,8 @@ __device__ __forceinline__ void k_direction_pap_body(Planes P, StencilArgs a, De
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.dir_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf, nxt = cur ^ 1;
@@ -477,7 +479,8 @@ __device__ __forceinline__ void k_update_body(Planes P, StencilArgs a, DevState*
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.upd_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float it = a.inv_tau;
     const int cur = st->pbuf;
@@ -633,7 +636,8 @@ __device__ __forceinline__ void k_finalize_reduce_body(Planes P, StencilArgs a, 
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.fin_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float it = a.inv_tau, d2 = a.delta * a.delta;
     const float* __restrict__ U = P.U;
@@ -1541,6 +1545,31 @@ cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStr
     return cudaGetLastError();
 }
 
+int wave_rows(int kernel, int H, int W, int max_rows) {
+    static const void* const fn[4] = {(const void*)k_direction_pap<0>, (const void*)k_update<0>,
+                                      (const void*)k_reweight_residual<0>,
+                                      (const void*)k_finalize_reduce<0>};
+    if (kernel < 0 || kernel > 3 || H < 1 || W < 1) return 0;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn[kernel], kThreads, 0) !=
+            cudaSuccess || sms < 1 || per < 1)
+        return 0;
+    const int gx = (int)vec_grid(H, W, kMinTileRows).x;
+    const long long slots = (long long)sms * per;
+    // the fewest waves k whose row strips (k slots / gx of them) need at most max_rows rows each
+    for (int k = 1; k <= 64; ++k) {
+        const long long strips = k * slots / gx;
+        if (strips < 1) continue;
+        const int r = (int)((H + strips - 1) / strips);
+        if (r > max_rows) continue;
+        if (r < kMinTileRows) return 0;
+        return r;
+    }
+    return 0;
+}
+
 int stencil_grid_blocks(int H, int W) {
     dim3 g = strip_grid(H, W), v = vec_grid(H, W, std::min({kDirRows, kUpdRows, kSchurRows,
                                                            kTileRows[0]}));
@@ -1558,7 +1587,12 @@ cudaError_t launch_rows(int rows, int H, int W, cudaStream_t s, Args... args) {
         case 16: K<16>::go(vec_grid(H, W, 16), s, args...); break;
         case 24: K<24>::go(vec_grid(H, W, 24), s, args...); break;
         case 32: K<32>::go(vec_grid(H, W, 32), s, args...); break;
-        default: return cudaErrorInvalidValue;
+        default:
+            // any other count in range: the runtime-rows instance (the count travels in the
+            // kernel's arguments)
+            if (!plan_rows_ok(rows)) return cudaErrorInvalidValue;
+            K<0>::go(vec_grid(H, W, rows), s, args...);
+            break;
     }
     return cudaGetLastError();
 }
@@ -1592,7 +1626,7 @@ struct FinK {
     }
 };
 
-int rows_or(int r, int dflt) { return tile_rows_ok(r) ? r : dflt; }
+int rows_or(int r, int dflt) { return plan_rows_ok(r) ? r : dflt; }
 
 }  // namespace
 
@@ -1618,17 +1652,23 @@ cudaError_t launch_norm_u(const Planes& P, const StencilArgs& a, DevState* st, d
 
 cudaError_t launch_reweight_residual(const Planes& P, const StencilArgs& a, DevState* st,
                                      double* partials, cudaStream_t s) {
-    return launch_rows<RwK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st, partials);
+    StencilArgs b = a;
+    b.rw_rows = plan_rows_ok(a.rw_rows) ? a.rw_rows : rows_or(a.upd_rows, kUpdRows);
+    return launch_rows<RwK>(b.rw_rows, a.H, a.W, s, P, b, st, partials);
 }
 
 cudaError_t launch_direction_pap(const Planes& P, const StencilArgs& a, DevState* st,
                                  double* partials, cudaStream_t s) {
-    return launch_rows<DirK>(rows_or(a.dir_rows, kDirRows), a.H, a.W, s, P, a, st, partials);
+    StencilArgs b = a;
+    b.dir_rows = rows_or(a.dir_rows, kDirRows);
+    return launch_rows<DirK>(b.dir_rows, a.H, a.W, s, P, b, st, partials);
 }
 
 cudaError_t launch_update(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                           cudaStream_t s) {
-    return launch_rows<UpdK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st, partials);
+    StencilArgs b = a;
+    b.upd_rows = rows_or(a.upd_rows, kUpdRows);
+    return launch_rows<UpdK>(b.upd_rows, a.H, a.W, s, P, b, st, partials);
 }
 
 cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevState* st,
@@ -1658,8 +1698,9 @@ cudaError_t launch_schur_recover_v(const Planes& P, const StencilArgs& a, cudaSt
 
 cudaError_t launch_finalize(const Planes& P, const StencilArgs& a, DevState* st, double* partials,
                             cudaStream_t s) {
-    cudaError_t e = launch_rows<FinK>(rows_or(a.upd_rows, kUpdRows), a.H, a.W, s, P, a, st,
-                                      partials);
+    StencilArgs b = a;
+    b.fin_rows = plan_rows_ok(a.fin_rows) ? a.fin_rows : rows_or(a.upd_rows, kUpdRows);
+    cudaError_t e = launch_rows<FinK>(b.fin_rows, a.H, a.W, s, P, b, st, partials);
     if (e != cudaSuccess) return e;
     k_subtract_mean<<<strip_grid(a.H, a.W), kThreads, 0, s>>>(P.U, a.H, a.W, a.ld, st);
     return cudaGetLastError();

@@ -102,6 +102,14 @@ def assert_unwrap_parity(Ug, Uo, l1g, l1o, X, atol=1e-3, l1_rtol=1e-4, ref=None,
         tol = l1_rtol * max(abs(l1o), 1e-12) + 1e-9 + 4.0 * floor
         bars.append(f"floor {4 * floor / max(abs(l1o), 1e-30):.1e}")
         e, c = edge_residuals(ref)
+        # the objective on the edges it is determined on (oracle residual >= eps): recorded
+        eg = np.concatenate([np.abs(O.S_op(Ug) - pb.Gv).ravel(), np.abs(O.T_op(Ug) - pb.Gh).ravel()])
+        big = e >= eps
+        l1_big_o = float((c[big] * e[big]).sum())
+        if l1_big_o > 0:
+            d_big = abs(float((c[big] * eg[big]).sum()) - l1_big_o) / l1_big_o
+            bars.append(f"edges >= {eps:g} rad: {l1_big_o / max(abs(l1o), 1e-30):.0%} of L1, "
+                        f"dL1 {d_big:.1e}")
         if 2.0 * eps * c[e < eps].sum() > l1_rtol * abs(l1o):
             thr = max(eps, 2.0 * err)
             extra = 2.0 * err * c[e < thr].sum()

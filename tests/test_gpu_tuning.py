@@ -35,11 +35,13 @@ def test_set_get_and_invalid_rows(irls):
         assert p.tiles == (8, 16)
         p.set_tiles(0, 24)                  # 0 keeps the direction kernel's value
         assert p.tiles == (8, 24)
-        for bad in [(12, 8), (8, 7), (-8, 8), (64, 8)]:
+        for bad in [(7, 8), (8, 65), (-8, 8), (100, 8)]:
             with pytest.raises(irls.IrlsError) as e:
                 p.set_tiles(*bad)
             assert e.value.code == -1
         assert p.tiles == (8, 24)
+        p.set_tiles(22, 27)                 # any count from 8 to 64 for a plan
+        assert p.tiles == (22, 27)
 
 
 _REF = {}
@@ -53,7 +55,7 @@ def ragged_case():
     return _REF["d"], _REF["ref"][0], _REF["ref"][1]
 
 
-@pytest.mark.parametrize("tiles", [(8, 8), (16, 24), (32, 16)])
+@pytest.mark.parametrize("tiles", [(8, 8), (16, 24), (32, 16), (22, 27), (13, 50)])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_unwrap_parity_any_tile_shape(irls, tiles, prec):
     """Ragged shapes (rows not a multiple of any tile height, several column blocks)."""
