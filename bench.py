@@ -174,6 +174,96 @@ def extrapolated_oracle_rate(n, t_setup, t_outer, t_iter, cg_total, outer=OUTER,
 
 
 # ------------------------------------------------------------------------------------------
+# Evaluation of results (measurement only; the solver's own statistics are float32 sums)
+# ------------------------------------------------------------------------------------------
+def l1_fp64(U, X, coh):
+    """The L1 objective of problem (main), Sec. 2, of an unwrapped U, evaluated in FP64 on the
+    host: wrapped float32 gradients of X, edge weights = mean of the two end-pixel coherences."""
+    U = np.asarray(U, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float32)
+    c = np.asarray(coh, dtype=np.float64)
+    two_pi = np.float32(2.0 * np.pi)
+
+    def wrap(d):
+        return (d - two_pi * np.rint(d / two_pi).astype(np.float32)).astype(np.float64)
+
+    gv = wrap((X[1:, :] - X[:-1, :]).astype(np.float32))
+    gh = wrap((X[:, 1:] - X[:, :-1]).astype(np.float32))
+    cv = 0.5 * (c[1:, :] + c[:-1, :])
+    ch = 0.5 * (c[:, 1:] + c[:, :-1])
+    return float(np.sum(cv * np.abs(U[1:, :] - U[:-1, :] - gv)) +
+                 np.sum(ch * np.abs(U[:, 1:] - U[:, :-1] - gh)))
+
+
+def k_agreement(U1, U2):
+    """Share of pixels whose 2pi multiple of U1 - U2 (less its circular mean) is the most common
+    one: 1.0 when two unwraps of the same image differ by a constant only."""
+    d = np.asarray(U1, dtype=np.float64) - np.asarray(U2, dtype=np.float64)
+    c = float(np.angle(np.sum(np.exp(1j * d))))
+    k = np.rint((d - c) / (2.0 * np.pi)).astype(np.int64)
+    _, cnt = np.unique(k, return_counts=True)
+    return float(cnt.max() / k.size)
+
+
+def measure_forms(d, X, C, timed_unwraps=2):
+    """The other forms of the same 4096 x 4096 unwrap (and the 64-tile batch), each timed with
+    CUDA events after one warm-up unwrap (the plain float32 form: one unwrap, no warm-up), with
+    the final L1 objective evaluated in FP64 on each result.  Not part of `value`."""
+    import torch
+    import paper_2401_09961_gb300 as irls
+    import synthetic
+    stream = torch.cuda.current_stream()
+    H, W = X.shape
+    out = {}
+
+    def timed(run, n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            r = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / n, r
+
+    single = [("fp32_plain_simt_dct", dict(precision="fp32"), 0, 1),
+              ("fp32_fft_dct", dict(precision="fp32", dct_form="fft"), 1, timed_unwraps),
+              ("fp32_fft_dct_u_only_system", dict(precision="fp32", dct_form="fft",
+                                                  system="schur"), 1, timed_unwraps),
+              ("fp16_folded", dict(precision="fp16"), 1, timed_unwraps),
+              ("bf16x3_folded_u_only_system", dict(precision="bf16x3", system="schur"), 1,
+               timed_unwraps)]
+    for name, kw, warm, n in single:
+        with irls.Plan(H, W, tau=TAU, delta=DELTA, outer_iters=OUTER, cg_tol=CG_TOL,
+                       cg_max_iter=1000, **kw) as p:
+            U = torch.empty_like(X)
+            for _ in range(warm):
+                p.unwrap(X, C, out=U)
+            t, (_, st) = timed(lambda: p.unwrap(X, C, out=U), n)
+            out[name] = {"s_per_unwrap": t, "mpix_s": H * W / 1e6 / t, "unwraps_timed": n,
+                         "cg_iters_total": st["cg_total"],
+                         "l1_fp64": l1_fp64(U.cpu().numpy(), d["X"], d["coherence"])}
+    shapes = synthetic.batched_tile_shapes(n=64, seed_base=1000)
+    tiles = synthetic.batched_tiles(n=64, seed_base=1000, indices=list(range(64)))
+    Xs = [torch.as_tensor(t["X"]).cuda() for t in tiles]
+    Cs = [torch.as_tensor(t["coherence"]).cuda() for t in tiles]
+    mpix = sum(h * w for h, w in shapes) / 1e6
+    with irls.Batch(shapes, precision="bf16x3", tau=TAU, delta=DELTA, outer_iters=OUTER,
+                    cg_tol=CG_TOL, cg_max_iter=1000) as b:
+        b.autotune()
+        b.unwrap(Xs, Cs)
+        t, (_, st) = timed(lambda: b.unwrap(Xs, Cs), timed_unwraps)
+        out["bf16x3_batched_64_tiles"] = {
+            "s_per_batch": t, "mpix_s": mpix / t, "batches_timed": timed_unwraps,
+            "mpix_per_batch": mpix, "cg_iters_total": sum(x["cg_total"] for x in st)}
+    out["_note"] = ("same image and options as the headline (one warm-up, then CUDA-event "
+                    "timing); the batch is the 64-tile uneven-size workload; l1_fp64 is the "
+                    "objective of problem (main) evaluated in FP64 on each result")
+    return out
+
+
+# ------------------------------------------------------------------------------------------
 def rank_max(x, world, device="cuda"):
     """x maximised over the ranks of the process group (the slowest rank's time); x at N = 1."""
     if world == 1:
@@ -210,8 +300,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default stencil tile shapes (no timing pass before warm-up)")
-    ap.add_argument("--dct-form", default="auto", choices=["auto", "direct", "folded"],
-                    help="preconditioner form (auto: folded where allowed)")
+    ap.add_argument("--dct-form", default="auto", choices=["auto", "direct", "folded", "fft"],
+                    help="preconditioner form (auto: folded where allowed; fft: fast transforms "
+                         "in float32, with --precision fp32)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "tiled"],
                     help="single: one 4096 x 4096 image per step (the benchmark); batched: 64 "
@@ -226,6 +317,9 @@ def main():
     ap.add_argument("--system", default="full", choices=["full", "schur"],
                     help="full: the paper's (U, V) system (the benchmark); schur: the U-only "
                          "system left after eliminating V")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the comparison of the other forms (plain float32, float16, U-only "
+                         "system, 64-tile batch) after the headline at 4096 x 4096")
     ap.add_argument("--cg-schedule", default="fixed", choices=["fixed", "paper"],
                     help="fixed: every solve capped at 1000 CG iterations (the benchmark); paper: "
                          "the adaptive CG budget and IRLS stop of Sec. 4.3")
@@ -320,6 +414,7 @@ def main():
             "dct_precond": (cg_total + outer_done) * prof_steps,
             "reweight_residual": outer_done * prof_steps, "finalize": outer_done * prof_steps}
     folded = plan.folded
+    fft = plan.dct_form_name == "fft"
     # bf16 copy of r_U written for the direct tensor-core forms (hi, plus lo in split precision)
     emit = 0.0 if (prec == "fp32" or folded) else (4.0 if prec == "bf16x3" else 2.0)
     if args.system == "schur":
@@ -332,7 +427,11 @@ def main():
                     "update": 68.0 + emit + (4.0 if flexible else 0)}
     # finalize: U, G (2), C (2), V (2), W (2) read; then U read and written by the mean removal
     bytes_px["finalize"] = 44.0
-    for c in ("direction_pap", "update", "reweight_residual", "finalize"):
+    # fast-transform preconditioner: three passes, each reading and writing one float32 plane
+    if fft:
+        bytes_px["dct_precond"] = 24.0
+    for c in ("direction_pap", "update", "reweight_residual", "finalize") + (
+            ("dct_precond",) if fft else ()):
         if per_cls[c]["ms"] > 0 and live.get(c):
             t = per_cls[c]["ms"] / 1e3 / live[c]
             per_cls[c].update({"ms_per_live_launch": t * 1e3, "bytes_per_px": bytes_px[c],
@@ -345,7 +444,7 @@ def main():
     dom = max(("direction_pap", "update", "dct_precond", "reweight_residual"),
               key=lambda c: per_cls[c]["ms"])
     avg_s = per_cls[dom]["ms"] / 1e3 / max(live[dom], 1)
-    if dom == "dct_precond":
+    if dom == "dct_precond" and not fft:
         if prec == "fp32":
             clk_mhz = clk.get("sm_mhz") or 1900.0
             peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
@@ -369,7 +468,9 @@ def main():
                     "tensor_pipe_frac_of_bf16_peak": alg * passes / sus}
     else:
         achieved = bytes_px[dom] * P / avg_s / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+        name = ("dct_precond (k_fftdct_rows_fwd + k_fftdct_cols + k_fftdct_rows_inv: fast "
+                "transforms, float32)" if dom == "dct_precond" else dom)
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["sm_mhz_median_timed_region"] = clk.get("sm_mhz")
@@ -387,7 +488,7 @@ def main():
                                               "sm_clock_ghz_under_ncu": 1.84}
     roof["avg_launch_ms"] = avg_s * 1e3
     kernels_per_class = {"init": 2, "reweight_residual": 1, "direction_pap": 1, "update": 1,
-                         "dct_precond": 2 if folded else 4, "finalize": 2}
+                         "dct_precond": 2 if folded else (3 if fft else 4), "finalize": 2}
     # launches of the timed region: the profiled pass ran the same kernels per unwrap
     gpu_launches = sum(per_cls[c]["launches"] * kernels_per_class[c] for c in classes)
     gpu_launches = gpu_launches * args.steps // max(prof_steps, 1) + args.steps  # + copy-out
@@ -421,6 +522,17 @@ def main():
                           f"iterations: {tfull:.0f} s"),
                "extrapolated": True}
 
+    # ---- the headline result's objective in FP64, and the other forms (rank 0, N = 1) ----
+    l1_head = None
+    forms = None
+    if rank == 0 and world == 1:
+        l1_head = l1_fp64(U.cpu().numpy(), d["X"], d["coherence"])
+        if (not args.no_forms and n == 4096 and wd == 4096 and prec == "bf16x3"
+                and args.system == "full" and args.cg_schedule == "fixed" and args.outer == OUTER):
+            forms = measure_forms(d, X, C)
+            forms["bf16x3_folded_headline"] = {"s_per_unwrap": ms_step / 1e3, "mpix_s": value,
+                                               "cg_iters_total": cg_total, "l1_fp64": l1_head}
+
     if rank == 0:
         out = {
             "metric": metric_name(n, wd, args.cg_schedule),
@@ -428,18 +540,19 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else
             f"f32+{prec}-tensor-core-dct", "data": "synthetic",
-            "config": {"workload": workload_name(n, prec, wd), "size": [n, wd],
+            "config": {"workload": workload_name(n, "fp32 fast transforms" if fft else prec, wd),
+                       "size": [n, wd],
                        "outer_iters": args.outer, "outer_done": outer_done,
                        "cg_schedule": args.cg_schedule, "system": args.system,
                        "delta": DELTA, "tau": TAU,
                        "cg_tol": CG_TOL,
                        "precision": prec, "flexible_cg": bool(flexible),
-                       "dct_form": "folded" if folded else ("direct" if prec != "fp32" else
-                                                            "fp32 simt"),
+                       "dct_form": plan.dct_form_name,
                        "stencil_tiles": {"direction_rows": plan.tiles[0],
                                          "update_rows": plan.tiles[1],
                                          "autotuned": tune is not None},
                        "cg_iters_total": cg_total, "l1_objective": stats[-1]["l1_obj"][-1],
+                       "l1_objective_fp64": l1_head,
                        "cg_iters_per_outer": stats[-1]["cg_iters"],
                        **({"cg_caps": stats[-1]["cg_cap"]} if args.cg_schedule == "paper"
                           else {}),
@@ -451,6 +564,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clk,
+            "forms": forms,
         }
         print(json.dumps(out))
     plan.close()
@@ -599,23 +713,18 @@ def tiled_arm(args, rank, world, local):
     t.close()
     extra = {}
     if not args.no_e2e and rank == 0:
-        import oracle.irls as O
         with irls.Plan(H, W, **kw) as p:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Us, ss = p.unwrap(X, C)
             torch.cuda.synchronize()
             t_single = time.perf_counter() - t0
-        Gv, Gh = O.wrapped_gradients(d["X"])
-        Cv, Ch = O.edge_weights(d["coherence"], H, W)
-        Ut = U.cpu().numpy().astype(np.float64)
-        Usn = Us.cpu().numpy().astype(np.float64)
-        dk = O.k_map(Ut, d["X"]) - O.k_map(Usn, d["X"])
-        _, cnt = np.unique(dk, return_counts=True)
+        Ut = U.cpu().numpy()
+        Usn = Us.cpu().numpy()
         extra = {"single_plan_s": t_single, "single_plan_mpix_s": H * W / 1e6 / t_single,
-                 "k_map_agreement_vs_single_plan": float(cnt.max() / dk.size),
-                 "l1_tiled": O.l1_objective(Ut, Gv, Gh, Cv, Ch),
-                 "l1_single_plan": O.l1_objective(Usn, Gv, Gh, Cv, Ch)}
+                 "k_map_agreement_vs_single_plan": k_agreement(Ut, Usn),
+                 "l1_tiled": l1_fp64(Ut, d["X"], d["coherence"]),
+                 "l1_single_plan": l1_fp64(Usn, d["X"], d["coherence"])}
     if rank == 0:
         out = {
             "metric": f"Mpix/s per tiled IRLS unwrap of one {H}x{W} image",

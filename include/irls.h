@@ -59,13 +59,22 @@ extern "C" {
                             /* stage by (mu + lambda_1) / tau, undone by a pre-scaled basis   */
                             /* in the last stage; not for batches or the adjoint              */
 
-/* Form of the tensor-core preconditioner (split precision only). */
+/* Form of the preconditioner's Laplacian block (Sec. 3.3).  AUTO, DIRECT and FOLDED choose
+ * how the tensor-core precisions run the dense products; FFT replaces the products by fast
+ * transforms of the same map. */
 #define IRLS_DCT_AUTO   0   /* folded where allowed, else direct                                  */
 #define IRLS_DCT_DIRECT 1   /* four full-size products per application                            */
 #define IRLS_DCT_FOLDED 2   /* even / odd folded products, half the multiply-adds, all four
                              * stages in one persistent launch; needs precision IRLS_PREC_BF16X3
                              * or IRLS_PREC_FP16 (which always runs it) and H, W >= 256 (odd or
                              * even); otherwise plan creation returns IRLS_ERR_UNSUPPORTED       */
+#define IRLS_DCT_FFT    3   /* every orthonormal DCT-II / DCT-III of the map evaluated by a
+                             * complex FFT of the same length in float32 on the CUDA cores
+                             * (three passes over a float32 plane per application; r_U^T z_U
+                             * from the spectrum by Parseval); needs precision IRLS_PREC_FP32,
+                             * H a power of two in [64, 8192] and W one in [64, 16384];
+                             * single-image plans only (batches: IRLS_ERR_UNSUPPORTED).  Not
+                             * in the paper, which forms the dense products                      */
 
 /* Inner-solve budget (Sec. 4.3). */
 #define IRLS_CG_FIXED 0     /* outer_iters IRLS iterations, each solve capped at cg_max_iter    */
@@ -102,7 +111,7 @@ typedef struct {
     int   precision;    /* IRLS_PREC_*                                                         */
     int   flexible_cg;  /* 0: beta = rho_new / rho (Alg. 2); 1: Polak-Ribiere (flexible) beta  */
     int   warm_start;   /* 1: CG starts from the current (U, V); 0: from zero each outer step  */
-    int   dct_form;     /* IRLS_DCT_*; IRLS_DCT_FOLDED where not allowed: IRLS_ERR_UNSUPPORTED  */
+    int   dct_form;     /* IRLS_DCT_*; FOLDED or FFT where not allowed: IRLS_ERR_UNSUPPORTED   */
     /* IRLS_CG_PAPER (Sec. 4.3): solve k is capped at min(m_CG(k), cg_max_iter), m_CG(0) = cg_m0.
      * For k >= 1, with Delta = (H_delta(x^k, W^{k-1}) - H_delta(x^k, W^k)) / H_delta(x^k,
      * W^{k-1}): Delta > cg_eps_tol keeps m_CG; otherwise the run stops and returns U^k if m_CG
@@ -154,8 +163,9 @@ int irls_plan_destroy(irls_plan plan);
 int irls_plan_set_opts(irls_plan plan, const irls_opts* opts);
 
 /* Preconditioner form the plan runs with its current options: IRLS_DCT_FOLDED or
- * IRLS_DCT_DIRECT for the tensor-core precisions, IRLS_DCT_AUTO for IRLS_PREC_FP32 (no tensor
- * cores); IRLS_ERR_ARG for a NULL plan.  The paper has no counterpart (an implementation
+ * IRLS_DCT_DIRECT for the tensor-core precisions, IRLS_DCT_FFT for the fast-transform form,
+ * IRLS_DCT_AUTO for IRLS_PREC_FP32 with dense products (float32 SIMT GEMMs, no tensor cores);
+ * IRLS_ERR_ARG for a NULL plan.  The paper has no counterpart (an implementation
  * choice of this library). */
 int irls_plan_dct_form(irls_plan plan);
 

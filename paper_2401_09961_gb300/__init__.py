@@ -62,6 +62,15 @@ class Plan:
         return lib().irls_plan_dct_form(self.handle) == DCT_FORMS["folded"]
 
     @property
+    def dct_form_name(self):
+        """The preconditioner form in use: "folded", "direct" (tensor-core products), "fft"
+        (fast transforms) or "simt" (float32 dense products on the CUDA cores)."""
+        f = lib().irls_plan_dct_form(self.handle)
+        names = {DCT_FORMS["folded"]: "folded", DCT_FORMS["direct"]: "direct",
+                 DCT_FORMS["fft"]: "fft", DCT_FORMS["auto"]: "simt"}
+        return names.get(f, str(f))
+
+    @property
     def handle(self):
         if self._h is None:
             raise RuntimeError("plan destroyed")

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libirls.so")
 
 IRLS_MAX_OUTER = 256
-DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2}
+DCT_FORMS = {"auto": 0, "direct": 1, "folded": 2, "fft": 3}
 CG_SCHEDULES = {"fixed": 0, "paper": 1}
 SYSTEMS = {"full": 0, "schur": 1}
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16": 3}

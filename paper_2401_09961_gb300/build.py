@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libirls.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["irls_kernels.cu", "dct.cu", "dct_umma.cu", "irls_api.cu", "noalloc.cu", "post.cu",
-           "tiled.cu"]
+           "tiled.cu", "dct_fft.cu"]
 
 
 def _nvcc():

@@ -217,7 +217,7 @@ size_t dct_bytes(int H, int W, int prec) {
     if (H != W) n += 2 * Wp * Wp;
     size_t bytes = n * sizeof(float) + 4096;
     if (prec != IRLS_PREC_FP32) bytes += umma_dct_bytes(H, W, prec);
-    return bytes;
+    return bytes + fft_dct_bytes(H, W);   // the fast-transform tables at the tail
 }
 
 cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) {
@@ -240,8 +240,14 @@ cudaError_t dct_setup(DctPlan& d, int H, int W, int prec, float tau, char* mem) 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     d.umma_ok = 0;
+    d.fft = 0;
+    {
+        char* mt = mem + (dct_bytes(H, W, prec) - fft_dct_bytes(H, W));
+        mt = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(mt) + 255) & ~uintptr_t(255));
+        if ((e = fft_dct_setup(d, mt)) != cudaSuccess) return e;
+    }
     if (prec != IRLS_PREC_FP32) {
-        char* m16 = mem + (dct_bytes(H, W, IRLS_PREC_FP32) - 4096);
+        char* m16 = mem + (dct_bytes(H, W, IRLS_PREC_FP32) - fft_dct_bytes(H, W) - 4096);
         m16 = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(m16) + 1023) & ~uintptr_t(1023));
         e = umma_dct_setup(d, m16);
     }
@@ -255,6 +261,7 @@ bool dct_stall(DctPlan& d, int on) { return umma_dct_stall(d, on); }
 cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
                       int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
                       cudaStream_t s) {
+    if (d.fft) return fft_dct_apply(d, rU, zU, ld, st, reduce_rho, a, partials, skip_if_done, s);
     if (d.prec != IRLS_PREC_FP32)
         return umma_dct_apply(d, rU, zU, ld, st, reduce_rho, a, partials, skip_if_done, s);
     const int H = d.H, W = d.W, Hp = d.Hp, Wp = d.Wp;

@@ -53,7 +53,7 @@ bool opts_valid(const irls_opts& o) {
     if (o.outer_iters < 0 || o.outer_iters > IRLS_MAX_OUTER) return false;
     if (o.cg_max_iter < 0) return false;
     if (o.precision < IRLS_PREC_FP32 || o.precision > IRLS_PREC_FP16) return false;
-    if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FOLDED) return false;
+    if (o.dct_form < IRLS_DCT_AUTO || o.dct_form > IRLS_DCT_FFT) return false;
     if (o.cg_schedule != IRLS_CG_FIXED && o.cg_schedule != IRLS_CG_PAPER) return false;
     if (o.system != IRLS_SYS_FULL && o.system != IRLS_SYS_SCHUR) return false;
     if (o.cg_schedule == IRLS_CG_PAPER &&
@@ -86,7 +86,8 @@ Layout layout(int H, int W, int prec) {
     L.planes = 0;
     L.state = L.planes + kPlanes * L.plane_bytes;
     L.partials = L.state + align_up(sizeof(DevState), 256);
-    L.max_blocks = std::max(stencil_grid_blocks(H, W), dct_max_blocks(H, W));
+    L.max_blocks = std::max({stencil_grid_blocks(H, W), dct_max_blocks(H, W),
+                             fft_dct_max_blocks(H, W)});
     L.dct = L.partials + align_up(partial_count(H, W, L.max_blocks) * sizeof(double), 1024);
     L.total = L.dct + align_up(dct_bytes(H, W, prec), 1024) + 1024;
     return L;
@@ -230,6 +231,14 @@ StencilArgs make_args(const irls_plan_s* p) {
 // Folded preconditioner on or off for the given options; false when IRLS_DCT_FOLDED is asked for
 // and the plan has no folded form (a shape or precision that does not allow it).
 bool select_dct_form(irls_plan_s* p, const irls_opts& o) {
+    // the fast-transform form computes in float32 and takes power-of-two sides
+    if (o.dct_form == IRLS_DCT_FFT) {
+        if (o.precision != IRLS_PREC_FP32 || !p->dct.fft_ready) return false;
+        p->dct.fft = 1;
+        p->dct.fold = 0;
+        return true;
+    }
+    p->dct.fft = 0;
     const bool ready = p->dct.fold_ready &&
                        (o.precision == IRLS_PREC_BF16X3 || o.precision == IRLS_PREC_FP16);
     if (o.dct_form == IRLS_DCT_FOLDED && !ready) return false;
@@ -729,6 +738,7 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
 
 int irls_plan_dct_form(irls_plan p) {
     if (!p) return IRLS_ERR_ARG;
+    if (p->dct.fft) return IRLS_DCT_FFT;
     if (p->opts.precision == IRLS_PREC_FP32) return IRLS_DCT_AUTO;
     return p->dct.fold ? IRLS_DCT_FOLDED : IRLS_DCT_DIRECT;
 }
@@ -1032,6 +1042,7 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
     for (int t = 0; t < ntiles; ++t)
         all_fold &= foldable(H[t], W[t], o.precision == IRLS_PREC_BF16X3 ? 1 : 0);
     if (o.dct_form == IRLS_DCT_FOLDED && !all_fold) return IRLS_ERR_UNSUPPORTED;
+    if (o.dct_form == IRLS_DCT_FFT) return IRLS_ERR_UNSUPPORTED;   // single-image plans only
     const int fold = all_fold && o.dct_form != IRLS_DCT_DIRECT ? 1 : 0;
     irls_batch_s* b = new (std::nothrow) irls_batch_s();
     if (!b) return IRLS_ERR_OOM;

@@ -143,6 +143,11 @@ struct DctPlan {
     int fold_ready;            // folded form built (memory, bases)
     void *Re, *Relo, *Ro, *Rolo;   // folded residual, H x W/2 each
     void* fold_host;               // host-side record of the folded form (owned)
+    // fast-transform form (float32 FFTs on the CUDA cores; power-of-two sides)
+    int fft;                       // in use
+    int fft_ready;                 // twiddle tables built
+    float2 *fftTwN, *fftTtN;       // exp(-2 pi i m / H), exp(-i pi k / 2H)
+    float2 *fftTwM, *fftTtM;       // the same for W
     alignas(64) unsigned char tmap_storage[2048];   // TMA descriptors of the four stages
 };
 
@@ -281,6 +286,15 @@ cudaError_t dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevS
                       cudaStream_t s);
 int dct_max_blocks(int H, int W);
 size_t dct_rho_slots(int H, int W);
+// fast-transform form (dct_fft.cu): shapes it takes, its table memory, its widest grid-reduced
+// launch, set-up and application (same contract as dct_apply, float32 only)
+bool fft_dct_supported(int H, int W);
+size_t fft_dct_bytes(int H, int W);
+int fft_dct_max_blocks(int H, int W);
+cudaError_t fft_dct_setup(DctPlan& d, char* mem);
+cudaError_t fft_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, DevState* st,
+                          int reduce_rho, const StencilArgs& a, double* partials, int skip_if_done,
+                          cudaStream_t s);
 // batched form (dct_umma.cu): memory for T images of sizes H[t] x W[t], set-up, application
 bool foldable(int H, int W, int split);
 size_t batch_dct_bytes(const int* H, const int* W, int T, int prec, int fold);

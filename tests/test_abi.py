@@ -129,3 +129,28 @@ def test_new_entry_points_reject_null_handles(L):
     h = ctypes.c_void_p()
     o = _binding.default_opts(precision="fp16")
     assert L.irls_batch_create(1, H, W, ctypes.byref(o), ctypes.byref(h)) == -8
+
+
+def test_header_constants_match_the_binding():
+    """The IRLS_DCT_* / IRLS_PREC_* / IRLS_SYS_* / IRLS_CG_* values of include/irls.h are the
+    ones the Python binding passes."""
+    from paper_2401_09961_gb300 import _binding
+    txt = open(HEADER).read()
+    consts = {k: int(v) for k, v in re.findall(r"#define\s+(IRLS_[A-Z0-9_]+)\s+(-?\d+)", txt)}
+    for name, v in _binding.DCT_FORMS.items():
+        assert consts[f"IRLS_DCT_{name.upper()}"] == v
+    for name, v in _binding.PRECISIONS.items():
+        assert consts[f"IRLS_PREC_{name.upper()}"] == v
+    assert consts["IRLS_SYS_FULL"] == _binding.SYSTEMS["full"]
+    assert consts["IRLS_SYS_SCHUR"] == _binding.SYSTEMS["schur"]
+    assert consts["IRLS_CG_FIXED"] == _binding.CG_SCHEDULES["fixed"]
+    assert consts["IRLS_CG_PAPER"] == _binding.CG_SCHEDULES["paper"]
+
+
+def test_fft_form_is_validated(L):
+    """dct_form beyond IRLS_DCT_FFT is an invalid argument (no device work needed to say so)."""
+    from paper_2401_09961_gb300 import _binding
+    ok = _binding.default_opts(dct_form=3)
+    bad = _binding.default_opts(dct_form=4)
+    assert L.irls_workspace_bytes(256, 256, ctypes.byref(ok)) > 0
+    assert L.irls_workspace_bytes(256, 256, ctypes.byref(bad)) == 0

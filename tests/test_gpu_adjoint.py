@@ -48,7 +48,7 @@ def test_adjoint_matches_oracle_adjoint(irls, prec):
                               "law of the 1024^2 workload")
 
 
-def assert_grads_match_oracle(irls, X, coh, Uref, prec, outer, cg_tol, case):
+def assert_grads_match_oracle(irls, X, coh, Uref, prec, outer, cg_tol, case, **plan_kw):
     """GPU adjoint (dL/dX, dL/dcoherence of L = sum (U - mean U - U_ref)^2) against the FP64
     oracle adjoint, both from their own forward runs.  Bar: max(2e-3 of the largest gradient,
     2 x the spread between the FP64 oracle and the same oracle with float32 vector storage)."""
@@ -59,10 +59,10 @@ def assert_grads_match_oracle(irls, X, coh, Uref, prec, outer, cg_tol, case):
     _, gX32, gC32 = oracle_grads(X, coh, dLdU, storage=np.float32, **kw)
     H, W = X.shape
     with irls.Plan(H, W, precision=prec, tau=1e-2, delta=1e-3, outer_iters=outer,
-                   cg_tol=cg_tol, cg_max_iter=3000) as p:
-        form = "folded" if p.folded else "direct" if prec != "fp32" else "simt"
+                   cg_tol=cg_tol, cg_max_iter=3000, **plan_kw) as p:
+        form = p.dct_form_name
     U, dX, dc, st = gpu_grads(irls, X, coh, dLdU, prec=prec, tau=1e-2, delta=1e-3,
-                              outer_iters=outer, cg_tol=cg_tol, cg_max_iter=3000)
+                              outer_iters=outer, cg_tol=cg_tol, cg_max_iter=3000, **plan_kw)
     assert st["outer_done"] == outer and np.all(np.isfinite(dX)) and np.all(np.isfinite(dc))
     for name, g, r, r32 in (("dL/dX", dX, gX, gX32), ("dL/dcoh", dc, gC, gC32)):
         env = np.abs(r32 - r).max()
