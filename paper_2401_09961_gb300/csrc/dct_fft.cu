@@ -331,7 +331,10 @@ struct ColCfg {
     static constexpr int NF = (2048 / N) < 2 ? 2 : ((2048 / N) > 16 ? 16 : 2048 / N);
     static constexpr int T = N * NF / 16;
     using L = StripL<N, NF>;
-    static constexpr size_t SMEM = (size_t)L::FLOATS * sizeof(float) + (64 + N / 64) * sizeof(float2);
+    static constexpr int TWN = 64 + ((N / 64 + 1) & ~1);   // twiddle table, 16-byte multiple
+    static constexpr int TTN = N / 2 + 2;                  // exp(-i pi k / 2N), k <= N/2
+    static constexpr size_t SMEM = (size_t)L::FLOATS * sizeof(float) +
+                                   (size_t)(TWN + TTN) * sizeof(float2) + (size_t)N * sizeof(float);
     static constexpr int MINB = 1024 / T;   // at most 64 registers a thread
     static constexpr int WANT = MINB;
 };
@@ -405,6 +408,9 @@ k_fftdct_cols(float* __restrict__ Tio, int W, int ld, float tau, const float* __
     if (skip_if_done && st->done) return;
     extern __shared__ __align__(16) float sm[];
     float2* tws = reinterpret_cast<float2*>(sm + L::FLOATS);
+    // the middle step's tables (t_k for k <= N/2 and the eigenvalues l_k) come in with the strip
+    float2* stt = tws + C::TWN;
+    float* slam = reinterpret_cast<float*>(stt + C::TTN);
     load_twiddles<N, T>(tws, tw);
     const int j0 = blockIdx.x * 2 * NF;
     for (int c = threadIdx.x; c < N * QC; c += T) {
@@ -413,6 +419,8 @@ k_fftdct_cols(float* __restrict__ Tio, int W, int ld, float tau, const float* __
         const bool ok = col < W;
         cp_async16(sm + L::off(2 * q, i), Tio + (size_t)i * ld + (ok ? col : 0), ok);
     }
+    for (int c = threadIdx.x; c < C::TTN / 2; c += T) cp_async16(stt + 2 * c, tt + 2 * c, true);
+    for (int c = threadIdx.x; c < N / 4; c += T) cp_async16(slam + 4 * c, lamN + 4 * c, true);
     cp_async_wait_all();
     __syncthreads();
     fft_stages<L, N, NF, T, 1, true>(sm, tws);
@@ -422,11 +430,11 @@ k_fftdct_cols(float* __restrict__ Tio, int W, int ld, float tau, const float* __
         const int f = it % NF, k = it / NF;
         const int kc = (N - k) & (N - 1);
         const int ja = j0 + 2 * f, jb = ja + 1;
-        const float2 t = __ldg(&tt[k]);
+        const float2 t = stt[k];
         const float ck = dct_c<N>(k), cc = dct_c<N>(kc);
         float xa_k, xb_k, xa_c, xb_c;
         dct2_pair(L::ld(sm, f, k), L::ld(sm, f, kc), t, ck, cc, xa_k, xb_k, xa_c, xb_c);
-        const float lk = __ldg(&lamN[k]), lc = __ldg(&lamN[kc]);
+        const float lk = slam[k], lc = slam[kc];
         const float ma = ja < W ? __ldg(&lamM[ja]) : 0.f, mb = jb < W ? __ldg(&lamM[jb]) : 0.f;
         // S / (l + m); the (0,0) entry (the constant, the Laplacian's null space) and the
         // columns past W are zero
