@@ -178,6 +178,7 @@ struct irls_plan_s {
     std::vector<int> caps;     // cap of each inner solve of the last run
     int schedule_stop = 0;
     int dir_rows = 0, upd_rows = 0;   // stencil tile shapes (0: the defaults)
+    int rw_rows = 0, fin_rows = 0;    // reweighting and finalize rows (aux_rows of H, W)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profiler prof;
 };
@@ -222,9 +223,10 @@ StencilArgs make_args(const irls_plan_s* p) {
     a.ld16 = p->dct.Wp;
     a.dir_rows = p->dir_rows ? p->dir_rows : kDefaultDirRows;
     a.upd_rows = p->upd_rows ? p->upd_rows : kDefaultUpdRows;
-    // the reweighting and finalize kernels take the update kernel's block shape (so that a batch
-    // and a single-image plan with the same tiles sum in the same order)
-    a.rw_rows = a.fin_rows = 0;
+    // the reweighting and finalize kernels take rows of their own, a function of the image's
+    // size that a batch uses as well (so both sum in the same order)
+    a.rw_rows = p->rw_rows;
+    a.fin_rows = p->fin_rows;
     return a;
 }
 
@@ -463,7 +465,7 @@ struct irls_batch_s {
     std::vector<TileRec> recs;
     TileRec* d_recs = nullptr;
     DevState* states = nullptr;
-    int total_strip = 0, total_vec = 0, total_upd = 0;
+    int total_strip = 0, total_vec = 0, total_upd = 0, total_rw = 0, total_fin = 0;
     int dir_rows = kDefaultDirRows, upd_rows = kDefaultUpdRows;   // stencil tile shapes
     BatchDctPlan dct;
     int* d_count = nullptr;          // device, 2 slots
@@ -499,17 +501,25 @@ void destroy_batch(irls_batch_s* b) {
 // Each image's blocks in the batched direction and update launches for the batch's tile shapes
 // (host records; uploaded with the image pointers at the start of every run).
 void layout_vec_blocks(irls_batch_s* b) {
-    int vblk = 0, ublk = 0;
+    int vblk = 0, ublk = 0, rblk = 0, fblk = 0;
     for (int t = 0; t < b->T; ++t) {
         TileRec& r = b->recs[t];
         vec_dims(b->H[t], b->W[t], b->dir_rows, b->upd_rows, r.vgx, r.vgy, r.ugy);
         r.vblk0 = vblk;
         r.ublk0 = ublk;
+        r.rblk0 = rblk;
+        r.fblk0 = fblk;
+        r.rgy = (b->H[t] + r.a.rw_rows - 1) / r.a.rw_rows;
+        r.fgy = (b->H[t] + r.a.fin_rows - 1) / r.a.fin_rows;
         vblk += r.vgx * r.vgy;
         ublk += r.vgx * r.ugy;
+        rblk += r.vgx * r.rgy;
+        fblk += r.vgx * r.fgy;
     }
     b->total_vec = vblk;
     b->total_upd = ublk;
+    b->total_rw = rblk;
+    b->total_fin = fblk;
 }
 
 // The CG chunk graphs bake in the launches' grids and kernels: captured again on the next run.
@@ -596,7 +606,7 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
     prepare_graphs(b);
     for (int k = 0; k < b->opts.outer_iters; ++k) {
         TraceRange r_outer("irls_outer");
-        ck(launch_reweight_batched(b->d_recs, T, b->total_upd, b->upd_rows, s));
+        ck(launch_reweight_batched(b->d_recs, T, b->total_rw, s));
         {
             TraceRange r_pcg("irls_pcg");
             ck(batch_dct_apply(b->dct, s));
@@ -621,7 +631,7 @@ int run_batch(irls_batch_s* b, const float* const* X, const float* const* coh, f
             }
         }
         TraceRange r_fin("irls_finalize");
-        ck(launch_finalize_batched(b->d_recs, T, b->total_strip, b->total_upd, b->upd_rows, s));
+        ck(launch_finalize_batched(b->d_recs, T, b->total_strip, b->total_fin, s));
     }
     for (int t = 0; t < T; ++t)
         ck(launch_copy_out(b->recs[t].P.U, b->H[t], b->W[t], b->ld[t], U[t], s));
@@ -693,6 +703,8 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
     try {
         ck(cudaGetDevice(&p->dev));
         p->H = H; p->W = W; p->ld = row_pitch(W);
+        p->rw_rows = aux_rows(2, H, W);
+        p->fin_rows = aux_rows(3, H, W);
         p->opts = o;
         p->prec_alloc = o.precision;
         p->L = layout(H, W, o.precision);
@@ -1122,6 +1134,8 @@ int irls_batch_create(int ntiles, const int* H, const int* W, const irls_opts* o
             a.flexible = o.flexible_cg;
             a.warm_start = o.warm_start;
             a.prec = o.precision;
+            a.rw_rows = aux_rows(2, H[t], W[t]);
+            a.fin_rows = aux_rows(3, H[t], W[t]);
             // the direct form reads the update kernel's bf16 copy of r_U; the folded form folds
             // r_U itself
             if (!fold) {

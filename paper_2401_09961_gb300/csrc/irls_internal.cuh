@@ -109,7 +109,8 @@ struct StencilArgs {
     // image rows per block of the CG direction and update kernels, set per plan by
     // irls_plan_set_tiles / irls_plan_autotune (single images: kMinTileRows .. kMaxTileRows;
     // batches: one of kTileRows); rw_rows / fin_rows: the reweighting and finalize kernels'
-    // (0: the update kernel's; the launchers fill in the count they dispatch)
+    // (aux_rows of the image's size; 0: the update kernel's; the launchers fill in the count
+    // they dispatch)
     int dir_rows, upd_rows;
     int rw_rows, fin_rows;
 };
@@ -164,6 +165,8 @@ struct TileRec {
     int sblk0, sgx, sgy;
     int vblk0, vgx, vgy;       // direction kernel's blocks
     int ublk0, ugy;            // update kernel's blocks (same columns, its own rows per block)
+    int rblk0, rgy;            // reweighting kernel's blocks (same columns, a.rw_rows rows)
+    int fblk0, fgy;            // finalize kernel's blocks (same columns, a.fin_rows rows)
 };
 
 // Tensor-core preconditioner of a batched solve, with the DCT bases cached per distinct side
@@ -219,6 +222,10 @@ int stencil_grid_blocks(int H, int W);
 // 2 reweighting, 3 finalize) on an H x W image a whole number of waves on the current device,
 // between kMinTileRows and `max_rows` (0 when no count in that range does)
 int wave_rows(int kernel, int H, int W, int max_rows);
+// rows per block of the reweighting (kernel 2) or finalize (kernel 3) launch for an H x W image:
+// the whole-wave count up to 32 rows, else kDefaultUpdRows.  A single-image plan and a batch
+// both take it, so that they sum in the same order.
+int aux_rows(int kernel, int H, int W);
 // adjoint sweep (reverse over the outer steps)
 cudaError_t launch_record_step(DevState* st, cudaStream_t s);
 cudaError_t launch_adj_init(const Planes& P, const StencilArgs& a, const float* dLdU, DevState* st,
@@ -244,14 +251,13 @@ void strip_dims(int H, int W, int& gx, int& gy);
 void vec_dims(int H, int W, int dir_rows, int upd_rows, int& gx, int& gy_dir, int& gy_upd);
 cudaError_t launch_init_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
 cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total_strip, cudaStream_t s);
-cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_upd, int rows,
-                                    cudaStream_t s);
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_rw, cudaStream_t s);
 cudaError_t launch_direction_batched(const TileRec* recs, int T, int total_vec, int rows,
                                      cudaStream_t s);
 cudaError_t launch_update_batched(const TileRec* recs, int T, int total_upd, int rows,
                                   cudaStream_t s);
-cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, int total_upd,
-                                    int rows, cudaStream_t s);
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total_strip, int total_fin,
+                                    cudaStream_t s);
 cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStream_t s);
 
 // ---- DCT preconditioner (dct.cu) ------------------------------------------------------------

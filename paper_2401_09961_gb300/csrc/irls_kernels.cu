@@ -969,10 +969,17 @@ k_adj_final(Planes P, StencilArgs a, const float* __restrict__ Gbv, const float*
 // own coordinates, state and scratch.
 // ------------------------------------------------------------------------------------------
 // grid of a batched launch: the strip kernels, the direction kernel, the update kernel
-enum GridKind : int { GK_STRIP = 0, GK_DIR = 1, GK_UPD = 2 };
+// and the reweighting and finalize kernels (the direction kernel's columns, their own rows)
+enum GridKind : int { GK_STRIP = 0, GK_DIR = 1, GK_UPD = 2, GK_RW = 3, GK_FIN = 4 };
 
 __device__ __forceinline__ int grid_blk0(const TileRec& r, int kind) {
-    return kind == GK_STRIP ? r.sblk0 : (kind == GK_DIR ? r.vblk0 : r.ublk0);
+    switch (kind) {
+        case GK_STRIP: return r.sblk0;
+        case GK_DIR: return r.vblk0;
+        case GK_UPD: return r.ublk0;
+        case GK_RW: return r.rblk0;
+        default: return r.fblk0;
+    }
 }
 
 __device__ __forceinline__ int find_tile(const TileRec* __restrict__ r, int T, int bid, int kind) {
@@ -987,7 +994,8 @@ __device__ __forceinline__ int find_tile(const TileRec* __restrict__ r, int T, i
 __device__ __forceinline__ Blk tile_blk(const TileRec& r, int bid, int kind) {
     Blk b;
     const int gx = kind == GK_STRIP ? r.sgx : r.vgx;
-    const int gy = kind == GK_STRIP ? r.sgy : (kind == GK_DIR ? r.vgy : r.ugy);
+    const int gy = kind == GK_STRIP ? r.sgy : kind == GK_DIR ? r.vgy : kind == GK_UPD ? r.ugy
+                 : kind == GK_RW ? r.rgy : r.fgy;
     const int local = bid - grid_blk0(r, kind);
     b.bx = local % gx;
     b.by = local / gx;
@@ -1007,10 +1015,11 @@ __global__ void __launch_bounds__(kThreads) kb_bnorm(const TileRec* __restrict__
     k_bnorm_body(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_STRIP));
 }
 
-template <int ROWS>
+// the reweighting and finalize kernels run each image with its own row count (a.rw_rows,
+// a.fin_rows: the same function of the image's size as in a single-image plan)
 __global__ void __launch_bounds__(kThreads) kb_reweight(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_UPD)];
-    k_reweight_residual_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_RW)];
+    k_reweight_residual_body<0>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_RW));
 }
 
 template <int ROWS>
@@ -1025,10 +1034,9 @@ __global__ void __launch_bounds__(kThreads) kb_update(const TileRec* __restrict_
     k_update_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
 }
 
-template <int ROWS>
 __global__ void __launch_bounds__(kThreads) kb_finalize(const TileRec* __restrict__ recs, int T) {
-    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_UPD)];
-    k_finalize_reduce_body<ROWS>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_UPD));
+    const TileRec& r = recs[find_tile(recs, T, blockIdx.x, GK_FIN)];
+    k_finalize_reduce_body<0>(r.P, r.a, r.st, r.partials, tile_blk(r, blockIdx.x, GK_FIN));
 }
 
 __global__ void __launch_bounds__(kThreads) kb_subtract_mean(const TileRec* __restrict__ recs, int T) {
@@ -1489,15 +1497,8 @@ cudaError_t launch_bnorm_batched(const TileRec* recs, int T, int total, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_upd, int rows,
-                                    cudaStream_t s) {
-    switch (rows) {
-        case 8: kb_reweight<8><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 16: kb_reweight<16><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 24: kb_reweight<24><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 32: kb_reweight<32><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_reweight_batched(const TileRec* recs, int T, int total_rw, cudaStream_t s) {
+    kb_reweight<<<total_rw, kThreads, 0, s>>>(recs, T);
     return cudaGetLastError();
 }
 
@@ -1525,15 +1526,9 @@ cudaError_t launch_update_batched(const TileRec* recs, int T, int total, int row
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total, int total_upd,
-                                    int rows, cudaStream_t s) {
-    switch (rows) {
-        case 8: kb_finalize<8><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 16: kb_finalize<16><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 24: kb_finalize<24><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        case 32: kb_finalize<32><<<total_upd, kThreads, 0, s>>>(recs, T); break;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_finalize_batched(const TileRec* recs, int T, int total, int total_fin,
+                                    cudaStream_t s) {
+    kb_finalize<<<total_fin, kThreads, 0, s>>>(recs, T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     kb_subtract_mean<<<total, kThreads, 0, s>>>(recs, T);
@@ -1568,6 +1563,11 @@ int wave_rows(int kernel, int H, int W, int max_rows) {
         return r;
     }
     return 0;
+}
+
+int aux_rows(int kernel, int H, int W) {
+    const int r = wave_rows(kernel, H, W, 32);
+    return r ? r : kDefaultUpdRows;
 }
 
 int stencil_grid_blocks(int H, int W) {
