@@ -72,7 +72,9 @@ extern "C" {
                              * complex FFT of the same length in float32 on the CUDA cores
                              * (three passes over a float32 plane per application; r_U^T z_U
                              * from the spectrum by Parseval); needs precision IRLS_PREC_FP32,
-                             * H a power of two in [64, 8192] and W one in [64, 16384];
+                             * H a power of two in [64, 8192] or one of 2000, 4000, 8000, and
+                             * W a power of two in [64, 16384] or one of 2000, 4000, 8000,
+                             * 16000 (the 4000 x M sizes; radix-5 stages);
                              * single-image plans only (batches: IRLS_ERR_UNSUPPORTED).  Not
                              * in the paper, which forms the dense products                      */
 

@@ -16,7 +16,8 @@
 // in registers between the stage's two barriers.  Row blocks load their two rows with 16-byte
 // loads and store every element straight to its slot of the even/odd reordering; column blocks
 // copy their strip in by 16-byte asynchronous copies in its natural order and fold the
-// reordering into the first stage's reads.  Lengths are powers of two.
+// reordering into the first stage's reads.  Lengths: powers of two, and 2000, 4000, 8000, 16000
+// (radix-5 stages after the radix-2^k ones).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -134,6 +135,26 @@ __device__ __forceinline__ void dft<16>(float2* v) {
     }
 }
 
+// Length 5: X_0 = v_0 + t1 + t2, X_{1,4} = a1 -/+ i b1, X_{2,3} = a2 -/+ i b2 with
+// t1 = v1 + v4, t2 = v2 + v3, a1 = v0 + c1 t1 + c2 t2, a2 = v0 + c2 t1 + c1 t2,
+// b1 = s1 (v1 - v4) + s2 (v2 - v3), b2 = s2 (v1 - v4) - s1 (v2 - v3), c_k + i s_k = exp(2 pi i k / 5).
+constexpr float kC51 = 0.30901699437494745f, kC52 = -0.80901699437494734f;
+constexpr float kS51 = 0.95105651629515353f, kS52 = 0.58778525229247325f;
+template <>
+__device__ __forceinline__ void dft<5>(float2* v) {
+    const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    const float2 a1 = make_float2(v[0].x + kC51 * t1.x + kC52 * t2.x, v[0].y + kC51 * t1.y + kC52 * t2.y);
+    const float2 a2 = make_float2(v[0].x + kC52 * t1.x + kC51 * t2.x, v[0].y + kC52 * t1.y + kC51 * t2.y);
+    const float2 b1 = make_float2(kS51 * t3.x + kS52 * t4.x, kS51 * t3.y + kS52 * t4.y);
+    const float2 b2 = make_float2(kS52 * t3.x - kS51 * t4.x, kS52 * t3.y - kS51 * t4.y);
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = make_float2(a1.x + b1.y, a1.y - b1.x);   // a1 - i b1
+    v[4] = make_float2(a1.x - b1.y, a1.y + b1.x);   // a1 + i b1
+    v[2] = make_float2(a2.x + b2.y, a2.y - b2.x);
+    v[3] = make_float2(a2.x - b2.y, a2.y + b2.x);
+}
+
 // ---- shared-memory layouts of NF complex sequences of length N ------------------------------
 // Pair: element m of transform f as one float2 (row 2f, row 2f + 1), one float2 of padding
 // every 16 (the stages' strided accesses and the reordered stores of the load fall on distinct
@@ -199,10 +220,17 @@ __device__ __forceinline__ float2 twiddle(const float2* tws, int e) {
     return cmul(tws[e & 63], tws[64 + (e >> 6)]);
 }
 
-// Copies the two-level twiddle table of length N (64 + N / 64 entries) into shared memory.
+// Entries of the two-level twiddle table of length N: 64 low and ceil(N / 64) high.
+template <int N>
+struct TwN {
+    static constexpr int V = 64 + (N + 63) / 64;
+    static constexpr int PADDED = (V + 1) & ~1;   // a 16-byte multiple
+};
+
+// Copies the two-level twiddle table of length N into shared memory.
 template <int N, int T>
 __device__ __forceinline__ void load_twiddles(float2* tws, const float2* __restrict__ tw) {
-    for (int e = threadIdx.x; e < 64 + N / 64; e += T)
+    for (int e = threadIdx.x; e < TwN<N>::V; e += T)
         tws[e] = e < 64 ? __ldg(&tw[e]) : __ldg(&tw[(e - 64) * 64]);
 }
 
@@ -214,7 +242,9 @@ template <class L, int N, int NF, int T, int NS, bool REORD>
 __device__ __forceinline__ void fft_stages(float* s, const float2* tws) {
     if constexpr (NS < N) {
         constexpr int REM = N / NS;
-        constexpr int R = (REM % 16 == 0) ? 16 : (REM % 8 == 0) ? 8 : (REM % 4 == 0) ? 4 : 2;
+        constexpr int R = (REM % 16 == 0) ? 16 : (REM % 8 == 0) ? 8 : (REM % 4 == 0) ? 4
+                        : (REM % 2 == 0) ? 2 : 5;
+        static_assert(REM % R == 0, "lengths of the form 2^a 5^b");
         constexpr int NJ = N / R;                 // butterflies per transform
         constexpr int NB = NJ * NF;               // butterflies per stage
         constexpr int PER = (NB + T - 1) / T;     // butterflies per thread
@@ -321,17 +351,17 @@ __device__ __forceinline__ void dct2_pair(float2 Z, float2 Zc, float2 t, float c
 template <int N>
 struct RowCfg {
     static constexpr int NF = (4096 / N) < 1 ? 1 : ((4096 / N) > 16 ? 16 : 4096 / N);
-    static constexpr int T = N * NF / 16;
+    static constexpr int T = (N * NF / 16 + 31) / 32 * 32;   // whole warps
     using L = PairL<N, NF>;
-    static constexpr size_t SMEM = (size_t)L::FLOATS * sizeof(float) + (64 + N / 64) * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)L::FLOATS * sizeof(float) + TwN<N>::PADDED * sizeof(float2);
     static constexpr int WANT = 4;          // blocks per SM the carve-out is sized for
 };
 template <int N>
 struct ColCfg {
     static constexpr int NF = (2048 / N) < 2 ? 2 : ((2048 / N) > 16 ? 16 : 2048 / N);
-    static constexpr int T = N * NF / 16;
+    static constexpr int T = (N * NF / 16 + 31) / 32 * 32;   // whole warps
     using L = StripL<N, NF>;
-    static constexpr int TWN = 64 + ((N / 64 + 1) & ~1);   // twiddle table, 16-byte multiple
+    static constexpr int TWN = TwN<N>::PADDED;             // twiddle table, 16-byte multiple
     static constexpr int TTN = N / 2 + 2;                  // exp(-i pi k / 2N), k <= N/2
     static constexpr size_t SMEM = (size_t)L::FLOATS * sizeof(float) +
                                    (size_t)(TWN + TTN) * sizeof(float2) + (size_t)N * sizeof(float);
@@ -353,9 +383,9 @@ k_fftdct_rows_fwd(const float* __restrict__ R, float* __restrict__ Tout, int H, 
     float2* tws = reinterpret_cast<float2*>(sm + L::FLOATS);
     load_twiddles<N, T>(tws, tw);
     const int row0 = blockIdx.x * 2 * NF;
-    // four 16-byte pieces of each of the two rows a thread (all loads first), every element
+    // up to four 16-byte pieces of each of the two rows a thread (all loads first), every element
     // stored straight to its slot of the even/odd reordering
-    static_assert(NF * Q == 4 * T, "four pieces per thread");
+    static_assert(NF * Q <= 4 * T, "four pieces per thread at most");
     float4 va[4], vb[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -363,12 +393,14 @@ k_fftdct_rows_fwd(const float* __restrict__ R, float* __restrict__ Tout, int H, 
         const int f = it / Q, n = (it % Q) * 4;
         const int ra = row0 + 2 * f, rb = ra + 1;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        va[u] = ra < H ? __ldg(reinterpret_cast<const float4*>(R + (size_t)ra * ld + n)) : z4;
-        vb[u] = rb < H ? __ldg(reinterpret_cast<const float4*>(R + (size_t)rb * ld + n)) : z4;
+        const bool in = it < NF * Q;
+        va[u] = in && ra < H ? __ldg(reinterpret_cast<const float4*>(R + (size_t)ra * ld + n)) : z4;
+        vb[u] = in && rb < H ? __ldg(reinterpret_cast<const float4*>(R + (size_t)rb * ld + n)) : z4;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int it = threadIdx.x + u * T;
+        if (NF * Q < 4 * T && it >= NF * Q) continue;
         const int f = it / Q, n = (it % Q) * 4;
         L::st(sm, f, reorder_pos<N>(n), make_float2(va[u].x, vb[u].x));
         L::st(sm, f, reorder_pos<N>(n + 1), make_float2(va[u].y, vb[u].y));
@@ -384,7 +416,7 @@ k_fftdct_rows_fwd(const float* __restrict__ R, float* __restrict__ Tout, int H, 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int k = k0 + c;
-            dct2_coeffs(L::ld(sm, f, k), L::ld(sm, f, (N - k) & (N - 1)), __ldg(&tt[k]),
+            dct2_coeffs(L::ld(sm, f, k), L::ld(sm, f, (k == 0 ? 0 : N - k)), __ldg(&tt[k]),
                         dct_c<N>(k) * tau, xa[c], xb[c]);
         }
         if (ra < H)
@@ -428,7 +460,7 @@ k_fftdct_cols(float* __restrict__ Tio, int W, int ld, float tau, const float* __
     constexpr int NK = N / 2 + 1;
     for (int it = threadIdx.x; it < NF * NK; it += T) {
         const int f = it % NF, k = it / NF;
-        const int kc = (N - k) & (N - 1);
+        const int kc = (k == 0 ? 0 : N - k);
         const int ja = j0 + 2 * f, jb = ja + 1;
         const float2 t = stt[k];
         const float ck = dct_c<N>(k), cc = dct_c<N>(kc);
@@ -492,7 +524,7 @@ k_fftdct_rows_inv(const float* __restrict__ Tin, float* __restrict__ Z, int H, i
     float2* tws = reinterpret_cast<float2*>(sm + L::FLOATS);
     load_twiddles<N, T>(tws, tw);
     const int row0 = blockIdx.x * 2 * NF;
-    static_assert(NF * Q == 4 * T, "four pieces per thread");
+    static_assert(NF * Q <= 4 * T, "four pieces per thread at most");
     float4 va[4], vb[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -500,12 +532,14 @@ k_fftdct_rows_inv(const float* __restrict__ Tin, float* __restrict__ Z, int H, i
         const int f = it / Q, k = (it % Q) * 4;
         const int ra = row0 + 2 * f, rb = ra + 1;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        va[u] = ra < H ? *reinterpret_cast<const float4*>(Tin + (size_t)ra * ld + k) : z4;
-        vb[u] = rb < H ? *reinterpret_cast<const float4*>(Tin + (size_t)rb * ld + k) : z4;
+        const bool in = it < NF * Q;
+        va[u] = in && ra < H ? *reinterpret_cast<const float4*>(Tin + (size_t)ra * ld + k) : z4;
+        vb[u] = in && rb < H ? *reinterpret_cast<const float4*>(Tin + (size_t)rb * ld + k) : z4;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int it = threadIdx.x + u * T;
+        if (NF * Q < 4 * T && it >= NF * Q) continue;
         const int f = it / Q, k = (it % Q) * 4;
         L::st(sm, f, k, make_float2(va[u].x, vb[u].x));
         L::st(sm, f, k + 1, make_float2(va[u].y, vb[u].y));
@@ -516,7 +550,7 @@ k_fftdct_rows_inv(const float* __restrict__ Tin, float* __restrict__ Z, int H, i
     constexpr int NK = N / 2 + 1;
     for (int it = threadIdx.x; it < NF * NK; it += T) {
         const int f = it % NF, k = it / NF;
-        const int kc = (N - k) & (N - 1);
+        const int kc = (k == 0 ? 0 : N - k);
         const float2 xk = L::ld(sm, f, k), xc = L::ld(sm, f, kc);
         const float ck = dct_c<N>(k), cc = dct_c<N>(kc);
         inv_pair<L, N>(sm, f, k, ck * xk.x, ck * xk.y, cc * xc.x, cc * xc.y, __ldg(&tt[k]));
@@ -546,6 +580,15 @@ __global__ void k_build_fft_tables(float2* tw, float2* tt, int N) {
 }
 
 bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+// Lengths compiled in besides the powers of two: 2^a 5^3 (radix-5 stages after the radix-2^k
+// ones), the sides of the 4000 x M images of the paper's size study.
+bool row_len_ok(int n) {
+    return pow2_in(n, kFftMinN, kFftMaxRowN) || n == 2000 || n == 4000 || n == 8000 || n == 16000;
+}
+bool col_len_ok(int n) {
+    return pow2_in(n, kFftMinN, kFftMaxColN) || n == 2000 || n == 4000 || n == 8000;
+}
 
 // Dynamic shared memory of a launch, and a carve-out that holds `want` blocks per SM (the rest
 // of the SM's 256 KB stays L1, which keeps the twiddle table).
@@ -598,7 +641,7 @@ int col_nf(int H) { return std::max(2, std::min(16, 2048 / H)); }
 }  // namespace
 
 bool fft_dct_supported(int H, int W) {
-    return pow2_in(H, kFftMinN, kFftMaxColN) && pow2_in(W, kFftMinN, kFftMaxRowN);
+    return col_len_ok(H) && row_len_ok(W);
 }
 
 size_t fft_dct_bytes(int H, int W) {
@@ -638,7 +681,8 @@ cudaError_t fft_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, 
     case n: e = rows_fwd<n>(rU, T, H, ld, d.tau, d.fftTwM, d.fftTtM, st, skip_if_done, s); break;
         IRLS_FFT_ROWS(64) IRLS_FFT_ROWS(128) IRLS_FFT_ROWS(256) IRLS_FFT_ROWS(512)
         IRLS_FFT_ROWS(1024) IRLS_FFT_ROWS(2048) IRLS_FFT_ROWS(4096) IRLS_FFT_ROWS(8192)
-        IRLS_FFT_ROWS(16384)
+        IRLS_FFT_ROWS(16384) IRLS_FFT_ROWS(2000) IRLS_FFT_ROWS(4000) IRLS_FFT_ROWS(8000)
+        IRLS_FFT_ROWS(16000)
 #undef IRLS_FFT_ROWS
         default: break;
     }
@@ -652,6 +696,7 @@ cudaError_t fft_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, 
         break;
         IRLS_FFT_COLS(64) IRLS_FFT_COLS(128) IRLS_FFT_COLS(256) IRLS_FFT_COLS(512)
         IRLS_FFT_COLS(1024) IRLS_FFT_COLS(2048) IRLS_FFT_COLS(4096) IRLS_FFT_COLS(8192)
+        IRLS_FFT_COLS(2000) IRLS_FFT_COLS(4000) IRLS_FFT_COLS(8000)
 #undef IRLS_FFT_COLS
         default: break;
     }
@@ -662,7 +707,8 @@ cudaError_t fft_dct_apply(const DctPlan& d, const float* rU, float* zU, int ld, 
     case n: e = rows_inv<n>(T, zU, H, ld, d.fftTwM, d.fftTtM, st, skip_if_done, s); break;
         IRLS_FFT_ROWS(64) IRLS_FFT_ROWS(128) IRLS_FFT_ROWS(256) IRLS_FFT_ROWS(512)
         IRLS_FFT_ROWS(1024) IRLS_FFT_ROWS(2048) IRLS_FFT_ROWS(4096) IRLS_FFT_ROWS(8192)
-        IRLS_FFT_ROWS(16384)
+        IRLS_FFT_ROWS(16384) IRLS_FFT_ROWS(2000) IRLS_FFT_ROWS(4000) IRLS_FFT_ROWS(8000)
+        IRLS_FFT_ROWS(16000)
 #undef IRLS_FFT_ROWS
         default: break;
     }

@@ -8,7 +8,7 @@ numpy float64 and checked against the oracle's dense DCT basis and preconditione
   * the fused step per frequency pair (k, N-k): one complex product per sequence gives both
     coefficients, the division by the eigenvalues, and one product per sequence gives both
     inverse spectra; the inverse sum by a forward FFT of the conjugate;
-  * the Stockham auto-sort stage formula with radix 16, 8, 4, 2 stages;
+  * the Stockham auto-sort stage formula with radix 16, 8, 4, 2 and 5 stages;
   * the shared-memory layouts: every map is a bijection, and the access patterns of a stage fall
     on distinct banks (the swizzled column strip and the padded pair layout)."""
 import numpy as np
@@ -20,7 +20,8 @@ from oracle import irls as O
 def radices(n):
     rs = []
     while n > 1:
-        r = 16 if n % 16 == 0 else 8 if n % 8 == 0 else 4 if n % 4 == 0 else 2
+        r = 16 if n % 16 == 0 else 8 if n % 8 == 0 else 4 if n % 4 == 0 else 2 if n % 2 == 0 \
+            else 5
         rs.append(r)
         n //= r
     return rs
@@ -61,13 +62,13 @@ def ck(n):
     return c
 
 
-@pytest.mark.parametrize("n", [2, 16, 64, 128, 256, 2048])
+@pytest.mark.parametrize("n", [2, 16, 64, 128, 256, 2048, 2000, 4000])
 def test_stockham_stages_are_the_dft(n):
     x = np.random.default_rng(n).standard_normal(n) + 1j * np.random.default_rng(n + 1).standard_normal(n)
     assert np.allclose(stockham(x), np.fft.fft(x), atol=1e-10 * np.sqrt(n))
 
 
-@pytest.mark.parametrize("n", [64, 128, 512])
+@pytest.mark.parametrize("n", [64, 128, 512, 2000])
 def test_dct2_of_two_sequences_by_one_fft(n):
     P = O.dct_basis(n)[0]
     rng = np.random.default_rng(n)

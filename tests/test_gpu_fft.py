@@ -71,9 +71,42 @@ def test_fft_precond_large(irls, H, W):
     assert np.abs(Z - z_ref).max() <= 2e-5 * np.abs(z_ref).max() and rel2 <= 1e-5, rel2
 
 
+@pytest.mark.parametrize("H,W", [(4000, 2000), (2000, 4000), (8000, 64), (64, 16000),
+                                 (4000, 16000)])
+def test_fft_precond_composite_lengths(irls, H, W):
+    """The lengths 2^a 5^3 (2000, 4000, 8000, 16000: radix-5 stages after the radix-2^k ones),
+    the sides of the paper's 4000 x M images, against the float64 DCT reference."""
+    from test_gpu_parity import precond_reference_fft
+    R = np.random.default_rng(H + 5 * W).standard_normal((H, W)).astype(np.float32)
+    with irls.Plan(H, W, tau=1e-2, precision="fp32", dct_form="fft") as plan:
+        assert plan.dct_form_name == "fft"
+        Z = irls.precond_laplacian(plan, cuda(R)).cpu().numpy().astype(np.float64)
+    z_ref = precond_reference_fft(R, 1e-2)
+    rel2 = np.linalg.norm(Z - z_ref) / np.linalg.norm(z_ref)
+    assert np.abs(Z - z_ref).max() <= 2e-5 * np.abs(z_ref).max() and rel2 <= 1e-5, rel2
+
+
+def test_fft_unwrap_4000x2000_first_outer_matches_oracle(irls):
+    """4000 x 2000 (composite lengths), one outer step truncated at 4 CG iterations, element by
+    element against the oracle (the form's relative error, about 1e-6, is far inside 1e-3)."""
+    from test_gpu_parity import assert_unwrap_parity
+    d = synthetic.config_4096_mixed(seed=40, H=4000, W=2000)
+    kw = dict(tau=1e-2, delta=1e-3, outer_iters=1, cg_tol=1e-6, cg_max=4)
+    ref = O.irls_unwrap(d["X"], d["coherence"], **kw)
+    with irls.Plan(4000, 2000, precision="fp32", dct_form="fft", tau=1e-2, delta=1e-3,
+                   outer_iters=1, cg_tol=1e-6, cg_max_iter=4) as p:
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+    assert st["cg_iters"] == [4]
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
+                         atol=1e-3, ref=ref, case="4000x2000 fp32 (fft) 1 step x 4 CG",
+                         truncated=True)
+
+
 def test_fft_form_only_where_allowed(irls):
-    """Power-of-two sides in range and float32 only; batches do not take it."""
-    for H, W in ((100, 128), (128, 100), (32, 64), (16384, 64), (64, 32768)):
+    """Power-of-two sides in range (and the compiled-in 2^a 5^3 lengths) and float32 only;
+    batches do not take it."""
+    for H, W in ((100, 128), (128, 100), (32, 64), (16384, 64), (64, 32768), (3000, 2000),
+                 (16000, 64)):
         with pytest.raises(irls.IrlsError):
             irls.Plan(H, W, precision="fp32", dct_form="fft")
     with pytest.raises(irls.IrlsError):
