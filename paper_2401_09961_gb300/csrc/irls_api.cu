@@ -179,6 +179,7 @@ struct irls_plan_s {
     int schedule_stop = 0;
     int dir_rows = 0, upd_rows = 0;   // stencil tile shapes (0: the defaults)
     int rw_rows = 0, fin_rows = 0;    // reweighting and finalize rows (aux_rows of H, W)
+    int sdir_rows = 0, supd_rows = 0; // U-only direction and update rows (whole waves, or 0)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     Profiler prof;
 };
@@ -227,6 +228,8 @@ StencilArgs make_args(const irls_plan_s* p) {
     // size that a batch uses as well (so both sum in the same order)
     a.rw_rows = p->rw_rows;
     a.fin_rows = p->fin_rows;
+    a.sdir_rows = p->sdir_rows;
+    a.supd_rows = p->supd_rows;
     return a;
 }
 
@@ -705,6 +708,8 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
         p->H = H; p->W = W; p->ld = row_pitch(W);
         p->rw_rows = aux_rows(2, H, W);
         p->fin_rows = aux_rows(3, H, W);
+        p->sdir_rows = wave_rows(4, H, W, 32);
+        p->supd_rows = wave_rows(5, H, W, 32);
         p->opts = o;
         p->prec_alloc = o.precision;
         p->L = layout(H, W, o.precision);

@@ -113,6 +113,7 @@ struct StencilArgs {
     // they dispatch)
     int dir_rows, upd_rows;
     int rw_rows, fin_rows;
+    int sdir_rows, supd_rows;   // U-only system's direction and update kernels (0: 24)
 };
 
 // Image rows per block the CG direction and update kernels are built for, and the defaults
@@ -219,7 +220,7 @@ cudaError_t launch_emit16(const float* src, int H, int W, int ld, void* r16, voi
                          cudaStream_t s);
 int stencil_grid_blocks(int H, int W);
 // rows per block that make a launch of the single-image kernel (0 direction, 1 update,
-// 2 reweighting, 3 finalize) on an H x W image a whole number of waves on the current device,
+// 2 reweighting, 3 finalize, 4 and 5 the U-only system's direction and update) on an H x W image a whole number of waves on the current device,
 // between kMinTileRows and `max_rows` (0 when no count in that range does)
 int wave_rows(int kernel, int H, int W, int max_rows);
 // rows per block of the reweighting (kernel 2) or finalize (kernel 3) launch for an H x W image:

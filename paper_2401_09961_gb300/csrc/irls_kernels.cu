@@ -1220,7 +1220,8 @@ k_schur_direction(Planes P, StencilArgs a, DevState* st, double* partials) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.sdir_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float tau = a.tau;
     const int cur = st->pbuf, nxt = cur ^ 1;
@@ -1323,7 +1324,8 @@ k_schur_update(Planes P, StencilArgs a, DevState* st, double* partials) {
     const int H = a.H, W = a.W, ld = a.ld;
     const int j0 = (blk.bx * kThreads + threadIdx.x) * kVec;
     const int lane = threadIdx.x & 31;
-    const int i0 = blk.by * ROWS, i1 = min(i0 + ROWS, H);
+    const int R = ROWS > 0 ? ROWS : a.supd_rows;   // 0: the row count of the launch's arguments
+    const int i0 = blk.by * R, i1 = min(i0 + R, H);
     const bool act = j0 < W;
     const float tau = a.tau;
     const int cur = st->pbuf;
@@ -1541,10 +1543,12 @@ cudaError_t launch_count_active(const DevState* states, int T, int* out, cudaStr
 }
 
 int wave_rows(int kernel, int H, int W, int max_rows) {
-    static const void* const fn[4] = {(const void*)k_direction_pap<0>, (const void*)k_update<0>,
+    static const void* const fn[6] = {(const void*)k_direction_pap<0>, (const void*)k_update<0>,
                                       (const void*)k_reweight_residual<0>,
-                                      (const void*)k_finalize_reduce<0>};
-    if (kernel < 0 || kernel > 3 || H < 1 || W < 1) return 0;
+                                      (const void*)k_finalize_reduce<0>,
+                                      (const void*)k_schur_direction<0>,
+                                      (const void*)k_schur_update<0>};
+    if (kernel < 0 || kernel > 5 || H < 1 || W < 1) return 0;
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -1677,17 +1681,26 @@ cudaError_t launch_schur_reweight(const Planes& P, const StencilArgs& a, DevStat
     return cudaGetLastError();
 }
 
+// U-only CG kernels: the plan's whole-wave row counts (a.sdir_rows, a.supd_rows), else 24 rows
 cudaError_t launch_schur_direction(const Planes& P, const StencilArgs& a, DevState* st,
                                    double* partials, cudaStream_t s) {
-    k_schur_direction<kSchurRows><<<vec_grid(a.H, a.W, kSchurRows), kThreads, 0, s>>>(P, a, st,
-                                                                                      partials);
+    const int rows = plan_rows_ok(a.sdir_rows) ? a.sdir_rows : kSchurRows;
+    if (rows == kSchurRows)
+        k_schur_direction<kSchurRows><<<vec_grid(a.H, a.W, rows), kThreads, 0, s>>>(P, a, st,
+                                                                                   partials);
+    else
+        k_schur_direction<0><<<vec_grid(a.H, a.W, rows), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_schur_update(const Planes& P, const StencilArgs& a, DevState* st,
                                 double* partials, cudaStream_t s) {
-    k_schur_update<kSchurRows><<<vec_grid(a.H, a.W, kSchurRows), kThreads, 0, s>>>(P, a, st,
-                                                                                   partials);
+    const int rows = plan_rows_ok(a.supd_rows) ? a.supd_rows : kSchurRows;
+    if (rows == kSchurRows)
+        k_schur_update<kSchurRows><<<vec_grid(a.H, a.W, rows), kThreads, 0, s>>>(P, a, st,
+                                                                                partials);
+    else
+        k_schur_update<0><<<vec_grid(a.H, a.W, rows), kThreads, 0, s>>>(P, a, st, partials);
     return cudaGetLastError();
 }
 
