@@ -304,11 +304,13 @@ def main():
                     help="preconditioner form (auto: folded where allowed; fft: fast transforms "
                          "in float32, with --precision fp32)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "tiled"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "tiled", "adjoint"],
                     help="single: one 4096 x 4096 image per step (the benchmark); batched: 64 "
                          "tiles with sides in {256, ..., 1536} per step, one batched solve; "
                          "tiled: one --size x --width image cut into overlapping tiles solved "
-                         "as one batch and stitched")
+                         "as one batch and stitched; adjoint: the 1024 x 1024 15-step forward "
+                         "with its checkpoints and the adjoint sweep (dL/dX, dL/dcoherence)")
     ap.add_argument("--tile", type=int, default=1024, help="tile side of --workload tiled")
     ap.add_argument("--overlap", type=int, default=64, help="tile overlap of --workload tiled")
     ap.add_argument("--outer", type=int, default=OUTER,
@@ -337,6 +339,8 @@ def main():
         return batched_arm(args, rank, world, local)
     if args.workload == "tiled":
         return tiled_arm(args, rank, world, local)
+    if args.workload == "adjoint":
+        return adjoint_arm(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
@@ -742,6 +746,79 @@ def tiled_arm(args, rank, world, local):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def adjoint_arm(args, rank, world, local):
+    """The differentiation workload: a 1024 x 1024 image of the adjoint law (ramp 0-200 rad, 20
+    bumps, coherence weights), 15 IRLS steps recorded with their checkpoints, then the adjoint
+    sweep for L = sum (U - mean U - U_ref)^2, U_ref the noise-free phase.  One step = forward
+    with checkpoints + adjoint sweep, timed with CUDA events; the split-bf16 folded form, with
+    the float32 dense and fast-transform forms measured after it (not part of `value`)."""
+    import torch
+    from paper_2401_09961_gb300.autograd import unwrap_backward, unwrap_record
+    import paper_2401_09961_gb300 as irls
+    import synthetic
+    torch.cuda.set_device(local)
+    n = 1024
+    d = synthetic.config_adjoint_1024(seed=30 + rank)
+    X = torch.as_tensor(d["X"]).cuda()
+    C = torch.as_tensor(d["coherence"]).cuda()
+    Uref = torch.as_tensor((d["phi_true"] - d["phi_true"].mean()).astype(np.float32)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def run(plan):
+        U, tape, st = unwrap_record(plan, X, C)
+        e_mid = torch.cuda.Event(enable_timing=True)
+        e_mid.record(stream)
+        dX, dc, sb = unwrap_backward(tape, 2.0 * (U - U.mean() - Uref))
+        tape.free()
+        return e_mid, st, sb, dX
+
+    def measure(kw, steps, warmup):
+        with irls.Plan(n, n, tau=TAU, delta=DELTA, outer_iters=15, cg_tol=CG_TOL,
+                       cg_max_iter=1000, **kw) as p:
+            for _ in range(warmup):
+                run(p)
+            torch.cuda.synchronize()
+            fwd = bwd = 0.0
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                e_mid, st, sb, dX = run(p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                fwd += e0.elapsed_time(e_mid)
+                bwd += e_mid.elapsed_time(e1)
+            return {"form": p.dct_form_name, "forward_s": fwd / steps / 1e3,
+                    "adjoint_s": bwd / steps / 1e3,
+                    "mpix_s": n * n / 1e6 / ((fwd + bwd) / steps / 1e3),
+                    "cg_forward": st["cg_total"], "cg_adjoint": sb["cg_total"],
+                    "dldx_sum": float(dX.sum().item())}
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.mark()
+    head = measure(dict(precision="bf16x3"), args.steps, args.warmup)
+    clk = clocks.stop()
+    others = {}
+    if not args.no_forms:
+        others["fp32_dense"] = measure(dict(precision="fp32"), 1, 0)
+        others["fp32_fft"] = measure(dict(precision="fp32", dct_form="fft"), args.steps, 1)
+    if rank == 0:
+        out = {
+            "metric": "Mpix/s per forward (15 IRLS steps, checkpointed) + adjoint sweep at 1024^2",
+            "value": head["mpix_s"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * (head["forward_s"] + head["adjoint_s"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16x3-tensor-core-dct", "data": "synthetic",
+            "config": {"workload": "1024x1024 adjoint law (ramp 0-200 rad, 20 bumps, noise 0.5 "
+                                   "rad, coherence weights), 15 IRLS steps, delta 1e-3, tau 1e-2, "
+                                   f"cg_tol {CG_TOL:g}; L = sum (U - mean U - U_ref)^2",
+                       **head},
+            "forms": others or None,
+            "clocks": clk,
+        }
+        print(json.dumps(out))
 
 
 def reference_arm(args, rank, world, n, prec):
