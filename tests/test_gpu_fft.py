@@ -200,3 +200,39 @@ def test_fft_and_dense_float32_forms_reach_the_same_unwrap(irls):
     assert k_agreement(Uf, Ua, d["X"]) >= 0.999
     assert abs(sa["cg_total"] - sf["cg_total"]) <= 0.02 * sa["cg_total"], (sa["cg_total"],
                                                                             sf["cg_total"])
+
+
+def test_fft_paper_schedule_matches_oracle(irls):
+    """The CG budget and IRLS stop of Sec. 4.3 with the fast-transform preconditioner: the same
+    caps and stop as the oracle (whose Delta values sit at least 4.5e-4 from eps_tol on this
+    image), and U within the measured spread of valid executions (preconditioner output rounded
+    at 5e-7 relative, the form's measured rounding)."""
+    from test_gpu_parity import assert_unwrap_parity, parity_atol
+    from test_gpu_schedule import check_rule, schedule_envelope
+    d = synthetic.config_2048(seed=29, H=128, W=64)
+    kw = dict(tau=1e-2, delta=0.05, outer_iters=60, cg_tol=1e-8, cg_max=1000,
+              cg_schedule="paper")
+    ref, env = schedule_envelope(d["X"], d["coherence"], kw, 5e-7)
+    assert ref["schedule_stop"] and max(ref["cg_cap"]) > 5
+    assert all(abs(x - 1e-3) > 2e-5 for x in ref["delta_rel"])
+    with irls.Plan(128, 64, precision="fp32", dct_form="fft", tau=1e-2, delta=0.05,
+                   outer_iters=60, cg_tol=1e-8, cg_schedule="paper") as p:
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+    assert st["cg_cap"] == ref["cg_cap"] and st["schedule_stop"] == ref["schedule_stop"]
+    check_rule(st)
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
+                         atol=parity_atol(env), ref=ref, env=env,
+                         case="128x64 Sec. 4.3 CG schedule fp32 (fft)")
+
+
+def test_fft_flexible_ratio_matches_oracle(irls):
+    """The Polak-Ribiere ratio with the fast-transform preconditioner, on the determined
+    trajectory (cg_tol 1e-8), at the strict bars."""
+    from test_gpu_parity import assert_unwrap_parity, determined_reference
+    d, ref = determined_reference("mixed", 256, 256, 12, 4)
+    with irls.Plan(256, 256, precision="fp32", dct_form="fft", flexible_cg=1, tau=1e-2,
+                   delta=1e-3, outer_iters=4, cg_tol=1e-8, cg_max_iter=3000) as p:
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+    assert st["return_code"] == 0
+    assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
+                         ref=ref, strict=True, case="256x256 mixed-law fp32 (fft, flexible) tol 1e-8")
