@@ -235,9 +235,10 @@ __device__ __forceinline__ void load_twiddles(float2* tws, const float2* __restr
 }
 
 // Stockham stages of NF forward complex FFTs of length N in shared memory (layout L), from the
-// stage whose sub-transforms have length NS; tws is the two-level table of exp(-2 pi i m / N).  Thread t takes
-// butterflies t, t + T, ... (the transform index varies fastest).  With REORD the first stage reads its inputs through the
-// even/odd reordering.  Every stage reads, waits at a barrier, then writes over its inputs.
+// stage whose sub-transforms have length NS; tws is the two-level table of exp(-2 pi i m / N).
+// Thread t takes butterflies t, t + T, ... (the transform index varies fastest).  With REORD
+// the first stage reads its inputs through the even/odd reordering.  Every stage reads, waits
+// at a barrier, then writes over its inputs.
 template <class L, int N, int NF, int T, int NS, bool REORD>
 __device__ __forceinline__ void fft_stages(float* s, const float2* tws) {
     if constexpr (NS < N) {
