@@ -592,7 +592,8 @@ bool col_len_ok(int n) {
 }
 
 // Dynamic shared memory of a launch, and a carve-out that holds `want` blocks per SM (the rest
-// of the SM's 256 KB stays L1, which keeps the twiddle table).
+// of the SM's 256 KB stays L1).  Set before every launch: a host call of about a microsecond,
+// and still right after the device's state was reset.
 template <class K>
 cudaError_t prepare(K k, size_t smem, int want) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
