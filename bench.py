@@ -768,9 +768,10 @@ def adjoint_arm(args, rank, world, local):
 
     def run(plan):
         U, tape, st = unwrap_record(plan, X, C)
+        dLdU = 2.0 * (U - U.mean() - Uref)
         e_mid = torch.cuda.Event(enable_timing=True)
         e_mid.record(stream)
-        dX, dc, sb = unwrap_backward(tape, 2.0 * (U - U.mean() - Uref))
+        dX, dc, sb = unwrap_backward(tape, dLdU)
         tape.free()
         return e_mid, st, sb, dX
 
