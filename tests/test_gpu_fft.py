@@ -236,3 +236,23 @@ def test_fft_flexible_ratio_matches_oracle(irls):
     assert st["return_code"] == 0
     assert_unwrap_parity(U.cpu().numpy(), ref["U"], st["l1_obj"][-1], ref["l1_obj"][-1], d["X"],
                          ref=ref, strict=True, case="256x256 mixed-law fp32 (fft, flexible) tol 1e-8")
+
+
+@pytest.mark.parametrize("H,W", [(8192, 8192), (4000, 16000)])
+def test_fft_large_solve_invariants(irls, H, W):
+    """The largest column length (8192) and the composite 4000 x 16000 in a full solve of three
+    outer steps: the monotone quantities of Sec. 3.1 hold on the device statistics, U has zero
+    mean, the solve reports no error, and the L1 objective falls."""
+    d = synthetic.config_4096_mixed(seed=43, H=H, W=W)
+    with irls.Plan(H, W, precision="fp32", dct_form="fft", delta=1e-3, outer_iters=3,
+                   cg_tol=1e-6) as p:
+        assert p.dct_form_name == "fft"
+        U, st = p.unwrap(cuda(d["X"]), cuda(d["coherence"]))
+    assert st["return_code"] in (0, 1)
+    f, h = st["f_delta"], st["h_delta"]
+    for k in range(len(h)):
+        assert h[k] <= f[k] * (1 + 1e-5)
+        if k + 1 < len(f):
+            assert f[k + 1] <= h[k] * (1 + 1e-5)
+    assert st["l1_obj"][-1] < st["l1_obj"][0]
+    assert abs(float(U.double().mean())) < 1e-3
