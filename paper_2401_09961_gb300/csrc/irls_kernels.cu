@@ -186,8 +186,8 @@ __device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4]) 
 }
 
 
-// Start of an outer step (see the comment above emit16), on float4 lanes with the update
-// kernel's block shape: a thread owns four columns; the horizontal neighbour of its last column
+// Start of an outer step (see the comment above emit16), on float4 lanes (the update kernel's
+// columns per block, rows a.rw_rows): a thread owns four columns; the horizontal neighbour of its last column
 // comes from the next lane (lane 31 loads it), the horizontal edge left of its first column from
 // the previous lane (lane 0 recomputes it).  Padding columns (>= W) get no W, D or r.
 template <int ROWS>
@@ -619,9 +619,9 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
 // End of an outer step: sum U (for U -= mean(U), Prop. 'minimising (alt1)'), the objective of
 // problem (main) and H_delta(x^{k+1}, W^k) of problem (alt1); then record the statistics.
 // ------------------------------------------------------------------------------------------
-// On float4 lanes with the update kernel's block shape.  Per edge in float32: the difference
-// U_{i+1} - U_i and its residual e = (U_{i+1} - U_i) - G are formed with two-sums, so e is exact
-// up to one rounding of itself; C |e| and the H_delta term are each one or two roundings of
+// On float4 lanes (the update kernel's columns per block, rows a.fin_rows).  Per edge in
+// float32: the difference U_{i+1} - U_i and its residual e = (U_{i+1} - U_i) - G are formed with
+// two-sums, so e is exact up to one rounding of itself; C |e| and the H_delta term are each one or two roundings of
 // themselves, and all sums are compensated per thread, then FP64 across threads.
 __device__ __forceinline__ float edge_residual(float un, float u, float g) {
     float d, dl, e, el;
