@@ -621,8 +621,9 @@ k_update(Planes P, StencilArgs a, DevState* st, double* partials) {
 // ------------------------------------------------------------------------------------------
 // On float4 lanes (the update kernel's columns per block, rows a.fin_rows).  Per edge in
 // float32: the difference U_{i+1} - U_i and its residual e = (U_{i+1} - U_i) - G are formed with
-// two-sums, so e is exact up to one rounding of itself; C |e| and the H_delta term are each one or two roundings of
-// themselves, and all sums are compensated per thread, then FP64 across threads.
+// two-sums, so e is exact up to one rounding of itself; C |e| and the H_delta term are each one
+// or two roundings of themselves, and all sums are compensated per thread, then FP64 across
+// threads.
 __device__ __forceinline__ float edge_residual(float un, float u, float g) {
     float d, dl, e, el;
     two_sum(un, -u, d, dl);
