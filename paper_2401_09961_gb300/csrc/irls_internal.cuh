@@ -224,7 +224,7 @@ int stencil_grid_blocks(int H, int W);
 // between kMinTileRows and `max_rows` (0 when no count in that range does)
 int wave_rows(int kernel, int H, int W, int max_rows);
 // rows per block of the reweighting (kernel 2) or finalize (kernel 3) launch for an H x W image:
-// the whole-wave count up to 32 rows, else kDefaultUpdRows.  A single-image plan and a batch
+// the count of the fewest whole waves up to kMaxTileRows rows, else kDefaultUpdRows.  A single-image plan and a batch
 // both take it, so that they sum in the same order.
 int aux_rows(int kernel, int H, int W);
 // adjoint sweep (reverse over the outer steps)

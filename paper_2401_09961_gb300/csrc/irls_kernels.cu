@@ -1571,7 +1571,7 @@ int wave_rows(int kernel, int H, int W, int max_rows) {
 }
 
 int aux_rows(int kernel, int H, int W) {
-    const int r = wave_rows(kernel, H, W, 32);
+    const int r = wave_rows(kernel, H, W, kMaxTileRows);
     return r ? r : kDefaultUpdRows;
 }
 
