@@ -177,8 +177,9 @@ int irls_plan_dct_form(irls_plan plan);
  * the block decomposition, so results change within rounding (the reductions' summation order
  * follows the blocks), never the method.  irls_plan_set_tiles sets them (0 keeps a value;
  * anything outside 8..64 is IRLS_ERR_ARG); irls_plan_get_tiles reads the values in use.
- * irls_plan_autotune times, for each kernel, 8, 16, 24 and 32 rows and the row count that makes
- * the kernel's launch a whole number of waves on this device (when that count is another one),
+ * irls_plan_autotune times, for each kernel, 8, 16, 24 and 32 rows and the row counts that make
+ * the kernel's launch the fewest whole waves on this device with at most 32 and at most 64 rows
+ * a block (when those counts are other ones),
  * on the plan's workspace (ten launches each, after two warm-up launches, CUDA events on
  * `stream`), and keeps the fastest; h_ms (NULL allowed) receives eight mean times in ms:
  * direction for 8, 16, 24, 32 rows, then update.  It overwrites the plan's scratch planes and

@@ -708,8 +708,8 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
         p->H = H; p->W = W; p->ld = row_pitch(W);
         p->rw_rows = aux_rows(2, H, W);
         p->fin_rows = aux_rows(3, H, W);
-        p->sdir_rows = wave_rows(4, H, W, 32);
-        p->supd_rows = wave_rows(5, H, W, 32);
+        p->sdir_rows = wave_rows(4, H, W, kMaxTileRows);
+        p->supd_rows = wave_rows(5, H, W, kMaxTileRows);
         p->opts = o;
         p->prec_alloc = o.precision;
         p->L = layout(H, W, o.precision);
@@ -819,17 +819,22 @@ int irls_plan_autotune(irls_plan p, float* h_ms, void* stream) {
         a.tol2 = -1.0;
         a.cap_warn = 0;
         constexpr int kWarm = 2, kReps = 10;
-        // candidates: the fixed row counts, then for each kernel the count that makes its
-        // launch a whole number of waves (if it is not one of them)
-        int cand[2][5];
+        // candidates: the fixed row counts, then for each kernel the counts that make its
+        // launch the fewest whole waves with at most 32 and at most 64 rows a block (where they
+        // are not among the others)
+        int cand[2][6];
         int ncand[2];
         for (int k = 0; k < 2; ++k) {
             for (int i = 0; i < 4; ++i) cand[k][i] = kTileRows[i];
             ncand[k] = 4;
-            const int w = wave_rows(k, p->H, p->W, 32);
-            if (w && w != 8 && w != 16 && w != 24 && w != 32) cand[k][ncand[k]++] = w;
+            for (int cap : {32, kMaxTileRows}) {
+                const int w = wave_rows(k, p->H, p->W, cap);
+                bool seen = (w == 0);
+                for (int i = 0; i < ncand[k]; ++i) seen |= (cand[k][i] == w);
+                if (!seen) cand[k][ncand[k]++] = w;
+            }
         }
-        float ms[2][5];
+        float ms[2][6];
         for (int k = 0; k < 2; ++k)
             for (int i = 0; i < ncand[k]; ++i) {
                 StencilArgs b = a;
