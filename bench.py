@@ -258,8 +258,9 @@ def measure_forms(d, X, C, timed_unwraps=2):
             "s_per_batch": t, "mpix_s": mpix / t, "batches_timed": timed_unwraps,
             "mpix_per_batch": mpix, "cg_iters_total": sum(x["cg_total"] for x in st)}
     out["_note"] = ("same image and options as the headline (one warm-up, then CUDA-event "
-                    "timing), stencil tiles at their defaults (the headline's are autotuned); "
-                    "the batch is the 64-tile uneven-size workload; l1_fp64 is the objective of "
+                    "timing), single-image forms at the default stencil tiles (the headline's "
+                    "and the batch's are autotuned); the batch is the 64-tile uneven-size "
+                    "workload; l1_fp64 is the objective of "
                     "problem (main) evaluated in FP64 on each result")
     return out
 
