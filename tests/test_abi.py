@@ -129,6 +129,10 @@ def test_new_entry_points_reject_null_handles(L):
     h = ctypes.c_void_p()
     o = _binding.default_opts(precision="fp16")
     assert L.irls_batch_create(1, H, W, ctypes.byref(o), ctypes.byref(h)) == -8
+    # and so are fast-transform batches (single-image plans only), in either precision
+    for prec in ("bf16x3", "fp32"):
+        o = _binding.default_opts(precision=prec, dct_form="fft")
+        assert L.irls_batch_create(1, H, W, ctypes.byref(o), ctypes.byref(h)) == -8, prec
 
 
 def test_header_constants_match_the_binding():
