@@ -701,6 +701,10 @@ int irls_plan_create(int H, int W, const irls_opts* opts, irls_plan* out) {
     if (opts) o = *opts;
     if (!opts_valid(o)) return IRLS_ERR_ARG;
     if (!shape_valid(H, W)) return IRLS_ERR_SHAPE;
+    // the fast-transform form's precision and lengths are known before any device work
+    if (o.dct_form == IRLS_DCT_FFT &&
+        (o.precision != IRLS_PREC_FP32 || !fft_dct_supported(H, W)))
+        return IRLS_ERR_UNSUPPORTED;
     irls_plan_s* p = new (std::nothrow) irls_plan_s();
     if (!p) return IRLS_ERR_OOM;
     try {

@@ -129,6 +129,11 @@ def test_new_entry_points_reject_null_handles(L):
     h = ctypes.c_void_p()
     o = _binding.default_opts(precision="fp16")
     assert L.irls_batch_create(1, H, W, ctypes.byref(o), ctypes.byref(h)) == -8
+    # fast-transform plans of a shape or precision the form does not take are refused first too
+    for (Hh, Ww, prec) in ((100, 128, "fp32"), (128, 100, "fp32"), (16384, 64, "fp32"),
+                           (64, 32768, "fp32"), (3000, 2000, "fp32"), (256, 256, "bf16x3")):
+        o = _binding.default_opts(precision=prec, dct_form="fft")
+        assert L.irls_plan_create(Hh, Ww, ctypes.byref(o), ctypes.byref(h)) == -8, (Hh, Ww, prec)
     # and so are fast-transform batches (single-image plans only), in either precision
     for prec in ("bf16x3", "fp32"):
         o = _binding.default_opts(precision=prec, dct_form="fft")
